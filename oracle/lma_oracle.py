@@ -1,0 +1,605 @@
+"""Plain FP64 CPU oracle for the Lattice Multislice Algorithm (LMA) hot path.
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module. The CUDA library never
+calls it and shares no code, table or constant with it.
+
+Everything is numpy float64 / complex128, written for a reader who checks it
+against the paper by eye: no blocking, no fusion, no reordering. Library
+primitives used as steps: ``numpy.fft`` (DFT), ``numpy.linalg.lstsq`` (least
+squares), ``numpy.lexsort`` (ordering).
+
+Conventions (fixed here because the paper leaves them open):
+  * arrays are indexed [y, x]; pixel j sits at j*dx, periodic boundaries
+    (Sec. 3.1: the simulation domain is periodic because of the DFT);
+  * frequencies are in FFT order, k_m = m'/(n*d) with m' = m for m < n/2 else
+    m - n; this is the paper's centred g(k) of Sec. 4.1 after an fftshift;
+  * the forward DFT is unnormalised with kernel exp(-2 pi i k.x), the inverse
+    carries 1/n^2 (numpy's convention);
+  * the bandlimit mask keeps (m'/nx)^2 + (n'/ny)^2 <= (frac/2)^2 (2/3 of
+    Nyquist by default). The paper does not discuss anti-aliasing; the mask is
+    applied in the propagation step only;
+  * the detector collects r1 <= lambda*|k| < r2 on the detection window,
+    intersected with the same bandlimit mask (eq. for 2D STEM, Sec. 3.1).
+
+Parity pins for every function live in ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+from typing import Dict, List, Sequence, Tuple
+
+import numpy as np
+
+# CODATA 2018 exact / recommended values (SI).
+_H = 6.62607015e-34
+_C = 299792458.0
+_M0 = 9.1093837015e-31
+_E = 1.602176634e-19
+
+
+# ----------------------------------------------------------------------------
+# electron optics constants
+# ----------------------------------------------------------------------------
+
+def electron_wavelength(voltage: float) -> float:
+    """Relativistic electron wavelength in Angstrom for an accelerating voltage in V.
+
+    lambda = h c / sqrt(E (2 m0 c^2 + E)), E = e V. The paper quotes
+    lambda = 0.0250793 A for 200 kV (captions of the Sec. 4.2.3 figures).
+    """
+    energy = _E * voltage
+    mc2 = _M0 * _C * _C
+    return _H * _C / math.sqrt(energy * (2.0 * mc2 + energy)) * 1e10
+
+
+def interaction_constant(voltage: float) -> float:
+    """Beam-sample interaction constant sigma of eq. schroedinger_equation, rad/(V*A).
+
+    sigma = 2 pi / (lambda V) * (m0 c^2 + E) / (2 m0 c^2 + E).
+    """
+    energy = _E * voltage
+    mc2 = _M0 * _C * _C
+    lam = electron_wavelength(voltage)
+    return 2.0 * math.pi / (lam * voltage) * (mc2 + energy) / (2.0 * mc2 + energy)
+
+
+def gaussian_width(lam: float, alpha_max: float) -> float:
+    """Gaussian input-wave width sigma = lambda / (2 alpha_max) (Sec. 4.2.3, Gaussians)."""
+    return lam / (2.0 * alpha_max)
+
+
+# ----------------------------------------------------------------------------
+# grids and transforms
+# ----------------------------------------------------------------------------
+
+def signed_index(n: int) -> np.ndarray:
+    """m' for m = 0..n-1 in FFT order (m' = m for m < n/2, else m - n)."""
+    m = np.arange(n)
+    return np.where(m < (n + 1) // 2, m, m - n)
+
+
+def freqs(n: int, d: float) -> np.ndarray:
+    """Spatial frequencies k_m = m' / (n d) in FFT order (1/Angstrom)."""
+    return signed_index(n) / (n * d)
+
+
+def dft2(a: np.ndarray) -> np.ndarray:
+    """Unnormalised forward 2D DFT with kernel exp(-2 pi i k.x)."""
+    return np.fft.fft2(a)
+
+
+def idft2(a: np.ndarray) -> np.ndarray:
+    """Inverse 2D DFT with the 1/(nx ny) factor."""
+    return np.fft.ifft2(a)
+
+
+def k_squared(ny: int, nx: int, dy: float, dx: float) -> np.ndarray:
+    """|k|^2 on the [ny, nx] frequency grid."""
+    ky = freqs(ny, dy)[:, None]
+    kx = freqs(nx, dx)[None, :]
+    return ky * ky + kx * kx
+
+
+def bandlimit_mask(ny: int, nx: int, frac: float) -> np.ndarray:
+    """Circular bandlimit: (m'/nx)^2 + (n'/ny)^2 <= (frac/2)^2, decided in FP64.
+
+    For a square n-point window and frac = 2/3 this is 9 (m'^2 + n'^2) <= n^2.
+    """
+    my = signed_index(ny)[:, None] / ny
+    mx = signed_index(nx)[None, :] / nx
+    if ny == nx:
+        # exact integer form for square windows: 4 (m'^2 + n'^2) <= frac^2 n^2
+        iy = signed_index(ny)[:, None].astype(np.int64)
+        ix = signed_index(nx)[None, :].astype(np.int64)
+        return (4 * (iy * iy + ix * ix)).astype(np.float64) <= frac * frac * nx * nx
+    return my * my + mx * mx <= 0.25 * frac * frac
+
+
+# ----------------------------------------------------------------------------
+# physics model (Sec. 3.1 and Sec. 3.2)
+# ----------------------------------------------------------------------------
+
+def aberration(k2: np.ndarray, lam: float, cs: float, defocus: float) -> np.ndarray:
+    """chi(k) = 1/2 pi Cs lambda^3 |k|^4 - pi Z lambda |k|^2 (eq. aberration_function)."""
+    return 0.5 * math.pi * cs * lam ** 3 * k2 * k2 - math.pi * defocus * lam * k2
+
+
+def aperture(k2: np.ndarray, lam: float, alpha_max: float) -> np.ndarray:
+    """A(k) = 1 iff lambda |k| < alpha_max (eq. aperture_function, strict)."""
+    return (lam * np.sqrt(k2) < alpha_max).astype(np.float64)
+
+
+def probe(ny: int, nx: int, dy: float, dx: float, lam: float, alpha_max: float,
+          cs: float = 0.0, defocus: float = 0.0, p: Tuple[float, float] = (0.0, 0.0)
+          ) -> np.ndarray:
+    """STEM probe psi_p^init on the full periodic grid (eq. probe_wave_function).
+
+    Fourier values exp(-i chi) A mu_{-p}, mu_p(k) = exp(2 pi i k.p) (Sec. 4.1),
+    inverse DFT, then normalised so that sum |psi|^2 = 1. ``p`` = (py, px) in
+    Angstrom.
+    """
+    k2 = k_squared(ny, nx, dy, dx)
+    ky = freqs(ny, dy)[:, None]
+    kx = freqs(nx, dx)[None, :]
+    spec = np.exp(-1j * aberration(k2, lam, cs, defocus)) * aperture(k2, lam, alpha_max)
+    spec = spec * np.exp(-2j * math.pi * (ky * p[0] + kx * p[1]))
+    psi = idft2(spec)
+    return psi / math.sqrt(float(np.sum(np.abs(psi) ** 2)))
+
+
+def fresnel_propagator(ny: int, nx: int, dy: float, dx: float, lam: float, dz: float,
+                       frac: float | None) -> np.ndarray:
+    """Fourier-space propagation factor for one slice of thickness dz.
+
+    The propagation term of eq. schroedinger_equation, d psi/dz = (i lambda/4pi)
+    Laplacian psi, becomes d psi^/dz = -i pi lambda |k|^2 psi^ for the forward
+    DFT exp(-2 pi i k.x); over dz this is exp(-i pi lambda dz |k|^2), the DFT of
+    the real-space kernel q of Sec. 3.2. Multiplied by the bandlimit mask when
+    ``frac`` is given.
+    """
+    prop = np.exp(-1j * math.pi * lam * dz * k_squared(ny, nx, dy, dx))
+    if frac is not None:
+        prop = prop * bandlimit_mask(ny, nx, frac)
+    return prop
+
+
+def projected_potential(x: np.ndarray, y: np.ndarray, slc: np.ndarray, species: np.ndarray,
+                        n_slices: int, ny: int, nx: int, ly: float, lx: float,
+                        peak: Sequence[float], term_frac: Sequence[float],
+                        term_width: Sequence[float], r_cut: float) -> np.ndarray:
+    """Projected potential v_s(x) per slice (V*A) on the periodic grid.
+
+    v_s(x_j) = sum over atoms a of slice s, over periodic images with r < r_cut,
+    of peak[species(a)] * sum_t term_frac[t] exp(-r^2 / (2 term_width[t]^2)).
+    The integral over the slice of Sec. 3.2 (v_eps) is given directly as this
+    Gaussian-sum model.
+    """
+    dx = lx / nx
+    dy = ly / ny
+    v = np.zeros((n_slices, ny, nx), dtype=np.float64)
+    jx_lo_off = int(math.ceil(r_cut / dx)) + 1
+    jy_lo_off = int(math.ceil(r_cut / dy)) + 1
+    for a in range(x.shape[0]):
+        xa, ya, s = float(x[a]), float(y[a]), int(slc[a])
+        # unwrapped pixel indices around the atom: each one is one (pixel, image) pair
+        cx = int(math.floor(xa / dx))
+        cy = int(math.floor(ya / dy))
+        jx = np.arange(cx - jx_lo_off, cx + jx_lo_off + 1)
+        jy = np.arange(cy - jy_lo_off, cy + jy_lo_off + 1)
+        rx = jx * dx - xa
+        ry = jy * dy - ya
+        r2 = ry[:, None] ** 2 + rx[None, :] ** 2
+        inside = r2 < r_cut * r_cut
+        val = np.zeros_like(r2)
+        for f, w in zip(term_frac, term_width):
+            val += f * np.exp(-r2 / (2.0 * w * w))
+        val = np.where(inside, float(peak[int(species[a])]) * val, 0.0)
+        np.add.at(v[s], (np.mod(jy, ny)[:, None], np.mod(jx, nx)[None, :]), val)
+    return v
+
+
+def transmission(v: np.ndarray, sigma: float) -> np.ndarray:
+    """t = exp(i sigma v_eps) (Sec. 3.2)."""
+    return np.exp(1j * sigma * v)
+
+
+def multislice(psi: np.ndarray, t: Sequence[np.ndarray], prop: np.ndarray) -> np.ndarray:
+    """Standard multislice (Fig. multislice_pseudocode): for each slice, transmit then propagate."""
+    psi = np.array(psi, dtype=np.complex128)
+    for ts in t:
+        psi = psi * ts
+        psi = idft2(prop * dft2(psi))
+    return psi
+
+
+def periodic_crop(a: np.ndarray, oy: int, ox: int, h: int, w: int) -> np.ndarray:
+    """a[(oy + 0..h-1) mod ny, (ox + 0..w-1) mod nx] (last two axes)."""
+    ny, nx = a.shape[-2], a.shape[-1]
+    iy = np.mod(oy + np.arange(h), ny)
+    ix = np.mod(ox + np.arange(w), nx)
+    return a[..., iy[:, None], ix[None, :]]
+
+
+def detector_mask(n: int, dy: float, dx: float, lam: float, r1: float, r2: float,
+                  frac: float | None) -> np.ndarray:
+    """Pixels of an n x n window with r1 <= lambda |k| < r2, intersected with the bandlimit."""
+    ang = lam * np.sqrt(k_squared(n, n, dy, dx))
+    m = (ang >= r1) & (ang < r2)
+    if frac is not None:
+        m &= bandlimit_mask(n, n, frac)
+    return m
+
+
+def detect(psi: np.ndarray, mask: np.ndarray) -> float:
+    """2D STEM reading (Sec. 3.1): (1/n^2) sum over the detector of |DFT(psi)|^2.
+
+    With a unit-norm probe this is the fraction of the incident intensity that
+    reaches the detector.
+    """
+    spec = dft2(psi)
+    return float(np.sum(np.abs(spec[mask]) ** 2) / psi.size)
+
+
+# ----------------------------------------------------------------------------
+# LMA geometry (Sec. 4.2.1, 4.2.2)
+# ----------------------------------------------------------------------------
+
+def input_lattice(nx: int, ny: int, spacing: Tuple[int, int], offset: Tuple[int, int],
+                  f: int) -> np.ndarray:
+    """Pixel positions of I_f (Sec. 4.2.1, option (i)), shape (R_y/f * R_x/f, 2) as (x, y).
+
+    I = {a r_x e1 + b r_y e2 + I_offset}, with R_x r_x = X covering the periodic
+    domain, and I_f keeps every f-th point in both directions. Raster order:
+    index = b * (R_x/f) + a.
+    """
+    sx, sy = spacing
+    if nx % sx or ny % sy:
+        raise ValueError("input lattice does not cover the grid")
+    rx, ry = nx // sx, ny // sy
+    if rx % f or ry % f:
+        raise ValueError("R must be a multiple of f")
+    a = np.arange(rx // f)
+    b = np.arange(ry // f)
+    xs = (offset[0] + a * f * sx) % nx
+    ys = (offset[1] + b * f * sy) % ny
+    out = np.empty((ys.size * xs.size, 2), dtype=np.int64)
+    out[:, 0] = np.tile(xs, ys.size)
+    out[:, 1] = np.repeat(ys, xs.size)
+    return out
+
+
+def min_image(d: np.ndarray, n: int) -> np.ndarray:
+    """Signed minimum-image offset in [-n/2, n/2)."""
+    return np.mod(d + n // 2, n) - n // 2
+
+
+def nearest_translates(p: Tuple[int, int], lattice: np.ndarray, L: int, nx: int, ny: int
+                       ) -> Tuple[np.ndarray, np.ndarray]:
+    """I_{f,p,L}: the L input waves closest to p (Sec. 4.2.1, option (iii)).
+
+    Distance is the periodic minimum-image distance. Ties are broken by
+    (distance^2, dy, dx) ascending on the signed offsets. Returns (indices into
+    ``lattice``, offsets (L, 2) as (dx, dy) in pixels).
+    """
+    if L > lattice.shape[0]:
+        raise ValueError("L exceeds |I_f|")
+    ddx = min_image(lattice[:, 0] - p[0], nx)
+    ddy = min_image(lattice[:, 1] - p[1], ny)
+    d2 = ddx * ddx + ddy * ddy
+    order = np.lexsort((ddx, ddy, d2))[:L]
+    return order, np.stack([ddx[order], ddy[order]], axis=1)
+
+
+def class_key(p: Tuple[int, int], spacing: Tuple[int, int], offset: Tuple[int, int], f: int
+              ) -> Tuple[int, int]:
+    """Position of p relative to the I_f lattice; probes with equal keys share coefficients.
+
+    Case 1 (R = cP) gives a single key, Case 2 (P = cR) gives c*d keys
+    (eqs. lma_approximation_exit1 / exit2).
+    """
+    return ((p[0] - offset[0]) % (f * spacing[0]), (p[1] - offset[1]) % (f * spacing[1]))
+
+
+def input_wave_window(kind: int, W: int, ny: int, nx: int, dy: float, dx: float, lam: float,
+                      alpha_max: float, cs: float, defocus: float, gauss_sigma: float
+                      ) -> np.ndarray:
+    """The input wave u sampled on a W x W window with its centre at window pixel (W/2, W/2).
+
+    kind 0: Gaussian g_sigma (Sec. 4.2.3, Gaussians), sigma = lambda/(2 alpha_max)
+    unless given; kind 1: the probe itself, u = psi_0^init (Sec. 4.2.3).
+    Offsets from the centre run over [-W/2, W/2), taken periodically on the
+    full grid.
+    """
+    off = np.arange(W) - W // 2
+    if kind == 0:
+        s = gauss_sigma if gauss_sigma > 0 else gaussian_width(lam, alpha_max)
+        ry = off * dy
+        rx = off * dx
+        r2 = ry[:, None] ** 2 + rx[None, :] ** 2
+        return np.exp(-r2 / (2.0 * s * s)).astype(np.complex128)
+    if kind == 1:
+        p0 = probe(ny, nx, dy, dx, lam, alpha_max, cs, defocus)
+        return periodic_crop(p0, -(W // 2), -(W // 2), W, W)
+    raise ValueError("unknown input wave kind")
+
+
+def embed_window(wave: np.ndarray, oy: int, ox: int, ny: int, nx: int) -> np.ndarray:
+    """Place a W x W window wave with origin (oy, ox) on the full periodic grid (zeros elsewhere)."""
+    full = np.zeros((ny, nx), dtype=np.complex128)
+    W = wave.shape[0]
+    iy = np.mod(oy + np.arange(W), ny)
+    ix = np.mod(ox + np.arange(W), nx)
+    full[iy[:, None], ix[None, :]] += wave
+    return full
+
+
+@dataclass
+class CoefficientSet:
+    alpha: np.ndarray        # (L,) complex128
+    offsets: np.ndarray      # (L, 2) int (dx, dy) of each translate relative to the probe
+    err_l2: float            # relative Euclidean error of the probe approximation
+    err_sup: float           # relative supremum error
+
+
+def coefficients(psi0: np.ndarray, uW: np.ndarray, offsets: np.ndarray) -> CoefficientSet:
+    """Least-squares coefficients for one probe (eqs. lma_approximation_exit1_0 / exit2_0).
+
+    Relative coordinates: the probe ``psi0`` is centred at pixel (0, 0) of the
+    full periodic grid and translate j sits at ``offsets[j]``; its window is
+    [offset - W/2, offset + W/2). Solves min_alpha ||psi0 - sum_j alpha_j u_j||_2
+    over the whole grid.
+    """
+    ny, nx = psi0.shape
+    W = uW.shape[0]
+    cols = [embed_window(uW, int(o[1]) - W // 2, int(o[0]) - W // 2, ny, nx).ravel()
+            for o in offsets]
+    A = np.stack(cols, axis=1)
+    b = psi0.ravel()
+    alpha = np.linalg.lstsq(A, b, rcond=None)[0]
+    approx = A @ alpha
+    err_l2 = float(np.linalg.norm(b - approx) / np.linalg.norm(b))
+    err_sup = float(np.max(np.abs(b - approx)) / np.max(np.abs(b)))
+    return CoefficientSet(alpha=alpha, offsets=np.asarray(offsets, dtype=np.int64),
+                          err_l2=err_l2, err_sup=err_sup)
+
+
+# ----------------------------------------------------------------------------
+# LMA steps (Fig. lma_pseudocode)
+# ----------------------------------------------------------------------------
+
+def translate_exit_wave(uW: np.ndarray, t_full: np.ndarray, prop_W: np.ndarray,
+                        pos: Tuple[int, int]) -> np.ndarray:
+    """Step 1 for one input wave: multislice of u_i on its W x W window.
+
+    The window is [i - W/2, i + W/2) of the periodic grid (option (ii)); the
+    slices of ``t_full`` are cropped to it.
+    """
+    W = uW.shape[0]
+    ts = periodic_crop(t_full, pos[1] - W // 2, pos[0] - W // 2, W, W)
+    return multislice(uW, ts, prop_W)
+
+
+def synthesize(U: Sequence[np.ndarray], alpha: np.ndarray, offsets: np.ndarray, D: int,
+               cyclic: bool) -> np.ndarray:
+    """Step 2: Psi_p = sum_j alpha_j U_{i_j} on the D x D window centred at p.
+
+    U_{i_j} has its own window [i_j - W/2, i_j + W/2); relative to the probe
+    window [p - D/2, p + D/2) it is shifted by offsets[j] + (D - W)/2 and
+    truncated to the probe window. When the windows are the whole periodic grid
+    (``cyclic``) the placement is a cyclic shift.
+    """
+    psi = np.zeros((D, D), dtype=np.complex128)
+    for Uj, a, o in zip(U, alpha, offsets):
+        W = Uj.shape[0]
+        sx = int(o[0]) + (D - W) // 2
+        sy = int(o[1]) + (D - W) // 2
+        if cyclic:
+            psi += a * np.roll(Uj, shift=(sy, sx), axis=(0, 1))
+            continue
+        y0, y1 = max(0, sy), min(D, sy + W)
+        x0, x1 = max(0, sx), min(D, sx + W)
+        if y0 < y1 and x0 < x1:
+            psi[y0:y1, x0:x1] += a * Uj[y0 - sy:y1 - sy, x0 - sx:x1 - sx]
+    return psi
+
+
+@dataclass
+class LmaParams:
+    nx: int
+    ny: int
+    lx: float
+    ly: float
+    slice_dz: float
+    n_slices: int
+    lam: float
+    sigma: float
+    bandlimit_frac: float
+    alpha_max: float
+    cs: float
+    defocus: float
+    kind: int
+    gauss_sigma: float
+    in_spacing: Tuple[int, int]
+    in_offset: Tuple[int, int]
+    f: int
+    L: int
+    W: int
+    D: int
+
+    @property
+    def dx(self) -> float:
+        return self.lx / self.nx
+
+    @property
+    def dy(self) -> float:
+        return self.ly / self.ny
+
+    @property
+    def cyclic(self) -> bool:
+        return self.W == self.nx and self.W == self.ny and self.D == self.W
+
+
+class LmaOracle:
+    """The LMA image pipeline of Fig. lma_pseudocode in FP64.
+
+    Construct with the grid, probe and basis parameters; call ``image`` with
+    per-phonon atom lists, the potential model, detectors and probe positions.
+    Exit waves are cached per (phonon, translate) so that sampled probes share
+    propagations.
+    """
+
+    def __init__(self, prm: LmaParams):
+        self.prm = prm
+        p = prm
+        self.lattice = input_lattice(p.nx, p.ny, p.in_spacing, p.in_offset, p.f)
+        self.uW = input_wave_window(p.kind, p.W, p.ny, p.nx, p.dy, p.dx, p.lam, p.alpha_max,
+                                    p.cs, p.defocus, p.gauss_sigma)
+        self.prop_W = fresnel_propagator(p.W, p.W, p.dy, p.dx, p.lam, p.slice_dz,
+                                         p.bandlimit_frac)
+        self._psi0 = None
+        self._sets: Dict[Tuple[int, int], CoefficientSet] = {}
+        self._t: Dict[int, np.ndarray] = {}
+        self._U: Dict[Tuple[int, int], np.ndarray] = {}
+
+    # -- coefficients -------------------------------------------------------
+    @property
+    def psi0(self) -> np.ndarray:
+        if self._psi0 is None:
+            p = self.prm
+            self._psi0 = probe(p.ny, p.nx, p.dy, p.dx, p.lam, p.alpha_max, p.cs, p.defocus)
+        return self._psi0
+
+    def coefficient_set(self, p: Tuple[int, int]) -> Tuple[CoefficientSet, np.ndarray]:
+        """Coefficients for probe pixel p and the lattice indices of its L translates."""
+        prm = self.prm
+        key = class_key(p, prm.in_spacing, prm.in_offset, prm.f)
+        idx, offs = nearest_translates(p, self.lattice, prm.L, prm.nx, prm.ny)
+        if key not in self._sets:
+            self._sets[key] = coefficients(self.psi0, self.uW, offs)
+        cs = self._sets[key]
+        if not np.array_equal(cs.offsets, offs):
+            raise AssertionError("coefficient reuse broken: offsets differ inside a class")
+        return cs, idx
+
+    # -- specimen -----------------------------------------------------------
+    def set_specimen(self, phonons: Sequence, peak, term_frac, term_width, r_cut):
+        self._phonons = list(phonons)
+        self._pot = (tuple(peak), tuple(term_frac), tuple(term_width), float(r_cut))
+        self._t.clear()
+        self._U.clear()
+
+    def transmission_stack(self, phi: int) -> np.ndarray:
+        if phi not in self._t:
+            p = self.prm
+            at = self._phonons[phi]
+            peak, tf, tw, rc = self._pot
+            v = projected_potential(at.x, at.y, at.slice, at.species, p.n_slices, p.ny, p.nx,
+                                    p.ly, p.lx, peak, tf, tw, rc)
+            self._t[phi] = transmission(v, p.sigma)
+        return self._t[phi]
+
+    def exit_wave(self, phi: int, i: int) -> np.ndarray:
+        if (phi, i) not in self._U:
+            pos = (int(self.lattice[i, 0]), int(self.lattice[i, 1]))
+            self._U[(phi, i)] = translate_exit_wave(self.uW, self.transmission_stack(phi),
+                                                    self.prop_W, pos)
+        return self._U[(phi, i)]
+
+    # -- image ----------------------------------------------------------------
+    def pixel(self, phi: int, p: Tuple[int, int], masks: Sequence[np.ndarray]) -> List[float]:
+        cs, idx = self.coefficient_set(p)
+        U = [self.exit_wave(phi, int(i)) for i in idx]
+        psi = synthesize(U, cs.alpha, cs.offsets, self.prm.D, self.prm.cyclic)
+        return [detect(psi, m) for m in masks]
+
+    def detector_masks(self, detectors) -> List[np.ndarray]:
+        p = self.prm
+        return [detector_mask(p.D, p.dy, p.dx, p.lam, d.r1, d.r2, p.bandlimit_frac)
+                for d in detectors]
+
+    def image(self, detectors, probes: np.ndarray) -> np.ndarray:
+        """Phonon-averaged readings, shape (n_det, n_probes); probes (n, 2) pixel (x, y)."""
+        masks = self.detector_masks(detectors)
+        out = np.zeros((len(masks), probes.shape[0]), dtype=np.float64)
+        nphi = len(self._phonons)
+        for phi in range(nphi):
+            for k, pr in enumerate(probes):
+                out[:, k] += self.pixel(phi, (int(pr[0]), int(pr[1])), masks)
+        return out / nphi
+
+
+def region_probes(px0: int, py0: int, npx: int, npy: int, spacing: Tuple[int, int],
+                  nx: int, ny: int) -> np.ndarray:
+    """Probe lattice points of a region (row-major, x fastest), pixel (x, y) mod grid."""
+    a = np.arange(npx)
+    b = np.arange(npy)
+    xs = np.mod(px0 + a * spacing[0], nx)
+    ys = np.mod(py0 + b * spacing[1], ny)
+    out = np.empty((npy * npx, 2), dtype=np.int64)
+    out[:, 0] = np.tile(xs, npy)
+    out[:, 1] = np.repeat(ys, npx)
+    return out
+
+
+def standard_image(prm: LmaParams, t_full: np.ndarray, detectors, probes: np.ndarray,
+                   psi_init=None) -> np.ndarray:
+    """Brute force (Fig. multislice_pseudocode per probe) on the full grid, D = X.
+
+    ``psi_init`` (optional callable p -> full-grid wave) replaces the probe,
+    e.g. by its LMA approximation.
+    """
+    p = prm
+    prop = fresnel_propagator(p.ny, p.nx, p.dy, p.dx, p.lam, p.slice_dz, p.bandlimit_frac)
+    masks = []
+    for d in detectors:
+        ang = p.lam * np.sqrt(k_squared(p.ny, p.nx, p.dy, p.dx))
+        m = (ang >= d.r1) & (ang < d.r2) & bandlimit_mask(p.ny, p.nx, p.bandlimit_frac)
+        masks.append(m)
+    out = np.zeros((len(masks), probes.shape[0]))
+    for k, pr in enumerate(probes):
+        if psi_init is None:
+            psi = probe(p.ny, p.nx, p.dy, p.dx, p.lam, p.alpha_max, p.cs, p.defocus,
+                        p=(pr[1] * p.dy, pr[0] * p.dx))
+        else:
+            psi = psi_init((int(pr[0]), int(pr[1])))
+        ex = multislice(psi, t_full, prop)
+        for j, m in enumerate(masks):
+            out[j, k] = float(np.sum(np.abs(dft2(ex)[m]) ** 2) / ex.size)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# local recompute (Sec. 4.2.6)
+# ----------------------------------------------------------------------------
+
+def edit_column(x: np.ndarray, y: np.ndarray, slc: np.ndarray, species: np.ndarray,
+                lx: float, ly: float, cx: float, cy: float, r_site: float, op: int,
+                new_species: int):
+    """Change one atomic column: atoms whose lateral minimum-image distance to
+    (cx, cy) is below r_site are removed (op 0) or given ``new_species`` (op 1)."""
+    ddx = x - cx
+    ddy = y - cy
+    ddx = ddx - lx * np.round(ddx / lx)
+    ddy = ddy - ly * np.round(ddy / ly)
+    hit = ddx * ddx + ddy * ddy < r_site * r_site
+    if op == 0:
+        keep = ~hit
+        return x[keep], y[keep], slc[keep], species[keep], int(hit.sum())
+    if op == 1:
+        sp = species.copy()
+        sp[hit] = new_species
+        return x.copy(), y.copy(), slc.copy(), sp, int(hit.sum())
+    raise ValueError("unknown edit op")
+
+
+def params_from_workload(w) -> LmaParams:
+    """Flatten a ``workloads.Workload`` (duck-typed) into LmaParams."""
+    g, b, pr = w.grid, w.basis, w.probe
+    return LmaParams(nx=g.nx, ny=g.ny, lx=g.lx, ly=g.ly, slice_dz=g.slice_dz,
+                     n_slices=g.n_slices, lam=g.lam, sigma=g.sigma,
+                     bandlimit_frac=g.bandlimit_frac, alpha_max=pr.alpha_max, cs=pr.cs,
+                     defocus=pr.defocus, kind=b.kind, gauss_sigma=b.gauss_sigma,
+                     in_spacing=tuple(b.in_spacing_px), in_offset=tuple(b.in_offset_px),
+                     f=b.f, L=b.L, W=b.window, D=b.det_window)

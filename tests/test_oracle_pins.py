@@ -1,0 +1,455 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a direct sum,
+a closed form, a value printed in the paper, brute force on a tiny input, an
+invariant or a symmetry. They are chosen so that a plausible slip (a dropped
+term, a wrong sign or index, a transposed operand) fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import lma_oracle as O
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / np.max(np.abs(np.asarray(b))))
+
+
+# --------------------------------------------------------------------------- transforms
+
+def test_dft2_matches_direct_double_sum():
+    rng = np.random.default_rng(1)
+    n, m = 16, 12
+    a = rng.normal(size=(m, n)) + 1j * rng.normal(size=(m, n))
+    direct = np.zeros((m, n), dtype=np.complex128)
+    ys, xs = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+    for ky in range(m):
+        for kx in range(n):
+            direct[ky, kx] = np.sum(a * np.exp(-2j * np.pi * (ky * ys / m + kx * xs / n)))
+    assert rel(O.dft2(a), direct) < 1e-13
+    assert rel(O.idft2(O.dft2(a)), a) < 1e-14
+    inv = np.zeros_like(direct)
+    for y in range(m):
+        for x in range(n):
+            inv[y, x] = np.sum(direct * np.exp(2j * np.pi * (ys * y / m + xs * x / n))) / (m * n)
+    assert rel(inv, a) < 1e-13
+
+
+def test_frequencies_are_the_papers_centred_grid_in_fft_order():
+    # Sec. 4.1: g(k) = (k - 1 - floor(X/2)) / l_x for k = 1..X (centred order)
+    for n, l in ((16, 4.0), (15, 3.0), (128, 16.0)):
+        centred = (np.arange(1, n + 1) - 1 - n // 2) / l
+        assert np.allclose(np.fft.fftshift(O.freqs(n, l / n)), centred, rtol=0, atol=1e-15)
+
+
+# --------------------------------------------------------------------------- propagation
+
+def _gaussian(ny, nx, dy, dx, s, cy=0.0, cx=0.0):
+    y = O.min_image(np.arange(ny), ny) * dy - cy
+    x = O.min_image(np.arange(nx), nx) * dx - cx
+    return np.exp(-(y[:, None] ** 2 + x[None, :] ** 2) / (2 * s * s)).astype(np.complex128)
+
+
+def _free_gaussian(ny, nx, dy, dx, s, lam, z, cy=0.0, cx=0.0):
+    """Closed form of the paraxial equation (Sec. 3.1, V = 0) for a Gaussian start.
+
+    psi(0) = exp(-r^2 / 2 s^2)  ->  psi(z) = (s^2/Q) exp(-r^2 / 2Q), Q = s^2 + i lambda z / 2 pi.
+    """
+    q = s * s + 1j * lam * z / (2 * np.pi)
+    y = O.min_image(np.arange(ny), ny) * dy - cy
+    x = O.min_image(np.arange(nx), nx) * dx - cx
+    r2 = y[:, None] ** 2 + x[None, :] ** 2
+    return (s * s / q) * np.exp(-r2 / (2 * q))
+
+
+def test_fresnel_propagation_of_a_gaussian_matches_closed_form():
+    # non-square grid and pixels so that a transposed axis fails
+    ny, nx, dy, dx = 192, 256, 0.11, 0.1
+    s, lam, dz, n = 0.5, 0.025, 5.0, 10
+    psi = _gaussian(ny, nx, dy, dx, s)
+    prop = O.fresnel_propagator(ny, nx, dy, dx, lam, dz, 2.0 / 3.0)
+    ex = O.multislice(psi, [np.ones((ny, nx))] * n, prop)
+    assert rel(ex, _free_gaussian(ny, nx, dy, dx, s, lam, n * dz)) < 1e-11
+
+
+def test_transmit_then_propagate_order_with_a_tilt():
+    # Fig. multislice_pseudocode: transmission first, then propagation. A tilt
+    # t = exp(2 pi i q.x) then propagation over z moves the Gaussian by lambda z q
+    # and adds the phase exp(2 pi i q.x - i pi lambda z |q|^2).
+    ny, nx, dy, dx = 256, 256, 0.1, 0.1
+    s, lam, z = 0.5, 0.025, 40.0
+    mq, nq = 9, -5
+    qx, qy = mq / (nx * dx), nq / (ny * dy)
+    y = np.arange(ny) * dy
+    x = np.arange(nx) * dx
+    tilt = np.exp(2j * np.pi * (qy * y[:, None] + qx * x[None, :]))
+    psi0 = _gaussian(ny, nx, dy, dx, s)
+    prop = O.fresnel_propagator(ny, nx, dy, dx, lam, z, 2.0 / 3.0)
+    ex = O.multislice(psi0, [tilt], prop)
+    # evaluate the closed form on the periodic grid with the tilt written on
+    # min-image coordinates (tilt is periodic because q lies on the grid)
+    ym = O.min_image(np.arange(ny), ny) * dy
+    xm = O.min_image(np.arange(nx), nx) * dx
+    phase = np.exp(2j * np.pi * (qy * ym[:, None] + qx * xm[None, :]) - 1j * np.pi * lam * z * (qx * qx + qy * qy))
+    expect = phase * _free_gaussian(ny, nx, dy, dx, s, lam, z, cy=lam * z * qy, cx=lam * z * qx)
+    assert rel(ex, expect) < 1e-10
+
+
+def test_slices_compose_in_free_space():
+    rng = np.random.default_rng(2)
+    n, d, lam = 64, 0.1, 0.02
+    mask = O.bandlimit_mask(n, n, 2.0 / 3.0)
+    psi = O.idft2(mask * (rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))))
+    many = O.multislice(psi, [np.ones((n, n))] * 7, O.fresnel_propagator(n, n, d, d, lam, 1.5, 2 / 3))
+    one = O.multislice(psi, [np.ones((n, n))], O.fresnel_propagator(n, n, d, d, lam, 7 * 1.5, 2 / 3))
+    assert rel(many, one) < 1e-12
+
+
+def test_constant_potential_is_a_global_phase():
+    rng = np.random.default_rng(3)
+    n, d, lam, sigma, v0, ns = 64, 0.1, 0.02, 7e-4, 37.0, 5
+    psi = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    prop = O.fresnel_propagator(n, n, d, d, lam, 2.0, 2 / 3)
+    free = O.multislice(psi, [np.ones((n, n))] * ns, prop)
+    t = O.transmission(np.full((n, n), v0), sigma)
+    tilted = O.multislice(psi, [t] * ns, prop)
+    assert rel(tilted, np.exp(1j * ns * sigma * v0) * free) < 1e-13
+
+
+def test_norm_identity_per_slice():
+    # |t| = 1 and |P| = 1: each slice loses exactly the energy outside the mask
+    rng = np.random.default_rng(4)
+    n, d, lam, sigma = 64, 0.1, 0.02, 7e-4
+    mask = O.bandlimit_mask(n, n, 2 / 3)
+    prop = O.fresnel_propagator(n, n, d, d, lam, 2.0, 2 / 3)
+    psi = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    for _ in range(3):
+        t = O.transmission(rng.uniform(0, 500, size=(n, n)), sigma)
+        nxt = O.multislice(psi, [t], prop)
+        lost = np.sum(np.abs(O.dft2(t * psi)[~mask]) ** 2) / n ** 2
+        assert abs(np.sum(np.abs(nxt) ** 2) - (np.sum(np.abs(psi) ** 2) - lost)) < 1e-9 * np.sum(np.abs(psi) ** 2)
+        psi = nxt
+    # band-limited input in free space keeps its norm
+    bl = O.idft2(mask * O.dft2(psi))
+    out = O.multislice(bl, [np.ones((n, n))] * 3, prop)
+    assert abs(np.sum(np.abs(out) ** 2) / np.sum(np.abs(bl) ** 2) - 1) < 1e-13
+
+
+def test_multislice_is_linear():
+    rng = np.random.default_rng(5)
+    n, d, lam, sigma = 48, 0.1, 0.02, 7e-4
+    prop = O.fresnel_propagator(n, n, d, d, lam, 2.0, 2 / 3)
+    ts = [O.transmission(rng.uniform(0, 300, size=(n, n)), sigma) for _ in range(4)]
+    us = [rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n)) for _ in range(3)]
+    al = rng.normal(size=3) + 1j * rng.normal(size=3)
+    lhs = O.multislice(sum(a * u for a, u in zip(al, us)), ts, prop)
+    rhs = sum(a * O.multislice(u, ts, prop) for a, u in zip(al, us))
+    assert rel(lhs, rhs) < 1e-13
+
+
+def test_multislice_commutes_with_grid_shifts():
+    rng = np.random.default_rng(6)
+    n, d, lam, sigma = 48, 0.1, 0.02, 7e-4
+    prop = O.fresnel_propagator(n, n, d, d, lam, 2.0, 2 / 3)
+    ts = [O.transmission(rng.uniform(0, 300, size=(n, n)), sigma) for _ in range(3)]
+    u = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    sh = (5, -11)
+    a = np.roll(O.multislice(u, ts, prop), sh, axis=(0, 1))
+    b = O.multislice(np.roll(u, sh, axis=(0, 1)), [np.roll(t, sh, axis=(0, 1)) for t in ts], prop)
+    assert rel(a, b) < 1e-13
+
+
+# --------------------------------------------------------------------------- physics model
+
+def test_wavelength_and_gaussian_width_match_the_paper():
+    g = GOLDEN["wavelength_200kV_A"]
+    assert round(O.electron_wavelength(200e3), g["digits"]) == g["value"]
+    s = GOLDEN["gaussian_sigma_A"]
+    assert round(O.gaussian_width(s["inputs"]["lambda"], s["inputs"]["alpha_max"]), s["digits"]) == s["value"]
+
+
+def test_workload_literals_match_the_formulas():
+    from paper_2310_16829_gb300 import workloads as WL
+    assert abs(WL.LAMBDA_300KV / O.electron_wavelength(300e3) - 1) < 1e-12
+    assert abs(WL.SIGMA_300KV / O.interaction_constant(300e3) - 1) < 1e-12
+    # the toy workload states rounded 200 kV constants
+    assert abs(WL.LAMBDA_CFG0 - O.electron_wavelength(200e3)) < 1e-5
+    assert abs(WL.SIGMA_CFG0 - O.interaction_constant(200e3)) < 1e-6
+
+
+def test_probe_is_normalised_band_limited_and_shifts_by_modulation():
+    ny, nx, d, lam, a = 96, 96, 0.1, 0.02, 0.03
+    p0 = O.probe(ny, nx, d, d, lam, a, cs=1000.0, defocus=50.0)
+    assert abs(np.sum(np.abs(p0) ** 2) - 1) < 1e-13
+    k2 = O.k_squared(ny, nx, d, d)
+    outside = lam * np.sqrt(k2) >= a
+    assert np.max(np.abs(O.dft2(p0)[outside])) < 1e-12
+    # aperture is strict and the aberration phase is applied: |spectrum| is flat inside
+    spec = O.dft2(p0)
+    inside = ~outside
+    assert np.ptp(np.abs(spec[inside])) < 1e-10
+    # eq. probe_wave_function with an integer-pixel p equals a roll of psi_0
+    pshift = O.probe(ny, nx, d, d, lam, a, cs=1000.0, defocus=50.0, p=(7 * d, -3 * d))
+    assert rel(pshift, np.roll(p0, (7, -3), axis=(0, 1))) < 1e-12
+
+
+def test_aberration_phase_sign_and_powers():
+    # chi = 1/2 pi Cs lambda^3 k^4 - pi Z lambda k^2 evaluated at two points
+    lam = 0.02
+    k2 = np.array([0.25, 4.0])
+    chi_cs = O.aberration(k2, lam, 1e7, 0.0)
+    chi_z = O.aberration(k2, lam, 0.0, 100.0)
+    assert abs(chi_cs[1] / chi_cs[0] - 256.0) < 1e-12      # |k|^4
+    assert abs(chi_z[1] / chi_z[0] - 16.0) < 1e-12         # |k|^2
+    assert chi_z[0] < 0 and chi_cs[0] > 0
+    assert abs(chi_cs[0] - 0.5 * np.pi * 1e7 * lam ** 3 * 0.0625) < 1e-12 * chi_cs[0]
+
+
+def test_projected_potential_closed_forms():
+    # one atom on a fine grid: v at its pixel is peak * sum(frac); the pixel sum
+    # times dx dy is the truncated Gaussian integral 2 pi w^2 (1 - exp(-rc^2 / 2w^2))
+    n, l = 512, 10.24
+    d = l / n
+    peak, fr, wd, rc = (250.0,), (0.7, 0.3), (0.15, 0.5), 3.0
+    xa, ya = 20 * d, 230 * d     # exactly on pixel (x=20, y=230)
+    v = O.projected_potential(np.array([xa]), np.array([ya]), np.array([0]), np.array([0]),
+                              1, n, n, l, l, peak, fr, wd, rc)[0]
+    assert abs(v[230, 20] - 250.0) < 1e-12
+    assert v[20, 230] == 0.0   # not transposed
+    integral = 250.0 * sum(f * 2 * np.pi * w * w * (1 - np.exp(-rc * rc / (2 * w * w))) for f, w in zip(fr, wd))
+    assert abs(np.sum(v) * d * d / integral - 1) < 1e-8
+    # periodic images: an atom across the boundary gives the same field shifted
+    v2 = O.projected_potential(np.array([l - 3 * d]), np.array([0.5 * d]), np.array([0]), np.array([0]),
+                               1, n, n, l, l, peak, fr, wd, rc)[0]
+    v3 = O.projected_potential(np.array([30 * d]), np.array([0.5 * d]), np.array([0]), np.array([0]),
+                               1, n, n, l, l, peak, fr, wd, rc)[0]
+    assert rel(np.roll(v3, -33, axis=1), v2) < 1e-12
+    # hard cutoff
+    yy, xx = np.meshgrid(np.arange(n) * d, np.arange(n) * d, indexing="ij")
+    ddx = (xx - xa) - l * np.round((xx - xa) / l)
+    ddy = (yy - ya) - l * np.round((yy - ya) / l)
+    r = np.sqrt(ddx ** 2 + ddy ** 2)
+    assert np.all(v[r > rc + 1e-9] == 0.0) and np.all(v[r < rc - 1e-9] > 0.0)
+
+
+def test_detector_reads_a_plane_wave():
+    n, d, lam = 64, 0.1, 0.025
+    m0, n0 = 5, -3
+    k = math.hypot(m0 / (n * d), n0 / (n * d))
+    y = np.arange(n) * d
+    pw = np.exp(2j * np.pi * (n0 / (n * d) * y[:, None] + m0 / (n * d) * y[None, :])) / n
+    inside = O.detector_mask(n, d, d, lam, lam * k * 0.99, lam * k * 1.01, 2 / 3)
+    assert abs(O.detect(pw, inside) - 1.0) < 1e-13
+    assert O.detect(pw, O.detector_mask(n, d, d, lam, lam * k * 1.01, 1.0, 2 / 3)) < 1e-25
+    # an annulus ending just below the wave's angle does not see it
+    assert O.detect(pw, O.detector_mask(n, d, d, lam, 0.0, lam * k * 0.999999, 2 / 3)) < 1e-25
+
+
+def test_detector_over_all_frequencies_is_parseval():
+    rng = np.random.default_rng(7)
+    psi = rng.normal(size=(32, 32)) + 1j * rng.normal(size=(32, 32))
+    assert abs(O.detect(psi, np.ones((32, 32), bool)) / np.sum(np.abs(psi) ** 2) - 1) < 1e-13
+
+
+def test_bandlimit_mask_is_the_integer_two_thirds_circle():
+    for n in (64, 128, 256):
+        m = O.bandlimit_mask(n, n, 2 / 3)
+        i = O.signed_index(n)
+        brute = np.array([[9 * (a * a + b * b) <= n * n for b in i] for a in i])
+        assert np.array_equal(m, brute)
+
+
+# --------------------------------------------------------------------------- LMA geometry
+
+def test_input_lattice_count_matches_the_recompute_example():
+    g = GOLDEN["input_lattice_count"]
+    # 848 x 800 grid, probes every 2 px (P = (424, 400)), I = P + p/2, f = 2
+    lat = O.input_lattice(848, 800, (2, 2), (1, 1), 2)
+    assert lat.shape[0] == g["value"]
+    assert 424 * 400 == GOLDEN["probe_count"]["value"]
+    assert len(set(map(tuple, lat.tolist()))) == g["value"]
+
+
+def test_nearest_translates_form_complete_shells():
+    lat = O.input_lattice(64, 64, (4, 4), (2, 2), 1)
+    idx, offs = O.nearest_translates((0, 0), lat, 32, 64, 64)
+    d2 = offs[:, 0] ** 2 + offs[:, 1] ** 2
+    # brute force: all offsets (2 + 4a) in both axes, sorted by distance
+    vals = sorted((x * x + y * y) for x in range(-30, 31) for y in range(-30, 31)
+                  if x % 4 == 2 and y % 4 == 2)
+    assert sorted(d2.tolist()) == vals[:32]
+    assert set(np.unique(d2).tolist()) == {8, 40, 72, 104, 136}
+    # returned indices address the same translates as the offsets
+    assert np.array_equal(O.min_image(lat[idx, 0], 64), offs[:, 0])
+
+
+def _small_params(**kw):
+    base = dict(nx=64, ny=64, lx=8.0, ly=8.0, slice_dz=2.0, n_slices=3, lam=0.025, sigma=7.3e-4,
+                bandlimit_frac=2 / 3, alpha_max=0.03, cs=0.0, defocus=0.0, kind=0, gauss_sigma=0.0,
+                in_spacing=(4, 4), in_offset=(2, 2), f=1, L=8, W=64, D=64)
+    base.update(kw)
+    return O.LmaParams(**base)
+
+
+def _direct_ls(prm, p, L):
+    """Least squares written against absolute positions for probe p (no reuse)."""
+    lat = O.input_lattice(prm.nx, prm.ny, prm.in_spacing, prm.in_offset, prm.f)
+    idx, _ = O.nearest_translates(p, lat, L, prm.nx, prm.ny)
+    psi = O.probe(prm.ny, prm.nx, prm.dy, prm.dx, prm.lam, prm.alpha_max, p=(p[1] * prm.dy, p[0] * prm.dx))
+    uW = O.input_wave_window(prm.kind, prm.W, prm.ny, prm.nx, prm.dy, prm.dx, prm.lam, prm.alpha_max, 0, 0, 0)
+    A = np.stack([O.embed_window(uW, int(lat[i, 1]) - prm.W // 2, int(lat[i, 0]) - prm.W // 2,
+                                 prm.ny, prm.nx).ravel() for i in idx], 1)
+    al = np.linalg.lstsq(A, psi.ravel(), rcond=None)[0]
+    res = np.linalg.norm(psi.ravel() - A @ al)
+    return al, res, A, psi.ravel()
+
+
+def test_case1_same_coefficients_and_error_for_every_probe():
+    # Case 1 (eq. lma_approximation_exit1): probes every 8 px, translates every 4 px
+    prm = _small_params(W=32, D=32)
+    ref = None
+    for p in [(0, 0), (8, 16), (56, 40), (24, 56)]:
+        al, res, _, _ = _direct_ls(prm, p, 12)
+        if ref is None:
+            ref = (al, res)
+        assert rel(al, ref[0]) < 1e-9
+        assert abs(res - ref[1]) < 1e-12
+    orc = O.LmaOracle(_small_params(W=32, D=32, L=12))
+    cs, _ = orc.coefficient_set((24, 56))
+    assert rel(cs.alpha, ref[0]) < 1e-9
+
+
+def test_case2_gives_c_times_d_coefficient_sets_reused_by_translation():
+    # Case 2 (eq. lma_approximation_exit2): probes every 2 px, translates every 4 px
+    prm = _small_params(W=32, D=32, L=10)
+    orc = O.LmaOracle(prm)
+    probes = O.region_probes(0, 0, 8, 8, (2, 2), 64, 64)
+    for pr in probes:
+        orc.coefficient_set((int(pr[0]), int(pr[1])))
+    assert len(orc._sets) == 4
+    al, _, _, _ = _direct_ls(prm, (6, 10), 10)      # a probe of class (0, 0), solved directly
+    cs, _ = orc.coefficient_set((6, 10))
+    assert rel(cs.alpha, al) < 1e-9
+
+
+def test_least_squares_residual_is_orthogonal_and_matches_normal_equations():
+    prm = _small_params(W=32, D=32)
+    al, _, A, b = _direct_ls(prm, (0, 0), 6)
+    r = b - A @ al
+    assert np.max(np.abs(A.conj().T @ r)) < 1e-12 * np.linalg.norm(b) * np.max(np.abs(A))
+    ne = np.linalg.solve(A.conj().T @ A, A.conj().T @ b)
+    assert rel(ne, al) < 1e-8
+
+
+def test_synthesis_placement_truncates_or_wraps():
+    U = (np.arange(16).reshape(4, 4) + 1).astype(np.complex128)
+    out = O.synthesize([U], np.array([2.0]), np.array([[1, -2]]), 4, cyclic=False)
+    exp = np.zeros((4, 4), complex)
+    exp[0:2, 1:4] = 2 * U[2:4, 0:3]
+    assert np.array_equal(out, exp)
+    out_c = O.synthesize([U], np.array([1.0]), np.array([[1, -2]]), 4, cyclic=True)
+    assert np.array_equal(out_c, np.roll(U, (-2, 1), axis=(0, 1)))
+    # a larger detection window centres the exit wave
+    out_d = O.synthesize([U], np.array([1.0]), np.array([[0, 0]]), 8, cyclic=False)
+    assert np.array_equal(out_d[2:6, 2:6], U) and np.sum(np.abs(out_d)) == np.sum(np.abs(U))
+
+
+# --------------------------------------------------------------------------- LMA vs brute force
+
+def _tiny_specimen(prm, seed=11, per_slice=3):
+    rng = np.random.default_rng(seed)
+    n = per_slice * prm.n_slices
+    x = rng.uniform(0, prm.lx, n)
+    y = rng.uniform(0, prm.ly, n)
+    s = np.repeat(np.arange(prm.n_slices), per_slice).astype(np.int32)
+    sp = rng.integers(0, 2, n).astype(np.int16)
+    class A:
+        pass
+    a = A()
+    a.x, a.y, a.slice, a.species = x, y, s, sp
+    return a
+
+
+class _Det:
+    def __init__(self, r1, r2):
+        self.r1, self.r2 = r1, r2
+
+
+def test_lma_with_probe_input_waves_is_the_standard_algorithm():
+    # Sec. 4.2.3: u = psi_0, I = P, f = 1, L = 1 retrieves the standard algorithm
+    prm = _small_params(kind=1, in_spacing=(8, 8), in_offset=(0, 0), L=1, n_slices=4)
+    at = _tiny_specimen(prm)
+    orc = O.LmaOracle(prm)
+    orc.set_specimen([at], (300.0, 150.0), (0.7, 0.3), (0.15, 0.5), 3.0)
+    probes = O.region_probes(0, 0, 8, 8, (8, 8), 64, 64)
+    dets = [_Det(0.0, 0.02), _Det(0.03, 0.066)]
+    img = orc.image(dets, probes)
+    std = O.standard_image(prm, orc.transmission_stack(0), dets, probes)
+    assert rel(img, std) < 1e-12
+    cs, _ = orc.coefficient_set((0, 0))
+    assert cs.err_l2 < 1e-13 and abs(cs.alpha[0] - 1) < 1e-13
+
+
+def test_lma_with_gaussian_waves_propagates_the_approximated_probe_exactly():
+    # linearity (Sec. 4.2): with W = D = X, LMA is standard multislice of sum alpha u_i
+    prm = _small_params(kind=0, L=12, n_slices=3)
+    at = _tiny_specimen(prm, seed=12)
+    orc = O.LmaOracle(prm)
+    orc.set_specimen([at], (300.0, 150.0), (0.7, 0.3), (0.15, 0.5), 3.0)
+    probes = O.region_probes(4, 0, 5, 3, (12, 20), 64, 64)
+
+    def approx(p):
+        cs, idx = orc.coefficient_set(p)
+        full = np.zeros((64, 64), complex)
+        for a, i in zip(cs.alpha, idx):
+            full += a * O.embed_window(orc.uW, int(orc.lattice[i, 1]) - 32, int(orc.lattice[i, 0]) - 32, 64, 64)
+        return full
+
+    dets = [_Det(0.03, 0.066)]
+    img = orc.image(dets, probes)
+    std = O.standard_image(prm, orc.transmission_stack(0), dets, probes, psi_init=approx)
+    assert rel(img, std) < 1e-12
+
+
+def test_simple_cubic_image_has_crystal_period_and_4mm_symmetry():
+    # simple-cubic 2x2 cells of 4 A on 64^2: image periodic with 32 px and 4mm symmetric
+    prm = _small_params(L=32, n_slices=3, alpha_max=0.02)
+    xs, ys, ss = [], [], []
+    for s in range(prm.n_slices):
+        for j in range(2):
+            for i in range(2):
+                xs.append(4.0 * i); ys.append(4.0 * j); ss.append(s)
+
+    class A:
+        pass
+    at = A()
+    at.x, at.y = np.array(xs), np.array(ys)
+    at.slice, at.species = np.array(ss, np.int32), np.zeros(len(xs), np.int16)
+    orc = O.LmaOracle(prm)
+    orc.set_specimen([at], (300.0,), (0.7, 0.3), (0.15, 0.5), 3.0)
+    probes = O.region_probes(0, 0, 16, 16, (4, 4), 64, 64)
+    img = orc.image([_Det(0.03, 0.066)], probes)[0].reshape(16, 16)
+    tol = 1e-10 * np.max(img)
+    assert np.max(np.abs(img - np.roll(img, 8, axis=0))) < tol
+    assert np.max(np.abs(img - np.roll(img, 8, axis=1))) < tol
+    assert np.max(np.abs(img - img.T)) < tol
+    mirror = img[:, (-np.arange(16)) % 16]
+    assert np.max(np.abs(img - mirror)) < tol
+    assert np.ptp(img) > 1e3 * tol   # not trivially constant
+
+
+def test_edit_column_removes_or_swaps_only_that_column():
+    x = np.array([0.01, 3.9, 7.99, 2.0, 0.05])
+    y = np.array([0.02, 0.0, 7.98, 2.0, 0.03])
+    s = np.array([0, 0, 1, 1, 2], np.int32)
+    sp = np.array([0, 1, 0, 1, 2], np.int16)
+    x2, y2, s2, sp2, nhit = O.edit_column(x, y, s, sp, 8.0, 8.0, 0.0, 0.0, 0.3, 0, 0)
+    assert nhit == 3 and list(x2) == [3.9, 2.0]
+    _, _, _, sp3, nhit = O.edit_column(x, y, s, sp, 8.0, 8.0, 0.0, 0.0, 0.3, 1, 2)
+    assert nhit == 3 and list(sp3) == [2, 1, 2, 1, 2]
