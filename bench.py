@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the LMA hot path on GB300: HAADF pixels/s of the full image pipeline.
+
+One step = one pass of the whole path over the ABO3 workload (512^2 grid,
+50 slices of 2 A, 8 frozen-phonon configurations, 128 x 128 probes, Gaussian
+input waves on a 4-px lattice, L = 32, W = D = 128, complex64): for every
+configuration the transmission is built (step a1), all 16384 translates are
+propagated (a3), every probe is synthesized and read out (a4, a5), and the
+readings are averaged in FP64 (a6). ``value`` is measured with the atoms
+already resident in HBM and the image written to device memory; ``e2e`` runs
+the same step through the public API with host buffers (new atom lists
+uploaded, image copied back) inside the timed region.
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
+workload (the reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2310_16829_gb300 import workloads as WL  # noqa: E402
+
+METRIC = "HAADF pixels/s (LMA mixed vs FP32, ≤1e-3 rel err); p50/p99 column-edit latency"
+UNIT = "pixels/s"
+# algorithmic work of one translate-slice on a 128 x 128 window: two 2D FFTs at
+# 5 N log2 N flops (N = W^2) plus the transmission and propagator products at 6 flops each
+W = 128
+FLOPS_PER_TRANSLATE_SLICE = 2 * 5 * W * W * 14 + 12 * W * W   # 2,490,368
+FP32_LANES_PER_SM = 128
+N_SMS = 152
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ----------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.active = False
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.active = True
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            if self.active:
+                self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        self.active = False
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _gpu_id(torch) -> str:
+    try:
+        p = torch.cuda.get_device_properties(torch.cuda.current_device())
+        return "%08x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+    except Exception:
+        return os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+
+
+# ----------------------------------------------------------------------------------- oracle sample
+def oracle_sample(w, n_probes: int, seed: int) -> dict:
+    """Time the FP64 oracle, as it stands, on a bounded sample of the workload.
+
+    The sample is one configuration: its transmission stack, the exit waves of
+    the translates that ``n_probes`` adjacent probes need, and those probes'
+    synthesis and detection. The full-job time is extrapolated linearly:
+    N_phi * (T_t + |I_f| * T_translate + |P| * T_probe).
+    """
+    from oracle import lma_oracle as O
+    orc = O.LmaOracle(O.params_from_workload(w))
+    orc.set_specimen(w.phonons[:1], w.potential.peak, w.potential.term_frac, w.potential.term_width,
+                     w.potential.r_cut)
+    rng = np.random.default_rng(seed)
+    a0 = int(rng.integers(0, w.region.npx - 2))
+    b0 = int(rng.integers(0, w.region.npy - 2))
+    probes = [(w.region.px0 + (a0 + k % 2) * w.region.spacing_px[0],
+               w.region.py0 + (b0 + k // 2) * w.region.spacing_px[1]) for k in range(n_probes)]
+    t0 = time.perf_counter()
+    orc.transmission_stack(0)
+    t1 = time.perf_counter()
+    needed = set()
+    for p in probes:
+        _, idx = orc.coefficient_set(p)
+        needed.update(int(i) for i in idx)
+    t2 = time.perf_counter()
+    for i in sorted(needed):
+        orc.exit_wave(0, i)
+    t3 = time.perf_counter()
+    masks = orc.detector_masks(w.detectors)
+    for p in probes:
+        orc.pixel(0, p, masks)
+    t4 = time.perf_counter()
+    t_pot, t_tr, t_probe = t1 - t0, (t3 - t2) / len(needed), (t4 - t3) / len(probes)
+    n_tr = orc.lattice.shape[0]
+    full = len(w.phonons) * (t_pot + n_tr * t_tr + w.n_pixels * t_probe)
+    return {"value": w.n_pixels / full, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"1 of {len(w.phonons)} configurations: transmission stack, "
+                       f"{len(needed)} of {n_tr} translate exit waves, {len(probes)} of "
+                       f"{w.n_pixels} probes; full job extrapolated linearly "
+                       f"({full:.0f} s); numpy FFT single-threaded"),
+            "sample_seconds": t4 - t0, "coefficient_setup_s": t2 - t1}
+
+
+def run_reference(args, w) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals, secs = [], []
+    for step in range(args.warmup + args.steps):
+        r = oracle_sample(w, 1, seed=100 + step)
+        if step >= args.warmup:
+            vals.append(r["value"])
+            secs.append(r["sample_seconds"])
+    v = statistics.mean(vals)
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name, "parallelism": "single process (host cores)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------- main arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lma", choices=["lma", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    w = WL.perovskite_workload()
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    from paper_2310_16829_gb300 import lma
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # replicas: every rank simulates its own specimen (independent phonon seeds)
+    if rank:
+        w = WL.perovskite_workload(seed_base=1000 + 97 * rank)
+    ctx = lma.Context(local)
+    stream = torch.cuda.current_stream()
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    region, dets = w.region, w.detectors
+    out = torch.empty((len(dets), region.npy, region.npx), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    t_setup = time.perf_counter()
+    basis.image(dets, region, out=out, recompute=True, stream=stream)   # coefficients + first pass
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for _ in range(args.warmup):
+        basis.image(dets, region, out=out, recompute=True, stream=stream)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(_gpu_id(torch))
+    clocks.start()
+    ctx.profile_enable(True)
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))                      # evict L2 between steps (outside the events)
+        ev[k][0].record(stream)
+        basis.image(dets, region, out=out, recompute=True, stream=stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * w.n_pixels / (ms_per_step / 1e3)
+    img = out.cpu().numpy()
+
+    # ---- end to end through the public API with host buffers
+    host_out = np.empty((len(dets), region.npy, region.npx), dtype=np.float64)
+    h2d = sum(a.x.nbytes + a.y.nbytes + a.species.nbytes + 4 * (w.grid.n_slices + 1) for a in w.phonons)
+    e2e_steps = max(1, min(3, args.steps))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        spec.set_atoms(w.phonons)
+        basis.image(dets, region, out=host_out, recompute=True)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_consistent = bool(np.array_equal(host_out, img))
+
+    # ---- roofline of the dominant kernel (slice kernel, FP32 ALU bound)
+    peaks = _peaks()
+    sl = prof["slice"]
+    slice_ms = sl["total_ms"] / max(1, sl["launches"])
+    flops_per_launch = FLOPS_PER_TRANSLATE_SLICE * sl["units"] / max(1, sl["launches"])
+    achieved = flops_per_launch / (slice_ms / 1e3) / 1e12
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    roofline = {"kernel": "k_slice", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "peak_source": f"FP32 FMA: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz "
+                               "(sm_max_mhz of MEASURED_PEAKS.json)",
+                "algorithmic": f"{FLOPS_PER_TRANSLATE_SLICE} flop per translate-slice x "
+                               f"{sl['units'] // max(1, sl['launches'])} translate-slices per launch",
+                "share_of_step": sl["total_ms"] / max(1e-9, sum(v["total_ms"] for v in prof.values())),
+                "launch_ms": slice_ms}
+    syn = prof["synth"]
+    synth_ms = syn["total_ms"] / max(1, syn["launches"])
+    u_bytes = basis.info().exit_wave_bytes
+    kernels = {k: {"launches_per_step": v["launches"] / args.steps,
+                   "ms_per_launch": v["total_ms"] / max(1, v["launches"])} for k, v in prof.items()}
+    kernels["synth"]["exit_wave_store_GBps"] = u_bytes / (synth_ms / 1e3) / 1e9 if synth_ms else None
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_sample(w, 2, seed=5)
+        cpu.pop("sample_seconds", None)
+        cpu.pop("coefficient_setup_s", None)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+            "data": "synthetic (seeded ABO3 slab, Gaussian frozen-phonon displacements)",
+            "config": {"workload": w.name, "grid": [w.grid.nx, w.grid.ny], "slices": w.grid.n_slices,
+                       "phonons": len(w.phonons), "probes": w.n_pixels,
+                       "translates": int(basis.info().n_translates), "L": w.basis.L, "W": W, "D": W,
+                       "input_wave": "gaussian sigma=lambda/(2 alpha_max)", "precision": "complex64",
+                       "detector_mrad": [1e3 * dets[0].r1, 1e3 * dets[0].r2],
+                       "l2": "256 MiB buffer written between timed steps; per-step working set "
+                             f"{u_bytes / 1e9:.2f} GB of exit waves > L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * w.n_pixels / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(host_out.nbytes), "matches_device_run": e2e_consistent},
+            "gpu_launches": int(sum(v["launches"] for v in prof.values())),
+            "clocks": clk,
+            "kernels": kernels,
+            "wall_s_timed_region": wall,
+            "setup_s_first_call": t_setup,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

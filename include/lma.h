@@ -1,0 +1,265 @@
+/*
+ * lma.h -- C-ABI of the GB300 Lattice Multislice Algorithm (LMA) library.
+ *
+ * The library computes STEM images with the Lattice Multislice Algorithm of
+ * arXiv:2310.16829 (Fig. lma_pseudocode): multislice propagation of the
+ * lattice translates u_i of a localized input wave (Sec. 4.2.1, step 1),
+ * synthesis of every probe's exit wave as a linear combination of the
+ * propagated translates (Sec. 4.2.2, step 2), the annular detector of the 2D
+ * STEM reading (Sec. 3.1) and the frozen-phonon average (Sec. 3.1, last
+ * paragraph). Local recompute after a change of one atomic column follows
+ * Sec. 4.2.6.
+ *
+ * Conventions (all functions):
+ *   - Arrays are row-major [y][x]; pixel j sits at j*dx; boundaries are
+ *     periodic. Complex values are interleaved (re, im) float pairs.
+ *   - Every function returns an lma_status; no exception crosses the ABI. On
+ *     error, lma_last_error(ctx) returns a message for that context.
+ *   - Input arrays are owned by the caller and are copied during the call;
+ *     the caller may free them on return. Opaque handles are owned by the
+ *     library until the matching lma_free_* / lma_destroy. Output buffers are
+ *     allocated by the caller.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = default stream).
+ *     Device work is queued on it; a call that writes a HOST output buffer
+ *     synchronizes that stream before returning. An output pointer may be
+ *     host or device memory: the library asks the CUDA runtime which.
+ *   - One context per host thread. Contexts created with device = -1 are
+ *     host-only: the host-side functions (geometry, coefficients) work, every
+ *     device call returns LMA_ERR_UNSUPPORTED.
+ *   - Sizes: the propagation window W and the detection window D are 128
+ *     pixels in this version (LMA_ERR_UNSUPPORTED otherwise); the grid must be
+ *     at least W pixels in each direction.
+ */
+#ifndef LMA_H
+#define LMA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t lma_status;
+#define LMA_OK 0
+#define LMA_ERR_INVALID 1      /* bad argument, incompatible lattices, off-grid position */
+#define LMA_ERR_OOM 2          /* device or host allocation failed */
+#define LMA_ERR_CUDA 3         /* CUDA runtime error (message in lma_last_error) */
+#define LMA_ERR_TIMEOUT 4      /* a bounded device wait gave up */
+#define LMA_ERR_UNSUPPORTED 5  /* valid request outside what this build implements */
+
+#define LMA_BASIS_GAUSS 0      /* u = g_sigma (Sec. 4.2.3, Gaussians) */
+#define LMA_BASIS_PROBE 1      /* u = psi_0^init (Sec. 4.2.3, first paragraph) */
+
+#define LMA_PREC_C64 0         /* complex64 everywhere on the device */
+
+#define LMA_EDIT_REMOVE 0      /* remove the atoms of a column */
+#define LMA_EDIT_SET_SPECIES 1 /* give the atoms of a column another species */
+
+#define LMA_IMAGE_RECOMPUTE 1u /* treat every stored exit wave as stale (full path) */
+
+typedef struct lma_ctx lma_ctx;
+typedef struct lma_specimen lma_specimen;
+typedef struct lma_basis lma_basis;
+
+/* Simulation grid (Sec. 3.2, complexity paragraph: X x Y pixels over l_x x l_y). */
+typedef struct {
+  int32_t nx, ny;          /* pixels */
+  double lx, ly;           /* Angstrom */
+  double slice_dz;         /* slice thickness epsilon, Angstrom */
+  int32_t n_slices;        /* N */
+  double lambda;           /* electron wavelength, Angstrom */
+  double sigma;            /* interaction constant, rad/(V*Angstrom) (eq. schroedinger_equation) */
+  double bandlimit_frac;   /* propagator mask radius as a fraction of Nyquist (2/3 typical) */
+} lma_grid;
+
+/* Projected potential per atom and slice: peak[species] * sum_t frac_t exp(-r^2 / 2 w_t^2)
+ * for r < r_cut, in V*Angstrom; the slice integral v_eps of Sec. 3.2. */
+typedef struct {
+  int32_t n_species;
+  const double* peak;        /* [n_species] */
+  int32_t n_terms;           /* 1..4 */
+  const double* term_frac;   /* [n_terms] */
+  const double* term_width;  /* [n_terms], Angstrom */
+  double r_cut;              /* Angstrom, hard cutoff, < min(lx, ly) / 2 */
+} lma_potential;
+
+/* One frozen-phonon configuration (structure of arrays). */
+typedef struct {
+  int64_t n_atoms;
+  const double* x;           /* [n_atoms] Angstrom */
+  const double* y;           /* [n_atoms] Angstrom */
+  const int32_t* slice;      /* [n_atoms] 0..n_slices-1 */
+  const int16_t* species;    /* [n_atoms] 0..n_species-1 */
+} lma_atoms;
+
+/* Probe (eqs. probe_wave_function, aberration_function, aperture_function). */
+typedef struct {
+  double alpha_max;          /* rad */
+  double cs;                 /* third-order spherical aberration C_s, Angstrom */
+  double defocus;            /* focus Z, Angstrom */
+} lma_probe;
+
+/* Input-wave lattice and approximation parameters (Sec. 4.2.1 options (i)-(iii)). */
+typedef struct {
+  int32_t kind;              /* LMA_BASIS_* */
+  double gauss_sigma;        /* Angstrom; 0 selects lambda / (2 alpha_max) */
+  int32_t in_spacing_px[2];  /* input lattice spacing r_x, r_y in pixels; must divide nx, ny */
+  int32_t in_offset_px[2];   /* I_offset in pixels, 0 <= offset < spacing */
+  int32_t f;                 /* keep every f-th input wave (I_f) */
+  int32_t L;                 /* input waves per probe (I_{f,p,L}) */
+  int32_t window;            /* W: propagation window X' = Y' (128) */
+  int32_t det_window;        /* D: synthesis / detection window (128) */
+  int32_t precision;         /* LMA_PREC_C64 */
+} lma_basis_desc;
+
+/* Annular detector r1 <= lambda |k| < r2 (rad), intersected with the bandlimit (Sec. 3.1, 2D STEM). */
+typedef struct { double r1, r2; } lma_detector;
+
+/* A rectangle of the probe lattice: p(a, b) = (px0 + a*sx, py0 + b*sy) mod grid, pixels. */
+typedef struct {
+  int32_t px0, py0;
+  int32_t npx, npy;
+  int32_t spacing_px[2];
+} lma_region;
+
+/* Summary of a basis (host-side numbers). */
+typedef struct {
+  int64_t n_translates;      /* |I_f| */
+  int32_t nax, nay;          /* I_f lattice points along x, y */
+  int32_t n_sets;            /* coefficient sets computed so far (Case 1: 1, Case 2: c*d) */
+  int32_t L, window, det_window;
+  double gauss_sigma;        /* Angstrom, resolved */
+  int64_t exit_wave_bytes;   /* device bytes of the exit-wave store */
+} lma_basis_info;
+
+/* ---- context ------------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` (or a host-only context with device = -1).
+ * Errors: LMA_ERR_CUDA if the device cannot be selected, LMA_ERR_OOM. */
+lma_status lma_create(int32_t device, lma_ctx** out);
+void lma_destroy(lma_ctx* ctx);
+/* Last error message of the context ("" if none). The pointer stays valid until the next call. */
+const char* lma_last_error(const lma_ctx* ctx);
+
+/* ---- specimen (step a1: projected potential and transmission, Sec. 3.2) -------------- */
+
+/* Copy grid, potential model and n_phonons atom lists into a new specimen.
+ * Atoms are ordered by slice with a stable sort; that order fixes the
+ * summation order of the potential. No device work happens here.
+ * Errors: LMA_ERR_INVALID (non-positive sizes, slice or species out of range,
+ * r_cut >= half the cell, n_terms outside 1..4). */
+lma_status lma_create_specimen(lma_ctx* ctx, const lma_grid* grid, const lma_potential* pot,
+                               const lma_atoms* phonons, int32_t n_phonons, lma_specimen** out);
+lma_status lma_free_specimen(lma_specimen* spec);
+
+/* Build t_s = exp(i sigma v_s) for all slices of configuration `phonon` on the
+ * device (Sec. 3.2, transmission function) and copy it to `out`
+ * ([n_slices][ny][nx] complex64, host or device). For parity tests. */
+lma_status lma_transmission(lma_ctx* ctx, lma_specimen* spec, int32_t phonon, float* out,
+                            void* stream);
+
+/* Replace the atoms of all configurations (same count as at creation; same
+ * validation as lma_create_specimen). Every transmission and exit wave built
+ * from the old atoms becomes stale. Host-side copy; the device upload happens
+ * at the next device call that needs the atoms. */
+lma_status lma_specimen_set_atoms(lma_ctx* ctx, lma_specimen* spec, const lma_atoms* phonons,
+                                  int32_t n_phonons);
+
+/* ---- basis (steps a2 and a3) ----------------------------------------------------------- */
+
+/* Create the input-wave basis: the lattice I_f (Sec. 4.2.1), the input wave u
+ * on its W x W window (Sec. 4.2.3), and the per-slice propagator
+ * exp(-i pi lambda eps |k|^2) with the bandlimit mask (Sec. 3.2). Least-squares
+ * coefficients (Sec. 4.2.2) are computed on the host in FP64 when a probe
+ * class is first needed. Device memory is allocated on first device use.
+ * Errors: LMA_ERR_INVALID when the lattice does not cover the grid, f does not
+ * divide R, offset >= spacing, L > |I_f| or L > 64; LMA_ERR_UNSUPPORTED for
+ * W or D != 128 or a grid smaller than W. */
+lma_status lma_create_basis(lma_ctx* ctx, const lma_specimen* spec, const lma_probe* probe,
+                            const lma_basis_desc* desc, lma_basis** out);
+lma_status lma_free_basis(lma_basis* basis);
+lma_status lma_basis_get_info(const lma_basis* basis, lma_basis_info* out);
+
+/* Coefficients of the probe at pixel (px, py) (eqs. lma_approximation_exit1_0 /
+ * exit2_0): alpha[2L] (re, im) FP64, offsets[2L] (dx, dy) of the L nearest
+ * translates relative to the probe (pixels, minimum image), translates[L] their
+ * indices in I_f (raster order, x fastest), err[2] = relative L2 and sup error
+ * of the probe approximation. Host-only; works on host-only contexts. Any of
+ * the output pointers may be NULL. */
+lma_status lma_basis_coefficients(lma_ctx* ctx, lma_basis* basis, int32_t px, int32_t py,
+                                  double* alpha, int32_t* offsets, int64_t* translates,
+                                  double* err);
+
+/* Step 1 of Fig. lma_pseudocode for configuration `phonon`: build t (step a1)
+ * and propagate every translate of I_f through all slices on its W x W window
+ * (step a3), keeping the exit waves U_i resident in HBM.
+ * Errors: LMA_ERR_INVALID (phonon out of range), LMA_ERR_OOM, LMA_ERR_CUDA. */
+lma_status lma_propagate_basis(lma_ctx* ctx, lma_specimen* spec, lma_basis* basis,
+                               int32_t phonon, void* stream);
+
+/* Copy the stored exit wave U_i of translate `translate` ([W][W] complex64, window
+ * origin at its position - W/2) to `out` (host or device). Fails with
+ * LMA_ERR_INVALID if that exit wave is not current. */
+lma_status lma_exit_wave(lma_ctx* ctx, lma_basis* basis, int64_t translate, float* out,
+                         void* stream);
+
+/* ---- image (steps a4-a6) ---------------------------------------------------------------- */
+
+/* STEM image of a probe-lattice region: for every phonon configuration, the
+ * exit waves the region needs are made current (steps a1, a3; only stale ones
+ * unless LMA_IMAGE_RECOMPUTE), each probe's exit wave is synthesized on its
+ * D x D window (step a4, Sec. 4.2.2), the detectors are read from its DFT
+ * (step a5, Sec. 3.1) and the readings are averaged over configurations in
+ * FP64 (step a6). out[n_det][npy][npx] (double, host or device).
+ * Errors: LMA_ERR_INVALID (empty detectors, probe off the grid, n_det > 4). */
+lma_status lma_image(lma_ctx* ctx, lma_specimen* spec, lma_basis* basis,
+                     const lma_detector* det, int32_t n_det, const lma_region* region,
+                     uint32_t flags, double* out, void* stream);
+
+/* ---- local recompute (step a7, Sec. 4.2.6) --------------------------------------------- */
+
+/* Edit one atomic column in every configuration: atoms whose lateral
+ * minimum-image distance to (cx, cy) is below r_site are removed
+ * (LMA_EDIT_REMOVE) or set to new_species (LMA_EDIT_SET_SPECIES). Marks stale
+ * the transmission pixels within r_cut of the touched atoms and the exit waves
+ * whose W x W window meets those pixels; the next lma_image rebuilds and
+ * re-propagates only those. Outputs (may be NULL): number of atoms changed,
+ * number of exit waves marked stale. Host-only bookkeeping; no device work. */
+lma_status lma_edit_column(lma_ctx* ctx, lma_specimen* spec, lma_basis* basis, double cx,
+                           double cy, double r_site, int32_t op, int16_t new_species,
+                           int64_t* n_atoms_changed, int64_t* n_stale);
+
+/* For each probe of `region`, 1 if any of its L translates is stale, else 0
+ * (out_mask[npy][npx], host). Returns the count in *n_affected. Host-only. */
+lma_status lma_affected_probes(lma_ctx* ctx, lma_basis* basis, const lma_region* region,
+                               uint8_t* out_mask, int64_t* n_affected);
+
+/* ---- measurement ------------------------------------------------------------------------ */
+
+/* Launch counters and CUDA-event durations per kernel. `units` counts the work
+ * each launch did: pixel-slices (potential), translate-slices (slice),
+ * probes (synthesis), outputs (finalize). */
+typedef struct {
+  int64_t launches;
+  double total_ms;           /* sum of event-timed durations; 0 unless timing is on */
+  int64_t units;
+} lma_kernel_stat;
+
+typedef struct {
+  lma_kernel_stat potential;   /* step a1 */
+  lma_kernel_stat slice;       /* step a3 */
+  lma_kernel_stat synth;       /* steps a4-a5 (and the FP64 accumulation of a6) */
+  lma_kernel_stat finalize;    /* step a6 */
+} lma_profile;
+
+/* Reset the counters; with on != 0 also record a CUDA event pair around every
+ * kernel launch, on the stream the kernel is launched on. */
+lma_status lma_profile_enable(lma_ctx* ctx, int32_t on);
+/* Wait for the recorded events and return the totals since the last reset. */
+lma_status lma_profile_read(lma_ctx* ctx, lma_profile* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LMA_H */

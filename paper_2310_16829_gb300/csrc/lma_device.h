@@ -1,0 +1,73 @@
+// Internal interface between the host library (lma_host.cpp) and the CUDA
+// kernels (lma_kernels.cu). Not part of the public C-ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lma_dev {
+
+constexpr int kW = 128;              // propagation window W = detection window D
+constexpr int kThreads = 512;        // threads per CTA of the FFT kernels
+constexpr int kMaxTerms = 4;
+constexpr int kMaxDet = 4;
+
+// Step a1: projected potential and transmission of one configuration.
+struct PotArgs {
+  const double* ax;            // atom x (Angstrom), sorted by slice
+  const double* ay;            // atom y
+  const int16_t* asp;          // species
+  const int32_t* slice_start;  // [n_slices + 1]
+  const float* peak;           // [n_species] V*Angstrom
+  int n_species;
+  int n_terms;
+  float frac[kMaxTerms];
+  float inv2w2[kMaxTerms];     // 1 / (2 w^2)
+  float rc2;                   // r_cut^2
+  double rc;
+  int nx, ny, n_slices;
+  double dx, dy, lx, ly;
+  float dx_hi, dx_lo, dy_hi, dy_lo;
+  float sigma;
+  int rx0, ry0, rw, rh;        // pixel rectangle to (re)build, may wrap; full grid = (0,0,nx,ny)
+  float2* t;                   // [n_slices][ny][nx]
+};
+
+// Step a3: multislice of lattice translates on W x W windows.
+struct SliceArgs {
+  const float2* t;             // [n_slices][ny][nx]
+  int nx, ny, n_slices;
+  const float2* uW;            // [W][W] input wave, centre at (W/2, W/2)
+  const int32_t* list;         // translate indices to propagate
+  int n_list;
+  int lat_ox, lat_oy, lat_sx, lat_sy, lat_nax;   // I_f: pos(a, b) = (ox + a sx, oy + b sy)
+  float2* U;                   // [n_translates][W][W]
+  const float2* ex;            // [W] exp(-i pi lambda eps kx^2) / W^2
+  const float2* ey;            // [W] exp(-i pi lambda eps ky^2)
+  int r2max;                   // bandlimit: m'^2 + n'^2 <= r2max
+};
+
+// Steps a4-a6: synthesis, detector reading, FP64 accumulation over configurations.
+struct SynthArgs {
+  const float2* U;             // [n_translates][W][W]
+  const int32_t* tidx;         // [n_probes][L]
+  const float2* alpha;         // [n_probes][L]
+  const int2* shift;           // [n_probes][L] placement of U in the probe window
+  int L;
+  int n_probes;
+  int cyclic;                  // windows are the whole periodic grid
+  const uint32_t* det_bits;    // [n_det][kThreads] detector bits in C layout
+  int n_det;
+  double* acc;                 // [n_det][n_probes] sum over configurations
+};
+
+cudaError_t init_device_constants();
+size_t slice_smem_bytes();
+size_t synth_smem_bytes();
+cudaError_t launch_potential(const PotArgs& a, cudaStream_t s);
+cudaError_t launch_slice(const SliceArgs& a, cudaStream_t s);
+cudaError_t launch_synth(const SynthArgs& a, cudaStream_t s);
+cudaError_t launch_finalize(const double* acc, int64_t n, double scale, double* out,
+                            cudaStream_t s);
+
+}  // namespace lma_dev

@@ -1,0 +1,579 @@
+// CUDA kernels of the LMA hot path for sm_103a (GB300).
+//
+//   k_potential      step a1: v_s(x) = sum of Gaussian-sum atom potentials, t_s = exp(i sigma v_s)
+//                    (Sec. 3.2, transmission function)
+//   k_slice          step a3: multislice of each lattice translate u_i on its W x W window,
+//                    transmit -> 2D FFT -> propagator and bandlimit -> inverse 2D FFT per slice
+//                    (Fig. multislice_pseudocode on the window of option (ii), Sec. 4.2.1)
+//   k_synth_detect   steps a4-a6: Psi_p = sum_j alpha_j U_{i_j} on the D x D probe window
+//                    (Sec. 4.2.2), |DFT(Psi_p)|^2 summed over the annular detector (Sec. 3.1),
+//                    FP64 accumulation over frozen-phonon configurations
+//   k_finalize       step a6: average over configurations
+//
+// The 128 x 128 complex64 wave of one translate stays in registers of one
+// 512-thread CTA for all slices (32 values per thread). The 2D DFT is split
+// into three register passes over the 14 index bits (x = 4 n1 + r,
+// y = 32 n1y + n2y, Cooley-Tukey with 128 = 32 * 4 on each axis):
+//   pass A: 32-point DFT over n1 (x axis) + twiddle W_128^(r k1)   thread (y, r)
+//   pass B: 4-point DFTs over r (x axis) and n1y (y axis)
+//           + twiddle W_128^(n2y k1y)                              group (k1, n2y)
+//   pass C: 32-point DFT over n2y (y axis)                         thread (kx, k1y)
+// The propagator multiply sits in pass C; the inverse runs the passes back
+// (C, B, A) with conjugate twiddles, so no index permutation is ever stored.
+// Between passes the data crosses threads through padded shared-memory tables
+// (conflict-free 64-bit accesses). The transmission of the next slice is
+// prefetched with cp.async into the 128 KiB region that the exchanges are not
+// using at that time; the B -> A exchange then runs in two halves through a
+// separate 68 KiB region. The transmission is stored with a periodic halo of
+// W pixels ([ny + W][nx + W] per slice), so that every window is a plain
+// rectangle of the array.
+#include "lma_device.h"
+
+#include <cstdio>
+
+namespace lma_dev {
+
+// exp(-2 pi i m / 128), m = 0..127: built on the host in FP64 and rounded once.
+__constant__ float2 c_w128[128];
+
+// ------------------------------------------------------------------------------------------
+// complex helpers
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 cfma(float2 acc, float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
+}
+
+__host__ __device__ constexpr int brev5(int k) {
+  return ((k & 1) << 4) | ((k & 2) << 2) | (k & 4) | ((k & 8) >> 2) | ((k & 16) >> 4);
+}
+
+// d * W_32^m (forward) or d * W_32^-m (inverse); m is a compile-time constant after unrolling.
+template <bool INV>
+__device__ __forceinline__ float2 tw32(float2 d, int m) {
+  if (m == 0) return d;
+  if (m == 8) return INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
+  const float2 w = c_w128[4 * m];
+  return INV ? cmulc(d, w) : cmul(d, w);
+}
+
+// In-register 32-point DFT, natural order in and out (radix-2 decimation in
+// frequency, output reordered by register renaming).
+template <bool INV>
+__device__ __forceinline__ void dft32(float2 (&v)[32]) {
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int h = 16 >> st;
+#pragma unroll
+    for (int blk = 0; blk < 32; blk += 2 * h) {
+#pragma unroll
+      for (int j = 0; j < h; ++j) {
+        const float2 a = v[blk + j];
+        const float2 b = v[blk + j + h];
+        v[blk + j] = cadd(a, b);
+        v[blk + j + h] = tw32<INV>(csub(a, b), j * (16 / h));
+      }
+    }
+  }
+  float2 t[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) t[k] = v[brev5(k)];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = t[k];
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
+  // forward: X1 = d02 - i d13, X3 = d02 + i d13; inverse swaps the sign of i
+  const float2 j13 = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
+  a0 = cadd(s02, s13);
+  a2 = csub(s02, s13);
+  a1 = cadd(d02, j13);
+  a3 = csub(d02, j13);
+}
+
+// ------------------------------------------------------------------------------------------
+// the three passes
+// ------------------------------------------------------------------------------------------
+// pass A, thread (y, r): v[n1] = psi(y, 4 n1 + r) -> v[k1] after the x-axis 32-point stage
+// twA points at the row W_128^(r k), k = 0..31, of this thread's r
+__device__ __forceinline__ void passA_fwd(float2 (&v)[32], const float2* twA) {
+  dft32<false>(v);
+#pragma unroll
+  for (int k = 1; k < 32; ++k) v[k] = cmul(v[k], twA[k]);
+}
+__device__ __forceinline__ void passA_inv(float2 (&v)[32], const float2* twA) {
+#pragma unroll
+  for (int k = 1; k < 32; ++k) v[k] = cmulc(v[k], twA[k]);
+  dft32<true>(v);
+}
+
+// pass B, group (k1, n2y): a[n1y * 4 + r] -> a[k1y * 4 + k2x]
+// twB points at W_128^(n2y k1y), k1y = 0..3, of this group's n2y
+__device__ __forceinline__ void passB_fwd(float2 (&a)[16], const float2* twB) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dft4<false>(a[q * 4 + 0], a[q * 4 + 1], a[q * 4 + 2], a[q * 4 + 3]);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dft4<false>(a[0 * 4 + q], a[1 * 4 + q], a[2 * 4 + q], a[3 * 4 + q]);
+#pragma unroll
+  for (int k1y = 1; k1y < 4; ++k1y) {
+    const float2 w = twB[k1y];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a[k1y * 4 + q] = cmul(a[k1y * 4 + q], w);
+  }
+}
+__device__ __forceinline__ void passB_inv(float2 (&a)[16], const float2* twB) {
+#pragma unroll
+  for (int k1y = 1; k1y < 4; ++k1y) {
+    const float2 w = twB[k1y];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a[k1y * 4 + q] = cmulc(a[k1y * 4 + q], w);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dft4<true>(a[0 * 4 + q], a[1 * 4 + q], a[2 * 4 + q], a[3 * 4 + q]);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dft4<true>(a[q * 4 + 0], a[q * 4 + 1], a[q * 4 + 2], a[q * 4 + 3]);
+}
+
+// shared-memory layouts of the exchanges (float2 units); row paddings keep the
+// 64-bit accesses of every half-warp on 16 distinct bank pairs and make every
+// address a per-thread base plus a compile-time offset
+//   X1 (A <-> B), 512 x 33 entries: element (y, r, k1) at TA*33 + k1, TA = 4y + r
+//   X2 (B <-> C), 16384 entries: element (k1y, k2x, n2y, k1x) at ((k1y*4 + k2x)*32 + n2y)*32 + k1x
+//   X4 (B -> A, one half), 512 x 17 entries: element (y, r, k1 mod 16) at TA*17 + (k1 & 15)
+constexpr int kX1 = 512 * 33;
+constexpr int kX4 = 512 * 17;
+__device__ __forceinline__ int x1_addr(int ta, int k1) { return ta * 33 + k1; }
+__device__ __forceinline__ int x2_addr(int k1y, int k2x, int n2y, int k1x) {
+  return ((k1y * 4 + k2x) * 32 + n2y) * 32 + k1x;
+}
+__device__ __forceinline__ int x4_addr(int ta, int k1) { return ta * 17 + (k1 & 15); }
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// ------------------------------------------------------------------------------------------
+// per-CTA shared tables
+// ------------------------------------------------------------------------------------------
+// twA[r*32 + k] = W_128^(r k); twB[n2y*4 + k1y] = W_128^(n2y k1y)
+__device__ __forceinline__ void load_twiddles(float2* twA, float2* twB, int T) {
+  if (T < 128) {
+    twA[T] = c_w128[((T >> 5) * (T & 31)) & 127];
+    twB[T] = c_w128[((T >> 2) * (T & 3)) & 127];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// step a3: slice kernel
+// ------------------------------------------------------------------------------------------
+constexpr int kSliceSmemFloat2 = kX1 + kX4 + 3 * 128;
+
+__global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
+  extern __shared__ __align__(16) float2 sm[];
+  float2* R0 = sm;             // t prefetch (thread-private slots n1*512 + T) / exchanges X1, X2
+  float2* R1 = sm + kX1;       // exchange X4 (two halves)
+  float2* twA = R1 + kX4;
+  float2* twB = twA + 128;
+  float2* eys = twB + 128;
+
+  const int T = threadIdx.x;
+  load_twiddles(twA, twB, T);
+  if (T < 128) eys[T] = a.ey[T];
+  // A layout: thread (y, r)
+  const int ya = T >> 2, ra = T & 3;
+  // B layout: groups (k1 = (T & 15) + 16 h, n2y = T >> 4), h = 0, 1
+  const int k1lo = T & 15, n2y = T >> 4;
+  // C layout: thread (kx, k1y)
+  const int kx = T & 127, k1y = T >> 7, k1x = kx & 31, k2x = kx >> 5;
+  const float2* tA = twA + ra * 32;
+  const float2* tB = twB + n2y * 4;
+  const float2 exr = a.ex[kx];
+  uint32_t mbits = 0;
+  {
+    const int kxs = kx < 64 ? kx : kx - 128;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int ky = k1y + 4 * j;
+      const int kys = ky < 64 ? ky : ky - 128;
+      if (kxs * kxs + kys * kys <= a.r2max) mbits |= 1u << j;
+    }
+  }
+  __syncthreads();
+
+  const int pitch = a.nx + kW;                                    // padded row
+  const size_t slice_elems = static_cast<size_t>(pitch) * (a.ny + kW);
+  float2* const tslot = R0 + T;                                   // + n1 * 512
+  float2* const x1w = R0 + T * 33;                                // A side of X1
+  float2* const x1r = R0 + (4 * n2y) * 33 + k1lo;                 // B side of X1, + (128 q + r) * 33
+  float2* const x2b = R0 + n2y * 32 + k1lo;                       // B side of X2, + (q*4 + r) * 1024
+  float2* const x2c = R0 + (k1y * 4 + k2x) * 1024 + k1x;          // C side of X2, + j * 32
+  float2* const x4w = R1 + (4 * n2y) * 17 + k1lo;                 // B side of X4, + (128 q + r) * 17
+  float2* const x4r = R1 + T * 17;                                // A side of X4
+
+  for (int li = blockIdx.x; li < a.n_list; li += gridDim.x) {
+    const int ti = a.list[li];
+    const int ia = ti % a.lat_nax, ib = ti / a.lat_nax;
+    int ox = (a.lat_ox + ia * a.lat_sx - kW / 2) % a.nx;
+    if (ox < 0) ox += a.nx;
+    int oy = (a.lat_oy + ib * a.lat_sy - kW / 2) % a.ny;
+    if (oy < 0) oy += a.ny;
+    // the halo of W pixels keeps every window inside the padded array
+    const float2* tp = a.t + static_cast<size_t>(oy + ya) * pitch + ox + ra;
+
+#pragma unroll
+    for (int n1 = 0; n1 < 32; ++n1) cp_async8(tslot + n1 * kThreads, tp + 4 * n1);
+    cp_async_commit();
+
+    float2 v[32];
+#pragma unroll
+    for (int n1 = 0; n1 < 32; ++n1) v[n1] = a.uW[ya * kW + 4 * n1 + ra];
+
+    for (int s = 0; s < a.n_slices; ++s) {
+      // transmission (Sec. 3.2): psi <- t_s psi
+      cp_async_wait_all();
+#pragma unroll
+      for (int n1 = 0; n1 < 32; ++n1) v[n1] = cmul(v[n1], tslot[n1 * kThreads]);
+
+      // forward 2D DFT
+      passA_fwd(v, tA);
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < 32; ++k) x1w[k] = v[k];
+      __syncthreads();
+      float2 b0[16], b1[16];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          b0[q * 4 + r] = x1r[(128 * q + r) * 33];
+          b1[q * 4 + r] = x1r[(128 * q + r) * 33 + 16];
+        }
+      passB_fwd(b0, tB);
+      passB_fwd(b1, tB);
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          x2b[(q * 4 + r) * 1024] = b0[q * 4 + r];
+          x2b[(q * 4 + r) * 1024 + 16] = b1[q * 4 + r];
+        }
+      __syncthreads();
+      float2 c[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) c[j] = x2c[j * 32];
+      dft32<false>(c);
+      // propagation (Sec. 3.2): exp(-i pi lambda eps |k|^2), bandlimit, 1/W^2
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float2 pr = cmul(exr, eys[k1y + 4 * j]);
+        c[j] = ((mbits >> j) & 1u) ? cmul(c[j], pr) : make_float2(0.f, 0.f);
+      }
+      dft32<true>(c);
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < 32; ++j) x2c[j * 32] = c[j];
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          b0[q * 4 + r] = x2b[(q * 4 + r) * 1024];
+          b1[q * 4 + r] = x2b[(q * 4 + r) * 1024 + 16];
+        }
+      __syncthreads();  // R0 is free: prefetch the next slice's transmission
+      if (s + 1 < a.n_slices) {
+        const float2* tn = tp + (s + 1) * slice_elems;
+#pragma unroll
+        for (int n1 = 0; n1 < 32; ++n1) cp_async8(tslot + n1 * kThreads, tn + 4 * n1);
+        cp_async_commit();
+      }
+      passB_inv(b0, tB);
+      passB_inv(b1, tB);
+      // B -> A in two halves through R1
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) x4w[(128 * q + r) * 17] = b0[q * 4 + r];
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = x4r[k];
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) x4w[(128 * q + r) * 17] = b1[q * 4 + r];
+      __syncthreads();
+#pragma unroll
+      for (int k = 16; k < 32; ++k) v[k] = x4r[k - 16];
+      passA_inv(v, tA);
+    }
+
+    float2* ud = a.U + static_cast<size_t>(ti) * (kW * kW) + ya * kW + ra;
+#pragma unroll
+    for (int n1 = 0; n1 < 32; ++n1) ud[4 * n1] = v[n1];
+    __syncthreads();  // R1 reads of this translate finish before the next one writes
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// steps a4-a6: synthesis and detector reading
+// ------------------------------------------------------------------------------------------
+constexpr int kSynthSmemFloat2 = kX1 + 2 * 128 + (kThreads / 32) * kMaxDet;
+
+__global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a) {
+  extern __shared__ __align__(16) float2 sm[];
+  float2* R0 = sm;
+  float2* twA = sm + kX1;
+  float2* twB = twA + 128;
+  float* red = reinterpret_cast<float*>(twB + 128);   // [16 warps][kMaxDet]
+
+  const int T = threadIdx.x;
+  load_twiddles(twA, twB, T);
+  const int ya = T >> 2, ra = T & 3;
+  const int k1lo = T & 15, n2y = T >> 4;
+  const int kx = T & 127, k1y = T >> 7, k1x = kx & 31, k2x = kx >> 5;
+  const float2* tA = twA + ra * 32;
+  const float2* tB = twB + n2y * 4;
+  float2* const x1w = R0 + T * 33;
+  float2* const x1r = R0 + (4 * n2y) * 33 + k1lo;
+  float2* const x2b = R0 + n2y * 32 + k1lo;
+  float2* const x2c = R0 + (k1y * 4 + k2x) * 1024 + k1x;
+  uint32_t dbits[kMaxDet];
+#pragma unroll
+  for (int d = 0; d < kMaxDet; ++d) dbits[d] = d < a.n_det ? a.det_bits[d * kThreads + T] : 0u;
+  __syncthreads();
+
+  for (int p = blockIdx.x; p < a.n_probes; p += gridDim.x) {
+    float2 v[32];
+#pragma unroll
+    for (int n1 = 0; n1 < 32; ++n1) v[n1] = make_float2(0.f, 0.f);
+    const int32_t* tp = a.tidx + static_cast<size_t>(p) * a.L;
+    const float2* ap = a.alpha + static_cast<size_t>(p) * a.L;
+    const int2* sp = a.shift + static_cast<size_t>(p) * a.L;
+    for (int j = 0; j < a.L; ++j) {
+      const float2 al = ap[j];
+      const int2 sh = sp[j];
+      int yy = ya - sh.y;
+      if (a.cyclic) {
+        yy &= (kW - 1);
+      } else if (yy < 0 || yy >= kW) {
+        continue;
+      }
+      const float2* row = a.U + static_cast<size_t>(tp[j]) * (kW * kW) + yy * kW;
+      const int x0 = ra - sh.x;
+#pragma unroll
+      for (int n1 = 0; n1 < 32; ++n1) {
+        int xx = x0 + 4 * n1;
+        if (a.cyclic) {
+          xx &= (kW - 1);
+          v[n1] = cfma(v[n1], al, row[xx]);
+        } else if (xx >= 0 && xx < kW) {
+          v[n1] = cfma(v[n1], al, row[xx]);
+        }
+      }
+    }
+    // forward 2D DFT of Psi_p (passes A, B, C)
+    passA_fwd(v, tA);
+    __syncthreads();   // previous probe's C reads are done
+#pragma unroll
+    for (int k = 0; k < 32; ++k) x1w[k] = v[k];
+    __syncthreads();
+    float2 b0[16], b1[16];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        b0[q * 4 + r] = x1r[(128 * q + r) * 33];
+        b1[q * 4 + r] = x1r[(128 * q + r) * 33 + 16];
+      }
+    passB_fwd(b0, tB);
+    passB_fwd(b1, tB);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        x2b[(q * 4 + r) * 1024] = b0[q * 4 + r];
+        x2b[(q * 4 + r) * 1024 + 16] = b1[q * 4 + r];
+      }
+    __syncthreads();
+    float2 c[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) c[j] = x2c[j * 32];
+    dft32<false>(c);
+    // detector (Sec. 3.1, 2D STEM): sum of |DFT|^2 over the annulus
+    const int warp = T >> 5, lane = T & 31;
+#pragma unroll
+    for (int d = 0; d < kMaxDet; ++d) {
+      if (d >= a.n_det) break;
+      float sum = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if ((dbits[d] >> j) & 1u) sum = fmaf(c[j].x, c[j].x, fmaf(c[j].y, c[j].y, sum));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (lane == 0) red[warp * kMaxDet + d] = sum;
+    }
+    __syncthreads();
+    if (T < a.n_det) {
+      double tot = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) tot += static_cast<double>(red[w * kMaxDet + T]);
+      a.acc[static_cast<size_t>(T) * a.n_probes + p] += tot * (1.0 / (kW * kW));
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// step a1: potential and transmission
+// ------------------------------------------------------------------------------------------
+struct AtomRel {
+  float x_hi, x_lo, y_hi, y_lo, peak;
+};
+
+// One CTA = a 16 x 16 pixel tile of one slice. Atoms of the slice are filtered
+// against the tile in list order (ordered compaction), so every pixel adds its
+// atom terms in the same order whatever the tile or rectangle: a partial
+// rebuild is bitwise equal to a full one. Each pixel value is written to all
+// its periodic copies in the padded array [ny + W][nx + W].
+__global__ void __launch_bounds__(256) k_potential(const PotArgs a) {
+  __shared__ AtomRel lst[256];
+  __shared__ int wcount[8];
+  const int s = blockIdx.z;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int bx = blockIdx.x * 16, by = blockIdx.y * 16;
+  const bool in_rect = (bx + tx < a.rw) && (by + ty < a.rh);
+  const int gx0 = (a.rx0 + bx) % a.nx;
+  const int gy0 = (a.ry0 + by) % a.ny;
+  // atoms are taken relative to the tile origin; the minimum image is found in FP64
+  const double Xc = (gx0 + 7.5) * a.dx, Yc = (gy0 + 7.5) * a.dy;
+  const double limx = a.rc + 8.0 * a.dx, limy = a.rc + 8.0 * a.dy;
+  const int a0 = a.slice_start[s], a1 = a.slice_start[s + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float v = 0.f;
+  for (int base = a0; base < a1; base += 256) {
+    const int k = base + threadIdx.x;
+    bool keep = false;
+    AtomRel e{0.f, 0.f, 0.f, 0.f, 0.f};
+    if (k < a1) {
+      double ddx = a.ax[k] - Xc, ddy = a.ay[k] - Yc;
+      ddx -= a.lx * floor(ddx / a.lx + 0.5);
+      ddy -= a.ly * floor(ddy / a.ly + 0.5);
+      keep = fabs(ddx) < limx && fabs(ddy) < limy;
+      const double rx = ddx + 7.5 * a.dx, ry = ddy + 7.5 * a.dy;
+      e.x_hi = static_cast<float>(rx);
+      e.x_lo = static_cast<float>(rx - static_cast<double>(e.x_hi));
+      e.y_hi = static_cast<float>(ry);
+      e.y_lo = static_cast<float>(ry - static_cast<double>(e.y_hi));
+      const int spc = a.asp[k];
+      e.peak = (spc >= 0 && spc < a.n_species) ? a.peak[spc] : 0.f;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) wcount[warp] = __popc(bal);
+    __syncthreads();
+    int off = 0, total = 0;
+    for (int w = 0; w < 8; ++w) {
+      off += (w < warp) ? wcount[w] : 0;
+      total += wcount[w];
+    }
+    if (keep) lst[off + __popc(bal & ((1u << lane) - 1u))] = e;
+    __syncthreads();
+    for (int j = 0; j < total; ++j) {
+      const AtomRel at = lst[j];
+      const float ddx = fmaf(static_cast<float>(tx), a.dx_hi, -at.x_hi) +
+                        fmaf(static_cast<float>(tx), a.dx_lo, -at.x_lo);
+      const float ddy = fmaf(static_cast<float>(ty), a.dy_hi, -at.y_hi) +
+                        fmaf(static_cast<float>(ty), a.dy_lo, -at.y_lo);
+      const float r2 = ddx * ddx + ddy * ddy;
+      if (r2 < a.rc2) {
+        float g = 0.f;
+        for (int q = 0; q < a.n_terms; ++q) g = fmaf(a.frac[q], expf(-r2 * a.inv2w2[q]), g);
+        v = fmaf(at.peak, g, v);
+      }
+    }
+    __syncthreads();
+  }
+  if (in_rect) {
+    int gx = gx0 + tx;
+    if (gx >= a.nx) gx -= a.nx;
+    int gy = gy0 + ty;
+    if (gy >= a.ny) gy -= a.ny;
+    float sn, cs;
+    sincosf(a.sigma * v, &sn, &cs);
+    const float2 tv = make_float2(cs, sn);
+    const int pitch = a.nx + kW;
+    float2* ts = a.t + static_cast<size_t>(s) * pitch * (a.ny + kW);
+    ts[static_cast<size_t>(gy) * pitch + gx] = tv;
+    const bool hx = gx < kW, hy = gy < kW;
+    if (hx) ts[static_cast<size_t>(gy) * pitch + gx + a.nx] = tv;
+    if (hy) ts[static_cast<size_t>(gy + a.ny) * pitch + gx] = tv;
+    if (hx && hy) ts[static_cast<size_t>(gy + a.ny) * pitch + gx + a.nx] = tv;
+  }
+}
+
+__global__ void k_finalize(const double* acc, int64_t n, double scale, double* out) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = acc[i] * scale;
+}
+
+// ------------------------------------------------------------------------------------------
+// host-side launchers
+// ------------------------------------------------------------------------------------------
+size_t slice_smem_bytes() { return static_cast<size_t>(kSliceSmemFloat2) * sizeof(float2); }
+size_t synth_smem_bytes() { return static_cast<size_t>(kSynthSmemFloat2) * sizeof(float2); }
+
+cudaError_t init_device_constants() {
+  float2 w[128];
+  const double pi = 3.14159265358979323846;
+  for (int m = 0; m < 128; ++m) {
+    const double ang = -2.0 * pi * m / 128.0;
+    w[m] = make_float2(static_cast<float>(cos(ang)), static_cast<float>(sin(ang)));
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_w128, w, sizeof(w));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_slice, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(slice_smem_bytes()));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_synth_detect, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(synth_smem_bytes()));
+}
+
+cudaError_t launch_potential(const PotArgs& a, cudaStream_t s) {
+  dim3 grid((a.rw + 15) / 16, (a.rh + 15) / 16, a.n_slices);
+  k_potential<<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slice(const SliceArgs& a, cudaStream_t s) {
+  if (a.n_list <= 0) return cudaSuccess;
+  k_slice<<<a.n_list, kThreads, slice_smem_bytes(), s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_synth(const SynthArgs& a, cudaStream_t s) {
+  if (a.n_probes <= 0) return cudaSuccess;
+  k_synth_detect<<<a.n_probes, kThreads, synth_smem_bytes(), s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double* acc, int64_t n, double scale, double* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = static_cast<int>((n + 255) / 256);
+  k_finalize<<<blocks, 256, 0, s>>>(acc, n, scale, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lma_dev

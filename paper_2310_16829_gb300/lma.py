@@ -1,0 +1,365 @@
+"""ctypes binding of the LMA C-ABI (include/lma.h).
+
+Argument marshalling only: every step of the path runs in the CUDA library
+``_build/liblma.so``, built in-tree by ``paper_2310_16829_gb300.build``. There
+is no fallback: ``load()`` raises if the library is missing.
+
+Array arguments may be numpy arrays (host memory) or torch CUDA tensors
+(device memory, passed by ``data_ptr()``); streams are torch streams or raw
+``cudaStream_t`` integers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblma.so")
+
+LMA_OK = 0
+LMA_ERR_INVALID = 1
+LMA_ERR_OOM = 2
+LMA_ERR_CUDA = 3
+LMA_ERR_TIMEOUT = 4
+LMA_ERR_UNSUPPORTED = 5
+STATUS_NAMES = {0: "LMA_OK", 1: "LMA_ERR_INVALID", 2: "LMA_ERR_OOM", 3: "LMA_ERR_CUDA",
+                4: "LMA_ERR_TIMEOUT", 5: "LMA_ERR_UNSUPPORTED"}
+
+LMA_BASIS_GAUSS = 0
+LMA_BASIS_PROBE = 1
+LMA_PREC_C64 = 0
+LMA_EDIT_REMOVE = 0
+LMA_EDIT_SET_SPECIES = 1
+LMA_IMAGE_RECOMPUTE = 1
+
+# every symbol include/lma.h declares (checked by the CPU tests)
+EXPORTS = [
+    "lma_create", "lma_destroy", "lma_last_error",
+    "lma_create_specimen", "lma_free_specimen", "lma_specimen_set_atoms", "lma_transmission",
+    "lma_create_basis", "lma_free_basis", "lma_basis_get_info", "lma_basis_coefficients",
+    "lma_propagate_basis", "lma_exit_wave",
+    "lma_image", "lma_edit_column", "lma_affected_probes",
+    "lma_profile_enable", "lma_profile_read",
+]
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("lx", C.c_double), ("ly", C.c_double),
+                ("slice_dz", C.c_double), ("n_slices", C.c_int32), ("lam", C.c_double),
+                ("sigma", C.c_double), ("bandlimit_frac", C.c_double)]
+
+
+class Potential(C.Structure):
+    _fields_ = [("n_species", C.c_int32), ("peak", C.POINTER(C.c_double)), ("n_terms", C.c_int32),
+                ("term_frac", C.POINTER(C.c_double)), ("term_width", C.POINTER(C.c_double)),
+                ("r_cut", C.c_double)]
+
+
+class Atoms(C.Structure):
+    _fields_ = [("n_atoms", C.c_int64), ("x", C.POINTER(C.c_double)), ("y", C.POINTER(C.c_double)),
+                ("slice", C.POINTER(C.c_int32)), ("species", C.POINTER(C.c_int16))]
+
+
+class Probe(C.Structure):
+    _fields_ = [("alpha_max", C.c_double), ("cs", C.c_double), ("defocus", C.c_double)]
+
+
+class BasisDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("gauss_sigma", C.c_double), ("in_spacing_px", C.c_int32 * 2),
+                ("in_offset_px", C.c_int32 * 2), ("f", C.c_int32), ("L", C.c_int32),
+                ("window", C.c_int32), ("det_window", C.c_int32), ("precision", C.c_int32)]
+
+
+class Detector(C.Structure):
+    _fields_ = [("r1", C.c_double), ("r2", C.c_double)]
+
+
+class Region(C.Structure):
+    _fields_ = [("px0", C.c_int32), ("py0", C.c_int32), ("npx", C.c_int32), ("npy", C.c_int32),
+                ("spacing_px", C.c_int32 * 2)]
+
+
+class BasisInfo(C.Structure):
+    _fields_ = [("n_translates", C.c_int64), ("nax", C.c_int32), ("nay", C.c_int32),
+                ("n_sets", C.c_int32), ("L", C.c_int32), ("window", C.c_int32),
+                ("det_window", C.c_int32), ("gauss_sigma", C.c_double),
+                ("exit_wave_bytes", C.c_int64)]
+
+
+class KernelStat(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("total_ms", C.c_double), ("units", C.c_int64)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("potential", KernelStat), ("slice", KernelStat), ("synth", KernelStat),
+                ("finalize", KernelStat)]
+
+    def as_dict(self):
+        return {k: {"launches": int(getattr(self, k).launches), "total_ms": float(getattr(self, k).total_ms),
+                    "units": int(getattr(self, k).units)} for k, _ in self._fields_}
+
+
+class LmaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_VP = C.c_void_p
+_SIGS = {
+    "lma_create": (C.c_int32, [C.c_int32, C.POINTER(_VP)]),
+    "lma_destroy": (None, [_VP]),
+    "lma_last_error": (C.c_char_p, [_VP]),
+    "lma_create_specimen": (C.c_int32, [_VP, C.POINTER(Grid), C.POINTER(Potential), C.POINTER(Atoms),
+                                        C.c_int32, C.POINTER(_VP)]),
+    "lma_free_specimen": (C.c_int32, [_VP]),
+    "lma_specimen_set_atoms": (C.c_int32, [_VP, _VP, C.POINTER(Atoms), C.c_int32]),
+    "lma_profile_enable": (C.c_int32, [_VP, C.c_int32]),
+    "lma_profile_read": (C.c_int32, [_VP, C.POINTER(Profile)]),
+    "lma_transmission": (C.c_int32, [_VP, _VP, C.c_int32, _VP, _VP]),
+    "lma_create_basis": (C.c_int32, [_VP, _VP, C.POINTER(Probe), C.POINTER(BasisDesc), C.POINTER(_VP)]),
+    "lma_free_basis": (C.c_int32, [_VP]),
+    "lma_basis_get_info": (C.c_int32, [_VP, C.POINTER(BasisInfo)]),
+    "lma_basis_coefficients": (C.c_int32, [_VP, _VP, C.c_int32, C.c_int32, _VP, _VP, _VP, _VP]),
+    "lma_propagate_basis": (C.c_int32, [_VP, _VP, _VP, C.c_int32, _VP]),
+    "lma_exit_wave": (C.c_int32, [_VP, _VP, C.c_int64, _VP, _VP]),
+    "lma_image": (C.c_int32, [_VP, _VP, _VP, C.POINTER(Detector), C.c_int32, C.POINTER(Region),
+                              C.c_uint32, _VP, _VP]),
+    "lma_edit_column": (C.c_int32, [_VP, _VP, _VP, C.c_double, C.c_double, C.c_double, C.c_int32,
+                                    C.c_int16, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "lma_affected_probes": (C.c_int32, [_VP, _VP, C.POINTER(Region), _VP, C.POINTER(C.c_int64)]),
+}
+
+_LIB: Optional[C.CDLL] = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"LMA CUDA library not built: {path} is missing "
+                           "(run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return 0
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return int(a.data_ptr())
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _stream(s) -> int:
+    if s is None:
+        return 0
+    if hasattr(s, "cuda_stream"):
+        return int(s.cuda_stream)
+    return int(s)
+
+
+class Context:
+    """An lma_ctx; device = -1 gives a host-only context."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        h = _VP()
+        st = self.lib.lma_create(device, C.byref(h))
+        if st != LMA_OK:
+            raise LmaError(st, f"lma_create({device}) failed")
+        self.h = h
+        self.device = device
+
+    def check(self, st: int) -> None:
+        if st != LMA_OK:
+            raise LmaError(st, self.lib.lma_last_error(self.h).decode())
+
+    def profile_enable(self, on: bool = True) -> None:
+        self.check(self.lib.lma_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self) -> dict:
+        p = Profile()
+        self.check(self.lib.lma_profile_read(self.h, C.byref(p)))
+        return p.as_dict()
+
+    def close(self) -> None:
+        if self.h:
+            self.lib.lma_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Specimen:
+    """An lma_specimen built from a ``workloads.Workload`` (or its parts)."""
+
+    def __init__(self, ctx: Context, grid, potential, phonons: Sequence):
+        self.ctx = ctx
+        self.grid = grid
+        g = Grid(grid.nx, grid.ny, grid.lx, grid.ly, grid.slice_dz, grid.n_slices, grid.lam,
+                 grid.sigma, grid.bandlimit_frac)
+        self._keep: List = []
+        peak = _f64(potential.peak)
+        frac = _f64(potential.term_frac)
+        width = _f64(potential.term_width)
+        self._keep += [peak, frac, width]
+        pot = Potential(len(peak), peak.ctypes.data_as(C.POINTER(C.c_double)), len(frac),
+                        frac.ctypes.data_as(C.POINTER(C.c_double)),
+                        width.ctypes.data_as(C.POINTER(C.c_double)), potential.r_cut)
+        arr = self._atoms_array(phonons)
+        h = _VP()
+        ctx.check(ctx.lib.lma_create_specimen(ctx.h, C.byref(g), C.byref(pot), arr, len(phonons),
+                                              C.byref(h)))
+        self._keep = []   # the library copied everything
+        self.h = h
+        self.n_phonons = len(phonons)
+
+    def _atoms_array(self, phonons):
+        arr = (Atoms * len(phonons))()
+        for k, at in enumerate(phonons):
+            x, y = _f64(at.x), _f64(at.y)
+            s = np.ascontiguousarray(at.slice, dtype=np.int32)
+            sp = np.ascontiguousarray(at.species, dtype=np.int16)
+            self._keep += [x, y, s, sp]
+            arr[k] = Atoms(x.shape[0], x.ctypes.data_as(C.POINTER(C.c_double)),
+                           y.ctypes.data_as(C.POINTER(C.c_double)),
+                           s.ctypes.data_as(C.POINTER(C.c_int32)),
+                           sp.ctypes.data_as(C.POINTER(C.c_int16)))
+        return arr
+
+    def set_atoms(self, phonons: Sequence) -> None:
+        arr = self._atoms_array(phonons)
+        try:
+            self.ctx.check(self.ctx.lib.lma_specimen_set_atoms(self.ctx.h, self.h, arr, len(phonons)))
+        finally:
+            self._keep = []
+
+    def transmission(self, phonon: int, out=None, stream=None) -> np.ndarray:
+        g = self.grid
+        if out is None:
+            out = np.empty((g.n_slices, g.ny, g.nx), dtype=np.complex64)
+        self.ctx.check(self.ctx.lib.lma_transmission(self.ctx.h, self.h, phonon, _ptr(out),
+                                                     _stream(stream)))
+        return out
+
+    def edit_column(self, basis: Optional["Basis"], cx: float, cy: float, r_site: float, op: int,
+                    new_species: int = 0):
+        n_changed = C.c_int64()
+        n_stale = C.c_int64()
+        self.ctx.check(self.ctx.lib.lma_edit_column(self.ctx.h, self.h, basis.h if basis else None,
+                                                    cx, cy, r_site, op, new_species,
+                                                    C.byref(n_changed), C.byref(n_stale)))
+        return int(n_changed.value), int(n_stale.value)
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.lma_free_specimen(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _region(r) -> Region:
+    return Region(r.px0, r.py0, r.npx, r.npy, (C.c_int32 * 2)(*r.spacing_px))
+
+
+class Basis:
+    """An lma_basis (input-wave lattice, coefficients, resident exit waves)."""
+
+    def __init__(self, ctx: Context, spec: Specimen, probe, desc):
+        self.ctx = ctx
+        self.spec = spec
+        pr = Probe(probe.alpha_max, probe.cs, probe.defocus)
+        d = BasisDesc(desc.kind, desc.gauss_sigma, (C.c_int32 * 2)(*desc.in_spacing_px),
+                      (C.c_int32 * 2)(*desc.in_offset_px), desc.f, desc.L, desc.window,
+                      desc.det_window, getattr(desc, "precision", LMA_PREC_C64))
+        h = _VP()
+        ctx.check(ctx.lib.lma_create_basis(ctx.h, spec.h, C.byref(pr), C.byref(d), C.byref(h)))
+        self.h = h
+        self.L = desc.L
+        self.W = desc.window
+
+    def info(self) -> BasisInfo:
+        i = BasisInfo()
+        self.ctx.check(self.ctx.lib.lma_basis_get_info(self.h, C.byref(i)))
+        return i
+
+    def coefficients(self, px: int, py: int):
+        L = self.L
+        al = np.empty(2 * L, dtype=np.float64)
+        off = np.empty(2 * L, dtype=np.int32)
+        tr = np.empty(L, dtype=np.int64)
+        err = np.empty(2, dtype=np.float64)
+        self.ctx.check(self.ctx.lib.lma_basis_coefficients(self.ctx.h, self.h, px, py, _ptr(al),
+                                                           _ptr(off), _ptr(tr), _ptr(err)))
+        return al[0::2] + 1j * al[1::2], off.reshape(L, 2), tr, err
+
+    def propagate(self, phonon: int, stream=None) -> None:
+        self.ctx.check(self.ctx.lib.lma_propagate_basis(self.ctx.h, self.spec.h, self.h, phonon,
+                                                        _stream(stream)))
+
+    def exit_wave(self, translate: int, out=None, stream=None) -> np.ndarray:
+        if out is None:
+            out = np.empty((self.W, self.W), dtype=np.complex64)
+        self.ctx.check(self.ctx.lib.lma_exit_wave(self.ctx.h, self.h, translate, _ptr(out),
+                                                  _stream(stream)))
+        return out
+
+    def image(self, detectors, region, out=None, recompute: bool = False, stream=None):
+        dets = (Detector * len(detectors))(*[Detector(d.r1, d.r2) for d in detectors])
+        if out is None:
+            out = np.empty((len(detectors), region.npy, region.npx), dtype=np.float64)
+        reg = _region(region)
+        flags = LMA_IMAGE_RECOMPUTE if recompute else 0
+        self.ctx.check(self.ctx.lib.lma_image(self.ctx.h, self.spec.h, self.h, dets, len(detectors),
+                                              C.byref(reg), flags, _ptr(out), _stream(stream)))
+        return out
+
+    def affected_probes(self, region) -> np.ndarray:
+        mask = np.empty((region.npy, region.npx), dtype=np.uint8)
+        n = C.c_int64()
+        reg = _region(region)
+        self.ctx.check(self.ctx.lib.lma_affected_probes(self.ctx.h, self.h, C.byref(reg), _ptr(mask),
+                                                        C.byref(n)))
+        return mask
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.lma_free_basis(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

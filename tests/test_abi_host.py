@@ -1,0 +1,132 @@
+"""CPU checks of the C-ABI library: exports and the host-side logic (no device compute).
+
+The host-only context (device = -1) runs the FP64 coefficient builder, the
+lattice geometry and the edit bookkeeping; these are compared with the oracle.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import lma_oracle as O
+from paper_2310_16829_gb300 import lma, workloads as WL
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_functions():
+    src = open(os.path.join(ROOT, "include", "lma.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lma_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_function():
+    lib = lma.load()
+    declared = _header_functions()
+    assert declared == sorted(lma.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def _host_objects(w):
+    ctx = lma.Context(-1)
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    return ctx, spec, basis
+
+
+def _check_coefficients(w, probes, tol=1e-9):
+    ctx, spec, basis = _host_objects(w)
+    orc = O.LmaOracle(O.params_from_workload(w))
+    for (px, py) in probes:
+        al, off, tr, err = basis.coefficients(px, py)
+        cs, idx = orc.coefficient_set((px, py))
+        assert np.array_equal(off, cs.offsets), (px, py)
+        assert np.array_equal(tr, idx), (px, py)
+        assert np.max(np.abs(al - cs.alpha)) < tol * np.max(np.abs(cs.alpha))
+        assert abs(err[0] - cs.err_l2) < 1e-9 and abs(err[1] - cs.err_sup) < 1e-9
+    return basis
+
+
+def test_coefficients_match_oracle_periodic_window():
+    w = WL.simple_cubic_workload()
+    b = _check_coefficients(w, [(0, 0), (8, 120), (127, 3)])
+    assert b.info().n_sets == 2   # (0,0) and (8,120) share a class; (127,3) has its own
+
+
+def test_coefficients_match_oracle_case1_single_set():
+    w = WL.simple_cubic_workload()
+    ctx, spec, basis = _host_objects(w)
+    for p in [(0, 0), (8, 16), (120, 64), (40, 40)]:
+        basis.coefficients(*p)
+    assert basis.info().n_sets == 1      # Case 1: one coefficient set for the whole probe lattice
+
+
+def test_coefficients_match_oracle_case2_and_probe_basis():
+    w = WL.simple_cubic_workload()
+    w.basis.kind = WL.BASIS_PROBE
+    w.basis.L = 9
+    _check_coefficients(w, [(0, 0), (1, 2), (2, 2), (3, 1)], tol=1e-8)
+
+
+def test_coefficients_match_oracle_on_a_512_grid():
+    w = WL.perovskite_workload(n_phonons=1)
+    _check_coefficients(w, [(0, 0), (508, 4)])
+
+
+def test_basis_info_and_lattice_count():
+    w = WL.perovskite_workload(n_phonons=1)
+    ctx, spec, basis = _host_objects(w)
+    i = basis.info()
+    assert i.n_translates == 128 * 128 and i.nax == 128 and i.nay == 128
+    assert abs(i.gauss_sigma - O.gaussian_width(w.grid.lam, w.probe.alpha_max)) < 1e-15
+    assert i.exit_wave_bytes == 128 * 128 * 128 * 128 * 8
+
+
+def test_validation_errors():
+    w = WL.simple_cubic_workload()
+    ctx = lma.Context(-1)
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    bad = [
+        dict(in_spacing_px=(3, 4)),        # does not divide the grid
+        dict(in_offset_px=(4, 0)),         # offset >= spacing
+        dict(f=3),                         # does not divide R
+        dict(L=0),
+        dict(L=65),
+    ]
+    for kw in bad:
+        d = WL.BasisDesc(**{**w.basis.__dict__, **kw})
+        with pytest.raises(lma.LmaError) as e:
+            lma.Basis(ctx, spec, w.probe, d)
+        assert e.value.status == lma.LMA_ERR_INVALID, kw
+    d = WL.BasisDesc(**{**w.basis.__dict__, "window": 64})
+    with pytest.raises(lma.LmaError) as e:
+        lma.Basis(ctx, spec, w.probe, d)
+    assert e.value.status == lma.LMA_ERR_UNSUPPORTED
+    # atoms with a slice out of range
+    at = w.phonons[0]
+    bad_at = WL.Atoms(at.x, at.y, at.slice + 100, at.species)
+    with pytest.raises(lma.LmaError) as e:
+        lma.Specimen(ctx, w.grid, w.potential, [bad_at])
+    assert e.value.status == lma.LMA_ERR_INVALID
+    # device calls on a host-only context
+    b = lma.Basis(ctx, spec, w.probe, w.basis)
+    with pytest.raises(lma.LmaError) as e:
+        b.propagate(0)
+    assert e.value.status == lma.LMA_ERR_UNSUPPORTED
+
+
+def test_edit_bookkeeping_matches_oracle_edit():
+    w = WL.perovskite_workload(n_phonons=2, cells=10, nx=512, n_slices=4)
+    ctx = lma.Context(-1)
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    cx, cy = 4.5 * WL.ABO3_A, 7.5 * WL.ABO3_A   # the O/B column at (1/2, 1/2) of cell (4, 7)
+    n_changed, n_stale = spec.edit_column(None, cx, cy, 0.5, lma.LMA_EDIT_REMOVE)
+    expect = 0
+    for at in w.phonons:
+        *_, nhit = O.edit_column(at.x, at.y, at.slice, at.species, w.grid.lx, w.grid.ly, cx, cy, 0.5, 0, 0)
+        expect += nhit
+    assert n_changed == expect and expect > 0 and n_stale == 0

@@ -1,0 +1,217 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances. The complex64 path must meet the bound of 1e-4 maximum relative
+error per HAADF pixel. Intermediate arrays are held to tighter, derived
+bounds: the transmission t = exp(i sigma v) to 2e-6 absolute (|t| = 1, FP32
+potential sum and sincos), exit waves to 5e-5 of their peak after up to 50
+slices of FP32 2D FFTs (about 2^-24 * log2(16384) per transform, accumulated
+over 100 transforms).
+"""
+import numpy as np
+import pytest
+
+from oracle import lma_oracle as O
+from paper_2310_16829_gb300 import lma, workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+PIXEL_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return lma.Context(0)
+
+
+def _oracle(w):
+    orc = O.LmaOracle(O.params_from_workload(w))
+    orc.set_specimen(w.phonons, w.potential.peak, w.potential.term_frac, w.potential.term_width,
+                     w.potential.r_cut)
+    return orc
+
+
+def _probes(region, nx, ny):
+    return O.region_probes(region.px0, region.py0, region.npx, region.npy, region.spacing_px, nx, ny)
+
+
+def _rel_pixel_err(got, ref):
+    ref = np.asarray(ref)
+    assert np.all(ref > 0)
+    return float(np.max(np.abs(np.asarray(got) - ref) / ref))
+
+
+def test_transmission_matches_oracle_simple_cubic(ctx):
+    w = WL.simple_cubic_workload()
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    t = spec.transmission(0)
+    ref = _oracle(w).transmission_stack(0)
+    assert np.max(np.abs(t - ref)) < 2e-6
+
+
+def test_transmission_matches_oracle_perovskite_with_phonons(ctx):
+    w = WL.perovskite_workload(n_phonons=2, n_slices=6)
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    orc = _oracle(w)
+    for phi in (0, 1):
+        t = spec.transmission(phi)
+        assert np.max(np.abs(t - orc.transmission_stack(phi))) < 2e-6
+
+
+def test_exit_waves_match_oracle_periodic_window(ctx):
+    w = WL.simple_cubic_workload()
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    basis.propagate(0)
+    orc = _oracle(w)
+    for i in (0, 31, 33, 517, 1023):
+        got = basis.exit_wave(i)
+        ref = orc.exit_wave(0, i)
+        assert np.max(np.abs(got - ref)) < 5e-5 * np.max(np.abs(ref)), i
+
+
+def test_exit_waves_match_oracle_full_thickness_512(ctx):
+    # 512^2 grid, 50 slices of 2 A, windows that wrap around the cell edge
+    w = WL.perovskite_workload(n_phonons=1)
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    basis.propagate(0)
+    orc = _oracle(w)
+    for i in (0, 127, 128 * 64 + 70, 128 * 128 - 1):
+        got = basis.exit_wave(i)
+        ref = orc.exit_wave(0, i)
+        assert np.max(np.abs(got - ref)) < 5e-5 * np.max(np.abs(ref)), i
+
+
+def test_image_simple_cubic_full(ctx):
+    w = WL.simple_cubic_workload()
+    dets = [WL.Detector(0.0, 0.02), WL.Detector(0.02, 0.06), WL.Detector(0.06, 0.2)]
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    img = basis.image(dets, w.region)
+    ref = _oracle(w).image(dets, _probes(w.region, 128, 128))
+    assert _rel_pixel_err(img.reshape(3, -1), ref) < PIXEL_TOL
+    # reuse of resident exit waves gives the same bits
+    again = basis.image(dets, w.region)
+    assert np.array_equal(img, again)
+
+
+def test_image_ragged_region_many_coefficient_sets(ctx):
+    w = WL.simple_cubic_workload()
+    region = WL.Region(px0=3, py0=5, npx=13, npy=7, spacing_px=(3, 5))
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    img = basis.image(w.detectors, region)
+    assert basis.info().n_sets > 4
+    ref = _oracle(w).image(w.detectors, _probes(region, 128, 128))
+    assert _rel_pixel_err(img.reshape(1, -1), ref) < PIXEL_TOL
+
+
+def test_image_probe_input_waves(ctx):
+    w = WL.simple_cubic_workload()
+    w.basis.kind = WL.BASIS_PROBE
+    w.basis.L = 9
+    region = WL.Region(0, 0, 6, 5, (8, 8))
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    img = basis.image(w.detectors, region)
+    ref = _oracle(w).image(w.detectors, _probes(region, 128, 128))
+    assert _rel_pixel_err(img.reshape(1, -1), ref) < PIXEL_TOL
+
+
+def test_image_device_output_matches_host_output(ctx):
+    import torch
+    w = WL.simple_cubic_workload()
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    host = basis.image(w.detectors, w.region, recompute=True)
+    dev = torch.empty((1, 16, 16), dtype=torch.float64, device="cuda")
+    basis.image(w.detectors, w.region, out=dev, recompute=True,
+                stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert np.array_equal(host, dev.cpu().numpy())
+
+
+def test_invalid_region_is_rejected(ctx):
+    w = WL.simple_cubic_workload()
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    with pytest.raises(lma.LmaError) as e:
+        basis.image(w.detectors, WL.Region(0, 0, 0, 4, (8, 8)))
+    assert e.value.status == lma.LMA_ERR_INVALID
+    with pytest.raises(lma.LmaError) as e:
+        basis.image([WL.Detector(0.1, 0.05)], w.region)
+    assert e.value.status == lma.LMA_ERR_INVALID
+
+
+@pytest.mark.slow
+def test_perovskite_512_eight_phonons_sampled_pixels(ctx):
+    """Full ABO3 workload in the launch configuration the benchmark times
+    (512^2, 50 slices, 8 configurations, 128 x 128 probes, RECOMPUTE); the
+    oracle recomputes a seeded sample of pixels one by one."""
+    w = WL.perovskite_workload()
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    img = basis.image(w.detectors, w.region, recompute=True)[0]
+    assert np.all(np.isfinite(img)) and np.all(img > 0)
+    sample = WL.sample_probes(w.region, 4, seed=7)
+    orc = _oracle(w)
+    pix = np.stack([w.region.px0 + sample[:, 0] * w.region.spacing_px[0],
+                    w.region.py0 + sample[:, 1] * w.region.spacing_px[1]], axis=1)
+    ref = orc.image(w.detectors, pix)[0]
+    got = img[sample[:, 1], sample[:, 0]]
+    assert _rel_pixel_err(got, ref) < PIXEL_TOL
+
+
+def _edited_workload(w, cx, cy, r_site, op, spc):
+    ph = []
+    for at in w.phonons:
+        x, y, s, sp, _ = O.edit_column(at.x, at.y, at.slice, at.species, w.grid.lx, w.grid.ly, cx, cy,
+                                       r_site, op, spc)
+        ph.append(WL.Atoms(x, y, s, sp))
+    return w.__class__(**{**w.__dict__, "phonons": ph})
+
+
+def test_column_edit_equals_full_recompute(ctx):
+    # 20 x 20 A ABO3 slab on 256^2 (windows smaller than the cell), one configuration
+    w = WL.perovskite_workload(cells=5, nx=256, n_slices=12, n_phonons=1, seed_base=3100)
+    region = WL.Region(0, 0, 64, 64, (4, 4))
+    cx, cy, r_site = 2.5 * WL.ABO3_A, 2.5 * WL.ABO3_A, 0.5
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    before = basis.image(w.detectors, region)
+    n_changed, n_stale = spec.edit_column(basis, cx, cy, r_site, lma.LMA_EDIT_SET_SPECIES, 2)
+    assert n_changed == 12 and 0 < n_stale < basis.info().n_translates
+    mask = basis.affected_probes(region)
+    assert 0 < mask.sum() < mask.size
+    after = basis.image(w.detectors, region)
+    # a fresh specimen built from the edited atoms, computed from scratch
+    we = _edited_workload(w, cx, cy, r_site, 1, 2)
+    spec2 = lma.Specimen(ctx, we.grid, we.potential, we.phonons)
+    basis2 = lma.Basis(ctx, spec2, we.probe, we.basis)
+    full = basis2.image(we.detectors, region, recompute=True)
+    assert np.array_equal(after, full)
+    # pixels not affected by the edit keep their bits; affected ones changed
+    same = np.equal(after, before)[0]
+    assert np.all(same[mask == 0])
+    assert not np.all(same[mask == 1])
+    # and the edited image matches the oracle on affected probes
+    idx = np.argwhere(mask == 1)[:: max(1, int(mask.sum()) // 3)][:3]
+    pix = np.stack([idx[:, 1] * 4, idx[:, 0] * 4], axis=1)
+    ref = _oracle(we).image(we.detectors, pix)[0]
+    assert _rel_pixel_err(after[0][idx[:, 0], idx[:, 1]], ref) < PIXEL_TOL
+
+
+def test_profile_counts_launches(ctx):
+    w = WL.simple_cubic_workload()
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    ctx.profile_enable(True)
+    basis.image(w.detectors, w.region, recompute=True)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    assert prof["potential"]["launches"] == 1 and prof["slice"]["launches"] == 1
+    assert prof["synth"]["launches"] == 1 and prof["finalize"]["launches"] == 1
+    assert prof["slice"]["units"] == 1024 * 10
+    assert prof["slice"]["total_ms"] > 0
