@@ -183,6 +183,25 @@ def run_reference(args, w) -> None:
     print(json.dumps(line), flush=True)
 
 
+def profile_case() -> None:
+    """The benchmark workload with one configuration, imaged twice with RECOMPUTE.
+
+    Launch order per pass: k_potential, k_slice, k_synth_detect, k_finalize.
+    Device footprint about 2.5 GB (exit waves 2.15 GB, padded transmission 164 MB).
+    """
+    import torch
+    from paper_2310_16829_gb300 import lma
+    w = WL.perovskite_workload(n_phonons=1)
+    ctx = lma.Context(0)
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    out = torch.empty((1, w.region.npy, w.region.npx), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        basis.image(w.detectors, w.region, out=out, recompute=True, stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": w.name, "mean_haadf": float(out.mean())}))
+
+
 # ----------------------------------------------------------------------------------- main arm
 def main():
     ap = argparse.ArgumentParser()
@@ -191,10 +210,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lma", choices=["lma", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="one configuration of the workload, two image passes (for ncu captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     w = WL.perovskite_workload()
+    if args.profile_case:
+        profile_case()
+        return
     if args.impl == "reference":
         run_reference(args, w)
         return

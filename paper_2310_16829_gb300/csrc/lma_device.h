@@ -65,7 +65,8 @@ cudaError_t init_device_constants();
 size_t slice_smem_bytes();
 size_t synth_smem_bytes();
 cudaError_t launch_potential(const PotArgs& a, cudaStream_t s);
-cudaError_t launch_slice(const SliceArgs& a, cudaStream_t s);
+// even_origins: every translate of the list has an even window x origin (16-byte staging)
+cudaError_t launch_slice(const SliceArgs& a, bool even_origins, cudaStream_t s);
 cudaError_t launch_synth(const SynthArgs& a, cudaStream_t s);
 cudaError_t launch_finalize(const double* acc, int64_t n, double scale, double* out,
                             cudaStream_t s);

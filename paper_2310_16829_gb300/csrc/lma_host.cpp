@@ -548,10 +548,14 @@ lma_status launch_t(lma_specimen* sp, int phi, const Rect& r, cudaStream_t st) {
   a.dy_hi = static_cast<float>(a.dy);
   a.dy_lo = static_cast<float>(a.dy - static_cast<double>(a.dy_hi));
   a.sigma = static_cast<float>(g.sigma);
-  a.rx0 = r.x0;
-  a.ry0 = r.y0;
-  a.rw = r.w;
-  a.rh = r.h;
+  // Tiles sit on the absolute 16-pixel grid whatever the rectangle, so a
+  // pixel is always computed by the same tile origin: a partial rebuild is
+  // bitwise equal to a full one (atoms are taken relative to the tile origin).
+  const int x0 = r.x0 - r.x0 % 16, y0 = r.y0 - r.y0 % 16;
+  a.rx0 = x0;
+  a.ry0 = y0;
+  a.rw = std::min(g.nx, ((r.x0 - x0 + r.w + 15) / 16) * 16);
+  a.rh = std::min(g.ny, ((r.y0 - y0 + r.h + 15) / 16) * 16);
   a.t = static_cast<float2*>(sp->d_t.p);
   const int64_t units = static_cast<int64_t>(r.w) * r.h * g.n_slices;
   CUDA_TRY(ctx, counted(ctx, K_POT, units, st, [&] { return lma_dev::launch_potential(a, st); }));
@@ -587,10 +591,23 @@ lma_status ensure_t(lma_specimen* sp, int phi, bool force, cudaStream_t st) {
   return LMA_OK;
 }
 
-lma_status propagate_list(lma_basis* b, lma_specimen* sp, const std::vector<int32_t>& list,
+// window x origin parity of translate i: (ox + a Sx - W/2) mod nx, nx and W even
+bool origin_even(const lma_basis* b, int32_t i) {
+  return ((b->ox + (i % b->nax) * b->Sx) & 1) == 0;
+}
+
+lma_status propagate_list(lma_basis* b, lma_specimen* sp, const std::vector<int32_t>& list_in,
                           cudaStream_t st) {
   lma_ctx* ctx = b->ctx;
-  if (list.empty()) return LMA_OK;
+  if (list_in.empty()) return LMA_OK;
+  // even window origins first (16-byte staging), then odd ones
+  std::vector<int32_t> list;
+  list.reserve(list_in.size());
+  for (int32_t i : list_in)
+    if (origin_even(b, i)) list.push_back(i);
+  const size_t n_even = list.size();
+  for (int32_t i : list_in)
+    if (!origin_even(b, i)) list.push_back(i);
   if (list != b->last_list) {
     // stream order keeps this copy behind the kernels that read the previous list
     CUDA_TRY(ctx, ensure(b->d_list, list.size() * sizeof(int32_t)));
@@ -605,8 +622,6 @@ lma_status propagate_list(lma_basis* b, lma_specimen* sp, const std::vector<int3
   a.ny = g.ny;
   a.n_slices = g.n_slices;
   a.uW = static_cast<const float2*>(b->d_uW.p);
-  a.list = static_cast<const int32_t*>(b->d_list.p);
-  a.n_list = static_cast<int>(list.size());
   a.lat_ox = b->ox;
   a.lat_oy = b->oy;
   a.lat_sx = b->Sx;
@@ -616,8 +631,16 @@ lma_status propagate_list(lma_basis* b, lma_specimen* sp, const std::vector<int3
   a.ex = static_cast<const float2*>(b->d_ex.p);
   a.ey = static_cast<const float2*>(b->d_ey.p);
   a.r2max = b->r2max;
-  const int64_t units = static_cast<int64_t>(list.size()) * g.n_slices;
-  CUDA_TRY(ctx, counted(ctx, K_SLICE, units, st, [&] { return lma_dev::launch_slice(a, st); }));
+  const int32_t* dl = static_cast<const int32_t*>(b->d_list.p);
+  for (int part = 0; part < 2; ++part) {
+    const size_t off = part == 0 ? 0 : n_even;
+    const size_t cnt = part == 0 ? n_even : list.size() - n_even;
+    if (cnt == 0) continue;
+    a.list = dl + off;
+    a.n_list = static_cast<int>(cnt);
+    const int64_t units = static_cast<int64_t>(cnt) * g.n_slices;
+    CUDA_TRY(ctx, counted(ctx, K_SLICE, units, st, [&] { return lma_dev::launch_slice(a, part == 0, st); }));
+  }
   for (int32_t i : list) b->valid[i] = 1;
   return LMA_OK;
 }
@@ -821,6 +844,7 @@ lma_status lma_create_specimen(lma_ctx* ctx, const lma_grid* grid, const lma_pot
   if (g.nx <= 0 || g.ny <= 0 || !(g.lx > 0) || !(g.ly > 0) || !(g.slice_dz > 0) || g.n_slices <= 0 ||
       !(g.lambda > 0) || !(g.sigma >= 0) || !(g.bandlimit_frac > 0) || g.bandlimit_frac > 1.0)
     return fail(ctx, LMA_ERR_INVALID, "grid: non-positive size, thickness, wavelength or bandlimit");
+  if (g.nx % 16 || g.ny % 16) return fail(ctx, LMA_ERR_UNSUPPORTED, "grid sizes must be multiples of 16");
   if (n_phonons <= 0) return fail(ctx, LMA_ERR_INVALID, "need at least one configuration");
   if (pot->n_species <= 0 || !pot->peak || pot->n_terms < 1 || pot->n_terms > lma_dev::kMaxTerms ||
       !pot->term_frac || !pot->term_width)

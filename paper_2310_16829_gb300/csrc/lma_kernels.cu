@@ -105,15 +105,16 @@ __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2&
 // the three passes
 // ------------------------------------------------------------------------------------------
 // pass A, thread (y, r): v[n1] = psi(y, 4 n1 + r) -> v[k1] after the x-axis 32-point stage
-// twA points at the row W_128^(r k), k = 0..31, of this thread's r
+// twA points at W_128^(r k) of this thread's r, stride 4 over k = 0..31 (the four r of
+// a warp read four consecutive entries: no bank conflict)
 __device__ __forceinline__ void passA_fwd(float2 (&v)[32], const float2* twA) {
   dft32<false>(v);
 #pragma unroll
-  for (int k = 1; k < 32; ++k) v[k] = cmul(v[k], twA[k]);
+  for (int k = 1; k < 32; ++k) v[k] = cmul(v[k], twA[4 * k]);
 }
 __device__ __forceinline__ void passA_inv(float2 (&v)[32], const float2* twA) {
 #pragma unroll
-  for (int k = 1; k < 32; ++k) v[k] = cmulc(v[k], twA[k]);
+  for (int k = 1; k < 32; ++k) v[k] = cmulc(v[k], twA[4 * k]);
   dft32<true>(v);
 }
 
@@ -151,6 +152,8 @@ __device__ __forceinline__ void passB_inv(float2 (&a)[16], const float2* twB) {
 //   X2 (B <-> C), 16384 entries: element (k1y, k2x, n2y, k1x) at ((k1y*4 + k2x)*32 + n2y)*32 + k1x
 //   X4 (B -> A, one half), 512 x 17 entries: element (y, r, k1 mod 16) at TA*17 + (k1 & 15)
 constexpr int kX1 = 512 * 33;
+constexpr int kTPitch = 132;          // staged transmission: W rows of 132 entries (= kX1 entries)
+static_assert(kW * kTPitch == kX1, "staged transmission must fit the exchange region");
 constexpr int kX4 = 512 * 17;
 __device__ __forceinline__ int x1_addr(int ta, int k1) { return ta * 33 + k1; }
 __device__ __forceinline__ int x2_addr(int k1y, int k2x, int n2y, int k1x) {
@@ -162,16 +165,20 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // ------------------------------------------------------------------------------------------
 // per-CTA shared tables
 // ------------------------------------------------------------------------------------------
-// twA[r*32 + k] = W_128^(r k); twB[n2y*4 + k1y] = W_128^(n2y k1y)
+// twA[k*4 + r] = W_128^(r k); twB[n2y*4 + k1y] = W_128^(n2y k1y)
 __device__ __forceinline__ void load_twiddles(float2* twA, float2* twB, int T) {
   if (T < 128) {
-    twA[T] = c_w128[((T >> 5) * (T & 31)) & 127];
+    twA[T] = c_w128[((T & 3) * (T >> 2)) & 127];
     twB[T] = c_w128[((T >> 2) * (T & 3)) & 127];
   }
 }
@@ -181,6 +188,26 @@ __device__ __forceinline__ void load_twiddles(float2* twA, float2* twB, int T) {
 // ------------------------------------------------------------------------------------------
 constexpr int kSliceSmemFloat2 = kX1 + kX4 + 3 * 128;
 
+// Stage a W x W window of one slice into R0 (asynchronous, completed by
+// cp_async_wait_all + __syncthreads). With an even window origin every row is
+// copied in 16-byte pieces, a warp covering 512 contiguous bytes; with an odd
+// origin in 8-byte pieces.
+template <bool EVEN>
+__device__ __forceinline__ void stage_t(float2* sdst, const float2* g, int pitch) {
+  if (EVEN) {
+    const size_t step = static_cast<size_t>(8) * pitch;
+#pragma unroll
+    for (int i = 0; i < 16; ++i, g += step) cp_async16(sdst + i * 8 * kTPitch, g);
+  } else {
+    const size_t step = static_cast<size_t>(4) * pitch;
+#pragma unroll
+    for (int i = 0; i < 32; ++i, g += step) cp_async8(sdst + i * 4 * kTPitch, g);
+  }
+  cp_async_commit();
+}
+
+// One CTA per translate; EVEN selects the window-origin parity of the translates in the list.
+template <bool EVEN>
 __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
   extern __shared__ __align__(16) float2 sm[];
   float2* R0 = sm;             // t prefetch (thread-private slots n1*512 + T) / exchanges X1, X2
@@ -198,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
   const int k1lo = T & 15, n2y = T >> 4;
   // C layout: thread (kx, k1y)
   const int kx = T & 127, k1y = T >> 7, k1x = kx & 31, k2x = kx >> 5;
-  const float2* tA = twA + ra * 32;
+  const float2* tA = twA + ra;
   const float2* tB = twB + n2y * 4;
   const float2 exr = a.ex[kx];
   uint32_t mbits = 0;
@@ -215,7 +242,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
 
   const int pitch = a.nx + kW;                                    // padded row
   const size_t slice_elems = static_cast<size_t>(pitch) * (a.ny + kW);
-  float2* const tslot = R0 + T;                                   // + n1 * 512
+  // t staging: row-major W x 132 tile in R0 (the 132-float2 row keeps the A-layout
+  // reads of 8 rows x 4 columns on distinct banks); element (y, x) at y * 132 + x
+  float2* const tA_rd = R0 + ya * kTPitch + ra;                   // + 4 * n1
   float2* const x1w = R0 + T * 33;                                // A side of X1
   float2* const x1r = R0 + (4 * n2y) * 33 + k1lo;                 // B side of X1, + (128 q + r) * 33
   float2* const x2b = R0 + n2y * 32 + k1lo;                       // B side of X2, + (q*4 + r) * 1024
@@ -231,21 +260,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
     int oy = (a.lat_oy + ib * a.lat_sy - kW / 2) % a.ny;
     if (oy < 0) oy += a.ny;
     // the halo of W pixels keeps every window inside the padded array
-    const float2* tp = a.t + static_cast<size_t>(oy + ya) * pitch + ox + ra;
+    // chunk i of thread T: row (T >> 6) + 8 i, columns 2 (T & 63) + {0, 1} (even origins)
+    //                   or row (T >> 7) + 4 i, column T & 127          (odd origins)
+    const int sy0 = EVEN ? (T >> 6) : (T >> 7);
+    const int sx0 = EVEN ? 2 * (T & 63) : (T & 127);
+    float2* const sdst = R0 + sy0 * kTPitch + sx0;
+    const float2* const gsrc = a.t + static_cast<size_t>(oy + sy0) * pitch + ox + sx0;
 
-#pragma unroll
-    for (int n1 = 0; n1 < 32; ++n1) cp_async8(tslot + n1 * kThreads, tp + 4 * n1);
-    cp_async_commit();
-
+    stage_t<EVEN>(sdst, gsrc, pitch);
     float2 v[32];
 #pragma unroll
     for (int n1 = 0; n1 < 32; ++n1) v[n1] = a.uW[ya * kW + 4 * n1 + ra];
+    cp_async_wait_all();
+    __syncthreads();
 
     for (int s = 0; s < a.n_slices; ++s) {
       // transmission (Sec. 3.2): psi <- t_s psi
-      cp_async_wait_all();
+      if (s > 0) {
+        cp_async_wait_all();
+        __syncthreads();   // publishes the staged transmission to every thread
+      }
 #pragma unroll
-      for (int n1 = 0; n1 < 32; ++n1) v[n1] = cmul(v[n1], tslot[n1 * kThreads]);
+      for (int n1 = 0; n1 < 32; ++n1) v[n1] = cmul(v[n1], tA_rd[4 * n1]);
 
       // forward 2D DFT
       passA_fwd(v, tA);
@@ -295,12 +331,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
           b1[q * 4 + r] = x2b[(q * 4 + r) * 1024 + 16];
         }
       __syncthreads();  // R0 is free: prefetch the next slice's transmission
-      if (s + 1 < a.n_slices) {
-        const float2* tn = tp + (s + 1) * slice_elems;
-#pragma unroll
-        for (int n1 = 0; n1 < 32; ++n1) cp_async8(tslot + n1 * kThreads, tn + 4 * n1);
-        cp_async_commit();
-      }
+      const bool more = s + 1 < a.n_slices;
+      if (more) stage_t<EVEN>(sdst, gsrc + (s + 1) * slice_elems, pitch);
       passB_inv(b0, tB);
       passB_inv(b1, tB);
       // B -> A in two halves through R1
@@ -346,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
   const int ya = T >> 2, ra = T & 3;
   const int k1lo = T & 15, n2y = T >> 4;
   const int kx = T & 127, k1y = T >> 7, k1x = kx & 31, k2x = kx >> 5;
-  const float2* tA = twA + ra * 32;
+  const float2* tA = twA + ra;
   const float2* tB = twB + n2y * 4;
   float2* const x1w = R0 + T * 33;
   float2* const x1r = R0 + (4 * n2y) * 33 + k1lo;
@@ -544,7 +576,10 @@ cudaError_t init_device_constants() {
   }
   cudaError_t e = cudaMemcpyToSymbol(c_w128, w, sizeof(w));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_slice, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_slice<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(slice_smem_bytes()));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_slice<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(slice_smem_bytes()));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_synth_detect, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -557,9 +592,12 @@ cudaError_t launch_potential(const PotArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_slice(const SliceArgs& a, cudaStream_t s) {
+cudaError_t launch_slice(const SliceArgs& a, bool even_origins, cudaStream_t s) {
   if (a.n_list <= 0) return cudaSuccess;
-  k_slice<<<a.n_list, kThreads, slice_smem_bytes(), s>>>(a);
+  if (even_origins)
+    k_slice<true><<<a.n_list, kThreads, slice_smem_bytes(), s>>>(a);
+  else
+    k_slice<false><<<a.n_list, kThreads, slice_smem_bytes(), s>>>(a);
   return cudaGetLastError();
 }
 
