@@ -30,6 +30,7 @@
 #include "lma_device.h"
 
 #include <cstdio>
+#include <type_traits>
 
 namespace lma_dev {
 
@@ -65,29 +66,65 @@ __device__ __forceinline__ float2 tw32(float2 d, int m) {
   return INV ? cmulc(d, w) : cmul(d, w);
 }
 
-// In-register 32-point DFT, natural order in and out (radix-2 decimation in
-// frequency, output reordered by register renaming).
+// compile-time loop: f(std::integral_constant<int, I>) for I = B..E-1
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+
+// One radix-2 decimation-in-time butterfly on t[I] (a) and t[I + H] (b) with the
+// twiddle W_32^M. A general twiddle computes X = a + w b and Y = a - w b with
+// four FMAs each (two roundings per component; Y is not formed as 2a - X,
+// which would carry X's rounding error into Y).
+template <bool INV, int I, int H, int M>
+__device__ __forceinline__ void bfly(float2 (&t)[32]) {
+  const float2 a = t[I];
+  const float2 b = t[I + H];
+  if constexpr (M == 0) {
+    t[I] = cadd(a, b);
+    t[I + H] = csub(a, b);
+  } else if constexpr (M == 8) {
+    // w b = -i b (forward) or i b (inverse)
+    const float2 wb = INV ? make_float2(-b.y, b.x) : make_float2(b.y, -b.x);
+    t[I] = cadd(a, wb);
+    t[I + H] = csub(a, wb);
+  } else {
+    const float2 w = c_w128[4 * M];
+    const float wy = INV ? -w.y : w.y;
+    float2 x;
+    x.x = fmaf(b.x, w.x, fmaf(-b.y, wy, a.x));
+    x.y = fmaf(b.y, w.x, fmaf(b.x, wy, a.y));
+    t[I] = x;
+    t[I + H] = make_float2(fmaf(-b.x, w.x, fmaf(b.y, wy, a.x)), fmaf(-b.y, w.x, fmaf(-b.x, wy, a.y)));
+  }
+}
+
+// In-register 32-point DFT, natural order in and out: radix-2 decimation in
+// time on the bit-reversed input (a register renaming), 5 stages of spans 1..16.
 template <bool INV>
 __device__ __forceinline__ void dft32(float2 (&v)[32]) {
-#pragma unroll
-  for (int st = 0; st < 5; ++st) {
-    const int h = 16 >> st;
-#pragma unroll
-    for (int blk = 0; blk < 32; blk += 2 * h) {
-#pragma unroll
-      for (int j = 0; j < h; ++j) {
-        const float2 a = v[blk + j];
-        const float2 b = v[blk + j + h];
-        v[blk + j] = cadd(a, b);
-        v[blk + j + h] = tw32<INV>(csub(a, b), j * (16 / h));
-      }
-    }
-  }
   float2 t[32];
-#pragma unroll
-  for (int k = 0; k < 32; ++k) t[k] = v[brev5(k)];
-#pragma unroll
-  for (int k = 0; k < 32; ++k) v[k] = t[k];
+  static_for<0, 32>([&](auto k) {
+    constexpr int K = decltype(k)::value;
+    t[K] = v[brev5(K)];
+  });
+  static_for<0, 5>([&](auto st) {
+    constexpr int H = 1 << decltype(st)::value;
+    static_for<0, 16 / H>([&](auto blk) {
+      static_for<0, H>([&](auto j) {
+        constexpr int I = decltype(blk)::value * 2 * H + decltype(j)::value;
+        constexpr int M = decltype(j)::value * (16 / H);
+        bfly<INV, I, H, M>(t);
+      });
+    });
+  });
+  static_for<0, 32>([&](auto k) {
+    constexpr int K = decltype(k)::value;
+    v[K] = t[K];
+  });
 }
 
 template <bool INV>
@@ -105,16 +142,27 @@ __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2&
 // the three passes
 // ------------------------------------------------------------------------------------------
 // pass A, thread (y, r): v[n1] = psi(y, 4 n1 + r) -> v[k1] after the x-axis 32-point stage
-// twA points at W_128^(r k) of this thread's r, stride 4 over k = 0..31 (the four r of
-// a warp read four consecutive entries: no bank conflict)
+// twA points at the row W_128^(r k), k = 0..31, of this thread's r; rows are 34
+// entries apart so that the four r of a warp read distinct banks, two entries
+// per 128-bit load
 __device__ __forceinline__ void passA_fwd(float2 (&v)[32], const float2* twA) {
   dft32<false>(v);
+  const float4* w4 = reinterpret_cast<const float4*>(twA);
 #pragma unroll
-  for (int k = 1; k < 32; ++k) v[k] = cmul(v[k], twA[4 * k]);
+  for (int k = 0; k < 32; k += 2) {
+    const float4 w = w4[k / 2];
+    if (k > 0) v[k] = cmul(v[k], make_float2(w.x, w.y));
+    v[k + 1] = cmul(v[k + 1], make_float2(w.z, w.w));
+  }
 }
 __device__ __forceinline__ void passA_inv(float2 (&v)[32], const float2* twA) {
+  const float4* w4 = reinterpret_cast<const float4*>(twA);
 #pragma unroll
-  for (int k = 1; k < 32; ++k) v[k] = cmulc(v[k], twA[4 * k]);
+  for (int k = 0; k < 32; k += 2) {
+    const float4 w = w4[k / 2];
+    if (k > 0) v[k] = cmulc(v[k], make_float2(w.x, w.y));
+    v[k + 1] = cmulc(v[k + 1], make_float2(w.z, w.w));
+  }
   dft32<true>(v);
 }
 
@@ -148,18 +196,20 @@ __device__ __forceinline__ void passB_inv(float2 (&a)[16], const float2* twB) {
 // shared-memory layouts of the exchanges (float2 units); row paddings keep the
 // 64-bit accesses of every half-warp on 16 distinct bank pairs and make every
 // address a per-thread base plus a compile-time offset
-//   X1 (A <-> B), 512 x 33 entries: element (y, r, k1) at TA*33 + k1, TA = 4y + r
+//   X1 (A <-> B), 512 x 34 entries: element (y, r, k1) at TA*34 + k1, TA = 4y + r
+//      (A writes two entries per 128-bit store: 8 lanes on 8 distinct 16-byte slots)
 //   X2 (B <-> C), 16384 entries: element (k1y, k2x, n2y, k1x) at ((k1y*4 + k2x)*32 + n2y)*32 + k1x
-//   X4 (B -> A, one half), 512 x 17 entries: element (y, r, k1 mod 16) at TA*17 + (k1 & 15)
-constexpr int kX1 = 512 * 33;
+//   X4 (B -> A, one half), 512 x 18 entries: element (y, r, k1 mod 16) at TA*18 + (k1 & 15)
+//      (A reads two entries per 128-bit load)
+constexpr int kX1 = 512 * 34;
 constexpr int kTPitch = 132;          // staged transmission: W rows of 132 entries (= kX1 entries)
-static_assert(kW * kTPitch == kX1, "staged transmission must fit the exchange region");
-constexpr int kX4 = 512 * 17;
-__device__ __forceinline__ int x1_addr(int ta, int k1) { return ta * 33 + k1; }
+static_assert(kW * kTPitch <= kX1, "staged transmission must fit the exchange region");
+constexpr int kX4 = 512 * 18;
+__device__ __forceinline__ int x1_addr(int ta, int k1) { return ta * 34 + k1; }
 __device__ __forceinline__ int x2_addr(int k1y, int k2x, int n2y, int k1x) {
   return ((k1y * 4 + k2x) * 32 + n2y) * 32 + k1x;
 }
-__device__ __forceinline__ int x4_addr(int ta, int k1) { return ta * 17 + (k1 & 15); }
+__device__ __forceinline__ int x4_addr(int ta, int k1) { return ta * 18 + (k1 & 15); }
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
@@ -175,10 +225,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // ------------------------------------------------------------------------------------------
 // per-CTA shared tables
 // ------------------------------------------------------------------------------------------
-// twA[k*4 + r] = W_128^(r k); twB[n2y*4 + k1y] = W_128^(n2y k1y)
+// twA[r*34 + k] = W_128^(r k) (k < 32); twB[n2y*4 + k1y] = W_128^(n2y k1y)
+constexpr int kTwA = 4 * 34;
 __device__ __forceinline__ void load_twiddles(float2* twA, float2* twB, int T) {
   if (T < 128) {
-    twA[T] = c_w128[((T & 3) * (T >> 2)) & 127];
+    twA[(T >> 5) * 34 + (T & 31)] = c_w128[((T >> 5) * (T & 31)) & 127];
     twB[T] = c_w128[((T >> 2) * (T & 3)) & 127];
   }
 }
@@ -186,7 +237,7 @@ __device__ __forceinline__ void load_twiddles(float2* twA, float2* twB, int T) {
 // ------------------------------------------------------------------------------------------
 // step a3: slice kernel
 // ------------------------------------------------------------------------------------------
-constexpr int kSliceSmemFloat2 = kX1 + kX4 + 3 * 128;
+constexpr int kSliceSmemFloat2 = kX1 + kX4 + kTwA + 128 + 128;
 
 // Stage a W x W window of one slice into R0 (asynchronous, completed by
 // cp_async_wait_all + __syncthreads). With an even window origin every row is
@@ -213,20 +264,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
   float2* R0 = sm;             // t prefetch (thread-private slots n1*512 + T) / exchanges X1, X2
   float2* R1 = sm + kX1;       // exchange X4 (two halves)
   float2* twA = R1 + kX4;
-  float2* twB = twA + 128;
-  float2* eys = twB + 128;
+  float2* twB = twA + kTwA;
+  float2* eys = twB + 128;     // eys[k1y*32 + j] = e_y(k1y + 4 j)
 
   const int T = threadIdx.x;
   load_twiddles(twA, twB, T);
-  if (T < 128) eys[T] = a.ey[T];
+  if (T < 128) eys[(T & 3) * 32 + (T >> 2)] = a.ey[T];
   // A layout: thread (y, r)
   const int ya = T >> 2, ra = T & 3;
   // B layout: groups (k1 = (T & 15) + 16 h, n2y = T >> 4), h = 0, 1
   const int k1lo = T & 15, n2y = T >> 4;
   // C layout: thread (kx, k1y)
   const int kx = T & 127, k1y = T >> 7, k1x = kx & 31, k2x = kx >> 5;
-  const float2* tA = twA + ra;
+  const float2* tA = twA + ra * 34;
   const float2* tB = twB + n2y * 4;
+  const float4* ey4 = reinterpret_cast<const float4*>(eys + k1y * 32);
   const float2 exr = a.ex[kx];
   uint32_t mbits = 0;
   {
@@ -245,12 +297,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
   // t staging: row-major W x 132 tile in R0 (the 132-float2 row keeps the A-layout
   // reads of 8 rows x 4 columns on distinct banks); element (y, x) at y * 132 + x
   float2* const tA_rd = R0 + ya * kTPitch + ra;                   // + 4 * n1
-  float2* const x1w = R0 + T * 33;                                // A side of X1
-  float2* const x1r = R0 + (4 * n2y) * 33 + k1lo;                 // B side of X1, + (128 q + r) * 33
+  float4* const x1w = reinterpret_cast<float4*>(R0 + T * 34);     // A side of X1 (pairs)
+  float2* const x1r = R0 + (4 * n2y) * 34 + k1lo;                 // B side of X1, + (128 q + r) * 34
   float2* const x2b = R0 + n2y * 32 + k1lo;                       // B side of X2, + (q*4 + r) * 1024
   float2* const x2c = R0 + (k1y * 4 + k2x) * 1024 + k1x;          // C side of X2, + j * 32
-  float2* const x4w = R1 + (4 * n2y) * 17 + k1lo;                 // B side of X4, + (128 q + r) * 17
-  float2* const x4r = R1 + T * 17;                                // A side of X4
+  float2* const x4w = R1 + (4 * n2y) * 18 + k1lo;                 // B side of X4, + (128 q + r) * 18
+  const float4* const x4r = reinterpret_cast<const float4*>(R1 + T * 18);   // A side of X4 (pairs)
 
   for (int li = blockIdx.x; li < a.n_list; li += gridDim.x) {
     const int ti = a.list[li];
@@ -287,15 +339,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
       passA_fwd(v, tA);
       __syncthreads();
 #pragma unroll
-      for (int k = 0; k < 32; ++k) x1w[k] = v[k];
+      for (int k = 0; k < 32; k += 2) x1w[k / 2] = make_float4(v[k].x, v[k].y, v[k + 1].x, v[k + 1].y);
       __syncthreads();
       float2 b0[16], b1[16];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          b0[q * 4 + r] = x1r[(128 * q + r) * 33];
-          b1[q * 4 + r] = x1r[(128 * q + r) * 33 + 16];
+          b0[q * 4 + r] = x1r[(128 * q + r) * 34];
+          b1[q * 4 + r] = x1r[(128 * q + r) * 34 + 16];
         }
       passB_fwd(b0, tB);
       passB_fwd(b1, tB);
@@ -314,9 +366,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
       dft32<false>(c);
       // propagation (Sec. 3.2): exp(-i pi lambda eps |k|^2), bandlimit, 1/W^2
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const float2 pr = cmul(exr, eys[k1y + 4 * j]);
-        c[j] = ((mbits >> j) & 1u) ? cmul(c[j], pr) : make_float2(0.f, 0.f);
+      for (int j = 0; j < 32; j += 2) {
+        const float4 e2 = ey4[j / 2];
+        const float2 p0 = cmul(exr, make_float2(e2.x, e2.y));
+        const float2 p1 = cmul(exr, make_float2(e2.z, e2.w));
+        c[j] = ((mbits >> j) & 1u) ? cmul(c[j], p0) : make_float2(0.f, 0.f);
+        c[j + 1] = ((mbits >> (j + 1)) & 1u) ? cmul(c[j + 1], p1) : make_float2(0.f, 0.f);
       }
       dft32<true>(c);
       __syncthreads();
@@ -339,18 +394,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) x4w[(128 * q + r) * 17] = b0[q * 4 + r];
+        for (int r = 0; r < 4; ++r) x4w[(128 * q + r) * 18] = b0[q * 4 + r];
       __syncthreads();
 #pragma unroll
-      for (int k = 0; k < 16; ++k) v[k] = x4r[k];
+      for (int k = 0; k < 16; k += 2) {
+        const float4 p = x4r[k / 2];
+        v[k] = make_float2(p.x, p.y);
+        v[k + 1] = make_float2(p.z, p.w);
+      }
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) x4w[(128 * q + r) * 17] = b1[q * 4 + r];
+        for (int r = 0; r < 4; ++r) x4w[(128 * q + r) * 18] = b1[q * 4 + r];
       __syncthreads();
 #pragma unroll
-      for (int k = 16; k < 32; ++k) v[k] = x4r[k - 16];
+      for (int k = 16; k < 32; k += 2) {
+        const float4 p = x4r[(k - 16) / 2];
+        v[k] = make_float2(p.x, p.y);
+        v[k + 1] = make_float2(p.z, p.w);
+      }
       passA_inv(v, tA);
     }
 
@@ -364,13 +427,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
 // ------------------------------------------------------------------------------------------
 // steps a4-a6: synthesis and detector reading
 // ------------------------------------------------------------------------------------------
-constexpr int kSynthSmemFloat2 = kX1 + 2 * 128 + (kThreads / 32) * kMaxDet;
+constexpr int kSynthSmemFloat2 = kX1 + kTwA + 128 + (kThreads / 32) * kMaxDet;
 
 __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a) {
   extern __shared__ __align__(16) float2 sm[];
   float2* R0 = sm;
   float2* twA = sm + kX1;
-  float2* twB = twA + 128;
+  float2* twB = twA + kTwA;
   float* red = reinterpret_cast<float*>(twB + 128);   // [16 warps][kMaxDet]
 
   const int T = threadIdx.x;
@@ -378,10 +441,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
   const int ya = T >> 2, ra = T & 3;
   const int k1lo = T & 15, n2y = T >> 4;
   const int kx = T & 127, k1y = T >> 7, k1x = kx & 31, k2x = kx >> 5;
-  const float2* tA = twA + ra;
+  const float2* tA = twA + ra * 34;
   const float2* tB = twB + n2y * 4;
-  float2* const x1w = R0 + T * 33;
-  float2* const x1r = R0 + (4 * n2y) * 33 + k1lo;
+  float4* const x1w = reinterpret_cast<float4*>(R0 + T * 34);
+  float2* const x1r = R0 + (4 * n2y) * 34 + k1lo;
   float2* const x2b = R0 + n2y * 32 + k1lo;
   float2* const x2c = R0 + (k1y * 4 + k2x) * 1024 + k1x;
   uint32_t dbits[kMaxDet];
@@ -422,15 +485,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
     passA_fwd(v, tA);
     __syncthreads();   // previous probe's C reads are done
 #pragma unroll
-    for (int k = 0; k < 32; ++k) x1w[k] = v[k];
+    for (int k = 0; k < 32; k += 2) x1w[k / 2] = make_float4(v[k].x, v[k].y, v[k + 1].x, v[k + 1].y);
     __syncthreads();
     float2 b0[16], b1[16];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        b0[q * 4 + r] = x1r[(128 * q + r) * 33];
-        b1[q * 4 + r] = x1r[(128 * q + r) * 33 + 16];
+        b0[q * 4 + r] = x1r[(128 * q + r) * 34];
+        b1[q * 4 + r] = x1r[(128 * q + r) * 34 + 16];
       }
     passB_fwd(b0, tB);
     passB_fwd(b1, tB);

@@ -7,8 +7,10 @@ about 1e-13 per wave after 10-50 slices) puts an absolute error of 1e-10 to
 3e-9 of the incident intensity on an annulus reading, which exceeds 1e-4
 relative when the annulus holds less than about 1e-5 of the beam (the 60-67
 mrad sliver of the simple-cubic crystal holds 1e-7 to 1e-4). For such weak
-images the per-pixel bound applies to pixels above 10% of the image maximum
-and every pixel is held to 1e-4 of the image maximum (``_assert_image``).
+images the per-pixel bound applies to readings above STRICT_READING = 2.5e-5
+of the incident intensity (the measured floor of about 1e-9 with a 2.5x
+margin) and every pixel is held to 1e-4 of the image maximum
+(``_assert_image``).
 Intermediate arrays are held to tighter, derived bounds: the transmission
 t = exp(i sigma v) to 2e-6 absolute (|t| = 1, FP32 potential sum and sincos),
 exit waves to 5e-5 of their peak after up to 50 slices of FP32 2D FFTs.
@@ -22,6 +24,7 @@ from paper_2310_16829_gb300 import lma, workloads as WL
 pytestmark = pytest.mark.gpu
 
 PIXEL_TOL = 1e-4
+STRICT_READING = 2.5e-5
 
 
 @pytest.fixture(scope="module")
@@ -48,13 +51,15 @@ def _rel_pixel_err(got, ref):
     return float(np.max(np.abs(np.asarray(got) - ref) / ref))
 
 
-def _assert_image(got, ref, strict_frac=0.1):
-    """Per detector row: relative error <= 1e-4 on pixels above strict_frac of the row
-    maximum, and absolute error <= 1e-4 of the row maximum everywhere."""
+def _assert_image(got, ref):
+    """Per detector row: relative error <= 1e-4 on readings above STRICT_READING of the
+    incident intensity, and absolute error <= 1e-4 of the row maximum everywhere."""
     got = np.asarray(got).reshape(np.asarray(ref).shape)
     for g, r in zip(np.atleast_2d(got), np.atleast_2d(ref)):
         assert np.all(r > 0)
-        top = r >= strict_frac * r.max()
+        top = r >= STRICT_READING
+        if not top.any():
+            top = r >= r.max()
         rel = np.abs(g - r) / r
         assert rel[top].max() < PIXEL_TOL, f"strict pixels: {rel[top].max():.2e}"
         assert np.abs(g - r).max() < PIXEL_TOL * r.max(), f"vs max: {np.abs(g - r).max() / r.max():.2e}"
