@@ -234,6 +234,35 @@ lma_status lma_edit_column(lma_ctx* ctx, lma_specimen* spec, lma_basis* basis, d
 lma_status lma_affected_probes(lma_ctx* ctx, lma_basis* basis, const lma_region* region,
                                uint8_t* out_mask, int64_t* n_affected);
 
+/* ---- readout without device allocation -------------------------------------------------- */
+
+/* The readout of steps a4-a5 for callers that cannot allocate device memory:
+ * an application whose device memory is already taken by its own allocator or
+ * by a framework's caching allocator, or a process that must not grow its
+ * device footprint while it runs. The paper has no counterpart; this is a
+ * service of the library.
+ *
+ * The caller passes the exit waves ([n_translates][W][W] complex64, device
+ * memory, e.g. filled with lma_exit_wave) and the output
+ * (out[n_det][npy][npx] double, device memory); the readings are those of one
+ * configuration, as lma_image gives for a specimen with one configuration. The
+ * per-call tables and the FP64 accumulator live in one file-scope device array
+ * of 8 MiB that every device loading this library holds until the process
+ * exits; no cudaMalloc, cudaFree or other allocating call is made. A region
+ * whose tables do not fit (about 6000 probes at L = 64, 12000 at L = 32) is
+ * rejected with LMA_ERR_INVALID and a message giving the limit.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the array and the accumulator is cleared at the start of
+ * each call, so calls that overlap on the GPU (several streams or host
+ * threads) race: serialize them. The call synchronizes `stream` before it
+ * returns. Errors as for lma_image; LMA_ERR_INVALID also when exit_waves or
+ * out is not device memory. */
+lma_status lma_readout_noalloc(lma_ctx* ctx, lma_basis* basis, const float* exit_waves,
+                               const lma_detector* det, int32_t n_det, const lma_region* region,
+                               double* out, void* stream);
+
 /* ---- measurement ------------------------------------------------------------------------ */
 
 /* Launch counters and CUDA-event durations per kernel. `units` counts the work

@@ -61,6 +61,12 @@ struct SynthArgs {
   double* acc;                 // [n_det][n_probes] sum over configurations
 };
 
+// Scratch of the no-allocation readout: a file-scope device array of this size
+// on each device; noalloc_scratch() returns its device address for the current device.
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;
+constexpr int kMaxDevices = 64;
+cudaError_t noalloc_scratch(void** ptr);
+
 cudaError_t init_device_constants();
 size_t slice_smem_bytes();
 size_t synth_smem_bytes();

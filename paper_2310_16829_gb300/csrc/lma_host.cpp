@@ -1202,6 +1202,99 @@ lma_status lma_edit_column(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, double 
   return LMA_OK;
 }
 
+lma_status lma_readout_noalloc(lma_ctx* ctx, lma_basis* b, const float* exit_waves, const lma_detector* det,
+                               int32_t n_det, const lma_region* region, double* out, void* stream) {
+  if (!ctx || !b || !exit_waves || !out) return fail(ctx, LMA_ERR_INVALID, "null argument");
+  if (n_det <= 0 || n_det > lma_dev::kMaxDet || !det)
+    return fail(ctx, LMA_ERR_INVALID, "need 1..%d detectors", lma_dev::kMaxDet);
+  for (int d = 0; d < n_det; ++d)
+    if (!(det[d].r1 >= 0) || !(det[d].r2 > det[d].r1))
+      return fail(ctx, LMA_ERR_INVALID, "detector %d: need 0 <= r1 < r2", d);
+  lma_status s = validate_region(ctx, b, region);
+  if (s != LMA_OK) return s;
+  if (!device_ready(ctx)) return fail(ctx, LMA_ERR_UNSUPPORTED, "no device in this context");
+  if (!is_device_pointer(exit_waves) || !is_device_pointer(out))
+    return fail(ctx, LMA_ERR_INVALID, "exit_waves and out must be device memory");
+  const int L = b->desc.L;
+  const int64_t np = static_cast<int64_t>(region->npx) * region->npy;
+  const int64_t nout = np * n_det;
+  // scratch layout: accumulator | detector bits | translate indices | coefficients | shifts
+  auto up = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
+  const size_t o_acc = 0;
+  const size_t o_det = up(o_acc + static_cast<size_t>(nout) * sizeof(double));
+  const size_t o_tidx = up(o_det + static_cast<size_t>(n_det) * lma_dev::kThreads * sizeof(uint32_t));
+  const size_t o_alpha = up(o_tidx + static_cast<size_t>(np) * L * sizeof(int32_t));
+  const size_t o_shift = up(o_alpha + static_cast<size_t>(np) * L * 2 * sizeof(float));
+  const size_t need = up(o_shift + static_cast<size_t>(np) * L * 2 * sizeof(int32_t));
+  if (need > lma_dev::kNoAllocScratchBytes)
+    return fail(ctx, LMA_ERR_INVALID,
+                "region of %lld probes with L = %d needs %zu bytes of scratch; the no-allocation readout "
+                "holds %zu bytes (about %lld probes at L = %d)",
+                static_cast<long long>(np), L, need, lma_dev::kNoAllocScratchBytes,
+                static_cast<long long>(lma_dev::kNoAllocScratchBytes / (L * 20 + 8 * n_det + 1)), L);
+  // host tables (FP64 coefficients rounded once, as in lma_image)
+  std::vector<int32_t> tidx(static_cast<size_t>(np) * L), sh(2 * static_cast<size_t>(np) * L);
+  std::vector<float> al(2 * static_cast<size_t>(np) * L);
+  const int half = (b->desc.det_window - b->desc.window) / 2;
+  for (int pb = 0; pb < region->npy; ++pb)
+    for (int pa = 0; pa < region->npx; ++pa) {
+      const int px = mod(region->px0 + pa * region->spacing_px[0], b->nx);
+      const int py = mod(region->py0 + pb * region->spacing_px[1], b->ny);
+      const CoefSet* cs = nullptr;
+      if ((s = coef_set(b, px, py, &cs)) != LMA_OK) return s;
+      const size_t base = (static_cast<size_t>(pb) * region->npx + pa) * L;
+      for (int j = 0; j < L; ++j) {
+        tidx[base + j] = static_cast<int32_t>(translate_index(b, px + cs->odx[j], py + cs->ody[j]));
+        al[2 * (base + j)] = static_cast<float>(cs->alpha[j].real());
+        al[2 * (base + j) + 1] = static_cast<float>(cs->alpha[j].imag());
+        sh[2 * (base + j)] = cs->odx[j] + half;
+        sh[2 * (base + j) + 1] = cs->ody[j] + half;
+      }
+    }
+  const lma_grid& g = b->spec->g;
+  const int D = b->desc.det_window;
+  const double dx = g.lx / g.nx, dy = g.ly / g.ny, lam = g.lambda, frac = g.bandlimit_frac;
+  std::vector<uint32_t> bits(static_cast<size_t>(n_det) * lma_dev::kThreads, 0u);
+  for (int d = 0; d < n_det; ++d)
+    for (int iy = 0; iy < D; ++iy) {
+      const int my = signed_index(iy, D);
+      const double ky = my / (D * dy);
+      for (int ix = 0; ix < D; ++ix) {
+        const int mx = signed_index(ix, D);
+        const double kx = mx / (D * dx);
+        const double ang = lam * std::sqrt(ky * ky + kx * kx);
+        const bool band = static_cast<double>(4 * (my * my + mx * mx)) <= frac * frac * D * D;
+        if (ang >= det[d].r1 && ang < det[d].r2 && band)
+          bits[static_cast<size_t>(d) * lma_dev::kThreads + ix + 128 * (iy & 3)] |= 1u << (iy >> 2);
+      }
+    }
+  void* scratch = nullptr;
+  CUDA_TRY(ctx, lma_dev::noalloc_scratch(&scratch));
+  char* base = static_cast<char*>(scratch);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CUDA_TRY(ctx, cudaMemsetAsync(base + o_acc, 0, static_cast<size_t>(nout) * sizeof(double), st));
+  CUDA_TRY(ctx, cudaMemcpyAsync(base + o_det, bits.data(), bits.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(ctx, cudaMemcpyAsync(base + o_tidx, tidx.data(), tidx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(ctx, cudaMemcpyAsync(base + o_alpha, al.data(), al.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(ctx, cudaMemcpyAsync(base + o_shift, sh.data(), sh.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  lma_dev::SynthArgs a{};
+  a.U = reinterpret_cast<const float2*>(exit_waves);
+  a.tidx = reinterpret_cast<const int32_t*>(base + o_tidx);
+  a.alpha = reinterpret_cast<const float2*>(base + o_alpha);
+  a.shift = reinterpret_cast<const int2*>(base + o_shift);
+  a.L = L;
+  a.n_probes = static_cast<int>(np);
+  a.cyclic = (b->nx == kW && b->ny == kW) ? 1 : 0;
+  a.det_bits = reinterpret_cast<const uint32_t*>(base + o_det);
+  a.n_det = n_det;
+  a.acc = reinterpret_cast<double*>(base + o_acc);
+  CUDA_TRY(ctx, lma_dev::launch_synth(a, st));
+  CUDA_TRY(ctx, lma_dev::launch_finalize(a.acc, nout, 1.0, out, st));
+  // the host tables above are pageable: keep them alive until the copies have run
+  CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  return LMA_OK;
+}
+
 lma_status lma_profile_enable(lma_ctx* ctx, int32_t on) {
   if (!ctx) return LMA_ERR_INVALID;
   for (auto& p : ctx->pend) {

@@ -30,6 +30,7 @@
 #include "lma_device.h"
 
 #include <cstdio>
+#include <mutex>
 #include <type_traits>
 
 namespace lma_dev {
@@ -622,6 +623,34 @@ __global__ void __launch_bounds__(256) k_potential(const PotArgs a) {
 __global__ void k_finalize(const double* acc, int64_t n, double scale, double* out) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i < n) out[i] = acc[i] * scale;
+}
+
+// ------------------------------------------------------------------------------------------
+// scratch of the no-allocation readout
+// ------------------------------------------------------------------------------------------
+// One file-scope array on every device that loads this library, held until the
+// process exits. lma_readout_noalloc places its per-call tables and its FP64
+// accumulator here instead of allocating. Host code must not use the symbol's
+// name as an address: noalloc_scratch() looks the device address up with
+// cudaGetSymbolAddress, once per device, with that device current.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+cudaError_t noalloc_scratch(void** ptr) {
+  static std::mutex mu;
+  static void* addr[kMaxDevices] = {};
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    addr[dev] = p;
+  }
+  *ptr = addr[dev];
+  return cudaSuccess;
 }
 
 // ------------------------------------------------------------------------------------------

@@ -42,7 +42,7 @@ EXPORTS = [
     "lma_create_basis", "lma_free_basis", "lma_basis_get_info", "lma_basis_coefficients",
     "lma_propagate_basis", "lma_exit_wave",
     "lma_image", "lma_edit_column", "lma_affected_probes",
-    "lma_profile_enable", "lma_profile_read",
+    "lma_profile_enable", "lma_profile_read", "lma_readout_noalloc",
 ]
 
 
@@ -131,6 +131,8 @@ _SIGS = {
     "lma_edit_column": (C.c_int32, [_VP, _VP, _VP, C.c_double, C.c_double, C.c_double, C.c_int32,
                                     C.c_int16, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "lma_affected_probes": (C.c_int32, [_VP, _VP, C.POINTER(Region), _VP, C.POINTER(C.c_int64)]),
+    "lma_readout_noalloc": (C.c_int32, [_VP, _VP, _VP, C.POINTER(Detector), C.c_int32, C.POINTER(Region),
+                                        _VP, _VP]),
 }
 
 _LIB: Optional[C.CDLL] = None
@@ -343,6 +345,19 @@ class Basis:
         flags = LMA_IMAGE_RECOMPUTE if recompute else 0
         self.ctx.check(self.ctx.lib.lma_image(self.ctx.h, self.spec.h, self.h, dets, len(detectors),
                                               C.byref(reg), flags, _ptr(out), _stream(stream)))
+        return out
+
+    def readout_noalloc(self, exit_waves, detectors, region, out, stream=None):
+        """Readings of one configuration from caller-held exit waves, without device allocation.
+
+        ``exit_waves`` and ``out`` are device buffers owned by the caller (e.g. torch CUDA
+        tensors); the library uses a fixed scratch array instead of allocating.
+        """
+        dets = (Detector * len(detectors))(*[Detector(d.r1, d.r2) for d in detectors])
+        reg = _region(region)
+        self.ctx.check(self.ctx.lib.lma_readout_noalloc(self.ctx.h, self.h, _ptr(exit_waves), dets,
+                                                        len(detectors), C.byref(reg), _ptr(out),
+                                                        _stream(stream)))
         return out
 
     def affected_probes(self, region) -> np.ndarray:
