@@ -40,6 +40,9 @@ W = 128
 FLOPS_PER_TRANSLATE_SLICE = 2 * 5 * W * W * 14 + 12 * W * W   # 2,490,368
 FP32_LANES_PER_SM = 128
 N_SMS = 152
+# DRAM bytes (read + write) of one k_slice launch of this workload, from the ncu capture
+# summarised in profiles/k_slice_abo3_512sq_50sl.md; set to None when the kernel changes
+K_SLICE_TRAFFIC_BYTES = 0.519823104e9 + 2.112205e9
 
 
 def _peaks():
@@ -183,6 +186,46 @@ def run_reference(args, w) -> None:
     print(json.dumps(line), flush=True)
 
 
+def edit_latency(n_edits: int, seed_base: int = 3000) -> dict:
+    """Single-column edit latency on the resident serving specimen.
+
+    20 x 20 ABO3 cells on a 1024^2 grid, 100 slices of 2 A, one configuration,
+    all 65536 exit waves resident. Each request edits one seeded column (remove
+    or change species, every slice) and images the 64 x 64 probes (4 px
+    spacing) centred on it; only exit waves whose window meets the changed
+    pixels are re-propagated (Sec. 4.2.6). Latency = host wall time of
+    lma_edit_column + lma_image with a host output, per request.
+    """
+    from paper_2310_16829_gb300 import lma
+    w = WL.serving_workload()
+    ctx = lma.Context(0)
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    t0 = time.perf_counter()
+    basis.propagate(0)
+    full = basis.image(w.detectors, w.region)
+    t_full = time.perf_counter() - t0
+    dx = w.grid.lx / w.grid.nx
+    lat, stale = [], []
+    for req in range(n_edits):
+        cx, cy, op, spc = WL.edit_request(20, req, seed_base)
+        px = int(round(cx / dx)) // 4 * 4
+        py = int(round(cy / dx)) // 4 * 4
+        region = WL.Region(px - 32 * 4, py - 32 * 4, 64, 64, (4, 4))
+        a = time.perf_counter()
+        _, n_stale = spec.edit_column(basis, cx, cy, 0.5, op, spc)
+        img = basis.image(w.detectors, region)
+        lat.append(time.perf_counter() - a)
+        stale.append(n_stale)
+        assert np.all(np.isfinite(img))
+    lat_ms = np.array(lat) * 1e3
+    return {"workload": w.name, "requests": n_edits, "region_probes": 64 * 64,
+            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+            "mean_ms": float(lat_ms.mean()), "translates_repropagated_mean": float(np.mean(stale)),
+            "translates_resident": int(basis.info().n_translates),
+            "full_image_s": t_full, "full_image_pixels": int(full.size)}
+
+
 def profile_case() -> None:
     """The benchmark workload with one configuration, imaged twice with RECOMPUTE.
 
@@ -210,6 +253,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lma", choices=["lma", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--edits", type=int, default=24, help="column-edit requests timed (0: skip)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one configuration of the workload, two image passes (for ncu captures)")
     args = ap.parse_args()
@@ -318,7 +362,8 @@ def main():
     peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     roofline = {"kernel": "k_slice", "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None,
+                "traffic": K_SLICE_TRAFFIC_BYTES,
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "peak_source": f"FP32 FMA: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz "
                                "(sm_max_mhz of MEASURED_PEAKS.json)",
                 "algorithmic": f"{FLOPS_PER_TRANSLATE_SLICE} flop per translate-slice x "
@@ -328,9 +373,17 @@ def main():
     syn = prof["synth"]
     synth_ms = syn["total_ms"] / max(1, syn["launches"])
     u_bytes = basis.info().exit_wave_bytes
+    n_translates = int(basis.info().n_translates)
     kernels = {k: {"launches_per_step": v["launches"] / args.steps,
                    "ms_per_launch": v["total_ms"] / max(1, v["launches"])} for k, v in prof.items()}
     kernels["synth"]["exit_wave_store_GBps"] = u_bytes / (synth_ms / 1e3) / 1e9 if synth_ms else None
+
+    edits = None
+    if rank == 0 and args.edits > 0:
+        basis.close()                 # free the 8-configuration workload's exit waves first
+        spec.close()
+        torch.cuda.synchronize()
+        edits = edit_latency(args.edits)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -346,7 +399,7 @@ def main():
             "data": "synthetic (seeded ABO3 slab, Gaussian frozen-phonon displacements)",
             "config": {"workload": w.name, "grid": [w.grid.nx, w.grid.ny], "slices": w.grid.n_slices,
                        "phonons": len(w.phonons), "probes": w.n_pixels,
-                       "translates": int(basis.info().n_translates), "L": w.basis.L, "W": W, "D": W,
+                       "translates": n_translates, "L": w.basis.L, "W": W, "D": W,
                        "input_wave": "gaussian sigma=lambda/(2 alpha_max)", "precision": "complex64",
                        "detector_mrad": [1e3 * dets[0].r1, 1e3 * dets[0].r2],
                        "l2": "256 MiB buffer written between timed steps; per-step working set "
@@ -357,6 +410,7 @@ def main():
             "e2e": {"value": world * w.n_pixels / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(host_out.nbytes), "matches_device_run": e2e_consistent},
             "gpu_launches": int(sum(v["launches"] for v in prof.values())),
+            "edit_latency": edits,
             "clocks": clk,
             "kernels": kernels,
             "wall_s_timed_region": wall,
