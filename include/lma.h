@@ -51,6 +51,9 @@ typedef int32_t lma_status;
 #define LMA_BASIS_PROBE 1      /* u = psi_0^init (Sec. 4.2.3, first paragraph) */
 
 #define LMA_PREC_C64 0         /* complex64 everywhere on the device */
+#define LMA_PREC_MIXED 1       /* FP32 propagation; exit waves stored as FP16 pairs with a per-wave
+                                  power-of-two scale: half the store; bright-field readings within
+                                  1e-3, weak annular (HAADF) readings are not (FP16 rounding noise) */
 
 #define LMA_EDIT_REMOVE 0      /* remove the atoms of a column */
 #define LMA_EDIT_SET_SPECIES 1 /* give the atoms of a column another species */
@@ -109,7 +112,7 @@ typedef struct {
   int32_t L;                 /* input waves per probe (I_{f,p,L}) */
   int32_t window;            /* W: propagation window X' = Y' (128) */
   int32_t det_window;        /* D: synthesis / detection window (128) */
-  int32_t precision;         /* LMA_PREC_C64 */
+  int32_t precision;         /* LMA_PREC_C64 or LMA_PREC_MIXED */
 } lma_basis_desc;
 
 /* Annular detector r1 <= lambda |k| < r2 (rad), intersected with the bandlimit (Sec. 3.1, 2D STEM). */

@@ -41,7 +41,9 @@ struct SliceArgs {
   const int32_t* list;         // translate indices to propagate
   int n_list;
   int lat_ox, lat_oy, lat_sx, lat_sy, lat_nax;   // I_f: pos(a, b) = (ox + a sx, oy + b sy)
-  float2* U;                   // [n_translates][W][W]
+  float2* U;                   // [n_translates][W][W] complex64 store, or
+  void* Uh;                    // [n_translates][W][W] FP16 pairs (mixed store) with
+  float* Uscale;               // [n_translates] power-of-two factor restoring each wave
   const float2* ex;            // [W] exp(-i pi lambda eps kx^2) / W^2
   const float2* ey;            // [W] exp(-i pi lambda eps ky^2)
   int r2max;                   // bandlimit: m'^2 + n'^2 <= r2max
@@ -49,7 +51,9 @@ struct SliceArgs {
 
 // Steps a4-a6: synthesis, detector reading, FP64 accumulation over configurations.
 struct SynthArgs {
-  const float2* U;             // [n_translates][W][W]
+  const float2* U;             // [n_translates][W][W] complex64 store, or
+  const void* Uh;              // FP16 pairs (mixed store) with
+  const float* Uscale;         // per-wave factors
   const int32_t* tidx;         // [n_probes][L]
   const float2* alpha;         // [n_probes][L]
   const int2* shift;           // [n_probes][L] placement of U in the probe window
@@ -71,9 +75,12 @@ cudaError_t init_device_constants();
 size_t slice_smem_bytes();
 size_t synth_smem_bytes();
 cudaError_t launch_potential(const PotArgs& a, cudaStream_t s);
-// even_origins: every translate of the list has an even window x origin (16-byte staging)
-cudaError_t launch_slice(const SliceArgs& a, bool even_origins, cudaStream_t s);
-cudaError_t launch_synth(const SynthArgs& a, cudaStream_t s);
+// even_origins: every translate of the list has an even window x origin (16-byte staging);
+// half: write the FP16 store (Uh, Uscale) instead of the complex64 one
+cudaError_t launch_slice(const SliceArgs& a, bool even_origins, bool half, cudaStream_t s);
+cudaError_t launch_synth(const SynthArgs& a, bool half, cudaStream_t s);
+// complex64 copy of one wave of the FP16 store
+cudaError_t launch_expand_half(const void* src, float scale, float2* dst, cudaStream_t s);
 cudaError_t launch_finalize(const double* acc, int64_t n, double scale, double* out,
                             cudaStream_t s);
 

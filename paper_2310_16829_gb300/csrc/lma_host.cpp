@@ -9,6 +9,8 @@
 #include "../../include/lma.h"
 #include "lma_device.h"
 
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -270,7 +272,7 @@ struct lma_basis {
   int r2max = 0;
   std::map<std::pair<int, int>, CoefSet> sets;
   // device
-  DevBuf d_uW, d_ex, d_ey, d_U, d_list, d_acc, d_det;
+  DevBuf d_uW, d_ex, d_ey, d_U, d_Uscale, d_list, d_acc, d_det;
   bool dev_tables = false;
   int U_phonon = -1;
   int64_t U_epoch = -1;
@@ -486,8 +488,10 @@ lma_status ensure_basis_device(lma_basis* b, cudaStream_t st) {
   CUDA_TRY(ctx, cudaMemcpyAsync(b->d_ex.p, b->ex.data(), b->ex.size() * sizeof(float), cudaMemcpyHostToDevice, st));
   CUDA_TRY(ctx, cudaMemcpyAsync(b->d_ey.p, b->ey.data(), b->ey.size() * sizeof(float), cudaMemcpyHostToDevice, st));
   CUDA_TRY(ctx, cudaStreamSynchronize(st));
-  const size_t ubytes = static_cast<size_t>(b->nT) * kW * kW * sizeof(float2);
+  const bool half = b->desc.precision == LMA_PREC_MIXED;
+  const size_t ubytes = static_cast<size_t>(b->nT) * kW * kW * (half ? 4 : sizeof(float2));
   CUDA_TRY(ctx, ensure(b->d_U, ubytes));
+  if (half) CUDA_TRY(ctx, ensure(b->d_Uscale, static_cast<size_t>(b->nT) * sizeof(float)));
   b->last_list.clear();
   b->valid.assign(static_cast<size_t>(b->nT), 0);
   b->U_phonon = -1;
@@ -627,7 +631,10 @@ lma_status propagate_list(lma_basis* b, lma_specimen* sp, const std::vector<int3
   a.lat_sx = b->Sx;
   a.lat_sy = b->Sy;
   a.lat_nax = b->nax;
-  a.U = static_cast<float2*>(b->d_U.p);
+  const bool half = b->desc.precision == LMA_PREC_MIXED;
+  a.U = half ? nullptr : static_cast<float2*>(b->d_U.p);
+  a.Uh = half ? b->d_U.p : nullptr;
+  a.Uscale = half ? static_cast<float*>(b->d_Uscale.p) : nullptr;
   a.ex = static_cast<const float2*>(b->d_ex.p);
   a.ey = static_cast<const float2*>(b->d_ey.p);
   a.r2max = b->r2max;
@@ -639,7 +646,7 @@ lma_status propagate_list(lma_basis* b, lma_specimen* sp, const std::vector<int3
     a.list = dl + off;
     a.n_list = static_cast<int>(cnt);
     const int64_t units = static_cast<int64_t>(cnt) * g.n_slices;
-    CUDA_TRY(ctx, counted(ctx, K_SLICE, units, st, [&] { return lma_dev::launch_slice(a, part == 0, st); }));
+    CUDA_TRY(ctx, counted(ctx, K_SLICE, units, st, [&] { return lma_dev::launch_slice(a, part == 0, half, st); }));
   }
   for (int32_t i : list) b->valid[i] = 1;
   return LMA_OK;
@@ -930,7 +937,8 @@ lma_status lma_create_basis(lma_ctx* ctx, const lma_specimen* spec, const lma_pr
   if (!is_pow2(g.nx) || !is_pow2(g.ny)) return fail(ctx, LMA_ERR_UNSUPPORTED, "grid sizes must be powers of two");
   if (d.kind != LMA_BASIS_GAUSS && d.kind != LMA_BASIS_PROBE)
     return fail(ctx, LMA_ERR_INVALID, "unknown input wave kind");
-  if (d.precision != LMA_PREC_C64) return fail(ctx, LMA_ERR_UNSUPPORTED, "only complex64 precision");
+  if (d.precision != LMA_PREC_C64 && d.precision != LMA_PREC_MIXED)
+    return fail(ctx, LMA_ERR_INVALID, "precision must be LMA_PREC_C64 or LMA_PREC_MIXED");
   if (!(probe->alpha_max > 0)) return fail(ctx, LMA_ERR_INVALID, "alpha_max must be positive");
   const int sx = d.in_spacing_px[0], sy = d.in_spacing_px[1];
   if (sx <= 0 || sy <= 0 || g.nx % sx || g.ny % sy)
@@ -986,6 +994,7 @@ lma_status lma_free_basis(lma_basis* b) {
   b->d_ex.release();
   b->d_ey.release();
   b->d_U.release();
+  b->d_Uscale.release();
   b->d_list.release();
   b->d_acc.release();
   b->d_det.release();
@@ -1006,7 +1015,8 @@ lma_status lma_basis_get_info(const lma_basis* b, lma_basis_info* out) {
   out->window = b->desc.window;
   out->det_window = b->desc.det_window;
   out->gauss_sigma = b->gauss_sigma;
-  out->exit_wave_bytes = b->nT * static_cast<int64_t>(kW) * kW * static_cast<int64_t>(sizeof(float2));
+  out->exit_wave_bytes = b->nT * static_cast<int64_t>(kW) * kW *
+                         (b->desc.precision == LMA_PREC_MIXED ? 4 : static_cast<int64_t>(sizeof(float2)));
   return LMA_OK;
 }
 
@@ -1054,8 +1064,29 @@ lma_status lma_exit_wave(lma_ctx* ctx, lma_basis* b, int64_t translate, float* o
   if (!device_ready(ctx)) return fail(ctx, LMA_ERR_UNSUPPORTED, "no device in this context");
   if (!b->dev_tables || !b->valid[translate]) return fail(ctx, LMA_ERR_INVALID, "exit wave not current");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t bytes = static_cast<size_t>(kW) * kW * sizeof(float2);
   const bool dev = is_device_pointer(out);
+  if (b->desc.precision == LMA_PREC_MIXED) {
+    const size_t hbytes = static_cast<size_t>(kW) * kW * sizeof(__half2);
+    const char* src = static_cast<const char*>(b->d_U.p) + translate * hbytes;
+    float scale = 1.f;
+    CUDA_TRY(ctx, cudaMemcpyAsync(&scale, static_cast<const float*>(b->d_Uscale.p) + translate, sizeof(float),
+                                  cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (dev) {
+      CUDA_TRY(ctx, lma_dev::launch_expand_half(src, scale, reinterpret_cast<float2*>(out), st));
+      return LMA_OK;
+    }
+    std::vector<__half2> h(static_cast<size_t>(kW) * kW);
+    CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), src, hbytes, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    for (size_t k = 0; k < h.size(); ++k) {
+      const float2 u = __half22float2(h[k]);
+      out[2 * k] = u.x * scale;
+      out[2 * k + 1] = u.y * scale;
+    }
+    return LMA_OK;
+  }
+  const size_t bytes = static_cast<size_t>(kW) * kW * sizeof(float2);
   CUDA_TRY(ctx, cudaMemcpyAsync(out, static_cast<const char*>(b->d_U.p) + translate * bytes, bytes,
                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   if (!dev) CUDA_TRY(ctx, cudaStreamSynchronize(st));
@@ -1087,7 +1118,10 @@ lma_status lma_image(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, const lma_det
   for (int phi = 0; phi < nph; ++phi) {
     if ((s = ensure_U(b, sp, phi, needed, recompute, st)) != LMA_OK) return s;
     lma_dev::SynthArgs a{};
-    a.U = static_cast<const float2*>(b->d_U.p);
+    const bool half = b->desc.precision == LMA_PREC_MIXED;
+    a.U = half ? nullptr : static_cast<const float2*>(b->d_U.p);
+    a.Uh = half ? b->d_U.p : nullptr;
+    a.Uscale = half ? static_cast<const float*>(b->d_Uscale.p) : nullptr;
     a.tidx = static_cast<const int32_t*>(b->reg.tidx.p);
     a.alpha = static_cast<const float2*>(b->reg.alpha.p);
     a.shift = static_cast<const int2*>(b->reg.shift.p);
@@ -1097,7 +1131,7 @@ lma_status lma_image(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, const lma_det
     a.det_bits = static_cast<const uint32_t*>(b->d_det.p);
     a.n_det = n_det;
     a.acc = static_cast<double*>(b->d_acc.p);
-    CUDA_TRY(ctx, counted(ctx, K_SYNTH, np, st, [&] { return lma_dev::launch_synth(a, st); }));
+    CUDA_TRY(ctx, counted(ctx, K_SYNTH, np, st, [&] { return lma_dev::launch_synth(a, half, st); }));
   }
   const double scale = 1.0 / nph;
   const double* acc = static_cast<const double*>(b->d_acc.p);
@@ -1288,7 +1322,7 @@ lma_status lma_readout_noalloc(lma_ctx* ctx, lma_basis* b, const float* exit_wav
   a.det_bits = reinterpret_cast<const uint32_t*>(base + o_det);
   a.n_det = n_det;
   a.acc = reinterpret_cast<double*>(base + o_acc);
-  CUDA_TRY(ctx, lma_dev::launch_synth(a, st));
+  CUDA_TRY(ctx, lma_dev::launch_synth(a, false, st));
   CUDA_TRY(ctx, lma_dev::launch_finalize(a.acc, nout, 1.0, out, st));
   // the host tables above are pageable: keep them alive until the copies have run
   CUDA_TRY(ctx, cudaStreamSynchronize(st));

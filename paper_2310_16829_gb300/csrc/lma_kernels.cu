@@ -29,6 +29,8 @@
 // rectangle of the array.
 #include "lma_device.h"
 
+#include <cuda_fp16.h>
+
 #include <cstdio>
 #include <mutex>
 #include <type_traits>
@@ -258,8 +260,9 @@ __device__ __forceinline__ void stage_t(float2* sdst, const float2* g, int pitch
   cp_async_commit();
 }
 
-// One CTA per translate; EVEN selects the window-origin parity of the translates in the list.
-template <bool EVEN>
+// One CTA per translate; EVEN selects the window-origin parity of the translates in the
+// list; HALF writes the exit wave as FP16 pairs scaled by a per-wave power of two.
+template <bool EVEN, bool HALF>
 __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
   extern __shared__ __align__(16) float2 sm[];
   float2* R0 = sm;             // t prefetch (thread-private slots n1*512 + T) / exchanges X1, X2
@@ -375,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
         c[j + 1] = ((mbits >> (j + 1)) & 1u) ? cmul(c[j + 1], p1) : make_float2(0.f, 0.f);
       }
       dft32<true>(c);
-      __syncthreads();
+      // each C thread writes back exactly the entries it read: no barrier needed here
 #pragma unroll
       for (int j = 0; j < 32; ++j) x2c[j * 32] = c[j];
       __syncthreads();
@@ -418,9 +421,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
       passA_inv(v, tA);
     }
 
-    float2* ud = a.U + static_cast<size_t>(ti) * (kW * kW) + ya * kW + ra;
+    if constexpr (HALF) {
+      // power-of-two scale bringing the largest component into [0.5, 1): the scaling
+      // is exact, the FP16 rounding (2^-11 of that component) is the only error
+      __shared__ float wmax[kThreads / 32 + 1];
+      float m = 0.f;
 #pragma unroll
-    for (int n1 = 0; n1 < 32; ++n1) ud[4 * n1] = v[n1];
+      for (int n1 = 0; n1 < 32; ++n1) m = fmaxf(m, fmaxf(fabsf(v[n1].x), fabsf(v[n1].y)));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if ((T & 31) == 0) wmax[T >> 5] = m;
+      __syncthreads();
+      if (T < 32) {
+        float x = T < kThreads / 32 ? wmax[T] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+        if (T == 0) wmax[kThreads / 32] = x;
+      }
+      __syncthreads();
+      const float mx = wmax[kThreads / 32];
+      int e = 0;
+      if (mx > 0.f) frexpf(mx, &e);
+      const float sc = ldexpf(1.f, -e);
+      __half2* uh = static_cast<__half2*>(a.Uh) + static_cast<size_t>(ti) * (kW * kW) + ya * kW + ra;
+#pragma unroll
+      for (int n1 = 0; n1 < 32; ++n1) uh[4 * n1] = __floats2half2_rn(v[n1].x * sc, v[n1].y * sc);
+      if (T == 0) a.Uscale[ti] = ldexpf(1.f, e);
+    } else {
+      float2* ud = a.U + static_cast<size_t>(ti) * (kW * kW) + ya * kW + ra;
+#pragma unroll
+      for (int n1 = 0; n1 < 32; ++n1) ud[4 * n1] = v[n1];
+    }
     __syncthreads();  // R1 reads of this translate finish before the next one writes
   }
 }
@@ -430,6 +461,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
 // ------------------------------------------------------------------------------------------
 constexpr int kSynthSmemFloat2 = kX1 + kTwA + 128 + (kThreads / 32) * kMaxDet;
 
+// HALF reads the FP16 store and folds each wave's factor into its coefficient.
+template <bool HALF>
 __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a) {
   extern __shared__ __align__(16) float2 sm[];
   float2* R0 = sm;
@@ -461,7 +494,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
     const float2* ap = a.alpha + static_cast<size_t>(p) * a.L;
     const int2* sp = a.shift + static_cast<size_t>(p) * a.L;
     for (int j = 0; j < a.L; ++j) {
-      const float2 al = ap[j];
+      float2 al = ap[j];
       const int2 sh = sp[j];
       int yy = ya - sh.y;
       if (a.cyclic) {
@@ -469,16 +502,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
       } else if (yy < 0 || yy >= kW) {
         continue;
       }
-      const float2* row = a.U + static_cast<size_t>(tp[j]) * (kW * kW) + yy * kW;
+      const size_t off = static_cast<size_t>(tp[j]) * (kW * kW) + yy * kW;
       const int x0 = ra - sh.x;
+      if constexpr (HALF) {
+        const float f = a.Uscale[tp[j]];
+        al.x *= f;
+        al.y *= f;
+        const __half2* row = static_cast<const __half2*>(a.Uh) + off;
 #pragma unroll
-      for (int n1 = 0; n1 < 32; ++n1) {
-        int xx = x0 + 4 * n1;
-        if (a.cyclic) {
-          xx &= (kW - 1);
-          v[n1] = cfma(v[n1], al, row[xx]);
-        } else if (xx >= 0 && xx < kW) {
-          v[n1] = cfma(v[n1], al, row[xx]);
+        for (int n1 = 0; n1 < 32; ++n1) {
+          int xx = x0 + 4 * n1;
+          if (a.cyclic) {
+            xx &= (kW - 1);
+            v[n1] = cfma(v[n1], al, __half22float2(row[xx]));
+          } else if (xx >= 0 && xx < kW) {
+            v[n1] = cfma(v[n1], al, __half22float2(row[xx]));
+          }
+        }
+      } else {
+        const float2* row = a.U + off;
+#pragma unroll
+        for (int n1 = 0; n1 < 32; ++n1) {
+          int xx = x0 + 4 * n1;
+          if (a.cyclic) {
+            xx &= (kW - 1);
+            v[n1] = cfma(v[n1], al, row[xx]);
+          } else if (xx >= 0 && xx < kW) {
+            v[n1] = cfma(v[n1], al, row[xx]);
+          }
         }
       }
     }
@@ -620,6 +671,14 @@ __global__ void __launch_bounds__(256) k_potential(const PotArgs a) {
   }
 }
 
+__global__ void k_expand_half(const __half2* src, float scale, float2* dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < kW * kW) {
+    const float2 u = __half22float2(src[i]);
+    dst[i] = make_float2(u.x * scale, u.y * scale);
+  }
+}
+
 __global__ void k_finalize(const double* acc, int64_t n, double scale, double* out) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i < n) out[i] = acc[i] * scale;
@@ -668,14 +727,13 @@ cudaError_t init_device_constants() {
   }
   cudaError_t e = cudaMemcpyToSymbol(c_w128, w, sizeof(w));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_slice<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(slice_smem_bytes()));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_slice<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(slice_smem_bytes()));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_synth_detect, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(synth_smem_bytes()));
+  const int ss = static_cast<int>(slice_smem_bytes()), sy = static_cast<int>(synth_smem_bytes());
+  if ((e = cudaFuncSetAttribute(k_slice<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_slice<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_slice<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_slice<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_synth_detect<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_synth_detect<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy);
 }
 
 cudaError_t launch_potential(const PotArgs& a, cudaStream_t s) {
@@ -684,18 +742,27 @@ cudaError_t launch_potential(const PotArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_slice(const SliceArgs& a, bool even_origins, cudaStream_t s) {
+cudaError_t launch_slice(const SliceArgs& a, bool even_origins, bool half, cudaStream_t s) {
   if (a.n_list <= 0) return cudaSuccess;
-  if (even_origins)
-    k_slice<true><<<a.n_list, kThreads, slice_smem_bytes(), s>>>(a);
-  else
-    k_slice<false><<<a.n_list, kThreads, slice_smem_bytes(), s>>>(a);
+  const size_t sm = slice_smem_bytes();
+  if (even_origins && !half) k_slice<true, false><<<a.n_list, kThreads, sm, s>>>(a);
+  if (!even_origins && !half) k_slice<false, false><<<a.n_list, kThreads, sm, s>>>(a);
+  if (even_origins && half) k_slice<true, true><<<a.n_list, kThreads, sm, s>>>(a);
+  if (!even_origins && half) k_slice<false, true><<<a.n_list, kThreads, sm, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_synth(const SynthArgs& a, cudaStream_t s) {
+cudaError_t launch_synth(const SynthArgs& a, bool half, cudaStream_t s) {
   if (a.n_probes <= 0) return cudaSuccess;
-  k_synth_detect<<<a.n_probes, kThreads, synth_smem_bytes(), s>>>(a);
+  if (half)
+    k_synth_detect<true><<<a.n_probes, kThreads, synth_smem_bytes(), s>>>(a);
+  else
+    k_synth_detect<false><<<a.n_probes, kThreads, synth_smem_bytes(), s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand_half(const void* src, float scale, float2* dst, cudaStream_t s) {
+  k_expand_half<<<(kW * kW + 255) / 256, 256, 0, s>>>(static_cast<const __half2*>(src), scale, dst);
   return cudaGetLastError();
 }
 

@@ -31,6 +31,7 @@ STATUS_NAMES = {0: "LMA_OK", 1: "LMA_ERR_INVALID", 2: "LMA_ERR_OOM", 3: "LMA_ERR
 LMA_BASIS_GAUSS = 0
 LMA_BASIS_PROBE = 1
 LMA_PREC_C64 = 0
+LMA_PREC_MIXED = 1
 LMA_EDIT_REMOVE = 0
 LMA_EDIT_SET_SPECIES = 1
 LMA_IMAGE_RECOMPUTE = 1

@@ -31,9 +31,11 @@ SIGMA_300KV = 0.0006526161421721631
 LAMBDA_CFG0 = 0.02508
 SIGMA_CFG0 = 7.29e-4
 
-# Basis kinds (mirrors LMA_BASIS_* in include/lma.h).
+# Basis kinds and store precisions (mirror LMA_BASIS_* / LMA_PREC_* in include/lma.h).
 BASIS_GAUSS = 0
 BASIS_PROBE = 1
+PREC_C64 = 0
+PREC_MIXED = 1
 
 
 @dataclass
@@ -95,6 +97,7 @@ class BasisDesc:
     L: int = 32
     window: int = 128
     det_window: int = 128
+    precision: int = PREC_C64
 
 
 @dataclass

@@ -24,6 +24,12 @@ from paper_2310_16829_gb300 import lma, workloads as WL
 pytestmark = pytest.mark.gpu
 
 PIXEL_TOL = 1e-4
+# FP16 exit-wave store: every stored value carries up to 2^-11 relative rounding, a white
+# noise of about 1.4e-4 of the wave; bright-field readings stay within 1e-3, HAADF readings
+# (1e-7..1e-4 of the beam) do not: measured 6e-3 (ABO3) and 5e-2 (simple cubic), held here
+# only to a regression bound
+MIXED_TOL = 1e-3
+MIXED_HAADF_REGRESSION = 1e-2
 STRICT_READING = 2.5e-5
 
 
@@ -51,9 +57,9 @@ def _rel_pixel_err(got, ref):
     return float(np.max(np.abs(np.asarray(got) - ref) / ref))
 
 
-def _assert_image(got, ref):
-    """Per detector row: relative error <= 1e-4 on readings above STRICT_READING of the
-    incident intensity, and absolute error <= 1e-4 of the row maximum everywhere."""
+def _assert_image(got, ref, tol=PIXEL_TOL):
+    """Per detector row: relative error <= tol on readings above STRICT_READING of the
+    incident intensity, and absolute error <= tol of the row maximum everywhere."""
     got = np.asarray(got).reshape(np.asarray(ref).shape)
     for g, r in zip(np.atleast_2d(got), np.atleast_2d(ref)):
         assert np.all(r > 0)
@@ -61,8 +67,8 @@ def _assert_image(got, ref):
         if not top.any():
             top = r >= r.max()
         rel = np.abs(g - r) / r
-        assert rel[top].max() < PIXEL_TOL, f"strict pixels: {rel[top].max():.2e}"
-        assert np.abs(g - r).max() < PIXEL_TOL * r.max(), f"vs max: {np.abs(g - r).max() / r.max():.2e}"
+        assert rel[top].max() < tol, f"strict pixels: {rel[top].max():.2e}"
+        assert np.abs(g - r).max() < tol * r.max(), f"vs max: {np.abs(g - r).max() / r.max():.2e}"
 
 
 def test_transmission_matches_oracle_simple_cubic(ctx):
@@ -170,6 +176,32 @@ def test_invalid_region_is_rejected(ctx):
     assert e.value.status == lma.LMA_ERR_INVALID
 
 
+def test_mixed_store_simple_cubic(ctx):
+    w = WL.simple_cubic_workload()
+    w.basis.precision = WL.PREC_MIXED
+    dets = [WL.Detector(0.0, 0.02), WL.Detector(0.06, 0.2)]
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    assert basis.info().exit_wave_bytes == 1024 * 128 * 128 * 4
+    img = basis.image(dets, w.region)
+    ref = _oracle(w).image(dets, _probes(w.region, 128, 128))
+    assert _rel_pixel_err(img.reshape(2, -1)[:1], ref[:1]) < MIXED_TOL
+    # HAADF: error relative to the image maximum (the readings are 1e-7..1e-4 of the beam)
+    h, r = img.reshape(2, -1)[1], ref[1]
+    assert np.max(np.abs(h - r)) < MIXED_HAADF_REGRESSION * np.max(r)
+    # the stored waves restore to the complex64 ones within FP16 rounding: 2^-11 of each
+    # component, plus the subnormal spacing 2^-24 of the per-wave scale
+    basis.propagate(0)
+    w64 = WL.simple_cubic_workload()
+    b64 = lma.Basis(ctx, spec, w64.probe, w64.basis)
+    b64.propagate(0)
+    for i in (0, 517):
+        got, ref_u = basis.exit_wave(i), b64.exit_wave(i)
+        m = np.max(np.abs(np.stack([ref_u.real, ref_u.imag])))
+        for a, b in ((got.real, ref_u.real), (got.imag, ref_u.imag)):
+            assert np.all(np.abs(a - b) <= 2.0 ** -11 * np.abs(b) + 2.0 ** -23 * m)
+
+
 @pytest.mark.slow
 def test_perovskite_512_eight_phonons_sampled_pixels(ctx):
     """Full ABO3 workload in the launch configuration the benchmark times
@@ -187,6 +219,11 @@ def test_perovskite_512_eight_phonons_sampled_pixels(ctx):
     ref = orc.image(w.detectors, pix)[0]
     got = img[sample[:, 1], sample[:, 0]]
     assert _rel_pixel_err(got, ref) < PIXEL_TOL
+    # the mixed store (FP16 exit waves) on the same workload, same launch configuration
+    w.basis.precision = WL.PREC_MIXED
+    bm = lma.Basis(ctx, spec, w.probe, w.basis)
+    img_m = bm.image(w.detectors, w.region, recompute=True)[0]
+    assert _rel_pixel_err(img_m[sample[:, 1], sample[:, 0]], ref) < MIXED_HAADF_REGRESSION
 
 
 def _edited_workload(w, cx, cy, r_site, op, spc):
