@@ -227,6 +227,76 @@ def edit_latency(n_edits: int, seed_base: int = 3000) -> dict:
             "full_image_s": t_full, "full_image_pixels": int(full.size)}
 
 
+def serving_measure(n_requests: int, loads=(0.5, 0.8), seed: int = 4000) -> dict:
+    """Continuous batching on the serving mix (paper_2310_16829_gb300/serving.py).
+
+    Lanes: edits on the resident 1024^2 / 100-slice specimen (64 x 64-probe region per
+    edit), and full 256 x 256-probe images of fresh seeded 256^2 (20 slices), 512^2
+    (50 slices) and 1024^2 (100 slices) ABO3 specimens, up to two instances each.
+    HBM budget 75 % of the free memory. Mix 90 % edits / 10 % full images. Arrivals
+    Poisson at `loads` x the capacity estimated from measured service times.
+    """
+    import torch
+    from paper_2310_16829_gb300 import serving as S
+    sizes = {"full_256": (5, 256, 20), "full_512": (10, 512, 50), "full_1024": (20, 1024, 100)}
+
+    def builder(cells, nx, ns):
+        return lambda sd: WL.perovskite_workload(cells=cells, nx=nx, n_slices=ns, n_phonons=1,
+                                                 seed_base=sd, probes=256)
+
+    lanes = [S.edit_lane(WL.serving_workload())]
+    lanes += [S.image_lane(k, builder(*v), max_instances=2) for k, v in sizes.items()]
+    free, _ = torch.cuda.mem_get_info()
+    srv = S.Server(lanes, budget_bytes=int(0.75 * free))
+    rng = np.random.default_rng(seed)
+    edit_k = [0]
+
+    def make_requests(n):
+        reqs = []
+        for _ in range(n):
+            if rng.random() < 0.9:
+                cx, cy, op, spc = WL.edit_request(20, 1000 + edit_k[0], seed)
+                edit_k[0] += 1
+                reqs.append(S.EditRequest(cx, cy, op, spc, region_probes=64))
+            else:
+                lane = list(sizes)[int(rng.integers(0, 3))]
+                reqs.append(S.ImageRequest(lane, seed=int(rng.integers(1 << 30))))
+        return reqs
+
+    # calibration: two requests per type (the first brings the instance up); service time
+    # of the second
+    svc = {}
+    for lane in ["edit"] + list(sizes):
+        for rep in range(2):
+            if lane == "edit":
+                cx, cy, op, spc = WL.edit_request(20, 900 + rep, seed)
+                req = S.EditRequest(cx, cy, op, spc, region_probes=64)
+            else:
+                req = S.ImageRequest(lane, seed=7 + rep)
+            r = srv.submit(req).wait(600)
+            if r.error is not None:
+                raise r.error
+        svc[lane] = r.t_done - r.t_start
+    mean_svc = 0.9 * svc["edit"] + 0.1 * sum(svc[k] for k in sizes) / 3
+    capacity = 1.0 / mean_svc
+    out = {"service_ms": {k: 1e3 * v for k, v in svc.items()}, "capacity_req_per_s": capacity,
+           "budget_GB": srv.budget / 1e9, "loads": {}}
+    for load in loads:
+        reqs = make_requests(n_requests)
+        arr = S.poisson_arrivals(n_requests, load * capacity, seed + int(100 * load))
+        t0 = time.perf_counter()
+        res = S.run_stream(srv, reqs, arr)
+        span = time.perf_counter() - t0
+        pix = sum(int(r.image.shape[-1] * r.image.shape[-2]) for r in res if r.image is not None)
+        summ = S.latency_summary(res)
+        summ["pixels_per_s"] = pix / span
+        summ["offered_req_per_s"] = load * capacity
+        out["loads"][str(load)] = summ
+    out["instances"] = {k: len(l.instances) for k, l in srv.lanes.items()}
+    srv.close()
+    return out
+
+
 def profile_case() -> None:
     """The benchmark workload with one configuration, imaged twice with RECOMPUTE.
 
@@ -255,6 +325,7 @@ def main():
     ap.add_argument("--impl", default="lma", choices=["lma", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--edits", type=int, default=24, help="column-edit requests timed (0: skip)")
+    ap.add_argument("--serving", type=int, default=60, help="requests per offered load (0: skip)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one configuration of the workload, two image passes (for ncu captures)")
     args = ap.parse_args()
@@ -418,6 +489,10 @@ def main():
         spec.close()
         torch.cuda.synchronize()
         edits = edit_latency(args.edits)
+    serving = None
+    if rank == 0 and args.serving > 0:
+        torch.cuda.synchronize()
+        serving = serving_measure(args.serving)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -446,6 +521,7 @@ def main():
             "gpu_launches": int(sum(v["launches"] for v in prof.values())),
             "mixed": mixed,
             "edit_latency": edits,
+            "serving": serving,
             "clocks": clk,
             "kernels": kernels,
             "wall_s_timed_region": wall,
