@@ -297,6 +297,98 @@ def serving_measure(n_requests: int, loads=(0.5, 0.8), seed: int = 4000) -> dict
     return out
 
 
+def batching_measure(n_phonons: int, steps: int) -> dict:
+    """Batched form against the plain complex64 LMA on three specimens of uneven size.
+
+    Specimens: ABO3 5x5 cells on 256^2 (20 slices), 10x10 on 512^2 (50 slices), 20x20
+    on 1024^2 (100 slices), 64^2 / 128^2 / 256^2 probes every 4 px, `n_phonons` seeded
+    frozen-phonon configurations each.
+      plain:   one lma_image per specimen, one configuration per slice and synthesis
+               launch (phonon batch 1), one CTA per translate.
+      batched: one lma_image_many call: configurations in phonon batches (as many as fit
+               in memory), the slice work of all specimens of a round in one launch (mode
+               chosen by the autotuner), the whole call replayed as one CUDA graph.
+    Both run on one stream with device outputs and are timed with CUDA events; the
+    outputs of the two forms are compared bitwise.
+    """
+    import torch
+    from paper_2310_16829_gb300 import lma
+    from dataclasses import replace
+    ws = WL.batch_workloads(n_phonons)
+    pixels = sum(w.n_pixels for w in ws)
+    ctx = lma.Context(0)
+    st = torch.cuda.Stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def make(pb):
+        objs = []
+        for w in ws:
+            spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+            objs.append((spec, lma.Basis(ctx, spec, w.probe, replace(w.basis, phonon_batch=pb))))
+        return objs
+
+    def outs():
+        return [torch.empty((1, w.region.npy, w.region.npx), dtype=torch.float64, device="cuda:0")
+                for w in ws]
+
+    def timed(fn):
+        ms = []
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            ev[0].record(st)
+            fn()
+            ev[1].record(st)
+            ev[1].synchronize()
+            ms.append(ev[0].elapsed_time(ev[1]))
+        return float(np.mean(ms))
+
+    objs = make(1)
+    o_plain = outs()
+
+    def plain():
+        for (spec, basis), w, o in zip(objs, ws, o_plain):
+            basis.image(w.detectors, w.region, out=o, recompute=True, stream=st)
+
+    plain()
+    ms_plain = timed(plain)
+    ref = [o.cpu().numpy() for o in o_plain]
+    for spec, basis in objs:
+        basis.close()
+        spec.close()
+    torch.cuda.synchronize()
+
+    objs = make(0)
+    bases = [b for _, b in objs]
+    regions = [w.region for w in ws]
+    o_b = outs()
+    t0 = time.perf_counter()
+    lma.image_many(ctx, bases, ws[0].detectors, regions, o_b, graph=True, autotune=True, stream=st)
+    st.synchronize()
+    first_s = time.perf_counter() - t0
+
+    def batched():
+        lma.image_many(ctx, bases, ws[0].detectors, regions, o_b, graph=True, stream=st)
+
+    batched()
+    ms_b = timed(batched)
+    same = all(np.array_equal(o.cpu().numpy(), r) for o, r in zip(o_b, ref))
+    info = [b.info() for b in bases]
+    out = {"workload": "abo3 256^2/20sl + 512^2/50sl + 1024^2/100sl, %d configurations each" % n_phonons,
+           "pixels": pixels, "steps": steps,
+           "plain": {"ms": ms_plain, "pixels_per_s": pixels / (ms_plain / 1e3)},
+           "batched": {"ms": ms_b, "pixels_per_s": pixels / (ms_b / 1e3),
+                       "phonon_batch": [int(i.phonon_batch) for i in info],
+                       "rounds": int(max(-(-n_phonons // max(1, i.phonon_batch)) for i in info)),
+                       "first_call_s": first_s},
+           "speedup": ms_plain / ms_b, "bitwise_equal": bool(same),
+           "tuning": ctx.tuning()}
+    for spec, basis in objs:
+        basis.close()
+        spec.close()
+    ctx.close()
+    return out
+
+
 def profile_case() -> None:
     """The benchmark workload with one configuration, imaged twice with RECOMPUTE.
 
@@ -326,6 +418,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--edits", type=int, default=24, help="column-edit requests timed (0: skip)")
     ap.add_argument("--serving", type=int, default=60, help="requests per offered load (0: skip)")
+    ap.add_argument("--batch-phonons", type=int, default=4,
+                    help="configurations per specimen of the uneven three-specimen batch (0: skip)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one configuration of the workload, two image passes (for ncu captures)")
     args = ap.parse_args()
@@ -494,6 +588,11 @@ def main():
         torch.cuda.synchronize()
         serving = serving_measure(args.serving)
 
+    batching = None
+    if rank == 0 and args.batch_phonons > 0:
+        torch.cuda.synchronize()
+        batching = batching_measure(args.batch_phonons, steps=2)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_sample(w, 2, seed=5)
@@ -522,6 +621,7 @@ def main():
             "mixed": mixed,
             "edit_latency": edits,
             "serving": serving,
+            "batching": batching,
             "clocks": clk,
             "kernels": kernels,
             "wall_s_timed_region": wall,

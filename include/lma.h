@@ -59,6 +59,15 @@ typedef int32_t lma_status;
 #define LMA_EDIT_SET_SPECIES 1 /* give the atoms of a column another species */
 
 #define LMA_IMAGE_RECOMPUTE 1u /* treat every stored exit wave as stale (full path) */
+#define LMA_IMAGE_GRAPH 2u     /* lma_image_many: replay the device work as one CUDA graph */
+#define LMA_IMAGE_AUTOTUNE 4u  /* time every slice launch mode on this call's first launch of each
+                                  shape and keep the fastest for that shape (lma_tuning_read) */
+
+/* How the CTAs of a slice launch (step a3) take their translates. */
+#define LMA_SLICE_AUTO -1          /* the tuned mode of the launch shape, else the default */
+#define LMA_SLICE_ONE_PER_ITEM 0   /* one CTA per translate, scheduled by the hardware */
+#define LMA_SLICE_PERSISTENT 1     /* one CTA per SM, translates taken with a fixed stride */
+#define LMA_SLICE_DYNAMIC 2        /* one CTA per SM, translates taken from an atomic counter */
 
 typedef struct lma_ctx lma_ctx;
 typedef struct lma_specimen lma_specimen;
@@ -113,6 +122,8 @@ typedef struct {
   int32_t window;            /* W: propagation window X' = Y' (128) */
   int32_t det_window;        /* D: synthesis / detection window (128) */
   int32_t precision;         /* LMA_PREC_C64 or LMA_PREC_MIXED */
+  int32_t phonon_batch;      /* configurations propagated per launch and held at once;
+                                0 = as many as fit in 40 % of the free device memory */
 } lma_basis_desc;
 
 /* Annular detector r1 <= lambda |k| < r2 (rad), intersected with the bandlimit (Sec. 3.1, 2D STEM). */
@@ -132,7 +143,8 @@ typedef struct {
   int32_t n_sets;            /* coefficient sets computed so far (Case 1: 1, Case 2: c*d) */
   int32_t L, window, det_window;
   double gauss_sigma;        /* Angstrom, resolved */
-  int64_t exit_wave_bytes;   /* device bytes of the exit-wave store */
+  int64_t exit_wave_bytes;   /* device bytes of one configuration's exit-wave store */
+  int32_t phonon_batch;      /* resolved phonon batch (0 before the first device use) */
 } lma_basis_info;
 
 /* ---- context ------------------------------------------------------------------------- */
@@ -219,6 +231,22 @@ lma_status lma_image(lma_ctx* ctx, lma_specimen* spec, lma_basis* basis,
                      const lma_detector* det, int32_t n_det, const lma_region* region,
                      uint32_t flags, double* out, void* stream);
 
+/* Images of several specimens (of any sizes) in one call on one stream (the
+ * batching form of steps a1-a6): for each specimen its configurations go through
+ * the slice and synthesis kernels in phonon batches (see lma_basis_desc). With
+ * LMA_IMAGE_GRAPH (which requires LMA_IMAGE_RECOMPUTE, device outputs and a
+ * non-default stream) the whole sequence of launches of all specimens is
+ * captured once into a CUDA graph and replayed by later calls with the same
+ * arguments; the host only uploads changed atoms before the replay. A call whose
+ * buffers moved (new region, new sizes) captures a new graph.
+ * outs[k] is device memory, [n_det][npy_k][npx_k] doubles.
+ * Errors as for lma_image; LMA_ERR_INVALID for a host output or the default
+ * stream with LMA_IMAGE_GRAPH. */
+lma_status lma_image_many(lma_ctx* ctx, int32_t n, lma_specimen* const* specs,
+                          lma_basis* const* bases, const lma_detector* det, int32_t n_det,
+                          const lma_region* regions, uint32_t flags, double* const* outs,
+                          void* stream);
+
 /* ---- local recompute (step a7, Sec. 4.2.6) --------------------------------------------- */
 
 /* Edit one atomic column in every configuration: atoms whose lateral
@@ -284,11 +312,36 @@ typedef struct {
   lma_kernel_stat finalize;    /* step a6 */
 } lma_profile;
 
+/* One autotuned slice launch shape: the jobs (specimens) of the launch, its
+ * translates, store precision and window-origin parity, the chosen
+ * LMA_SLICE_* mode and the measured duration of each mode (ms; CUDA events on
+ * the caller's stream, one launch each, the launch's own results kept). */
+typedef struct {
+  int32_t n_jobs;
+  int32_t half;              /* 1: FP16 exit-wave store */
+  int32_t even;              /* 1: even window origins (16-byte staging) */
+  int64_t n_items;           /* translates in the launch */
+  int64_t translate_slices;  /* sum over translates of the slice count */
+  int32_t mode;              /* LMA_SLICE_* chosen */
+  double ms[3];              /* duration per mode, indexed by LMA_SLICE_* */
+} lma_tuning;
+
 /* Reset the counters; with on != 0 also record a CUDA event pair around every
  * kernel launch, on the stream the kernel is launched on. */
 lma_status lma_profile_enable(lma_ctx* ctx, int32_t on);
 /* Wait for the recorded events and return the totals since the last reset. */
 lma_status lma_profile_read(lma_ctx* ctx, lma_profile* out);
+
+/* ---- launch modes and autotuning (batching) -------------------------------------------- */
+
+/* Force the slice launch mode of this context (LMA_SLICE_*); LMA_SLICE_AUTO
+ * restores the tuned mode of each launch shape, else the default (one CTA per
+ * translate for one specimen, dynamic for several). Every mode computes
+ * bitwise the same exit waves. LMA_ERR_INVALID for an unknown mode. */
+lma_status lma_set_slice_mode(lma_ctx* ctx, int32_t mode);
+/* Copy up to cap tuned launch shapes (LMA_IMAGE_AUTOTUNE) to out, oldest
+ * first (out may be NULL when cap is 0); *n receives how many the context holds. */
+lma_status lma_tuning_read(lma_ctx* ctx, lma_tuning* out, int32_t cap, int32_t* n);
 
 #ifdef __cplusplus
 }

@@ -33,20 +33,41 @@ struct PotArgs {
   float2* t;                   // [n_slices][ny][nx]
 };
 
-// Step a3: multislice of lattice translates on W x W windows.
-struct SliceArgs {
-  const float2* t;             // [n_slices][ny][nx]
+// Step a3: multislice of lattice translates on W x W windows. One job = one
+// specimen and basis; a launch covers the items of up to kMaxJobs jobs.
+constexpr int kMaxJobs = 8;
+
+struct SliceJob {
+  const float2* t;             // [slots][n_slices][ny + W][nx + W] (periodic halo of W pixels)
   int nx, ny, n_slices;
+  size_t t_slot;               // elements of one configuration's transmission stack
   const float2* uW;            // [W][W] input wave, centre at (W/2, W/2)
-  const int32_t* list;         // translate indices to propagate
-  int n_list;
+  int n_translates;            // |I_f|
+  size_t u_slot;               // elements (waves x W x W) of one configuration's exit-wave store
   int lat_ox, lat_oy, lat_sx, lat_sy, lat_nax;   // I_f: pos(a, b) = (ox + a sx, oy + b sy)
-  float2* U;                   // [n_translates][W][W] complex64 store, or
-  void* Uh;                    // [n_translates][W][W] FP16 pairs (mixed store) with
-  float* Uscale;               // [n_translates] power-of-two factor restoring each wave
+  float2* U;                   // [slots][n_translates][W][W] complex64 store, or
+  void* Uh;                    // [slots][n_translates][W][W] FP16 pairs (mixed store) with
+  float* Uscale;               // [slots][n_translates] power-of-two factor restoring each wave
   const float2* ex;            // [W] exp(-i pi lambda eps kx^2) / W^2
   const float2* ey;            // [W] exp(-i pi lambda eps ky^2)
   int r2max;                   // bandlimit: m'^2 + n'^2 <= r2max
+};
+
+// How the CTAs of a slice launch take their items.
+enum SliceMode : int {
+  kSliceOnePerItem = 0,        // grid = items, the hardware schedules the CTAs
+  kSlicePersistent = 1,        // one CTA per SM, item li = blockIdx + k * gridDim
+  kSliceDynamic = 2,           // one CTA per SM, items fetched from an atomic counter
+  kSliceModes = 3
+};
+
+struct SliceLaunch {
+  SliceJob job[kMaxJobs];
+  int start[kMaxJobs + 1];     // list[start[j] .. start[j + 1]) holds job j's items
+  int n_jobs;
+  const int32_t* list;         // items slot * n_translates + translate
+  int n_list;
+  int* counter;                // kSliceDynamic: zeroed before the launch
 };
 
 // Steps a4-a6: synthesis, detector reading, FP64 accumulation over configurations.
@@ -59,10 +80,14 @@ struct SynthArgs {
   const int2* shift;           // [n_probes][L] placement of U in the probe window
   int L;
   int n_probes;
+  int n_cfg;                   // configurations in this launch (store slots 0..n_cfg-1)
+  int cfg_base;                // index of slot 0's configuration in the accumulator
+  int n_translates;            // |I_f| (stride of the per-wave factors between slots)
+  size_t u_slot;               // elements of one slot of the exit-wave store
   int cyclic;                  // windows are the whole periodic grid
   const uint32_t* det_bits;    // [n_det][kThreads] detector bits in C layout
   int n_det;
-  double* acc;                 // [n_det][n_probes] sum over configurations
+  double* acc;                 // [configuration][n_det][n_probes] readings (assigned)
 };
 
 // Scratch of the no-allocation readout: a file-scope device array of this size
@@ -76,12 +101,15 @@ size_t slice_smem_bytes();
 size_t synth_smem_bytes();
 cudaError_t launch_potential(const PotArgs& a, cudaStream_t s);
 // even_origins: every translate of the list has an even window x origin (16-byte staging);
-// half: write the FP16 store (Uh, Uscale) instead of the complex64 one
-cudaError_t launch_slice(const SliceArgs& a, bool even_origins, bool half, cudaStream_t s);
+// half: write the FP16 store (Uh, Uscale) instead of the complex64 one; mode: SliceMode
+// (kSliceDynamic zeroes a.counter on the stream first)
+cudaError_t launch_slice(const SliceLaunch& a, bool even_origins, bool half, int mode, cudaStream_t s);
+int sm_count();
 cudaError_t launch_synth(const SynthArgs& a, bool half, cudaStream_t s);
 // complex64 copy of one wave of the FP16 store
 cudaError_t launch_expand_half(const void* src, float scale, float2* dst, cudaStream_t s);
-cudaError_t launch_finalize(const double* acc, int64_t n, double scale, double* out,
+// out[i] = scale * sum over n_cfg slots (in slot order) of acc[c * n + i]
+cudaError_t launch_finalize(const double* acc, int64_t n, int n_cfg, double scale, double* out,
                             cudaStream_t s);
 
 }  // namespace lma_dev

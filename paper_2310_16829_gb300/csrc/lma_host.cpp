@@ -48,6 +48,34 @@ struct lma_ctx {
   };
   std::vector<Pending> pend;
   std::vector<cudaEvent_t> pool;
+  bool capturing = false;
+  // device copies of slice item lists, keyed by contents; a full cache reuses the
+  // oldest entry's buffer (cudaFree would synchronize the whole device)
+  struct List {
+    std::vector<int32_t> items;
+    uint64_t hash = 0;
+    void* p = nullptr;
+    size_t bytes = 0;
+  };
+  std::vector<List> lists;
+  std::vector<std::pair<void*, uint64_t>> capture_lists;   // lists read by the capture in progress
+  int* d_counter = nullptr;                                 // work counter of dynamic slice launches
+  // slice launch modes: forced (>= 0), or the timed choice per launch shape
+  int forced_mode = -1;
+  bool autotune = false;
+  struct Tune {
+    std::vector<int64_t> key;
+    lma_tuning rec;
+  };
+  std::vector<Tune> tune;
+  // captured image sequences (lma_image_many with LMA_IMAGE_GRAPH)
+  struct Graph {
+    std::vector<uintptr_t> key;
+    std::vector<std::pair<void*, uint64_t>> lists;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+  };
+  std::vector<Graph> graphs;
 };
 
 namespace {
@@ -202,6 +230,7 @@ cudaEvent_t pool_event(lma_ctx* ctx) {
 // count a launch and, when timing is on, bracket it with events on its stream
 template <class F>
 cudaError_t counted(lma_ctx* ctx, int kind, int64_t units, cudaStream_t st, F&& launch) {
+  if (ctx->capturing) return launch();
   ctx->stat[kind].launches++;
   ctx->stat[kind].units += units;
   if (!ctx->prof) return launch();
@@ -235,9 +264,10 @@ struct lma_specimen {
   double r_cut = 0.0;
   std::vector<PhononSet> ph;
   DevBuf d_peak;
-  DevBuf d_t;                 // transmission of configuration t_phonon
-  int t_phonon = -1;
-  std::vector<Rect> t_stale;  // pixel rectangles of d_t to rebuild
+  DevBuf d_t;                          // transmission stacks, one slot per configuration in flight
+  int t_slots = 0;                     // slots allocated in d_t
+  std::vector<int> t_phonon;           // configuration held by each slot (-1: none)
+  std::vector<std::vector<Rect>> t_stale;   // per slot: pixel rectangles to rebuild
   int64_t epoch = 0;          // bumps on every edit
 };
 
@@ -255,6 +285,7 @@ struct RegionTables {
   int64_t n_probes = 0;
   DevBuf tidx, alpha, shift;
   std::vector<int32_t> h_tidx;   // host copy of the translate indices
+  std::vector<uint8_t> needed;   // translates the region reads
 };
 
 struct lma_basis {
@@ -272,12 +303,12 @@ struct lma_basis {
   int r2max = 0;
   std::map<std::pair<int, int>, CoefSet> sets;
   // device
-  DevBuf d_uW, d_ex, d_ey, d_U, d_Uscale, d_list, d_acc, d_det;
+  DevBuf d_uW, d_ex, d_ey, d_U, d_Uscale, d_acc, d_det;
   bool dev_tables = false;
-  int U_phonon = -1;
+  int B = 0;                     // exit-wave store slots (configurations in flight)
+  std::vector<int> U_phonon;     // configuration held by each slot (-1: none)
   int64_t U_epoch = -1;
-  std::vector<uint8_t> valid;
-  std::vector<int32_t> last_list;
+  std::vector<uint8_t> valid;    // [slot][translate]
   RegionTables reg;
   bool reg_valid = false;
   std::vector<double> det_key;
@@ -488,13 +519,24 @@ lma_status ensure_basis_device(lma_basis* b, cudaStream_t st) {
   CUDA_TRY(ctx, cudaMemcpyAsync(b->d_ex.p, b->ex.data(), b->ex.size() * sizeof(float), cudaMemcpyHostToDevice, st));
   CUDA_TRY(ctx, cudaMemcpyAsync(b->d_ey.p, b->ey.data(), b->ey.size() * sizeof(float), cudaMemcpyHostToDevice, st));
   CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  // phonon batch: configurations whose exit waves (and transmissions) are held at once
   const bool half = b->desc.precision == LMA_PREC_MIXED;
-  const size_t ubytes = static_cast<size_t>(b->nT) * kW * kW * (half ? 4 : sizeof(float2));
-  CUDA_TRY(ctx, ensure(b->d_U, ubytes));
-  if (half) CUDA_TRY(ctx, ensure(b->d_Uscale, static_cast<size_t>(b->nT) * sizeof(float)));
-  b->last_list.clear();
-  b->valid.assign(static_cast<size_t>(b->nT), 0);
-  b->U_phonon = -1;
+  const int nph = static_cast<int>(b->spec->ph.size());
+  const lma_grid& g = b->spec->g;
+  const size_t u_cfg = static_cast<size_t>(b->nT) * kW * kW * (half ? 4 : sizeof(float2));
+  const size_t t_cfg = static_cast<size_t>(g.n_slices) * (g.nx + kW) * (g.ny + kW) * sizeof(float2);
+  int B = b->desc.phonon_batch;
+  if (B <= 0) {
+    size_t fr = 0, tot = 0;
+    CUDA_TRY(ctx, cudaMemGetInfo(&fr, &tot));
+    B = static_cast<int>(std::min<size_t>(static_cast<size_t>(nph), (fr * 2 / 5) / (u_cfg + t_cfg)));
+  }
+  B = std::max(1, std::min(B, nph));
+  CUDA_TRY(ctx, ensure(b->d_U, u_cfg * B));
+  if (half) CUDA_TRY(ctx, ensure(b->d_Uscale, static_cast<size_t>(b->nT) * B * sizeof(float)));
+  b->B = B;
+  b->valid.assign(static_cast<size_t>(b->nT) * B, 0);
+  b->U_phonon.assign(B, -1);
   b->dev_tables = true;
   return LMA_OK;
 }
@@ -522,7 +564,11 @@ lma_status ensure_atoms_device(lma_specimen* sp, int phi, cudaStream_t st) {
   return LMA_OK;
 }
 
-lma_status launch_t(lma_specimen* sp, int phi, const Rect& r, cudaStream_t st) {
+size_t t_slot_elems(const lma_grid& g) {
+  return static_cast<size_t>(g.n_slices) * (g.nx + kW) * (g.ny + kW);
+}
+
+lma_status launch_t(lma_specimen* sp, int slot, int phi, const Rect& r, cudaStream_t st) {
   lma_ctx* ctx = sp->ctx;
   const lma_grid& g = sp->g;
   PhononSet& p = sp->ph[phi];
@@ -560,116 +606,273 @@ lma_status launch_t(lma_specimen* sp, int phi, const Rect& r, cudaStream_t st) {
   a.ry0 = y0;
   a.rw = std::min(g.nx, ((r.x0 - x0 + r.w + 15) / 16) * 16);
   a.rh = std::min(g.ny, ((r.y0 - y0 + r.h + 15) / 16) * 16);
-  a.t = static_cast<float2*>(sp->d_t.p);
+  a.t = static_cast<float2*>(sp->d_t.p) + slot * t_slot_elems(g);
   const int64_t units = static_cast<int64_t>(r.w) * r.h * g.n_slices;
   CUDA_TRY(ctx, counted(ctx, K_POT, units, st, [&] { return lma_dev::launch_potential(a, st); }));
   return LMA_OK;
 }
 
-// make d_t hold configuration phi with no stale pixels
-lma_status ensure_t(lma_specimen* sp, int phi, bool force, cudaStream_t st) {
+// at least n transmission slots (growing the buffer forgets every slot's contents)
+lma_status reserve_t_slots(lma_specimen* sp, int n) {
+  lma_ctx* ctx = sp->ctx;
+  if (n <= sp->t_slots) return LMA_OK;
+  CUDA_TRY(ctx, ensure(sp->d_t, t_slot_elems(sp->g) * n * sizeof(float2)));
+  sp->t_slots = n;
+  sp->t_phonon.assign(n, -1);
+  sp->t_stale.assign(n, {});
+  return LMA_OK;
+}
+
+// make transmission slot `slot` hold configuration phi with no stale pixels
+lma_status ensure_t(lma_specimen* sp, int slot, int phi, bool force, cudaStream_t st) {
   lma_ctx* ctx = sp->ctx;
   const lma_grid& g = sp->g;
-  // periodic halo of W pixels on the right and bottom of every slice
-  const size_t tbytes = static_cast<size_t>(g.n_slices) * (g.nx + kW) * (g.ny + kW) * sizeof(float2);
-  CUDA_TRY(ctx, ensure(sp->d_t, tbytes));
+  lma_status s = reserve_t_slots(sp, slot + 1);
+  if (s != LMA_OK) return s;
   if (!sp->d_peak.p) {
     std::vector<float> pk(sp->peak.begin(), sp->peak.end());
     CUDA_TRY(ctx, ensure(sp->d_peak, pk.size() * sizeof(float)));
     CUDA_TRY(ctx, cudaMemcpy(sp->d_peak.p, pk.data(), pk.size() * sizeof(float), cudaMemcpyHostToDevice));
   }
-  lma_status s = ensure_atoms_device(sp, phi, st);
+  s = ensure_atoms_device(sp, phi, st);
   if (s != LMA_OK) return s;
-  if (force || sp->t_phonon != phi) {
-    s = launch_t(sp, phi, Rect{0, 0, g.nx, g.ny}, st);
+  if (force || sp->t_phonon[slot] != phi) {
+    s = launch_t(sp, slot, phi, Rect{0, 0, g.nx, g.ny}, st);
     if (s != LMA_OK) return s;
-    sp->t_phonon = phi;
-    sp->t_stale.clear();
+    sp->t_phonon[slot] = phi;
+    sp->t_stale[slot].clear();
     return LMA_OK;
   }
-  for (const Rect& r : sp->t_stale) {
-    s = launch_t(sp, phi, r, st);
+  for (const Rect& r : sp->t_stale[slot]) {
+    s = launch_t(sp, slot, phi, r, st);
     if (s != LMA_OK) return s;
   }
-  sp->t_stale.clear();
+  sp->t_stale[slot].clear();
   return LMA_OK;
 }
 
-// window x origin parity of translate i: (ox + a Sx - W/2) mod nx, nx and W even
-bool origin_even(const lma_basis* b, int32_t i) {
+// window x origin parity of list item (slot * nT + translate): (ox + a Sx - W/2) mod nx
+bool origin_even(const lma_basis* b, int32_t item) {
+  const int64_t i = item % b->nT;
   return ((b->ox + (i % b->nax) * b->Sx) & 1) == 0;
 }
 
-lma_status propagate_list(lma_basis* b, lma_specimen* sp, const std::vector<int32_t>& list_in,
-                          cudaStream_t st) {
-  lma_ctx* ctx = b->ctx;
-  if (list_in.empty()) return LMA_OK;
-  // even window origins first (16-byte staging), then odd ones
-  std::vector<int32_t> list;
-  list.reserve(list_in.size());
-  for (int32_t i : list_in)
-    if (origin_even(b, i)) list.push_back(i);
-  const size_t n_even = list.size();
-  for (int32_t i : list_in)
-    if (!origin_even(b, i)) list.push_back(i);
-  if (list != b->last_list) {
-    // stream order keeps this copy behind the kernels that read the previous list
-    CUDA_TRY(ctx, ensure(b->d_list, list.size() * sizeof(int32_t)));
-    CUDA_TRY(ctx, cudaMemcpyAsync(b->d_list.p, list.data(), list.size() * sizeof(int32_t),
-                                  cudaMemcpyHostToDevice, st));
-    b->last_list = list;
+uint64_t hash_items(const std::vector<int32_t>& v) {
+  uint64_t h = 1469598103934665603ull;   // FNV-1a over the items
+  for (int32_t x : v) {
+    h ^= static_cast<uint32_t>(x);
+    h *= 1099511628211ull;
   }
-  const lma_grid& g = sp->g;
-  lma_dev::SliceArgs a{};
-  a.t = static_cast<const float2*>(sp->d_t.p);
-  a.nx = g.nx;
-  a.ny = g.ny;
-  a.n_slices = g.n_slices;
-  a.uW = static_cast<const float2*>(b->d_uW.p);
-  a.lat_ox = b->ox;
-  a.lat_oy = b->oy;
-  a.lat_sx = b->Sx;
-  a.lat_sy = b->Sy;
-  a.lat_nax = b->nax;
-  const bool half = b->desc.precision == LMA_PREC_MIXED;
-  a.U = half ? nullptr : static_cast<float2*>(b->d_U.p);
-  a.Uh = half ? b->d_U.p : nullptr;
-  a.Uscale = half ? static_cast<float*>(b->d_Uscale.p) : nullptr;
-  a.ex = static_cast<const float2*>(b->d_ex.p);
-  a.ey = static_cast<const float2*>(b->d_ey.p);
-  a.r2max = b->r2max;
-  const int32_t* dl = static_cast<const int32_t*>(b->d_list.p);
-  for (int part = 0; part < 2; ++part) {
-    const size_t off = part == 0 ? 0 : n_even;
-    const size_t cnt = part == 0 ? n_even : list.size() - n_even;
-    if (cnt == 0) continue;
-    a.list = dl + off;
-    a.n_list = static_cast<int>(cnt);
-    const int64_t units = static_cast<int64_t>(cnt) * g.n_slices;
-    CUDA_TRY(ctx, counted(ctx, K_SLICE, units, st, [&] { return lma_dev::launch_slice(a, part == 0, half, st); }));
+  return h;
+}
+
+// device copy of an item list from the context's content-keyed cache; repeated
+// batches and captured graphs never copy from host memory
+lma_status upload_list(lma_ctx* ctx, const std::vector<int32_t>& list, cudaStream_t st, const int32_t** out) {
+  const uint64_t h = hash_items(list);
+  for (auto& e : ctx->lists)
+    if (e.hash == h && e.items == list) {
+      if (ctx->capturing) ctx->capture_lists.emplace_back(e.p, h);
+      *out = static_cast<const int32_t*>(e.p);
+      return LMA_OK;
+    }
+  if (ctx->capturing) return fail(ctx, LMA_ERR_CUDA, "slice list not resident during graph capture");
+  lma_ctx::List e;
+  if (ctx->lists.size() >= 16) {
+    e = std::move(ctx->lists.front());   // reuse the buffer: no cudaFree, no device-wide sync
+    ctx->lists.erase(ctx->lists.begin());
   }
-  for (int32_t i : list) b->valid[i] = 1;
+  const size_t bytes = list.size() * sizeof(int32_t);
+  if (e.bytes < bytes) {
+    if (e.p) CUDA_TRY(ctx, cudaFree(e.p));
+    e.p = nullptr;
+    e.bytes = 0;
+    size_t cap = size_t(64) << 10;
+    while (cap < bytes) cap <<= 1;
+    CUDA_TRY(ctx, cudaMalloc(&e.p, cap));
+    e.bytes = cap;
+  }
+  CUDA_TRY(ctx, cudaMemcpyAsync(e.p, list.data(), bytes, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(ctx, cudaStreamSynchronize(st));   // pageable source
+  e.items = list;
+  e.hash = h;
+  *out = static_cast<const int32_t*>(e.p);
+  ctx->lists.push_back(std::move(e));
   return LMA_OK;
 }
 
-// make U current for configuration phi on the given translates
-lma_status ensure_U(lma_basis* b, lma_specimen* sp, int phi, const std::vector<uint8_t>& needed,
-                    bool recompute, cudaStream_t st) {
-  if (b->U_phonon != phi || recompute || b->U_epoch != sp->epoch) {
-    if (b->U_epoch != sp->epoch && b->U_phonon == phi && !recompute) {
-      // edited through another basis: no exact bookkeeping here, recompute all
+lma_dev::SliceJob make_job(const lma_basis* b, const lma_specimen* sp) {
+  const lma_grid& g = sp->g;
+  lma_dev::SliceJob J{};
+  J.t = static_cast<const float2*>(sp->d_t.p);
+  J.nx = g.nx;
+  J.ny = g.ny;
+  J.n_slices = g.n_slices;
+  J.t_slot = t_slot_elems(g);
+  J.uW = static_cast<const float2*>(b->d_uW.p);
+  J.n_translates = static_cast<int>(b->nT);
+  J.u_slot = static_cast<size_t>(b->nT) * kW * kW;
+  J.lat_ox = b->ox;
+  J.lat_oy = b->oy;
+  J.lat_sx = b->Sx;
+  J.lat_sy = b->Sy;
+  J.lat_nax = b->nax;
+  const bool half = b->desc.precision == LMA_PREC_MIXED;
+  J.U = half ? nullptr : static_cast<float2*>(b->d_U.p);
+  J.Uh = half ? b->d_U.p : nullptr;
+  J.Uscale = half ? static_cast<float*>(b->d_Uscale.p) : nullptr;
+  J.ex = static_cast<const float2*>(b->d_ex.p);
+  J.ey = static_cast<const float2*>(b->d_ey.p);
+  J.r2max = b->r2max;
+  return J;
+}
+
+// Issue one slice launch, in the forced, tuned or default mode. With autotuning on
+// and a shape not seen before, every mode runs once (each writes the same exit
+// waves) and is timed with events on the stream; the fastest is kept.
+lma_status slice_launch(lma_ctx* ctx, const lma_dev::SliceLaunch& L, bool even, bool half, int64_t units,
+                        cudaStream_t st) {
+  std::vector<int64_t> key{half ? 1 : 0, even ? 1 : 0, L.n_jobs, L.n_list};
+  for (int j = 0; j < L.n_jobs; ++j) {
+    key.push_back(L.job[j].nx);
+    key.push_back(L.job[j].ny);
+    key.push_back(L.job[j].n_slices);
+    key.push_back(L.start[j + 1] - L.start[j]);
+  }
+  int mode = L.n_jobs > 1 ? lma_dev::kSliceDynamic : lma_dev::kSliceOnePerItem;
+  bool tuned = false;
+  for (const auto& t : ctx->tune)
+    if (t.key == key) {
+      mode = t.rec.mode;
+      tuned = true;
     }
+  if (ctx->forced_mode >= 0) mode = ctx->forced_mode;
+  auto launch = [&](int m) {
+    return counted(ctx, K_SLICE, units, st, [&] { return lma_dev::launch_slice(L, even, half, m, st); });
+  };
+  if (tuned || ctx->forced_mode >= 0 || !ctx->autotune || ctx->capturing) {
+    CUDA_TRY(ctx, launch(mode));
+    return LMA_OK;
+  }
+  lma_ctx::Tune t;
+  t.key = key;
+  t.rec.n_jobs = L.n_jobs;
+  t.rec.half = half ? 1 : 0;
+  t.rec.even = even ? 1 : 0;
+  t.rec.n_items = L.n_list;
+  t.rec.translate_slices = units;
+  cudaEvent_t ev[lma_dev::kSliceModes + 1];
+  for (auto& e : ev) CUDA_TRY(ctx, cudaEventCreate(&e));
+  cudaError_t err = cudaEventRecord(ev[0], st);
+  for (int m = 0; m < lma_dev::kSliceModes && err == cudaSuccess; ++m) {
+    err = launch(m);
+    if (err == cudaSuccess) err = cudaEventRecord(ev[m + 1], st);
+  }
+  if (err == cudaSuccess) err = cudaEventSynchronize(ev[lma_dev::kSliceModes]);
+  int best = 0;
+  for (int m = 0; m < lma_dev::kSliceModes && err == cudaSuccess; ++m) {
+    float ms = 0.f;
+    err = cudaEventElapsedTime(&ms, ev[m], ev[m + 1]);
+    t.rec.ms[m] = ms;
+    if (t.rec.ms[m] < t.rec.ms[best]) best = m;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  CUDA_TRY(ctx, err);
+  t.rec.mode = best;
+  ctx->tune.push_back(t);
+  return LMA_OK;
+}
+
+// The exit waves of several jobs (basis, specimen, items slot * nT + translate) in as
+// few slice launches as the jobs allow: one per store precision and window-origin
+// parity (and per kMaxJobs jobs). Marks the items current.
+struct JobWork {
+  lma_basis* b;
+  lma_specimen* sp;
+  std::vector<int32_t> items;
+};
+
+lma_status propagate_jobs(lma_ctx* ctx, std::vector<JobWork>& work, cudaStream_t st) {
+  if (!ctx->d_counter) {
+    if (ctx->capturing) return fail(ctx, LMA_ERR_CUDA, "work counter missing during graph capture");
+    CUDA_TRY(ctx, cudaMalloc(&ctx->d_counter, sizeof(int)));
+  }
+  for (int hv = 0; hv < 2; ++hv) {
+    std::vector<JobWork*> group;
+    for (JobWork& w : work)
+      if (!w.items.empty() && (w.b->desc.precision == LMA_PREC_MIXED) == (hv == 1)) group.push_back(&w);
+    for (size_t c0 = 0; c0 < group.size(); c0 += lma_dev::kMaxJobs) {
+      const int nj = static_cast<int>(std::min<size_t>(lma_dev::kMaxJobs, group.size() - c0));
+      for (int part = 0; part < 2; ++part) {
+        const bool even = part == 0;
+        lma_dev::SliceLaunch L{};
+        std::vector<int32_t> list;
+        int64_t units = 0;
+        L.n_jobs = nj;
+        for (int j = 0; j < nj; ++j) {
+          const JobWork& w = *group[c0 + j];
+          L.job[j] = make_job(w.b, w.sp);
+          L.start[j] = static_cast<int>(list.size());
+          for (int32_t i : w.items)
+            if (origin_even(w.b, i) == even) list.push_back(i);
+          units += static_cast<int64_t>(list.size() - L.start[j]) * w.sp->g.n_slices;
+        }
+        L.start[nj] = static_cast<int>(list.size());
+        if (list.empty()) continue;
+        if (list.size() > static_cast<size_t>(INT32_MAX)) return fail(ctx, LMA_ERR_UNSUPPORTED, "slice list too long");
+        lma_status s = upload_list(ctx, list, st, &L.list);
+        if (s != LMA_OK) return s;
+        L.n_list = static_cast<int>(list.size());
+        L.counter = ctx->d_counter;
+        if ((s = slice_launch(ctx, L, even, hv == 1, units, st)) != LMA_OK) return s;
+      }
+    }
+  }
+  for (JobWork& w : work)
+    for (int32_t i : w.items) w.b->valid[i] = 1;
+  return LMA_OK;
+}
+
+// Make configurations [phi0, phi0 + nb) of one basis ready to propagate on the needed
+// translates: transmissions current in their slots; the translates whose exit waves
+// are not current are returned as items. Slots [0, nb), or slot phi when every
+// configuration has its own slot (then stored waves are reused across calls).
+lma_status prepare_batch(lma_basis* b, lma_specimen* sp, int phi0, int nb, const std::vector<uint8_t>& needed,
+                         bool recompute, cudaStream_t st, std::vector<int32_t>* items) {
+  const int nph = static_cast<int>(sp->ph.size());
+  const bool own = b->B >= nph;
+  if (b->U_epoch != sp->epoch) {
+    // atoms replaced, or edited through another basis: nothing stored is current
     std::fill(b->valid.begin(), b->valid.end(), 0);
-    b->U_phonon = phi;
+    std::fill(b->U_phonon.begin(), b->U_phonon.end(), -1);
     b->U_epoch = sp->epoch;
   }
-  std::vector<int32_t> list;
-  for (int64_t i = 0; i < b->nT; ++i)
-    if (needed[i] && !b->valid[i]) list.push_back(static_cast<int32_t>(i));
-  if (list.empty()) return LMA_OK;
-  lma_status s = ensure_t(sp, phi, recompute, st);
+  lma_status s = reserve_t_slots(sp, b->B);
   if (s != LMA_OK) return s;
-  return propagate_list(b, sp, list, st);
+  for (int j = 0; j < nb; ++j) {
+    const int phi = phi0 + j;
+    const int slot = own ? phi : j;
+    uint8_t* v = b->valid.data() + static_cast<size_t>(slot) * b->nT;
+    if (recompute || b->U_phonon[slot] != phi) {
+      std::fill(v, v + b->nT, 0);
+      b->U_phonon[slot] = phi;
+    }
+    const size_t before = items->size();
+    for (int64_t i = 0; i < b->nT; ++i)
+      if (needed[i] && !v[i]) items->push_back(static_cast<int32_t>(slot * b->nT + i));
+    if (items->size() > before && (s = ensure_t(sp, slot, phi, recompute, st)) != LMA_OK) return s;
+  }
+  return LMA_OK;
+}
+
+lma_status ensure_batch(lma_basis* b, lma_specimen* sp, int phi0, int nb, const std::vector<uint8_t>& needed,
+                        bool recompute, cudaStream_t st) {
+  std::vector<JobWork> work(1);
+  work[0].b = b;
+  work[0].sp = sp;
+  lma_status s = prepare_batch(b, sp, phi0, nb, needed, recompute, st, &work[0].items);
+  if (s != LMA_OK) return s;
+  return propagate_jobs(b->ctx, work, st);
 }
 
 lma_status build_region(lma_basis* b, const lma_region* r, cudaStream_t st) {
@@ -699,6 +902,8 @@ lma_status build_region(lma_basis* b, const lma_region* r, cudaStream_t st) {
     }
   }
   RegionTables& R = b->reg;
+  R.needed.assign(static_cast<size_t>(b->nT), 0);
+  for (int32_t i : tidx) R.needed[i] = 1;
   CUDA_TRY(ctx, ensure(R.tidx, tidx.size() * sizeof(int32_t)));
   CUDA_TRY(ctx, ensure(R.alpha, al.size() * sizeof(float)));
   CUDA_TRY(ctx, ensure(R.shift, sh.size() * sizeof(int32_t)));
@@ -761,6 +966,92 @@ bool is_device_pointer(const void* p) {
 }  // namespace
 
 namespace {
+
+// Device work of the images of several (basis, specimen) pairs (steps a1, a3-a6).
+// Configurations go in rounds: round r takes each pair's r-th phonon batch; the
+// slice work of all pairs in a round is one launch (per precision and origin
+// parity), then each pair's batch is synthesized into its accumulator slots.
+// After the last round each pair's average goes to its dev_out (or, when that is
+// null, to the accumulator's last slot). Needs build_region / build_detectors done.
+struct ImageJob {
+  lma_basis* b;
+  lma_specimen* sp;
+  double* dev_out;
+};
+
+lma_status images_work(lma_ctx* ctx, const std::vector<ImageJob>& jobs, int n_det, bool recompute,
+                       cudaStream_t st) {
+  int rounds = 0;
+  for (const ImageJob& J : jobs) {
+    const int nph = static_cast<int>(J.sp->ph.size());
+    const int64_t nout = J.b->reg.n_probes * n_det;
+    // one slot per configuration plus one for the average
+    CUDA_TRY(ctx, ensure(J.b->d_acc, static_cast<size_t>(nout) * (nph + 1) * sizeof(double)));
+    rounds = std::max(rounds, (nph + J.b->B - 1) / J.b->B);
+  }
+  lma_status s;
+  for (int r = 0; r < rounds; ++r) {
+    std::vector<JobWork> work;
+    std::vector<std::pair<int, int>> batch;   // (phi0, nb) per job in this round
+    for (const ImageJob& J : jobs) {
+      const int nph = static_cast<int>(J.sp->ph.size());
+      const int phi0 = r * J.b->B;
+      const int nb = phi0 < nph ? std::min(J.b->B, nph - phi0) : 0;
+      batch.emplace_back(phi0, nb);
+      work.push_back(JobWork{J.b, J.sp, {}});
+      if (nb > 0 &&
+          (s = prepare_batch(J.b, J.sp, phi0, nb, J.b->reg.needed, recompute, st, &work.back().items)) != LMA_OK)
+        return s;
+    }
+    if ((s = propagate_jobs(ctx, work, st)) != LMA_OK) return s;
+    for (size_t k = 0; k < jobs.size(); ++k) {
+      const int nb = batch[k].second;
+      if (nb == 0) continue;
+      lma_basis* b = jobs[k].b;
+      const bool half = b->desc.precision == LMA_PREC_MIXED;
+      const int64_t np = b->reg.n_probes;
+      lma_dev::SynthArgs a{};
+      a.U = half ? nullptr : static_cast<const float2*>(b->d_U.p);
+      a.Uh = half ? b->d_U.p : nullptr;
+      a.Uscale = half ? static_cast<const float*>(b->d_Uscale.p) : nullptr;
+      a.tidx = static_cast<const int32_t*>(b->reg.tidx.p);
+      a.alpha = static_cast<const float2*>(b->reg.alpha.p);
+      a.shift = static_cast<const int2*>(b->reg.shift.p);
+      a.L = b->desc.L;
+      a.n_probes = static_cast<int>(np);
+      a.n_cfg = nb;
+      a.cfg_base = batch[k].first;
+      a.n_translates = static_cast<int>(b->nT);
+      a.u_slot = static_cast<size_t>(b->nT) * kW * kW;
+      a.cyclic = (b->nx == kW && b->ny == kW) ? 1 : 0;
+      a.det_bits = static_cast<const uint32_t*>(b->d_det.p);
+      a.n_det = n_det;
+      a.acc = static_cast<double*>(b->d_acc.p);
+      CUDA_TRY(ctx, counted(ctx, K_SYNTH, np * nb, st, [&] { return lma_dev::launch_synth(a, half, st); }));
+    }
+  }
+  for (const ImageJob& J : jobs) {
+    const int nph = static_cast<int>(J.sp->ph.size());
+    const int64_t nout = J.b->reg.n_probes * n_det;
+    const double* acc = static_cast<const double*>(J.b->d_acc.p);
+    double* fin = J.dev_out ? J.dev_out : static_cast<double*>(J.b->d_acc.p) + static_cast<size_t>(nph) * nout;
+    CUDA_TRY(ctx, counted(ctx, K_FIN, nout, st,
+                          [&] { return lma_dev::launch_finalize(acc, nout, nph, 1.0 / nph, fin, st); }));
+  }
+  return LMA_OK;
+}
+
+lma_status image_work(lma_basis* b, lma_specimen* sp, int n_det, bool recompute, double* dev_out,
+                      cudaStream_t st) {
+  return images_work(b->ctx, {ImageJob{b, sp, dev_out}}, n_det, recompute, st);
+}
+
+// slice launches of one API call time their modes (LMA_IMAGE_AUTOTUNE)
+struct AutotuneScope {
+  lma_ctx* c;
+  AutotuneScope(lma_ctx* c_, bool on) : c(c_) { c->autotune = on; }
+  ~AutotuneScope() { c->autotune = false; }
+};
 
 // validate and slice-sort the atom lists of every configuration into sp->ph
 lma_status load_atoms(lma_ctx* ctx, lma_specimen* sp, const lma_atoms* phonons, int n_phonons) {
@@ -839,7 +1130,17 @@ lma_status lma_create(int32_t device, lma_ctx** out) {
   return LMA_OK;
 }
 
-void lma_destroy(lma_ctx* ctx) { delete ctx; }
+void lma_destroy(lma_ctx* ctx) {
+  if (!ctx) return;
+  for (auto& g : ctx->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+  }
+  for (auto& l : ctx->lists)
+    if (l.p) cudaFree(l.p);
+  if (ctx->d_counter) cudaFree(ctx->d_counter);
+  delete ctx;
+}
 
 const char* lma_last_error(const lma_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
@@ -883,8 +1184,8 @@ lma_status lma_specimen_set_atoms(lma_ctx* ctx, lma_specimen* sp, const lma_atom
     return fail(ctx, LMA_ERR_INVALID, "configuration count differs from the specimen's");
   lma_status st = load_atoms(ctx, sp, phonons, n_phonons);
   if (st != LMA_OK) return st;
-  sp->t_phonon = -1;
-  sp->t_stale.clear();
+  std::fill(sp->t_phonon.begin(), sp->t_phonon.end(), -1);
+  for (auto& v : sp->t_stale) v.clear();
   sp->epoch++;
   return LMA_OK;
 }
@@ -909,7 +1210,7 @@ lma_status lma_transmission(lma_ctx* ctx, lma_specimen* sp, int32_t phonon, floa
     return fail(ctx, LMA_ERR_INVALID, "phonon index out of range");
   if (!device_ready(ctx)) return fail(ctx, LMA_ERR_UNSUPPORTED, "no device in this context");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  lma_status s = ensure_t(sp, phonon, false, st);
+  lma_status s = ensure_t(sp, 0, phonon, false, st);
   if (s != LMA_OK) return s;
   const lma_grid& g = sp->g;
   const bool dev = is_device_pointer(out);
@@ -995,7 +1296,6 @@ lma_status lma_free_basis(lma_basis* b) {
   b->d_ey.release();
   b->d_U.release();
   b->d_Uscale.release();
-  b->d_list.release();
   b->d_acc.release();
   b->d_det.release();
   b->reg.tidx.release();
@@ -1017,6 +1317,7 @@ lma_status lma_basis_get_info(const lma_basis* b, lma_basis_info* out) {
   out->gauss_sigma = b->gauss_sigma;
   out->exit_wave_bytes = b->nT * static_cast<int64_t>(kW) * kW *
                          (b->desc.precision == LMA_PREC_MIXED ? 4 : static_cast<int64_t>(sizeof(float2)));
+  out->phonon_batch = b->B;
   return LMA_OK;
 }
 
@@ -1055,14 +1356,15 @@ lma_status lma_propagate_basis(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, int
   lma_status s = ensure_basis_device(b, st);
   if (s != LMA_OK) return s;
   std::vector<uint8_t> all(static_cast<size_t>(b->nT), 1);
-  return ensure_U(b, sp, phonon, all, true, st);
+  return ensure_batch(b, sp, phonon, 1, all, true, st);
 }
 
 lma_status lma_exit_wave(lma_ctx* ctx, lma_basis* b, int64_t translate, float* out, void* stream) {
   if (!ctx || !b || !out) return fail(ctx, LMA_ERR_INVALID, "null argument");
   if (translate < 0 || translate >= b->nT) return fail(ctx, LMA_ERR_INVALID, "translate out of range");
   if (!device_ready(ctx)) return fail(ctx, LMA_ERR_UNSUPPORTED, "no device in this context");
-  if (!b->dev_tables || !b->valid[translate]) return fail(ctx, LMA_ERR_INVALID, "exit wave not current");
+  if (!b->dev_tables || b->U_epoch != b->spec->epoch || !b->valid[translate])
+    return fail(ctx, LMA_ERR_INVALID, "exit wave not current");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool dev = is_device_pointer(out);
   if (b->desc.precision == LMA_PREC_MIXED) {
@@ -1107,43 +1409,164 @@ lma_status lma_image(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, const lma_det
   if ((s = ensure_basis_device(b, st)) != LMA_OK) return s;
   if ((s = build_region(b, region, st)) != LMA_OK) return s;
   if ((s = build_detectors(b, det, n_det, st)) != LMA_OK) return s;
-  const int64_t np = b->reg.n_probes;
-  const int64_t nout = np * n_det;
-  CUDA_TRY(ctx, ensure(b->d_acc, static_cast<size_t>(nout) * sizeof(double)));
-  CUDA_TRY(ctx, cudaMemsetAsync(b->d_acc.p, 0, static_cast<size_t>(nout) * sizeof(double), st));
-  std::vector<uint8_t> needed(static_cast<size_t>(b->nT), 0);
-  for (int32_t i : b->reg.h_tidx) needed[i] = 1;
-  const bool recompute = (flags & LMA_IMAGE_RECOMPUTE) != 0;
-  const int nph = static_cast<int>(sp->ph.size());
-  for (int phi = 0; phi < nph; ++phi) {
-    if ((s = ensure_U(b, sp, phi, needed, recompute, st)) != LMA_OK) return s;
-    lma_dev::SynthArgs a{};
-    const bool half = b->desc.precision == LMA_PREC_MIXED;
-    a.U = half ? nullptr : static_cast<const float2*>(b->d_U.p);
-    a.Uh = half ? b->d_U.p : nullptr;
-    a.Uscale = half ? static_cast<const float*>(b->d_Uscale.p) : nullptr;
-    a.tidx = static_cast<const int32_t*>(b->reg.tidx.p);
-    a.alpha = static_cast<const float2*>(b->reg.alpha.p);
-    a.shift = static_cast<const int2*>(b->reg.shift.p);
-    a.L = b->desc.L;
-    a.n_probes = static_cast<int>(np);
-    a.cyclic = (b->nx == kW && b->ny == kW) ? 1 : 0;
-    a.det_bits = static_cast<const uint32_t*>(b->d_det.p);
-    a.n_det = n_det;
-    a.acc = static_cast<double*>(b->d_acc.p);
-    CUDA_TRY(ctx, counted(ctx, K_SYNTH, np, st, [&] { return lma_dev::launch_synth(a, half, st); }));
-  }
-  const double scale = 1.0 / nph;
-  const double* acc = static_cast<const double*>(b->d_acc.p);
-  if (is_device_pointer(out)) {
-    CUDA_TRY(ctx, counted(ctx, K_FIN, nout, st, [&] { return lma_dev::launch_finalize(acc, nout, scale, out, st); }));
-  } else {
-    double* acc_out = static_cast<double*>(b->d_acc.p);
-    CUDA_TRY(ctx, counted(ctx, K_FIN, nout, st, [&] { return lma_dev::launch_finalize(acc, nout, scale, acc_out, st); }));
-    CUDA_TRY(ctx, cudaMemcpyAsync(out, b->d_acc.p, static_cast<size_t>(nout) * sizeof(double), cudaMemcpyDeviceToHost, st));
+  const bool dev_out = is_device_pointer(out);
+  AutotuneScope tuning(ctx, (flags & LMA_IMAGE_AUTOTUNE) != 0);
+  if ((s = image_work(b, sp, n_det, (flags & LMA_IMAGE_RECOMPUTE) != 0, dev_out ? out : nullptr, st)) != LMA_OK)
+    return s;
+  if (!dev_out) {
+    const int64_t nout = b->reg.n_probes * n_det;
+    const double* fin = static_cast<const double*>(b->d_acc.p) + static_cast<size_t>(sp->ph.size()) * nout;
+    CUDA_TRY(ctx, cudaMemcpyAsync(out, fin, static_cast<size_t>(nout) * sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(ctx, cudaStreamSynchronize(st));
   }
   CUDA_TRY(ctx, cudaGetLastError());
+  return LMA_OK;
+}
+
+lma_status lma_image_many(lma_ctx* ctx, int32_t n, lma_specimen* const* specs, lma_basis* const* bases,
+                          const lma_detector* det, int32_t n_det, const lma_region* regions, uint32_t flags,
+                          double* const* outs, void* stream) {
+  if (!ctx || n <= 0 || !specs || !bases || !regions || !outs) return fail(ctx, LMA_ERR_INVALID, "null argument");
+  if (n_det <= 0 || n_det > lma_dev::kMaxDet || !det)
+    return fail(ctx, LMA_ERR_INVALID, "need 1..%d detectors", lma_dev::kMaxDet);
+  for (int d = 0; d < n_det; ++d)
+    if (!(det[d].r1 >= 0) || !(det[d].r2 > det[d].r1)) return fail(ctx, LMA_ERR_INVALID, "detector %d: need 0 <= r1 < r2", d);
+  if (!device_ready(ctx)) return fail(ctx, LMA_ERR_UNSUPPORTED, "no device in this context");
+  const bool graph = (flags & LMA_IMAGE_GRAPH) != 0;
+  const bool recompute = (flags & LMA_IMAGE_RECOMPUTE) != 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (graph && (!recompute || !stream))
+    return fail(ctx, LMA_ERR_INVALID, "LMA_IMAGE_GRAPH needs LMA_IMAGE_RECOMPUTE and a non-default stream");
+  lma_status s;
+  for (int k = 0; k < n; ++k) {
+    if (!specs[k] || !bases[k] || !outs[k]) return fail(ctx, LMA_ERR_INVALID, "null specimen, basis or output %d", k);
+    if (bases[k]->spec != specs[k]) return fail(ctx, LMA_ERR_INVALID, "basis %d belongs to another specimen", k);
+    if (bases[k]->ctx != ctx) return fail(ctx, LMA_ERR_INVALID, "basis %d belongs to another context", k);
+    for (int q = 0; q < k; ++q)
+      if (specs[q] == specs[k]) return fail(ctx, LMA_ERR_INVALID, "specimen %d appears twice", k);
+    if ((s = validate_region(ctx, bases[k], &regions[k])) != LMA_OK) return s;
+    if (graph && !is_device_pointer(outs[k])) return fail(ctx, LMA_ERR_INVALID, "LMA_IMAGE_GRAPH needs device outputs");
+  }
+  for (int k = 0; k < n; ++k) {
+    if ((s = ensure_basis_device(bases[k], st)) != LMA_OK) return s;
+    if ((s = build_region(bases[k], &regions[k], st)) != LMA_OK) return s;
+    if ((s = build_detectors(bases[k], det, n_det, st)) != LMA_OK) return s;
+  }
+  std::vector<bool> dev_out(n);
+  std::vector<ImageJob> jobs;
+  for (int k = 0; k < n; ++k) {
+    dev_out[k] = is_device_pointer(outs[k]);
+    jobs.push_back(ImageJob{bases[k], specs[k], dev_out[k] ? outs[k] : nullptr});
+  }
+  AutotuneScope tuning(ctx, (flags & LMA_IMAGE_AUTOTUNE) != 0);
+  if (!graph) {
+    if ((s = images_work(ctx, jobs, n_det, recompute, st)) != LMA_OK) return s;
+    for (int k = 0; k < n; ++k)
+      if (!dev_out[k]) {
+        const int64_t nout = bases[k]->reg.n_probes * n_det;
+        const double* fin = static_cast<const double*>(bases[k]->d_acc.p) + specs[k]->ph.size() * nout;
+        CUDA_TRY(ctx, cudaMemcpyAsync(outs[k], fin, static_cast<size_t>(nout) * sizeof(double),
+                                      cudaMemcpyDeviceToHost, st));
+      }
+    CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    return LMA_OK;
+  }
+  // host-side preparation that a captured graph cannot do: atoms on the device
+  for (int k = 0; k < n; ++k)
+    for (int phi = 0; phi < static_cast<int>(specs[k]->ph.size()); ++phi)
+      if ((s = ensure_atoms_device(specs[k], phi, st)) != LMA_OK) return s;
+  // signature of every buffer and size the captured launches depend on; the item
+  // lists they read are checked separately against the context's list cache
+  auto signature = [&]() {
+    std::vector<uintptr_t> key;
+    key.push_back(static_cast<uintptr_t>(n));
+    key.push_back(static_cast<uintptr_t>(n_det));
+    key.push_back(static_cast<uintptr_t>(ctx->forced_mode + 1));
+    key.push_back(reinterpret_cast<uintptr_t>(ctx->d_counter));
+    for (int d = 0; d < n_det; ++d) {
+      uint64_t r1, r2;
+      std::memcpy(&r1, &det[d].r1, 8);
+      std::memcpy(&r2, &det[d].r2, 8);
+      key.push_back(static_cast<uintptr_t>(r1));
+      key.push_back(static_cast<uintptr_t>(r2));
+    }
+    for (int k = 0; k < n; ++k) {
+      const lma_specimen* sp = specs[k];
+      const lma_basis* b = bases[k];
+      for (uintptr_t v : {reinterpret_cast<uintptr_t>(sp), reinterpret_cast<uintptr_t>(b),
+                          reinterpret_cast<uintptr_t>(outs[k]), reinterpret_cast<uintptr_t>(sp->d_t.p),
+                          reinterpret_cast<uintptr_t>(sp->d_peak.p), reinterpret_cast<uintptr_t>(b->d_U.p),
+                          reinterpret_cast<uintptr_t>(b->d_Uscale.p), reinterpret_cast<uintptr_t>(b->d_acc.p),
+                          reinterpret_cast<uintptr_t>(b->d_det.p), reinterpret_cast<uintptr_t>(b->reg.tidx.p),
+                          reinterpret_cast<uintptr_t>(b->reg.alpha.p), reinterpret_cast<uintptr_t>(b->reg.shift.p),
+                          static_cast<uintptr_t>(b->B)})
+        key.push_back(v);
+      const lma_region& r = regions[k];
+      for (int32_t v : {r.px0, r.py0, r.npx, r.npy, r.spacing_px[0], r.spacing_px[1]})
+        key.push_back(static_cast<uintptr_t>(static_cast<uint32_t>(v)));
+      for (const PhononSet& p : sp->ph)
+        for (const DevBuf* d : {&p.dx, &p.dy, &p.dsp, &p.dss}) key.push_back(reinterpret_cast<uintptr_t>(d->p));
+    }
+    return key;
+  };
+  auto lists_resident = [&](const lma_ctx::Graph& g) {
+    for (const auto& u : g.lists) {
+      bool found = false;
+      for (const auto& e : ctx->lists) found = found || (e.p == u.first && e.hash == u.second);
+      if (!found) return false;
+    }
+    return true;
+  };
+  std::vector<uintptr_t> key = signature();
+  for (auto& g : ctx->graphs)
+    if (g.key == key && lists_resident(g)) {
+      CUDA_TRY(ctx, cudaGraphLaunch(g.exec, st));
+      return LMA_OK;
+    }
+  // first call with these buffers: an ordinary run (allocations, list uploads, tuning,
+  // outputs), then the same launches captured for later calls
+  if ((s = images_work(ctx, jobs, n_det, true, st)) != LMA_OK) return s;
+  CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  key = signature();
+  lma_ctx::Graph g;
+  g.key = key;
+  ctx->capture_lists.clear();
+  CUDA_TRY(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  ctx->capturing = true;
+  lma_status cs = images_work(ctx, jobs, n_det, true, st);
+  ctx->capturing = false;
+  cudaError_t e = cudaStreamEndCapture(st, &g.graph);
+  g.lists.swap(ctx->capture_lists);
+  if (cs != LMA_OK) {
+    if (g.graph) cudaGraphDestroy(g.graph);
+    return cs;
+  }
+  if (e != cudaSuccess) return fail(ctx, LMA_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&g.exec, g.graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g.graph);
+    return fail(ctx, LMA_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  if (ctx->graphs.size() >= 8) {
+    cudaGraphExecDestroy(ctx->graphs.front().exec);
+    cudaGraphDestroy(ctx->graphs.front().graph);
+    ctx->graphs.erase(ctx->graphs.begin());
+  }
+  ctx->graphs.push_back(g);
+  return LMA_OK;   // this call's outputs came from the ordinary run
+}
+
+lma_status lma_set_slice_mode(lma_ctx* ctx, int32_t mode) {
+  if (!ctx) return LMA_ERR_INVALID;
+  if (mode < LMA_SLICE_AUTO || mode >= lma_dev::kSliceModes) return fail(ctx, LMA_ERR_INVALID, "unknown slice mode %d", mode);
+  ctx->forced_mode = mode;
+  return LMA_OK;
+}
+
+lma_status lma_tuning_read(lma_ctx* ctx, lma_tuning* out, int32_t cap, int32_t* n) {
+  if (!ctx || !n || cap < 0 || (cap > 0 && !out)) return fail(ctx, LMA_ERR_INVALID, "null argument");
+  *n = static_cast<int32_t>(ctx->tune.size());
+  for (int32_t i = 0; i < cap && i < *n; ++i) out[i] = ctx->tune[i].rec;
   return LMA_OK;
 }
 
@@ -1206,7 +1629,8 @@ lma_status lma_edit_column(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, double 
     const int y0 = static_cast<int>(std::floor((ymin - sp->r_cut) / dy)) - 1;
     const int y1 = static_cast<int>(std::ceil((ymax + sp->r_cut) / dy)) + 1;
     Rect r{mod(x0, g.nx), mod(y0, g.ny), std::min(x1 - x0 + 1, g.nx), std::min(y1 - y0 + 1, g.ny)};
-    if (sp->t_phonon >= 0) sp->t_stale.push_back(r);
+    for (int k = 0; k < sp->t_slots; ++k)
+      if (sp->t_phonon[k] >= 0) sp->t_stale[k].push_back(r);
     sp->epoch++;
     if (b && b->dev_tables) {
       // exit waves whose window [pos - W/2, pos + W/2) meets the rectangle (periodic)
@@ -1222,9 +1646,12 @@ lma_status lma_edit_column(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, double 
           const int wx0 = mod(b->ox + ia * b->Sx - kW / 2, g.nx);
           if (!meets(wx0, kW, r.x0, r.w, g.nx)) continue;
           const int64_t i = static_cast<int64_t>(ib) * b->nax + ia;
-          if (b->valid[i]) {
-            b->valid[i] = 0;
-            ++stale;
+          for (int k = 0; k < b->B; ++k) {
+            uint8_t& v = b->valid[static_cast<size_t>(k) * b->nT + i];
+            if (v) {
+              v = 0;
+              ++stale;
+            }
           }
         }
       }
@@ -1318,12 +1745,16 @@ lma_status lma_readout_noalloc(lma_ctx* ctx, lma_basis* b, const float* exit_wav
   a.shift = reinterpret_cast<const int2*>(base + o_shift);
   a.L = L;
   a.n_probes = static_cast<int>(np);
+  a.n_cfg = 1;
+  a.cfg_base = 0;
+  a.n_translates = static_cast<int>(b->nT);
+  a.u_slot = 0;
   a.cyclic = (b->nx == kW && b->ny == kW) ? 1 : 0;
   a.det_bits = reinterpret_cast<const uint32_t*>(base + o_det);
   a.n_det = n_det;
   a.acc = reinterpret_cast<double*>(base + o_acc);
   CUDA_TRY(ctx, lma_dev::launch_synth(a, false, st));
-  CUDA_TRY(ctx, lma_dev::launch_finalize(a.acc, nout, 1.0, out, st));
+  CUDA_TRY(ctx, lma_dev::launch_finalize(a.acc, nout, 1, 1.0, out, st));
   // the host tables above are pageable: keep them alive until the copies have run
   CUDA_TRY(ctx, cudaStreamSynchronize(st));
   return LMA_OK;
@@ -1375,7 +1806,7 @@ lma_status lma_affected_probes(lma_ctx* ctx, lma_basis* b, const lma_region* reg
       bool hit = false;
       for (int j = 0; j < b->desc.L && !hit; ++j) {
         const int64_t i = translate_index(b, px + cs->odx[j], py + cs->ody[j]);
-        hit = b->valid.empty() || !b->valid[i];
+        hit = b->valid.empty() || !b->valid[i];   // first slot (the serving case holds one)
       }
       if (out_mask) out_mask[static_cast<size_t>(pb) * region->npx + pa] = hit ? 1 : 0;
       cnt += hit ? 1 : 0;

@@ -18,6 +18,8 @@
 //   pass B: 4-point DFTs over r (x axis) and n1y (y axis)
 //           + twiddle W_128^(n2y k1y)                              group (k1, n2y)
 //   pass C: 32-point DFT over n2y (y axis)                         thread (kx, k1y)
+//           (kx permuted so that one warp of four holds only columns outside
+//           the 2/3 bandlimit and skips the pass)
 // The propagator multiply sits in pass C; the inverse runs the passes back
 // (C, B, A) with conjugate twiddles, so no index permutation is ever stored.
 // Between passes the data crosses threads through padded shared-memory tables
@@ -67,6 +69,20 @@ __device__ __forceinline__ float2 tw32(float2 d, int m) {
   if (m == 8) return INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
   const float2 w = c_w128[4 * m];
   return INV ? cmulc(d, w) : cmul(d, w);
+}
+
+// Column kx of pass-C thread T (k1y = T >> 7). Logical warps 1 and 2 of each k1y group
+// exchange their lanes l < 11, so that logical warp 1 holds kx = 43..74: with the 2/3
+// bandlimit (|kx| <= 42 at W = 128) every one of its columns is masked and it skips
+// pass C. The logical warps are rotated by k1y within the group, so that the four
+// skipping warps have four different warp ids mod 4 (one per SM sub-partition). Every
+// warp keeps 32 distinct kx mod 32 (conflict-free X2 accesses).
+__device__ __forceinline__ int c_column(int T) {
+  const int k1y = T >> 7;
+  const int w = (((T >> 5) & 3) - k1y) & 3, l = T & 31;
+  if (w == 1) return l < 11 ? 64 + l : 32 + l;
+  if (w == 2) return l < 11 ? 32 + l : 64 + l;
+  return 32 * w + l;
 }
 
 // compile-time loop: f(std::integral_constant<int, I>) for I = B..E-1
@@ -260,10 +276,11 @@ __device__ __forceinline__ void stage_t(float2* sdst, const float2* g, int pitch
   cp_async_commit();
 }
 
-// One CTA per translate; EVEN selects the window-origin parity of the translates in the
-// list; HALF writes the exit wave as FP16 pairs scaled by a per-wave power of two.
+// One translate per CTA at a time, items taken as SliceLaunch's mode says; EVEN selects
+// the window-origin parity of the translates in the list; HALF writes the exit wave as
+// FP16 pairs scaled by a per-wave power of two.
 template <bool EVEN, bool HALF>
-__global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, const int mode) {
   extern __shared__ __align__(16) float2 sm[];
   float2* R0 = sm;             // t prefetch (thread-private slots n1*512 + T) / exchanges X1, X2
   float2* R1 = sm + kX1;       // exchange X4 (two halves)
@@ -273,31 +290,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
 
   const int T = threadIdx.x;
   load_twiddles(twA, twB, T);
-  if (T < 128) eys[(T & 3) * 32 + (T >> 2)] = a.ey[T];
   // A layout: thread (y, r)
   const int ya = T >> 2, ra = T & 3;
   // B layout: groups (k1 = (T & 15) + 16 h, n2y = T >> 4), h = 0, 1
   const int k1lo = T & 15, n2y = T >> 4;
-  // C layout: thread (kx, k1y)
-  const int kx = T & 127, k1y = T >> 7, k1x = kx & 31, k2x = kx >> 5;
+  // C layout: thread (kx, k1y), kx permuted within each k1y group (c_column)
+  const int kx = c_column(T), k1y = T >> 7, k1x = kx & 31, k2x = kx >> 5;
   const float2* tA = twA + ra * 34;
   const float2* tB = twB + n2y * 4;
   const float4* ey4 = reinterpret_cast<const float4*>(eys + k1y * 32);
-  const float2 exr = a.ex[kx];
+  const int kxs = kx < 64 ? kx : kx - 128;
+  // per-job propagator constants (reloaded when the job changes)
+  float2 exr = make_float2(0.f, 0.f);
   uint32_t mbits = 0;
-  {
-    const int kxs = kx < 64 ? kx : kx - 128;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int ky = k1y + 4 * j;
-      const int kys = ky < 64 ? ky : ky - 128;
-      if (kxs * kxs + kys * kys <= a.r2max) mbits |= 1u << j;
-    }
-  }
-  __syncthreads();
-
-  const int pitch = a.nx + kW;                                    // padded row
-  const size_t slice_elems = static_cast<size_t>(pitch) * (a.ny + kW);
+  bool c_live = false;
+  int cur_job = -1;
+  __shared__ int s_next;
   // t staging: row-major W x 132 tile in R0 (the 132-float2 row keeps the A-layout
   // reads of 8 rows x 4 columns on distinct banks); element (y, x) at y * 132 + x
   float2* const tA_rd = R0 + ya * kTPitch + ra;                   // + 4 * n1
@@ -308,29 +316,64 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
   float2* const x4w = R1 + (4 * n2y) * 18 + k1lo;                 // B side of X4, + (128 q + r) * 18
   const float4* const x4r = reinterpret_cast<const float4*>(R1 + T * 18);   // A side of X4 (pairs)
 
-  for (int li = blockIdx.x; li < a.n_list; li += gridDim.x) {
-    const int ti = a.list[li];
-    const int ia = ti % a.lat_nax, ib = ti / a.lat_nax;
-    int ox = (a.lat_ox + ia * a.lat_sx - kW / 2) % a.nx;
-    if (ox < 0) ox += a.nx;
-    int oy = (a.lat_oy + ib * a.lat_sy - kW / 2) % a.ny;
-    if (oy < 0) oy += a.ny;
+  __syncthreads();   // twiddles
+
+  for (int it = 0;; ++it) {
+    int li;
+    if (mode == kSliceDynamic) {
+      if (T == 0) s_next = atomicAdd(a.counter, 1);
+      __syncthreads();   // the previous item ended with a barrier: s_next is free to rewrite
+      li = s_next;
+    } else {
+      li = blockIdx.x + it * gridDim.x;
+    }
+    if (li >= a.n_list) break;
+    int jb = 0;
+    while (jb + 1 < a.n_jobs && li >= a.start[jb + 1]) ++jb;
+    const SliceJob& J = a.job[jb];
+    if (jb != cur_job) {
+      // the previous item's last barrier has passed: eys is free; the staging barrier
+      // below publishes it before pass C reads it
+      cur_job = jb;
+      if (T < 128) eys[(T & 3) * 32 + (T >> 2)] = J.ey[T];
+      exr = J.ex[kx];
+      mbits = 0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int ky = k1y + 4 * j;
+        const int kys = ky < 64 ? ky : ky - 128;
+        if (kxs * kxs + kys * kys <= J.r2max) mbits |= 1u << j;
+      }
+      // a warp whose columns are all outside the bandlimit skips pass C: its spectrum is zero
+      c_live = __any_sync(0xffffffffu, mbits != 0u);
+    }
+    const int n_slices = J.n_slices;
+    const int pitch = J.nx + kW;                                  // padded row
+    const size_t slice_elems = static_cast<size_t>(pitch) * (J.ny + kW);
+    const int item = a.list[li];
+    const int cfg = item / J.n_translates;
+    const int ti = item - cfg * J.n_translates;
+    const int ia = ti % J.lat_nax, ib = ti / J.lat_nax;
+    int ox = (J.lat_ox + ia * J.lat_sx - kW / 2) % J.nx;
+    if (ox < 0) ox += J.nx;
+    int oy = (J.lat_oy + ib * J.lat_sy - kW / 2) % J.ny;
+    if (oy < 0) oy += J.ny;
     // the halo of W pixels keeps every window inside the padded array
     // chunk i of thread T: row (T >> 6) + 8 i, columns 2 (T & 63) + {0, 1} (even origins)
     //                   or row (T >> 7) + 4 i, column T & 127          (odd origins)
     const int sy0 = EVEN ? (T >> 6) : (T >> 7);
     const int sx0 = EVEN ? 2 * (T & 63) : (T & 127);
     float2* const sdst = R0 + sy0 * kTPitch + sx0;
-    const float2* const gsrc = a.t + static_cast<size_t>(oy + sy0) * pitch + ox + sx0;
+    const float2* const gsrc = J.t + cfg * J.t_slot + static_cast<size_t>(oy + sy0) * pitch + ox + sx0;
 
     stage_t<EVEN>(sdst, gsrc, pitch);
     float2 v[32];
 #pragma unroll
-    for (int n1 = 0; n1 < 32; ++n1) v[n1] = a.uW[ya * kW + 4 * n1 + ra];
+    for (int n1 = 0; n1 < 32; ++n1) v[n1] = J.uW[ya * kW + 4 * n1 + ra];
     cp_async_wait_all();
     __syncthreads();
 
-    for (int s = 0; s < a.n_slices; ++s) {
+    for (int s = 0; s < n_slices; ++s) {
       // transmission (Sec. 3.2): psi <- t_s psi
       if (s > 0) {
         cp_async_wait_all();
@@ -364,23 +407,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
           x2b[(q * 4 + r) * 1024 + 16] = b1[q * 4 + r];
         }
       __syncthreads();
-      float2 c[32];
+      if (c_live) {
+        float2 c[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) c[j] = x2c[j * 32];
-      dft32<false>(c);
-      // propagation (Sec. 3.2): exp(-i pi lambda eps |k|^2), bandlimit, 1/W^2
+        for (int j = 0; j < 32; ++j) c[j] = x2c[j * 32];
+        dft32<false>(c);
+        // propagation (Sec. 3.2): exp(-i pi lambda eps |k|^2), bandlimit, 1/W^2
 #pragma unroll
-      for (int j = 0; j < 32; j += 2) {
-        const float4 e2 = ey4[j / 2];
-        const float2 p0 = cmul(exr, make_float2(e2.x, e2.y));
-        const float2 p1 = cmul(exr, make_float2(e2.z, e2.w));
-        c[j] = ((mbits >> j) & 1u) ? cmul(c[j], p0) : make_float2(0.f, 0.f);
-        c[j + 1] = ((mbits >> (j + 1)) & 1u) ? cmul(c[j + 1], p1) : make_float2(0.f, 0.f);
+        for (int j = 0; j < 32; j += 2) {
+          const float4 e2 = ey4[j / 2];
+          const float2 p0 = cmul(exr, make_float2(e2.x, e2.y));
+          const float2 p1 = cmul(exr, make_float2(e2.z, e2.w));
+          c[j] = ((mbits >> j) & 1u) ? cmul(c[j], p0) : make_float2(0.f, 0.f);
+          c[j + 1] = ((mbits >> (j + 1)) & 1u) ? cmul(c[j + 1], p1) : make_float2(0.f, 0.f);
+        }
+        dft32<true>(c);
+        // each C thread writes back exactly the entries it read: no barrier needed here
+#pragma unroll
+        for (int j = 0; j < 32; ++j) x2c[j * 32] = c[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) x2c[j * 32] = make_float2(0.f, 0.f);
       }
-      dft32<true>(c);
-      // each C thread writes back exactly the entries it read: no barrier needed here
-#pragma unroll
-      for (int j = 0; j < 32; ++j) x2c[j * 32] = c[j];
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < 4; ++q)
@@ -390,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
           b1[q * 4 + r] = x2b[(q * 4 + r) * 1024 + 16];
         }
       __syncthreads();  // R0 is free: prefetch the next slice's transmission
-      const bool more = s + 1 < a.n_slices;
+      const bool more = s + 1 < n_slices;
       if (more) stage_t<EVEN>(sdst, gsrc + (s + 1) * slice_elems, pitch);
       passB_inv(b0, tB);
       passB_inv(b1, tB);
@@ -443,12 +491,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceArgs a) {
       int e = 0;
       if (mx > 0.f) frexpf(mx, &e);
       const float sc = ldexpf(1.f, -e);
-      __half2* uh = static_cast<__half2*>(a.Uh) + static_cast<size_t>(ti) * (kW * kW) + ya * kW + ra;
+      __half2* uh = static_cast<__half2*>(J.Uh) + cfg * J.u_slot + static_cast<size_t>(ti) * (kW * kW) + ya * kW + ra;
 #pragma unroll
       for (int n1 = 0; n1 < 32; ++n1) uh[4 * n1] = __floats2half2_rn(v[n1].x * sc, v[n1].y * sc);
-      if (T == 0) a.Uscale[ti] = ldexpf(1.f, e);
+      if (T == 0) J.Uscale[static_cast<size_t>(cfg) * J.n_translates + ti] = ldexpf(1.f, e);
     } else {
-      float2* ud = a.U + static_cast<size_t>(ti) * (kW * kW) + ya * kW + ra;
+      float2* ud = J.U + cfg * J.u_slot + static_cast<size_t>(ti) * (kW * kW) + ya * kW + ra;
 #pragma unroll
       for (int n1 = 0; n1 < 32; ++n1) ud[4 * n1] = v[n1];
     }
@@ -474,7 +522,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
   load_twiddles(twA, twB, T);
   const int ya = T >> 2, ra = T & 3;
   const int k1lo = T & 15, n2y = T >> 4;
-  const int kx = T & 127, k1y = T >> 7, k1x = kx & 31, k2x = kx >> 5;
+  const int kx = c_column(T), k1y = T >> 7, k1x = kx & 31, k2x = kx >> 5;
   const float2* tA = twA + ra * 34;
   const float2* tB = twB + n2y * 4;
   float4* const x1w = reinterpret_cast<float4*>(R0 + T * 34);
@@ -482,11 +530,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
   float2* const x2b = R0 + n2y * 32 + k1lo;
   float2* const x2c = R0 + (k1y * 4 + k2x) * 1024 + k1x;
   uint32_t dbits[kMaxDet];
+  uint32_t any_bits = 0u;
 #pragma unroll
-  for (int d = 0; d < kMaxDet; ++d) dbits[d] = d < a.n_det ? a.det_bits[d * kThreads + T] : 0u;
+  for (int d = 0; d < kMaxDet; ++d) {
+    dbits[d] = d < a.n_det ? a.det_bits[d * kThreads + kx + 128 * k1y] : 0u;
+    any_bits |= dbits[d];
+  }
+  // a warp whose columns meet no detector skips pass C
+  const bool c_live = __any_sync(0xffffffffu, any_bits != 0u);
   __syncthreads();
 
-  for (int p = blockIdx.x; p < a.n_probes; p += gridDim.x) {
+  const int n_items = a.n_probes * a.n_cfg;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int cfg = item / a.n_probes;
+    const int p = item - cfg * a.n_probes;
+    const float2* const Uc = a.U ? a.U + cfg * a.u_slot : nullptr;
+    const void* const Uhc = a.Uh ? static_cast<const void*>(static_cast<const __half2*>(a.Uh) + cfg * a.u_slot) : nullptr;
+    const float* const Usc = a.Uscale ? a.Uscale + static_cast<size_t>(cfg) * a.n_translates : nullptr;
     float2 v[32];
 #pragma unroll
     for (int n1 = 0; n1 < 32; ++n1) v[n1] = make_float2(0.f, 0.f);
@@ -505,10 +565,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
       const size_t off = static_cast<size_t>(tp[j]) * (kW * kW) + yy * kW;
       const int x0 = ra - sh.x;
       if constexpr (HALF) {
-        const float f = a.Uscale[tp[j]];
+        const float f = Usc[tp[j]];
         al.x *= f;
         al.y *= f;
-        const __half2* row = static_cast<const __half2*>(a.Uh) + off;
+        const __half2* row = static_cast<const __half2*>(Uhc) + off;
 #pragma unroll
         for (int n1 = 0; n1 < 32; ++n1) {
           int xx = x0 + 4 * n1;
@@ -520,7 +580,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
           }
         }
       } else {
-        const float2* row = a.U + off;
+        const float2* row = Uc + off;
 #pragma unroll
         for (int n1 = 0; n1 < 32; ++n1) {
           int xx = x0 + 4 * n1;
@@ -558,28 +618,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
         x2b[(q * 4 + r) * 1024 + 16] = b1[q * 4 + r];
       }
     __syncthreads();
-    float2 c[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) c[j] = x2c[j * 32];
-    dft32<false>(c);
-    // detector (Sec. 3.1, 2D STEM): sum of |DFT|^2 over the annulus
     const int warp = T >> 5, lane = T & 31;
+    if (c_live) {
+      float2 c[32];
 #pragma unroll
-    for (int d = 0; d < kMaxDet; ++d) {
-      if (d >= a.n_det) break;
-      float sum = 0.f;
+      for (int j = 0; j < 32; ++j) c[j] = x2c[j * 32];
+      dft32<false>(c);
+      // detector (Sec. 3.1, 2D STEM): sum of |DFT|^2 over the annulus
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if ((dbits[d] >> j) & 1u) sum = fmaf(c[j].x, c[j].x, fmaf(c[j].y, c[j].y, sum));
+      for (int d = 0; d < kMaxDet; ++d) {
+        if (d >= a.n_det) break;
+        float sum = 0.f;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-      if (lane == 0) red[warp * kMaxDet + d] = sum;
+        for (int j = 0; j < 32; ++j)
+          if ((dbits[d] >> j) & 1u) sum = fmaf(c[j].x, c[j].x, fmaf(c[j].y, c[j].y, sum));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) red[warp * kMaxDet + d] = sum;
+      }
+    } else if (lane < kMaxDet) {
+      red[warp * kMaxDet + lane] = 0.f;
     }
     __syncthreads();
     if (T < a.n_det) {
       double tot = 0.0;
       for (int w = 0; w < kThreads / 32; ++w) tot += static_cast<double>(red[w * kMaxDet + T]);
-      a.acc[static_cast<size_t>(T) * a.n_probes + p] += tot * (1.0 / (kW * kW));
+      a.acc[(static_cast<size_t>(a.cfg_base + cfg) * a.n_det + T) * a.n_probes + p] = tot * (1.0 / (kW * kW));
     }
   }
 }
@@ -679,9 +743,14 @@ __global__ void k_expand_half(const __half2* src, float scale, float2* dst) {
   }
 }
 
-__global__ void k_finalize(const double* acc, int64_t n, double scale, double* out) {
+// step a6: average over configurations, summed in configuration order (deterministic)
+__global__ void k_finalize(const double* acc, int64_t n, int n_cfg, double scale, double* out) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = acc[i] * scale;
+  if (i < n) {
+    double s = 0.0;
+    for (int c = 0; c < n_cfg; ++c) s += acc[static_cast<size_t>(c) * n + i];
+    out[i] = s * scale;
+  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -742,22 +811,45 @@ cudaError_t launch_potential(const PotArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_slice(const SliceArgs& a, bool even_origins, bool half, cudaStream_t s) {
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      n = v;
+    else
+      return 1;
+  }
+  return n;
+}
+
+cudaError_t launch_slice(const SliceLaunch& a, bool even_origins, bool half, int mode, cudaStream_t s) {
   if (a.n_list <= 0) return cudaSuccess;
+  if (a.n_jobs < 1 || a.n_jobs > kMaxJobs || a.start[0] != 0 || a.start[a.n_jobs] != a.n_list)
+    return cudaErrorInvalidValue;
+  if (mode == kSliceDynamic && !a.counter) return cudaErrorInvalidValue;
   const size_t sm = slice_smem_bytes();
-  if (even_origins && !half) k_slice<true, false><<<a.n_list, kThreads, sm, s>>>(a);
-  if (!even_origins && !half) k_slice<false, false><<<a.n_list, kThreads, sm, s>>>(a);
-  if (even_origins && half) k_slice<true, true><<<a.n_list, kThreads, sm, s>>>(a);
-  if (!even_origins && half) k_slice<false, true><<<a.n_list, kThreads, sm, s>>>(a);
+  // one CTA per SM fits (216 KiB of shared memory): persistent grids are one wave
+  const int grid = mode == kSliceOnePerItem ? a.n_list : (a.n_list < sm_count() ? a.n_list : sm_count());
+  if (mode == kSliceDynamic) {
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+  }
+  if (even_origins && !half) k_slice<true, false><<<grid, kThreads, sm, s>>>(a, mode);
+  if (!even_origins && !half) k_slice<false, false><<<grid, kThreads, sm, s>>>(a, mode);
+  if (even_origins && half) k_slice<true, true><<<grid, kThreads, sm, s>>>(a, mode);
+  if (!even_origins && half) k_slice<false, true><<<grid, kThreads, sm, s>>>(a, mode);
   return cudaGetLastError();
 }
 
 cudaError_t launch_synth(const SynthArgs& a, bool half, cudaStream_t s) {
   if (a.n_probes <= 0) return cudaSuccess;
+  const int grid = a.n_probes * a.n_cfg;
   if (half)
-    k_synth_detect<true><<<a.n_probes, kThreads, synth_smem_bytes(), s>>>(a);
+    k_synth_detect<true><<<grid, kThreads, synth_smem_bytes(), s>>>(a);
   else
-    k_synth_detect<false><<<a.n_probes, kThreads, synth_smem_bytes(), s>>>(a);
+    k_synth_detect<false><<<grid, kThreads, synth_smem_bytes(), s>>>(a);
   return cudaGetLastError();
 }
 
@@ -766,10 +858,11 @@ cudaError_t launch_expand_half(const void* src, float scale, float2* dst, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const double* acc, int64_t n, double scale, double* out, cudaStream_t s) {
+cudaError_t launch_finalize(const double* acc, int64_t n, int n_cfg, double scale, double* out,
+                            cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int blocks = static_cast<int>((n + 255) / 256);
-  k_finalize<<<blocks, 256, 0, s>>>(acc, n, scale, out);
+  k_finalize<<<blocks, 256, 0, s>>>(acc, n, n_cfg, scale, out);
   return cudaGetLastError();
 }
 

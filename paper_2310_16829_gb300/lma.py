@@ -35,6 +35,13 @@ LMA_PREC_MIXED = 1
 LMA_EDIT_REMOVE = 0
 LMA_EDIT_SET_SPECIES = 1
 LMA_IMAGE_RECOMPUTE = 1
+LMA_IMAGE_GRAPH = 2
+LMA_IMAGE_AUTOTUNE = 4
+LMA_SLICE_AUTO = -1
+LMA_SLICE_ONE_PER_ITEM = 0
+LMA_SLICE_PERSISTENT = 1
+LMA_SLICE_DYNAMIC = 2
+SLICE_MODE_NAMES = {0: "one_per_item", 1: "persistent", 2: "dynamic"}
 
 # every symbol include/lma.h declares (checked by the CPU tests)
 EXPORTS = [
@@ -42,8 +49,9 @@ EXPORTS = [
     "lma_create_specimen", "lma_free_specimen", "lma_specimen_set_atoms", "lma_transmission",
     "lma_create_basis", "lma_free_basis", "lma_basis_get_info", "lma_basis_coefficients",
     "lma_propagate_basis", "lma_exit_wave",
-    "lma_image", "lma_edit_column", "lma_affected_probes",
+    "lma_image", "lma_image_many", "lma_edit_column", "lma_affected_probes",
     "lma_profile_enable", "lma_profile_read", "lma_readout_noalloc",
+    "lma_set_slice_mode", "lma_tuning_read",
 ]
 
 
@@ -71,7 +79,8 @@ class Probe(C.Structure):
 class BasisDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("gauss_sigma", C.c_double), ("in_spacing_px", C.c_int32 * 2),
                 ("in_offset_px", C.c_int32 * 2), ("f", C.c_int32), ("L", C.c_int32),
-                ("window", C.c_int32), ("det_window", C.c_int32), ("precision", C.c_int32)]
+                ("window", C.c_int32), ("det_window", C.c_int32), ("precision", C.c_int32),
+                ("phonon_batch", C.c_int32)]
 
 
 class Detector(C.Structure):
@@ -87,7 +96,7 @@ class BasisInfo(C.Structure):
     _fields_ = [("n_translates", C.c_int64), ("nax", C.c_int32), ("nay", C.c_int32),
                 ("n_sets", C.c_int32), ("L", C.c_int32), ("window", C.c_int32),
                 ("det_window", C.c_int32), ("gauss_sigma", C.c_double),
-                ("exit_wave_bytes", C.c_int64)]
+                ("exit_wave_bytes", C.c_int64), ("phonon_batch", C.c_int32)]
 
 
 class KernelStat(C.Structure):
@@ -101,6 +110,17 @@ class Profile(C.Structure):
     def as_dict(self):
         return {k: {"launches": int(getattr(self, k).launches), "total_ms": float(getattr(self, k).total_ms),
                     "units": int(getattr(self, k).units)} for k, _ in self._fields_}
+
+
+class Tuning(C.Structure):
+    _fields_ = [("n_jobs", C.c_int32), ("half", C.c_int32), ("even", C.c_int32), ("n_items", C.c_int64),
+                ("translate_slices", C.c_int64), ("mode", C.c_int32), ("ms", C.c_double * 3)]
+
+    def as_dict(self):
+        return {"n_jobs": int(self.n_jobs), "half": bool(self.half), "even": bool(self.even),
+                "n_items": int(self.n_items), "translate_slices": int(self.translate_slices),
+                "mode": SLICE_MODE_NAMES.get(int(self.mode), int(self.mode)),
+                "ms": {SLICE_MODE_NAMES[m]: float(self.ms[m]) for m in range(3)}}
 
 
 class LmaError(RuntimeError):
@@ -129,11 +149,15 @@ _SIGS = {
     "lma_exit_wave": (C.c_int32, [_VP, _VP, C.c_int64, _VP, _VP]),
     "lma_image": (C.c_int32, [_VP, _VP, _VP, C.POINTER(Detector), C.c_int32, C.POINTER(Region),
                               C.c_uint32, _VP, _VP]),
+    "lma_image_many": (C.c_int32, [_VP, C.c_int32, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(Detector),
+                                   C.c_int32, C.POINTER(Region), C.c_uint32, C.POINTER(_VP), _VP]),
     "lma_edit_column": (C.c_int32, [_VP, _VP, _VP, C.c_double, C.c_double, C.c_double, C.c_int32,
                                     C.c_int16, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "lma_affected_probes": (C.c_int32, [_VP, _VP, C.POINTER(Region), _VP, C.POINTER(C.c_int64)]),
     "lma_readout_noalloc": (C.c_int32, [_VP, _VP, _VP, C.POINTER(Detector), C.c_int32, C.POINTER(Region),
                                         _VP, _VP]),
+    "lma_set_slice_mode": (C.c_int32, [_VP, C.c_int32]),
+    "lma_tuning_read": (C.c_int32, [_VP, C.POINTER(Tuning), C.c_int32, C.POINTER(C.c_int32)]),
 }
 
 _LIB: Optional[C.CDLL] = None
@@ -202,6 +226,16 @@ class Context:
         p = Profile()
         self.check(self.lib.lma_profile_read(self.h, C.byref(p)))
         return p.as_dict()
+
+    def set_slice_mode(self, mode: int) -> None:
+        self.check(self.lib.lma_set_slice_mode(self.h, mode))
+
+    def tuning(self) -> list:
+        n = C.c_int32()
+        self.check(self.lib.lma_tuning_read(self.h, None, 0, C.byref(n)))
+        recs = (Tuning * max(1, n.value))()
+        self.check(self.lib.lma_tuning_read(self.h, recs, n.value, C.byref(n)))
+        return [recs[i].as_dict() for i in range(n.value)]
 
     def close(self) -> None:
         if self.h:
@@ -305,7 +339,8 @@ class Basis:
         pr = Probe(probe.alpha_max, probe.cs, probe.defocus)
         d = BasisDesc(desc.kind, desc.gauss_sigma, (C.c_int32 * 2)(*desc.in_spacing_px),
                       (C.c_int32 * 2)(*desc.in_offset_px), desc.f, desc.L, desc.window,
-                      desc.det_window, getattr(desc, "precision", LMA_PREC_C64))
+                      desc.det_window, getattr(desc, "precision", LMA_PREC_C64),
+                      getattr(desc, "phonon_batch", 0))
         h = _VP()
         ctx.check(ctx.lib.lma_create_basis(ctx.h, spec.h, C.byref(pr), C.byref(d), C.byref(h)))
         self.h = h
@@ -338,12 +373,13 @@ class Basis:
                                                   _stream(stream)))
         return out
 
-    def image(self, detectors, region, out=None, recompute: bool = False, stream=None):
+    def image(self, detectors, region, out=None, recompute: bool = False, stream=None,
+              autotune: bool = False):
         dets = (Detector * len(detectors))(*[Detector(d.r1, d.r2) for d in detectors])
         if out is None:
             out = np.empty((len(detectors), region.npy, region.npx), dtype=np.float64)
         reg = _region(region)
-        flags = LMA_IMAGE_RECOMPUTE if recompute else 0
+        flags = (LMA_IMAGE_RECOMPUTE if recompute else 0) | (LMA_IMAGE_AUTOTUNE if autotune else 0)
         self.ctx.check(self.ctx.lib.lma_image(self.ctx.h, self.spec.h, self.h, dets, len(detectors),
                                               C.byref(reg), flags, _ptr(out), _stream(stream)))
         return out
@@ -379,3 +415,20 @@ class Basis:
             self.close()
         except Exception:
             pass
+
+
+def image_many(ctx: Context, bases, detectors, regions, outs, recompute: bool = True,
+               graph: bool = False, stream=None, autotune: bool = False):
+    """lma_image_many over several (specimen, basis) pairs; ``outs`` are per-basis buffers
+    [n_det][npy][npx] float64 (device tensors when ``graph``)."""
+    n = len(bases)
+    specs = (_VP * n)(*[b.spec.h.value for b in bases])
+    hs = (_VP * n)(*[b.h.value for b in bases])
+    dets = (Detector * len(detectors))(*[Detector(d.r1, d.r2) for d in detectors])
+    regs = (Region * n)(*[_region(r) for r in regions])
+    ptrs = (_VP * n)(*[_ptr(o) for o in outs])
+    flags = ((LMA_IMAGE_RECOMPUTE if recompute else 0) | (LMA_IMAGE_GRAPH if graph else 0) |
+             (LMA_IMAGE_AUTOTUNE if autotune else 0))
+    ctx.check(ctx.lib.lma_image_many(ctx.h, n, specs, hs, dets, len(detectors), regs, flags, ptrs,
+                                     _stream(stream)))
+    return outs

@@ -98,6 +98,7 @@ class BasisDesc:
     window: int = 128
     det_window: int = 128
     precision: int = PREC_C64
+    phonon_batch: int = 0                    # configurations per launch; 0 = by free memory
 
 
 @dataclass
