@@ -80,6 +80,8 @@ struct SynthArgs {
   const int2* shift;           // [n_probes][L] placement of U in the probe window
   int L;
   int n_probes;
+  int npx, npy;                // region shape: probe p = b * npx + a
+  int strip;                   // probes are visited in vertical strips of this many columns
   int n_cfg;                   // configurations in this launch (store slots 0..n_cfg-1)
   int cfg_base;                // index of slot 0's configuration in the accumulator
   int n_translates;            // |I_f| (stride of the per-wave factors between slots)

@@ -30,6 +30,9 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kW = lma_dev::kW;
 constexpr int kMaxL = 64;
+// probe strip width of the synthesis walk: 32 probe columns keep the exit waves that the
+// CTAs in flight read (about (32 + 6) x 11 translates at 4-pixel spacing) well inside L2
+constexpr int kSynthStrip = 32;
 
 }  // namespace
 
@@ -60,6 +63,7 @@ struct lma_ctx {
   std::vector<List> lists;
   std::vector<std::pair<void*, uint64_t>> capture_lists;   // lists read by the capture in progress
   int* d_counter = nullptr;                                 // work counter of dynamic slice launches
+  void* stage = nullptr;                                    // pinned staging buffer (kStageBytes)
   // slice launch modes: forced (>= 0), or the timed choice per launch shape
   int forced_mode = -1;
   bool autotune = false;
@@ -215,6 +219,66 @@ cudaError_t ensure(DevBuf& b, size_t bytes) {
 struct Rect {
   int x0, y0, w, h;   // periodic pixel rectangle
 };
+
+// Host <-> device copies through the context's pinned staging buffer. A pageable copy
+// is staged by the driver through a buffer shared by the whole process, so one
+// thread's pageable read-back of a long stream holds up every other thread's
+// pageable uploads (an edit waited for a full image). Each chunk is synchronized on
+// the stream before the buffer is reused, and the buffer is free when a call returns.
+constexpr size_t kStageBytes = size_t(8) << 20;
+
+struct HostPart {
+  void* dst;
+  const void* src;
+  size_t bytes;
+};
+
+cudaError_t ensure_stage(lma_ctx* ctx) {
+  if (ctx->stage) return cudaSuccess;
+  return cudaMallocHost(&ctx->stage, kStageBytes);
+}
+
+// several host -> device copies, packed into the staging buffer
+cudaError_t upload_parts(lma_ctx* ctx, std::initializer_list<HostPart> parts, cudaStream_t st) {
+  cudaError_t e = ensure_stage(ctx);
+  if (e != cudaSuccess) return e;
+  char* stage = static_cast<char*>(ctx->stage);
+  size_t used = 0;
+  for (const HostPart& p : parts) {
+    for (size_t off = 0; off < p.bytes;) {
+      if (used == kStageBytes) {
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+        used = 0;
+      }
+      const size_t n = std::min(kStageBytes - used, p.bytes - off);
+      std::memcpy(stage + used, static_cast<const char*>(p.src) + off, n);
+      e = cudaMemcpyAsync(static_cast<char*>(p.dst) + off, stage + used, n, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return e;
+      used += n;
+      off += n;
+    }
+  }
+  return cudaStreamSynchronize(st);
+}
+
+cudaError_t upload(lma_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  return upload_parts(ctx, {HostPart{dst, src, bytes}}, st);
+}
+
+// device -> host through the staging buffer; returns when dst holds the data
+cudaError_t download(lma_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  cudaError_t e = ensure_stage(ctx);
+  if (e != cudaSuccess) return e;
+  for (size_t off = 0; off < bytes; off += kStageBytes) {
+    const size_t n = std::min(kStageBytes, bytes - off);
+    if ((e = cudaMemcpyAsync(ctx->stage, static_cast<const char*>(src) + off, n, cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    std::memcpy(static_cast<char*>(dst) + off, ctx->stage, n);
+  }
+  return cudaSuccess;
+}
 
 cudaEvent_t pool_event(lma_ctx* ctx) {
   if (!ctx->pool.empty()) {
@@ -515,10 +579,10 @@ lma_status ensure_basis_device(lma_basis* b, cudaStream_t st) {
   CUDA_TRY(ctx, ensure(b->d_uW, uw.size() * sizeof(float)));
   CUDA_TRY(ctx, ensure(b->d_ex, b->ex.size() * sizeof(float)));
   CUDA_TRY(ctx, ensure(b->d_ey, b->ey.size() * sizeof(float)));
-  CUDA_TRY(ctx, cudaMemcpyAsync(b->d_uW.p, uw.data(), uw.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(ctx, cudaMemcpyAsync(b->d_ex.p, b->ex.data(), b->ex.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(ctx, cudaMemcpyAsync(b->d_ey.p, b->ey.data(), b->ey.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  CUDA_TRY(ctx, upload_parts(ctx, {HostPart{b->d_uW.p, uw.data(), uw.size() * sizeof(float)},
+                                    HostPart{b->d_ex.p, b->ex.data(), b->ex.size() * sizeof(float)},
+                                    HostPart{b->d_ey.p, b->ey.data(), b->ey.size() * sizeof(float)}},
+                             st));
   // phonon batch: configurations whose exit waves (and transmissions) are held at once
   const bool half = b->desc.precision == LMA_PREC_MIXED;
   const int nph = static_cast<int>(b->spec->ph.size());
@@ -551,15 +615,11 @@ lma_status ensure_atoms_device(lma_specimen* sp, int phi, cudaStream_t st) {
   CUDA_TRY(ctx, ensure(p.dy, n * sizeof(double)));
   CUDA_TRY(ctx, ensure(p.dsp, n * sizeof(int16_t)));
   CUDA_TRY(ctx, ensure(p.dss, p.slice_start.size() * sizeof(int32_t)));
-  if (!p.x.empty()) {
-    CUDA_TRY(ctx, cudaMemcpyAsync(p.dx.p, p.x.data(), p.x.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(ctx, cudaMemcpyAsync(p.dy.p, p.y.data(), p.y.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(ctx, cudaMemcpyAsync(p.dsp.p, p.sp.data(), p.sp.size() * sizeof(int16_t), cudaMemcpyHostToDevice, st));
-  }
-  CUDA_TRY(ctx, cudaMemcpyAsync(p.dss.p, p.slice_start.data(), p.slice_start.size() * sizeof(int32_t),
-                                cudaMemcpyHostToDevice, st));
-  // pageable sources: make sure the host vectors may change after return
-  CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  CUDA_TRY(ctx, upload_parts(ctx, {HostPart{p.dx.p, p.x.data(), p.x.size() * sizeof(double)},
+                                    HostPart{p.dy.p, p.y.data(), p.y.size() * sizeof(double)},
+                                    HostPart{p.dsp.p, p.sp.data(), p.sp.size() * sizeof(int16_t)},
+                                    HostPart{p.dss.p, p.slice_start.data(), p.slice_start.size() * sizeof(int32_t)}},
+                             st));
   p.dirty = false;
   return LMA_OK;
 }
@@ -632,7 +692,7 @@ lma_status ensure_t(lma_specimen* sp, int slot, int phi, bool force, cudaStream_
   if (!sp->d_peak.p) {
     std::vector<float> pk(sp->peak.begin(), sp->peak.end());
     CUDA_TRY(ctx, ensure(sp->d_peak, pk.size() * sizeof(float)));
-    CUDA_TRY(ctx, cudaMemcpy(sp->d_peak.p, pk.data(), pk.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(ctx, upload(ctx, sp->d_peak.p, pk.data(), pk.size() * sizeof(float), st));
   }
   s = ensure_atoms_device(sp, phi, st);
   if (s != LMA_OK) return s;
@@ -692,8 +752,7 @@ lma_status upload_list(lma_ctx* ctx, const std::vector<int32_t>& list, cudaStrea
     CUDA_TRY(ctx, cudaMalloc(&e.p, cap));
     e.bytes = cap;
   }
-  CUDA_TRY(ctx, cudaMemcpyAsync(e.p, list.data(), bytes, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(ctx, cudaStreamSynchronize(st));   // pageable source
+  CUDA_TRY(ctx, upload(ctx, e.p, list.data(), bytes, st));
   e.items = list;
   e.hash = h;
   *out = static_cast<const int32_t*>(e.p);
@@ -907,10 +966,10 @@ lma_status build_region(lma_basis* b, const lma_region* r, cudaStream_t st) {
   CUDA_TRY(ctx, ensure(R.tidx, tidx.size() * sizeof(int32_t)));
   CUDA_TRY(ctx, ensure(R.alpha, al.size() * sizeof(float)));
   CUDA_TRY(ctx, ensure(R.shift, sh.size() * sizeof(int32_t)));
-  CUDA_TRY(ctx, cudaMemcpyAsync(R.tidx.p, tidx.data(), tidx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(ctx, cudaMemcpyAsync(R.alpha.p, al.data(), al.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(ctx, cudaMemcpyAsync(R.shift.p, sh.data(), sh.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  CUDA_TRY(ctx, upload_parts(ctx, {HostPart{R.tidx.p, tidx.data(), tidx.size() * sizeof(int32_t)},
+                                    HostPart{R.alpha.p, al.data(), al.size() * sizeof(float)},
+                                    HostPart{R.shift.p, sh.data(), sh.size() * sizeof(int32_t)}},
+                             st));
   R.r = *r;
   R.n_probes = np;
   R.h_tidx.swap(tidx);
@@ -948,8 +1007,7 @@ lma_status build_detectors(lma_basis* b, const lma_detector* det, int n_det, cud
     }
   }
   CUDA_TRY(ctx, ensure(b->d_det, bits.size() * sizeof(uint32_t)));
-  CUDA_TRY(ctx, cudaMemcpyAsync(b->d_det.p, bits.data(), bits.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  CUDA_TRY(ctx, upload(ctx, b->d_det.p, bits.data(), bits.size() * sizeof(uint32_t), st));
   b->det_key = key;
   return LMA_OK;
 }
@@ -961,6 +1019,17 @@ bool is_device_pointer(const void* p) {
     return false;
   }
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// device -> host result copy: straight into pinned memory, else through the staging buffer
+cudaError_t read_back(lma_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, dst) == cudaSuccess && at.type == cudaMemoryTypeHost) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st);
+    return e != cudaSuccess ? e : cudaStreamSynchronize(st);
+  }
+  cudaGetLastError();
+  return download(ctx, dst, src, bytes, st);
 }
 
 }  // namespace
@@ -1019,6 +1088,9 @@ lma_status images_work(lma_ctx* ctx, const std::vector<ImageJob>& jobs, int n_de
       a.shift = static_cast<const int2*>(b->reg.shift.p);
       a.L = b->desc.L;
       a.n_probes = static_cast<int>(np);
+      a.npx = b->reg.r.npx;
+      a.npy = b->reg.r.npy;
+      a.strip = kSynthStrip;
       a.n_cfg = nb;
       a.cfg_base = batch[k].first;
       a.n_translates = static_cast<int>(b->nT);
@@ -1139,6 +1211,7 @@ void lma_destroy(lma_ctx* ctx) {
   for (auto& l : ctx->lists)
     if (l.p) cudaFree(l.p);
   if (ctx->d_counter) cudaFree(ctx->d_counter);
+  if (ctx->stage) cudaFreeHost(ctx->stage);
   delete ctx;
 }
 
@@ -1416,8 +1489,7 @@ lma_status lma_image(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, const lma_det
   if (!dev_out) {
     const int64_t nout = b->reg.n_probes * n_det;
     const double* fin = static_cast<const double*>(b->d_acc.p) + static_cast<size_t>(sp->ph.size()) * nout;
-    CUDA_TRY(ctx, cudaMemcpyAsync(out, fin, static_cast<size_t>(nout) * sizeof(double), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    CUDA_TRY(ctx, read_back(ctx, out, fin, static_cast<size_t>(nout) * sizeof(double), st));
   }
   CUDA_TRY(ctx, cudaGetLastError());
   return LMA_OK;
@@ -1465,8 +1537,7 @@ lma_status lma_image_many(lma_ctx* ctx, int32_t n, lma_specimen* const* specs, l
       if (!dev_out[k]) {
         const int64_t nout = bases[k]->reg.n_probes * n_det;
         const double* fin = static_cast<const double*>(bases[k]->d_acc.p) + specs[k]->ph.size() * nout;
-        CUDA_TRY(ctx, cudaMemcpyAsync(outs[k], fin, static_cast<size_t>(nout) * sizeof(double),
-                                      cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(ctx, read_back(ctx, outs[k], fin, static_cast<size_t>(nout) * sizeof(double), st));
       }
     CUDA_TRY(ctx, cudaStreamSynchronize(st));
     return LMA_OK;
@@ -1745,6 +1816,9 @@ lma_status lma_readout_noalloc(lma_ctx* ctx, lma_basis* b, const float* exit_wav
   a.shift = reinterpret_cast<const int2*>(base + o_shift);
   a.L = L;
   a.n_probes = static_cast<int>(np);
+  a.npx = region->npx;
+  a.npy = region->npy;
+  a.strip = kSynthStrip;
   a.n_cfg = 1;
   a.cfg_base = 0;
   a.n_translates = static_cast<int>(b->nT);

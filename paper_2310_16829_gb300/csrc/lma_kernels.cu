@@ -110,6 +110,24 @@ __device__ __forceinline__ void bfly(float2 (&t)[32]) {
     const float2 wb = INV ? make_float2(-b.y, b.x) : make_float2(b.y, -b.x);
     t[I] = cadd(a, wb);
     t[I + H] = csub(a, wb);
+  } else if constexpr (M == 4 || M == 12) {
+    // w = (c, s) with |c| = |s| = r = 1/sqrt(2): w b = (c b.x - s b.y, c b.y + s b.x) is
+    // r times a sum or difference of b.x and b.y, so X and Y take one add and one FMA
+    // per component (two roundings, as for a general twiddle)
+    const float r = c_w128[16].x;                       // cos(pi / 4), rounded once
+    constexpr int sc = M == 4 ? 1 : -1;                 // sign of c
+    constexpr int ss = INV ? 1 : -1;                    // sign of s: -r forward, +r inverse
+    float u, v;                                         // w b = sc r (u, v)
+    if constexpr (sc == ss) {
+      u = b.x - b.y;
+      v = b.y + b.x;
+    } else {
+      u = b.x + b.y;
+      v = b.y - b.x;
+    }
+    const float rs = sc > 0 ? r : -r;
+    t[I] = make_float2(fmaf(rs, u, a.x), fmaf(rs, v, a.y));
+    t[I + H] = make_float2(fmaf(-rs, u, a.x), fmaf(-rs, v, a.y));
   } else {
     const float2 w = c_w128[4 * M];
     const float wy = INV ? -w.y : w.y;
@@ -509,6 +527,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
 // ------------------------------------------------------------------------------------------
 constexpr int kSynthSmemFloat2 = kX1 + kTwA + 128 + (kThreads / 32) * kMaxDet;
 
+// Probe of visit index q: the region is walked in vertical strips of sw columns (the
+// last strip narrower), row by row within a strip. The CTAs in flight then read the
+// exit waves of a compact patch of translates, which stays in L2 while the strip moves
+// down; a raster walk over whole rows needs about seven 128-translate rows at once.
+__device__ __forceinline__ int probe_of(int q, int npx, int npy, int sw) {
+  const int per = npy * sw;
+  const int s = q / per;
+  const int x0 = s * sw;
+  const int w = min(sw, npx - x0);
+  const int r = q - s * per;
+  return (r / w) * npx + x0 + (r - (r / w) * w);
+}
+
 // HALF reads the FP16 store and folds each wave's factor into its coefficient.
 template <bool HALF>
 __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a) {
@@ -543,7 +574,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
   const int n_items = a.n_probes * a.n_cfg;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
     const int cfg = item / a.n_probes;
-    const int p = item - cfg * a.n_probes;
+    const int p = probe_of(item - cfg * a.n_probes, a.npx, a.npy, a.strip);
     const float2* const Uc = a.U ? a.U + cfg * a.u_slot : nullptr;
     const void* const Uhc = a.Uh ? static_cast<const void*>(static_cast<const __half2*>(a.Uh) + cfg * a.u_slot) : nullptr;
     const float* const Usc = a.Uscale ? a.Uscale + static_cast<size_t>(cfg) * a.n_translates : nullptr;

@@ -18,6 +18,12 @@ measured device footprint: exit waves, transmission, tables). A blocked lane doe
 hold back the others. Results are bitwise independent of the mix: kernels are
 deterministic and lanes share nothing.
 
+Warm pool. A lane may ask for ``min_instances`` instances that the server brings up
+and warms (one request's worth of device allocation and work) before it admits any
+request. Device allocation can synchronize the whole device, so an instance created
+while other lanes' kernels are in flight would stall every lane once; with a warm pool
+that only happens when load grows past the pool.
+
 This module holds host logic only; every computation runs in the CUDA library.
 """
 from __future__ import annotations
@@ -84,18 +90,27 @@ class Ticket:
 class Instance:
     """A worker: thread + context + stream + resources of one lane."""
 
-    def __init__(self, lane: "Lane", index: int, reserve_bytes: int):
+    def __init__(self, lane: "Lane", index: int, reserve_bytes: int, warm: bool = False):
         self.lane = lane
         self.index = index
         self.reserve_bytes = reserve_bytes
         self.busy = False
         self.jobs: "queue.Queue" = queue.Queue()
         self.state = None
+        self.warm = warm
+        self.ready = threading.Event()
+        self.error: Optional[BaseException] = None
         self.thread = threading.Thread(target=self._run, daemon=True)
         self.thread.start()
 
     def _run(self):
-        self.state = self.lane.make_state()
+        try:
+            self.state = self.lane.make_state()
+            if self.warm and self.lane.warm is not None:
+                self.lane.warm(self.state)
+        except BaseException as e:   # reported by Server.__init__
+            self.error = e
+        self.ready.set()
         while True:
             job = self.jobs.get()
             if job is None:
@@ -116,20 +131,23 @@ class Lane:
     """A request class: how to build an instance's state and how to serve a request."""
 
     def __init__(self, name: str, make_state: Callable, handle: Callable, close_state: Callable,
-                 reserve_bytes: int, max_instances: int = 1 << 30):
+                 reserve_bytes: int, max_instances: int = 1 << 30, min_instances: int = 0,
+                 warm: Optional[Callable] = None):
         self.name = name
         self.make_state = make_state
         self.handle = handle
         self.close_state = close_state
         self.reserve_bytes = reserve_bytes
         self.max_instances = max_instances
+        self.min_instances = min(min_instances, max_instances)
+        self.warm = warm
         self.instances: List[Instance] = []
 
 
 class Server:
     """Continuous batching: admission by idle instance or HBM budget, per-lane FIFO."""
 
-    def __init__(self, lanes: List[Lane], budget_bytes: int):
+    def __init__(self, lanes: List[Lane], budget_bytes: int, warm_timeout: float = 600.0):
         self.lanes: Dict[str, Lane] = {l.name: l for l in lanes}
         self.budget = budget_bytes
         self.reserved = 0
@@ -137,6 +155,18 @@ class Server:
         self.cv = threading.Condition()
         self.closed = False
         self.admissions: List[tuple] = []          # (time, lane, instance, queued behind)
+        # warm pool: brought up before any request is admitted, within the budget
+        for lane in lanes:
+            while (len(lane.instances) < lane.min_instances and
+                   self.reserved + lane.reserve_bytes <= self.budget):
+                lane.instances.append(Instance(lane, len(lane.instances), lane.reserve_bytes, warm=True))
+                self.reserved += lane.reserve_bytes
+        for lane in lanes:
+            for inst in lane.instances:
+                if not inst.ready.wait(warm_timeout):
+                    raise TimeoutError(f"lane {lane.name}: instance {inst.index} not ready")
+                if inst.error is not None:
+                    raise inst.error
         self.dispatcher = threading.Thread(target=self._dispatch, daemon=True)
         self.dispatcher.start()
 
@@ -211,7 +241,7 @@ def _stream(priority: int = 0):
     return torch.cuda.Stream(priority=priority)
 
 
-def edit_lane(workload, device: int = 0, max_instances: int = 1) -> Lane:
+def edit_lane(workload, device: int = 0, max_instances: int = 1, min_instances: int = 0) -> Lane:
     """Resident specimen: all exit waves propagated once, edits re-propagate locally."""
     from . import lma
 
@@ -244,11 +274,12 @@ def edit_lane(workload, device: int = 0, max_instances: int = 1) -> Lane:
         s["ctx"].close()
 
     reserve = _footprint(workload)
-    return Lane("edit", make, handle, close, reserve, max_instances)
+    # make() already propagates every exit wave and images the region: no extra warm-up
+    return Lane("edit", make, handle, close, reserve, max_instances, min_instances, warm=lambda s: None)
 
 
 def image_lane(name: str, build: Callable[[int], object], device: int = 0,
-               max_instances: int = 4) -> Lane:
+               max_instances: int = 4, min_instances: int = 0) -> Lane:
     """Fresh specimens of one size: each request uploads its own seeded atoms
     (lma_specimen_set_atoms) and computes the full image from scratch."""
     from . import lma
@@ -271,7 +302,11 @@ def image_lane(name: str, build: Callable[[int], object], device: int = 0,
         s["spec"].close()
         s["ctx"].close()
 
-    return Lane(name, make, handle, close, _footprint(proto), max_instances)
+    def warm(s):
+        handle(s, ImageRequest(name, seed=0))
+        s["stream"].synchronize()
+
+    return Lane(name, make, handle, close, _footprint(proto), max_instances, min_instances, warm)
 
 
 def _footprint(w) -> int:

@@ -152,24 +152,25 @@ def _layered_crystal(a: float, ncx: int, ncy: int, n_slices: int,
     lateral displacement of standard deviation ``rms`` (Angstrom) is drawn
     independently for x and y of every atom when ``seed`` is given.
     """
+    # atom order: slice, layer entry, row j, column i (i fastest)
+    ii = np.tile(np.arange(ncx, dtype=np.float64), ncy)
+    jj = np.repeat(np.arange(ncy, dtype=np.float64), ncx)
     xs, ys, ss, sp = [], [], [], []
     for s in range(n_slices):
         for (fx, fy, spc) in layers[s % len(layers)]:
-            for j in range(ncy):
-                for i in range(ncx):
-                    xs.append((i + fx) * a)
-                    ys.append((j + fy) * a)
-                    ss.append(s)
-                    sp.append(spc)
-    x = np.asarray(xs, dtype=np.float64)
-    y = np.asarray(ys, dtype=np.float64)
+            xs.append((ii + fx) * a)
+            ys.append((jj + fy) * a)
+            ss.append(np.full(ii.shape, s, dtype=np.int32))
+            sp.append(np.full(ii.shape, spc, dtype=np.int16))
+    x = np.concatenate(xs) if xs else np.zeros(0)
+    y = np.concatenate(ys) if ys else np.zeros(0)
     if seed is not None and rms > 0.0:
         rng = np.random.default_rng(seed)
         d = rng.normal(0.0, rms, size=(2, x.shape[0]))
         x = x + d[0]
         y = y + d[1]
-    return Atoms(x=x, y=y, slice=np.asarray(ss, dtype=np.int32),
-                 species=np.asarray(sp, dtype=np.int16))
+    return Atoms(x=x, y=y, slice=np.concatenate(ss) if ss else np.zeros(0, np.int32),
+                 species=np.concatenate(sp) if sp else np.zeros(0, np.int16))
 
 
 # ABO3 perovskite projected along [001]: AO and BO2 layers alternate.

@@ -97,3 +97,30 @@ def test_poisson_arrivals_are_seeded():
     a = S.poisson_arrivals(100, 10.0, 4)
     assert np.array_equal(a, S.poisson_arrivals(100, 10.0, 4))
     assert abs(np.mean(np.diff(a)) - 0.1) < 0.03 and np.all(np.diff(a) > 0)
+
+
+def test_warm_pool_is_ready_before_admission_and_within_budget():
+    warmed = []
+    a = fake_lane("a", reserve=10, max_instances=4)
+    a.min_instances = 3
+    a.warm = lambda state: warmed.append(time.perf_counter())
+    srv = S.Server([a], budget_bytes=25)            # the budget admits two of the three
+    t0 = time.perf_counter()
+    assert len(a.instances) == 2 and len(warmed) == 2 and srv.reserved == 20
+    assert all(w < t0 for w in warmed)
+    res = [srv.submit(Req("a", k, dur=0.01)).wait(10) for k in range(4)]
+    srv.close()
+    assert [float(r.image[0, 0, 0]) for r in res] == [0.0, 1.0, 2.0, 3.0]
+    assert len(a.instances) == 2
+
+
+def test_warm_failure_is_reported_at_start():
+    a = fake_lane("a", reserve=1)
+    a.min_instances = 1
+
+    def bad_warm(state):
+        raise RuntimeError("warm-up failed")
+
+    a.warm = bad_warm
+    with pytest.raises(RuntimeError, match="warm-up failed"):
+        S.Server([a], budget_bytes=10)
