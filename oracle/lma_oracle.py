@@ -242,6 +242,29 @@ def detect(psi: np.ndarray, mask: np.ndarray) -> float:
     return float(np.sum(np.abs(spec[mask]) ** 2) / psi.size)
 
 
+def ring_masks(n: int, dy: float, dx: float, lam: float, width: float, n_rings: int,
+               frac: float | None) -> List[np.ndarray]:
+    """3D STEM detector (Sec. 3.1): ring a collects a*width <= lambda |k| < (a+1)*width,
+    a = 0..n_rings-1, each intersected with the bandlimit like the 2D detector."""
+    return [detector_mask(n, dy, dx, lam, a * width, (a + 1) * width, frac) for a in range(n_rings)]
+
+
+def pattern(psi: np.ndarray, A: int, B: int, frac: float | None) -> np.ndarray:
+    """4D STEM reading (Sec. 3.1): |DFT(psi)|^2 / n^2 at the frequencies (a, b) * (1/(n dx),
+    1/(n dy)) for a = -A..A, b = -B..B, shape (2B+1, 2A+1) indexed [b + B, a + A]; zero
+    outside the bandlimit. With a unit-norm wave the entries are fractions of the incident
+    intensity, and summing them over an annulus gives the 2D STEM reading."""
+    ny, nx = psi.shape
+    spec = np.abs(dft2(psi)) ** 2 / psi.size
+    if frac is not None:
+        spec = np.where(bandlimit_mask(ny, nx, frac), spec, 0.0)
+    out = np.zeros((2 * B + 1, 2 * A + 1), dtype=np.float64)
+    for b in range(-B, B + 1):
+        for a in range(-A, A + 1):
+            out[b + B, a + A] = spec[b % ny, a % nx]
+    return out
+
+
 # ----------------------------------------------------------------------------
 # LMA geometry (Sec. 4.2.1, 4.2.2)
 # ----------------------------------------------------------------------------
@@ -527,6 +550,31 @@ class LmaOracle:
         for phi in range(nphi):
             for k, pr in enumerate(probes):
                 out[:, k] += self.pixel(phi, (int(pr[0]), int(pr[1])), masks)
+        return out / nphi
+
+    def image_rings(self, width: float, n_rings: int, probes: np.ndarray) -> np.ndarray:
+        """3D STEM image (Sec. 3.1), shape (n_rings, n_probes): the 2D image with one ring
+        per detector, averaged over configurations."""
+        p = self.prm
+        masks = ring_masks(p.D, p.dy, p.dx, p.lam, width, n_rings, p.bandlimit_frac)
+        out = np.zeros((n_rings, probes.shape[0]), dtype=np.float64)
+        nphi = len(self._phonons)
+        for phi in range(nphi):
+            for k, pr in enumerate(probes):
+                out[:, k] += self.pixel(phi, (int(pr[0]), int(pr[1])), masks)
+        return out / nphi
+
+    def image_4d(self, A: int, B: int, probes: np.ndarray) -> np.ndarray:
+        """4D STEM image (Sec. 3.1), shape (n_probes, 2B+1, 2A+1): the diffraction pattern of
+        each synthesized exit wave on its D x D window, averaged over configurations."""
+        out = np.zeros((probes.shape[0], 2 * B + 1, 2 * A + 1), dtype=np.float64)
+        nphi = len(self._phonons)
+        for phi in range(nphi):
+            for k, pr in enumerate(probes):
+                cs, idx = self.coefficient_set((int(pr[0]), int(pr[1])))
+                U = [self.exit_wave(phi, int(i)) for i in idx]
+                psi = synthesize(U, cs.alpha, cs.offsets, self.prm.D, self.prm.cyclic)
+                out[k] += pattern(psi, A, B, self.prm.bandlimit_frac)
         return out / nphi
 
 

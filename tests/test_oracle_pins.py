@@ -257,6 +257,68 @@ def test_detector_over_all_frequencies_is_parseval():
     assert abs(O.detect(psi, np.ones((32, 32), bool)) / np.sum(np.abs(psi) ** 2) - 1) < 1e-13
 
 
+def _plane_wave(ny, nx, d, m0, n0):
+    """Unit-norm plane wave exp(2 pi i (m0 x / (nx d) + n0 y / (ny d))) on an ny x nx grid."""
+    y = np.arange(ny)[:, None] * d
+    x = np.arange(nx)[None, :] * d
+    return np.exp(2j * np.pi * (m0 * x / (nx * d) + n0 * y / (ny * d))) / math.sqrt(nx * ny)
+
+
+def test_rings_put_a_plane_wave_in_its_ring_only():
+    # 3D STEM of Sec. 3.1: consecutive rings of width r from 0
+    n, d, lam, width = 64, 0.1, 0.025, 0.004
+    m0, n0 = 5, -3
+    ang = lam * math.hypot(m0 / (n * d), n0 / (n * d))
+    pw = _plane_wave(n, n, d, m0, n0)
+    rings = O.ring_masks(n, d, d, lam, width, 30, 2 / 3)
+    reads = np.array([O.detect(pw, m) for m in rings])
+    a = int(ang // width)
+    assert abs(reads[a] - 1.0) < 1e-13
+    assert np.all(np.delete(reads, a) < 1e-25)
+
+
+def test_rings_add_up_to_the_annulus_they_tile():
+    rng = np.random.default_rng(3)
+    n, d, lam, width, nr = 64, 0.1, 0.025, 0.0037, 21
+    psi = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    total = sum(O.detect(psi, m) for m in O.ring_masks(n, d, d, lam, width, nr, 2 / 3))
+    annulus = O.detect(psi, O.detector_mask(n, d, d, lam, 0.0, nr * width, 2 / 3))
+    assert abs(total / annulus - 1) < 1e-12
+
+
+def test_pattern_of_a_plane_wave_is_a_unit_delta_at_its_frequency():
+    # non-square grid: a transposed axis or a sign slip moves the delta
+    ny, nx, d = 48, 64, 0.1
+    for m0, n0 in ((5, -3), (-7, 2)):
+        pw = _plane_wave(ny, nx, d, m0, n0)
+        for frac in (None, 2 / 3):
+            pat = O.pattern(pw, 10, 6, frac)
+            assert pat.shape == (13, 21)
+            assert abs(pat[n0 + 6, m0 + 10] - 1.0) < 1e-13
+            rest = pat.copy()
+            rest[n0 + 6, m0 + 10] = 0
+            assert np.all(rest < 1e-25)
+    # a wave outside the bandlimit leaves nothing in the pattern (rounding noise only)
+    pw = _plane_wave(64, 64, d, 30, 0)
+    pat = O.pattern(pw, 31, 31, 2 / 3)
+    assert pat[31, 61] == 0.0 and np.all(pat < 1e-25)
+    assert abs(O.pattern(pw, 31, 31, None)[31, 61] - 1.0) < 1e-13
+
+
+def test_pattern_summed_over_an_annulus_is_the_2d_reading():
+    rng = np.random.default_rng(5)
+    n, d, lam = 64, 0.1, 0.025
+    psi = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    A = n // 2 - 1
+    pat = O.pattern(psi, A, A, 2 / 3)
+    ia = np.arange(-A, A + 1)
+    k = np.hypot(ia[None, :] / (n * d), ia[:, None] / (n * d))
+    for r1, r2 in ((0.0, 0.02), (0.01, 0.05), (0.03, 0.07)):
+        sel = (lam * k >= r1) & (lam * k < r2)
+        ref = O.detect(psi, O.detector_mask(n, d, d, lam, r1, r2, 2 / 3))
+        assert abs(pat[sel].sum() / ref - 1) < 1e-12
+
+
 def test_bandlimit_mask_is_the_integer_two_thirds_circle():
     for n in (64, 128, 256):
         m = O.bandlimit_mask(n, n, 2 / 3)
@@ -442,6 +504,32 @@ def test_simple_cubic_image_has_crystal_period_and_4mm_symmetry():
     mirror = img[:, (-np.arange(16)) % 16]
     assert np.max(np.abs(img - mirror)) < tol
     assert np.ptp(img) > 1e3 * tol   # not trivially constant
+
+
+def test_3d_and_4d_images_agree_with_the_2d_image():
+    # the same synthesized exit waves read three ways: rings tiling an annulus add up to
+    # its 2D reading, and so does the 4D pattern summed over the annulus
+    prm = _small_params(L=32, n_slices=3, alpha_max=0.02)
+
+    class A:
+        pass
+    at = A()
+    at.x, at.y = np.array([0.0, 4.0, 0.0, 4.0]), np.array([0.0, 0.0, 4.0, 4.0])
+    at.slice, at.species = np.zeros(4, np.int32), np.zeros(4, np.int16)
+    orc = O.LmaOracle(prm)
+    orc.set_specimen([at], (300.0,), (0.7, 0.3), (0.15, 0.5), 3.0)
+    probes = np.array([[0, 0], [6, 2], [33, 17]])
+    width, nr = 0.005, 13
+    rings = orc.image_rings(width, nr, probes)
+    two_d = orc.image([_Det(0.02, 0.045), _Det(0.0, nr * width)], probes)
+    assert rel(rings[4:9].sum(axis=0), two_d[0]) < 1e-12
+    assert rel(rings.sum(axis=0), two_d[1]) < 1e-12
+    A4 = prm.D // 2 - 1
+    pat = orc.image_4d(A4, A4, probes)
+    ia = np.arange(-A4, A4 + 1)
+    ang = prm.lam * np.hypot(ia[None, :] / (prm.D * prm.dx), ia[:, None] / (prm.D * prm.dy))
+    sel = (ang >= 0.02) & (ang < 0.045)
+    assert rel(pat[:, sel].sum(axis=1), two_d[0]) < 1e-12
 
 
 def test_edit_column_removes_or_swaps_only_that_column():
