@@ -12,14 +12,20 @@ the same step through the public API with host buffers (new atom lists
 uploaded, image copied back) inside the timed region.
 
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
-workload (the reference arm of this build).
+workload (the reference arm).
 """
 from __future__ import annotations
+
+import os
+
+# Concurrent streams (the serving lanes) each need their own hardware work queue: with
+# fewer queues than streams, a stream's kernels can wait behind another stream's kernels
+# that share its queue. Set before CUDA initializes.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import argparse
 import dataclasses
 import json
-import os
 import statistics
 import subprocess
 import sys
@@ -310,7 +316,7 @@ def batching_measure(n_phonons: int, steps: int) -> dict:
       plain:   one lma_image per specimen, one configuration per slice and synthesis
                launch (phonon batch 1), one CTA per translate.
       batched: one lma_image_many call: configurations in phonon batches (as many as fit
-               in memory), the slice work of all specimens of a round in one launch (mode
+               in memory), the slice work of all specimens of a pass in one launch (mode
                chosen by the autotuner), the whole call replayed as one CUDA graph.
     Both run on one stream with device outputs and are timed with CUDA events; the
     outputs of the two forms are compared bitwise.
@@ -382,7 +388,7 @@ def batching_measure(n_phonons: int, steps: int) -> dict:
            "plain": {"ms": ms_plain, "pixels_per_s": pixels / (ms_plain / 1e3)},
            "batched": {"ms": ms_b, "pixels_per_s": pixels / (ms_b / 1e3),
                        "phonon_batch": [int(i.phonon_batch) for i in info],
-                       "rounds": int(max(-(-n_phonons // max(1, i.phonon_batch)) for i in info)),
+                       "passes": int(max(-(-n_phonons // max(1, i.phonon_batch)) for i in info)),
                        "first_call_s": first_s},
            "speedup": ms_plain / ms_b, "bitwise_equal": bool(same),
            "tuning": ctx.tuning()}
@@ -422,6 +428,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--edits", type=int, default=24, help="column-edit requests timed (0: skip)")
     ap.add_argument("--serving", type=int, default=60, help="requests per offered load (0: skip)")
+    ap.add_argument("--no-partition", dest="partition", action="store_false",
+                    help="skip the memory-bounded (partitioned) image measurement")
+    ap.add_argument("--no-stem34", dest="stem34", action="store_false",
+                    help="skip the 3D (rings) and 4D (pattern) STEM readout timings")
     ap.add_argument("--batch-phonons", type=int, default=4,
                     help="configurations per specimen of the uneven three-specimen batch (0: skip)")
     ap.add_argument("--profile-case", action="store_true",
@@ -536,6 +546,68 @@ def main():
     bm.close()
     del out_m
 
+    # ---- 3D and 4D STEM readouts of the same workload (Sec. 3.1): 20 rings of 5 mrad, and
+    # the diffraction pattern on the 85 x 85 frequencies of the bandlimit's bounding square
+    stem34 = None
+    if args.stem34 and rank == 0:
+        out_r = torch.empty((20, region.npy, region.npx), dtype=torch.float64, device="cuda")
+        half = int(np.floor(w.basis.det_window / 3))     # |k| <= 42 at D = 128
+        out_4 = torch.empty((region.npy, region.npx, 2 * half + 1, 2 * half + 1), dtype=torch.float32,
+                            device="cuda")
+        stem34 = {}
+        for name, fn in (("rings_3d", lambda: basis.image_rings(0.005, 20, region, out=out_r, recompute=True,
+                                                                  stream=stream)),
+                         ("pattern_4d", lambda: basis.image_4d(half, half, region, out=out_4, recompute=True,
+                                                                stream=stream))):
+            fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(2):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 2
+            stem34[name] = {"ms_per_image": ms, "pixels_per_s": w.n_pixels / (ms / 1e3),
+                            "vs_2d_time": ms / ms_per_step}
+        stem34["rings_3d"]["rings"] = "20 rings of 5 mrad from 0 (band ends at 86 mrad)"
+        stem34["pattern_4d"]["pattern"] = f"{2 * half + 1} x {2 * half + 1} frequencies per probe, float32, " \
+                                          f"{out_4.numel() * 4 / 1e9:.2f} GB per image"
+        del out_r, out_4
+
+    # ---- memory-bounded image (Sec. 4.2.4): 4096 resident exit waves per configuration
+    # (0.54 GB instead of 2.15 GB), partition plans of the three strategies, and the plan
+    # with the fewest Multislice runs timed on the same workload
+    partition = None
+    if args.partition and rank == 0:
+        M = 4096
+        plans = {}
+        for name, strat in (("rows", lma.LMA_PART_ROWS), ("rectangles", lma.LMA_PART_RECTANGLES),
+                            ("greedy", lma.LMA_PART_GREEDY)):
+            t0 = time.perf_counter()
+            _, n_parts, runs, peak = basis.partition(region, strat, M, start=0)
+            plans[name] = {"parts": n_parts, "runs_per_configuration": runs, "peak_resident": peak,
+                           "plan_s": time.perf_counter() - t0}
+        codes = {"rows": lma.LMA_PART_ROWS, "rectangles": lma.LMA_PART_RECTANGLES, "greedy": lma.LMA_PART_GREEDY}
+        best = min(plans, key=lambda k: plans[k]["runs_per_configuration"])
+        out_p = torch.empty_like(out)
+        basis.image_partitioned(dets, region, codes[best], M, out=out_p, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        basis.image_partitioned(dets, region, codes[best], M, out=out_p, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_p = e0.elapsed_time(e1)
+        n_t = int(basis.info().n_translates)
+        partition = {"max_resident": M, "store_GB": M * W * W * 8 / 1e9,
+                     "unbounded_store_GB": n_t * W * W * 8 / 1e9,
+                     "minimum_runs": n_t, "plans": plans,
+                     "timed": {"strategy": best, "ms_per_image": ms_p, "pixels_per_s": w.n_pixels / (ms_p / 1e3),
+                                          "vs_unbounded_time": ms_p / ms_per_step,
+                                          "bitwise_equal_to_unbounded": bool(torch.equal(out_p, out))}}
+        del out_p
+
     # ---- end to end through the public API with host buffers
     host_out = np.empty((len(dets), region.npy, region.npx), dtype=np.float64)
     h2d = sum(a.x.nbytes + a.y.nbytes + a.species.nbytes + 4 * (w.grid.n_slices + 1) for a in w.phonons)
@@ -573,14 +645,15 @@ def main():
                                "(sm_max_mhz of MEASURED_PEAKS.json)",
                 "algorithmic": f"{FLOPS_PER_TRANSLATE_SLICE} flop per translate-slice x "
                                f"{sl['units'] // max(1, sl['launches'])} translate-slices per launch",
-                "share_of_step": sl["total_ms"] / max(1e-9, sum(v["total_ms"] for v in prof.values())),
+                "share_of_step": sl["total_ms"] / max(1e-9, sum(v["total_ms"] for v in prof.values() if isinstance(v, dict))),
                 "launch_ms": slice_ms}
     syn = prof["synth"]
     synth_ms = syn["total_ms"] / max(1, syn["launches"])
     u_bytes = basis.info().exit_wave_bytes
     n_translates = int(basis.info().n_translates)
     kernels = {k: {"launches_per_step": v["launches"] / args.steps,
-                   "ms_per_launch": v["total_ms"] / max(1, v["launches"])} for k, v in prof.items()}
+                   "ms_per_launch": v["total_ms"] / max(1, v["launches"])} for k, v in prof.items()
+               if isinstance(v, dict)}
     kernels["synth"]["exit_wave_store_GBps"] = u_bytes / (synth_ms / 1e3) / 1e9 if synth_ms else None
 
     edits = None
@@ -623,11 +696,14 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": world * w.n_pixels / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(host_out.nbytes), "matches_device_run": e2e_consistent},
-            "gpu_launches": int(sum(v["launches"] for v in prof.values())),
+            "gpu_launches": int(sum(v["launches"] for v in prof.values() if isinstance(v, dict))),
+            "allocations_timed": int(prof.get("allocations", 0)),
             "mixed": mixed,
             "edit_latency": edits,
             "serving": serving,
             "batching": batching,
+            "stem34": stem34,
+            "partition": partition,
             "clocks": clk,
             "kernels": kernels,
             "wall_s_timed_region": wall,

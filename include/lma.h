@@ -45,7 +45,7 @@ typedef int32_t lma_status;
 #define LMA_ERR_OOM 2          /* device or host allocation failed */
 #define LMA_ERR_CUDA 3         /* CUDA runtime error (message in lma_last_error) */
 #define LMA_ERR_TIMEOUT 4      /* a bounded device wait gave up */
-#define LMA_ERR_UNSUPPORTED 5  /* valid request outside what this build implements */
+#define LMA_ERR_UNSUPPORTED 5  /* valid request outside what the library implements */
 
 #define LMA_BASIS_GAUSS 0      /* u = g_sigma (Sec. 4.2.3, Gaussians) */
 #define LMA_BASIS_PROBE 1      /* u = psi_0^init (Sec. 4.2.3, first paragraph) */
@@ -59,9 +59,16 @@ typedef int32_t lma_status;
 #define LMA_EDIT_SET_SPECIES 1 /* give the atoms of a column another species */
 
 #define LMA_IMAGE_RECOMPUTE 1u /* treat every stored exit wave as stale (full path) */
+#define LMA_MAX_RINGS 256      /* rings of one 3D STEM image */
 #define LMA_IMAGE_GRAPH 2u     /* lma_image_many: replay the device work as one CUDA graph */
 #define LMA_IMAGE_AUTOTUNE 4u  /* time every slice launch mode on this call's first launch of each
                                   shape and keep the fastest for that shape (lma_tuning_read) */
+
+/* Partition strategies of a probe region (Sec. 4.2.4). */
+#define LMA_PART_ROWS 0                    /* row by row */
+#define LMA_PART_RECTANGLES 1              /* equal rectangles, row-major order */
+#define LMA_PART_RECTANGLES_COLUMN_MAJOR 2 /* equal rectangles, column-major order */
+#define LMA_PART_GREEDY 3                  /* greedy growth from a start probe */
 
 /* How the CTAs of a slice launch (step a3) take their translates. */
 #define LMA_SLICE_AUTO -1          /* the tuned mode of the launch shape, else the default */
@@ -136,6 +143,15 @@ typedef struct {
   int32_t spacing_px[2];
 } lma_region;
 
+/* A memory bound for the exit-wave store (Sec. 4.2.4): the probe region is split into
+ * parts P_1..P_l whose translates I_{f,P_j,L} number at most max_resident each; parts are
+ * computed in order and the exit waves shared by consecutive parts are kept. */
+typedef struct {
+  int32_t strategy;          /* LMA_PART_* */
+  int32_t start;             /* LMA_PART_GREEDY: first probe, region index b * npx + a */
+  int64_t max_resident;      /* M: exit waves of one configuration held at once, >= L */
+} lma_partition_desc;
+
 /* Summary of a basis (host-side numbers). */
 typedef struct {
   int64_t n_translates;      /* |I_f| */
@@ -150,6 +166,10 @@ typedef struct {
 /* ---- context ------------------------------------------------------------------------- */
 
 /* Create a context on CUDA device `device` (or a host-only context with device = -1).
+ * A context and the specimens and bases made in it serve one host thread: its calls
+ * must not overlap in time, also not on different streams (the slice work counter, the
+ * item-list cache and the pinned staging buffer of host copies belong to the context).
+ * Use one context per thread for concurrent work.
  * Errors: LMA_ERR_CUDA if the device cannot be selected, LMA_ERR_OOM. */
 lma_status lma_create(int32_t device, lma_ctx** out);
 void lma_destroy(lma_ctx* ctx);
@@ -231,6 +251,60 @@ lma_status lma_image(lma_ctx* ctx, lma_specimen* spec, lma_basis* basis,
                      const lma_detector* det, int32_t n_det, const lma_region* region,
                      uint32_t flags, double* out, void* stream);
 
+/* 3D STEM image (Sec. 3.1, eq. for 3D STEM): ring a = 0..n_rings-1 collects the
+ * synthesized exit wave's (1/D^2) |DFT|^2 over a*ring_width <= lambda |k| < (a+1)*ring_width
+ * (rad), intersected with the bandlimit, on the D x D window; averaged over the
+ * configurations in FP64. Ring sums run in a fixed order (bitwise reproducible).
+ * out[n_rings][npy][npx] (double, host or device). Exit waves are made current as for
+ * lma_image (flags: LMA_IMAGE_RECOMPUTE, LMA_IMAGE_AUTOTUNE).
+ * Errors: LMA_ERR_INVALID (ring_width <= 0, n_rings outside 1..LMA_MAX_RINGS, bad region). */
+lma_status lma_image_rings(lma_ctx* ctx, lma_specimen* spec, lma_basis* basis, double ring_width,
+                           int32_t n_rings, const lma_region* region, uint32_t flags, double* out,
+                           void* stream);
+
+/* 4D STEM image (Sec. 3.1, eq. for 4D STEM): for every probe the diffraction pattern
+ * (1/D^2) |DFT(Psi_p)|^2 of its synthesized exit wave on the D x D window, sampled at the
+ * frequencies (a, b) * (1/(D dx), 1/(D dy)) for |a| <= half_x, |b| <= half_y, zero outside
+ * the bandlimit, averaged over configurations (FP64 sum, stored as float).
+ * out[npy][npx][2 half_y + 1][2 half_x + 1] (float, host or device), entry [b + half_y]
+ * [a + half_x]. Errors: LMA_ERR_INVALID (half widths outside 0..D/2-1, bad region). */
+lma_status lma_image_4d(lma_ctx* ctx, lma_specimen* spec, lma_basis* basis, int32_t half_x,
+                        int32_t half_y, const lma_region* region, uint32_t flags, float* out,
+                        void* stream);
+
+/* ---- memory-bounded partition (Sec. 4.2.4) ------------------------------------------------ */
+
+/* Partition of a probe region under a memory bound. Strategies:
+ *  - rows: probes in raster order join the current part while its translates stay within M;
+ *  - rectangles: one tile shape w x h from probe (0, 0), clipped at the edges, of largest
+ *    area such that a tile anchored at every phase of the probe/lattice period needs at
+ *    most M translates (for each width the height grows while that holds; ties: squarer,
+ *    then wider);
+ *  - greedy: from `start`, add the unassigned 8-neighbour of the last added probe that
+ *    adds the fewest translates (ties by (b, a)); a part closes when that neighbour would
+ *    exceed M and the next part starts with it; with no unassigned neighbour, continue at
+ *    the first unassigned probe in raster order.
+ * Outputs (each may be NULL): part[npy * npx] = part index of each probe (parts in
+ * processing order), n_parts = l, runs = T_{P_1..P_l} (Multislice runs per configuration:
+ * sum of |I(P_j)| minus the translates shared by consecutive parts), peak = max |I(P_j)|.
+ * Host-only work (valid in a host-only context). Errors: LMA_ERR_INVALID (bad region,
+ * strategy, start, or max_resident < L). */
+lma_status lma_partition(lma_ctx* ctx, lma_basis* basis, const lma_region* region,
+                         const lma_partition_desc* desc, int32_t* part, int32_t* n_parts,
+                         int64_t* runs, int64_t* peak);
+
+/* 2D STEM image (as lma_image, always recomputing) with an exit-wave store of
+ * max_resident waves per configuration instead of |I_f|: for each configuration the parts
+ * are propagated and read out in order, keeping the waves shared by consecutive parts.
+ * Every exit wave and reading is computed as in lma_image, so the image is bitwise equal
+ * to lma_image's. The device store is max_resident * W^2 * 8 bytes (complex64) or half
+ * that (LMA_PREC_MIXED); the plan's tables are kept in the basis for the next call.
+ * Errors as for lma_image and lma_partition. */
+lma_status lma_image_partitioned(lma_ctx* ctx, lma_specimen* spec, lma_basis* basis,
+                                 const lma_detector* det, int32_t n_det, const lma_region* region,
+                                 const lma_partition_desc* desc, uint32_t flags, double* out,
+                                 void* stream);
+
 /* Images of several specimens (of any sizes) in one call on one stream (the
  * batching form of steps a1-a6): for each specimen its configurations go through
  * the slice and synthesis kernels in phonon batches (see lma_basis_desc). With
@@ -310,6 +384,8 @@ typedef struct {
   lma_kernel_stat slice;       /* step a3 */
   lma_kernel_stat synth;       /* steps a4-a5 (and the FP64 accumulation of a6) */
   lma_kernel_stat finalize;    /* step a6 */
+  int64_t allocations;         /* device and pinned host allocations the library made since the
+                                  last lma_profile_enable (in any context of the process) */
 } lma_profile;
 
 /* One autotuned slice launch shape: the jobs (specimens) of the launch, its

@@ -622,6 +622,121 @@ def standard_image(prm: LmaParams, t_full: np.ndarray, detectors, probes: np.nda
 # local recompute (Sec. 4.2.6)
 # ----------------------------------------------------------------------------
 
+# ----------------------------------------------------------------------------
+# memory-bounded partition of the probe region (Sec. 4.2.4)
+# ----------------------------------------------------------------------------
+
+def probe_translate_sets(prm: "LmaParams", probes: np.ndarray) -> List[frozenset]:
+    """I_{f,p,L} of every probe (lattice indices), probes (n, 2) pixel (x, y)."""
+    lat = input_lattice(prm.nx, prm.ny, prm.in_spacing, prm.in_offset, prm.f)
+    return [frozenset(int(i) for i in nearest_translates((int(q[0]), int(q[1])), lat, prm.L, prm.nx, prm.ny)[0])
+            for q in probes]
+
+
+def partition_cost(sets: Sequence[frozenset], parts: Sequence[Sequence[int]]) -> int:
+    """T_{P_1..P_l} of Sec. 4.2.4: Multislice runs when the parts are computed in order and
+    only the solutions shared by consecutive parts are kept."""
+    unions = [frozenset().union(*[sets[q] for q in part]) for part in parts]
+    return sum(len(u) for u in unions) - sum(len(unions[j] & unions[j + 1]) for j in range(len(unions) - 1))
+
+
+def partition_rows(sets: Sequence[frozenset], npx: int, npy: int, M: int) -> List[List[int]]:
+    """Row by row (Sec. 4.2.4, strategy 1): probes in raster order (a fastest); a probe
+    joins the current part while the part's translates stay within M, else it starts the
+    next part. Probe index = b * npx + a."""
+    parts: List[List[int]] = []
+    cur: List[int] = []
+    union: set = set()
+    for q in range(npx * npy):
+        if cur and len(union | sets[q]) > M:
+            parts.append(cur)
+            cur, union = [], set()
+        cur.append(q)
+        union |= sets[q]
+    if cur:
+        parts.append(cur)
+    return parts
+
+
+def _tiles(npx: int, npy: int, w: int, h: int, column_major: bool) -> List[List[int]]:
+    """The w x h tiling from (0, 0); tiles at the right and bottom edges are clipped."""
+    xs = list(range(0, npx, w))
+    ys = list(range(0, npy, h))
+    order = [(x0, y0) for x0 in xs for y0 in ys] if column_major else [(x0, y0) for y0 in ys for x0 in xs]
+    return [[b * npx + a for b in range(y0, min(y0 + h, npy)) for a in range(x0, min(x0 + w, npx))]
+            for x0, y0 in order]
+
+
+def partition_rectangles(sets: Sequence[frozenset], npx: int, npy: int, M: int,
+                         column_major: bool = False, period: Tuple[int, int] = (1, 1)) -> List[List[int]]:
+    """Rectangles (Sec. 4.2.4, strategy 2): tiles of one shape w x h from probe (0, 0),
+    clipped at the right and bottom edges, in row-major (or column-major) order.
+
+    The shape has the largest area w h such that a w x h tile anchored at every phase
+    (ax, ay), 0 <= ax < period[0], 0 <= ay < period[1], needs at most M translates (the
+    probe/lattice geometry repeats every `period` probes, so every full tile of the tiling
+    is a translate of one of these; clipped tiles are subsets). For each width the height
+    grows while all phase tiles fit; ties go to the squarer shape, then the wider one.
+    """
+    def fits(w: int, h: int) -> bool:
+        for ay in range(period[1]):
+            for ax in range(period[0]):
+                u = set()
+                for b in range(ay, min(ay + h, npy)):
+                    for a in range(ax, min(ax + w, npx)):
+                        u |= sets[b * npx + a]
+                if len(u) > M:
+                    return False
+        return True
+
+    best = None
+    for w in range(1, npx + 1):
+        if not fits(w, 1):
+            break
+        h = 1
+        while h < npy and fits(w, h + 1):
+            h += 1
+        key = (w * h, -abs(w - h), w)
+        if best is None or key > best[0]:
+            best = (key, w, h)
+    return _tiles(npx, npy, best[1], best[2], column_major)
+
+
+def partition_greedy(sets: Sequence[frozenset], npx: int, npy: int, M: int, start: int = 0
+                     ) -> List[List[int]]:
+    """Greedy (Sec. 4.2.4, strategy 3): from the start probe, repeatedly add the unassigned
+    neighbour (8-neighbourhood, inside the region) of the last added probe whose addition
+    gives the fewest translates, ties by (b, a); the part closes when that neighbour would
+    exceed M, and the next part starts with it. A probe with no unassigned neighbour
+    continues with the first unassigned probe in raster order."""
+    n = npx * npy
+    assigned = [False] * n
+    parts: List[List[int]] = []
+    cur: List[int] = []
+    union: set = set()
+    nxt = start
+    while True:
+        q = nxt
+        if cur and len(union | sets[q]) > M:
+            parts.append(cur)
+            cur, union = [], set()
+        cur.append(q)
+        union |= sets[q]
+        assigned[q] = True
+        if len(cur) + sum(len(p) for p in parts) == n:
+            break
+        a, b = q % npx, q // npx
+        cand = []
+        for bb in range(b - 1, b + 2):
+            for aa in range(a - 1, a + 2):
+                if 0 <= aa < npx and 0 <= bb < npy and not assigned[bb * npx + aa]:
+                    r = bb * npx + aa
+                    cand.append((len(union) + len(sets[r] - union), bb, aa, r))
+        nxt = min(cand)[3] if cand else assigned.index(False)
+    parts.append(cur)
+    return parts
+
+
 def edit_column(x: np.ndarray, y: np.ndarray, slc: np.ndarray, species: np.ndarray,
                 lx: float, ly: float, cx: float, cy: float, r_site: float, op: int,
                 new_species: int):

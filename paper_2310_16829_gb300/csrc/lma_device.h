@@ -66,6 +66,8 @@ struct SliceLaunch {
   int start[kMaxJobs + 1];     // list[start[j] .. start[j + 1]) holds job j's items
   int n_jobs;
   const int32_t* list;         // items slot * n_translates + translate
+  const int32_t* out_index;    // null: item i's wave goes to store entry `translate`; else to
+                               // entry out_index[i] of its slot (bounded store of a partition)
   int n_list;
   int* counter;                // kSliceDynamic: zeroed before the launch
 };
@@ -79,7 +81,9 @@ struct SynthArgs {
   const float2* alpha;         // [n_probes][L]
   const int2* shift;           // [n_probes][L] placement of U in the probe window
   int L;
-  int n_probes;
+  int n_probes;                // probes of the region (stride of the accumulator)
+  const int32_t* probe_list;   // null: every region probe, walked in strips (tables indexed by p);
+  int n_list;                  // else these n_list probes (tables indexed by list position)
   int npx, npy;                // region shape: probe p = b * npx + a
   int strip;                   // probes are visited in vertical strips of this many columns
   int n_cfg;                   // configurations in this launch (store slots 0..n_cfg-1)
@@ -88,8 +92,23 @@ struct SynthArgs {
   size_t u_slot;               // elements of one slot of the exit-wave store
   int cyclic;                  // windows are the whole periodic grid
   const uint32_t* det_bits;    // [n_det][kThreads] detector bits in C layout
-  int n_det;
+  int n_det;                   // annuli: detectors; labels: labels (outputs per probe)
   double* acc;                 // [configuration][n_det][n_probes] readings (assigned)
+  // kReadLabels: pixel lists of the labels (3D STEM rings), CSR over pixel ky * W + kx
+  const int32_t* lab_start;    // [n_det + 1]
+  const int32_t* lab_pix;      // ascending pixel indices of each label
+  // kReadPattern: |DFT|^2 / W^2 at |kx| <= pat_a, |ky| <= pat_b (4D STEM), zero outside
+  // the band kx^2 + ky^2 <= band_r2, FP32 per configuration slot
+  float* pat;                  // [slot][n_probes][2 pat_b + 1][2 pat_a + 1]
+  int pat_a, pat_b;
+  int band_r2;
+};
+
+// Readouts of the synthesis kernel.
+enum ReadMode : int {
+  kReadAnnuli = 0,             // up to kMaxDet 2D STEM annuli (bit masks)
+  kReadLabels = 1,             // disjoint labelled pixel sets (3D STEM rings), deterministic sums
+  kReadPattern = 2             // the diffraction pattern on a centred crop (4D STEM)
 };
 
 // Scratch of the no-allocation readout: a file-scope device array of this size
@@ -107,7 +126,12 @@ cudaError_t launch_potential(const PotArgs& a, cudaStream_t s);
 // (kSliceDynamic zeroes a.counter on the stream first)
 cudaError_t launch_slice(const SliceLaunch& a, bool even_origins, bool half, int mode, cudaStream_t s);
 int sm_count();
-cudaError_t launch_synth(const SynthArgs& a, bool half, cudaStream_t s);
+cudaError_t launch_synth(const SynthArgs& a, bool half, int mode, cudaStream_t s);
+// acc[i] (+)= sum over n_cfg slots (in slot order) of slots[c * n + i]; first: assign
+cudaError_t launch_pattern_accumulate(const float* slots, int64_t n, int n_cfg, bool first, double* acc,
+                                      cudaStream_t s);
+// out[i] = scale * acc[i] as float
+cudaError_t launch_pattern_finalize(const double* acc, int64_t n, double scale, float* out, cudaStream_t s);
 // complex64 copy of one wave of the FP16 store
 cudaError_t launch_expand_half(const void* src, float scale, float2* dst, cudaStream_t s);
 // out[i] = scale * sum over n_cfg slots (in slot order) of acc[c * n + i]

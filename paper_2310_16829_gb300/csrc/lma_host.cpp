@@ -12,6 +12,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
@@ -52,15 +53,21 @@ struct lma_ctx {
   std::vector<Pending> pend;
   std::vector<cudaEvent_t> pool;
   bool capturing = false;
-  // device copies of slice item lists, keyed by contents; a full cache reuses the
-  // oldest entry's buffer (cudaFree would synchronize the whole device)
+  // device copies of slice item lists, keyed by contents, least recently used last out.
+  // Lists up to kListSlot bytes live in slots of one slab allocated at first use; longer
+  // ones get their own buffers, reused on eviction when large enough (cudaMalloc and
+  // cudaFree can wait for the whole device, which must not happen on an edit's path)
   struct List {
     std::vector<int32_t> items;
     uint64_t hash = 0;
     void* p = nullptr;
     size_t bytes = 0;
+    bool owned = false;   // own buffer (else a slab slot)
+    bool used = false;    // holds a list
   };
   std::vector<List> lists;
+  void* list_slab = nullptr;
+  int64_t alloc_base = 0;                                   // device allocations at profile reset
   std::vector<std::pair<void*, uint64_t>> capture_lists;   // lists read by the capture in progress
   int* d_counter = nullptr;                                 // work counter of dynamic slice launches
   void* stage = nullptr;                                    // pinned staging buffer (kStageBytes)
@@ -208,10 +215,18 @@ struct DevBuf {
   }
 };
 
+// device and pinned-host allocations made by the library (all contexts)
+std::atomic<int64_t> g_allocations{0};
+
+cudaError_t counted_malloc(void** p, size_t bytes) {
+  g_allocations.fetch_add(1, std::memory_order_relaxed);
+  return cudaMalloc(p, bytes);
+}
+
 cudaError_t ensure(DevBuf& b, size_t bytes) {
   if (b.bytes >= bytes && b.p) return cudaSuccess;
   b.release();
-  cudaError_t e = cudaMalloc(&b.p, bytes);
+  cudaError_t e = counted_malloc(&b.p, bytes);
   if (e == cudaSuccess) b.bytes = bytes;
   return e;
 }
@@ -235,6 +250,7 @@ struct HostPart {
 
 cudaError_t ensure_stage(lma_ctx* ctx) {
   if (ctx->stage) return cudaSuccess;
+  g_allocations.fetch_add(1, std::memory_order_relaxed);
   return cudaMallocHost(&ctx->stage, kStageBytes);
 }
 
@@ -368,6 +384,23 @@ struct lma_basis {
   std::map<std::pair<int, int>, CoefSet> sets;
   // device
   DevBuf d_uW, d_ex, d_ey, d_U, d_Uscale, d_acc, d_det;
+  DevBuf d_lab;                  // 3D STEM ring labels: [n_labels + 1] CSR starts, then pixels
+  std::vector<double> lab_key;   // (width, n_rings) of d_lab
+  DevBuf d_pat, d_pat_acc;       // 4D STEM: FP32 pattern slots, FP64 running sum
+  // memory-bounded partition (Sec. 4.2.4): the last plan and its device tables
+  struct Part {
+    std::vector<int32_t> probes;       // region indices b * npx + a
+    std::vector<int32_t> items, outs;  // new translates (even window origins first), their store entries
+    int n_even = 0;
+    size_t o_probes = 0, o_tidx = 0, o_alpha = 0, o_shift = 0, o_items = 0, o_outs = 0;   // in d_plan
+  };
+  lma_region plan_r{};
+  lma_partition_desc plan_d{};
+  bool plan_valid = false, plan_dev = false;
+  std::vector<Part> parts;
+  int64_t plan_runs = 0, plan_peak = 0;
+  std::vector<int32_t> plan_tab;     // host copy of d_plan
+  DevBuf d_plan, d_Up, d_Upscale;
   bool dev_tables = false;
   int B = 0;                     // exit-wave store slots (configurations in flight)
   std::vector<int> U_phonon;     // configuration held by each slot (-1: none)
@@ -568,9 +601,10 @@ lma_status validate_region(lma_ctx* ctx, const lma_basis* b, const lma_region* r
 }
 
 // device tables of a basis (input wave, propagator factors)
-lma_status ensure_basis_device(lma_basis* b, cudaStream_t st) {
+// input wave and propagator factors on the device (no exit-wave store)
+lma_status ensure_basis_tables(lma_basis* b, cudaStream_t st) {
   lma_ctx* ctx = b->ctx;
-  if (b->dev_tables) return LMA_OK;
+  if (b->d_uW.p && b->d_ex.p && b->d_ey.p) return LMA_OK;
   std::vector<float> uw(2 * static_cast<size_t>(kW) * kW);
   for (size_t k = 0; k < b->uW.size(); ++k) {
     uw[2 * k] = static_cast<float>(b->uW[k].real());
@@ -583,6 +617,15 @@ lma_status ensure_basis_device(lma_basis* b, cudaStream_t st) {
                                     HostPart{b->d_ex.p, b->ex.data(), b->ex.size() * sizeof(float)},
                                     HostPart{b->d_ey.p, b->ey.data(), b->ey.size() * sizeof(float)}},
                              st));
+  return LMA_OK;
+}
+
+// tables plus the exit-wave store of B configurations
+lma_status ensure_basis_device(lma_basis* b, cudaStream_t st) {
+  lma_ctx* ctx = b->ctx;
+  if (b->dev_tables) return LMA_OK;
+  lma_status s0 = ensure_basis_tables(b, st);
+  if (s0 != LMA_OK) return s0;
   // phonon batch: configurations whose exit waves (and transmissions) are held at once
   const bool half = b->desc.precision == LMA_PREC_MIXED;
   const int nph = static_cast<int>(b->spec->ph.size());
@@ -728,33 +771,62 @@ uint64_t hash_items(const std::vector<int32_t>& v) {
 
 // device copy of an item list from the context's content-keyed cache; repeated
 // batches and captured graphs never copy from host memory
+constexpr size_t kListSlot = size_t(64) << 10;
+constexpr int kListSlots = 16, kListOwned = 8;
+
 lma_status upload_list(lma_ctx* ctx, const std::vector<int32_t>& list, cudaStream_t st, const int32_t** out) {
   const uint64_t h = hash_items(list);
-  for (auto& e : ctx->lists)
-    if (e.hash == h && e.items == list) {
+  for (size_t k = 0; k < ctx->lists.size(); ++k) {
+    lma_ctx::List& e = ctx->lists[k];
+    if (e.used && e.hash == h && e.items == list) {
       if (ctx->capturing) ctx->capture_lists.emplace_back(e.p, h);
       *out = static_cast<const int32_t*>(e.p);
+      if (!ctx->capturing) std::rotate(ctx->lists.begin() + k, ctx->lists.begin() + k + 1, ctx->lists.end());
       return LMA_OK;
     }
-  if (ctx->capturing) return fail(ctx, LMA_ERR_CUDA, "slice list not resident during graph capture");
-  lma_ctx::List e;
-  if (ctx->lists.size() >= 16) {
-    e = std::move(ctx->lists.front());   // reuse the buffer: no cudaFree, no device-wide sync
-    ctx->lists.erase(ctx->lists.begin());
   }
+  if (ctx->capturing) return fail(ctx, LMA_ERR_CUDA, "slice list not resident during graph capture");
   const size_t bytes = list.size() * sizeof(int32_t);
-  if (e.bytes < bytes) {
+  if (!ctx->list_slab) {
+    CUDA_TRY(ctx, counted_malloc(&ctx->list_slab, kListSlot * kListSlots));
+    for (int k = 0; k < kListSlots; ++k) {
+      lma_ctx::List e;
+      e.p = static_cast<char*>(ctx->list_slab) + k * kListSlot;
+      e.bytes = kListSlot;
+      ctx->lists.insert(ctx->lists.begin(), std::move(e));
+    }
+  }
+  // victim: the least recently used entry of the right kind (slab slot or own buffer)
+  const bool small = bytes <= kListSlot;
+  int n_owned = 0;
+  for (const auto& e : ctx->lists) n_owned += e.owned ? 1 : 0;
+  // (a long list gets a new buffer until kListOwned exist)
+  auto victim = ctx->lists.end();
+  if (small || n_owned >= kListOwned)
+    for (auto it = ctx->lists.begin(); it != ctx->lists.end(); ++it)
+      if (it->owned != small) {
+        victim = it;
+        break;
+      }
+  lma_ctx::List e;
+  if (victim != ctx->lists.end()) {
+    e = std::move(*victim);
+    ctx->lists.erase(victim);
+  }
+  if (!small && e.bytes < bytes) {   // a new or too small own buffer
     if (e.p) CUDA_TRY(ctx, cudaFree(e.p));
+    size_t cap = kListSlot * 2;
+    while (cap < bytes) cap <<= 1;
     e.p = nullptr;
     e.bytes = 0;
-    size_t cap = size_t(64) << 10;
-    while (cap < bytes) cap <<= 1;
-    CUDA_TRY(ctx, cudaMalloc(&e.p, cap));
+    CUDA_TRY(ctx, counted_malloc(&e.p, cap));
     e.bytes = cap;
+    e.owned = true;
   }
   CUDA_TRY(ctx, upload(ctx, e.p, list.data(), bytes, st));
   e.items = list;
   e.hash = h;
+  e.used = true;
   *out = static_cast<const int32_t*>(e.p);
   ctx->lists.push_back(std::move(e));
   return LMA_OK;
@@ -854,7 +926,7 @@ struct JobWork {
 lma_status propagate_jobs(lma_ctx* ctx, std::vector<JobWork>& work, cudaStream_t st) {
   if (!ctx->d_counter) {
     if (ctx->capturing) return fail(ctx, LMA_ERR_CUDA, "work counter missing during graph capture");
-    CUDA_TRY(ctx, cudaMalloc(&ctx->d_counter, sizeof(int)));
+    CUDA_TRY(ctx, counted_malloc(reinterpret_cast<void**>(&ctx->d_counter), sizeof(int)));
   }
   for (int hv = 0; hv < 2; ++hv) {
     std::vector<JobWork*> group;
@@ -934,14 +1006,15 @@ lma_status ensure_batch(lma_basis* b, lma_specimen* sp, int phi0, int nb, const 
   return propagate_jobs(b->ctx, work, st);
 }
 
-lma_status build_region(lma_basis* b, const lma_region* r, cudaStream_t st) {
-  lma_ctx* ctx = b->ctx;
-  if (b->reg_valid && std::memcmp(&b->reg.r, r, sizeof(lma_region)) == 0) return LMA_OK;
+// Probe tables of a region on the host: for probe p = b * npx + a and j < L, the translate
+// index of its j-th input wave, its coefficient (complex64) and its window placement.
+lma_status region_tables_host(lma_basis* b, const lma_region* r, std::vector<int32_t>& tidx,
+                              std::vector<float>& al, std::vector<int32_t>& sh) {
   const int L = b->desc.L;
   const int64_t np = static_cast<int64_t>(r->npx) * r->npy;
-  std::vector<int32_t> tidx(static_cast<size_t>(np) * L);
-  std::vector<float> al(2 * static_cast<size_t>(np) * L);
-  std::vector<int32_t> sh(2 * static_cast<size_t>(np) * L);
+  tidx.assign(static_cast<size_t>(np) * L, 0);
+  al.assign(2 * static_cast<size_t>(np) * L, 0.f);
+  sh.assign(2 * static_cast<size_t>(np) * L, 0);
   const int half = (b->desc.det_window - b->desc.window) / 2;
   for (int pb = 0; pb < r->npy; ++pb) {
     for (int pa = 0; pa < r->npx; ++pa) {
@@ -960,6 +1033,17 @@ lma_status build_region(lma_basis* b, const lma_region* r, cudaStream_t st) {
       }
     }
   }
+  return LMA_OK;
+}
+
+lma_status build_region(lma_basis* b, const lma_region* r, cudaStream_t st) {
+  lma_ctx* ctx = b->ctx;
+  if (b->reg_valid && std::memcmp(&b->reg.r, r, sizeof(lma_region)) == 0) return LMA_OK;
+  const int64_t np = static_cast<int64_t>(r->npx) * r->npy;
+  std::vector<int32_t> tidx, sh;
+  std::vector<float> al;
+  lma_status s0 = region_tables_host(b, r, tidx, al, sh);
+  if (s0 != LMA_OK) return s0;
   RegionTables& R = b->reg;
   R.needed.assign(static_cast<size_t>(b->nT), 0);
   for (int32_t i : tidx) R.needed[i] = 1;
@@ -1012,6 +1096,43 @@ lma_status build_detectors(lma_basis* b, const lma_detector* det, int n_det, cud
   return LMA_OK;
 }
 
+// 3D STEM ring labels on the D x D detection window: ring a holds the pixels with
+// a * width <= lambda |k| < (a + 1) * width inside the bandlimit, decided in FP64 with the
+// operation order of the 2D detector. Device table: [n_rings + 1] CSR starts, then the
+// pixel indices iy * D + ix of each ring in ascending order.
+lma_status build_labels(lma_basis* b, double width, int n_rings, cudaStream_t st) {
+  lma_ctx* ctx = b->ctx;
+  const std::vector<double> key{width, static_cast<double>(n_rings)};
+  if (b->d_lab.p && key == b->lab_key) return LMA_OK;
+  const lma_grid& g = b->spec->g;
+  const int D = b->desc.det_window;
+  const double dx = g.lx / g.nx, dy = g.ly / g.ny, lam = g.lambda, frac = g.bandlimit_frac;
+  std::vector<std::vector<int32_t>> ring(n_rings);
+  for (int iy = 0; iy < D; ++iy) {
+    const int my = signed_index(iy, D);
+    const double ky = my / (D * dy);
+    for (int ix = 0; ix < D; ++ix) {
+      const int mx = signed_index(ix, D);
+      const double kx = mx / (D * dx);
+      const double ang = lam * std::sqrt(ky * ky + kx * kx);
+      const bool band = static_cast<double>(4 * (my * my + mx * mx)) <= frac * frac * D * D;
+      if (!band) continue;
+      for (int a = 0; a < n_rings; ++a)
+        if (ang >= a * width && ang < (a + 1) * width) {
+          ring[a].push_back(iy * D + ix);
+          break;
+        }
+    }
+  }
+  std::vector<int32_t> table(static_cast<size_t>(n_rings) + 1, 0);
+  for (int a = 0; a < n_rings; ++a) table[a + 1] = table[a] + static_cast<int32_t>(ring[a].size());
+  for (int a = 0; a < n_rings; ++a) table.insert(table.end(), ring[a].begin(), ring[a].end());
+  CUDA_TRY(ctx, ensure(b->d_lab, table.size() * sizeof(int32_t)));
+  CUDA_TRY(ctx, upload(ctx, b->d_lab.p, table.data(), table.size() * sizeof(int32_t), st));
+  b->lab_key = key;
+  return LMA_OK;
+}
+
 bool is_device_pointer(const void* p) {
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -1037,31 +1158,51 @@ cudaError_t read_back(lma_ctx* ctx, void* dst, const void* src, size_t bytes, cu
 namespace {
 
 // Device work of the images of several (basis, specimen) pairs (steps a1, a3-a6).
-// Configurations go in rounds: round r takes each pair's r-th phonon batch; the
-// slice work of all pairs in a round is one launch (per precision and origin
+// Configurations go in passes: pass r takes each pair's r-th phonon batch; the
+// slice work of all pairs in a pass is one launch (per precision and origin
 // parity), then each pair's batch is synthesized into its accumulator slots.
-// After the last round each pair's average goes to its dev_out (or, when that is
+// After the last pass each pair's average goes to its dev_out (or, when that is
 // null, to the accumulator's last slot). Needs build_region / build_detectors done.
 struct ImageJob {
   lma_basis* b;
   lma_specimen* sp;
-  double* dev_out;
+  void* dev_out;   // double (annuli, labels) or float (pattern); null: into the basis
 };
 
-lma_status images_work(lma_ctx* ctx, const std::vector<ImageJob>& jobs, int n_det, bool recompute,
+// what the synthesis kernel reads out of each probe's diffraction plane
+struct Readout {
+  int mode = lma_dev::kReadAnnuli;
+  int n_out = 0;                 // annuli or labels per probe
+  int pat_a = 0, pat_b = 0;      // pattern half-widths (4D STEM)
+  int64_t pat_size() const { return static_cast<int64_t>(2 * pat_a + 1) * (2 * pat_b + 1); }
+};
+
+// results of images_work left in the basis when a job has no device output
+const double* basis_result(const lma_basis* b, const lma_specimen* sp, int n_out) {
+  return static_cast<const double*>(b->d_acc.p) + sp->ph.size() * static_cast<size_t>(b->reg.n_probes * n_out);
+}
+
+lma_status images_work(lma_ctx* ctx, const std::vector<ImageJob>& jobs, const Readout& ro, bool recompute,
                        cudaStream_t st) {
-  int rounds = 0;
+  const bool pattern = ro.mode == lma_dev::kReadPattern;
+  int passes = 0;
   for (const ImageJob& J : jobs) {
     const int nph = static_cast<int>(J.sp->ph.size());
-    const int64_t nout = J.b->reg.n_probes * n_det;
-    // one slot per configuration plus one for the average
-    CUDA_TRY(ctx, ensure(J.b->d_acc, static_cast<size_t>(nout) * (nph + 1) * sizeof(double)));
-    rounds = std::max(rounds, (nph + J.b->B - 1) / J.b->B);
+    const int64_t np = J.b->reg.n_probes;
+    if (pattern) {
+      const size_t n = static_cast<size_t>(np) * ro.pat_size();
+      CUDA_TRY(ctx, ensure(J.b->d_pat, n * J.b->B * sizeof(float)));
+      CUDA_TRY(ctx, ensure(J.b->d_pat_acc, n * sizeof(double)));
+    } else {
+      // one slot per configuration plus one for the average
+      CUDA_TRY(ctx, ensure(J.b->d_acc, static_cast<size_t>(np * ro.n_out) * (nph + 1) * sizeof(double)));
+    }
+    passes = std::max(passes, (nph + J.b->B - 1) / J.b->B);
   }
   lma_status s;
-  for (int r = 0; r < rounds; ++r) {
+  for (int r = 0; r < passes; ++r) {
     std::vector<JobWork> work;
-    std::vector<std::pair<int, int>> batch;   // (phi0, nb) per job in this round
+    std::vector<std::pair<int, int>> batch;   // (phi0, nb) per job in this pass
     for (const ImageJob& J : jobs) {
       const int nph = static_cast<int>(J.sp->ph.size());
       const int phi0 = r * J.b->B;
@@ -1097,16 +1238,42 @@ lma_status images_work(lma_ctx* ctx, const std::vector<ImageJob>& jobs, int n_de
       a.u_slot = static_cast<size_t>(b->nT) * kW * kW;
       a.cyclic = (b->nx == kW && b->ny == kW) ? 1 : 0;
       a.det_bits = static_cast<const uint32_t*>(b->d_det.p);
-      a.n_det = n_det;
+      a.n_det = ro.n_out;
       a.acc = static_cast<double*>(b->d_acc.p);
-      CUDA_TRY(ctx, counted(ctx, K_SYNTH, np * nb, st, [&] { return lma_dev::launch_synth(a, half, st); }));
+      a.band_r2 = b->r2max;
+      if (ro.mode == lma_dev::kReadLabels) {
+        a.lab_start = static_cast<const int32_t*>(b->d_lab.p);
+        a.lab_pix = a.lab_start + ro.n_out + 1;
+      }
+      if (pattern) {
+        a.pat = static_cast<float*>(b->d_pat.p);
+        a.pat_a = ro.pat_a;
+        a.pat_b = ro.pat_b;
+      }
+      CUDA_TRY(ctx, counted(ctx, K_SYNTH, np * nb, st,
+                            [&] { return lma_dev::launch_synth(a, half, ro.mode, st); }));
+      if (pattern) {
+        const int64_t n = np * ro.pat_size();
+        CUDA_TRY(ctx, counted(ctx, K_FIN, n, st, [&] {
+          return lma_dev::launch_pattern_accumulate(static_cast<const float*>(b->d_pat.p), n, nb,
+                                                    batch[k].first == 0, static_cast<double*>(b->d_pat_acc.p), st);
+        }));
+      }
     }
   }
   for (const ImageJob& J : jobs) {
     const int nph = static_cast<int>(J.sp->ph.size());
-    const int64_t nout = J.b->reg.n_probes * n_det;
+    if (pattern) {
+      const int64_t n = J.b->reg.n_probes * ro.pat_size();
+      float* fin = J.dev_out ? static_cast<float*>(J.dev_out) : static_cast<float*>(J.b->d_pat.p);
+      CUDA_TRY(ctx, counted(ctx, K_FIN, n, st, [&] {
+        return lma_dev::launch_pattern_finalize(static_cast<const double*>(J.b->d_pat_acc.p), n, 1.0 / nph, fin, st);
+      }));
+      continue;
+    }
+    const int64_t nout = J.b->reg.n_probes * ro.n_out;
     const double* acc = static_cast<const double*>(J.b->d_acc.p);
-    double* fin = J.dev_out ? J.dev_out : static_cast<double*>(J.b->d_acc.p) + static_cast<size_t>(nph) * nout;
+    double* fin = J.dev_out ? static_cast<double*>(J.dev_out) : const_cast<double*>(basis_result(J.b, J.sp, ro.n_out));
     CUDA_TRY(ctx, counted(ctx, K_FIN, nout, st,
                           [&] { return lma_dev::launch_finalize(acc, nout, nph, 1.0 / nph, fin, st); }));
   }
@@ -1115,7 +1282,9 @@ lma_status images_work(lma_ctx* ctx, const std::vector<ImageJob>& jobs, int n_de
 
 lma_status image_work(lma_basis* b, lma_specimen* sp, int n_det, bool recompute, double* dev_out,
                       cudaStream_t st) {
-  return images_work(b->ctx, {ImageJob{b, sp, dev_out}}, n_det, recompute, st);
+  Readout ro;
+  ro.n_out = n_det;
+  return images_work(b->ctx, {ImageJob{b, sp, dev_out}}, ro, recompute, st);
 }
 
 // slice launches of one API call time their modes (LMA_IMAGE_AUTOTUNE)
@@ -1209,7 +1378,8 @@ void lma_destroy(lma_ctx* ctx) {
     if (g.graph) cudaGraphDestroy(g.graph);
   }
   for (auto& l : ctx->lists)
-    if (l.p) cudaFree(l.p);
+    if (l.owned && l.p) cudaFree(l.p);
+  if (ctx->list_slab) cudaFree(ctx->list_slab);
   if (ctx->d_counter) cudaFree(ctx->d_counter);
   if (ctx->stage) cudaFreeHost(ctx->stage);
   delete ctx;
@@ -1371,6 +1541,12 @@ lma_status lma_free_basis(lma_basis* b) {
   b->d_Uscale.release();
   b->d_acc.release();
   b->d_det.release();
+  b->d_lab.release();
+  b->d_pat.release();
+  b->d_pat_acc.release();
+  b->d_plan.release();
+  b->d_Up.release();
+  b->d_Upscale.release();
   b->reg.tidx.release();
   b->reg.alpha.release();
   b->reg.shift.release();
@@ -1495,6 +1671,473 @@ lma_status lma_image(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, const lma_det
   return LMA_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// memory-bounded partition (Sec. 4.2.4)
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+// union sizes by stamping translates with the id of the set they were counted for
+struct Stamps {
+  std::vector<int32_t> mark;
+  explicit Stamps(int64_t n) : mark(static_cast<size_t>(n), -1) {}
+  // translates of probe q not yet stamped with id
+  int fresh(const int32_t* t, int L, int32_t id) const {
+    int k = 0;
+    for (int j = 0; j < L; ++j) k += mark[t[j]] != id ? 1 : 0;
+    return k;
+  }
+  int add(const int32_t* t, int L, int32_t id) {
+    int k = 0;
+    for (int j = 0; j < L; ++j)
+      if (mark[t[j]] != id) {
+        mark[t[j]] = id;
+        ++k;
+      }
+    return k;
+  }
+};
+
+using Parts = std::vector<std::vector<int32_t>>;
+
+Parts plan_rows(const std::vector<int32_t>& sets, int L, int npx, int npy, int64_t M, int64_t nT) {
+  Parts parts;
+  Stamps st(nT);
+  int32_t id = 0;
+  int64_t size = 0;
+  std::vector<int32_t> cur;
+  for (int q = 0; q < npx * npy; ++q) {
+    const int32_t* t = &sets[static_cast<size_t>(q) * L];
+    if (!cur.empty() && size + st.fresh(t, L, id) > M) {
+      parts.push_back(cur);
+      cur.clear();
+      ++id;
+      size = 0;
+    }
+    cur.push_back(q);
+    size += st.add(t, L, id);
+  }
+  if (!cur.empty()) parts.push_back(cur);
+  return parts;
+}
+
+Parts tiles(int npx, int npy, int w, int h, bool column_major) {
+  Parts out;
+  std::vector<std::pair<int, int>> org;
+  if (column_major) {
+    for (int x0 = 0; x0 < npx; x0 += w)
+      for (int y0 = 0; y0 < npy; y0 += h) org.emplace_back(x0, y0);
+  } else {
+    for (int y0 = 0; y0 < npy; y0 += h)
+      for (int x0 = 0; x0 < npx; x0 += w) org.emplace_back(x0, y0);
+  }
+  for (auto [x0, y0] : org) {
+    std::vector<int32_t> t;
+    for (int b = y0; b < std::min(y0 + h, npy); ++b)
+      for (int a = x0; a < std::min(x0 + w, npx); ++a) t.push_back(b * npx + a);
+    out.push_back(t);
+  }
+  return out;
+}
+
+Parts plan_rectangles(const std::vector<int32_t>& sets, int L, int npx, int npy, int64_t M, int64_t nT,
+                      bool column_major, int per_x, int per_y) {
+  Stamps st(nT);
+  int32_t gen = 0;
+  auto fits = [&](int w, int h) {
+    for (int ay = 0; ay < per_y; ++ay)
+      for (int ax = 0; ax < per_x; ++ax) {
+        ++gen;
+        int64_t size = 0;
+        for (int b = ay; b < std::min(ay + h, npy); ++b)
+          for (int a = ax; a < std::min(ax + w, npx); ++a)
+            size += st.add(&sets[static_cast<size_t>(b * npx + a) * L], L, gen);
+        if (size > M) return false;
+      }
+    return true;
+  };
+  int64_t best_area = -1;
+  int best_sq = 0, best_w = 1, best_h = 1;
+  for (int w = 1; w <= npx; ++w) {
+    if (!fits(w, 1)) break;
+    int h = 1;
+    while (h < npy && fits(w, h + 1)) ++h;
+    const int64_t area = static_cast<int64_t>(w) * h;
+    const int sq = -std::abs(w - h);
+    // key (area, -|w - h|, w), strictly greater replaces
+    if (area > best_area || (area == best_area && (sq > best_sq || (sq == best_sq && w > best_w)))) {
+      best_area = area;
+      best_sq = sq;
+      best_w = w;
+      best_h = h;
+    }
+  }
+  return tiles(npx, npy, best_w, best_h, column_major);
+}
+
+Parts plan_greedy(const std::vector<int32_t>& sets, int L, int npx, int npy, int64_t M, int64_t nT, int start) {
+  const int n = npx * npy;
+  std::vector<uint8_t> assigned(n, 0);
+  Parts parts;
+  std::vector<int32_t> cur;
+  Stamps st(nT);
+  int32_t id = 0;
+  int64_t size = 0, done = 0;
+  int nxt = start, scan = 0;
+  while (true) {
+    const int q = nxt;
+    const int32_t* t = &sets[static_cast<size_t>(q) * L];
+    if (!cur.empty() && size + st.fresh(t, L, id) > M) {
+      parts.push_back(cur);
+      cur.clear();
+      ++id;
+      size = 0;
+    }
+    cur.push_back(q);
+    size += st.add(t, L, id);
+    assigned[q] = 1;
+    if (++done == n) break;
+    const int a = q % npx, b = q / npx;
+    int64_t best = -1;
+    int bb_best = 0, aa_best = 0;
+    for (int bb = b - 1; bb <= b + 1; ++bb)
+      for (int aa = a - 1; aa <= a + 1; ++aa) {
+        if (aa < 0 || aa >= npx || bb < 0 || bb >= npy || assigned[bb * npx + aa]) continue;
+        const int64_t c = size + st.fresh(&sets[static_cast<size_t>(bb * npx + aa) * L], L, id);
+        // (cost, b, a) ascending; candidates arrive in (b, a) order, so ties keep the first
+        if (best < 0 || c < best) {
+          best = c;
+          bb_best = bb;
+          aa_best = aa;
+        }
+      }
+    if (best >= 0) {
+      nxt = bb_best * npx + aa_best;
+    } else {
+      while (assigned[scan]) ++scan;
+      nxt = scan;
+    }
+  }
+  parts.push_back(cur);
+  return parts;
+}
+
+// T_{P_1..P_l} and max |I(P_j)|
+void plan_cost(const std::vector<int32_t>& sets, int L, const Parts& parts, int64_t nT, int64_t* runs, int64_t* peak) {
+  Stamps st(nT);
+  int64_t T = 0, pk = 0;
+  for (size_t j = 0; j < parts.size(); ++j) {
+    int64_t size = 0, shared = 0;
+    // translates stamped with j - 1 belong to the previous part's union
+    for (int32_t q : parts[j]) {
+      const int32_t* t = &sets[static_cast<size_t>(q) * L];
+      for (int k = 0; k < L; ++k) {
+        if (st.mark[t[k]] == static_cast<int32_t>(j)) continue;
+        if (j > 0 && st.mark[t[k]] == static_cast<int32_t>(j) - 1) ++shared;
+        st.mark[t[k]] = static_cast<int32_t>(j);
+        ++size;
+      }
+    }
+    T += size - shared;
+    pk = std::max(pk, size);
+  }
+  *runs = T;
+  *peak = pk;
+}
+
+int gcd_int(int a, int b) {
+  while (b) {
+    const int t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+}  // namespace
+
+static lma_status validate_partition(lma_ctx* ctx, const lma_basis* b, const lma_region* r,
+                                     const lma_partition_desc* d) {
+  if (!d) return fail(ctx, LMA_ERR_INVALID, "null partition descriptor");
+  if (d->strategy < LMA_PART_ROWS || d->strategy > LMA_PART_GREEDY)
+    return fail(ctx, LMA_ERR_INVALID, "unknown partition strategy %d", d->strategy);
+  if (d->max_resident < b->desc.L) return fail(ctx, LMA_ERR_INVALID, "max_resident must be at least L");
+  if (d->strategy == LMA_PART_GREEDY &&
+      (d->start < 0 || static_cast<int64_t>(d->start) >= static_cast<int64_t>(r->npx) * r->npy))
+    return fail(ctx, LMA_ERR_INVALID, "greedy start outside the region");
+  return LMA_OK;
+}
+
+// the partition of a region (cached in the basis with its cost)
+static lma_status make_plan(lma_basis* b, const lma_region* r, const lma_partition_desc* d) {
+  if (b->plan_valid && std::memcmp(&b->plan_r, r, sizeof(lma_region)) == 0 &&
+      std::memcmp(&b->plan_d, d, sizeof(lma_partition_desc)) == 0)
+    return LMA_OK;
+  std::vector<int32_t> tidx, sh;
+  std::vector<float> al;
+  lma_status s = region_tables_host(b, r, tidx, al, sh);
+  if (s != LMA_OK) return s;
+  const int L = b->desc.L;
+  Parts parts;
+  if (d->strategy == LMA_PART_ROWS) {
+    parts = plan_rows(tidx, L, r->npx, r->npy, d->max_resident, b->nT);
+  } else if (d->strategy == LMA_PART_GREEDY) {
+    parts = plan_greedy(tidx, L, r->npx, r->npy, d->max_resident, b->nT, d->start);
+  } else {
+    // the probe/lattice geometry repeats every S / gcd(S, s) probes per axis
+    const int per_x = b->Sx / gcd_int(b->Sx, r->spacing_px[0]);
+    const int per_y = b->Sy / gcd_int(b->Sy, r->spacing_px[1]);
+    parts = plan_rectangles(tidx, L, r->npx, r->npy, d->max_resident, b->nT,
+                            d->strategy == LMA_PART_RECTANGLES_COLUMN_MAJOR, per_x, per_y);
+  }
+  plan_cost(tidx, L, parts, b->nT, &b->plan_runs, &b->plan_peak);
+  // store entries: each part keeps the previous part's waves it shares, new waves take
+  // the entries freed by the previous part (lowest first). The device tables of every part
+  // go into one buffer (32-bit words): probes, store entries of the probes' translates,
+  // coefficients (float pairs), placements (int pairs), new items and their entries.
+  std::vector<int32_t> entry_of(static_cast<size_t>(b->nT), -1);
+  std::vector<int32_t> free_entries;
+  for (int64_t e = d->max_resident - 1; e >= 0; --e) free_entries.push_back(static_cast<int32_t>(e));
+  std::vector<int32_t> prev, tab;
+  auto align4 = [&]() {
+    while (tab.size() % 4) tab.push_back(0);
+  };
+  Stamps st(b->nT);
+  b->parts.clear();
+  for (size_t j = 0; j < parts.size(); ++j) {
+    const int32_t id = static_cast<int32_t>(j);
+    std::vector<int32_t> uni;
+    for (int32_t q : parts[j])
+      for (int k = 0; k < L; ++k) {
+        const int32_t t = tidx[static_cast<size_t>(q) * L + k];
+        if (st.mark[t] != id) {
+          st.mark[t] = id;
+          uni.push_back(t);
+        }
+      }
+    for (int32_t t : prev)
+      if (st.mark[t] != id) {
+        free_entries.push_back(entry_of[t]);
+        entry_of[t] = -1;
+      }
+    std::sort(free_entries.begin(), free_entries.end(), std::greater<int32_t>());
+    std::sort(uni.begin(), uni.end());
+    lma_basis::Part P;
+    P.probes = parts[j];
+    std::vector<int32_t> fresh;
+    for (int32_t t : uni)
+      if (entry_of[t] < 0) {
+        entry_of[t] = free_entries.back();
+        free_entries.pop_back();
+        fresh.push_back(t);
+      }
+    for (int pass = 0; pass < 2; ++pass)
+      for (int32_t t : fresh)
+        if (origin_even(b, t) == (pass == 0)) {
+          P.items.push_back(t);
+          P.outs.push_back(entry_of[t]);
+          if (pass == 0) ++P.n_even;
+        }
+    align4();
+    P.o_probes = tab.size();
+    tab.insert(tab.end(), P.probes.begin(), P.probes.end());
+    align4();
+    P.o_tidx = tab.size();
+    for (int32_t q : P.probes)
+      for (int k = 0; k < L; ++k) tab.push_back(entry_of[tidx[static_cast<size_t>(q) * L + k]]);
+    align4();
+    P.o_alpha = tab.size();
+    for (int32_t q : P.probes)
+      for (int k = 0; k < 2 * L; ++k) {
+        int32_t w;
+        std::memcpy(&w, &al[static_cast<size_t>(q) * 2 * L + k], sizeof(w));
+        tab.push_back(w);
+      }
+    align4();
+    P.o_shift = tab.size();
+    for (int32_t q : P.probes)
+      for (int k = 0; k < 2 * L; ++k) tab.push_back(sh[static_cast<size_t>(q) * 2 * L + k]);
+    align4();
+    P.o_items = tab.size();
+    tab.insert(tab.end(), P.items.begin(), P.items.end());
+    align4();
+    P.o_outs = tab.size();
+    tab.insert(tab.end(), P.outs.begin(), P.outs.end());
+    b->parts.push_back(std::move(P));
+    prev.swap(uni);
+  }
+  b->plan_tab.swap(tab);
+  b->plan_r = *r;
+  b->plan_d = *d;
+  b->plan_valid = true;
+  b->plan_dev = false;
+  return LMA_OK;
+}
+
+lma_status lma_partition(lma_ctx* ctx, lma_basis* b, const lma_region* region, const lma_partition_desc* desc,
+                         int32_t* part, int32_t* n_parts, int64_t* runs, int64_t* peak) {
+  if (!ctx || !b || !region) return fail(ctx, LMA_ERR_INVALID, "null argument");
+  lma_status s = validate_region(ctx, b, region);
+  if (s != LMA_OK) return s;
+  if ((s = validate_partition(ctx, b, region, desc)) != LMA_OK) return s;
+  if ((s = make_plan(b, region, desc)) != LMA_OK) return s;
+  if (part)
+    for (size_t j = 0; j < b->parts.size(); ++j)
+      for (int32_t q : b->parts[j].probes) part[q] = static_cast<int32_t>(j);
+  if (n_parts) *n_parts = static_cast<int32_t>(b->parts.size());
+  if (runs) *runs = b->plan_runs;
+  if (peak) *peak = b->plan_peak;
+  return LMA_OK;
+}
+
+lma_status lma_image_partitioned(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, const lma_detector* det,
+                                 int32_t n_det, const lma_region* region, const lma_partition_desc* desc,
+                                 uint32_t flags, double* out, void* stream) {
+  if (!ctx || !sp || !b || !out || !region) return fail(ctx, LMA_ERR_INVALID, "null argument");
+  if (b->spec != sp) return fail(ctx, LMA_ERR_INVALID, "basis belongs to another specimen");
+  if (n_det <= 0 || n_det > lma_dev::kMaxDet || !det)
+    return fail(ctx, LMA_ERR_INVALID, "need 1..%d detectors", lma_dev::kMaxDet);
+  for (int d = 0; d < n_det; ++d)
+    if (!(det[d].r1 >= 0) || !(det[d].r2 > det[d].r1)) return fail(ctx, LMA_ERR_INVALID, "detector %d: need 0 <= r1 < r2", d);
+  lma_status s = validate_region(ctx, b, region);
+  if (s != LMA_OK) return s;
+  if ((s = validate_partition(ctx, b, region, desc)) != LMA_OK) return s;
+  if (!device_ready(ctx)) return fail(ctx, LMA_ERR_UNSUPPORTED, "no device in this context");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((s = ensure_basis_tables(b, st)) != LMA_OK) return s;
+  if ((s = build_detectors(b, det, n_det, st)) != LMA_OK) return s;
+  if ((s = make_plan(b, region, desc)) != LMA_OK) return s;
+  const bool half = b->desc.precision == LMA_PREC_MIXED;
+  const int64_t M = std::min<int64_t>(desc->max_resident, b->nT);   // entries in use never exceed |I_f|
+  if (!b->plan_dev) {
+    CUDA_TRY(ctx, ensure(b->d_plan, std::max<size_t>(4, b->plan_tab.size() * sizeof(int32_t))));
+    CUDA_TRY(ctx, upload(ctx, b->d_plan.p, b->plan_tab.data(), b->plan_tab.size() * sizeof(int32_t), st));
+    b->plan_dev = true;
+  }
+  CUDA_TRY(ctx, ensure(b->d_Up, static_cast<size_t>(M) * kW * kW * (half ? 4 : sizeof(float2))));
+  if (half) CUDA_TRY(ctx, ensure(b->d_Upscale, static_cast<size_t>(M) * sizeof(float)));
+  if (!ctx->d_counter) CUDA_TRY(ctx, counted_malloc(reinterpret_cast<void**>(&ctx->d_counter), sizeof(int)));
+  const int nph = static_cast<int>(sp->ph.size());
+  const int64_t np = static_cast<int64_t>(region->npx) * region->npy;
+  const int64_t nout = np * n_det;
+  CUDA_TRY(ctx, ensure(b->d_acc, static_cast<size_t>(nout) * (nph + 1) * sizeof(double)));
+  const int32_t* tab = static_cast<const int32_t*>(b->d_plan.p);
+  AutotuneScope tuning(ctx, (flags & LMA_IMAGE_AUTOTUNE) != 0);
+  for (int phi = 0; phi < nph; ++phi) {
+    // transmission of this configuration in slot 0 (rebuilt: the bounded path keeps nothing)
+    if ((s = reserve_t_slots(sp, 1)) != LMA_OK) return s;
+    if ((s = ensure_t(sp, 0, phi, true, st)) != LMA_OK) return s;
+    for (const lma_basis::Part& P : b->parts) {
+      lma_dev::SliceLaunch Lh{};
+      Lh.n_jobs = 1;
+      Lh.job[0] = make_job(b, sp);
+      Lh.job[0].U = half ? nullptr : static_cast<float2*>(b->d_Up.p);
+      Lh.job[0].Uh = half ? b->d_Up.p : nullptr;
+      Lh.job[0].Uscale = half ? static_cast<float*>(b->d_Upscale.p) : nullptr;
+      Lh.job[0].u_slot = static_cast<size_t>(M) * kW * kW;
+      Lh.counter = ctx->d_counter;
+      for (int part = 0; part < 2; ++part) {
+        const int off = part == 0 ? 0 : P.n_even;
+        const int cnt = part == 0 ? P.n_even : static_cast<int>(P.items.size()) - P.n_even;
+        if (cnt == 0) continue;
+        Lh.list = tab + P.o_items + off;
+        Lh.out_index = tab + P.o_outs + off;
+        Lh.n_list = cnt;
+        Lh.start[0] = 0;
+        Lh.start[1] = cnt;
+        if ((s = slice_launch(ctx, Lh, part == 0, half, static_cast<int64_t>(cnt) * sp->g.n_slices, st)) != LMA_OK)
+          return s;
+      }
+      lma_dev::SynthArgs a{};
+      a.U = half ? nullptr : static_cast<const float2*>(b->d_Up.p);
+      a.Uh = half ? b->d_Up.p : nullptr;
+      a.Uscale = half ? static_cast<const float*>(b->d_Upscale.p) : nullptr;
+      a.tidx = tab + P.o_tidx;
+      a.alpha = reinterpret_cast<const float2*>(tab + P.o_alpha);
+      a.shift = reinterpret_cast<const int2*>(tab + P.o_shift);
+      a.L = b->desc.L;
+      a.n_probes = static_cast<int>(np);
+      a.probe_list = tab + P.o_probes;
+      a.n_list = static_cast<int>(P.probes.size());
+      a.npx = region->npx;
+      a.npy = region->npy;
+      a.strip = kSynthStrip;
+      a.n_cfg = 1;
+      a.cfg_base = phi;
+      a.n_translates = static_cast<int>(M);
+      a.u_slot = static_cast<size_t>(M) * kW * kW;
+      a.cyclic = (b->nx == kW && b->ny == kW) ? 1 : 0;
+      a.det_bits = static_cast<const uint32_t*>(b->d_det.p);
+      a.n_det = n_det;
+      a.acc = static_cast<double*>(b->d_acc.p);
+      a.band_r2 = b->r2max;
+      CUDA_TRY(ctx, counted(ctx, K_SYNTH, static_cast<int64_t>(P.probes.size()), st,
+                            [&] { return lma_dev::launch_synth(a, half, lma_dev::kReadAnnuli, st); }));
+    }
+  }
+  const double* acc = static_cast<const double*>(b->d_acc.p);
+  const bool dev_out = is_device_pointer(out);
+  double* fin = dev_out ? out : static_cast<double*>(b->d_acc.p) + static_cast<size_t>(nph) * nout;
+  CUDA_TRY(ctx, counted(ctx, K_FIN, nout, st, [&] { return lma_dev::launch_finalize(acc, nout, nph, 1.0 / nph, fin, st); }));
+  if (!dev_out) CUDA_TRY(ctx, read_back(ctx, out, fin, static_cast<size_t>(nout) * sizeof(double), st));
+  CUDA_TRY(ctx, cudaGetLastError());
+  return LMA_OK;
+}
+
+// common steps of the 3D and 4D images: checks, tables, device work, read-back
+static lma_status image_readout(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, const Readout& ro, const lma_region* region,
+                         uint32_t flags, void* out, size_t out_bytes, cudaStream_t st) {
+  lma_status s = validate_region(ctx, b, region);
+  if (s != LMA_OK) return s;
+  if (!device_ready(ctx)) return fail(ctx, LMA_ERR_UNSUPPORTED, "no device in this context");
+  if ((s = ensure_basis_device(b, st)) != LMA_OK) return s;
+  if ((s = build_region(b, region, st)) != LMA_OK) return s;
+  const bool dev_out = is_device_pointer(out);
+  AutotuneScope tuning(ctx, (flags & LMA_IMAGE_AUTOTUNE) != 0);
+  if ((s = images_work(ctx, {ImageJob{b, sp, dev_out ? out : nullptr}}, ro, (flags & LMA_IMAGE_RECOMPUTE) != 0,
+                       st)) != LMA_OK)
+    return s;
+  if (!dev_out) {
+    const void* fin = ro.mode == lma_dev::kReadPattern ? b->d_pat.p : static_cast<const void*>(basis_result(b, sp, ro.n_out));
+    CUDA_TRY(ctx, read_back(ctx, out, fin, out_bytes, st));
+  }
+  CUDA_TRY(ctx, cudaGetLastError());
+  return LMA_OK;
+}
+
+lma_status lma_image_rings(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, double ring_width, int32_t n_rings,
+                           const lma_region* region, uint32_t flags, double* out, void* stream) {
+  if (!ctx || !sp || !b || !out || !region) return fail(ctx, LMA_ERR_INVALID, "null argument");
+  if (b->spec != sp) return fail(ctx, LMA_ERR_INVALID, "basis belongs to another specimen");
+  if (!(ring_width > 0) || !std::isfinite(ring_width)) return fail(ctx, LMA_ERR_INVALID, "ring width must be positive");
+  if (n_rings < 1 || n_rings > LMA_MAX_RINGS) return fail(ctx, LMA_ERR_INVALID, "need 1..%d rings", LMA_MAX_RINGS);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!device_ready(ctx)) return fail(ctx, LMA_ERR_UNSUPPORTED, "no device in this context");
+  lma_status s = build_labels(b, ring_width, n_rings, st);
+  if (s != LMA_OK) return s;
+  Readout ro;
+  ro.mode = lma_dev::kReadLabels;
+  ro.n_out = n_rings;
+  const size_t bytes = static_cast<size_t>(region->npx) * region->npy * n_rings * sizeof(double);
+  return image_readout(ctx, sp, b, ro, region, flags, out, bytes, st);
+}
+
+lma_status lma_image_4d(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, int32_t half_x, int32_t half_y,
+                        const lma_region* region, uint32_t flags, float* out, void* stream) {
+  if (!ctx || !sp || !b || !out || !region) return fail(ctx, LMA_ERR_INVALID, "null argument");
+  if (b->spec != sp) return fail(ctx, LMA_ERR_INVALID, "basis belongs to another specimen");
+  const int lim = b->desc.det_window / 2 - 1;
+  if (half_x < 0 || half_y < 0 || half_x > lim || half_y > lim)
+    return fail(ctx, LMA_ERR_INVALID, "pattern half-widths must lie in 0..%d", lim);
+  Readout ro;
+  ro.mode = lma_dev::kReadPattern;
+  ro.pat_a = half_x;
+  ro.pat_b = half_y;
+  if (static_cast<int64_t>(region->npx) * region->npy * ro.pat_size() > (int64_t(1) << 34))
+    return fail(ctx, LMA_ERR_INVALID, "4D output too large");
+  const size_t bytes = static_cast<size_t>(region->npx) * region->npy * ro.pat_size() * sizeof(float);
+  return image_readout(ctx, sp, b, ro, region, flags, out, bytes, static_cast<cudaStream_t>(stream));
+}
+
 lma_status lma_image_many(lma_ctx* ctx, int32_t n, lma_specimen* const* specs, lma_basis* const* bases,
                           const lma_detector* det, int32_t n_det, const lma_region* regions, uint32_t flags,
                           double* const* outs, void* stream) {
@@ -1531,8 +2174,10 @@ lma_status lma_image_many(lma_ctx* ctx, int32_t n, lma_specimen* const* specs, l
     jobs.push_back(ImageJob{bases[k], specs[k], dev_out[k] ? outs[k] : nullptr});
   }
   AutotuneScope tuning(ctx, (flags & LMA_IMAGE_AUTOTUNE) != 0);
+  Readout ro;
+  ro.n_out = n_det;
   if (!graph) {
-    if ((s = images_work(ctx, jobs, n_det, recompute, st)) != LMA_OK) return s;
+    if ((s = images_work(ctx, jobs, ro, recompute, st)) != LMA_OK) return s;
     for (int k = 0; k < n; ++k)
       if (!dev_out[k]) {
         const int64_t nout = bases[k]->reg.n_probes * n_det;
@@ -1596,7 +2241,7 @@ lma_status lma_image_many(lma_ctx* ctx, int32_t n, lma_specimen* const* specs, l
     }
   // first call with these buffers: an ordinary run (allocations, list uploads, tuning,
   // outputs), then the same launches captured for later calls
-  if ((s = images_work(ctx, jobs, n_det, true, st)) != LMA_OK) return s;
+  if ((s = images_work(ctx, jobs, ro, true, st)) != LMA_OK) return s;
   CUDA_TRY(ctx, cudaStreamSynchronize(st));
   key = signature();
   lma_ctx::Graph g;
@@ -1604,7 +2249,7 @@ lma_status lma_image_many(lma_ctx* ctx, int32_t n, lma_specimen* const* specs, l
   ctx->capture_lists.clear();
   CUDA_TRY(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   ctx->capturing = true;
-  lma_status cs = images_work(ctx, jobs, n_det, true, st);
+  lma_status cs = images_work(ctx, jobs, ro, true, st);
   ctx->capturing = false;
   cudaError_t e = cudaStreamEndCapture(st, &g.graph);
   g.lists.swap(ctx->capture_lists);
@@ -1827,7 +2472,7 @@ lma_status lma_readout_noalloc(lma_ctx* ctx, lma_basis* b, const float* exit_wav
   a.det_bits = reinterpret_cast<const uint32_t*>(base + o_det);
   a.n_det = n_det;
   a.acc = reinterpret_cast<double*>(base + o_acc);
-  CUDA_TRY(ctx, lma_dev::launch_synth(a, false, st));
+  CUDA_TRY(ctx, lma_dev::launch_synth(a, false, lma_dev::kReadAnnuli, st));
   CUDA_TRY(ctx, lma_dev::launch_finalize(a.acc, nout, 1, 1.0, out, st));
   // the host tables above are pageable: keep them alive until the copies have run
   CUDA_TRY(ctx, cudaStreamSynchronize(st));
@@ -1843,6 +2488,7 @@ lma_status lma_profile_enable(lma_ctx* ctx, int32_t on) {
   }
   ctx->pend.clear();
   for (auto& k : ctx->stat) k = lma_kernel_stat{};
+  ctx->alloc_base = g_allocations.load(std::memory_order_relaxed);
   ctx->prof = on != 0 && !ctx->host_only;
   return LMA_OK;
 }
@@ -1862,6 +2508,7 @@ lma_status lma_profile_read(lma_ctx* ctx, lma_profile* out) {
   out->slice = ctx->stat[K_SLICE];
   out->synth = ctx->stat[K_SYNTH];
   out->finalize = ctx->stat[K_FIN];
+  out->allocations = g_allocations.load(std::memory_order_relaxed) - ctx->alloc_base;
   return LMA_OK;
 }
 

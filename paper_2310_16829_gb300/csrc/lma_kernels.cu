@@ -509,12 +509,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
       int e = 0;
       if (mx > 0.f) frexpf(mx, &e);
       const float sc = ldexpf(1.f, -e);
-      __half2* uh = static_cast<__half2*>(J.Uh) + cfg * J.u_slot + static_cast<size_t>(ti) * (kW * kW) + ya * kW + ra;
+      const int oi = a.out_index ? a.out_index[li] : ti;
+      __half2* uh = static_cast<__half2*>(J.Uh) + cfg * J.u_slot + static_cast<size_t>(oi) * (kW * kW) + ya * kW + ra;
 #pragma unroll
       for (int n1 = 0; n1 < 32; ++n1) uh[4 * n1] = __floats2half2_rn(v[n1].x * sc, v[n1].y * sc);
-      if (T == 0) J.Uscale[static_cast<size_t>(cfg) * J.n_translates + ti] = ldexpf(1.f, e);
+      if (T == 0) J.Uscale[static_cast<size_t>(cfg) * J.n_translates + oi] = ldexpf(1.f, e);
     } else {
-      float2* ud = J.U + cfg * J.u_slot + static_cast<size_t>(ti) * (kW * kW) + ya * kW + ra;
+      const int oi = a.out_index ? a.out_index[li] : ti;
+      float2* ud = J.U + cfg * J.u_slot + static_cast<size_t>(oi) * (kW * kW) + ya * kW + ra;
 #pragma unroll
       for (int n1 = 0; n1 < 32; ++n1) ud[4 * n1] = v[n1];
     }
@@ -540,8 +542,10 @@ __device__ __forceinline__ int probe_of(int q, int npx, int npy, int sw) {
   return (r / w) * npx + x0 + (r - (r / w) * w);
 }
 
-// HALF reads the FP16 store and folds each wave's factor into its coefficient.
-template <bool HALF>
+// HALF reads the FP16 store and folds each wave's factor into its coefficient. MODE
+// selects the readout (ReadMode): 2D annuli, labelled pixel sets (3D STEM rings) or the
+// diffraction pattern on a centred crop (4D STEM).
+template <bool HALF, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a) {
   extern __shared__ __align__(16) float2 sm[];
   float2* R0 = sm;
@@ -562,28 +566,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
   float2* const x2c = R0 + (k1y * 4 + k2x) * 1024 + k1x;
   uint32_t dbits[kMaxDet];
   uint32_t any_bits = 0u;
+  const int kxs = kx < 64 ? kx : kx - 128;
+  if constexpr (MODE == kReadAnnuli) {
 #pragma unroll
-  for (int d = 0; d < kMaxDet; ++d) {
-    dbits[d] = d < a.n_det ? a.det_bits[d * kThreads + kx + 128 * k1y] : 0u;
-    any_bits |= dbits[d];
+    for (int d = 0; d < kMaxDet; ++d) {
+      dbits[d] = d < a.n_det ? a.det_bits[d * kThreads + kx + 128 * k1y] : 0u;
+      any_bits |= dbits[d];
+    }
+  } else {
+    // labels and the pattern cover in-band pixels only
+    any_bits = kxs * kxs <= a.band_r2 ? 1u : 0u;
   }
   // a warp whose columns meet no detector skips pass C
   const bool c_live = __any_sync(0xffffffffu, any_bits != 0u);
   __syncthreads();
 
-  const int n_items = a.n_probes * a.n_cfg;
+  const int n_walk = a.probe_list ? a.n_list : a.n_probes;
+  const int n_items = n_walk * a.n_cfg;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-    const int cfg = item / a.n_probes;
-    const int p = probe_of(item - cfg * a.n_probes, a.npx, a.npy, a.strip);
+    const int cfg = item / n_walk;
+    const int q = item - cfg * n_walk;
+    // p: the probe's region index (accumulator); tq: its row of the probe tables
+    const int p = a.probe_list ? a.probe_list[q] : probe_of(q, a.npx, a.npy, a.strip);
+    const int tq = a.probe_list ? q : p;
     const float2* const Uc = a.U ? a.U + cfg * a.u_slot : nullptr;
     const void* const Uhc = a.Uh ? static_cast<const void*>(static_cast<const __half2*>(a.Uh) + cfg * a.u_slot) : nullptr;
     const float* const Usc = a.Uscale ? a.Uscale + static_cast<size_t>(cfg) * a.n_translates : nullptr;
     float2 v[32];
 #pragma unroll
     for (int n1 = 0; n1 < 32; ++n1) v[n1] = make_float2(0.f, 0.f);
-    const int32_t* tp = a.tidx + static_cast<size_t>(p) * a.L;
-    const float2* ap = a.alpha + static_cast<size_t>(p) * a.L;
-    const int2* sp = a.shift + static_cast<size_t>(p) * a.L;
+    const int32_t* tp = a.tidx + static_cast<size_t>(tq) * a.L;
+    const float2* ap = a.alpha + static_cast<size_t>(tq) * a.L;
+    const int2* sp = a.shift + static_cast<size_t>(tq) * a.L;
     for (int j = 0; j < a.L; ++j) {
       float2 al = ap[j];
       const int2 sh = sp[j];
@@ -650,33 +664,108 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
       }
     __syncthreads();
     const int warp = T >> 5, lane = T & 31;
-    if (c_live) {
-      float2 c[32];
+    if constexpr (MODE == kReadAnnuli) {
+      if (c_live) {
+        float2 c[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) c[j] = x2c[j * 32];
-      dft32<false>(c);
-      // detector (Sec. 3.1, 2D STEM): sum of |DFT|^2 over the annulus
+        for (int j = 0; j < 32; ++j) c[j] = x2c[j * 32];
+        dft32<false>(c);
+        // detector (Sec. 3.1, 2D STEM): sum of |DFT|^2 over the annulus
 #pragma unroll
-      for (int d = 0; d < kMaxDet; ++d) {
-        if (d >= a.n_det) break;
+        for (int d = 0; d < kMaxDet; ++d) {
+          if (d >= a.n_det) break;
+          float sum = 0.f;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if ((dbits[d] >> j) & 1u) sum = fmaf(c[j].x, c[j].x, fmaf(c[j].y, c[j].y, sum));
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+          if (lane == 0) red[warp * kMaxDet + d] = sum;
+        }
+      } else if (lane < kMaxDet) {
+        red[warp * kMaxDet + lane] = 0.f;
+      }
+      __syncthreads();
+      if (T < a.n_det) {
+        double tot = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) tot += static_cast<double>(red[w * kMaxDet + T]);
+        a.acc[(static_cast<size_t>(a.cfg_base + cfg) * a.n_det + T) * a.n_probes + p] = tot * (1.0 / (kW * kW));
+      }
+    } else if constexpr (MODE == kReadLabels) {
+      // 3D STEM (Sec. 3.1): |DFT|^2 into a W x W plane, then each label's pixels summed by
+      // one warp in a fixed order (lane-strided partial sums, then a fixed shuffle tree)
+      float e[32];
+      if (c_live) {
+        float2 c[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) c[j] = x2c[j * 32];
+        dft32<false>(c);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) e[j] = fmaf(c[j].x, c[j].x, c[j].y * c[j].y);
+      }
+      __syncthreads();   // every X2 read of R0 is done: R0 becomes the plane
+      float* plane = reinterpret_cast<float*>(R0);
+      if (c_live) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) plane[(k1y + 4 * j) * kW + kx] = e[j];
+      }
+      __syncthreads();
+      for (int l = warp; l < a.n_det; l += kThreads / 32) {
+        const int s0 = a.lab_start[l], s1 = a.lab_start[l + 1];
         float sum = 0.f;
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if ((dbits[d] >> j) & 1u) sum = fmaf(c[j].x, c[j].x, fmaf(c[j].y, c[j].y, sum));
+        for (int i = s0 + lane; i < s1; i += 32) sum += plane[a.lab_pix[i]];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) red[warp * kMaxDet + d] = sum;
+        if (lane == 0)
+          a.acc[(static_cast<size_t>(a.cfg_base + cfg) * a.n_det + l) * a.n_probes + p] =
+              static_cast<double>(sum) * (1.0 / (kW * kW));
       }
-    } else if (lane < kMaxDet) {
-      red[warp * kMaxDet + lane] = 0.f;
-    }
-    __syncthreads();
-    if (T < a.n_det) {
-      double tot = 0.0;
-      for (int w = 0; w < kThreads / 32; ++w) tot += static_cast<double>(red[w * kMaxDet + T]);
-      a.acc[(static_cast<size_t>(a.cfg_base + cfg) * a.n_det + T) * a.n_probes + p] = tot * (1.0 / (kW * kW));
+    } else {
+      // 4D STEM (Sec. 3.1): the pattern |DFT|^2 / W^2 on |kx| <= pat_a, |ky| <= pat_b, zero
+      // outside the band, one FP32 slot per configuration
+      const int pw = 2 * a.pat_a + 1;
+      float* const out = a.pat + (static_cast<size_t>(cfg) * a.n_probes + p) * static_cast<size_t>(pw * (2 * a.pat_b + 1)) +
+                         a.pat_b * pw + kxs + a.pat_a;
+      const bool col = kxs >= -a.pat_a && kxs <= a.pat_a;
+      if (c_live) {
+        float2 c[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) c[j] = x2c[j * 32];
+        dft32<false>(c);
+        if (col) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int ky = k1y + 4 * j;
+            const int kys = ky < 64 ? ky : ky - 128;
+            if (kys >= -a.pat_b && kys <= a.pat_b)
+              out[kys * pw] = kxs * kxs + kys * kys <= a.band_r2
+                                  ? fmaf(c[j].x, c[j].x, c[j].y * c[j].y) * (1.f / (kW * kW))
+                                  : 0.f;
+          }
+        }
+      } else if (col) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int ky = k1y + 4 * j;
+          const int kys = ky < 64 ? ky : ky - 128;
+          if (kys >= -a.pat_b && kys <= a.pat_b) out[kys * pw] = 0.f;
+        }
+      }
     }
   }
+}
+
+__global__ void k_pattern_accumulate(const float* slots, int64_t n, int n_cfg, int first, double* acc) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = first ? 0.0 : acc[i];
+  for (int c = 0; c < n_cfg; ++c) s += static_cast<double>(slots[static_cast<size_t>(c) * n + i]);
+  acc[i] = s;
+}
+
+__global__ void k_pattern_finalize(const double* acc, int64_t n, double scale, float* out) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = static_cast<float>(acc[i] * scale);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -832,8 +921,11 @@ cudaError_t init_device_constants() {
   if ((e = cudaFuncSetAttribute(k_slice<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_slice<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_slice<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_synth_detect<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy)) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_synth_detect<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy);
+  for (auto f : {k_synth_detect<false, kReadAnnuli>, k_synth_detect<true, kReadAnnuli>,
+                 k_synth_detect<false, kReadLabels>, k_synth_detect<true, kReadLabels>,
+                 k_synth_detect<false, kReadPattern>, k_synth_detect<true, kReadPattern>})
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sy)) != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
 cudaError_t launch_potential(const PotArgs& a, cudaStream_t s) {
@@ -874,13 +966,31 @@ cudaError_t launch_slice(const SliceLaunch& a, bool even_origins, bool half, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_synth(const SynthArgs& a, bool half, cudaStream_t s) {
-  if (a.n_probes <= 0) return cudaSuccess;
-  const int grid = a.n_probes * a.n_cfg;
-  if (half)
-    k_synth_detect<true><<<grid, kThreads, synth_smem_bytes(), s>>>(a);
-  else
-    k_synth_detect<false><<<grid, kThreads, synth_smem_bytes(), s>>>(a);
+cudaError_t launch_synth(const SynthArgs& a, bool half, int mode, cudaStream_t s) {
+  const int n_walk = a.probe_list ? a.n_list : a.n_probes;
+  if (n_walk <= 0) return cudaSuccess;
+  const int grid = n_walk * a.n_cfg;
+  const size_t sm = synth_smem_bytes();
+  if (mode == kReadAnnuli && half) k_synth_detect<true, kReadAnnuli><<<grid, kThreads, sm, s>>>(a);
+  else if (mode == kReadAnnuli) k_synth_detect<false, kReadAnnuli><<<grid, kThreads, sm, s>>>(a);
+  else if (mode == kReadLabels && half) k_synth_detect<true, kReadLabels><<<grid, kThreads, sm, s>>>(a);
+  else if (mode == kReadLabels) k_synth_detect<false, kReadLabels><<<grid, kThreads, sm, s>>>(a);
+  else if (mode == kReadPattern && half) k_synth_detect<true, kReadPattern><<<grid, kThreads, sm, s>>>(a);
+  else if (mode == kReadPattern) k_synth_detect<false, kReadPattern><<<grid, kThreads, sm, s>>>(a);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pattern_accumulate(const float* slots, int64_t n, int n_cfg, bool first, double* acc,
+                                      cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_pattern_accumulate<<<static_cast<int>((n + 255) / 256), 256, 0, s>>>(slots, n, n_cfg, first ? 1 : 0, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pattern_finalize(const double* acc, int64_t n, double scale, float* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_pattern_finalize<<<static_cast<int>((n + 255) / 256), 256, 0, s>>>(acc, n, scale, out);
   return cudaGetLastError();
 }
 

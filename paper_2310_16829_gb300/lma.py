@@ -35,8 +35,13 @@ LMA_PREC_MIXED = 1
 LMA_EDIT_REMOVE = 0
 LMA_EDIT_SET_SPECIES = 1
 LMA_IMAGE_RECOMPUTE = 1
+LMA_MAX_RINGS = 256
 LMA_IMAGE_GRAPH = 2
 LMA_IMAGE_AUTOTUNE = 4
+LMA_PART_ROWS = 0
+LMA_PART_RECTANGLES = 1
+LMA_PART_RECTANGLES_COLUMN_MAJOR = 2
+LMA_PART_GREEDY = 3
 LMA_SLICE_AUTO = -1
 LMA_SLICE_ONE_PER_ITEM = 0
 LMA_SLICE_PERSISTENT = 1
@@ -49,9 +54,10 @@ EXPORTS = [
     "lma_create_specimen", "lma_free_specimen", "lma_specimen_set_atoms", "lma_transmission",
     "lma_create_basis", "lma_free_basis", "lma_basis_get_info", "lma_basis_coefficients",
     "lma_propagate_basis", "lma_exit_wave",
-    "lma_image", "lma_image_many", "lma_edit_column", "lma_affected_probes",
+    "lma_image", "lma_image_rings", "lma_image_4d", "lma_image_many", "lma_edit_column",
+    "lma_affected_probes",
     "lma_profile_enable", "lma_profile_read", "lma_readout_noalloc",
-    "lma_set_slice_mode", "lma_tuning_read",
+    "lma_set_slice_mode", "lma_tuning_read", "lma_partition", "lma_image_partitioned",
 ]
 
 
@@ -92,6 +98,10 @@ class Region(C.Structure):
                 ("spacing_px", C.c_int32 * 2)]
 
 
+class PartitionDesc(C.Structure):
+    _fields_ = [("strategy", C.c_int32), ("start", C.c_int32), ("max_resident", C.c_int64)]
+
+
 class BasisInfo(C.Structure):
     _fields_ = [("n_translates", C.c_int64), ("nax", C.c_int32), ("nay", C.c_int32),
                 ("n_sets", C.c_int32), ("L", C.c_int32), ("window", C.c_int32),
@@ -105,11 +115,13 @@ class KernelStat(C.Structure):
 
 class Profile(C.Structure):
     _fields_ = [("potential", KernelStat), ("slice", KernelStat), ("synth", KernelStat),
-                ("finalize", KernelStat)]
+                ("finalize", KernelStat), ("allocations", C.c_int64)]
 
     def as_dict(self):
-        return {k: {"launches": int(getattr(self, k).launches), "total_ms": float(getattr(self, k).total_ms),
-                    "units": int(getattr(self, k).units)} for k, _ in self._fields_}
+        d = {k: {"launches": int(getattr(self, k).launches), "total_ms": float(getattr(self, k).total_ms),
+                 "units": int(getattr(self, k).units)} for k, _ in self._fields_ if k != "allocations"}
+        d["allocations"] = int(self.allocations)
+        return d
 
 
 class Tuning(C.Structure):
@@ -149,6 +161,10 @@ _SIGS = {
     "lma_exit_wave": (C.c_int32, [_VP, _VP, C.c_int64, _VP, _VP]),
     "lma_image": (C.c_int32, [_VP, _VP, _VP, C.POINTER(Detector), C.c_int32, C.POINTER(Region),
                               C.c_uint32, _VP, _VP]),
+    "lma_image_rings": (C.c_int32, [_VP, _VP, _VP, C.c_double, C.c_int32, C.POINTER(Region), C.c_uint32,
+                                    _VP, _VP]),
+    "lma_image_4d": (C.c_int32, [_VP, _VP, _VP, C.c_int32, C.c_int32, C.POINTER(Region), C.c_uint32, _VP,
+                                 _VP]),
     "lma_image_many": (C.c_int32, [_VP, C.c_int32, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(Detector),
                                    C.c_int32, C.POINTER(Region), C.c_uint32, C.POINTER(_VP), _VP]),
     "lma_edit_column": (C.c_int32, [_VP, _VP, _VP, C.c_double, C.c_double, C.c_double, C.c_int32,
@@ -157,6 +173,10 @@ _SIGS = {
     "lma_readout_noalloc": (C.c_int32, [_VP, _VP, _VP, C.POINTER(Detector), C.c_int32, C.POINTER(Region),
                                         _VP, _VP]),
     "lma_set_slice_mode": (C.c_int32, [_VP, C.c_int32]),
+    "lma_partition": (C.c_int32, [_VP, _VP, C.POINTER(Region), C.POINTER(PartitionDesc), _VP,
+                                  C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "lma_image_partitioned": (C.c_int32, [_VP, _VP, _VP, C.POINTER(Detector), C.c_int32, C.POINTER(Region),
+                                          C.POINTER(PartitionDesc), C.c_uint32, _VP, _VP]),
     "lma_tuning_read": (C.c_int32, [_VP, C.POINTER(Tuning), C.c_int32, C.POINTER(C.c_int32)]),
 }
 
@@ -382,6 +402,53 @@ class Basis:
         flags = (LMA_IMAGE_RECOMPUTE if recompute else 0) | (LMA_IMAGE_AUTOTUNE if autotune else 0)
         self.ctx.check(self.ctx.lib.lma_image(self.ctx.h, self.spec.h, self.h, dets, len(detectors),
                                               C.byref(reg), flags, _ptr(out), _stream(stream)))
+        return out
+
+    def image_rings(self, ring_width: float, n_rings: int, region, out=None, recompute: bool = False,
+                    stream=None):
+        """3D STEM image [n_rings][npy][npx]: ring a covers [a w, (a + 1) w) rad."""
+        if out is None:
+            out = np.empty((n_rings, region.npy, region.npx), dtype=np.float64)
+        reg = _region(region)
+        flags = LMA_IMAGE_RECOMPUTE if recompute else 0
+        self.ctx.check(self.ctx.lib.lma_image_rings(self.ctx.h, self.spec.h, self.h, ring_width, n_rings,
+                                                    C.byref(reg), flags, _ptr(out), _stream(stream)))
+        return out
+
+    def image_4d(self, half_x: int, half_y: int, region, out=None, recompute: bool = False, stream=None):
+        """4D STEM image [npy][npx][2 half_y + 1][2 half_x + 1] (float32)."""
+        if out is None:
+            out = np.empty((region.npy, region.npx, 2 * half_y + 1, 2 * half_x + 1), dtype=np.float32)
+        reg = _region(region)
+        flags = LMA_IMAGE_RECOMPUTE if recompute else 0
+        self.ctx.check(self.ctx.lib.lma_image_4d(self.ctx.h, self.spec.h, self.h, half_x, half_y,
+                                                 C.byref(reg), flags, _ptr(out), _stream(stream)))
+        return out
+
+    def partition(self, region, strategy: int, max_resident: int, start: int = 0):
+        """Partition of a probe region under a memory bound (Sec. 4.2.4): (part index per
+        probe [npy][npx], number of parts, Multislice runs T, peak resident waves)."""
+        part = np.empty((region.npy, region.npx), dtype=np.int32)
+        n = C.c_int32()
+        runs = C.c_int64()
+        peak = C.c_int64()
+        reg = _region(region)
+        d = PartitionDesc(strategy, start, max_resident)
+        self.ctx.check(self.ctx.lib.lma_partition(self.ctx.h, self.h, C.byref(reg), C.byref(d), _ptr(part),
+                                                  C.byref(n), C.byref(runs), C.byref(peak)))
+        return part, int(n.value), int(runs.value), int(peak.value)
+
+    def image_partitioned(self, detectors, region, strategy: int, max_resident: int, start: int = 0,
+                          out=None, stream=None):
+        """2D image with an exit-wave store of max_resident waves per configuration."""
+        dets = (Detector * len(detectors))(*[Detector(d.r1, d.r2) for d in detectors])
+        if out is None:
+            out = np.empty((len(detectors), region.npy, region.npx), dtype=np.float64)
+        reg = _region(region)
+        d = PartitionDesc(strategy, start, max_resident)
+        self.ctx.check(self.ctx.lib.lma_image_partitioned(self.ctx.h, self.spec.h, self.h, dets, len(detectors),
+                                                          C.byref(reg), C.byref(d), 0, _ptr(out),
+                                                          _stream(stream)))
         return out
 
     def readout_noalloc(self, exit_waves, detectors, region, out, stream=None):

@@ -24,13 +24,21 @@ request. Device allocation can synchronize the whole device, so an instance crea
 while other lanes' kernels are in flight would stall every lane once; with a warm pool
 that only happens when load grows past the pool.
 
+Hardware queues. The device runs CUDA_DEVICE_MAX_CONNECTIONS hardware work queues per
+process (8 unless set); streams beyond that share queues, and a kernel queued behind
+another stream's kernels in its queue cannot start before them (an edit then waits for a
+full image although its stream has priority). The environment variable has to be set
+before CUDA initializes; the server warns when it is below the number of instances + 1.
+
 This module holds host logic only; every computation runs in the CUDA library.
 """
 from __future__ import annotations
 
+import os
 import queue
 import threading
 import time
+import warnings
 from dataclasses import dataclass
 from typing import Callable, Dict, List, Optional
 
@@ -161,6 +169,11 @@ class Server:
                    self.reserved + lane.reserve_bytes <= self.budget):
                 lane.instances.append(Instance(lane, len(lane.instances), lane.reserve_bytes, warm=True))
                 self.reserved += lane.reserve_bytes
+        queues = int(os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8"))
+        wanted = sum(l.max_instances for l in lanes if l.max_instances < (1 << 20)) + 1
+        if queues < wanted:
+            warnings.warn(f"CUDA_DEVICE_MAX_CONNECTIONS={queues} is below {wanted} streams: lanes may "
+                          "wait for each other's kernels in shared hardware queues")
         for lane in lanes:
             for inst in lane.instances:
                 if not inst.ready.wait(warm_timeout):
@@ -279,9 +292,11 @@ def edit_lane(workload, device: int = 0, max_instances: int = 1, min_instances: 
 
 
 def image_lane(name: str, build: Callable[[int], object], device: int = 0,
-               max_instances: int = 4, min_instances: int = 0) -> Lane:
+               max_instances: int = 4, min_instances: int = 0, max_resident: Optional[int] = None) -> Lane:
     """Fresh specimens of one size: each request uploads its own seeded atoms
-    (lma_specimen_set_atoms) and computes the full image from scratch."""
+    (lma_specimen_set_atoms) and computes the full image from scratch. With max_resident
+    the image is computed part by part in a store of that many exit waves (Sec. 4.2.4),
+    using the partition strategy with the fewest Multislice runs for the lane's region."""
     from . import lma
     proto = build(0)
 
@@ -289,12 +304,21 @@ def image_lane(name: str, build: Callable[[int], object], device: int = 0,
         ctx = lma.Context(device)
         spec = lma.Specimen(ctx, proto.grid, proto.potential, proto.phonons)
         basis = lma.Basis(ctx, spec, proto.probe, proto.basis)
-        return {"ctx": ctx, "spec": spec, "basis": basis, "stream": _stream()}
+        state = {"ctx": ctx, "spec": spec, "basis": basis, "stream": _stream(), "strategy": None}
+        if max_resident:
+            runs = {st: basis.partition(proto.region, st, max_resident)[2]
+                    for st in (lma.LMA_PART_ROWS, lma.LMA_PART_RECTANGLES, lma.LMA_PART_GREEDY)}
+            state["strategy"] = min(runs, key=runs.get)
+        return state
 
     def handle(s, req: ImageRequest):
         w = build(req.seed)
         s["spec"].set_atoms(w.phonons)
-        img = s["basis"].image(w.detectors, w.region, recompute=True, stream=s["stream"])
+        if max_resident:
+            img = s["basis"].image_partitioned(w.detectors, w.region, s["strategy"], max_resident,
+                                               stream=s["stream"])
+        else:
+            img = s["basis"].image(w.detectors, w.region, recompute=True, stream=s["stream"])
         return img, 0
 
     def close(s):
@@ -306,18 +330,43 @@ def image_lane(name: str, build: Callable[[int], object], device: int = 0,
         handle(s, ImageRequest(name, seed=0))
         s["stream"].synchronize()
 
-    return Lane(name, make, handle, close, _footprint(proto), max_instances, min_instances, warm)
+    return Lane(name, make, handle, close, _footprint(proto, max_resident), max_instances, min_instances, warm)
 
 
-def _footprint(w) -> int:
-    """Device bytes an instance holds: exit-wave store, padded transmission, tables."""
+def _translates(w) -> int:
+    return (w.grid.nx // w.basis.in_spacing_px[0] // w.basis.f) * (w.grid.ny // w.basis.in_spacing_px[1] // w.basis.f)
+
+
+def _footprint(w, max_resident: Optional[int] = None) -> int:
+    """Device bytes an instance holds: exit-wave store (|I_f| waves, or max_resident of a
+    partitioned store), padded transmission, tables."""
     W = w.basis.window
-    nT = (w.grid.nx // w.basis.in_spacing_px[0] // w.basis.f) * (w.grid.ny // w.basis.in_spacing_px[1] // w.basis.f)
-    store = nT * W * W * (4 if getattr(w.basis, "precision", 0) else 8)
+    nT = _translates(w)
+    waves = min(nT, max_resident) if max_resident else nT
+    store = waves * W * W * (4 if getattr(w.basis, "precision", 0) else 8)
     t = w.grid.n_slices * (w.grid.nx + W) * (w.grid.ny + W) * 8
     probes = w.region.npx * w.region.npy
     tables = probes * w.basis.L * 20 + probes * 8 * len(w.detectors) + nT * 4
     return int(store + t + tables + (16 << 20))
+
+
+def fit_max_resident(w, budget_bytes: int) -> Optional[int]:
+    """None when an instance with the full exit-wave store fits budget_bytes; else the
+    largest store (in exit waves, a multiple of 256, at least L) whose instance fits, which
+    makes the lane compute its images part by part (Sec. 4.2.4). Raises when even an
+    L-wave store does not fit."""
+    if _footprint(w) <= budget_bytes:
+        return None
+    lo, hi = w.basis.L, _translates(w)
+    if _footprint(w, lo) > budget_bytes:
+        raise ValueError("the budget does not hold even L exit waves")
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if _footprint(w, mid) <= budget_bytes:
+            lo = mid
+        else:
+            hi = mid
+    return max(w.basis.L, lo // 256 * 256) if lo >= 256 else lo
 
 
 def poisson_arrivals(n: int, rate: float, seed: int) -> np.ndarray:
@@ -349,4 +398,12 @@ def latency_summary(results: List[Result]) -> dict:
         by.setdefault(r.request.lane, []).append(r.latency * 1e3)
     out["by_lane"] = {k: {"n": len(v), "p50_ms": float(np.percentile(v, 50)),
                           "p99_ms": float(np.percentile(v, 99))} for k, v in by.items()}
+    # where the time went: waiting for an instance, or being served
+    for k in out["by_lane"]:
+        rs = [r for r in results if r.request.lane == k]
+        q = np.array([r.t_start - r.t_arrival for r in rs]) * 1e3
+        sv = np.array([r.t_done - r.t_start for r in rs]) * 1e3
+        out["by_lane"][k].update({"queue_p99_ms": float(np.percentile(q, 99)),
+                                  "service_p50_ms": float(np.percentile(sv, 50)),
+                                  "service_p99_ms": float(np.percentile(sv, 99))})
     return out

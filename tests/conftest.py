@@ -1,7 +1,10 @@
 import os
 import sys
 
-import pytest
+# one hardware work queue per stream for the concurrent serving lanes (set before CUDA starts)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
+import pytest  # noqa: E402
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:

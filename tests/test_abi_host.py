@@ -19,7 +19,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _header_functions():
     src = open(os.path.join(ROOT, "include", "lma.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lma_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(lma_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_library_exports_every_declared_function():
@@ -130,3 +130,54 @@ def test_edit_bookkeeping_matches_oracle_edit():
         *_, nhit = O.edit_column(at.x, at.y, at.slice, at.species, w.grid.lx, w.grid.ly, cx, cy, 0.5, 0, 0)
         expect += nhit
     assert n_changed == expect and expect > 0 and n_stale == 0
+
+
+# --------------------------------------------------------------------------- partitions (Sec. 4.2.4)
+
+def _oracle_parts(w, region, strategy, M, start, period=(1, 1)):
+    prm = O.params_from_workload(w)
+    probes = O.region_probes(region.px0, region.py0, region.npx, region.npy, region.spacing_px,
+                             w.grid.nx, w.grid.ny)
+    sets = O.probe_translate_sets(prm, probes)
+    if strategy == lma.LMA_PART_ROWS:
+        parts = O.partition_rows(sets, region.npx, region.npy, M)
+    elif strategy == lma.LMA_PART_GREEDY:
+        parts = O.partition_greedy(sets, region.npx, region.npy, M, start)
+    else:
+        parts = O.partition_rectangles(sets, region.npx, region.npy, M,
+                                       column_major=strategy == lma.LMA_PART_RECTANGLES_COLUMN_MAJOR,
+                                       period=period)
+    return parts, O.partition_cost(sets, parts), max(len(frozenset().union(*[sets[q] for q in p])) for p in parts)
+
+
+@pytest.mark.parametrize("strategy", [lma.LMA_PART_ROWS, lma.LMA_PART_RECTANGLES,
+                                      lma.LMA_PART_RECTANGLES_COLUMN_MAJOR, lma.LMA_PART_GREEDY])
+def test_partition_equals_oracle(strategy):
+    # ABO3 256^2 (Case 1: probes on the input lattice, period 1) and the simple-cubic crystal
+    # with probes every 2 px (Case 2: input lattice every 4 px, period 2)
+    cases = [(WL.perovskite_workload(cells=5, nx=256, n_slices=2, n_phonons=1),
+              WL.Region(40, 200, 23, 17, (4, 4)), (1, 1), (60, 150, 400)),
+             (WL.simple_cubic_workload(), WL.Region(6, 2, 19, 13, (2, 2)), (2, 2), (40, 90, 200))]
+    for w, region, period, Ms in cases:
+        ctx, spec, basis = _host_objects(w)
+        for M in Ms:
+            start = (region.npx * region.npy) // 3
+            part, n, runs, peak = basis.partition(region, strategy, M, start)
+            parts, T, pk = _oracle_parts(w, region, strategy, M, start, period)
+            expect = np.empty(region.npx * region.npy, np.int32)
+            for j, p in enumerate(parts):
+                expect[p] = j
+            assert n == len(parts) and runs == T and peak == pk, (strategy, M)
+            assert np.array_equal(part.ravel(), expect), (strategy, M)
+            assert peak <= M
+
+
+def test_partition_validation():
+    w = WL.simple_cubic_workload()
+    ctx, spec, basis = _host_objects(w)
+    region = WL.Region(0, 0, 4, 4, (8, 8))
+    for strategy, M, start in ((7, 100, 0), (lma.LMA_PART_ROWS, w.basis.L - 1, 0),
+                               (lma.LMA_PART_GREEDY, 100, 16), (lma.LMA_PART_GREEDY, 100, -1)):
+        with pytest.raises(lma.LmaError) as e:
+            basis.partition(region, strategy, M, start)
+        assert e.value.status == lma.LMA_ERR_INVALID

@@ -64,3 +64,54 @@ def test_image_requests_match_a_direct_call():
     basis = lma.Basis(ctx, spec, w.probe, w.basis)
     direct = basis.image(w.detectors, w.region, recompute=True)
     assert np.array_equal(res[1].image, direct)
+
+
+def test_warm_edits_make_no_device_allocation():
+    """Once an edit lane is warm, an edit and its region image allocate nothing: device
+    allocation can wait for the whole device, which would hold an edit behind other
+    lanes' full images."""
+    import torch
+    assert torch.cuda.is_available()
+    w = _resident()
+    ctx = lma.Context(0)
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    st = torch.cuda.Stream()
+    basis.propagate(0, stream=st)
+    dx = w.grid.lx / w.grid.nx
+
+    def edit(k):
+        cx, cy, op, spc = WL.edit_request(5, k, 3300)
+        px, py = int(round(cx / dx)) // 4 * 4, int(round(cy / dx)) // 4 * 4
+        region = WL.Region(px - 32, py - 32, 16, 16, (4, 4))
+        spec.edit_column(basis, cx, cy, 0.5, op, spc)
+        return basis.image(w.detectors, region, stream=st)
+
+    edit(0)                       # warm: region tables, item-list slab, staging buffer
+    ctx.profile_enable(True)
+    for k in range(1, 6):
+        assert np.all(np.isfinite(edit(k)))
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    assert prof["allocations"] == 0, prof
+    assert prof["slice"]["launches"] >= 1
+    basis.close()
+    spec.close()
+    ctx.close()
+
+
+def test_bounded_lane_serves_the_unbounded_images():
+    """A lane whose store holds 1024 of the 4096 exit waves computes its images part by
+    part (Sec. 4.2.4) and returns the unbounded lane's images bit for bit."""
+    lanes = [S.image_lane("full_256", _fresh, max_instances=1),
+             S.image_lane("bounded_256", _fresh, max_instances=1, max_resident=1024)]
+    srv = S.Server(lanes, budget_bytes=1 << 40)
+    full = [srv.submit(S.ImageRequest("full_256", seed=700 + k)) for k in range(2)]
+    bounded = [srv.submit(S.ImageRequest("bounded_256", seed=700 + k)) for k in range(2)]
+    res_f = [t.wait(600) for t in full]
+    res_b = [t.wait(600) for t in bounded]
+    srv.close()
+    for a, b in zip(res_f, res_b):
+        assert a.error is None and b.error is None
+        assert np.array_equal(a.image, b.image)
+    assert lanes[1].reserve_bytes < lanes[0].reserve_bytes

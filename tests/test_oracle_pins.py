@@ -541,3 +541,59 @@ def test_edit_column_removes_or_swaps_only_that_column():
     assert nhit == 3 and list(x2) == [3.9, 2.0]
     _, _, _, sp3, nhit = O.edit_column(x, y, s, sp, 8.0, 8.0, 0.0, 0.0, 0.3, 1, 2)
     assert nhit == 3 and list(sp3) == [2, 1, 2, 1, 2]
+
+
+# --------------------------------------------------------------------------- partitions (Sec. 4.2.4)
+
+def _resident_runs(sets, parts):
+    """Count Multislice runs by simulating the store: each part keeps exactly its own
+    translates; a translate is computed when the part needs it and the previous one did not."""
+    runs, resident = 0, set()
+    for part in parts:
+        need = set().union(*[sets[q] for q in part])
+        runs += len(need - resident)
+        resident = need
+    return runs
+
+
+def test_partitions_cover_the_region_once_and_fit_the_memory_bound():
+    prm = _small_params(L=12)
+    npx, npy = 9, 7
+    probes = O.region_probes(4, 8, npx, npy, (4, 4), prm.nx, prm.ny)
+    sets = O.probe_translate_sets(prm, probes)
+    total = len(frozenset().union(*sets))
+    for M in (12, 20, 37, 60, total):
+        for parts in (O.partition_rows(sets, npx, npy, M), O.partition_rectangles(sets, npx, npy, M),
+                      O.partition_rectangles(sets, npx, npy, M, column_major=True),
+                      O.partition_rectangles(sets, npx, npy, M, period=(2, 3)),
+                      O.partition_greedy(sets, npx, npy, M, start=31)):
+            flat = sorted(q for p in parts for q in p)
+            assert flat == list(range(npx * npy))
+            assert all(len(frozenset().union(*[sets[q] for q in p])) <= M for p in parts)
+            T = O.partition_cost(sets, parts)
+            assert T == _resident_runs(sets, parts)
+            assert total <= T <= sum(len(s) for s in sets)
+    # enough memory for everything: one part, the minimum number of runs
+    for parts in (O.partition_rows(sets, npx, npy, total), O.partition_rectangles(sets, npx, npy, total),
+                  O.partition_greedy(sets, npx, npy, total, start=5)):
+        assert len(parts) == 1 and O.partition_cost(sets, parts) == total
+
+
+def test_greedy_partition_hand_worked():
+    # 3 x 3 probes each needing only its own translate, M = 3, start at the centre; derived
+    # by hand from the rule (fewest translates, ties by (b, a); dead end -> first unassigned)
+    sets = [frozenset([q]) for q in range(9)]
+    parts = O.partition_greedy(sets, 3, 3, 3, start=4)
+    assert parts == [[4, 0, 1], [2, 5, 7], [3, 6, 8]]
+    assert O.partition_cost(sets, parts) == 9
+
+
+def test_rectangle_partition_hand_worked():
+    # 5 x 4 probes, own translates, M = 6: largest area 6, squarest tie (2x3 vs 3x2) -> wider 3x2
+    sets = [frozenset([q]) for q in range(20)]
+    parts = O.partition_rectangles(sets, 5, 4, 6)
+    assert parts == [[0, 1, 2, 5, 6, 7], [3, 4, 8, 9], [10, 11, 12, 15, 16, 17], [13, 14, 18, 19]]
+    cm = O.partition_rectangles(sets, 5, 4, 6, column_major=True)
+    assert cm == [parts[0], parts[2], parts[1], parts[3]]
+    rows = O.partition_rows(sets, 5, 4, 6)
+    assert rows == [[0, 1, 2, 3, 4, 5], [6, 7, 8, 9, 10, 11], [12, 13, 14, 15, 16, 17], [18, 19]]

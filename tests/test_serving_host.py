@@ -124,3 +124,17 @@ def test_warm_failure_is_reported_at_start():
     a.warm = bad_warm
     with pytest.raises(RuntimeError, match="warm-up failed"):
         S.Server([a], budget_bytes=10)
+
+
+def test_fit_max_resident_bounds_the_store_to_the_budget():
+    from paper_2310_16829_gb300 import workloads as WL
+    w = WL.perovskite_workload(cells=20, nx=1024, n_slices=100, n_phonons=1, probes=256)
+    full = S._footprint(w)
+    assert S.fit_max_resident(w, full) is None
+    for frac in (0.9, 0.5, 0.2):
+        budget = int(full * frac)
+        M = S.fit_max_resident(w, budget)
+        assert M is not None and M % 256 == 0 and w.basis.L <= M < S._translates(w)
+        assert S._footprint(w, M) <= budget < S._footprint(w, M + 256)
+    with pytest.raises(ValueError):
+        S.fit_max_resident(w, 1 << 20)
