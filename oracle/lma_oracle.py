@@ -165,6 +165,41 @@ def fresnel_propagator(ny: int, nx: int, dy: float, dx: float, lam: float, dz: f
     return prop
 
 
+def kernel_offsets(K: int) -> np.ndarray:
+    """Offsets -floor(K/2) .. K - 1 - floor(K/2) of a K-pixel kernel axis (K = n covers every
+    residue of an n-pixel periodic axis once)."""
+    return np.arange(K) - K // 2
+
+
+def realspace_kernel(prop: np.ndarray, K1: int, K2: int) -> np.ndarray:
+    """q discretized to K1 x K2 pixels (Sec. 3.2, complexity paragraph): the real-space
+    kernel of the window's Fourier propagator, q = IDFT(prop), at the offsets
+    kernel_offsets(K2) (y) x kernel_offsets(K1) (x), shape (K2, K1). With K1 = K2 = n the
+    convolution with it is the Fourier-space propagation exactly."""
+    q = idft2(prop)
+    ny, nx = prop.shape
+    oy, ox = kernel_offsets(K2), kernel_offsets(K1)
+    return q[np.ix_(oy % ny, ox % nx)]
+
+
+def convolve_periodic(psi: np.ndarray, qK: np.ndarray) -> np.ndarray:
+    """(q * psi)(x) = sum over kernel offsets d of q(d) psi(x - d), periodic on the window."""
+    K2, K1 = qK.shape
+    out = np.zeros_like(psi)
+    for iy, dy in enumerate(kernel_offsets(K2)):
+        for ix, dx in enumerate(kernel_offsets(K1)):
+            out += qK[iy, ix] * np.roll(psi, (int(dy), int(dx)), axis=(0, 1))
+    return out
+
+
+def multislice_realspace(psi: np.ndarray, t: Sequence[np.ndarray], qK: np.ndarray) -> np.ndarray:
+    """The multislice pseudocode with the propagation step as a real-space convolution
+    with the K1 x K2 kernel: for each slice transmit, then convolve."""
+    for ts in t:
+        psi = convolve_periodic(ts * psi, qK)
+    return psi
+
+
 def projected_potential(x: np.ndarray, y: np.ndarray, slc: np.ndarray, species: np.ndarray,
                         n_slices: int, ny: int, nx: int, ly: float, lx: float,
                         peak: Sequence[float], term_frac: Sequence[float],

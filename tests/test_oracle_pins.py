@@ -597,3 +597,38 @@ def test_rectangle_partition_hand_worked():
     assert cm == [parts[0], parts[2], parts[1], parts[3]]
     rows = O.partition_rows(sets, 5, 4, 6)
     assert rows == [[0, 1, 2, 3, 4, 5], [6, 7, 8, 9, 10, 11], [12, 13, 14, 15, 16, 17], [18, 19]]
+
+
+# --------------------------------------------------------------------------- real-space propagation
+
+def test_convolution_matches_a_direct_double_sum():
+    rng = np.random.default_rng(11)
+    n = 10
+    psi = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    q = rng.normal(size=(3, 5)) + 1j * rng.normal(size=(3, 5))     # K2 = 3 (y), K1 = 5 (x)
+    direct = np.zeros_like(psi)
+    for y in range(n):
+        for x in range(n):
+            for iy, dy in enumerate((-1, 0, 1)):
+                for ix, dx in enumerate((-2, -1, 0, 1, 2)):
+                    direct[y, x] += q[iy, ix] * psi[(y - dy) % n, (x - dx) % n]
+    assert rel(O.convolve_periodic(psi, q), direct) < 1e-13
+
+
+def test_full_kernel_convolution_is_the_fourier_propagation():
+    rng = np.random.default_rng(12)
+    n, d, lam = 32, 0.1, 0.025
+    prop = O.fresnel_propagator(n, n, d, d, lam, 2.0, 2 / 3)
+    psi = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    t = [np.exp(1j * rng.normal(size=(n, n))) for _ in range(3)]
+    q = O.realspace_kernel(prop, n, n)
+    assert rel(O.multislice_realspace(psi, t, q), O.multislice(psi, t, prop)) < 1e-12
+    # a 1 x 1 kernel multiplies by q(0) = the mean of the propagator
+    q1 = O.realspace_kernel(prop, 1, 1)
+    assert abs(q1[0, 0] - prop.mean()) < 1e-15
+    # the truncated kernel approximates the propagation, better as it grows (the discrete
+    # Fresnel kernel is a chirp with the bandlimit's rings, so the decay is slow)
+    wave = O.probe(n, n, d, d, lam, 0.02)
+    ref = O.multislice(wave, t[:1], prop)
+    errs = [rel(O.multislice_realspace(wave, t[:1], O.realspace_kernel(prop, K, K)), ref) for K in (5, 9, 17, 31)]
+    assert all(a > b for a, b in zip(errs, errs[1:])) and errs[0] < 0.5
