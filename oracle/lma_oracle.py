@@ -587,6 +587,35 @@ class LmaOracle:
                 out[:, k] += self.pixel(phi, (int(pr[0]), int(pr[1])), masks)
         return out / nphi
 
+    def image_coherent(self, detectors, probes: np.ndarray, variants: Sequence[Tuple[float, float, float]]
+                       ) -> np.ndarray:
+        """Partial coherence (Sec. 1: the simulation repeated with slightly different probe
+        parameters and averaged): for each variant (defocus, C_s, weight) the coefficients
+        are fitted to that probe with the same input waves, and the images are averaged with
+        the normalised weights. The exit waves do not depend on the probe, so every variant
+        reuses them."""
+        p = self.prm
+        masks = self.detector_masks(detectors)
+        wsum = float(sum(v[2] for v in variants))
+        out = np.zeros((len(masks), probes.shape[0]), dtype=np.float64)
+        nphi = len(self._phonons)
+        for defocus, cs_v, weight in variants:
+            psi0 = probe(p.ny, p.nx, p.dy, p.dx, p.lam, p.alpha_max, cs_v, defocus)
+            sets: Dict[Tuple[int, int], CoefficientSet] = {}
+            img = np.zeros_like(out)
+            for phi in range(nphi):
+                for k, pr in enumerate(probes):
+                    q = (int(pr[0]), int(pr[1]))
+                    key = class_key(q, p.in_spacing, p.in_offset, p.f)
+                    idx, offs = nearest_translates(q, self.lattice, p.L, p.nx, p.ny)
+                    if key not in sets:
+                        sets[key] = coefficients(psi0, self.uW, offs)
+                    U = [self.exit_wave(phi, int(i)) for i in idx]
+                    psi = synthesize(U, sets[key].alpha, offs, p.D, p.cyclic)
+                    img[:, k] += [detect(psi, m) for m in masks]
+            out += (weight / wsum) * img / nphi
+        return out
+
     def image_rings(self, width: float, n_rings: int, probes: np.ndarray) -> np.ndarray:
         """3D STEM image (Sec. 3.1), shape (n_rings, n_probes): the 2D image with one ring
         per detector, averaged over configurations."""
@@ -611,6 +640,28 @@ class LmaOracle:
                 psi = synthesize(U, cs.alpha, cs.offsets, self.prm.D, self.prm.cyclic)
                 out[k] += pattern(psi, A, B, self.prm.bandlimit_frac)
         return out / nphi
+
+
+def select_L(prm: LmaParams, probes: np.ndarray, eps_sup: float, L_max: int) -> Tuple[int, float]:
+    """Smallest L (1..L_max) whose probe approximation error in the supremum norm, relative
+    to the probe's maximum, is at most eps_sup for every probe class of `probes` (the
+    parameter choice of Sec. 4.2.6: a target error fixes L). Returns (L, worst error), or
+    (0, error at L_max) when no L reaches the target."""
+    lat = input_lattice(prm.nx, prm.ny, prm.in_spacing, prm.in_offset, prm.f)
+    psi0 = probe(prm.ny, prm.nx, prm.dy, prm.dx, prm.lam, prm.alpha_max, prm.cs, prm.defocus)
+    uW = input_wave_window(prm.kind, prm.W, prm.ny, prm.nx, prm.dy, prm.dx, prm.lam, prm.alpha_max,
+                           prm.cs, prm.defocus, prm.gauss_sigma)
+    reps = {}
+    for q in probes:
+        key = class_key((int(q[0]), int(q[1])), prm.in_spacing, prm.in_offset, prm.f)
+        reps.setdefault(key, (int(q[0]), int(q[1])))
+    err = float("inf")
+    for L in range(1, L_max + 1):
+        err = max(coefficients(psi0, uW, nearest_translates(q, lat, L, prm.nx, prm.ny)[1]).err_sup
+                  for q in reps.values())
+        if err <= eps_sup:
+            return L, err
+    return 0, err
 
 
 def region_probes(px0: int, py0: int, npx: int, npy: int, spacing: Tuple[int, int],

@@ -632,3 +632,57 @@ def test_full_kernel_convolution_is_the_fourier_propagation():
     ref = O.multislice(wave, t[:1], prop)
     errs = [rel(O.multislice_realspace(wave, t[:1], O.realspace_kernel(prop, K, K)), ref) for K in (5, 9, 17, 31)]
     assert all(a > b for a, b in zip(errs, errs[1:])) and errs[0] < 0.5
+
+
+# --------------------------------------------------------------------------- partial coherence, L from a target error
+
+def _toy_specimen(orc):
+    class A:
+        pass
+    at = A()
+    at.x, at.y = np.array([0.0, 4.0, 0.0, 4.0]), np.array([0.0, 0.0, 4.0, 4.0])
+    at.slice, at.species = np.zeros(4, np.int32), np.zeros(4, np.int16)
+    orc.set_specimen([at], (300.0,), (0.7, 0.3), (0.15, 0.5), 3.0)
+    return orc
+
+
+def test_coherent_image_is_the_weighted_average_of_fresh_images():
+    # Gaussian input waves do not depend on the focus: every variant's image from scratch
+    # (new probe, coefficients and exit waves) must equal the shared-exit-wave result
+    import dataclasses
+    prm = _small_params(L=16, n_slices=2, alpha_max=0.025)
+    probes = np.array([[0, 0], [6, 10], [33, 17]])
+    dets = [_Det(0.0, 0.02), _Det(0.03, 0.066)]
+    variants = [(-40.0, 0.0, 1.0), (0.0, 0.0, 2.0), (55.0, 0.0, 0.5)]
+    got = _toy_specimen(O.LmaOracle(prm)).image_coherent(dets, probes, variants)
+    ref = np.zeros_like(got)
+    for dz, cs, wgt in variants:
+        fresh = _toy_specimen(O.LmaOracle(dataclasses.replace(prm, defocus=dz, cs=cs)))
+        ref += wgt / 3.5 * fresh.image(dets, probes)
+    assert rel(got, ref) < 1e-12
+    # one variant with the basis's own probe is the plain image
+    orc = _toy_specimen(O.LmaOracle(prm))
+    assert rel(orc.image_coherent(dets, probes, [(prm.defocus, prm.cs, 3.0)]), orc.image(dets, probes)) < 1e-14
+
+
+def test_select_L_is_the_smallest_L_meeting_the_target():
+    prm = _small_params(L=8)
+    probes = O.region_probes(0, 0, 4, 4, (4, 4), prm.nx, prm.ny)
+    lat = O.input_lattice(prm.nx, prm.ny, prm.in_spacing, prm.in_offset, prm.f)
+    psi0 = O.probe(prm.ny, prm.nx, prm.dy, prm.dx, prm.lam, prm.alpha_max, prm.cs, prm.defocus)
+    uW = O.input_wave_window(prm.kind, prm.W, prm.ny, prm.nx, prm.dy, prm.dx, prm.lam, prm.alpha_max,
+                             prm.cs, prm.defocus, prm.gauss_sigma)
+
+    def err(L):
+        return O.coefficients(psi0, uW, O.nearest_translates((0, 0), lat, L, prm.nx, prm.ny)[1]).err_sup
+
+    for eps in (0.75, 0.6, 0.5, 0.45):
+        L, e = O.select_L(prm, probes, eps, 40)
+        assert 1 <= L and e <= eps and abs(e - err(L)) < 1e-15
+        assert L == 1 or err(L - 1) > eps
+    assert O.select_L(prm, probes, 1e-9, 3)[0] == 0
+    # u = probe on I = P: the probe is one of the input waves, L = 1 is exact (Sec. 4.2.3)
+    import dataclasses
+    pp = dataclasses.replace(prm, kind=1, in_offset=(0, 0))
+    L, e = O.select_L(pp, probes, 1e-12, 4)
+    assert L == 1 and e < 1e-12
