@@ -428,6 +428,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--edits", type=int, default=24, help="column-edit requests timed (0: skip)")
     ap.add_argument("--serving", type=int, default=60, help="requests per offered load (0: skip)")
+    ap.add_argument("--no-coherence", dest="coherence", action="store_false",
+                    help="skip the partial-coherence (focal series) measurement")
     ap.add_argument("--no-partition", dest="partition", action="store_false",
                     help="skip the memory-bounded (partitioned) image measurement")
     ap.add_argument("--no-stem34", dest="stem34", action="store_false",
@@ -608,6 +610,26 @@ def main():
                                           "bitwise_equal_to_unbounded": bool(torch.equal(out_p, out))}}
         del out_p
 
+    # ---- partial coherence: a focal series of 5 defocus values (Gaussian weights, 20 A
+    # steps) from one set of exit waves, against 5 full images
+    coherence = None
+    if args.coherence and rank == 0:
+        series = [(dz, 0.0, float(np.exp(-0.5 * (dz / 30.0) ** 2))) for dz in (-40.0, -20.0, 0.0, 20.0, 40.0)]
+        out_c = torch.empty_like(out)
+        basis.image_coherent(series, dets, region, out=out_c, recompute=True, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        basis.image_coherent(series, dets, region, out=out_c, recompute=True, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_c = e0.elapsed_time(e1)
+        coherence = {"variants": len(series), "defocus_A": [v[0] for v in series],
+                     "ms_per_image": ms_c, "pixels_per_s": w.n_pixels / (ms_c / 1e3),
+                     "vs_one_image": ms_c / ms_per_step,
+                     "speedup_vs_separate_images": len(series) * ms_per_step / ms_c}
+        del out_c
+
     # ---- end to end through the public API with host buffers
     host_out = np.empty((len(dets), region.npy, region.npx), dtype=np.float64)
     h2d = sum(a.x.nbytes + a.y.nbytes + a.species.nbytes + 4 * (w.grid.n_slices + 1) for a in w.phonons)
@@ -704,6 +726,7 @@ def main():
             "batching": batching,
             "stem34": stem34,
             "partition": partition,
+            "coherence": coherence,
             "clocks": clk,
             "kernels": kernels,
             "wall_s_timed_region": wall,

@@ -127,6 +127,10 @@ cudaError_t launch_potential(const PotArgs& a, cudaStream_t s);
 cudaError_t launch_slice(const SliceLaunch& a, bool even_origins, bool half, int mode, cudaStream_t s);
 int sm_count();
 cudaError_t launch_synth(const SynthArgs& a, bool half, int mode, cudaStream_t s);
+// out[i] = sum over variants v (in order) of w[v] * sum over n_cfg slots (in order) of
+// acc[(v * n_cfg + c) * n + i]; w has n_var entries on the device
+cudaError_t launch_finalize_variants(const double* acc, int64_t n, int n_cfg, int n_var, const double* w, double* out,
+                                     cudaStream_t s);
 // acc[i] (+)= sum over n_cfg slots (in slot order) of slots[c * n + i]; first: assign
 cudaError_t launch_pattern_accumulate(const float* slots, int64_t n, int n_cfg, bool first, double* acc,
                                       cudaStream_t s);

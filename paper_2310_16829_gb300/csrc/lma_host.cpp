@@ -401,6 +401,9 @@ struct lma_basis {
   int64_t plan_runs = 0, plan_peak = 0;
   std::vector<int32_t> plan_tab;     // host copy of d_plan
   DevBuf d_plan, d_Up, d_Upscale;
+  // partial coherence: coefficient tables of the probe variants of the last call
+  std::vector<double> var_key;
+  DevBuf d_var;                  // [n_var][n_probes][L] complex64 coefficients, then [n_var] weights
   bool dev_tables = false;
   int B = 0;                     // exit-wave store slots (configurations in flight)
   std::vector<int> U_phonon;     // configuration held by each slot (-1: none)
@@ -418,9 +421,8 @@ bool device_ready(lma_ctx* ctx) {
   return cudaSetDevice(ctx->device) == cudaSuccess;
 }
 
-// full-grid probe psi_0 (eq. probe_wave_function at p = 0), unit norm
-void build_probe(lma_basis* b) {
-  if (!b->psi0.empty()) return;
+// full-grid probe psi_0 of probe parameters pr (eq. probe_wave_function at p = 0), unit norm
+void probe_at_origin(const lma_basis* b, const lma_probe& pr, std::vector<cd>& out) {
   const lma_grid& g = b->spec->g;
   const int nx = g.nx, ny = g.ny;
   const double dx = g.lx / nx, dy = g.ly / ny, lam = g.lambda;
@@ -430,10 +432,9 @@ void build_probe(lma_basis* b) {
     for (int ix = 0; ix < nx; ++ix) {
       const double kx = signed_index(ix, nx) / (nx * dx);
       const double k2 = ky * ky + kx * kx;
-      const bool ap = lam * std::sqrt(k2) < b->probe.alpha_max;
+      const bool ap = lam * std::sqrt(k2) < pr.alpha_max;
       if (!ap) continue;
-      const double chi = 0.5 * kPi * b->probe.cs * lam * lam * lam * k2 * k2 -
-                         kPi * b->probe.defocus * lam * k2;
+      const double chi = 0.5 * kPi * pr.cs * lam * lam * lam * k2 * k2 - kPi * pr.defocus * lam * k2;
       spec[static_cast<size_t>(iy) * nx + ix] = std::exp(cd(0.0, -chi));
     }
   }
@@ -442,7 +443,11 @@ void build_probe(lma_basis* b) {
   for (const cd& c : spec) n2 += std::norm(c);
   const double s = 1.0 / std::sqrt(n2);
   for (cd& c : spec) c *= s;
-  b->psi0.swap(spec);
+  out.swap(spec);
+}
+
+void build_probe(lma_basis* b) {
+  if (b->psi0.empty()) probe_at_origin(b, b->probe, b->psi0);
 }
 
 // the input wave on its window (Sec. 4.2.3)
@@ -469,7 +474,8 @@ void build_input_wave(lma_basis* b) {
 }
 
 // the L nearest translates of probe p (Sec. 4.2.1 option (iii)); ties by (d^2, dy, dx)
-void nearest(const lma_basis* b, int px, int py, std::vector<int>& odx, std::vector<int>& ody) {
+// offsets of the L input waves nearest to pixel (px, py) (the basis's L when L <= 0)
+void nearest(const lma_basis* b, int px, int py, std::vector<int>& odx, std::vector<int>& ody, int L = 0) {
   struct Cand {
     long d2;
     int dy, dx;
@@ -485,7 +491,7 @@ void nearest(const lma_basis* b, int px, int py, std::vector<int>& odx, std::vec
       c.push_back({static_cast<long>(ddx) * ddx + static_cast<long>(ddy) * ddy, ddy, ddx});
     }
   }
-  const int L = b->desc.L;
+  if (L <= 0) L = b->desc.L;
   std::partial_sort(c.begin(), c.begin() + L, c.end(), [](const Cand& u, const Cand& v) {
     if (u.d2 != v.d2) return u.d2 < v.d2;
     if (u.dy != v.dy) return u.dy < v.dy;
@@ -501,9 +507,9 @@ void nearest(const lma_basis* b, int px, int py, std::vector<int>& odx, std::vec
 
 // least-squares coefficients of one probe class (eqs. lma_approximation_exit1_0 / exit2_0),
 // in coordinates relative to the probe (probe at pixel 0, translate j at its offset)
-lma_status solve_set(lma_basis* b, CoefSet& cs) {
-  build_probe(b);
-  const int nx = b->nx, ny = b->ny, L = b->desc.L;
+// least squares of probe psi0 on the input waves at cs.odx / cs.ody (their count is L)
+lma_status solve_set_for(lma_basis* b, const std::vector<cd>& psi0, CoefSet& cs) {
+  const int nx = b->nx, ny = b->ny, L = static_cast<int>(cs.odx.size());
   // bounding box of the union of windows [o - W/2, o + W/2)
   int ylo = 1 << 30, yhi = -(1 << 30), xlo = 1 << 30, xhi = -(1 << 30);
   for (int j = 0; j < L; ++j) {
@@ -535,7 +541,7 @@ lma_status solve_set(lma_basis* b, CoefSet& cs) {
   for (int i = 0; i < m; ++i) {
     const int gy = static_cast<int>(rows[i] / nx), gx = static_cast<int>(rows[i] % nx);
     in_rows[rows[i]] = 1;
-    rhs[i] = b->psi0[rows[i]];
+    rhs[i] = psi0[rows[i]];
     for (int j = 0; j < L; ++j) {
       const int ly = mod(gy - (cs.ody[j] - kW / 2), ny), lx = mod(gx - (cs.odx[j] - kW / 2), nx);
       if (ly < kW && lx < kW) A[static_cast<size_t>(j) * m + i] = b->uW[static_cast<size_t>(ly) * kW + lx];
@@ -554,8 +560,8 @@ lma_status solve_set(lma_basis* b, CoefSet& cs) {
     r2 += e * e;
     rmax = std::max(rmax, e);
   }
-  for (size_t k = 0; k < b->psi0.size(); ++k) {
-    const double a = std::abs(b->psi0[k]);
+  for (size_t k = 0; k < psi0.size(); ++k) {
+    const double a = std::abs(psi0[k]);
     n2 += a * a;
     pmax = std::max(pmax, a);
     if (!in_rows[k]) {
@@ -566,6 +572,11 @@ lma_status solve_set(lma_basis* b, CoefSet& cs) {
   cs.err_l2 = std::sqrt(r2 / n2);
   cs.err_sup = rmax / pmax;
   return LMA_OK;
+}
+
+lma_status solve_set(lma_basis* b, CoefSet& cs) {
+  build_probe(b);
+  return solve_set_for(b, b->psi0, cs);
 }
 
 std::pair<int, int> class_key(const lma_basis* b, int px, int py) {
@@ -1545,6 +1556,7 @@ lma_status lma_free_basis(lma_basis* b) {
   b->d_pat.release();
   b->d_pat_acc.release();
   b->d_plan.release();
+  b->d_var.release();
   b->d_Up.release();
   b->d_Upscale.release();
   b->reg.tidx.release();
@@ -1970,6 +1982,173 @@ static lma_status make_plan(lma_basis* b, const lma_region* r, const lma_partiti
   b->plan_d = *d;
   b->plan_valid = true;
   b->plan_dev = false;
+  return LMA_OK;
+}
+
+lma_status lma_select_L(lma_ctx* ctx, const lma_specimen* spec, const lma_probe* probe, const lma_basis_desc* desc,
+                        const lma_region* region, int32_t L_max, double eps_sup, int32_t* L_out, double* err_out) {
+  if (!ctx || !spec || !probe || !desc || !region || !L_out) return fail(ctx, LMA_ERR_INVALID, "null argument");
+  if (L_max < 1 || L_max > kMaxL) return fail(ctx, LMA_ERR_INVALID, "L_max must be in [1, %d]", kMaxL);
+  if (!(eps_sup > 0)) return fail(ctx, LMA_ERR_INVALID, "eps_sup must be positive");
+  lma_basis_desc d = *desc;
+  d.L = L_max;
+  lma_basis* b = nullptr;
+  lma_status s = lma_create_basis(ctx, spec, probe, &d, &b);
+  if (s != LMA_OK) return s;
+  struct Free {
+    lma_basis* b;
+    ~Free() { lma_free_basis(b); }
+  } guard{b};
+  if ((s = validate_region(ctx, b, region)) != LMA_OK) return s;
+  // one representative probe per coefficient class of the region
+  std::map<std::pair<int, int>, std::pair<int, int>> reps;
+  for (int pb = 0; pb < region->npy; ++pb)
+    for (int pa = 0; pa < region->npx; ++pa) {
+      const int px = mod(region->px0 + pa * region->spacing_px[0], b->nx);
+      const int py = mod(region->py0 + pb * region->spacing_px[1], b->ny);
+      reps.emplace(class_key(b, px, py), std::make_pair(px, py));
+    }
+  build_probe(b);
+  double err = 0.0;
+  for (int L = 1; L <= L_max; ++L) {
+    err = 0.0;
+    for (const auto& kv : reps) {
+      CoefSet cs;
+      nearest(b, kv.second.first, kv.second.second, cs.odx, cs.ody, L);
+      if ((s = solve_set_for(b, b->psi0, cs)) != LMA_OK) return s;
+      err = std::max(err, cs.err_sup);
+    }
+    if (err <= eps_sup) {
+      *L_out = L;
+      if (err_out) *err_out = err;
+      return LMA_OK;
+    }
+  }
+  *L_out = 0;
+  if (err_out) *err_out = err;
+  return LMA_OK;
+}
+
+lma_status lma_image_coherent(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, const lma_probe* variants,
+                              const double* weights, int32_t n_var, const lma_detector* det, int32_t n_det,
+                              const lma_region* region, uint32_t flags, double* out, void* stream) {
+  if (!ctx || !sp || !b || !variants || !weights || !out || !region) return fail(ctx, LMA_ERR_INVALID, "null argument");
+  if (b->spec != sp) return fail(ctx, LMA_ERR_INVALID, "basis belongs to another specimen");
+  if (n_var < 1 || n_var > LMA_MAX_VARIANTS) return fail(ctx, LMA_ERR_INVALID, "need 1..%d variants", LMA_MAX_VARIANTS);
+  double wsum = 0.0;
+  for (int v = 0; v < n_var; ++v) {
+    if (!(weights[v] >= 0) || !std::isfinite(weights[v])) return fail(ctx, LMA_ERR_INVALID, "weight %d must be >= 0", v);
+    if (variants[v].alpha_max != b->probe.alpha_max)
+      return fail(ctx, LMA_ERR_INVALID, "variant %d: alpha_max differs from the basis probe", v);
+    if (!std::isfinite(variants[v].defocus) || !std::isfinite(variants[v].cs))
+      return fail(ctx, LMA_ERR_INVALID, "variant %d: non-finite aberration", v);
+    wsum += weights[v];
+  }
+  if (!(wsum > 0)) return fail(ctx, LMA_ERR_INVALID, "weights sum to zero");
+  if (n_det <= 0 || n_det > lma_dev::kMaxDet || !det)
+    return fail(ctx, LMA_ERR_INVALID, "need 1..%d detectors", lma_dev::kMaxDet);
+  for (int d = 0; d < n_det; ++d)
+    if (!(det[d].r1 >= 0) || !(det[d].r2 > det[d].r1)) return fail(ctx, LMA_ERR_INVALID, "detector %d: need 0 <= r1 < r2", d);
+  lma_status s = validate_region(ctx, b, region);
+  if (s != LMA_OK) return s;
+  if (!device_ready(ctx)) return fail(ctx, LMA_ERR_UNSUPPORTED, "no device in this context");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((s = ensure_basis_device(b, st)) != LMA_OK) return s;
+  if ((s = build_region(b, region, st)) != LMA_OK) return s;
+  if ((s = build_detectors(b, det, n_det, st)) != LMA_OK) return s;
+  const int L = b->desc.L;
+  const int64_t np = b->reg.n_probes;
+  // coefficient tables of the variants (kept for the next call with the same variants)
+  std::vector<double> key{static_cast<double>(n_var)};
+  for (int32_t v : {region->px0, region->py0, region->npx, region->npy, region->spacing_px[0], region->spacing_px[1]})
+    key.push_back(v);
+  for (int v = 0; v < n_var; ++v) {
+    key.push_back(variants[v].defocus);
+    key.push_back(variants[v].cs);
+    key.push_back(weights[v]);
+  }
+  const size_t tab_floats = static_cast<size_t>(n_var) * np * L * 2;
+  if (!b->d_var.p || key != b->var_key) {
+    std::vector<float> tab(tab_floats + 2 * static_cast<size_t>(n_var), 0.f);
+    for (int v = 0; v < n_var; ++v) {
+      std::vector<cd> psi0;
+      probe_at_origin(b, variants[v], psi0);
+      std::map<std::pair<int, int>, CoefSet> sets;
+      for (int pb = 0; pb < region->npy; ++pb)
+        for (int pa = 0; pa < region->npx; ++pa) {
+          const int px = mod(region->px0 + pa * region->spacing_px[0], b->nx);
+          const int py = mod(region->py0 + pb * region->spacing_px[1], b->ny);
+          const auto k = class_key(b, px, py);
+          auto it = sets.find(k);
+          if (it == sets.end()) {
+            CoefSet cs;
+            nearest(b, px, py, cs.odx, cs.ody);
+            if ((s = solve_set_for(b, psi0, cs)) != LMA_OK) return s;
+            it = sets.emplace(k, std::move(cs)).first;
+          }
+          // same translate order as the region tables (nearest() is deterministic)
+          const size_t base = ((static_cast<size_t>(v) * np) + static_cast<size_t>(pb) * region->npx + pa) * L;
+          for (int j = 0; j < L; ++j) {
+            tab[2 * (base + j)] = static_cast<float>(it->second.alpha[j].real());
+            tab[2 * (base + j) + 1] = static_cast<float>(it->second.alpha[j].imag());
+          }
+        }
+    }
+    // weights w_v / (sum w * configurations) as doubles after the coefficients
+    std::vector<double> wv(n_var);
+    for (int v = 0; v < n_var; ++v) wv[v] = weights[v] / wsum / static_cast<double>(sp->ph.size());
+    const size_t bytes = tab_floats * sizeof(float) + n_var * sizeof(double);
+    CUDA_TRY(ctx, ensure(b->d_var, bytes));
+    CUDA_TRY(ctx, upload_parts(ctx, {HostPart{b->d_var.p, tab.data(), tab_floats * sizeof(float)},
+                                      HostPart{static_cast<char*>(b->d_var.p) + tab_floats * sizeof(float), wv.data(),
+                                               n_var * sizeof(double)}},
+                               st));
+    b->var_key = key;
+  }
+  const int nph = static_cast<int>(sp->ph.size());
+  const int64_t nout = np * n_det;
+  CUDA_TRY(ctx, ensure(b->d_acc, static_cast<size_t>(nout) * (static_cast<size_t>(n_var) * nph + 1) * sizeof(double)));
+  const bool half = b->desc.precision == LMA_PREC_MIXED;
+  const bool recompute = (flags & LMA_IMAGE_RECOMPUTE) != 0;
+  AutotuneScope tuning(ctx, (flags & LMA_IMAGE_AUTOTUNE) != 0);
+  for (int phi0 = 0; phi0 < nph; phi0 += b->B) {
+    const int nb = std::min(b->B, nph - phi0);
+    if ((s = ensure_batch(b, sp, phi0, nb, b->reg.needed, recompute, st)) != LMA_OK) return s;
+    for (int v = 0; v < n_var; ++v) {
+      lma_dev::SynthArgs a{};
+      a.U = half ? nullptr : static_cast<const float2*>(b->d_U.p);
+      a.Uh = half ? b->d_U.p : nullptr;
+      a.Uscale = half ? static_cast<const float*>(b->d_Uscale.p) : nullptr;
+      a.tidx = static_cast<const int32_t*>(b->reg.tidx.p);
+      a.alpha = reinterpret_cast<const float2*>(static_cast<const float*>(b->d_var.p) +
+                                                static_cast<size_t>(v) * np * L * 2);
+      a.shift = static_cast<const int2*>(b->reg.shift.p);
+      a.L = L;
+      a.n_probes = static_cast<int>(np);
+      a.npx = region->npx;
+      a.npy = region->npy;
+      a.strip = kSynthStrip;
+      a.n_cfg = nb;
+      a.cfg_base = phi0;
+      a.n_translates = static_cast<int>(b->nT);
+      a.u_slot = static_cast<size_t>(b->nT) * kW * kW;
+      a.cyclic = (b->nx == kW && b->ny == kW) ? 1 : 0;
+      a.det_bits = static_cast<const uint32_t*>(b->d_det.p);
+      a.n_det = n_det;
+      a.acc = static_cast<double*>(b->d_acc.p) + static_cast<size_t>(v) * nph * nout;
+      a.band_r2 = b->r2max;
+      CUDA_TRY(ctx, counted(ctx, K_SYNTH, np * nb, st,
+                            [&] { return lma_dev::launch_synth(a, half, lma_dev::kReadAnnuli, st); }));
+    }
+  }
+  const double* acc = static_cast<const double*>(b->d_acc.p);
+  const double* wdev = reinterpret_cast<const double*>(static_cast<const char*>(b->d_var.p) + tab_floats * sizeof(float));
+  const bool dev_out = is_device_pointer(out);
+  double* fin = dev_out ? out : static_cast<double*>(b->d_acc.p) + static_cast<size_t>(n_var) * nph * nout;
+  CUDA_TRY(ctx, counted(ctx, K_FIN, nout, st,
+                        [&] { return lma_dev::launch_finalize_variants(acc, nout, nph, n_var, wdev, fin, st); }));
+  if (!dev_out) CUDA_TRY(ctx, read_back(ctx, out, fin, static_cast<size_t>(nout) * sizeof(double), st));
+  CUDA_TRY(ctx, cudaGetLastError());
   return LMA_OK;
 }
 

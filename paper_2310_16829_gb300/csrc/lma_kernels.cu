@@ -755,6 +755,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
   }
 }
 
+__global__ void k_finalize_variants(const double* acc, int64_t n, int n_cfg, int n_var, const double* w,
+                                    double* out) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double tot = 0.0;
+  for (int v = 0; v < n_var; ++v) {
+    double s = 0.0;
+    for (int c = 0; c < n_cfg; ++c) s += acc[(static_cast<size_t>(v) * n_cfg + c) * n + i];
+    tot += w[v] * s;
+  }
+  out[i] = tot;
+}
+
 __global__ void k_pattern_accumulate(const float* slots, int64_t n, int n_cfg, int first, double* acc) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -978,6 +991,13 @@ cudaError_t launch_synth(const SynthArgs& a, bool half, int mode, cudaStream_t s
   else if (mode == kReadPattern && half) k_synth_detect<true, kReadPattern><<<grid, kThreads, sm, s>>>(a);
   else if (mode == kReadPattern) k_synth_detect<false, kReadPattern><<<grid, kThreads, sm, s>>>(a);
   else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_variants(const double* acc, int64_t n, int n_cfg, int n_var, const double* w, double* out,
+                                     cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_finalize_variants<<<static_cast<int>((n + 255) / 256), 256, 0, s>>>(acc, n, n_cfg, n_var, w, out);
   return cudaGetLastError();
 }
 

@@ -36,6 +36,7 @@ LMA_EDIT_REMOVE = 0
 LMA_EDIT_SET_SPECIES = 1
 LMA_IMAGE_RECOMPUTE = 1
 LMA_MAX_RINGS = 256
+LMA_MAX_VARIANTS = 32
 LMA_IMAGE_GRAPH = 2
 LMA_IMAGE_AUTOTUNE = 4
 LMA_PART_ROWS = 0
@@ -58,6 +59,7 @@ EXPORTS = [
     "lma_affected_probes",
     "lma_profile_enable", "lma_profile_read", "lma_readout_noalloc",
     "lma_set_slice_mode", "lma_tuning_read", "lma_partition", "lma_image_partitioned",
+    "lma_image_coherent", "lma_select_L",
 ]
 
 
@@ -173,6 +175,10 @@ _SIGS = {
     "lma_readout_noalloc": (C.c_int32, [_VP, _VP, _VP, C.POINTER(Detector), C.c_int32, C.POINTER(Region),
                                         _VP, _VP]),
     "lma_set_slice_mode": (C.c_int32, [_VP, C.c_int32]),
+    "lma_image_coherent": (C.c_int32, [_VP, _VP, _VP, C.POINTER(Probe), C.POINTER(C.c_double), C.c_int32,
+                                       C.POINTER(Detector), C.c_int32, C.POINTER(Region), C.c_uint32, _VP, _VP]),
+    "lma_select_L": (C.c_int32, [_VP, _VP, C.POINTER(Probe), C.POINTER(BasisDesc), C.POINTER(Region), C.c_int32,
+                                 C.c_double, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "lma_partition": (C.c_int32, [_VP, _VP, C.POINTER(Region), C.POINTER(PartitionDesc), _VP,
                                   C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "lma_image_partitioned": (C.c_int32, [_VP, _VP, _VP, C.POINTER(Detector), C.c_int32, C.POINTER(Region),
@@ -366,6 +372,7 @@ class Basis:
         self.h = h
         self.L = desc.L
         self.W = desc.window
+        self.alpha_max = probe.alpha_max
 
     def info(self) -> BasisInfo:
         i = BasisInfo()
@@ -425,6 +432,22 @@ class Basis:
                                                  C.byref(reg), flags, _ptr(out), _stream(stream)))
         return out
 
+    def image_coherent(self, variants, detectors, region, out=None, recompute: bool = False, stream=None):
+        """Partially coherent image: variants = [(defocus, cs, weight), ...] of the basis probe
+        (same aperture), averaged with the normalised weights from one set of exit waves."""
+        n = len(variants)
+        probes = (Probe * n)(*[Probe(self.alpha_max, cs, dz) for dz, cs, _ in variants])
+        wts = (C.c_double * n)(*[w for _, _, w in variants])
+        dets = (Detector * len(detectors))(*[Detector(d.r1, d.r2) for d in detectors])
+        if out is None:
+            out = np.empty((len(detectors), region.npy, region.npx), dtype=np.float64)
+        reg = _region(region)
+        flags = LMA_IMAGE_RECOMPUTE if recompute else 0
+        self.ctx.check(self.ctx.lib.lma_image_coherent(self.ctx.h, self.spec.h, self.h, probes, wts, n, dets,
+                                                       len(detectors), C.byref(reg), flags, _ptr(out),
+                                                       _stream(stream)))
+        return out
+
     def partition(self, region, strategy: int, max_resident: int, start: int = 0):
         """Partition of a probe region under a memory bound (Sec. 4.2.4): (part index per
         probe [npy][npx], number of parts, Multislice runs T, peak resident waves)."""
@@ -482,6 +505,21 @@ class Basis:
             self.close()
         except Exception:
             pass
+
+
+def select_L(ctx: Context, spec: "Specimen", probe, desc, region, L_max: int, eps_sup: float):
+    """Smallest L <= L_max whose probe approximation error (supremum norm, relative) meets
+    eps_sup over the region's coefficient classes: (L or 0, error)."""
+    pr = Probe(probe.alpha_max, probe.cs, probe.defocus)
+    d = BasisDesc(desc.kind, desc.gauss_sigma, (C.c_int32 * 2)(*desc.in_spacing_px),
+                  (C.c_int32 * 2)(*desc.in_offset_px), desc.f, desc.L, desc.window,
+                  desc.det_window, getattr(desc, "precision", LMA_PREC_C64), getattr(desc, "phonon_batch", 0))
+    reg = _region(region)
+    L = C.c_int32()
+    err = C.c_double()
+    ctx.check(ctx.lib.lma_select_L(ctx.h, spec.h, C.byref(pr), C.byref(d), C.byref(reg), L_max, eps_sup,
+                                   C.byref(L), C.byref(err)))
+    return int(L.value), float(err.value)
 
 
 def image_many(ctx: Context, bases, detectors, regions, outs, recompute: bool = True,

@@ -19,7 +19,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _header_functions():
     src = open(os.path.join(ROOT, "include", "lma.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lma_[a-z0-9_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(lma_[A-Za-z0-9_]+)\s*\(", src)))
 
 
 def test_library_exports_every_declared_function():
@@ -181,3 +181,20 @@ def test_partition_validation():
         with pytest.raises(lma.LmaError) as e:
             basis.partition(region, strategy, M, start)
         assert e.value.status == lma.LMA_ERR_INVALID
+
+
+def test_select_L_equals_oracle():
+    import dataclasses
+    for w, region in ((WL.simple_cubic_workload(), WL.Region(0, 0, 6, 5, (2, 2))),
+                      (WL.perovskite_workload(cells=5, nx=256, n_slices=2, n_phonons=1), WL.Region(8, 4, 3, 3, (4, 4)))):
+        ctx, spec, basis = _host_objects(w)
+        prm = O.params_from_workload(w)
+        probes = O.region_probes(region.px0, region.py0, region.npx, region.npy, region.spacing_px,
+                                 w.grid.nx, w.grid.ny)
+        for eps in (0.3, 0.15, 0.08):
+            L, err = lma.select_L(ctx, spec, w.probe, w.basis, region, 40, eps)
+            L_ref, err_ref = O.select_L(dataclasses.replace(prm, L=40), probes, eps, 40)
+            assert L == L_ref and abs(err - err_ref) < 1e-9, (w.name, eps, L, L_ref, err, err_ref)
+        assert lma.select_L(ctx, spec, w.probe, w.basis, region, 2, 1e-9)[0] == 0
+        with pytest.raises(lma.LmaError):
+            lma.select_L(ctx, spec, w.probe, w.basis, region, 65, 0.1)
