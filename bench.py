@@ -428,6 +428,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--edits", type=int, default=24, help="column-edit requests timed (0: skip)")
     ap.add_argument("--serving", type=int, default=60, help="requests per offered load (0: skip)")
+    ap.add_argument("--no-realspace", dest="realspace", action="store_false",
+                    help="skip the real-space propagation measurement")
     ap.add_argument("--no-coherence", dest="coherence", action="store_false",
                     help="skip the partial-coherence (focal series) measurement")
     ap.add_argument("--no-partition", dest="partition", action="store_false",
@@ -630,6 +632,43 @@ def main():
                      "speedup_vs_separate_images": len(series) * ms_per_step / ms_c}
         del out_c
 
+    # ---- real-space propagation (Sec. 3.2): the propagation step as a K x K convolution,
+    # one configuration of the workload, against the Fourier step; the cost model of
+    # Sec. 3.2 predicts the ratio (1 + K^2) / (2 + 2 log2(W^2)) per slice
+    realspace = None
+    if args.realspace and rank == 0:
+        w1 = w.with_phonons(1)
+        spec1 = lma.Specimen(ctx, w1.grid, w1.potential, w1.phonons)
+        b1 = lma.Basis(ctx, spec1, w1.probe, w1.basis)
+        out1 = torch.empty_like(out)
+        rows = []
+
+        def timed_image(fn):
+            fn()
+            ctx.profile_enable(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            pr = ctx.profile_read()
+            ctx.profile_enable(False)
+            return e0.elapsed_time(e1), pr["slice"]["total_ms"]
+
+        ms_f, sl_f = timed_image(lambda: b1.image(dets, region, out=out1, recompute=True, stream=stream))
+        ref = out1.cpu().numpy()
+        for K in (3, 5, 7, 9, 13):
+            ms_r, sl_r = timed_image(lambda: b1.image_realspace(K, K, dets, region, out=out1, stream=stream))
+            img_r = out1.cpu().numpy()
+            rows.append({"K": K, "ms_per_image": ms_r, "slice_ms": sl_r, "slice_vs_fourier": sl_r / sl_f,
+                         "model_ratio": (1 + K * K) / (2 + 2 * 2 * np.log2(W)),
+                         "max_abs_diff_of_fourier_image_max": float(np.max(np.abs(img_r - ref)) / np.max(ref))})
+        realspace = {"workload": w1.name, "fourier": {"ms_per_image": ms_f, "slice_ms": sl_f}, "kernels": rows}
+        b1.close()
+        spec1.close()
+        del out1
+
     # ---- end to end through the public API with host buffers
     host_out = np.empty((len(dets), region.npy, region.npx), dtype=np.float64)
     h2d = sum(a.x.nbytes + a.y.nbytes + a.species.nbytes + 4 * (w.grid.n_slices + 1) for a in w.phonons)
@@ -727,6 +766,7 @@ def main():
             "stem34": stem34,
             "partition": partition,
             "coherence": coherence,
+            "realspace": realspace,
             "clocks": clk,
             "kernels": kernels,
             "wall_s_timed_region": wall,

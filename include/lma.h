@@ -49,6 +49,8 @@ typedef int32_t lma_status;
 
 #define LMA_BASIS_GAUSS 0      /* u = g_sigma (Sec. 4.2.3, Gaussians) */
 #define LMA_BASIS_PROBE 1      /* u = psi_0^init (Sec. 4.2.3, first paragraph) */
+#define LMA_BASIS_TRIG 2       /* u = phi_n(2 pi x / l_x) phi_n(2 pi y / l_y), trigonometric polynomials (Sec. 4.2.3) */
+#define LMA_BASIS_TRIG_RADIAL 3 /* u = phi_n(2 pi |v| / l_x), the circularly symmetric option (Sec. 4.2.3) */
 
 #define LMA_PREC_C64 0         /* complex64 everywhere on the device */
 #define LMA_PREC_MIXED 1       /* FP32 propagation; exit waves stored as FP16 pairs with a per-wave
@@ -131,6 +133,8 @@ typedef struct {
   int32_t precision;         /* LMA_PREC_C64 or LMA_PREC_MIXED */
   int32_t phonon_batch;      /* configurations propagated per launch and held at once;
                                 0 = as many as fit in 40 % of the free device memory */
+  int32_t trig_degree;       /* LMA_BASIS_TRIG*: degree n of phi_n(t) = sum_{|k|<=n} e^{ikt} cos(k pi/(2n+2));
+                                0 = round(alpha_max l_x / lambda) (maximum probe frequency / Fourier pixel) */
 } lma_basis_desc;
 
 /* Annular detector r1 <= lambda |k| < r2 (rad), intersected with the bandlimit (Sec. 3.1, 2D STEM). */
@@ -271,6 +275,20 @@ lma_status lma_image_rings(lma_ctx* ctx, lma_specimen* spec, lma_basis* basis, d
 lma_status lma_image_4d(lma_ctx* ctx, lma_specimen* spec, lma_basis* basis, int32_t half_x,
                         int32_t half_y, const lma_region* region, uint32_t flags, float* out,
                         void* stream);
+
+/* ---- real-space propagation (Sec. 3.2) --------------------------------------------------- */
+
+/* 2D STEM image with the propagation step of every slice computed as a periodic convolution
+ * on the W x W window with q discretized to K1 x K2 pixels (Sec. 3.2 costs it as N(XY +
+ * XY K1 K2) against N(2XY + 2XY log XY) for the Fourier step). q is the inverse DFT of the
+ * window propagator exp(-i pi lambda eps |k|^2) times the bandlimit (FP64, rounded once to
+ * complex64) at offsets -(K/2) .. K/2; with K1 = K2 = W it would reproduce the Fourier step.
+ * Always recomputes; afterwards the basis's stored exit waves are marked stale for
+ * lma_image. out as for lma_image. Errors: LMA_ERR_INVALID (K1 not odd in 3..13, K2 not odd
+ * in 1..25, bad detectors or region), LMA_ERR_UNSUPPORTED (mixed store). */
+lma_status lma_image_realspace(lma_ctx* ctx, lma_specimen* spec, lma_basis* basis, int32_t K1, int32_t K2,
+                               const lma_detector* det, int32_t n_det, const lma_region* region,
+                               uint32_t flags, double* out, void* stream);
 
 /* ---- partial coherence and the choice of L ---------------------------------------------- */
 

@@ -360,17 +360,39 @@ def class_key(p: Tuple[int, int], spacing: Tuple[int, int], offset: Tuple[int, i
     return ((p[0] - offset[0]) % (f * spacing[0]), (p[1] - offset[1]) % (f * spacing[1]))
 
 
+def trig_poly(n: int, t: np.ndarray) -> np.ndarray:
+    """phi_n(t) = sum_{k=-n..n} e^{ikt} cos(k pi / (2n + 2)) (Sec. 4.2.3, trigonometric
+    polynomials), real and even: 1 + 2 sum_{k=1..n} cos(k t) cos(k pi / (2n + 2))."""
+    out = np.ones_like(t, dtype=np.float64)
+    for k in range(1, n + 1):
+        out = out + 2.0 * np.cos(k * t) * math.cos(k * math.pi / (2 * n + 2))
+    return out
+
+
+def trig_degree(lam: float, alpha_max: float, lx: float) -> int:
+    """n = (alpha_max / lambda) / q with the Fourier pixel q = 1 / l_x, rounded to an integer."""
+    return int(round(alpha_max * lx / lam))
+
+
 def input_wave_window(kind: int, W: int, ny: int, nx: int, dy: float, dx: float, lam: float,
-                      alpha_max: float, cs: float, defocus: float, gauss_sigma: float
-                      ) -> np.ndarray:
+                      alpha_max: float, cs: float, defocus: float, gauss_sigma: float,
+                      degree: int = 0) -> np.ndarray:
     """The input wave u sampled on a W x W window with its centre at window pixel (W/2, W/2).
 
     kind 0: Gaussian g_sigma (Sec. 4.2.3, Gaussians), sigma = lambda/(2 alpha_max)
-    unless given; kind 1: the probe itself, u = psi_0^init (Sec. 4.2.3).
-    Offsets from the centre run over [-W/2, W/2), taken periodically on the
-    full grid.
+    unless given; kind 1: the probe itself, u = psi_0^init (Sec. 4.2.3); kind 2: the tensor
+    product phi_n(2 pi x / l_x) phi_n(2 pi y / l_y) of trigonometric polynomials; kind 3: the
+    radial phi_n(2 pi |v| / l_x). Degree n = ``degree`` or trig_degree(). Offsets from the
+    centre run over [-W/2, W/2), taken periodically on the full grid.
     """
     off = np.arange(W) - W // 2
+    if kind in (2, 3):
+        n = degree if degree > 0 else trig_degree(lam, alpha_max, nx * dx)
+        if kind == 2:
+            return np.outer(trig_poly(n, 2 * math.pi * off / ny), trig_poly(n, 2 * math.pi * off / nx)
+                            ).astype(np.complex128)
+        r = np.sqrt((off[:, None] * dy) ** 2 + (off[None, :] * dx) ** 2)
+        return trig_poly(n, 2 * math.pi * r / (nx * dx)).astype(np.complex128)
     if kind == 0:
         s = gauss_sigma if gauss_sigma > 0 else gaussian_width(lam, alpha_max)
         ry = off * dy
@@ -485,6 +507,7 @@ class LmaParams:
     L: int
     W: int
     D: int
+    trig_degree: int = 0      # input wave kinds 2, 3: degree n of phi_n (0: from alpha_max l_x / lambda)
 
     @property
     def dx(self) -> float:
@@ -508,14 +531,17 @@ class LmaOracle:
     propagations.
     """
 
-    def __init__(self, prm: LmaParams):
+    def __init__(self, prm: LmaParams, realspace: Tuple[int, int] | None = None):
+        """``realspace`` = (K1, K2): propagate with the K1 x K2 real-space kernel instead of
+        the Fourier step (Sec. 3.2)."""
         self.prm = prm
         p = prm
         self.lattice = input_lattice(p.nx, p.ny, p.in_spacing, p.in_offset, p.f)
         self.uW = input_wave_window(p.kind, p.W, p.ny, p.nx, p.dy, p.dx, p.lam, p.alpha_max,
-                                    p.cs, p.defocus, p.gauss_sigma)
+                                    p.cs, p.defocus, p.gauss_sigma, p.trig_degree)
         self.prop_W = fresnel_propagator(p.W, p.W, p.dy, p.dx, p.lam, p.slice_dz,
                                          p.bandlimit_frac)
+        self.qK = realspace_kernel(self.prop_W, realspace[0], realspace[1]) if realspace else None
         self._psi0 = None
         self._sets: Dict[Tuple[int, int], CoefficientSet] = {}
         self._t: Dict[int, np.ndarray] = {}
@@ -561,8 +587,13 @@ class LmaOracle:
     def exit_wave(self, phi: int, i: int) -> np.ndarray:
         if (phi, i) not in self._U:
             pos = (int(self.lattice[i, 0]), int(self.lattice[i, 1]))
-            self._U[(phi, i)] = translate_exit_wave(self.uW, self.transmission_stack(phi),
-                                                    self.prop_W, pos)
+            if self.qK is None:
+                self._U[(phi, i)] = translate_exit_wave(self.uW, self.transmission_stack(phi),
+                                                        self.prop_W, pos)
+            else:
+                W = self.prm.W
+                ts = periodic_crop(self.transmission_stack(phi), pos[1] - W // 2, pos[0] - W // 2, W, W)
+                self._U[(phi, i)] = multislice_realspace(self.uW, ts, self.qK)
         return self._U[(phi, i)]
 
     # -- image ----------------------------------------------------------------
@@ -650,7 +681,7 @@ def select_L(prm: LmaParams, probes: np.ndarray, eps_sup: float, L_max: int) -> 
     lat = input_lattice(prm.nx, prm.ny, prm.in_spacing, prm.in_offset, prm.f)
     psi0 = probe(prm.ny, prm.nx, prm.dy, prm.dx, prm.lam, prm.alpha_max, prm.cs, prm.defocus)
     uW = input_wave_window(prm.kind, prm.W, prm.ny, prm.nx, prm.dy, prm.dx, prm.lam, prm.alpha_max,
-                           prm.cs, prm.defocus, prm.gauss_sigma)
+                           prm.cs, prm.defocus, prm.gauss_sigma, prm.trig_degree)
     reps = {}
     for q in probes:
         key = class_key((int(q[0]), int(q[1])), prm.in_spacing, prm.in_offset, prm.f)
@@ -851,4 +882,5 @@ def params_from_workload(w) -> LmaParams:
                      bandlimit_frac=g.bandlimit_frac, alpha_max=pr.alpha_max, cs=pr.cs,
                      defocus=pr.defocus, kind=b.kind, gauss_sigma=b.gauss_sigma,
                      in_spacing=tuple(b.in_spacing_px), in_offset=tuple(b.in_offset_px),
-                     f=b.f, L=b.L, W=b.window, D=b.det_window)
+                     f=b.f, L=b.L, W=b.window, D=b.det_window,
+                     trig_degree=getattr(b, "trig_degree", 0))

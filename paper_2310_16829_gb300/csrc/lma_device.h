@@ -127,6 +127,9 @@ cudaError_t launch_potential(const PotArgs& a, cudaStream_t s);
 cudaError_t launch_slice(const SliceLaunch& a, bool even_origins, bool half, int mode, cudaStream_t s);
 int sm_count();
 cudaError_t launch_synth(const SynthArgs& a, bool half, int mode, cudaStream_t s);
+// step a3 with the propagation as a periodic convolution with the K1 x K2 kernel q (device,
+// [K2][K1] complex64, offsets -(K/2) .. K/2); K1 in {3, 5, ..., 13}, K2 odd <= 25; complex64 store
+cudaError_t launch_slice_rs(const SliceLaunch& a, const float2* q, int K1, int K2, cudaStream_t s);
 // out[i] = sum over variants v (in order) of w[v] * sum over n_cfg slots (in order) of
 // acc[(v * n_cfg + c) * n + i]; w has n_var entries on the device
 cudaError_t launch_finalize_variants(const double* acc, int64_t n, int n_cfg, int n_var, const double* w, double* out,

@@ -74,6 +74,9 @@ struct lma_ctx {
   // slice launch modes: forced (>= 0), or the timed choice per launch shape
   int forced_mode = -1;
   bool autotune = false;
+  // real-space propagation (lma_image_realspace): the K1 x K2 kernel of the call in progress
+  int rs_k1 = 0, rs_k2 = 0;
+  const float2* rs_q = nullptr;
   struct Tune {
     std::vector<int64_t> key;
     lma_tuning rec;
@@ -404,6 +407,8 @@ struct lma_basis {
   // partial coherence: coefficient tables of the probe variants of the last call
   std::vector<double> var_key;
   DevBuf d_var;                  // [n_var][n_probes][L] complex64 coefficients, then [n_var] weights
+  DevBuf d_rsq;                  // real-space propagation kernel [K2][K1] complex64
+  std::vector<int> rsq_key;
   bool dev_tables = false;
   int B = 0;                     // exit-wave store slots (configurations in flight)
   std::vector<int> U_phonon;     // configuration held by each slot (-1: none)
@@ -462,6 +467,32 @@ void build_input_wave(lma_basis* b) {
       for (int x = 0; x < kW; ++x) {
         const double rx = (x - kW / 2) * dx;
         b->uW[static_cast<size_t>(y) * kW + x] = cd(std::exp(-(ry * ry + rx * rx) / (2.0 * s * s)), 0.0);
+      }
+    }
+  } else if (b->desc.kind == LMA_BASIS_TRIG || b->desc.kind == LMA_BASIS_TRIG_RADIAL) {
+    // phi_n(t) = 1 + 2 sum_{k=1..n} cos(k t) cos(k pi / (2n + 2))
+    const int n = b->desc.trig_degree > 0 ? b->desc.trig_degree
+                                           : static_cast<int>(std::lround(b->probe.alpha_max * g.lx / g.lambda));
+    auto phi = [n](double t) {
+      double v = 1.0;
+      for (int k = 1; k <= n; ++k) v += 2.0 * std::cos(k * t) * std::cos(k * kPi / (2 * n + 2));
+      return v;
+    };
+    if (b->desc.kind == LMA_BASIS_TRIG) {
+      std::vector<double> py(kW), px(kW);
+      for (int i = 0; i < kW; ++i) {
+        py[i] = phi(2.0 * kPi * (i - kW / 2) / g.ny);
+        px[i] = phi(2.0 * kPi * (i - kW / 2) / g.nx);
+      }
+      for (int y = 0; y < kW; ++y)
+        for (int x = 0; x < kW; ++x) b->uW[static_cast<size_t>(y) * kW + x] = cd(py[y] * px[x], 0.0);
+    } else {
+      for (int y = 0; y < kW; ++y) {
+        const double ry = (y - kW / 2) * dy;
+        for (int x = 0; x < kW; ++x) {
+          const double rx = (x - kW / 2) * dx;
+          b->uW[static_cast<size_t>(y) * kW + x] = cd(phi(2.0 * kPi * std::sqrt(ry * ry + rx * rx) / g.lx), 0.0);
+        }
       }
     }
   } else {
@@ -889,6 +920,11 @@ lma_status slice_launch(lma_ctx* ctx, const lma_dev::SliceLaunch& L, bool even, 
       tuned = true;
     }
   if (ctx->forced_mode >= 0) mode = ctx->forced_mode;
+  if (ctx->rs_k1 > 0) {
+    CUDA_TRY(ctx, counted(ctx, K_SLICE, units, st,
+                          [&] { return lma_dev::launch_slice_rs(L, ctx->rs_q, ctx->rs_k1, ctx->rs_k2, st); }));
+    return LMA_OK;
+  }
   auto launch = [&](int m) {
     return counted(ctx, K_SLICE, units, st, [&] { return lma_dev::launch_slice(L, even, half, m, st); });
   };
@@ -1490,8 +1526,10 @@ lma_status lma_create_basis(lma_ctx* ctx, const lma_specimen* spec, const lma_pr
     return fail(ctx, LMA_ERR_UNSUPPORTED, "window and det_window must be %d", kW);
   if (g.nx < kW || g.ny < kW) return fail(ctx, LMA_ERR_UNSUPPORTED, "grid smaller than the window");
   if (!is_pow2(g.nx) || !is_pow2(g.ny)) return fail(ctx, LMA_ERR_UNSUPPORTED, "grid sizes must be powers of two");
-  if (d.kind != LMA_BASIS_GAUSS && d.kind != LMA_BASIS_PROBE)
+  if (d.kind != LMA_BASIS_GAUSS && d.kind != LMA_BASIS_PROBE && d.kind != LMA_BASIS_TRIG &&
+      d.kind != LMA_BASIS_TRIG_RADIAL)
     return fail(ctx, LMA_ERR_INVALID, "unknown input wave kind");
+  if (d.trig_degree < 0 || d.trig_degree > 4096) return fail(ctx, LMA_ERR_INVALID, "trig_degree must be in [0, 4096]");
   if (d.precision != LMA_PREC_C64 && d.precision != LMA_PREC_MIXED)
     return fail(ctx, LMA_ERR_INVALID, "precision must be LMA_PREC_C64 or LMA_PREC_MIXED");
   if (!(probe->alpha_max > 0)) return fail(ctx, LMA_ERR_INVALID, "alpha_max must be positive");
@@ -1557,6 +1595,7 @@ lma_status lma_free_basis(lma_basis* b) {
   b->d_pat_acc.release();
   b->d_plan.release();
   b->d_var.release();
+  b->d_rsq.release();
   b->d_Up.release();
   b->d_Upscale.release();
   b->reg.tidx.release();
@@ -1982,6 +2021,96 @@ static lma_status make_plan(lma_basis* b, const lma_region* r, const lma_partiti
   b->plan_d = *d;
   b->plan_valid = true;
   b->plan_dev = false;
+  return LMA_OK;
+}
+
+// q discretized to K1 x K2 pixels: the inverse DFT (FP64) of the window propagator
+// exp(-i pi lambda eps |k|^2) times the bandlimit, at offsets -(K/2) .. K/2
+static void realspace_kernel_host(const lma_basis* b, int K1, int K2, std::vector<float>& q) {
+  const lma_grid& g = b->spec->g;
+  const double dx = g.lx / g.nx, dy = g.ly / g.ny;
+  std::vector<cd> root(kW);
+  for (int m = 0; m < kW; ++m) root[m] = std::exp(cd(0.0, 2.0 * kPi * m / kW));
+  std::vector<cd> P(static_cast<size_t>(kW) * kW, cd(0.0, 0.0));
+  for (int iy = 0; iy < kW; ++iy) {
+    const int my = signed_index(iy, kW);
+    const double ky = my / (kW * dy);
+    for (int ix = 0; ix < kW; ++ix) {
+      const int mx = signed_index(ix, kW);
+      if (my * my + mx * mx > b->r2max) continue;
+      const double kx = mx / (kW * dx);
+      P[static_cast<size_t>(iy) * kW + ix] = std::exp(cd(0.0, -kPi * g.lambda * g.slice_dz * (ky * ky + kx * kx)));
+    }
+  }
+  q.assign(2 * static_cast<size_t>(K1) * K2, 0.f);
+  for (int a = 0; a < K2; ++a) {
+    const int oy = a - K2 / 2;
+    for (int c = 0; c < K1; ++c) {
+      const int ox = c - K1 / 2;
+      cd sum(0.0, 0.0);
+      for (int iy = 0; iy < kW; ++iy)
+        for (int ix = 0; ix < kW; ++ix)
+          sum += P[static_cast<size_t>(iy) * kW + ix] * root[mod(iy * oy + ix * ox, kW)];
+      sum /= static_cast<double>(kW) * kW;
+      q[2 * (static_cast<size_t>(a) * K1 + c)] = static_cast<float>(sum.real());
+      q[2 * (static_cast<size_t>(a) * K1 + c) + 1] = static_cast<float>(sum.imag());
+    }
+  }
+}
+
+lma_status lma_image_realspace(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, int32_t K1, int32_t K2,
+                               const lma_detector* det, int32_t n_det, const lma_region* region, uint32_t flags,
+                               double* out, void* stream) {
+  if (!ctx || !sp || !b || !out || !region) return fail(ctx, LMA_ERR_INVALID, "null argument");
+  if (b->spec != sp) return fail(ctx, LMA_ERR_INVALID, "basis belongs to another specimen");
+  if (K1 < 3 || K1 > 13 || (K1 & 1) == 0) return fail(ctx, LMA_ERR_INVALID, "K1 must be odd in 3..13");
+  if (K2 < 1 || K2 > 25 || (K2 & 1) == 0) return fail(ctx, LMA_ERR_INVALID, "K2 must be odd in 1..25");
+  if (b->desc.precision != LMA_PREC_C64)
+    return fail(ctx, LMA_ERR_UNSUPPORTED, "real-space propagation writes the complex64 store only");
+  if (n_det <= 0 || n_det > lma_dev::kMaxDet || !det)
+    return fail(ctx, LMA_ERR_INVALID, "need 1..%d detectors", lma_dev::kMaxDet);
+  for (int d = 0; d < n_det; ++d)
+    if (!(det[d].r1 >= 0) || !(det[d].r2 > det[d].r1)) return fail(ctx, LMA_ERR_INVALID, "detector %d: need 0 <= r1 < r2", d);
+  lma_status s = validate_region(ctx, b, region);
+  if (s != LMA_OK) return s;
+  if (!device_ready(ctx)) return fail(ctx, LMA_ERR_UNSUPPORTED, "no device in this context");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((s = ensure_basis_device(b, st)) != LMA_OK) return s;
+  if ((s = build_region(b, region, st)) != LMA_OK) return s;
+  if ((s = build_detectors(b, det, n_det, st)) != LMA_OK) return s;
+  const std::vector<int> key{K1, K2};
+  if (!b->d_rsq.p || key != b->rsq_key) {
+    std::vector<float> q;
+    realspace_kernel_host(b, K1, K2, q);
+    CUDA_TRY(ctx, ensure(b->d_rsq, q.size() * sizeof(float)));
+    CUDA_TRY(ctx, upload(ctx, b->d_rsq.p, q.data(), q.size() * sizeof(float), st));
+    b->rsq_key = key;
+  }
+  const bool dev_out = is_device_pointer(out);
+  struct RealSpace {
+    lma_ctx* c;
+    RealSpace(lma_ctx* c_, int k1, int k2, const void* q) : c(c_) {
+      c->rs_k1 = k1;
+      c->rs_k2 = k2;
+      c->rs_q = static_cast<const float2*>(q);
+    }
+    ~RealSpace() {
+      c->rs_k1 = 0;
+      c->rs_k2 = 0;
+      c->rs_q = nullptr;
+    }
+  } scope(ctx, K1, K2, b->d_rsq.p);
+  s = image_work(b, sp, n_det, true, dev_out ? out : nullptr, st);
+  // the store now holds real-space waves: the Fourier path must not reuse them
+  std::fill(b->valid.begin(), b->valid.end(), 0);
+  std::fill(b->U_phonon.begin(), b->U_phonon.end(), -1);
+  if (s != LMA_OK) return s;
+  (void)flags;
+  if (!dev_out) {
+    const int64_t nout = b->reg.n_probes * n_det;
+    CUDA_TRY(ctx, read_back(ctx, out, basis_result(b, sp, n_det), static_cast<size_t>(nout) * sizeof(double), st));
+  }
+  CUDA_TRY(ctx, cudaGetLastError());
   return LMA_OK;
 }
 

@@ -525,6 +525,85 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
 }
 
 // ------------------------------------------------------------------------------------------
+// step a3, real-space variant: the propagation step as a convolution with the K1 x K2
+// kernel q (Sec. 3.2, complexity paragraph). One CTA per translate, the wave in shared
+// memory; thread (lane, warp) accumulates the 32 outputs x = lane + 32 m (m < 4), y =
+// 8 warp + j (j < 8) in registers: out(x, y) = sum over offsets (oy, ox) of q(oy, ox) psi(y -
+// oy, x - ox), periodic on the window. MB columns share one register segment of K1 inputs.
+// ------------------------------------------------------------------------------------------
+template <int K1, int MB>
+__global__ void __launch_bounds__(kThreads, 1) k_slice_rs(const SliceLaunch a, const float2* qg, const int K2) {
+  extern __shared__ __align__(16) float2 sm[];
+  float2* psi = sm;                 // [W][W]
+  float2* q = sm + kW * kW;         // [K2][K1]
+  const int T = threadIdx.x, lane = T & 31, wy = T >> 5;
+  for (int i = T; i < K1 * K2; i += kThreads) q[i] = qg[i];
+  for (int li = blockIdx.x; li < a.n_list; li += gridDim.x) {
+    int jb = 0;
+    while (jb + 1 < a.n_jobs && li >= a.start[jb + 1]) ++jb;
+    const SliceJob& J = a.job[jb];
+    const int item = a.list[li];
+    const int cfg = item / J.n_translates;
+    const int ti = item - cfg * J.n_translates;
+    const int ia = ti % J.lat_nax, ib = ti / J.lat_nax;
+    int ox = (J.lat_ox + ia * J.lat_sx - kW / 2) % J.nx;
+    if (ox < 0) ox += J.nx;
+    int oy = (J.lat_oy + ib * J.lat_sy - kW / 2) % J.ny;
+    if (oy < 0) oy += J.ny;
+    const int pitch = J.nx + kW;
+    const size_t slice_elems = static_cast<size_t>(pitch) * (J.ny + kW);
+    const float2* tb = J.t + cfg * J.t_slot + static_cast<size_t>(oy) * pitch + ox;
+    __syncthreads();   // the previous item's reads of psi are done
+    for (int p = T; p < kW * kW; p += kThreads) psi[p] = J.uW[p];
+    for (int s = 0; s < J.n_slices; ++s) {
+      // transmission (Sec. 3.2): psi <- t_s psi
+      __syncthreads();
+      const float2* ts = tb + s * slice_elems;
+      for (int p = T; p < kW * kW; p += kThreads) psi[p] = cmul(psi[p], ts[static_cast<size_t>(p >> 7) * pitch + (p & 127)]);
+      __syncthreads();
+      // propagation: periodic convolution with q
+      float2 acc[8][4];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) acc[j][m] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int mb = 0; mb < 4; mb += MB) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int y = 8 * wy + j;
+#pragma unroll 1
+          for (int dyi = 0; dyi < K2; ++dyi) {
+            const float2* row = psi + ((y - (dyi - K2 / 2)) & (kW - 1)) * kW;
+            float2 seg[MB][K1];
+#pragma unroll
+            for (int mm = 0; mm < MB; ++mm)
+#pragma unroll
+              for (int dxi = 0; dxi < K1; ++dxi)
+                seg[mm][dxi] = row[(lane + 32 * (mb + mm) - (dxi - K1 / 2)) & (kW - 1)];
+#pragma unroll
+            for (int dxi = 0; dxi < K1; ++dxi) {
+              const float2 qv = q[dyi * K1 + dxi];
+#pragma unroll
+              for (int mm = 0; mm < MB; ++mm) acc[j][mb + mm] = cfma(acc[j][mb + mm], qv, seg[mm][dxi]);
+            }
+          }
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) psi[(8 * wy + j) * kW + lane + 32 * m] = acc[j][m];
+    }
+    __syncthreads();
+    const int oi = a.out_index ? a.out_index[li] : ti;
+    float2* ud = J.U + cfg * J.u_slot + static_cast<size_t>(oi) * (kW * kW);
+    for (int p = T; p < kW * kW; p += kThreads) ud[p] = psi[p];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // steps a4-a6: synthesis and detector reading
 // ------------------------------------------------------------------------------------------
 constexpr int kSynthSmemFloat2 = kX1 + kTwA + 128 + (kThreads / 32) * kMaxDet;
@@ -919,6 +998,7 @@ cudaError_t noalloc_scratch(void** ptr) {
 // ------------------------------------------------------------------------------------------
 size_t slice_smem_bytes() { return static_cast<size_t>(kSliceSmemFloat2) * sizeof(float2); }
 size_t synth_smem_bytes() { return static_cast<size_t>(kSynthSmemFloat2) * sizeof(float2); }
+size_t slice_rs_smem_bytes() { return static_cast<size_t>(kW * kW + 32 * 32) * sizeof(float2); }
 
 cudaError_t init_device_constants() {
   float2 w[128];
@@ -934,6 +1014,10 @@ cudaError_t init_device_constants() {
   if ((e = cudaFuncSetAttribute(k_slice<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_slice<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_slice<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
+  const int sr = static_cast<int>(slice_rs_smem_bytes());
+  for (auto f : {k_slice_rs<3, 4>, k_slice_rs<5, 4>, k_slice_rs<7, 4>, k_slice_rs<9, 2>, k_slice_rs<11, 2>,
+                 k_slice_rs<13, 2>})
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sr)) != cudaSuccess) return e;
   for (auto f : {k_synth_detect<false, kReadAnnuli>, k_synth_detect<true, kReadAnnuli>,
                  k_synth_detect<false, kReadLabels>, k_synth_detect<true, kReadLabels>,
                  k_synth_detect<false, kReadPattern>, k_synth_detect<true, kReadPattern>})
@@ -976,6 +1060,22 @@ cudaError_t launch_slice(const SliceLaunch& a, bool even_origins, bool half, int
   if (!even_origins && !half) k_slice<false, false><<<grid, kThreads, sm, s>>>(a, mode);
   if (even_origins && half) k_slice<true, true><<<grid, kThreads, sm, s>>>(a, mode);
   if (!even_origins && half) k_slice<false, true><<<grid, kThreads, sm, s>>>(a, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slice_rs(const SliceLaunch& a, const float2* q, int K1, int K2, cudaStream_t s) {
+  if (a.n_list <= 0) return cudaSuccess;
+  if (K2 < 1 || K2 > 25 || (K2 & 1) == 0) return cudaErrorInvalidValue;
+  const size_t sm = slice_rs_smem_bytes();
+  switch (K1) {
+    case 3: k_slice_rs<3, 4><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
+    case 5: k_slice_rs<5, 4><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
+    case 7: k_slice_rs<7, 4><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
+    case 9: k_slice_rs<9, 2><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
+    case 11: k_slice_rs<11, 2><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
+    case 13: k_slice_rs<13, 2><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

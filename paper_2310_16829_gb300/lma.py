@@ -30,6 +30,8 @@ STATUS_NAMES = {0: "LMA_OK", 1: "LMA_ERR_INVALID", 2: "LMA_ERR_OOM", 3: "LMA_ERR
 
 LMA_BASIS_GAUSS = 0
 LMA_BASIS_PROBE = 1
+LMA_BASIS_TRIG = 2
+LMA_BASIS_TRIG_RADIAL = 3
 LMA_PREC_C64 = 0
 LMA_PREC_MIXED = 1
 LMA_EDIT_REMOVE = 0
@@ -59,7 +61,7 @@ EXPORTS = [
     "lma_affected_probes",
     "lma_profile_enable", "lma_profile_read", "lma_readout_noalloc",
     "lma_set_slice_mode", "lma_tuning_read", "lma_partition", "lma_image_partitioned",
-    "lma_image_coherent", "lma_select_L",
+    "lma_image_coherent", "lma_select_L", "lma_image_realspace",
 ]
 
 
@@ -88,7 +90,7 @@ class BasisDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("gauss_sigma", C.c_double), ("in_spacing_px", C.c_int32 * 2),
                 ("in_offset_px", C.c_int32 * 2), ("f", C.c_int32), ("L", C.c_int32),
                 ("window", C.c_int32), ("det_window", C.c_int32), ("precision", C.c_int32),
-                ("phonon_batch", C.c_int32)]
+                ("phonon_batch", C.c_int32), ("trig_degree", C.c_int32)]
 
 
 class Detector(C.Structure):
@@ -175,6 +177,8 @@ _SIGS = {
     "lma_readout_noalloc": (C.c_int32, [_VP, _VP, _VP, C.POINTER(Detector), C.c_int32, C.POINTER(Region),
                                         _VP, _VP]),
     "lma_set_slice_mode": (C.c_int32, [_VP, C.c_int32]),
+    "lma_image_realspace": (C.c_int32, [_VP, _VP, _VP, C.c_int32, C.c_int32, C.POINTER(Detector), C.c_int32,
+                                        C.POINTER(Region), C.c_uint32, _VP, _VP]),
     "lma_image_coherent": (C.c_int32, [_VP, _VP, _VP, C.POINTER(Probe), C.POINTER(C.c_double), C.c_int32,
                                        C.POINTER(Detector), C.c_int32, C.POINTER(Region), C.c_uint32, _VP, _VP]),
     "lma_select_L": (C.c_int32, [_VP, _VP, C.POINTER(Probe), C.POINTER(BasisDesc), C.POINTER(Region), C.c_int32,
@@ -366,7 +370,7 @@ class Basis:
         d = BasisDesc(desc.kind, desc.gauss_sigma, (C.c_int32 * 2)(*desc.in_spacing_px),
                       (C.c_int32 * 2)(*desc.in_offset_px), desc.f, desc.L, desc.window,
                       desc.det_window, getattr(desc, "precision", LMA_PREC_C64),
-                      getattr(desc, "phonon_batch", 0))
+                      getattr(desc, "phonon_batch", 0), getattr(desc, "trig_degree", 0))
         h = _VP()
         ctx.check(ctx.lib.lma_create_basis(ctx.h, spec.h, C.byref(pr), C.byref(d), C.byref(h)))
         self.h = h
@@ -430,6 +434,17 @@ class Basis:
         flags = LMA_IMAGE_RECOMPUTE if recompute else 0
         self.ctx.check(self.ctx.lib.lma_image_4d(self.ctx.h, self.spec.h, self.h, half_x, half_y,
                                                  C.byref(reg), flags, _ptr(out), _stream(stream)))
+        return out
+
+    def image_realspace(self, K1: int, K2: int, detectors, region, out=None, stream=None):
+        """Image with the propagation step as a K1 x K2 real-space convolution."""
+        dets = (Detector * len(detectors))(*[Detector(d.r1, d.r2) for d in detectors])
+        if out is None:
+            out = np.empty((len(detectors), region.npy, region.npx), dtype=np.float64)
+        reg = _region(region)
+        self.ctx.check(self.ctx.lib.lma_image_realspace(self.ctx.h, self.spec.h, self.h, K1, K2, dets,
+                                                        len(detectors), C.byref(reg), 0, _ptr(out),
+                                                        _stream(stream)))
         return out
 
     def image_coherent(self, variants, detectors, region, out=None, recompute: bool = False, stream=None):
@@ -513,7 +528,8 @@ def select_L(ctx: Context, spec: "Specimen", probe, desc, region, L_max: int, ep
     pr = Probe(probe.alpha_max, probe.cs, probe.defocus)
     d = BasisDesc(desc.kind, desc.gauss_sigma, (C.c_int32 * 2)(*desc.in_spacing_px),
                   (C.c_int32 * 2)(*desc.in_offset_px), desc.f, desc.L, desc.window,
-                  desc.det_window, getattr(desc, "precision", LMA_PREC_C64), getattr(desc, "phonon_batch", 0))
+                  desc.det_window, getattr(desc, "precision", LMA_PREC_C64), getattr(desc, "phonon_batch", 0),
+                  getattr(desc, "trig_degree", 0))
     reg = _region(region)
     L = C.c_int32()
     err = C.c_double()

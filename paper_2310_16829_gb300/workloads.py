@@ -34,6 +34,8 @@ SIGMA_CFG0 = 7.29e-4
 # Basis kinds and store precisions (mirror LMA_BASIS_* / LMA_PREC_* in include/lma.h).
 BASIS_GAUSS = 0
 BASIS_PROBE = 1
+BASIS_TRIG = 2
+BASIS_TRIG_RADIAL = 3
 PREC_C64 = 0
 PREC_MIXED = 1
 
@@ -99,6 +101,7 @@ class BasisDesc:
     det_window: int = 128
     precision: int = PREC_C64
     phonon_batch: int = 0                    # configurations per launch; 0 = by free memory
+    trig_degree: int = 0                     # BASIS_TRIG*: degree of phi_n; 0 = alpha_max l_x / lambda
 
 
 @dataclass

@@ -198,3 +198,12 @@ def test_select_L_equals_oracle():
         assert lma.select_L(ctx, spec, w.probe, w.basis, region, 2, 1e-9)[0] == 0
         with pytest.raises(lma.LmaError):
             lma.select_L(ctx, spec, w.probe, w.basis, region, 65, 0.1)
+
+
+@pytest.mark.parametrize("kind", [WL.BASIS_TRIG, WL.BASIS_TRIG_RADIAL])
+def test_trig_input_waves_coefficients_match_oracle(kind):
+    w = WL.simple_cubic_workload()
+    w.basis.kind = kind
+    _check_coefficients(w, [(0, 0), (8, 120), (127, 3)], tol=1e-8)
+    w.basis.trig_degree = 9
+    _check_coefficients(w, [(0, 0), (40, 40)], tol=1e-8)

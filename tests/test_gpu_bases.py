@@ -1,0 +1,36 @@
+"""Trigonometric input waves (Sec. 4.2.3: the tensor product phi_n(x) phi_n(y) and the radial
+phi_n(|v|)) through the GPU path against the FP64 oracle. Tolerance as for the 3D STEM rings:
+1e-4 x max(reading, 1e-4 of the beam) (complex64 rounding floor on weak readings)."""
+import numpy as np
+import pytest
+
+from oracle import lma_oracle as O
+from paper_2310_16829_gb300 import lma, workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return lma.Context(0)
+
+
+@pytest.mark.parametrize("kind", [WL.BASIS_TRIG, WL.BASIS_TRIG_RADIAL])
+def test_trig_input_waves_match_oracle(ctx, kind):
+    for w, region in ((WL.simple_cubic_workload(), WL.Region(0, 0, 3, 2, (8, 8))),
+                      (WL.perovskite_workload(cells=5, nx=256, n_slices=5, n_phonons=1, seed_base=2800),
+                       WL.Region(252, 20, 3, 3, (4, 4)))):
+        w.basis.kind = kind
+        dets = [WL.Detector(0.0, 0.02), WL.Detector(0.06, 0.2)]
+        spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+        basis = lma.Basis(ctx, spec, w.probe, w.basis)
+        got = basis.image(dets, region, recompute=True).reshape(2, -1)
+        orc = O.LmaOracle(O.params_from_workload(w))
+        orc.set_specimen(w.phonons, w.potential.peak, w.potential.term_frac, w.potential.term_width,
+                         w.potential.r_cut)
+        ref = orc.image(dets, O.region_probes(region.px0, region.py0, region.npx, region.npy,
+                                             region.spacing_px, w.grid.nx, w.grid.ny))
+        err = np.abs(got - ref) / np.maximum(ref, 1e-4)
+        assert err.max() < 1e-4, (w.name, kind, err.max())

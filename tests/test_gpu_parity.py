@@ -278,3 +278,22 @@ def test_profile_counts_launches(ctx):
     assert prof["synth"]["launches"] == 1 and prof["finalize"]["launches"] == 1
     assert prof["slice"]["units"] == 1024 * 10
     assert prof["slice"]["total_ms"] > 0
+
+
+@pytest.mark.slow
+def test_serving_specimen_1024_100_slices_sampled_pixels(ctx):
+    """The largest workload: 20 x 20 ABO3 cells on 1024^2, 100 slices (200 A), 65536
+    resident exit waves, in the launch configuration of the edit and serving measurements;
+    the oracle recomputes a seeded sample of pixels (bright field and HAADF) one by one."""
+    w = WL.serving_workload()
+    dets = [WL.Detector(0.0, 0.02), WL.Detector(0.07, 0.2)]
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    img = basis.image(dets, w.region, recompute=True)
+    sample = WL.sample_probes(w.region, 3, seed=13)
+    pix = np.stack([w.region.px0 + sample[:, 0] * w.region.spacing_px[0],
+                    w.region.py0 + sample[:, 1] * w.region.spacing_px[1]], axis=1)
+    ref = _oracle(w).image(dets, pix)
+    got = img[:, sample[:, 1], sample[:, 0]]
+    assert _rel_pixel_err(got[0], ref[0]) < PIXEL_TOL
+    _assert_image(got[1], ref[1])

@@ -686,3 +686,47 @@ def test_select_L_is_the_smallest_L_meeting_the_target():
     pp = dataclasses.replace(prm, kind=1, in_offset=(0, 0))
     L, e = O.select_L(pp, probes, 1e-12, 4)
     assert L == 1 and e < 1e-12
+
+
+def test_realspace_lma_with_the_full_kernel_is_the_fourier_lma():
+    prm = _small_params(L=8, n_slices=2, alpha_max=0.03)
+    probes = np.array([[0, 0], [6, 10]])
+    dets = [_Det(0.0, 0.02), _Det(0.03, 0.066)]
+    fourier = _toy_specimen(O.LmaOracle(prm)).image(dets, probes)
+    full = _toy_specimen(O.LmaOracle(prm, realspace=(prm.W, prm.W))).image(dets, probes)
+    assert rel(full, fourier) < 1e-12
+    small = _toy_specimen(O.LmaOracle(prm, realspace=(5, 5))).image(dets, probes)
+    assert 1e-6 < rel(small, fourier) < 1.0      # an approximation, not the Fourier image
+
+
+# --------------------------------------------------------------------------- trigonometric input waves
+
+def test_trig_polynomial_has_the_stated_coefficients():
+    # phi_n sampled at M >= 2n + 1 points of one period: its DFT holds cos(k pi / (2n + 2)) at
+    # |k| <= n (times M) and nothing else; phi_n(0) = cot(pi / (4n + 4))
+    for n, M in ((3, 16), (7, 32), (12, 25)):
+        t = 2 * math.pi * np.arange(M) / M
+        c = np.fft.fft(O.trig_poly(n, t)) / M
+        for k in range(M):
+            kk = k if k <= M // 2 else k - M
+            expect = math.cos(kk * math.pi / (2 * n + 2)) if abs(kk) <= n else 0.0
+            assert abs(c[k] - expect) < 1e-12, (n, k)
+        assert abs(O.trig_poly(n, np.zeros(1))[0] - 1 / math.tan(math.pi / (4 * n + 4))) < 1e-12
+
+
+def test_trig_input_waves_tensor_and_radial():
+    W, n_grid, d, lam, amax = 32, 64, 0.1, 0.025, 0.02
+    n = O.trig_degree(lam, amax, n_grid * d)
+    assert n == round(amax * n_grid * d / lam)
+    u = O.input_wave_window(2, W, n_grid, n_grid, d, d, lam, amax, 0.0, 0.0, 0.0)
+    phi = O.trig_poly(n, 2 * math.pi * (np.arange(W) - W // 2) / n_grid)
+    assert np.allclose(u.real, np.outer(phi, phi), atol=1e-13, rtol=0) and np.all(u.imag == 0)
+    assert abs(u[W // 2, W // 2] - (1 / math.tan(math.pi / (4 * n + 4))) ** 2) < 1e-10
+    ur = O.input_wave_window(3, W, n_grid, n_grid, d, d, lam, amax, 0.0, 0.0, 0.0)
+    off = np.arange(W) - W // 2
+    r = np.hypot(off[:, None], off[None, :])
+    for a, b in ((3, 4), (0, 5), (5, 12), (6, 8)):     # equal radii -> equal values
+        pts = [(a, b), (b, a), (-a, b), (a, -b)]
+        vals = [ur[W // 2 + y, W // 2 + x] for y, x in pts]
+        assert np.ptp(np.real(vals)) < 1e-13
+    assert abs(ur[W // 2, W // 2 + 5] - ur[W // 2 + 3, W // 2 + 4]) < 1e-13 and r[W // 2 + 3, W // 2 + 4] == 5
