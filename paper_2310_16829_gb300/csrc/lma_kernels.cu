@@ -230,23 +230,13 @@ __device__ __forceinline__ void passB_inv(float2 (&a)[16], const float2* twB) {
   for (int q = 0; q < 4; ++q) dft4<true>(a[q * 4 + 0], a[q * 4 + 1], a[q * 4 + 2], a[q * 4 + 3]);
 }
 
-// shared-memory layouts of the exchanges (float2 units); row paddings keep the
-// 64-bit accesses of every half-warp on 16 distinct bank pairs and make every
-// address a per-thread base plus a compile-time offset
-//   X1 (A <-> B), 512 x 34 entries: element (y, r, k1) at TA*34 + k1, TA = 4y + r
+// shared-memory layouts of the synthesis kernel's exchanges (float2 units); row
+// paddings keep the 64-bit accesses of every half-warp on 16 distinct bank pairs and
+// make every address a per-thread base plus a compile-time offset
+//   X1 (A -> B), 512 x 34 entries: element (y, r, k1) at TA*34 + k1, TA = 4y + r
 //      (A writes two entries per 128-bit store: 8 lanes on 8 distinct 16-byte slots)
-//   X2 (B <-> C), 16384 entries: element (k1y, k2x, n2y, k1x) at ((k1y*4 + k2x)*32 + n2y)*32 + k1x
-//   X4 (B -> A, one half), 512 x 18 entries: element (y, r, k1 mod 16) at TA*18 + (k1 & 15)
-//      (A reads two entries per 128-bit load)
+//   X2 (B -> C), 16384 entries: element (k1y, k2x, n2y, k1x) at ((k1y*4 + k2x)*32 + n2y)*32 + k1x
 constexpr int kX1 = 512 * 34;
-constexpr int kTPitch = 132;          // staged transmission: W rows of 132 entries (= kX1 entries)
-static_assert(kW * kTPitch <= kX1, "staged transmission must fit the exchange region");
-constexpr int kX4 = 512 * 18;
-__device__ __forceinline__ int x1_addr(int ta, int k1) { return ta * 34 + k1; }
-__device__ __forceinline__ int x2_addr(int k1y, int k2x, int n2y, int k1x) {
-  return ((k1y * 4 + k2x) * 32 + n2y) * 32 + k1x;
-}
-__device__ __forceinline__ int x4_addr(int ta, int k1) { return ta * 18 + (k1 & 15); }
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
@@ -274,22 +264,46 @@ __device__ __forceinline__ void load_twiddles(float2* twA, float2* twB, int T) {
 // ------------------------------------------------------------------------------------------
 // step a3: slice kernel
 // ------------------------------------------------------------------------------------------
-constexpr int kSliceSmemFloat2 = kX1 + kX4 + kTwA + 128 + 128;
+// The slice kernel keeps every exchange in one table of 512 rows x 33 entries (row TA =
+// 4 y + r, entry k), and every thread writes only the entries it has just read:
+//   A thread (y, r):   row TA = T, entries 0..31: its pass-A outputs k1 (X1), later its
+//                      pass-B-inverse inputs (X4)
+//   B thread (k1, n2y): entries k1 of rows 4 (32 q + n2y) + r, q, r < 4: X1 element
+//                      (y = 32 q + n2y, r, k1) at slot (q, r); its pass-B output (k1y, k2x)
+//                      goes to slot (q, r) = (k2x, k1y) (X2) and its inverse output
+//                      (q, r) back to slot (q, r) (X4)
+//   C thread (kx, k1y): entry k1x of rows 4 (32 k2x + j) + k1y, j < 32 (read, write back)
+//   warp w:            rows 32 w .. 32 w + 31 (1056 entries) also hold the transmission
+//                      of its 8 window rows y = 8 w .. 8 w + 7 as 8 rows of 132 entries
+// No entry is written by one thread while another thread of the CTA may still read it,
+// so the only CTA barriers are the four that publish a phase's writes (read-after-write);
+// the transmission is shared within a warp only (__syncwarp). The odd row length keeps
+// every 64-bit access of a half-warp on 16 distinct bank pairs: A rows are 16
+// consecutive TA, B and C entries 16 consecutive k of one row.
+constexpr int kXP = 33;
+constexpr int kXRows = 512 * kXP;
+constexpr int kTRow = 132;   // staged transmission row: 4 table rows
+static_assert(8 * kTRow == 32 * kXP, "a warp's 8 transmission rows fill its 32 table rows");
+constexpr int kSliceSmemFloat2 = kXRows + kTwA + 128 + 128;
 
-// Stage a W x W window of one slice into R0 (asynchronous, completed by
-// cp_async_wait_all + __syncthreads). With an even window origin every row is
-// copied in 16-byte pieces, a warp covering 512 contiguous bytes; with an odd
-// origin in 8-byte pieces.
+// Warp w copies window rows 8 w .. 8 w + 7 of one slice (g points at the first) into its
+// table rows (asynchronous; the warp's threads read them after cp_async_wait_all and
+// __syncwarp). With an even window origin in 16-byte pieces, 512 contiguous bytes per
+// instruction; with an odd origin in 8-byte pieces.
 template <bool EVEN>
-__device__ __forceinline__ void stage_t(float2* sdst, const float2* g, int pitch) {
+__device__ __forceinline__ void stage_t_warp(float2* region, const float2* g, int pitch, int lane) {
   if (EVEN) {
-    const size_t step = static_cast<size_t>(8) * pitch;
 #pragma unroll
-    for (int i = 0; i < 16; ++i, g += step) cp_async16(sdst + i * 8 * kTPitch, g);
+    for (int i = 0; i < 16; ++i) {
+      const int yl = i >> 1, x = 64 * (i & 1) + 2 * lane;
+      cp_async16(region + yl * kTRow + x, g + static_cast<size_t>(yl) * pitch + x);
+    }
   } else {
-    const size_t step = static_cast<size_t>(4) * pitch;
 #pragma unroll
-    for (int i = 0; i < 32; ++i, g += step) cp_async8(sdst + i * 4 * kTPitch, g);
+    for (int i = 0; i < 32; ++i) {
+      const int yl = i >> 2, x = 32 * (i & 3) + lane;
+      cp_async8(region + yl * kTRow + x, g + static_cast<size_t>(yl) * pitch + x);
+    }
   }
   cp_async_commit();
 }
@@ -300,15 +314,14 @@ __device__ __forceinline__ void stage_t(float2* sdst, const float2* g, int pitch
 template <bool EVEN, bool HALF>
 __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, const int mode) {
   extern __shared__ __align__(16) float2 sm[];
-  float2* R0 = sm;             // t prefetch (thread-private slots n1*512 + T) / exchanges X1, X2
-  float2* R1 = sm + kX1;       // exchange X4 (two halves)
-  float2* twA = R1 + kX4;
+  float2* X = sm;              // exchange table, 512 rows x kXP
+  float2* twA = X + kXRows;
   float2* twB = twA + kTwA;
   float2* eys = twB + 128;     // eys[k1y*32 + j] = e_y(k1y + 4 j)
 
   const int T = threadIdx.x;
   load_twiddles(twA, twB, T);
-  // A layout: thread (y, r)
+  // A layout: thread (y, r), TA = T
   const int ya = T >> 2, ra = T & 3;
   // B layout: groups (k1 = (T & 15) + 16 h, n2y = T >> 4), h = 0, 1
   const int k1lo = T & 15, n2y = T >> 4;
@@ -324,15 +337,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
   bool c_live = false;
   int cur_job = -1;
   __shared__ int s_next;
-  // t staging: row-major W x 132 tile in R0 (the 132-float2 row keeps the A-layout
-  // reads of 8 rows x 4 columns on distinct banks); element (y, x) at y * 132 + x
-  float2* const tA_rd = R0 + ya * kTPitch + ra;                   // + 4 * n1
-  float4* const x1w = reinterpret_cast<float4*>(R0 + T * 34);     // A side of X1 (pairs)
-  float2* const x1r = R0 + (4 * n2y) * 34 + k1lo;                 // B side of X1, + (128 q + r) * 34
-  float2* const x2b = R0 + n2y * 32 + k1lo;                       // B side of X2, + (q*4 + r) * 1024
-  float2* const x2c = R0 + (k1y * 4 + k2x) * 1024 + k1x;          // C side of X2, + j * 32
-  float2* const x4w = R1 + (4 * n2y) * 18 + k1lo;                 // B side of X4, + (128 q + r) * 18
-  const float4* const x4r = reinterpret_cast<const float4*>(R1 + T * 18);   // A side of X4 (pairs)
+  float2* const xa = X + T * kXP;                                 // A row, + n or k1
+  float2* const xb = X + (4 * n2y) * kXP + k1lo;                  // B slot (q, r): + (128 q + r) * kXP, + 16 (h = 1)
+  float2* const xc = X + (128 * k2x + k1y) * kXP + k1x;           // C entry j: + 4 j * kXP
+  const int lane = T & 31;
+  float2* const xw = X + (T >> 5) * (32 * kXP);                   // this warp's table rows
+  const float2* const tr = xw + (ya & 7) * kTRow + ra;            // t(y, 4 n + r) at + 4 n
 
   __syncthreads();   // twiddles
 
@@ -350,8 +360,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
     while (jb + 1 < a.n_jobs && li >= a.start[jb + 1]) ++jb;
     const SliceJob& J = a.job[jb];
     if (jb != cur_job) {
-      // the previous item's last barrier has passed: eys is free; the staging barrier
-      // below publishes it before pass C reads it
+      // the previous item's last barrier has passed: eys is free; the X1 barrier below
+      // publishes it before pass C reads it
       cur_job = jb;
       if (T < 128) eys[(T & 3) * 32 + (T >> 2)] = J.ey[T];
       exr = J.ex[kx];
@@ -377,58 +387,49 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
     int oy = (J.lat_oy + ib * J.lat_sy - kW / 2) % J.ny;
     if (oy < 0) oy += J.ny;
     // the halo of W pixels keeps every window inside the padded array
-    // chunk i of thread T: row (T >> 6) + 8 i, columns 2 (T & 63) + {0, 1} (even origins)
-    //                   or row (T >> 7) + 4 i, column T & 127          (odd origins)
-    const int sy0 = EVEN ? (T >> 6) : (T >> 7);
-    const int sx0 = EVEN ? 2 * (T & 63) : (T & 127);
-    float2* const sdst = R0 + sy0 * kTPitch + sx0;
-    const float2* const gsrc = J.t + cfg * J.t_slot + static_cast<size_t>(oy + sy0) * pitch + ox + sx0;
+    const float2* const gsrc = J.t + cfg * J.t_slot + static_cast<size_t>(oy + 8 * (T >> 5)) * pitch + ox;
 
-    stage_t<EVEN>(sdst, gsrc, pitch);
+    stage_t_warp<EVEN>(xw, gsrc, pitch, lane);
     float2 v[32];
 #pragma unroll
     for (int n1 = 0; n1 < 32; ++n1) v[n1] = J.uW[ya * kW + 4 * n1 + ra];
-    cp_async_wait_all();
-    __syncthreads();
 
     for (int s = 0; s < n_slices; ++s) {
-      // transmission (Sec. 3.2): psi <- t_s psi
-      if (s > 0) {
-        cp_async_wait_all();
-        __syncthreads();   // publishes the staged transmission to every thread
-      }
+      // transmission (Sec. 3.2): psi <- t_s psi, from the warp's staged rows
+      cp_async_wait_all();
+      __syncwarp();
 #pragma unroll
-      for (int n1 = 0; n1 < 32; ++n1) v[n1] = cmul(v[n1], tA_rd[4 * n1]);
+      for (int n1 = 0; n1 < 32; ++n1) v[n1] = cmul(v[n1], tr[4 * n1]);
 
-      // forward 2D DFT
+      // forward 2D DFT; X1 goes to this warp's rows once every lane has read its t
       passA_fwd(v, tA);
-      __syncthreads();
+      __syncwarp();
 #pragma unroll
-      for (int k = 0; k < 32; k += 2) x1w[k / 2] = make_float4(v[k].x, v[k].y, v[k + 1].x, v[k + 1].y);
+      for (int k = 0; k < 32; ++k) xa[k] = v[k];
       __syncthreads();
       float2 b0[16], b1[16];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          b0[q * 4 + r] = x1r[(128 * q + r) * 34];
-          b1[q * 4 + r] = x1r[(128 * q + r) * 34 + 16];
+          b0[q * 4 + r] = xb[(128 * q + r) * kXP];
+          b1[q * 4 + r] = xb[(128 * q + r) * kXP + 16];
         }
       passB_fwd(b0, tB);
       passB_fwd(b1, tB);
-      __syncthreads();
+      // X2: element (k1y, k2x) to slot (q, r) = (k2x, k1y)
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          x2b[(q * 4 + r) * 1024] = b0[q * 4 + r];
-          x2b[(q * 4 + r) * 1024 + 16] = b1[q * 4 + r];
+          xb[(128 * q + r) * kXP] = b0[r * 4 + q];
+          xb[(128 * q + r) * kXP + 16] = b1[r * 4 + q];
         }
       __syncthreads();
       if (c_live) {
         float2 c[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) c[j] = x2c[j * 32];
+        for (int j = 0; j < 32; ++j) c[j] = xc[j * 4 * kXP];
         dft32<false>(c);
         // propagation (Sec. 3.2): exp(-i pi lambda eps |k|^2), bandlimit, 1/W^2
 #pragma unroll
@@ -440,50 +441,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
           c[j + 1] = ((mbits >> (j + 1)) & 1u) ? cmul(c[j + 1], p1) : make_float2(0.f, 0.f);
         }
         dft32<true>(c);
-        // each C thread writes back exactly the entries it read: no barrier needed here
 #pragma unroll
-        for (int j = 0; j < 32; ++j) x2c[j * 32] = c[j];
+        for (int j = 0; j < 32; ++j) xc[j * 4 * kXP] = c[j];
       } else {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) x2c[j * 32] = make_float2(0.f, 0.f);
+        for (int j = 0; j < 32; ++j) xc[j * 4 * kXP] = make_float2(0.f, 0.f);
       }
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          b0[q * 4 + r] = x2b[(q * 4 + r) * 1024];
-          b1[q * 4 + r] = x2b[(q * 4 + r) * 1024 + 16];
+          b0[r * 4 + q] = xb[(128 * q + r) * kXP];
+          b1[r * 4 + q] = xb[(128 * q + r) * kXP + 16];
         }
-      __syncthreads();  // R0 is free: prefetch the next slice's transmission
-      const bool more = s + 1 < n_slices;
-      if (more) stage_t<EVEN>(sdst, gsrc + (s + 1) * slice_elems, pitch);
       passB_inv(b0, tB);
       passB_inv(b1, tB);
-      // B -> A in two halves through R1
+      // X4: element (y = 32 q + n2y, r) back to slot (q, r)
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) x4w[(128 * q + r) * 18] = b0[q * 4 + r];
+        for (int r = 0; r < 4; ++r) {
+          xb[(128 * q + r) * kXP] = b0[q * 4 + r];
+          xb[(128 * q + r) * kXP + 16] = b1[q * 4 + r];
+        }
       __syncthreads();
 #pragma unroll
-      for (int k = 0; k < 16; k += 2) {
-        const float4 p = x4r[k / 2];
-        v[k] = make_float2(p.x, p.y);
-        v[k + 1] = make_float2(p.z, p.w);
-      }
-      __syncthreads();
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) x4w[(128 * q + r) * 18] = b1[q * 4 + r];
-      __syncthreads();
-#pragma unroll
-      for (int k = 16; k < 32; k += 2) {
-        const float4 p = x4r[(k - 16) / 2];
-        v[k] = make_float2(p.x, p.y);
-        v[k + 1] = make_float2(p.z, p.w);
-      }
+      for (int k = 0; k < 32; ++k) v[k] = xa[k];
+      // the warp's rows are free again once every lane has read them: prefetch the next
+      // slice's transmission while the inverse pass A runs
+      __syncwarp();
+      if (s + 1 < n_slices) stage_t_warp<EVEN>(xw, gsrc + (s + 1) * slice_elems, pitch, lane);
       passA_inv(v, tA);
     }
 
@@ -520,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
 #pragma unroll
       for (int n1 = 0; n1 < 32; ++n1) ud[4 * n1] = v[n1];
     }
-    __syncthreads();  // R1 reads of this translate finish before the next one writes
+    __syncthreads();  // eys, wmax and s_next are rewritten by the next item
   }
 }
 
