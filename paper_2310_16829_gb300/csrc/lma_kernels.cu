@@ -41,6 +41,10 @@ namespace lma_dev {
 
 // exp(-2 pi i m / 128), m = 0..127: built on the host in FP64 and rounded once.
 __constant__ float2 c_w128[128];
+// W_32^M = (cos th, -sin th), th = 2 pi M / 32, as a scale times (1, ratio) or (ratio, 1):
+// (cos th, tan th) where |cos th| >= |sin th| (M <= 4 or M >= 12), else (sin th, cot th);
+// built on the host in FP64 and rounded once. |ratio| <= 1 in both forms.
+__constant__ float2 c_tw32t[16];
 
 // ------------------------------------------------------------------------------------------
 // complex helpers
@@ -95,9 +99,11 @@ __device__ __forceinline__ void static_for(F&& f) {
 }
 
 // One radix-2 decimation-in-time butterfly on t[I] (a) and t[I + H] (b) with the
-// twiddle W_32^M. A general twiddle computes X = a + w b and Y = a - w b with
-// four FMAs each (two roundings per component; Y is not formed as 2a - X,
-// which would carry X's rounding error into Y).
+// twiddle W_32^M. A general twiddle w = s (1, t) or s (t, 1) with |t| <= 1 (the
+// tangent form of an FMA butterfly) computes (u, v) = w b / s with two FMAs and
+// X = a + s (u, v), Y = a - s (u, v) with four: two roundings per component, as for
+// a plain complex product (Y is not formed as 2a - X, which would carry X's rounding
+// error into Y).
 template <bool INV, int I, int H, int M>
 __device__ __forceinline__ void bfly(float2 (&t)[32]) {
   const float2 a = t[I];
@@ -128,14 +134,22 @@ __device__ __forceinline__ void bfly(float2 (&t)[32]) {
     const float rs = sc > 0 ? r : -r;
     t[I] = make_float2(fmaf(rs, u, a.x), fmaf(rs, v, a.y));
     t[I + H] = make_float2(fmaf(-rs, u, a.x), fmaf(-rs, v, a.y));
+  } else if constexpr (M < 4 || M > 12) {
+    // |cos| > |sin|: w b = cos th (b + i t b) with t = wy / wx (-tan th forward, +tan th
+    // inverse): two FMAs form (u, v) = b + i t b, four more give X and Y
+    const float2 k = c_tw32t[M];
+    const float tq = INV ? k.y : -k.y;
+    const float u = fmaf(-tq, b.y, b.x), v = fmaf(tq, b.x, b.y);
+    t[I] = make_float2(fmaf(k.x, u, a.x), fmaf(k.x, v, a.y));
+    t[I + H] = make_float2(fmaf(-k.x, u, a.x), fmaf(-k.x, v, a.y));
   } else {
-    const float2 w = c_w128[4 * M];
-    const float wy = INV ? -w.y : w.y;
-    float2 x;
-    x.x = fmaf(b.x, w.x, fmaf(-b.y, wy, a.x));
-    x.y = fmaf(b.y, w.x, fmaf(b.x, wy, a.y));
-    t[I] = x;
-    t[I + H] = make_float2(fmaf(-b.x, w.x, fmaf(b.y, wy, a.x)), fmaf(-b.y, w.x, fmaf(-b.x, wy, a.y)));
+    // |sin| > |cos|: w b = wy (c b + i b) with c = wx / wy, wy = -sin th forward, +sin th
+    // inverse
+    const float2 k = c_tw32t[M];
+    const float sy = INV ? k.x : -k.x, ct = INV ? k.y : -k.y;
+    const float u = fmaf(ct, b.x, -b.y), v = fmaf(ct, b.y, b.x);
+    t[I] = make_float2(fmaf(sy, u, a.x), fmaf(sy, v, a.y));
+    t[I + H] = make_float2(fmaf(-sy, u, a.x), fmaf(-sy, v, a.y));
   }
 }
 
@@ -284,7 +298,12 @@ constexpr int kXP = 33;
 constexpr int kXRows = 512 * kXP;
 constexpr int kTRow = 132;   // staged transmission row: 4 table rows
 static_assert(8 * kTRow == 32 * kXP, "a warp's 8 transmission rows fill its 32 table rows");
-constexpr int kSliceSmemFloat2 = kXRows + kTwA + 128 + 128;
+// propagator table P[a * 65 + b] = e_x(a) e_y(b) for |kx| = a, |ky| = b <= 64, zero
+// outside the bandlimit (e_x and e_y depend on k^2 only); the odd row length spreads
+// the 16 consecutive a of a half-warp over distinct bank pairs
+constexpr int kPRow = 65;
+constexpr int kPTab = kPRow * kPRow;
+constexpr int kSliceSmemFloat2 = kXRows + kTwA + 128 + kPTab;
 
 // Warp w copies window rows 8 w .. 8 w + 7 of one slice (g points at the first) into its
 // table rows (asynchronous; the warp's threads read them after cp_async_wait_all and
@@ -317,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
   float2* X = sm;              // exchange table, 512 rows x kXP
   float2* twA = X + kXRows;
   float2* twB = twA + kTwA;
-  float2* eys = twB + 128;     // eys[k1y*32 + j] = e_y(k1y + 4 j)
+  float2* ptab = twB + 128;    // propagator table, kPRow x kPRow
 
   const int T = threadIdx.x;
   load_twiddles(twA, twB, T);
@@ -329,11 +348,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
   const int kx = c_column(T), k1y = T >> 7, k1x = kx & 31, k2x = kx >> 5;
   const float2* tA = twA + ra * 34;
   const float2* tB = twB + n2y * 4;
-  const float4* ey4 = reinterpret_cast<const float4*>(eys + k1y * 32);
   const int kxs = kx < 64 ? kx : kx - 128;
-  // per-job propagator constants (reloaded when the job changes)
-  float2 exr = make_float2(0.f, 0.f);
-  uint32_t mbits = 0;
+  // entry j of this C thread: ky = k1y + 4 j, |ky| = k1y + 4 j (j < 16), 128 - k1y - 4 j
+  const float2* const pp = ptab + (kxs < 0 ? -kxs : kxs) * kPRow + k1y;            // + 4 j
+  const float2* const pm = ptab + (kxs < 0 ? -kxs : kxs) * kPRow + 128 - k1y;      // - 4 j
   bool c_live = false;
   int cur_job = -1;
   __shared__ int s_next;
@@ -360,20 +378,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
     while (jb + 1 < a.n_jobs && li >= a.start[jb + 1]) ++jb;
     const SliceJob& J = a.job[jb];
     if (jb != cur_job) {
-      // the previous item's last barrier has passed: eys is free; the X1 barrier below
-      // publishes it before pass C reads it
+      // the previous item's last barrier has passed: the table is free; the X1 barrier
+      // below publishes it before pass C reads it
       cur_job = jb;
-      if (T < 128) eys[(T & 3) * 32 + (T >> 2)] = J.ey[T];
-      exr = J.ex[kx];
-      mbits = 0;
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int ky = k1y + 4 * j;
-        const int kys = ky < 64 ? ky : ky - 128;
-        if (kxs * kxs + kys * kys <= J.r2max) mbits |= 1u << j;
+      for (int e = T; e < kPTab; e += kThreads) {
+        const int pa = e / kPRow, pb = e - pa * kPRow;
+        ptab[e] = pa * pa + pb * pb <= J.r2max ? cmul(J.ex[pa], J.ey[pb]) : make_float2(0.f, 0.f);
       }
       // a warp whose columns are all outside the bandlimit skips pass C: its spectrum is zero
-      c_live = __any_sync(0xffffffffu, mbits != 0u);
+      c_live = __any_sync(0xffffffffu, kxs * kxs <= J.r2max);
     }
     const int n_slices = J.n_slices;
     const int pitch = J.nx + kW;                                  // padded row
@@ -433,13 +446,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
         dft32<false>(c);
         // propagation (Sec. 3.2): exp(-i pi lambda eps |k|^2), bandlimit, 1/W^2
 #pragma unroll
-        for (int j = 0; j < 32; j += 2) {
-          const float4 e2 = ey4[j / 2];
-          const float2 p0 = cmul(exr, make_float2(e2.x, e2.y));
-          const float2 p1 = cmul(exr, make_float2(e2.z, e2.w));
-          c[j] = ((mbits >> j) & 1u) ? cmul(c[j], p0) : make_float2(0.f, 0.f);
-          c[j + 1] = ((mbits >> (j + 1)) & 1u) ? cmul(c[j + 1], p1) : make_float2(0.f, 0.f);
-        }
+        for (int j = 0; j < 32; ++j) c[j] = cmul(c[j], j < 16 ? pp[4 * j] : pm[-4 * j]);
         dft32<true>(c);
 #pragma unroll
         for (int j = 0; j < 32; ++j) xc[j * 4 * kXP] = c[j];
@@ -508,7 +515,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
 #pragma unroll
       for (int n1 = 0; n1 < 32; ++n1) ud[4 * n1] = v[n1];
     }
-    __syncthreads();  // eys, wmax and s_next are rewritten by the next item
+    __syncthreads();  // the table, wmax and s_next are rewritten by the next item
   }
 }
 
@@ -996,6 +1003,14 @@ cudaError_t init_device_constants() {
     w[m] = make_float2(static_cast<float>(cos(ang)), static_cast<float>(sin(ang)));
   }
   cudaError_t e = cudaMemcpyToSymbol(c_w128, w, sizeof(w));
+  if (e != cudaSuccess) return e;
+  float2 tt[16];
+  for (int m = 0; m < 16; ++m) {
+    const double th = 2.0 * pi * m / 32.0, c = cos(th), sn = sin(th);
+    tt[m] = (m <= 4 || m >= 12) ? make_float2(static_cast<float>(c), static_cast<float>(sn / c))
+                                : make_float2(static_cast<float>(sn), static_cast<float>(c / sn));
+  }
+  e = cudaMemcpyToSymbol(c_tw32t, tt, sizeof(tt));
   if (e != cudaSuccess) return e;
   const int ss = static_cast<int>(slice_smem_bytes()), sy = static_cast<int>(synth_smem_bytes());
   if ((e = cudaFuncSetAttribute(k_slice<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
