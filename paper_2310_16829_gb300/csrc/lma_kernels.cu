@@ -45,6 +45,12 @@ __constant__ float2 c_w128[128];
 // (cos th, tan th) where |cos th| >= |sin th| (M <= 4 or M >= 12), else (sin th, cot th);
 // built on the host in FP64 and rounded once. |ratio| <= 1 in both forms.
 __constant__ float2 c_tw32t[16];
+// Pass-A twiddles of the slice kernel's pass B, tau_r = W_128^(r k1), r = 1..3, per k1 < 32,
+// as a scale s_r times (1, t_r) for k1 < 16 and (t_r, 1) for k1 >= 16 (tangent form; the
+// form is the same across a half-warp): c_twrA[k1] = (t1, s1, t2, s2), c_twrB[k1] = (t3,
+// s3, s3 / s1, 0). Built on the host in FP64 and rounded once.
+__constant__ float4 c_twrA[32];
+__constant__ float4 c_twrB[32];
 
 // ------------------------------------------------------------------------------------------
 // complex helpers
@@ -244,6 +250,86 @@ __device__ __forceinline__ void passB_inv(float2 (&a)[16], const float2* twB) {
   for (int q = 0; q < 4; ++q) dft4<true>(a[q * 4 + 0], a[q * 4 + 1], a[q * 4 + 2], a[q * 4 + 3]);
 }
 
+// pass B of the slice kernel with pass A's twiddles W_128^(r k1) moved into it: r is
+// this thread's own index here, so r = 0 needs none (24 products per thread instead of
+// 31). Forward, they are fused into the radix-4 stage over r: with (u_r, v_r) = tau_r a_r
+// / s_r (two FMAs each) and rho = s3 / s1,
+//   a0 + tau_2 a2 = a0 + s2 (u2, v2),   tau_1 a1 + tau_3 a3 = s1 ((u1, v1) + rho (u3, v3)),
+// 22 instructions per radix-4 stage against 28 for three products and the plain stage.
+// COT selects the form of the twiddles (k1 >= 16).
+template <bool COT>
+__device__ __forceinline__ void tw_uv(float2 a, float t, float& u, float& v) {
+  if constexpr (COT) {
+    u = fmaf(t, a.x, -a.y);
+    v = fmaf(t, a.y, a.x);
+  } else {
+    u = fmaf(-t, a.y, a.x);
+    v = fmaf(t, a.x, a.y);
+  }
+}
+template <bool COT>
+__device__ __forceinline__ void dft4_tw(float2& a0, float2& a1, float2& a2, float2& a3, const float4 kA,
+                                        const float4 kB) {
+  float u1, v1, u2, v2, u3, v3;
+  tw_uv<COT>(a1, kA.x, u1, v1);
+  tw_uv<COT>(a2, kA.z, u2, v2);
+  tw_uv<COT>(a3, kB.x, u3, v3);
+  const float s1 = kA.y, s2 = kA.w, rho = kB.z;
+  const float2 s02 = make_float2(fmaf(s2, u2, a0.x), fmaf(s2, v2, a0.y));
+  const float2 d02 = make_float2(fmaf(-s2, u2, a0.x), fmaf(-s2, v2, a0.y));
+  const float2 P = make_float2(fmaf(rho, u3, u1), fmaf(rho, v3, v1));    // (tau_1 a1 + tau_3 a3) / s1
+  const float2 D = make_float2(fmaf(-rho, u3, u1), fmaf(-rho, v3, v1));  // (tau_1 a1 - tau_3 a3) / s1
+  // forward: X1 = d02 - i d13, X3 = d02 + i d13
+  a0 = make_float2(fmaf(s1, P.x, s02.x), fmaf(s1, P.y, s02.y));
+  a2 = make_float2(fmaf(-s1, P.x, s02.x), fmaf(-s1, P.y, s02.y));
+  a1 = make_float2(fmaf(s1, D.y, d02.x), fmaf(-s1, D.x, d02.y));
+  a3 = make_float2(fmaf(-s1, D.y, d02.x), fmaf(s1, D.x, d02.y));
+}
+// a * conj(tau) for tau = s (1, t) or s (t, 1)
+template <bool COT>
+__device__ __forceinline__ float2 tw_conj(float2 a, float s, float t) {
+  float u, v;
+  if constexpr (COT) {
+    u = fmaf(t, a.x, a.y);
+    v = fmaf(t, a.y, -a.x);
+  } else {
+    u = fmaf(t, a.y, a.x);
+    v = fmaf(-t, a.x, a.y);
+  }
+  return make_float2(s * u, s * v);
+}
+template <bool COT>
+__device__ __forceinline__ void passB_fwd_tw(float2 (&a)[16], const float2* twB, const float4 kA, const float4 kB) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dft4_tw<COT>(a[q * 4 + 0], a[q * 4 + 1], a[q * 4 + 2], a[q * 4 + 3], kA, kB);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dft4<false>(a[0 * 4 + q], a[1 * 4 + q], a[2 * 4 + q], a[3 * 4 + q]);
+#pragma unroll
+  for (int k1y = 1; k1y < 4; ++k1y) {
+    const float2 w = twB[k1y];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a[k1y * 4 + q] = cmul(a[k1y * 4 + q], w);
+  }
+}
+template <bool COT>
+__device__ __forceinline__ void passB_inv_tw(float2 (&a)[16], const float2* twB, const float4 kA, const float4 kB) {
+#pragma unroll
+  for (int k1y = 1; k1y < 4; ++k1y) {
+    const float2 w = twB[k1y];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a[k1y * 4 + q] = cmulc(a[k1y * 4 + q], w);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dft4<true>(a[0 * 4 + q], a[1 * 4 + q], a[2 * 4 + q], a[3 * 4 + q]);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    dft4<true>(a[q * 4 + 0], a[q * 4 + 1], a[q * 4 + 2], a[q * 4 + 3]);
+    a[q * 4 + 1] = tw_conj<COT>(a[q * 4 + 1], kA.y, kA.x);
+    a[q * 4 + 2] = tw_conj<COT>(a[q * 4 + 2], kA.w, kA.z);
+    a[q * 4 + 3] = tw_conj<COT>(a[q * 4 + 3], kB.y, kB.x);
+  }
+}
+
 // shared-memory layouts of the synthesis kernel's exchanges (float2 units); row
 // paddings keep the 64-bit accesses of every half-warp on 16 distinct bank pairs and
 // make every address a per-thread base plus a compile-time offset
@@ -303,7 +389,7 @@ static_assert(8 * kTRow == 32 * kXP, "a warp's 8 transmission rows fill its 32 t
 // the 16 consecutive a of a half-warp over distinct bank pairs
 constexpr int kPRow = 65;
 constexpr int kPTab = kPRow * kPRow;
-constexpr int kSliceSmemFloat2 = kXRows + kTwA + 128 + kPTab;
+constexpr int kSliceSmemFloat2 = kXRows + 128 + 128 + kPTab;
 
 // Warp w copies window rows 8 w .. 8 w + 7 of one slice (g points at the first) into its
 // table rows (asynchronous; the warp's threads read them after cp_async_wait_all and
@@ -334,19 +420,19 @@ template <bool EVEN, bool HALF>
 __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, const int mode) {
   extern __shared__ __align__(16) float2 sm[];
   float2* X = sm;              // exchange table, 512 rows x kXP
-  float2* twA = X + kXRows;
-  float2* twB = twA + kTwA;
+  float4* twr = reinterpret_cast<float4*>(X + kXRows);   // [0, 32): c_twrA, [32, 64): c_twrB
+  float2* twB = X + kXRows + 128;
   float2* ptab = twB + 128;    // propagator table, kPRow x kPRow
 
   const int T = threadIdx.x;
-  load_twiddles(twA, twB, T);
+  if (T < 128) twB[T] = c_w128[((T >> 2) * (T & 3)) & 127];
+  if (T < 64) twr[T] = T < 32 ? c_twrA[T] : c_twrB[T - 32];
   // A layout: thread (y, r), TA = T
   const int ya = T >> 2, ra = T & 3;
   // B layout: groups (k1 = (T & 15) + 16 h, n2y = T >> 4), h = 0, 1
   const int k1lo = T & 15, n2y = T >> 4;
   // C layout: thread (kx, k1y), kx permuted within each k1y group (c_column)
   const int kx = c_column(T), k1y = T >> 7, k1x = kx & 31, k2x = kx >> 5;
-  const float2* tA = twA + ra * 34;
   const float2* tB = twB + n2y * 4;
   const int kxs = kx < 64 ? kx : kx - 128;
   // entry j of this C thread: ky = k1y + 4 j, |ky| = k1y + 4 j (j < 16), 128 - k1y - 4 j
@@ -415,7 +501,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
       for (int n1 = 0; n1 < 32; ++n1) v[n1] = cmul(v[n1], tr[4 * n1]);
 
       // forward 2D DFT; X1 goes to this warp's rows once every lane has read its t
-      passA_fwd(v, tA);
+      dft32<false>(v);
       __syncwarp();
 #pragma unroll
       for (int k = 0; k < 32; ++k) xa[k] = v[k];
@@ -428,8 +514,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
           b0[q * 4 + r] = xb[(128 * q + r) * kXP];
           b1[q * 4 + r] = xb[(128 * q + r) * kXP + 16];
         }
-      passB_fwd(b0, tB);
-      passB_fwd(b1, tB);
+      passB_fwd_tw<false>(b0, tB, twr[k1lo], twr[32 + k1lo]);
+      passB_fwd_tw<true>(b1, tB, twr[16 + k1lo], twr[48 + k1lo]);
       // X2: element (k1y, k2x) to slot (q, r) = (k2x, k1y)
 #pragma unroll
       for (int q = 0; q < 4; ++q)
@@ -462,8 +548,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
           b0[r * 4 + q] = xb[(128 * q + r) * kXP];
           b1[r * 4 + q] = xb[(128 * q + r) * kXP + 16];
         }
-      passB_inv(b0, tB);
-      passB_inv(b1, tB);
+      passB_inv_tw<false>(b0, tB, twr[k1lo], twr[32 + k1lo]);
+      passB_inv_tw<true>(b1, tB, twr[16 + k1lo], twr[48 + k1lo]);
       // X4: element (y = 32 q + n2y, r) back to slot (q, r)
 #pragma unroll
       for (int q = 0; q < 4; ++q)
@@ -479,7 +565,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
       // slice's transmission while the inverse pass A runs
       __syncwarp();
       if (s + 1 < n_slices) stage_t_warp<EVEN>(xw, gsrc + (s + 1) * slice_elems, pitch, lane);
-      passA_inv(v, tA);
+      dft32<true>(v);
     }
 
     if constexpr (HALF) {
@@ -1011,6 +1097,27 @@ cudaError_t init_device_constants() {
                                 : make_float2(static_cast<float>(sn), static_cast<float>(c / sn));
   }
   e = cudaMemcpyToSymbol(c_tw32t, tt, sizeof(tt));
+  if (e != cudaSuccess) return e;
+  float4 ra[32], rb[32];
+  for (int k1 = 0; k1 < 32; ++k1) {
+    double sc[4] = {1, 0, 0, 0}, t[4] = {0, 0, 0, 0};
+    for (int r = 1; r <= 3; ++r) {
+      // forward W_128^(r k1) = (cos th, -sin th) = s (1, t) or s (t, 1)
+      const double th = 2.0 * pi * r * k1 / 128.0, c = cos(th), sn = sin(th);
+      if (k1 < 16) {
+        sc[r] = c;
+        t[r] = -sn / c;
+      } else {
+        sc[r] = -sn;
+        t[r] = c / -sn;
+      }
+    }
+    ra[k1] = make_float4(static_cast<float>(t[1]), static_cast<float>(sc[1]), static_cast<float>(t[2]),
+                         static_cast<float>(sc[2]));
+    rb[k1] = make_float4(static_cast<float>(t[3]), static_cast<float>(sc[3]), static_cast<float>(sc[3] / sc[1]), 0.f);
+  }
+  if ((e = cudaMemcpyToSymbol(c_twrA, ra, sizeof(ra))) != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(c_twrB, rb, sizeof(rb));
   if (e != cudaSuccess) return e;
   const int ss = static_cast<int>(slice_smem_bytes()), sy = static_cast<int>(synth_smem_bytes());
   if ((e = cudaFuncSetAttribute(k_slice<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
