@@ -29,3 +29,11 @@ def lib():
     """The CUDA library through its C-ABI binding (built in-tree by __graft_entry__.build)."""
     from paper_2310_16829_gb300 import lma
     return lma.load()
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built_library():
+    """Every test runs against the in-tree library: build it once if this checkout has none."""
+    from paper_2310_16829_gb300 import build as b
+    if not os.path.exists(b.LIB):
+        b.build()
