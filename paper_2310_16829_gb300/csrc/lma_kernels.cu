@@ -110,18 +110,28 @@ __device__ __forceinline__ void static_for(F&& f) {
 // X = a + s (u, v), Y = a - s (u, v) with four: two roundings per component, as for
 // a plain complex product (Y is not formed as 2a - X, which would carry X's rounding
 // error into Y).
-template <bool INV, int I, int H, int M>
+// NX / NY: whether X = t[I] / Y = t[I + H] is needed; Z (M = 0 only): 1 if a is known to
+// be zero, 2 if b is (the outputs are then copies of the other input, exactly as the sum
+// and difference would give).
+template <bool INV, int I, int H, int M, bool NX = true, bool NY = true, int Z = 0>
 __device__ __forceinline__ void bfly(float2 (&t)[32]) {
   const float2 a = t[I];
   const float2 b = t[I + H];
-  if constexpr (M == 0) {
-    t[I] = cadd(a, b);
-    t[I + H] = csub(a, b);
+  if constexpr (Z == 1) {
+    static_assert(M == 0, "zero inputs are pruned in the first stage only");
+    t[I] = b;
+    t[I + H] = make_float2(-b.x, -b.y);
+  } else if constexpr (Z == 2) {
+    static_assert(M == 0, "zero inputs are pruned in the first stage only");
+    t[I + H] = a;
+  } else if constexpr (M == 0) {
+    if constexpr (NX) t[I] = cadd(a, b);
+    if constexpr (NY) t[I + H] = csub(a, b);
   } else if constexpr (M == 8) {
     // w b = -i b (forward) or i b (inverse)
     const float2 wb = INV ? make_float2(-b.y, b.x) : make_float2(b.y, -b.x);
-    t[I] = cadd(a, wb);
-    t[I + H] = csub(a, wb);
+    if constexpr (NX) t[I] = cadd(a, wb);
+    if constexpr (NY) t[I + H] = csub(a, wb);
   } else if constexpr (M == 4 || M == 12) {
     // w = (c, s) with |c| = |s| = r = 1/sqrt(2): w b = (c b.x - s b.y, c b.y + s b.x) is
     // r times a sum or difference of b.x and b.y, so X and Y take one add and one FMA
@@ -138,30 +148,35 @@ __device__ __forceinline__ void bfly(float2 (&t)[32]) {
       v = b.y - b.x;
     }
     const float rs = sc > 0 ? r : -r;
-    t[I] = make_float2(fmaf(rs, u, a.x), fmaf(rs, v, a.y));
-    t[I + H] = make_float2(fmaf(-rs, u, a.x), fmaf(-rs, v, a.y));
+    if constexpr (NX) t[I] = make_float2(fmaf(rs, u, a.x), fmaf(rs, v, a.y));
+    if constexpr (NY) t[I + H] = make_float2(fmaf(-rs, u, a.x), fmaf(-rs, v, a.y));
   } else if constexpr (M < 4 || M > 12) {
     // |cos| > |sin|: w b = cos th (b + i t b) with t = wy / wx (-tan th forward, +tan th
     // inverse): two FMAs form (u, v) = b + i t b, four more give X and Y
     const float2 k = c_tw32t[M];
     const float tq = INV ? k.y : -k.y;
     const float u = fmaf(-tq, b.y, b.x), v = fmaf(tq, b.x, b.y);
-    t[I] = make_float2(fmaf(k.x, u, a.x), fmaf(k.x, v, a.y));
-    t[I + H] = make_float2(fmaf(-k.x, u, a.x), fmaf(-k.x, v, a.y));
+    if constexpr (NX) t[I] = make_float2(fmaf(k.x, u, a.x), fmaf(k.x, v, a.y));
+    if constexpr (NY) t[I + H] = make_float2(fmaf(-k.x, u, a.x), fmaf(-k.x, v, a.y));
   } else {
     // |sin| > |cos|: w b = wy (c b + i b) with c = wx / wy, wy = -sin th forward, +sin th
     // inverse
     const float2 k = c_tw32t[M];
     const float sy = INV ? k.x : -k.x, ct = INV ? k.y : -k.y;
     const float u = fmaf(ct, b.x, -b.y), v = fmaf(ct, b.y, b.x);
-    t[I] = make_float2(fmaf(sy, u, a.x), fmaf(sy, v, a.y));
-    t[I + H] = make_float2(fmaf(-sy, u, a.x), fmaf(-sy, v, a.y));
+    if constexpr (NX) t[I] = make_float2(fmaf(sy, u, a.x), fmaf(sy, v, a.y));
+    if constexpr (NY) t[I + H] = make_float2(fmaf(-sy, u, a.x), fmaf(-sy, v, a.y));
   }
 }
 
 // In-register 32-point DFT, natural order in and out: radix-2 decimation in
 // time on the bit-reversed input (a register renaming), 5 stages of spans 1..16.
-template <bool INV>
+// ZMODE 1: outputs 11..20 are not needed (the last stage skips them); ZMODE 2: inputs
+// 11..20 are zero (the first stage copies instead of adding). Both hold for the pass-C
+// columns of the slice kernel when the bandlimit radius is below 44: ky = k1y + 4 j has
+// |ky| >= 44 for every j in 11..20.
+__host__ __device__ constexpr bool in_gap(int j) { return j >= 11 && j <= 20; }
+template <bool INV, int ZMODE = 0>
 __device__ __forceinline__ void dft32(float2 (&v)[32]) {
   float2 t[32];
   static_for<0, 32>([&](auto k) {
@@ -174,7 +189,11 @@ __device__ __forceinline__ void dft32(float2 (&v)[32]) {
       static_for<0, H>([&](auto j) {
         constexpr int I = decltype(blk)::value * 2 * H + decltype(j)::value;
         constexpr int M = decltype(j)::value * (16 / H);
-        bfly<INV, I, H, M>(t);
+        // first stage: t[I] = v[brev5(I)], t[I + 1] = v[brev5(I) + 16]
+        constexpr int Z = (ZMODE == 2 && H == 1) ? (in_gap(brev5(I)) ? 1 : (in_gap(brev5(I) + 16) ? 2 : 0)) : 0;
+        constexpr bool NX = !(ZMODE == 1 && H == 16 && in_gap(I));
+        constexpr bool NY = !(ZMODE == 1 && H == 16 && in_gap(I + 16));
+        bfly<INV, I, H, M, NX, NY, Z>(t);
       });
     });
   });
@@ -188,6 +207,31 @@ template <bool INV>
 __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
   const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
   // forward: X1 = d02 - i d13, X3 = d02 + i d13; inverse swaps the sign of i
+  const float2 j13 = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
+  a0 = cadd(s02, s13);
+  a2 = csub(s02, s13);
+  a1 = cadd(d02, j13);
+  a3 = csub(d02, j13);
+}
+
+// dft4 with input Z known to be zero (Z = -1: none); the outputs are those of dft4
+template <bool INV, int Z>
+__device__ __forceinline__ void dft4z(float2& a0, float2& a1, float2& a2, float2& a3) {
+  float2 s02, d02, s13, d13;
+  if constexpr (Z == 2) {
+    s02 = a0;
+    d02 = a0;
+  } else {
+    s02 = cadd(a0, a2);
+    d02 = csub(a0, a2);
+  }
+  if constexpr (Z == 1) {
+    s13 = a3;
+    d13 = make_float2(-a3.x, -a3.y);
+  } else {
+    s13 = cadd(a1, a3);
+    d13 = csub(a1, a3);
+  }
   const float2 j13 = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
   a0 = cadd(s02, s13);
   a2 = csub(s02, s13);
@@ -267,7 +311,7 @@ __device__ __forceinline__ void tw_uv(float2 a, float t, float& u, float& v) {
     v = fmaf(t, a.x, a.y);
   }
 }
-template <bool COT>
+template <bool COT, int SKIP = -1>
 __device__ __forceinline__ void dft4_tw(float2& a0, float2& a1, float2& a2, float2& a3, const float4 kA,
                                         const float4 kB) {
   float u1, v1, u2, v2, u3, v3;
@@ -280,10 +324,11 @@ __device__ __forceinline__ void dft4_tw(float2& a0, float2& a1, float2& a2, floa
   const float2 P = make_float2(fmaf(rho, u3, u1), fmaf(rho, v3, v1));    // (tau_1 a1 + tau_3 a3) / s1
   const float2 D = make_float2(fmaf(-rho, u3, u1), fmaf(-rho, v3, v1));  // (tau_1 a1 - tau_3 a3) / s1
   // forward: X1 = d02 - i d13, X3 = d02 + i d13
-  a0 = make_float2(fmaf(s1, P.x, s02.x), fmaf(s1, P.y, s02.y));
-  a2 = make_float2(fmaf(-s1, P.x, s02.x), fmaf(-s1, P.y, s02.y));
-  a1 = make_float2(fmaf(s1, D.y, d02.x), fmaf(-s1, D.x, d02.y));
-  a3 = make_float2(fmaf(-s1, D.y, d02.x), fmaf(s1, D.x, d02.y));
+  // output SKIP is not needed
+  if constexpr (SKIP != 0) a0 = make_float2(fmaf(s1, P.x, s02.x), fmaf(s1, P.y, s02.y));
+  if constexpr (SKIP != 2) a2 = make_float2(fmaf(-s1, P.x, s02.x), fmaf(-s1, P.y, s02.y));
+  if constexpr (SKIP != 1) a1 = make_float2(fmaf(s1, D.y, d02.x), fmaf(-s1, D.x, d02.y));
+  if constexpr (SKIP != 3) a3 = make_float2(fmaf(-s1, D.y, d02.x), fmaf(s1, D.x, d02.y));
 }
 // a * conj(tau) for tau = s (1, t) or s (t, 1)
 template <bool COT>
@@ -298,32 +343,47 @@ __device__ __forceinline__ float2 tw_conj(float2 a, float s, float t) {
   }
   return make_float2(s * u, s * v);
 }
-template <bool COT>
+// With PRUNE, column k2x = MC of this half lies outside the bandlimit for every ky
+// (k1 < 16: kx = k1 + 64, |kx| >= 49; k1 >= 16: kx = k1 + 32 >= 48; the radius is below
+// 44): forward it is not formed, inverse it is zero (C writes zeros there).
+template <bool COT, bool PRUNE>
+__host__ __device__ constexpr int masked_k2x() { return PRUNE ? (COT ? 1 : 2) : -1; }
+template <bool COT, bool PRUNE>
 __device__ __forceinline__ void passB_fwd_tw(float2 (&a)[16], const float2* twB, const float4 kA, const float4 kB) {
+  constexpr int MC = masked_k2x<COT, PRUNE>();
 #pragma unroll
-  for (int q = 0; q < 4; ++q) dft4_tw<COT>(a[q * 4 + 0], a[q * 4 + 1], a[q * 4 + 2], a[q * 4 + 3], kA, kB);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) dft4<false>(a[0 * 4 + q], a[1 * 4 + q], a[2 * 4 + q], a[3 * 4 + q]);
+  for (int q = 0; q < 4; ++q) dft4_tw<COT, MC>(a[q * 4 + 0], a[q * 4 + 1], a[q * 4 + 2], a[q * 4 + 3], kA, kB);
+  static_for<0, 4>([&](auto qq) {
+    constexpr int q = decltype(qq)::value;
+    if constexpr (q != MC) dft4<false>(a[0 * 4 + q], a[1 * 4 + q], a[2 * 4 + q], a[3 * 4 + q]);
+  });
 #pragma unroll
   for (int k1y = 1; k1y < 4; ++k1y) {
     const float2 w = twB[k1y];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) a[k1y * 4 + q] = cmul(a[k1y * 4 + q], w);
+    static_for<0, 4>([&](auto qq) {
+      constexpr int q = decltype(qq)::value;
+      if constexpr (q != MC) a[k1y * 4 + q] = cmul(a[k1y * 4 + q], w);
+    });
   }
 }
-template <bool COT>
+template <bool COT, bool PRUNE>
 __device__ __forceinline__ void passB_inv_tw(float2 (&a)[16], const float2* twB, const float4 kA, const float4 kB) {
+  constexpr int MC = masked_k2x<COT, PRUNE>();
 #pragma unroll
   for (int k1y = 1; k1y < 4; ++k1y) {
     const float2 w = twB[k1y];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) a[k1y * 4 + q] = cmulc(a[k1y * 4 + q], w);
+    static_for<0, 4>([&](auto qq) {
+      constexpr int q = decltype(qq)::value;
+      if constexpr (q != MC) a[k1y * 4 + q] = cmulc(a[k1y * 4 + q], w);
+    });
   }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) dft4<true>(a[0 * 4 + q], a[1 * 4 + q], a[2 * 4 + q], a[3 * 4 + q]);
+  static_for<0, 4>([&](auto qq) {
+    constexpr int q = decltype(qq)::value;
+    if constexpr (q != MC) dft4<true>(a[0 * 4 + q], a[1 * 4 + q], a[2 * 4 + q], a[3 * 4 + q]);
+  });
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    dft4<true>(a[q * 4 + 0], a[q * 4 + 1], a[q * 4 + 2], a[q * 4 + 3]);
+    dft4z<true, MC>(a[q * 4 + 0], a[q * 4 + 1], a[q * 4 + 2], a[q * 4 + 3]);
     a[q * 4 + 1] = tw_conj<COT>(a[q * 4 + 1], kA.y, kA.x);
     a[q * 4 + 2] = tw_conj<COT>(a[q * 4 + 2], kA.w, kA.z);
     a[q * 4 + 3] = tw_conj<COT>(a[q * 4 + 3], kB.y, kB.x);
@@ -415,8 +475,10 @@ __device__ __forceinline__ void stage_t_warp(float2* region, const float2* g, in
 
 // One translate per CTA at a time, items taken as SliceLaunch's mode says; EVEN selects
 // the window-origin parity of the translates in the list; HALF writes the exit wave as
-// FP16 pairs scaled by a per-wave power of two.
-template <bool EVEN, bool HALF>
+// FP16 pairs scaled by a per-wave power of two; PRUNE (every job's bandlimit radius below
+// 44 pixels) skips the spectral entries that the bandlimit zeroes for every column (pass
+// B's masked k2x column per half, pass C's entries 11..20), with the same results.
+template <bool EVEN, bool HALF, bool PRUNE>
 __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, const int mode) {
   extern __shared__ __align__(16) float2 sm[];
   float2* X = sm;              // exchange table, 512 rows x kXP
@@ -514,26 +576,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
           b0[q * 4 + r] = xb[(128 * q + r) * kXP];
           b1[q * 4 + r] = xb[(128 * q + r) * kXP + 16];
         }
-      passB_fwd_tw<false>(b0, tB, twr[k1lo], twr[32 + k1lo]);
-      passB_fwd_tw<true>(b1, tB, twr[16 + k1lo], twr[48 + k1lo]);
-      // X2: element (k1y, k2x) to slot (q, r) = (k2x, k1y)
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
+      passB_fwd_tw<false, PRUNE>(b0, tB, twr[k1lo], twr[32 + k1lo]);
+      passB_fwd_tw<true, PRUNE>(b1, tB, twr[16 + k1lo], twr[48 + k1lo]);
+      // X2: element (k1y, k2x) to slot (q, r) = (k2x, k1y); a pruned column is not written
+      // (pass C finds finite values of this slice's X1 there and multiplies them by zero)
+      static_for<0, 4>([&](auto qq) {
+        constexpr int q = decltype(qq)::value;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          xb[(128 * q + r) * kXP] = b0[r * 4 + q];
-          xb[(128 * q + r) * kXP + 16] = b1[r * 4 + q];
+          if constexpr (q != masked_k2x<false, PRUNE>()) xb[(128 * q + r) * kXP] = b0[r * 4 + q];
+          if constexpr (q != masked_k2x<true, PRUNE>()) xb[(128 * q + r) * kXP + 16] = b1[r * 4 + q];
         }
+      });
       __syncthreads();
       if (c_live) {
         float2 c[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) c[j] = xc[j * 4 * kXP];
-        dft32<false>(c);
+        dft32<false, PRUNE ? 1 : 0>(c);
         // propagation (Sec. 3.2): exp(-i pi lambda eps |k|^2), bandlimit, 1/W^2
 #pragma unroll
-        for (int j = 0; j < 32; ++j) c[j] = cmul(c[j], j < 16 ? pp[4 * j] : pm[-4 * j]);
-        dft32<true>(c);
+        for (int j = 0; j < 32; ++j)
+          if (!PRUNE || !in_gap(j)) c[j] = cmul(c[j], j < 16 ? pp[4 * j] : pm[-4 * j]);
+        dft32<true, PRUNE ? 2 : 0>(c);
 #pragma unroll
         for (int j = 0; j < 32; ++j) xc[j * 4 * kXP] = c[j];
       } else {
@@ -541,15 +606,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
         for (int j = 0; j < 32; ++j) xc[j * 4 * kXP] = make_float2(0.f, 0.f);
       }
       __syncthreads();
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
+      static_for<0, 4>([&](auto qq) {
+        constexpr int q = decltype(qq)::value;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          b0[r * 4 + q] = xb[(128 * q + r) * kXP];
-          b1[r * 4 + q] = xb[(128 * q + r) * kXP + 16];
+          if constexpr (q != masked_k2x<false, PRUNE>()) b0[r * 4 + q] = xb[(128 * q + r) * kXP];
+          if constexpr (q != masked_k2x<true, PRUNE>()) b1[r * 4 + q] = xb[(128 * q + r) * kXP + 16];
         }
-      passB_inv_tw<false>(b0, tB, twr[k1lo], twr[32 + k1lo]);
-      passB_inv_tw<true>(b1, tB, twr[16 + k1lo], twr[48 + k1lo]);
+      });
+      passB_inv_tw<false, PRUNE>(b0, tB, twr[k1lo], twr[32 + k1lo]);
+      passB_inv_tw<true, PRUNE>(b1, tB, twr[16 + k1lo], twr[48 + k1lo]);
       // X4: element (y = 32 q + n2y, r) back to slot (q, r)
 #pragma unroll
       for (int q = 0; q < 4; ++q)
@@ -1120,10 +1186,14 @@ cudaError_t init_device_constants() {
   e = cudaMemcpyToSymbol(c_twrB, rb, sizeof(rb));
   if (e != cudaSuccess) return e;
   const int ss = static_cast<int>(slice_smem_bytes()), sy = static_cast<int>(synth_smem_bytes());
-  if ((e = cudaFuncSetAttribute(k_slice<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_slice<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_slice<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_slice<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
+  {
+    const void* ks[8] = {reinterpret_cast<const void*>(k_slice<false, false, false>), reinterpret_cast<const void*>(k_slice<false, false, true>),
+                         reinterpret_cast<const void*>(k_slice<false, true, false>),  reinterpret_cast<const void*>(k_slice<false, true, true>),
+                         reinterpret_cast<const void*>(k_slice<true, false, false>),  reinterpret_cast<const void*>(k_slice<true, false, true>),
+                         reinterpret_cast<const void*>(k_slice<true, true, false>),   reinterpret_cast<const void*>(k_slice<true, true, true>)};
+    for (const void* f : ks)
+      if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
+  }
   const int sr = static_cast<int>(slice_rs_smem_bytes());
   for (auto f : {k_slice_rs<3, 4>, k_slice_rs<5, 4>, k_slice_rs<7, 4>, k_slice_rs<9, 2>, k_slice_rs<11, 2>,
                  k_slice_rs<13, 2>})
@@ -1166,10 +1236,16 @@ cudaError_t launch_slice(const SliceLaunch& a, bool even_origins, bool half, int
     cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
   }
-  if (even_origins && !half) k_slice<true, false><<<grid, kThreads, sm, s>>>(a, mode);
-  if (!even_origins && !half) k_slice<false, false><<<grid, kThreads, sm, s>>>(a, mode);
-  if (even_origins && half) k_slice<true, true><<<grid, kThreads, sm, s>>>(a, mode);
-  if (!even_origins && half) k_slice<false, true><<<grid, kThreads, sm, s>>>(a, mode);
+  // the pruned kernel needs every job's bandlimit radius below 44 pixels (|ky| >= 44 for
+  // pass C's entries 11..20; |kx| >= 48 for pass B's masked columns)
+  bool prune = true;
+  for (int i = 0; i < a.n_jobs; ++i) prune = prune && a.job[i].r2max < 44 * 44;
+  using K = void (*)(const SliceLaunch, const int);
+  static const K table[8] = {k_slice<false, false, false>, k_slice<false, false, true>, k_slice<false, true, false>,
+                             k_slice<false, true, true>,   k_slice<true, false, false>,  k_slice<true, false, true>,
+                             k_slice<true, true, false>,   k_slice<true, true, true>};
+  const K f = table[(even_origins ? 4 : 0) + (half ? 2 : 0) + (prune ? 1 : 0)];
+  f<<<grid, kThreads, sm, s>>>(a, mode);
   return cudaGetLastError();
 }
 

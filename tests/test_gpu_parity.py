@@ -297,3 +297,27 @@ def test_serving_specimen_1024_100_slices_sampled_pixels(ctx):
     got = img[:, sample[:, 1], sample[:, 0]]
     assert _rel_pixel_err(got[0], ref[0]) < PIXEL_TOL
     _assert_image(got[1], ref[1])
+
+
+@pytest.mark.parametrize("frac", [0.68, 0.7, 1.0])
+def test_bandlimit_radius_selects_pruned_or_general_slice_kernel(ctx, frac):
+    """Bandlimit radii below 44 pixels of the 128-pixel window (2/3 and 0.68 here) run the
+    slice kernel that skips the spectral entries the bandlimit zeroes for every column;
+    wider bands (0.7: radius 44.8; 1.0: the whole square's inscribed circle) run the
+    general kernel. Both are held to the oracle with the same bounds."""
+    import dataclasses
+    w = WL.simple_cubic_workload()
+    w = dataclasses.replace(w, grid=dataclasses.replace(w.grid, bandlimit_frac=frac))
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    basis.propagate(0)
+    orc = _oracle(w)
+    for i in (0, 33, 517, 1023):
+        got = basis.exit_wave(i)
+        ref = orc.exit_wave(0, i)
+        assert np.max(np.abs(got - ref)) < 5e-5 * np.max(np.abs(ref)), (frac, i)
+    dets = [WL.Detector(0.0, 0.02), WL.Detector(0.02, 0.06)]
+    region = WL.Region(0, 0, 4, 3, (8, 8))
+    img = basis.image(dets, region)
+    ref = orc.image(dets, _probes(region, 128, 128))
+    assert _rel_pixel_err(img.reshape(2, -1), ref) < PIXEL_TOL
