@@ -818,55 +818,118 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
     const float2* const Uc = a.U ? a.U + cfg * a.u_slot : nullptr;
     const void* const Uhc = a.Uh ? static_cast<const void*>(static_cast<const __half2*>(a.Uh) + cfg * a.u_slot) : nullptr;
     const float* const Usc = a.Uscale ? a.Uscale + static_cast<size_t>(cfg) * a.n_translates : nullptr;
-    float2 v[32];
+    // Accumulation layout: lane l of warp w holds, for window rows y = 8 w + yl (yl < 8),
+    // columns x = 64 k + 2 l + e (k, e < 2) at acc[yl * 4 + k * 2 + e], so that one load
+    // instruction of a warp reads 512 contiguous bytes of a translate row (256 from the
+    // FP16 store). Pass A's layout (thread (y, r): x = 4 n1 + r) is reached afterwards
+    // through the warp's own rows of the X1 table.
+    float2 acc[32];
 #pragma unroll
-    for (int n1 = 0; n1 < 32; ++n1) v[n1] = make_float2(0.f, 0.f);
+    for (int i = 0; i < 32; ++i) acc[i] = make_float2(0.f, 0.f);
     const int32_t* tp = a.tidx + static_cast<size_t>(tq) * a.L;
     const float2* ap = a.alpha + static_cast<size_t>(tq) * a.L;
     const int2* sp = a.shift + static_cast<size_t>(tq) * a.L;
+    const int warp_id = T >> 5, lane_id = T & 31;
     for (int j = 0; j < a.L; ++j) {
       float2 al = ap[j];
       const int2 sh = sp[j];
-      int yy = ya - sh.y;
-      if (a.cyclic) {
-        yy &= (kW - 1);
-      } else if (yy < 0 || yy >= kW) {
-        continue;
-      }
-      const size_t off = static_cast<size_t>(tp[j]) * (kW * kW) + yy * kW;
-      const int x0 = ra - sh.x;
+      const int ti = tp[j];
       if constexpr (HALF) {
-        const float f = Usc[tp[j]];
+        const float f = Usc[ti];
         al.x *= f;
         al.y *= f;
-        const __half2* row = static_cast<const __half2*>(Uhc) + off;
+      }
+      const bool pair = (sh.x & 1) == 0;   // column pairs stay aligned and unbroken
+      if (pair) {
+        // all 16 loads of this translate first (pairs outside a non-periodic window read
+        // as zero), then the 32 complex FMAs; the FP16 store is kept packed until then
+        using Raw = typename std::conditional<HALF, uint2, float4>::type;
+        Raw buf[16];
 #pragma unroll
-        for (int n1 = 0; n1 < 32; ++n1) {
-          int xx = x0 + 4 * n1;
-          if (a.cyclic) {
-            xx &= (kW - 1);
-            v[n1] = cfma(v[n1], al, __half22float2(row[xx]));
-          } else if (xx >= 0 && xx < kW) {
-            v[n1] = cfma(v[n1], al, __half22float2(row[xx]));
+        for (int yl = 0; yl < 8; ++yl) {
+          int yy = 8 * warp_id + yl - sh.y;
+          bool ok = true;
+          if (a.cyclic)
+            yy &= (kW - 1);
+          else
+            ok = yy >= 0 && yy < kW;
+          const size_t off = static_cast<size_t>(ti) * (kW * kW) + yy * kW;
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            int xp = 64 * kk + 2 * lane_id - sh.x;
+            bool okx = ok;
+            if (a.cyclic)
+              xp &= (kW - 1);
+            else
+              okx = okx && xp >= 0 && xp < kW;
+            Raw r{};
+            if (okx) {
+              if constexpr (HALF)
+                r = *reinterpret_cast<const uint2*>(static_cast<const __half2*>(Uhc) + off + xp);
+              else
+                r = *reinterpret_cast<const float4*>(Uc + off + xp);
+            }
+            buf[yl * 2 + kk] = r;
           }
         }
-      } else {
-        const float2* row = Uc + off;
 #pragma unroll
-        for (int n1 = 0; n1 < 32; ++n1) {
-          int xx = x0 + 4 * n1;
+        for (int b = 0; b < 16; ++b) {
+          float2 f0, f1;
+          if constexpr (HALF) {
+            f0 = __half22float2(*reinterpret_cast<const __half2*>(&buf[b].x));
+            f1 = __half22float2(*reinterpret_cast<const __half2*>(&buf[b].y));
+          } else {
+            f0 = make_float2(buf[b].x, buf[b].y);
+            f1 = make_float2(buf[b].z, buf[b].w);
+          }
+          acc[2 * b] = cfma(acc[2 * b], al, f0);
+          acc[2 * b + 1] = cfma(acc[2 * b + 1], al, f1);
+        }
+      } else {
+#pragma unroll
+        for (int yl = 0; yl < 8; ++yl) {
+          int yy = 8 * warp_id + yl - sh.y;
           if (a.cyclic) {
-            xx &= (kW - 1);
-            v[n1] = cfma(v[n1], al, row[xx]);
-          } else if (xx >= 0 && xx < kW) {
-            v[n1] = cfma(v[n1], al, row[xx]);
+            yy &= (kW - 1);
+          } else if (yy < 0 || yy >= kW) {
+            continue;
+          }
+          const size_t off = static_cast<size_t>(ti) * (kW * kW) + yy * kW;
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            int xe = 64 * (m >> 1) + 2 * lane_id + (m & 1) - sh.x;
+            if (a.cyclic) {
+              xe &= (kW - 1);
+            } else if (xe < 0 || xe >= kW) {
+              continue;
+            }
+            if constexpr (HALF)
+              acc[yl * 4 + m] = cfma(acc[yl * 4 + m], al, __half22float2(static_cast<const __half2*>(Uhc)[off + xe]));
+            else
+              acc[yl * 4 + m] = cfma(acc[yl * 4 + m], al, Uc[off + xe]);
           }
         }
       }
     }
+    __syncthreads();   // previous probe's C reads of the table are done
+    // warp-private transpose through the warp's X1 rows (1088 entries): element (yl, x) at
+    // yl * 132 + x (16-byte writes of 512 contiguous bytes; the 64-bit reads of a half-warp,
+    // 4 rows x 4 residues, fall on 16 distinct bank pairs)
+    float2* const tb = R0 + warp_id * (32 * 34);
+#pragma unroll
+    for (int yl = 0; yl < 8; ++yl)
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk)
+        *reinterpret_cast<float4*>(tb + yl * 132 + 64 * kk + 2 * lane_id) =
+            make_float4(acc[yl * 4 + kk * 2].x, acc[yl * 4 + kk * 2].y, acc[yl * 4 + kk * 2 + 1].x,
+                        acc[yl * 4 + kk * 2 + 1].y);
+    __syncwarp();
+    float2 v[32];
+#pragma unroll
+    for (int n1 = 0; n1 < 32; ++n1) v[n1] = tb[(lane_id >> 2) * 132 + 4 * n1 + (lane_id & 3)];
+    __syncwarp();      // every lane has read its row before X1 overwrites the warp's rows
     // forward 2D DFT of Psi_p (passes A, B, C)
     passA_fwd(v, tA);
-    __syncthreads();   // previous probe's C reads are done
 #pragma unroll
     for (int k = 0; k < 32; k += 2) x1w[k / 2] = make_float4(v[k].x, v[k].y, v[k + 1].x, v[k + 1].y);
     __syncthreads();
