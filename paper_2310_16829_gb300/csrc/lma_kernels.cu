@@ -771,7 +771,7 @@ __device__ __forceinline__ int probe_of(int q, int npx, int npy, int sw) {
 // HALF reads the FP16 store and folds each wave's factor into its coefficient. MODE
 // selects the readout (ReadMode): 2D annuli, labelled pixel sets (3D STEM rings) or the
 // diffraction pattern on a centred crop (4D STEM).
-template <bool HALF, int MODE>
+template <bool HALF, int MODE, bool CYCLIC>
 __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a) {
   extern __shared__ __align__(16) float2 sm[];
   float2* R0 = sm;
@@ -845,11 +845,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
         // as zero), then the 32 complex FMAs; the FP16 store is kept packed until then
         using Raw = typename std::conditional<HALF, uint2, float4>::type;
         Raw buf[16];
+        if constexpr (!CYCLIC) {
+          // one pointer per translate, the 16 loads at fixed offsets (rows yl, halves kk);
+          // rows and columns outside the window are predicated off
+          // element (y0 + yl, x0 + 64 kk) of translate ti is at signed offset base + yl W +
+          // 64 kk; only offsets of rows and columns inside the window are dereferenced
+          const int y0 = 8 * warp_id - sh.y, x0 = 2 * lane_id - sh.x;
+          const long long base = static_cast<long long>(ti) * (kW * kW) + y0 * kW + x0;
+          const bool okx0 = static_cast<unsigned>(x0) < static_cast<unsigned>(kW);
+          const bool okx1 = static_cast<unsigned>(x0 + 64) < static_cast<unsigned>(kW);
+#pragma unroll
+          for (int yl = 0; yl < 8; ++yl) {
+            const bool oky = static_cast<unsigned>(y0 + yl) < static_cast<unsigned>(kW);
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+              Raw r{};
+              if (oky && (kk ? okx1 : okx0)) {
+                const long long e = base + (yl * kW + 64 * kk);
+                if constexpr (HALF)
+                  r = *reinterpret_cast<const uint2*>(static_cast<const __half2*>(Uhc) + e);
+                else
+                  r = *reinterpret_cast<const float4*>(Uc + e);
+              }
+              buf[yl * 2 + kk] = r;
+            }
+          }
+        } else {
 #pragma unroll
         for (int yl = 0; yl < 8; ++yl) {
           int yy = 8 * warp_id + yl - sh.y;
           bool ok = true;
-          if (a.cyclic)
+          if constexpr (CYCLIC)
             yy &= (kW - 1);
           else
             ok = yy >= 0 && yy < kW;
@@ -858,7 +884,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
           for (int kk = 0; kk < 2; ++kk) {
             int xp = 64 * kk + 2 * lane_id - sh.x;
             bool okx = ok;
-            if (a.cyclic)
+            if constexpr (CYCLIC)
               xp &= (kW - 1);
             else
               okx = okx && xp >= 0 && xp < kW;
@@ -871,6 +897,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
             }
             buf[yl * 2 + kk] = r;
           }
+        }
         }
 #pragma unroll
         for (int b = 0; b < 16; ++b) {
@@ -889,7 +916,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
 #pragma unroll
         for (int yl = 0; yl < 8; ++yl) {
           int yy = 8 * warp_id + yl - sh.y;
-          if (a.cyclic) {
+          if constexpr (CYCLIC) {
             yy &= (kW - 1);
           } else if (yy < 0 || yy >= kW) {
             continue;
@@ -898,7 +925,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
 #pragma unroll
           for (int m = 0; m < 4; ++m) {
             int xe = 64 * (m >> 1) + 2 * lane_id + (m & 1) - sh.x;
-            if (a.cyclic) {
+            if constexpr (CYCLIC) {
               xe &= (kW - 1);
             } else if (xe < 0 || xe >= kW) {
               continue;
@@ -1261,9 +1288,12 @@ cudaError_t init_device_constants() {
   for (auto f : {k_slice_rs<3, 4>, k_slice_rs<5, 4>, k_slice_rs<7, 4>, k_slice_rs<9, 2>, k_slice_rs<11, 2>,
                  k_slice_rs<13, 2>})
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sr)) != cudaSuccess) return e;
-  for (auto f : {k_synth_detect<false, kReadAnnuli>, k_synth_detect<true, kReadAnnuli>,
-                 k_synth_detect<false, kReadLabels>, k_synth_detect<true, kReadLabels>,
-                 k_synth_detect<false, kReadPattern>, k_synth_detect<true, kReadPattern>})
+  for (auto f : {k_synth_detect<false, kReadAnnuli, false>, k_synth_detect<true, kReadAnnuli, false>,
+                 k_synth_detect<false, kReadLabels, false>, k_synth_detect<true, kReadLabels, false>,
+                 k_synth_detect<false, kReadPattern, false>, k_synth_detect<true, kReadPattern, false>,
+                 k_synth_detect<false, kReadAnnuli, true>, k_synth_detect<true, kReadAnnuli, true>,
+                 k_synth_detect<false, kReadLabels, true>, k_synth_detect<true, kReadLabels, true>,
+                 k_synth_detect<false, kReadPattern, true>, k_synth_detect<true, kReadPattern, true>})
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sy)) != cudaSuccess) return e;
   return cudaSuccess;
 }
@@ -1333,13 +1363,18 @@ cudaError_t launch_synth(const SynthArgs& a, bool half, int mode, cudaStream_t s
   if (n_walk <= 0) return cudaSuccess;
   const int grid = n_walk * a.n_cfg;
   const size_t sm = synth_smem_bytes();
-  if (mode == kReadAnnuli && half) k_synth_detect<true, kReadAnnuli><<<grid, kThreads, sm, s>>>(a);
-  else if (mode == kReadAnnuli) k_synth_detect<false, kReadAnnuli><<<grid, kThreads, sm, s>>>(a);
-  else if (mode == kReadLabels && half) k_synth_detect<true, kReadLabels><<<grid, kThreads, sm, s>>>(a);
-  else if (mode == kReadLabels) k_synth_detect<false, kReadLabels><<<grid, kThreads, sm, s>>>(a);
-  else if (mode == kReadPattern && half) k_synth_detect<true, kReadPattern><<<grid, kThreads, sm, s>>>(a);
-  else if (mode == kReadPattern) k_synth_detect<false, kReadPattern><<<grid, kThreads, sm, s>>>(a);
-  else return cudaErrorInvalidValue;
+  // periodic probe windows (the window is the whole cell) wrap; others are zero outside
+  using K = void (*)(const SynthArgs);
+  static const K table[2][3][2] = {
+      {{k_synth_detect<false, kReadAnnuli, false>, k_synth_detect<false, kReadAnnuli, true>},
+       {k_synth_detect<false, kReadLabels, false>, k_synth_detect<false, kReadLabels, true>},
+       {k_synth_detect<false, kReadPattern, false>, k_synth_detect<false, kReadPattern, true>}},
+      {{k_synth_detect<true, kReadAnnuli, false>, k_synth_detect<true, kReadAnnuli, true>},
+       {k_synth_detect<true, kReadLabels, false>, k_synth_detect<true, kReadLabels, true>},
+       {k_synth_detect<true, kReadPattern, false>, k_synth_detect<true, kReadPattern, true>}}};
+  if (mode != kReadAnnuli && mode != kReadLabels && mode != kReadPattern) return cudaErrorInvalidValue;
+  const int mi = mode == kReadAnnuli ? 0 : (mode == kReadLabels ? 1 : 2);
+  table[half ? 1 : 0][mi][a.cyclic ? 1 : 0]<<<grid, kThreads, sm, s>>>(a);
   return cudaGetLastError();
 }
 
