@@ -715,7 +715,9 @@ def main():
     kernels = {k: {"launches_per_step": v["launches"] / args.steps,
                    "ms_per_launch": v["total_ms"] / max(1, v["launches"])} for k, v in prof.items()
                if isinstance(v, dict)}
-    kernels["synth"]["exit_wave_store_GBps"] = u_bytes / (synth_ms / 1e3) / 1e9 if synth_ms else None
+    # one synthesis launch reads the exit-wave store of every configuration once
+    kernels["synth"]["exit_wave_store_GBps"] = (u_bytes * len(w.phonons) / (synth_ms / 1e3) / 1e9
+                                                if synth_ms else None)
 
     edits = None
     if rank == 0 and args.edits > 0:
