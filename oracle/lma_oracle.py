@@ -445,6 +445,71 @@ def coefficients(psi0: np.ndarray, uW: np.ndarray, offsets: np.ndarray) -> Coeff
                           err_l2=err_l2, err_sup=err_sup)
 
 
+def trig_modulation_matrix(n: int) -> np.ndarray:
+    """W[k, j] = exp(-2 pi i j k / (2n + 1)), k = -n..n (rows), j = 0..2n (columns).
+
+    Sec. 2 writes the entries without the imaginary unit; with it, W carries the
+    coefficients of the elementary waves e^{ikt} into those of the 2n + 1 equispaced
+    translates t_j = 2 pi j / (2n + 1) (the reading taken here)."""
+    k = np.arange(-n, n + 1)[:, None]
+    j = np.arange(2 * n + 1)[None, :]
+    return np.exp(-2j * math.pi * j * k / (2 * n + 1))
+
+
+def trig_basis_matrix(n: int) -> np.ndarray:
+    """M with c = M a: the coefficients c_k of a polynomial in T_n from the coefficients a_j of
+    its expansion in the translates phi_n(t - t_j). phi_n(t - t_j) = sum_k w_k e^{-ik t_j} e^{ikt}
+    with w_k = cos(k pi / (2n + 2)), so M = diag(w) W (Sec. 2 prints W diag(w))."""
+    w = np.cos(np.arange(-n, n + 1) * math.pi / (2 * n + 2))
+    return w[:, None] * trig_modulation_matrix(n)
+
+
+def trig_basis_inverse(n: int) -> np.ndarray:
+    """M^-1 = W^* diag(1 / w) / (2n + 1), from W W^* = (2n + 1) I. Sec. 2 prints the factor
+    1 / (2n + 1)^2 and the factors in the other order; in two dimensions the tensor product
+    of two of these carries 1 / (2n + 1)^2."""
+    w = np.cos(np.arange(-n, n + 1) * math.pi / (2 * n + 2))
+    return trig_modulation_matrix(n).conj().T / w[None, :] / (2 * n + 1)
+
+
+def trig_closed_coefficients(psi0: np.ndarray, n: int, offsets: np.ndarray) -> np.ndarray:
+    """Closed-form coefficients of the tensor trigonometric input waves (Sec. 2, Sec. 4.2.3:
+    no least squares) for the probe ``psi0`` centred at pixel (0, 0) of the full N_y x N_x
+    grid and translates at ``offsets`` (dx, dy) relative to it.
+
+    With u(x, y) = phi_n(2 pi x / N_x) phi_n(2 pi y / N_y) and translates every N / (2n + 1)
+    pixels, the probe's part in T_n x T_n (its DFT coefficients with |k_x|, |k_y| <= n) is
+    sum_j a_j u_j with a_j the two-dimensional M^-1 applied to those coefficients; in the
+    coordinates of the translate offset d = X_j - p this is
+      a(d) = (2n + 1)^-2 sum_{|k_x|,|k_y|<=n} P(k) / (N_x N_y w_kx w_ky) e^{2 pi i (k_x d_x / N_x + k_y d_y / N_y)},
+    P the DFT of psi0. The DFT is numpy's; the sum is written out."""
+    ny, nx = psi0.shape
+    P = dft2(psi0)
+    ks = np.arange(-n, n + 1)
+    w = np.cos(ks * math.pi / (2 * n + 2))
+    G = P[np.mod(ks, ny)[:, None], np.mod(ks, nx)[None, :]] / (nx * ny * w[:, None] * w[None, :])
+    out = np.empty(len(offsets), dtype=np.complex128)
+    for j, (dx_, dy_) in enumerate(np.asarray(offsets)):
+        ph = np.exp(2j * math.pi * (ks[:, None] * dy_ / ny + ks[None, :] * dx_ / nx))
+        out[j] = np.sum(G * ph) / (2 * n + 1) ** 2
+    return out
+
+
+def coefficients_closed(psi0: np.ndarray, uW: np.ndarray, offsets: np.ndarray, n: int) -> CoefficientSet:
+    """Coefficient set with the closed-form trigonometric coefficients and the errors of the
+    windowed approximation, measured as for the least-squares sets."""
+    ny, nx = psi0.shape
+    W = uW.shape[0]
+    alpha = trig_closed_coefficients(psi0, n, offsets)
+    approx = np.zeros((ny, nx), dtype=np.complex128)
+    for a, o in zip(alpha, offsets):
+        approx += a * embed_window(uW, int(o[1]) - W // 2, int(o[0]) - W // 2, ny, nx)
+    err_l2 = float(np.linalg.norm(psi0 - approx) / np.linalg.norm(psi0))
+    err_sup = float(np.max(np.abs(psi0 - approx)) / np.max(np.abs(psi0)))
+    return CoefficientSet(alpha=alpha, offsets=np.asarray(offsets, dtype=np.int64),
+                          err_l2=err_l2, err_sup=err_sup)
+
+
 # ----------------------------------------------------------------------------
 # LMA steps (Fig. lma_pseudocode)
 # ----------------------------------------------------------------------------
@@ -508,6 +573,11 @@ class LmaParams:
     W: int
     D: int
     trig_degree: int = 0      # input wave kinds 2, 3: degree n of phi_n (0: from alpha_max l_x / lambda)
+    coef_mode: int = 0        # 0: least squares; 1: closed-form trigonometric coefficients (kind 2)
+
+    @property
+    def degree(self) -> int:
+        return self.trig_degree if self.trig_degree > 0 else trig_degree(self.lam, self.alpha_max, self.lx)
 
     @property
     def dx(self) -> float:
@@ -561,7 +631,10 @@ class LmaOracle:
         key = class_key(p, prm.in_spacing, prm.in_offset, prm.f)
         idx, offs = nearest_translates(p, self.lattice, prm.L, prm.nx, prm.ny)
         if key not in self._sets:
-            self._sets[key] = coefficients(self.psi0, self.uW, offs)
+            if prm.coef_mode == 1:
+                self._sets[key] = coefficients_closed(self.psi0, self.uW, offs, prm.degree)
+            else:
+                self._sets[key] = coefficients(self.psi0, self.uW, offs)
         cs = self._sets[key]
         if not np.array_equal(cs.offsets, offs):
             raise AssertionError("coefficient reuse broken: offsets differ inside a class")
@@ -640,7 +713,8 @@ class LmaOracle:
                     key = class_key(q, p.in_spacing, p.in_offset, p.f)
                     idx, offs = nearest_translates(q, self.lattice, p.L, p.nx, p.ny)
                     if key not in sets:
-                        sets[key] = coefficients(psi0, self.uW, offs)
+                        sets[key] = (coefficients_closed(psi0, self.uW, offs, self.prm.degree)
+                                     if self.prm.coef_mode == 1 else coefficients(psi0, self.uW, offs))
                     U = [self.exit_wave(phi, int(i)) for i in idx]
                     psi = synthesize(U, sets[key].alpha, offs, p.D, p.cyclic)
                     img[:, k] += [detect(psi, m) for m in masks]
@@ -883,4 +957,4 @@ def params_from_workload(w) -> LmaParams:
                      defocus=pr.defocus, kind=b.kind, gauss_sigma=b.gauss_sigma,
                      in_spacing=tuple(b.in_spacing_px), in_offset=tuple(b.in_offset_px),
                      f=b.f, L=b.L, W=b.window, D=b.det_window,
-                     trig_degree=getattr(b, "trig_degree", 0))
+                     trig_degree=getattr(b, "trig_degree", 0), coef_mode=getattr(b, "coef_mode", 0))

@@ -730,3 +730,74 @@ def test_trig_input_waves_tensor_and_radial():
         vals = [ur[W // 2 + y, W // 2 + x] for y, x in pts]
         assert np.ptp(np.real(vals)) < 1e-13
     assert abs(ur[W // 2, W // 2 + 5] - ur[W // 2 + 3, W // 2 + 4]) < 1e-13 and r[W // 2 + 3, W // 2 + 4] == 5
+
+
+# ---- closed-form coefficients of the tensor trigonometric input waves (Sec. 2, Sec. 4.2.3) ----
+
+def test_trig_basis_matrix_maps_translate_coefficients_to_fourier_coefficients():
+    """Brute force: sample sum_j a_j phi_n(t - 2 pi j / (2n + 1)) on 4n + 8 points, take its
+    Fourier coefficients with numpy's FFT, and compare with M a; M^-1 is the matrix inverse."""
+    rng = np.random.default_rng(41)
+    for n in (1, 3, 7):
+        a = rng.standard_normal(2 * n + 1) + 1j * rng.standard_normal(2 * n + 1)
+        npts = 4 * n + 8
+        t = 2 * np.pi * np.arange(npts) / npts
+        f = sum(a[j] * O.trig_poly(n, t - 2 * np.pi * j / (2 * n + 1)) for j in range(2 * n + 1))
+        c = np.fft.fft(f) / npts
+        c_k = c[np.mod(np.arange(-n, n + 1), npts)]
+        M = O.trig_basis_matrix(n)
+        assert np.max(np.abs(M @ a - c_k)) < 1e-12 * np.max(np.abs(c_k))
+        Minv = O.trig_basis_inverse(n)
+        assert np.max(np.abs(Minv - np.linalg.inv(M))) < 1e-12 * np.max(np.abs(Minv))
+        assert np.max(np.abs(Minv @ M - np.eye(2 * n + 1))) < 1e-12
+
+
+def _trig_full_period_translates(n, N, offsets):
+    """Columns u_j on the full N x N grid: phi_n(2 pi (x - d_x) / N) phi_n(2 pi (y - d_y) / N)."""
+    x = np.arange(N)
+    cols = []
+    for dx_, dy_ in offsets:
+        ux = O.trig_poly(n, 2 * np.pi * (x - dx_) / N)
+        uy = O.trig_poly(n, 2 * np.pi * (x - dy_) / N)
+        cols.append(np.outer(uy, ux).ravel())
+    return np.stack(cols, axis=1)
+
+
+def test_trig_closed_coefficients_reconstruct_every_band_limited_wave():
+    """A random wave with DFT coefficients only at |k_x|, |k_y| <= n is rebuilt exactly from all
+    (2n + 1)^2 full-period translates every N / (2n + 1) pixels, for lattice offsets 0 and
+    nonzero; least squares over the same translates gives the same coefficients."""
+    rng = np.random.default_rng(42)
+    for n, s, off in ((2, 3, (0, 0)), (3, 4, (1, 2))):
+        N = s * (2 * n + 1)
+        spec = np.zeros((N, N), dtype=np.complex128)
+        ks = np.mod(np.arange(-n, n + 1), N)
+        spec[ks[:, None], ks[None, :]] = rng.standard_normal((2 * n + 1, 2 * n + 1)) + \
+            1j * rng.standard_normal((2 * n + 1, 2 * n + 1))
+        f = np.fft.ifft2(spec)
+        offsets = np.array([(off[0] + jx * s, off[1] + jy * s) for jy in range(2 * n + 1)
+                            for jx in range(2 * n + 1)])
+        a = O.trig_closed_coefficients(f, n, offsets)
+        A = _trig_full_period_translates(n, N, offsets)
+        assert np.max(np.abs(A @ a - f.ravel())) < 1e-12 * np.max(np.abs(f))
+        a_ls = np.linalg.lstsq(A, f.ravel(), rcond=None)[0]
+        assert np.max(np.abs(a_ls - a)) < 1e-10 * np.max(np.abs(a))
+
+
+def test_trig_closed_coefficients_of_a_probe_on_a_periodic_window():
+    """W = N (the window is the whole period): a probe whose aperture lies inside |k| <= n is
+    represented with zero error by the closed-form coefficients of all translates, and the
+    coefficients decay away from the probe (the translates are localized)."""
+    n, s = 3, 4
+    N = s * (2 * n + 1)
+    dx = 0.5
+    lam = 0.02508
+    alpha = 2.5 * lam / (N * dx)          # aperture radius 2.5 Fourier pixels < n
+    psi0 = O.probe(N, N, dx, dx, lam, alpha)
+    uW = O.input_wave_window(2, N, N, N, dx, dx, lam, alpha, 0.0, 0.0, 0.0, degree=n)
+    offsets = np.array([(jx * s - (N // 2 // s) * s, jy * s - (N // 2 // s) * s)
+                        for jy in range(2 * n + 1) for jx in range(2 * n + 1)])
+    cs = O.coefficients_closed(psi0, uW, offsets, n)
+    assert cs.err_sup < 1e-12 and cs.err_l2 < 1e-12
+    d = np.hypot(offsets[:, 0], offsets[:, 1])
+    assert np.abs(cs.alpha[d == 0]).max() > 4 * np.abs(cs.alpha[d >= 3 * s]).max()
