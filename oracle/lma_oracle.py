@@ -472,18 +472,24 @@ def trig_basis_inverse(n: int) -> np.ndarray:
     return trig_modulation_matrix(n).conj().T / w[None, :] / (2 * n + 1)
 
 
-def trig_closed_coefficients(psi0: np.ndarray, n: int, offsets: np.ndarray) -> np.ndarray:
+def trig_closed_coefficients(psi0: np.ndarray, n: int, offsets: np.ndarray,
+                             m: Tuple[int, int] | None = None) -> np.ndarray:
     """Closed-form coefficients of the tensor trigonometric input waves (Sec. 2, Sec. 4.2.3:
     no least squares) for the probe ``psi0`` centred at pixel (0, 0) of the full N_y x N_x
-    grid and translates at ``offsets`` (dx, dy) relative to it.
+    grid and translates at ``offsets`` (dx, dy) relative to it, on a lattice of m = (m_x, m_y)
+    translates per axis (default 2n + 1).
 
-    With u(x, y) = phi_n(2 pi x / N_x) phi_n(2 pi y / N_y) and translates every N / (2n + 1)
-    pixels, the probe's part in T_n x T_n (its DFT coefficients with |k_x|, |k_y| <= n) is
+    With u(x, y) = phi_n(2 pi x / N_x) phi_n(2 pi y / N_y) and m = 2n + 1 translates per
+    period, the probe's part in T_n x T_n (its DFT coefficients with |k_x|, |k_y| <= n) is
     sum_j a_j u_j with a_j the two-dimensional M^-1 applied to those coefficients; in the
     coordinates of the translate offset d = X_j - p this is
-      a(d) = (2n + 1)^-2 sum_{|k_x|,|k_y|<=n} P(k) / (N_x N_y w_kx w_ky) e^{2 pi i (k_x d_x / N_x + k_y d_y / N_y)},
-    P the DFT of psi0. The DFT is numpy's; the sum is written out."""
+      a(d) = (m_x m_y)^-1 sum_{|k_x|,|k_y|<=n} P(k) / (N_x N_y w_kx w_ky) e^{2 pi i (k_x d_x / N_x + k_y d_y / N_y)},
+    P the DFT of psi0. For m > 2n + 1 (a denser lattice, as on power-of-two grids, which
+    2n + 1 never divides) the same sum with 1 / (m_x m_y) is again exact: the lattice sum of
+    e^{2 pi i (k' - k) X_j / N} vanishes for k' != k when |k' - k| <= 2n < m; it is the
+    minimum-norm representation. The DFT is numpy's; the sum is written out."""
     ny, nx = psi0.shape
+    mx, my = m if m is not None else (2 * n + 1, 2 * n + 1)
     P = dft2(psi0)
     ks = np.arange(-n, n + 1)
     w = np.cos(ks * math.pi / (2 * n + 2))
@@ -491,16 +497,18 @@ def trig_closed_coefficients(psi0: np.ndarray, n: int, offsets: np.ndarray) -> n
     out = np.empty(len(offsets), dtype=np.complex128)
     for j, (dx_, dy_) in enumerate(np.asarray(offsets)):
         ph = np.exp(2j * math.pi * (ks[:, None] * dy_ / ny + ks[None, :] * dx_ / nx))
-        out[j] = np.sum(G * ph) / (2 * n + 1) ** 2
+        out[j] = np.sum(G * ph) / (mx * my)
     return out
 
 
-def coefficients_closed(psi0: np.ndarray, uW: np.ndarray, offsets: np.ndarray, n: int) -> CoefficientSet:
-    """Coefficient set with the closed-form trigonometric coefficients and the errors of the
-    windowed approximation, measured as for the least-squares sets."""
+def coefficients_closed(psi0: np.ndarray, uW: np.ndarray, offsets: np.ndarray, n: int,
+                        m: Tuple[int, int] | None = None) -> CoefficientSet:
+    """Coefficient set with the closed-form trigonometric coefficients (lattice of m translates
+    per axis) and the errors of the windowed approximation, measured as for the least-squares
+    sets."""
     ny, nx = psi0.shape
     W = uW.shape[0]
-    alpha = trig_closed_coefficients(psi0, n, offsets)
+    alpha = trig_closed_coefficients(psi0, n, offsets, m)
     approx = np.zeros((ny, nx), dtype=np.complex128)
     for a, o in zip(alpha, offsets):
         approx += a * embed_window(uW, int(o[1]) - W // 2, int(o[0]) - W // 2, ny, nx)
@@ -580,6 +588,11 @@ class LmaParams:
         return self.trig_degree if self.trig_degree > 0 else trig_degree(self.lam, self.alpha_max, self.lx)
 
     @property
+    def lattice_m(self) -> Tuple[int, int]:
+        """Input waves per axis of the I_f lattice."""
+        return (self.nx // (self.in_spacing[0] * self.f), self.ny // (self.in_spacing[1] * self.f))
+
+    @property
     def dx(self) -> float:
         return self.lx / self.nx
 
@@ -632,7 +645,7 @@ class LmaOracle:
         idx, offs = nearest_translates(p, self.lattice, prm.L, prm.nx, prm.ny)
         if key not in self._sets:
             if prm.coef_mode == 1:
-                self._sets[key] = coefficients_closed(self.psi0, self.uW, offs, prm.degree)
+                self._sets[key] = coefficients_closed(self.psi0, self.uW, offs, prm.degree, prm.lattice_m)
             else:
                 self._sets[key] = coefficients(self.psi0, self.uW, offs)
         cs = self._sets[key]
@@ -713,7 +726,7 @@ class LmaOracle:
                     key = class_key(q, p.in_spacing, p.in_offset, p.f)
                     idx, offs = nearest_translates(q, self.lattice, p.L, p.nx, p.ny)
                     if key not in sets:
-                        sets[key] = (coefficients_closed(psi0, self.uW, offs, self.prm.degree)
+                        sets[key] = (coefficients_closed(psi0, self.uW, offs, self.prm.degree, self.prm.lattice_m)
                                      if self.prm.coef_mode == 1 else coefficients(psi0, self.uW, offs))
                     U = [self.exit_wave(phi, int(i)) for i in idx]
                     psi = synthesize(U, sets[key].alpha, offs, p.D, p.cyclic)

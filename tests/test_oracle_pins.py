@@ -765,19 +765,20 @@ def _trig_full_period_translates(n, N, offsets):
 
 def test_trig_closed_coefficients_reconstruct_every_band_limited_wave():
     """A random wave with DFT coefficients only at |k_x|, |k_y| <= n is rebuilt exactly from all
-    (2n + 1)^2 full-period translates every N / (2n + 1) pixels, for lattice offsets 0 and
-    nonzero; least squares over the same translates gives the same coefficients."""
+    full-period translates of the lattice, for m = 2n + 1 translates per axis (the paper's
+    M^-1) and for denser lattices on power-of-two grids (m = 8, 16 > 2n + 1), with zero and
+    nonzero lattice offsets; least squares (numpy's minimum-norm solution) over the same
+    translates gives the same coefficients."""
     rng = np.random.default_rng(42)
-    for n, s, off in ((2, 3, (0, 0)), (3, 4, (1, 2))):
-        N = s * (2 * n + 1)
+    for n, N, m, off in ((2, 15, 5, (0, 0)), (3, 28, 7, (1, 2)), (3, 16, 8, (1, 0)), (2, 32, 16, (0, 1))):
+        s = N // m
         spec = np.zeros((N, N), dtype=np.complex128)
         ks = np.mod(np.arange(-n, n + 1), N)
         spec[ks[:, None], ks[None, :]] = rng.standard_normal((2 * n + 1, 2 * n + 1)) + \
             1j * rng.standard_normal((2 * n + 1, 2 * n + 1))
         f = np.fft.ifft2(spec)
-        offsets = np.array([(off[0] + jx * s, off[1] + jy * s) for jy in range(2 * n + 1)
-                            for jx in range(2 * n + 1)])
-        a = O.trig_closed_coefficients(f, n, offsets)
+        offsets = np.array([(off[0] + jx * s, off[1] + jy * s) for jy in range(m) for jx in range(m)])
+        a = O.trig_closed_coefficients(f, n, offsets, (m, m))
         A = _trig_full_period_translates(n, N, offsets)
         assert np.max(np.abs(A @ a - f.ravel())) < 1e-12 * np.max(np.abs(f))
         a_ls = np.linalg.lstsq(A, f.ravel(), rcond=None)[0]
