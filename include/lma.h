@@ -52,6 +52,19 @@ typedef int32_t lma_status;
 #define LMA_BASIS_TRIG 2       /* u = phi_n(2 pi x / l_x) phi_n(2 pi y / l_y), trigonometric polynomials (Sec. 4.2.3) */
 #define LMA_BASIS_TRIG_RADIAL 3 /* u = phi_n(2 pi |v| / l_x), the circularly symmetric option (Sec. 4.2.3) */
 
+/* Coefficients of the input waves for each probe (lma_basis_desc.coef_mode). */
+#define LMA_COEF_LSQ 0          /* least squares over the L nearest input waves (eqs. lma_approximation_exit1_0 /
+                                   exit2_0), for every kind of input wave */
+#define LMA_COEF_TRIG_CLOSED 1  /* LMA_BASIS_TRIG only: the closed form of Sec. 2 and Sec. 4.2.3 (no least
+                                   squares). The probe's DFT coefficients P(k) with |k_x|, |k_y| <= n give
+                                   a(d) = sum_k P(k) / (N_x N_y w_kx w_ky m_x m_y) e^{2 pi i (k_x d_x / N_x + k_y d_y / N_y)}
+                                   for the input wave at offset d from the probe, w_k = cos(k pi / (2n + 2)),
+                                   m_x x m_y input waves of I_f. With m = 2n + 1 per axis this is the M^-1 of
+                                   Sec. 2 (derived from its definition M = diag(w) W, W_{k,j} = e^{-2 pi i jk/(2n+1)});
+                                   with m > 2n + 1 (power-of-two grids, which 2n + 1 never divides) it is the
+                                   exact minimum-norm representation. The probe uses the values at its L
+                                   nearest input waves; needs m_x, m_y >= 2n + 1. */
+
 #define LMA_PREC_C64 0         /* complex64 everywhere on the device */
 #define LMA_PREC_MIXED 1       /* FP32 propagation; exit waves stored as FP16 pairs with a per-wave
                                   power-of-two scale: half the store; bright-field readings within
@@ -135,6 +148,7 @@ typedef struct {
                                 0 = as many as fit in 40 % of the free device memory */
   int32_t trig_degree;       /* LMA_BASIS_TRIG*: degree n of phi_n(t) = sum_{|k|<=n} e^{ikt} cos(k pi/(2n+2));
                                 0 = round(alpha_max l_x / lambda) (maximum probe frequency / Fourier pixel) */
+  int32_t coef_mode;         /* LMA_COEF_LSQ or LMA_COEF_TRIG_CLOSED */
 } lma_basis_desc;
 
 /* Annular detector r1 <= lambda |k| < r2 (rad), intersected with the bandlimit (Sec. 3.1, 2D STEM). */

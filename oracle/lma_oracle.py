@@ -763,8 +763,9 @@ class LmaOracle:
 def select_L(prm: LmaParams, probes: np.ndarray, eps_sup: float, L_max: int) -> Tuple[int, float]:
     """Smallest L (1..L_max) whose probe approximation error in the supremum norm, relative
     to the probe's maximum, is at most eps_sup for every probe class of `probes` (the
-    parameter choice of Sec. 4.2.6: a target error fixes L). Returns (L, worst error), or
-    (0, error at L_max) when no L reaches the target."""
+    parameter choice of Sec. 4.2.6: a target error fixes L), with the coefficients of
+    ``prm.coef_mode``. Returns (L, worst error), or (0, error at L_max) when no L reaches
+    the target."""
     lat = input_lattice(prm.nx, prm.ny, prm.in_spacing, prm.in_offset, prm.f)
     psi0 = probe(prm.ny, prm.nx, prm.dy, prm.dx, prm.lam, prm.alpha_max, prm.cs, prm.defocus)
     uW = input_wave_window(prm.kind, prm.W, prm.ny, prm.nx, prm.dy, prm.dx, prm.lam, prm.alpha_max,
@@ -773,10 +774,14 @@ def select_L(prm: LmaParams, probes: np.ndarray, eps_sup: float, L_max: int) -> 
     for q in probes:
         key = class_key((int(q[0]), int(q[1])), prm.in_spacing, prm.in_offset, prm.f)
         reps.setdefault(key, (int(q[0]), int(q[1])))
+    def fit(offs):
+        if prm.coef_mode == 1:
+            return coefficients_closed(psi0, uW, offs, prm.degree, prm.lattice_m)
+        return coefficients(psi0, uW, offs)
+
     err = float("inf")
     for L in range(1, L_max + 1):
-        err = max(coefficients(psi0, uW, nearest_translates(q, lat, L, prm.nx, prm.ny)[1]).err_sup
-                  for q in reps.values())
+        err = max(fit(nearest_translates(q, lat, L, prm.nx, prm.ny)[1]).err_sup for q in reps.values())
         if err <= eps_sup:
             return L, err
     return 0, err

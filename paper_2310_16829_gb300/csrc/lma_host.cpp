@@ -377,6 +377,7 @@ struct lma_basis {
   lma_probe probe{};
   lma_basis_desc desc{};
   double gauss_sigma = 0.0;
+  int trig_n = 0;              // degree n of the trigonometric input waves
   int nx = 0, ny = 0;
   int Sx = 0, Sy = 0, ox = 0, oy = 0, nax = 0, nay = 0;
   int64_t nT = 0;
@@ -471,8 +472,7 @@ void build_input_wave(lma_basis* b) {
     }
   } else if (b->desc.kind == LMA_BASIS_TRIG || b->desc.kind == LMA_BASIS_TRIG_RADIAL) {
     // phi_n(t) = 1 + 2 sum_{k=1..n} cos(k t) cos(k pi / (2n + 2))
-    const int n = b->desc.trig_degree > 0 ? b->desc.trig_degree
-                                           : static_cast<int>(std::lround(b->probe.alpha_max * g.lx / g.lambda));
+    const int n = b->trig_n;
     auto phi = [n](double t) {
       double v = 1.0;
       for (int k = 1; k <= n; ++k) v += 2.0 * std::cos(k * t) * std::cos(k * kPi / (2 * n + 2));
@@ -536,6 +536,44 @@ void nearest(const lma_basis* b, int px, int py, std::vector<int>& odx, std::vec
   }
 }
 
+// Closed-form coefficients of the tensor trigonometric input waves (Sec. 2, Sec. 4.2.3: no
+// least squares). With P the DFT of the probe centred at pixel 0, w_k = cos(k pi / (2n + 2))
+// and m_x x m_y input waves of I_f (m >= 2n + 1 per axis), the input wave at offset d from
+// the probe gets
+//   a(d) = sum_{|k_x|,|k_y|<=n} P(k) / (N_x N_y w_kx w_ky m_x m_y) e^{2 pi i (k_x d_x / N_x + k_y d_y / N_y)};
+// over all input waves this represents the probe's part in T_n x T_n exactly (m = 2n + 1:
+// the M^-1 of Sec. 2 from its definition M = diag(w) W; m > 2n + 1: the minimum-norm
+// representation, the lattice sum of e^{2 pi i (k' - k) X / N} vanishing for k' != k).
+void trig_closed_alpha(const lma_basis* b, const std::vector<cd>& psi0, const CoefSet& cs, std::vector<cd>& x) {
+  const int nx = b->nx, ny = b->ny, n = b->trig_n, K = 2 * n + 1;
+  std::vector<cd> P = psi0;
+  fft2(P, ny, nx, false);
+  std::vector<double> w(K);
+  for (int i = 0; i < K; ++i) w[i] = std::cos((i - n) * kPi / (2 * n + 2));
+  const double norm = static_cast<double>(nx) * ny * static_cast<double>(b->nax) * b->nay;
+  std::vector<cd> G(static_cast<size_t>(K) * K);
+  for (int iy = 0; iy < K; ++iy)
+    for (int ix = 0; ix < K; ++ix)
+      G[static_cast<size_t>(iy) * K + ix] =
+          P[static_cast<size_t>(mod(iy - n, ny)) * nx + mod(ix - n, nx)] / (norm * w[ix] * w[iy]);
+  const int L = static_cast<int>(cs.odx.size());
+  x.assign(L, cd(0.0, 0.0));
+  std::vector<cd> ex(K), ey(K);
+  for (int j = 0; j < L; ++j) {
+    for (int i = 0; i < K; ++i) {
+      ex[i] = std::polar(1.0, 2.0 * kPi * (i - n) * cs.odx[j] / nx);
+      ey[i] = std::polar(1.0, 2.0 * kPi * (i - n) * cs.ody[j] / ny);
+    }
+    cd acc(0.0, 0.0);
+    for (int iy = 0; iy < K; ++iy) {
+      cd row(0.0, 0.0);
+      for (int ix = 0; ix < K; ++ix) row += G[static_cast<size_t>(iy) * K + ix] * ex[ix];
+      acc += row * ey[iy];
+    }
+    x[j] = acc;
+  }
+}
+
 // least-squares coefficients of one probe class (eqs. lma_approximation_exit1_0 / exit2_0),
 // in coordinates relative to the probe (probe at pixel 0, translate j at its offset)
 // least squares of probe psi0 on the input waves at cs.odx / cs.ody (their count is L)
@@ -579,8 +617,11 @@ lma_status solve_set_for(lma_basis* b, const std::vector<cd>& psi0, CoefSet& cs)
     }
   }
   std::vector<cd> A0 = A, rhs0 = rhs, x;
-  if (!lstsq_householder(A, m, L, rhs, x))
+  if (b->desc.coef_mode == LMA_COEF_TRIG_CLOSED) {
+    trig_closed_alpha(b, psi0, cs, x);
+  } else if (!lstsq_householder(A, m, L, rhs, x)) {
     return fail(b->ctx, LMA_ERR_INVALID, "least squares: input waves are linearly dependent");
+  }
   cs.alpha = x;
   // errors over the full grid (outside the windows the approximation is zero)
   double r2 = 0.0, rmax = 0.0, n2 = 0.0, pmax = 0.0;
@@ -1530,6 +1571,10 @@ lma_status lma_create_basis(lma_ctx* ctx, const lma_specimen* spec, const lma_pr
       d.kind != LMA_BASIS_TRIG_RADIAL)
     return fail(ctx, LMA_ERR_INVALID, "unknown input wave kind");
   if (d.trig_degree < 0 || d.trig_degree > 4096) return fail(ctx, LMA_ERR_INVALID, "trig_degree must be in [0, 4096]");
+  if (d.coef_mode != LMA_COEF_LSQ && d.coef_mode != LMA_COEF_TRIG_CLOSED)
+    return fail(ctx, LMA_ERR_INVALID, "coef_mode must be LMA_COEF_LSQ or LMA_COEF_TRIG_CLOSED");
+  if (d.coef_mode == LMA_COEF_TRIG_CLOSED && d.kind != LMA_BASIS_TRIG)
+    return fail(ctx, LMA_ERR_INVALID, "closed-form coefficients need the tensor trigonometric input waves (LMA_BASIS_TRIG)");
   if (d.precision != LMA_PREC_C64 && d.precision != LMA_PREC_MIXED)
     return fail(ctx, LMA_ERR_INVALID, "precision must be LMA_PREC_C64 or LMA_PREC_MIXED");
   if (!(probe->alpha_max > 0)) return fail(ctx, LMA_ERR_INVALID, "alpha_max must be positive");
@@ -1544,6 +1589,12 @@ lma_status lma_create_basis(lma_ctx* ctx, const lma_specimen* spec, const lma_pr
   if (d.L <= 0 || d.L > kMaxL || d.L > nT)
     return fail(ctx, LMA_ERR_INVALID, "L must be in [1, min(|I_f|, %d)]", kMaxL);
   if (nT > (1ll << 31) - 1) return fail(ctx, LMA_ERR_INVALID, "too many input waves");
+  const int trig_n = d.trig_degree > 0 ? d.trig_degree : static_cast<int>(std::lround(probe->alpha_max * g.lx / g.lambda));
+  if (d.coef_mode == LMA_COEF_TRIG_CLOSED &&
+      (g.nx / (sx * d.f) < 2 * trig_n + 1 || g.ny / (sy * d.f) < 2 * trig_n + 1))
+    return fail(ctx, LMA_ERR_INVALID,
+                "closed-form coefficients need at least 2n + 1 = %d input waves per axis (I_f has %d x %d)",
+                2 * trig_n + 1, g.nx / (sx * d.f), g.ny / (sy * d.f));
   lma_basis* b = new (std::nothrow) lma_basis();
   if (!b) return fail(ctx, LMA_ERR_OOM, "host allocation");
   b->ctx = ctx;
@@ -1560,6 +1611,7 @@ lma_status lma_create_basis(lma_ctx* ctx, const lma_specimen* spec, const lma_pr
   b->nax = g.nx / b->Sx;
   b->nay = g.ny / b->Sy;
   b->nT = nT;
+  b->trig_n = trig_n;
   build_input_wave(b);
   // propagator factors on the W-grid: exp(-i pi lambda eps k^2); 1/W^2 folded into e_x
   const double dx = g.lx / g.nx, dy = g.ly / g.ny;

@@ -32,6 +32,8 @@ LMA_BASIS_GAUSS = 0
 LMA_BASIS_PROBE = 1
 LMA_BASIS_TRIG = 2
 LMA_BASIS_TRIG_RADIAL = 3
+LMA_COEF_LSQ = 0
+LMA_COEF_TRIG_CLOSED = 1
 LMA_PREC_C64 = 0
 LMA_PREC_MIXED = 1
 LMA_EDIT_REMOVE = 0
@@ -90,7 +92,7 @@ class BasisDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("gauss_sigma", C.c_double), ("in_spacing_px", C.c_int32 * 2),
                 ("in_offset_px", C.c_int32 * 2), ("f", C.c_int32), ("L", C.c_int32),
                 ("window", C.c_int32), ("det_window", C.c_int32), ("precision", C.c_int32),
-                ("phonon_batch", C.c_int32), ("trig_degree", C.c_int32)]
+                ("phonon_batch", C.c_int32), ("trig_degree", C.c_int32), ("coef_mode", C.c_int32)]
 
 
 class Detector(C.Structure):
@@ -370,7 +372,8 @@ class Basis:
         d = BasisDesc(desc.kind, desc.gauss_sigma, (C.c_int32 * 2)(*desc.in_spacing_px),
                       (C.c_int32 * 2)(*desc.in_offset_px), desc.f, desc.L, desc.window,
                       desc.det_window, getattr(desc, "precision", LMA_PREC_C64),
-                      getattr(desc, "phonon_batch", 0), getattr(desc, "trig_degree", 0))
+                      getattr(desc, "phonon_batch", 0), getattr(desc, "trig_degree", 0),
+                      getattr(desc, "coef_mode", LMA_COEF_LSQ))
         h = _VP()
         ctx.check(ctx.lib.lma_create_basis(ctx.h, spec.h, C.byref(pr), C.byref(d), C.byref(h)))
         self.h = h
@@ -529,7 +532,7 @@ def select_L(ctx: Context, spec: "Specimen", probe, desc, region, L_max: int, ep
     d = BasisDesc(desc.kind, desc.gauss_sigma, (C.c_int32 * 2)(*desc.in_spacing_px),
                   (C.c_int32 * 2)(*desc.in_offset_px), desc.f, desc.L, desc.window,
                   desc.det_window, getattr(desc, "precision", LMA_PREC_C64), getattr(desc, "phonon_batch", 0),
-                  getattr(desc, "trig_degree", 0))
+                  getattr(desc, "trig_degree", 0), getattr(desc, "coef_mode", LMA_COEF_LSQ))
     reg = _region(region)
     L = C.c_int32()
     err = C.c_double()

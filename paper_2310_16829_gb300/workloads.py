@@ -102,6 +102,7 @@ class BasisDesc:
     precision: int = PREC_C64
     phonon_batch: int = 0                    # configurations per launch; 0 = by free memory
     trig_degree: int = 0                     # BASIS_TRIG*: degree of phi_n; 0 = alpha_max l_x / lambda
+    coef_mode: int = 0                       # 0: least squares; 1: closed-form trigonometric (BASIS_TRIG)
 
 
 @dataclass

@@ -207,3 +207,45 @@ def test_trig_input_waves_coefficients_match_oracle(kind):
     _check_coefficients(w, [(0, 0), (8, 120), (127, 3)], tol=1e-8)
     w.basis.trig_degree = 9
     _check_coefficients(w, [(0, 0), (40, 40)], tol=1e-8)
+
+
+def test_closed_form_trig_coefficients_match_oracle():
+    """LMA_COEF_TRIG_CLOSED: the host's closed-form coefficients (Sec. 2, Sec. 4.2.3) and their
+    approximation errors equal the oracle's, on the periodic 128^2 toy (n = 13, 32 input waves
+    per axis) and on a 256^2 ABO3 slab (n = 25, 64 per axis); the L selection agrees too."""
+    import dataclasses
+    for w, probes in ((WL.simple_cubic_workload(), [(0, 0), (8, 120), (127, 3)]),
+                      (WL.perovskite_workload(cells=5, nx=256, n_slices=2, n_phonons=1), [(2, 2), (101, 37)])):
+        w.basis.kind = WL.BASIS_TRIG
+        w.basis.coef_mode = 1
+        _check_coefficients(w, probes, tol=1e-9)
+    w = WL.simple_cubic_workload()
+    w.basis.kind = WL.BASIS_TRIG
+    w.basis.coef_mode = 1
+    region = WL.Region(0, 0, 6, 5, (2, 2))
+    ctx, spec, basis = _host_objects(w)
+    prm = O.params_from_workload(w)
+    probes = O.region_probes(region.px0, region.py0, region.npx, region.npy, region.spacing_px,
+                             w.grid.nx, w.grid.ny)
+    for eps in (0.5, 0.3):
+        L, err = lma.select_L(ctx, spec, w.probe, w.basis, region, 40, eps)
+        L_ref, err_ref = O.select_L(dataclasses.replace(prm, L=40), probes, eps, 40)
+        assert L == L_ref and abs(err - err_ref) < 1e-9, (eps, L, L_ref, err, err_ref)
+
+
+def test_closed_form_trig_coefficients_are_rejected_where_they_do_not_apply():
+    w = WL.simple_cubic_workload()
+    w.basis.coef_mode = 1                       # Gaussian input waves: no closed form
+    with pytest.raises(lma.LmaError) as e:
+        _host_objects(w)
+    assert e.value.status == lma.LMA_ERR_INVALID
+    w.basis.kind = WL.BASIS_TRIG
+    w.basis.in_spacing_px = (8, 8)              # 16 input waves per axis < 2n + 1 = 27
+    w.basis.in_offset_px = (0, 0)
+    with pytest.raises(lma.LmaError) as e:
+        _host_objects(w)
+    assert e.value.status == lma.LMA_ERR_INVALID and "2n + 1" in str(e.value)
+    w.basis.coef_mode = 2
+    with pytest.raises(lma.LmaError) as e:
+        _host_objects(w)
+    assert e.value.status == lma.LMA_ERR_INVALID

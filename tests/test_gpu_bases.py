@@ -34,3 +34,30 @@ def test_trig_input_waves_match_oracle(ctx, kind):
                                              region.spacing_px, w.grid.nx, w.grid.ny))
         err = np.abs(got - ref) / np.maximum(ref, 1e-4)
         assert err.max() < 1e-4, (w.name, kind, err.max())
+
+
+def test_closed_form_trig_coefficients_image_matches_oracle(ctx):
+    """LMA_COEF_TRIG_CLOSED (Sec. 2, Sec. 4.2.3: coefficients from the probe's Fourier
+    coefficients, no least squares) through synthesis and detection on the GPU against the
+    oracle's image with the same closed form; and, with all the other inputs fixed, the image
+    differs from the least-squares one (the coefficients are really the closed form)."""
+    for w, region in ((WL.simple_cubic_workload(), WL.Region(0, 0, 3, 2, (8, 8))),
+                      (WL.perovskite_workload(cells=5, nx=256, n_slices=5, n_phonons=1, seed_base=2800),
+                       WL.Region(252, 20, 3, 3, (4, 4)))):
+        w.basis.kind = WL.BASIS_TRIG
+        w.basis.coef_mode = 1
+        dets = [WL.Detector(0.0, 0.02), WL.Detector(0.06, 0.2)]
+        spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+        basis = lma.Basis(ctx, spec, w.probe, w.basis)
+        got = basis.image(dets, region, recompute=True).reshape(2, -1)
+        orc = O.LmaOracle(O.params_from_workload(w))
+        orc.set_specimen(w.phonons, w.potential.peak, w.potential.term_frac, w.potential.term_width,
+                         w.potential.r_cut)
+        probes = O.region_probes(region.px0, region.py0, region.npx, region.npy, region.spacing_px,
+                                 w.grid.nx, w.grid.ny)
+        ref = orc.image(dets, probes)
+        err = np.abs(got - ref) / np.maximum(ref, 1e-4)
+        assert err.max() < 1e-4, (w.name, err.max())
+        w.basis.coef_mode = 0
+        ls = lma.Basis(ctx, spec, w.probe, w.basis).image(dets, region, recompute=True).reshape(2, -1)
+        assert np.max(np.abs(ls - got) / np.maximum(ref, 1e-4)) > 1e-3, w.name
