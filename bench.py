@@ -418,6 +418,38 @@ def profile_case() -> None:
     print(json.dumps({"profile_case": w.name, "mean_haadf": float(out.mean())}))
 
 
+def approx_curves() -> None:
+    """Probe approximation error against L (1..64) and f for the input-wave kinds of Sec. 4.2.3
+    (the error-versus-L figures): host FP64 coefficients through the C-ABI, for the probe at
+    pixel (0, 0) of the E2-like geometry of workloads.probe_approximation_workload. Prints one
+    JSON line; no GPU work."""
+    from paper_2310_16829_gb300 import lma
+    ctx = lma.Context(-1)
+    cases = [("probe", WL.BASIS_PROBE, {}, (1, 2, 4)),
+             ("gauss_0.482A", WL.BASIS_GAUSS, {"gauss_sigma": 0.482}, (1, 2, 4)),
+             ("trig_lsq", WL.BASIS_TRIG, {}, (1, 2)),
+             ("trig_closed", WL.BASIS_TRIG, {"coef_mode": 1}, (1,))]
+    out = {}
+    t0 = time.perf_counter()
+    for name, kind, extra, fs in cases:
+        out[name] = {}
+        for f in fs:
+            rows = []
+            for L in range(1, 65):
+                w = WL.probe_approximation_workload(kind, f, L, **extra)
+                spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+                b = lma.Basis(ctx, spec, w.probe, w.basis)
+                err = b.coefficients(0, 0)[3]
+                rows.append([L, float(err[0]), float(err[1])])
+                b.close()
+                spec.close()
+            out[name][f"f{f}"] = rows
+    ctx.close()
+    print(json.dumps({"approx_curves": out, "geometry": "512^2 over 62.416 A, 200 kV, Z = 100 A, C_s = -2000 A, "
+                      "alpha_max = 26 mrad, input waves every 2 f px at offset 1 px, W = 128, probe at (0, 0)",
+                      "columns": ["L", "err_l2", "err_sup"], "seconds": time.perf_counter() - t0}))
+
+
 # ----------------------------------------------------------------------------------- main arm
 def main():
     ap = argparse.ArgumentParser()
@@ -440,12 +472,17 @@ def main():
                     help="configurations per specimen of the uneven three-specimen batch (0: skip)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one configuration of the workload, two image passes (for ncu captures)")
+    ap.add_argument("--approx-curves", action="store_true",
+                    help="probe approximation error against L and f per input-wave kind (host only)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     w = WL.perovskite_workload()
     if args.profile_case:
         profile_case()
+        return
+    if args.approx_curves:
+        approx_curves()
         return
     if args.impl == "reference":
         run_reference(args, w)

@@ -282,3 +282,30 @@ def sample_probes(region: Region, n: int, seed: int) -> np.ndarray:
     while len(pts) < n:
         pts.add((int(rng.integers(0, region.npx)), int(rng.integers(0, region.npy))))
     return np.asarray(sorted(pts), dtype=np.int64)
+
+
+# The probe-approximation geometry of Sec. 4.2.3's error-versus-L figures: 62.416 A at
+# 0.1219 A per pixel (512^2; the 128-pixel window then spans 15.6 A, the probe's extent),
+# 200 kV (lambda = 0.0250793 A), focus Z = 100 A, C_s = -2000 A, alpha_max = 26 mrad, probes
+# every 2 px and input waves at I = P + p/2.
+LAMBDA_200KV_FIG = 0.0250793
+
+
+def probe_approximation_workload(kind: int, f: int = 1, L: int = 32, gauss_sigma: float = 0.0,
+                                 coef_mode: int = 0) -> Workload:
+    """Probe approximation (coefficients only; one atom, one slice as a placeholder specimen)."""
+    grid = Grid(nx=512, ny=512, lx=62.416, ly=62.416, slice_dz=2.0, n_slices=1,
+                lam=LAMBDA_200KV_FIG, sigma=SIGMA_CFG0)
+    atoms = Atoms(np.array([0.0]), np.array([0.0]), np.array([0], np.int32), np.array([0], np.int16))
+    return Workload(
+        name=f"probe_approx_512sq_kind{kind}_f{f}",
+        grid=grid,
+        potential=Potential(peak=(300.0,)),
+        phonons=[atoms],
+        probe=Probe(alpha_max=0.026, cs=-2000.0, defocus=100.0),
+        basis=BasisDesc(kind=kind, gauss_sigma=gauss_sigma, in_spacing_px=(2, 2), in_offset_px=(1, 1),
+                        f=f, L=L, coef_mode=coef_mode),
+        detectors=[Detector(0.07, 0.2)],
+        region=Region(0, 0, 1, 1, (2, 2)),
+        notes="probe approximation error versus L and f (no image)",
+    )

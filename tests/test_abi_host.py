@@ -249,3 +249,23 @@ def test_closed_form_trig_coefficients_are_rejected_where_they_do_not_apply():
     with pytest.raises(lma.LmaError) as e:
         _host_objects(w)
     assert e.value.status == lma.LMA_ERR_INVALID
+
+
+def test_least_squares_error_never_rises_with_L():
+    """The L nearest input waves form nested sets (a fixed order), so the least-squares L2
+    error of the probe approximation cannot rise with L (the error-versus-L figures of
+    Sec. 4.2.3 fall in steps); probe, Gaussian and trigonometric input waves."""
+    ctx = lma.Context(-1)
+    for kind in (WL.BASIS_PROBE, WL.BASIS_GAUSS, WL.BASIS_TRIG):
+        prev = np.inf
+        for L in range(1, 25):
+            w = WL.simple_cubic_workload()
+            w.basis.kind = kind
+            w.basis.L = L
+            spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+            b = lma.Basis(ctx, spec, w.probe, w.basis)
+            e = b.coefficients(0, 0)[3][0]
+            assert e <= prev * (1 + 1e-12), (kind, L, e, prev)
+            prev = e
+            b.close()
+            spec.close()
