@@ -14,8 +14,8 @@ constexpr int kMaxDet = 4;
 
 // Step a1: projected potential and transmission of one configuration.
 struct PotArgs {
-  const double* ax;            // atom x (Angstrom), sorted by slice
-  const double* ay;            // atom y
+  const double* ax;            // atom x (Angstrom) in [0, l_x), sorted by slice
+  const double* ay;            // atom y in [0, l_y)
   const int16_t* asp;          // species
   const int32_t* slice_start;  // [n_slices + 1]
   const float* peak;           // [n_species] V*Angstrom

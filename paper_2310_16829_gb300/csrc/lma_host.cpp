@@ -750,6 +750,14 @@ lma_status ensure_atoms_device(lma_specimen* sp, int phi, cudaStream_t st) {
   return LMA_OK;
 }
 
+// x mod l in [0, l)
+double wrap_period(double x, double l) {
+  double w = x - l * std::floor(x / l);
+  if (w >= l) w -= l;
+  if (w < 0.0) w += l;
+  return w;
+}
+
 size_t t_slot_elems(const lma_grid& g) {
   return static_cast<size_t>(g.n_slices) * (g.nx + kW) * (g.ny + kW);
 }
@@ -1407,9 +1415,11 @@ lma_status load_atoms(lma_ctx* ctx, lma_specimen* sp, const lma_atoms* phonons, 
     P.y.resize(order.size());
     P.sp.resize(order.size());
     P.slc.resize(order.size());
+    // positions are kept in [0, l): the potential kernel then finds every minimum image
+    // with one comparison per axis
     for (size_t k = 0; k < order.size(); ++k) {
-      P.x[k] = A.x[order[k]];
-      P.y[k] = A.y[order[k]];
+      P.x[k] = wrap_period(A.x[order[k]], g.lx);
+      P.y[k] = wrap_period(A.y[order[k]], g.ly);
       P.sp[k] = A.species[order[k]];
       P.slc[k] = A.slice[order[k]];
     }

@@ -1129,17 +1129,27 @@ __global__ void __launch_bounds__(256) k_potential(const PotArgs a) {
     bool keep = false;
     AtomRel e{0.f, 0.f, 0.f, 0.f, 0.f};
     if (k < a1) {
+      // positions lie in [0, l) and the tile centre in [0, l + 8 dx): one period at most
+      // brings the offset to its minimum image
       double ddx = a.ax[k] - Xc, ddy = a.ay[k] - Yc;
-      ddx -= a.lx * floor(ddx / a.lx + 0.5);
-      ddy -= a.ly * floor(ddy / a.ly + 0.5);
+      if (ddx >= 0.5 * a.lx)
+        ddx -= a.lx;
+      else if (ddx < -0.5 * a.lx)
+        ddx += a.lx;
+      if (ddy >= 0.5 * a.ly)
+        ddy -= a.ly;
+      else if (ddy < -0.5 * a.ly)
+        ddy += a.ly;
       keep = fabs(ddx) < limx && fabs(ddy) < limy;
-      const double rx = ddx + 7.5 * a.dx, ry = ddy + 7.5 * a.dy;
-      e.x_hi = static_cast<float>(rx);
-      e.x_lo = static_cast<float>(rx - static_cast<double>(e.x_hi));
-      e.y_hi = static_cast<float>(ry);
-      e.y_lo = static_cast<float>(ry - static_cast<double>(e.y_hi));
-      const int spc = a.asp[k];
-      e.peak = (spc >= 0 && spc < a.n_species) ? a.peak[spc] : 0.f;
+      if (keep) {
+        const double rx = ddx + 7.5 * a.dx, ry = ddy + 7.5 * a.dy;
+        e.x_hi = static_cast<float>(rx);
+        e.x_lo = static_cast<float>(rx - static_cast<double>(e.x_hi));
+        e.y_hi = static_cast<float>(ry);
+        e.y_lo = static_cast<float>(ry - static_cast<double>(e.y_hi));
+        const int spc = a.asp[k];
+        e.peak = (spc >= 0 && spc < a.n_species) ? a.peak[spc] : 0.f;
+      }
     }
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
     if (lane == 0) wcount[warp] = __popc(bal);
