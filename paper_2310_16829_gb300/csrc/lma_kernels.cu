@@ -424,7 +424,7 @@ __device__ __forceinline__ void load_twiddles(float2* twA, float2* twB, int T) {
 // ------------------------------------------------------------------------------------------
 // step a3: slice kernel
 // ------------------------------------------------------------------------------------------
-// The slice kernel keeps every exchange in one table of 512 rows x 33 entries (row TA =
+// The slice kernel keeps every exchange in one table of 512 rows x 34 entries (row TA =
 // 4 y + r, entry k), and every thread writes only the entries it has just read:
 //   A thread (y, r):   row TA = T, entries 0..31: its pass-A outputs k1 (X1), later its
 //                      pass-B-inverse inputs (X4)
@@ -437,13 +437,15 @@ __device__ __forceinline__ void load_twiddles(float2* twA, float2* twB, int T) {
 //                      of its 8 window rows y = 8 w .. 8 w + 7 as 8 rows of 132 entries
 // No entry is written by one thread while another thread of the CTA may still read it,
 // so the only CTA barriers are the four that publish a phase's writes (read-after-write);
-// the transmission is shared within a warp only (__syncwarp). The odd row length keeps
-// every 64-bit access of a half-warp on 16 distinct bank pairs: A rows are 16
-// consecutive TA, B and C entries 16 consecutive k of one row.
-constexpr int kXP = 33;
+// the transmission is shared within a warp only (__syncwarp). With rows of 34 entries the
+// A side moves entry pairs (k, k + 1) with 128-bit accesses, a quarter-warp's 8 rows on 8
+// distinct 16-byte slots (17 TA + k/2 mod 8); the 64-bit B and C accesses of a half-warp
+// are 16 consecutive entries of one row (of two rows 128 x 34 entries apart in the warps
+// that mix k2x), on 16 distinct bank pairs.
+constexpr int kXP = 34;
 constexpr int kXRows = 512 * kXP;
 constexpr int kTRow = 132;   // staged transmission row: 4 table rows
-static_assert(8 * kTRow == 32 * kXP, "a warp's 8 transmission rows fill its 32 table rows");
+static_assert(8 * kTRow <= 32 * kXP, "a warp's 8 transmission rows fit its 32 table rows");
 // propagator table P[a * 65 + b] = e_x(a) e_y(b) for |kx| = a, |ky| = b <= 64, zero
 // outside the bandlimit (e_x and e_y depend on k^2 only); the odd row length spreads
 // the 16 consecutive a of a half-warp over distinct bank pairs
@@ -565,8 +567,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
       // forward 2D DFT; X1 goes to this warp's rows once every lane has read its t
       dft32<false>(v);
       __syncwarp();
+      float4* const xa4 = reinterpret_cast<float4*>(xa);
 #pragma unroll
-      for (int k = 0; k < 32; ++k) xa[k] = v[k];
+      for (int k = 0; k < 32; k += 2) xa4[k / 2] = make_float4(v[k].x, v[k].y, v[k + 1].x, v[k + 1].y);
       __syncthreads();
       float2 b0[16], b1[16];
 #pragma unroll
@@ -625,8 +628,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
           xb[(128 * q + r) * kXP + 16] = b1[q * 4 + r];
         }
       __syncthreads();
+      {
+        const float4* const xa4 = reinterpret_cast<const float4*>(xa);
 #pragma unroll
-      for (int k = 0; k < 32; ++k) v[k] = xa[k];
+        for (int k = 0; k < 32; k += 2) {
+          const float4 p = xa4[k / 2];
+          v[k] = make_float2(p.x, p.y);
+          v[k + 1] = make_float2(p.z, p.w);
+        }
+      }
       // the warp's rows are free again once every lane has read them: prefetch the next
       // slice's transmission while the inverse pass A runs
       __syncwarp();
