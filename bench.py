@@ -51,7 +51,7 @@ N_SMS = 152
 # slices) in the ncu capture summarised in profiles/k_slice_abo3_512sq_50sl.md; the bench
 # launch carries all configurations, so the figure is scaled by translate-slices (reads
 # and the exit-wave writes both grow in proportion). None when the kernel changes.
-K_SLICE_TRAFFIC_CAPTURE = (0.496857088e9 + 2.111407e9, 16384 * 50)
+K_SLICE_TRAFFIC_CAPTURE = (0.488835328e9 + 2.112114e9, 16384 * 50)
 
 
 def _peaks():
