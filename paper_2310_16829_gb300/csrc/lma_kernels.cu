@@ -14,21 +14,20 @@
 // 512-thread CTA for all slices (32 values per thread). The 2D DFT is split
 // into three register passes over the 14 index bits (x = 4 n1 + r,
 // y = 32 n1y + n2y, Cooley-Tukey with 128 = 32 * 4 on each axis):
-//   pass A: 32-point DFT over n1 (x axis) + twiddle W_128^(r k1)   thread (y, r)
-//   pass B: 4-point DFTs over r (x axis) and n1y (y axis)
-//           + twiddle W_128^(n2y k1y)                              group (k1, n2y)
+//   pass A: 32-point DFT over n1 (x axis)                          thread (y, r)
+//   pass B: 4-point DFTs over r (x axis, with pass A's twiddle W_128^(r k1),
+//           none for r = 0) and n1y (y axis) + twiddle W_128^(n2y k1y)   group (k1, n2y)
 //   pass C: 32-point DFT over n2y (y axis)                         thread (kx, k1y)
 //           (kx permuted so that one warp of four holds only columns outside
 //           the 2/3 bandlimit and skips the pass)
 // The propagator multiply sits in pass C; the inverse runs the passes back
 // (C, B, A) with conjugate twiddles, so no index permutation is ever stored.
-// Between passes the data crosses threads through padded shared-memory tables
-// (conflict-free 64-bit accesses). The transmission of the next slice is
-// prefetched with cp.async into the 128 KiB region that the exchanges are not
-// using at that time; the B -> A exchange then runs in two halves through a
-// separate 68 KiB region. The transmission is stored with a periodic halo of
-// W pixels ([ny + W][nx + W] per slice), so that every window is a plain
-// rectangle of the array.
+// Between passes the data crosses threads through one shared table in which
+// every thread writes only the entries it has just read (four barriers per
+// slice); each warp stages the transmission rows it multiplies into its own
+// table rows with cp.async while its inverse pass A runs. The transmission is
+// stored with a periodic halo of W pixels ([ny + W][nx + W] per slice), so
+// that every window is a plain rectangle of the array.
 #include "lma_device.h"
 
 #include <cuda_fp16.h>
@@ -72,14 +71,6 @@ __host__ __device__ constexpr int brev5(int k) {
   return ((k & 1) << 4) | ((k & 2) << 2) | (k & 4) | ((k & 8) >> 2) | ((k & 16) >> 4);
 }
 
-// d * W_32^m (forward) or d * W_32^-m (inverse); m is a compile-time constant after unrolling.
-template <bool INV>
-__device__ __forceinline__ float2 tw32(float2 d, int m) {
-  if (m == 0) return d;
-  if (m == 8) return INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
-  const float2 w = c_w128[4 * m];
-  return INV ? cmulc(d, w) : cmul(d, w);
-}
 
 // Column kx of pass-C thread T (k1y = T >> 7). Logical warps 1 and 2 of each k1y group
 // exchange their lanes l < 11, so that logical warp 1 holds kx = 43..74: with the 2/3
@@ -256,16 +247,6 @@ __device__ __forceinline__ void passA_fwd(float2 (&v)[32], const float2* twA) {
     v[k + 1] = cmul(v[k + 1], make_float2(w.z, w.w));
   }
 }
-__device__ __forceinline__ void passA_inv(float2 (&v)[32], const float2* twA) {
-  const float4* w4 = reinterpret_cast<const float4*>(twA);
-#pragma unroll
-  for (int k = 0; k < 32; k += 2) {
-    const float4 w = w4[k / 2];
-    if (k > 0) v[k] = cmulc(v[k], make_float2(w.x, w.y));
-    v[k + 1] = cmulc(v[k + 1], make_float2(w.z, w.w));
-  }
-  dft32<true>(v);
-}
 
 // pass B, group (k1, n2y): a[n1y * 4 + r] -> a[k1y * 4 + k2x]
 // twB points at W_128^(n2y k1y), k1y = 0..3, of this group's n2y
@@ -280,18 +261,6 @@ __device__ __forceinline__ void passB_fwd(float2 (&a)[16], const float2* twB) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) a[k1y * 4 + q] = cmul(a[k1y * 4 + q], w);
   }
-}
-__device__ __forceinline__ void passB_inv(float2 (&a)[16], const float2* twB) {
-#pragma unroll
-  for (int k1y = 1; k1y < 4; ++k1y) {
-    const float2 w = twB[k1y];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) a[k1y * 4 + q] = cmulc(a[k1y * 4 + q], w);
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) dft4<true>(a[0 * 4 + q], a[1 * 4 + q], a[2 * 4 + q], a[3 * 4 + q]);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) dft4<true>(a[q * 4 + 0], a[q * 4 + 1], a[q * 4 + 2], a[q * 4 + 3]);
 }
 
 // pass B of the slice kernel with pass A's twiddles W_128^(r k1) moved into it: r is
