@@ -1,0 +1,95 @@
+"""Edge cases of the GPU path against the FP64 oracle: free space (no atoms), the extreme
+numbers of input waves per probe (L = 1 and the maximum 64), a region of one probe, and a
+non-square grid. Tolerances as in the parity tests: 1e-4 relative per reading, with the
+absolute floor of 1e-4 of the beam for weak readings (complex64 rounding floor), exit waves
+to 5e-5 of their peak."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import lma_oracle as O
+from paper_2310_16829_gb300 import lma, workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return lma.Context(0)
+
+
+def _oracle(w):
+    orc = O.LmaOracle(O.params_from_workload(w))
+    orc.set_specimen(w.phonons, w.potential.peak, w.potential.term_frac, w.potential.term_width,
+                     w.potential.r_cut)
+    return orc
+
+
+def _image(ctx, w, dets, region):
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    got = basis.image(dets, region, recompute=True).reshape(len(dets), -1)
+    ref = _oracle(w).image(dets, O.region_probes(region.px0, region.py0, region.npx, region.npy,
+                                                 region.spacing_px, w.grid.nx, w.grid.ny))
+    return got, ref, basis
+
+
+def _assert_readings(got, ref):
+    err = np.abs(got - ref) / np.maximum(ref, 1e-4)
+    assert err.max() < 1e-4, err.max()
+
+
+def test_free_space_exit_waves_conserve_the_norm_and_match_the_oracle(ctx):
+    """No atoms: t = 1, every exit wave is the input wave propagated through the specimen
+    thickness; the Gaussian input wave lies inside the bandlimit, so its norm is conserved."""
+    w = WL.simple_cubic_workload()
+    w = dataclasses.replace(w, phonons=[WL.Atoms(np.zeros(0), np.zeros(0), np.zeros(0, np.int32),
+                                                 np.zeros(0, np.int16))])
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    basis.propagate(0)
+    orc = _oracle(w)
+    for i in (0, 33, 1023):
+        got = basis.exit_wave(i)
+        ref = orc.exit_wave(0, i)
+        assert np.max(np.abs(got - ref)) < 5e-5 * np.max(np.abs(ref)), i
+    u0 = O.input_wave_window(0, 128, 128, 128, w.grid.dy, w.grid.dx, w.grid.lam, w.probe.alpha_max,
+                             0.0, 0.0, 0.0)
+    n0 = np.sum(np.abs(u0) ** 2)
+    assert abs(np.sum(np.abs(basis.exit_wave(33).astype(np.complex128)) ** 2) / n0 - 1) < 1e-5
+    dets = [WL.Detector(0.0, 0.02), WL.Detector(0.02, 0.06)]
+    region = WL.Region(0, 0, 3, 2, (8, 8))
+    got = basis.image(dets, region, recompute=True).reshape(2, -1)
+    ref = orc.image(dets, O.region_probes(0, 0, 3, 2, (8, 8), 128, 128))
+    _assert_readings(got, ref)
+
+
+@pytest.mark.parametrize("L", [1, 64])
+def test_extreme_numbers_of_input_waves(ctx, L):
+    w = WL.simple_cubic_workload()
+    w.basis.L = L
+    dets = [WL.Detector(0.0, 0.02), WL.Detector(0.02, 0.06)]
+    got, ref, _ = _image(ctx, w, dets, WL.Region(3, 5, 3, 2, (8, 8)))
+    _assert_readings(got, ref)
+
+
+def test_region_of_one_probe(ctx):
+    w = WL.perovskite_workload(cells=5, nx=256, n_slices=6, n_phonons=2, seed_base=2900)
+    dets = [WL.Detector(0.0, 0.025), WL.Detector(0.07, 0.2)]
+    got, ref, _ = _image(ctx, w, dets, WL.Region(255, 130, 1, 1, (4, 4)))
+    _assert_readings(got, ref)
+
+
+def test_non_square_grid(ctx):
+    """256 x 128 pixels over 32 x 16 A: the window covers the whole period along y only."""
+    w = WL.simple_cubic_workload()
+    g = dataclasses.replace(w.grid, nx=256, lx=32.0)
+    at = WL._layered_crystal(4.0, 8, 4, 10, [[(0.0, 0.0, 0)]], 0.0, None)
+    w = dataclasses.replace(w, grid=g, phonons=[at])
+    dets = [WL.Detector(0.0, 0.02), WL.Detector(0.02, 0.06)]
+    got, ref, basis = _image(ctx, w, dets, WL.Region(250, 120, 4, 3, (4, 4)))
+    _assert_readings(got, ref)
+    assert basis.info().nax == 64 and basis.info().nay == 32
