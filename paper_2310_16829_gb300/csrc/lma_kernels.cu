@@ -636,9 +636,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
       if (mx > 0.f) frexpf(mx, &e);
       const float sc = ldexpf(1.f, -e);
       const int oi = a.out_index ? a.out_index[li] : ti;
-      __half2* uh = static_cast<__half2*>(J.Uh) + cfg * J.u_slot + static_cast<size_t>(oi) * (kW * kW) + ya * kW + ra;
+      // the warp's 8 rows go through its own table rows (rows of 132 pairs: the 4-byte
+      // writes of 8 rows x 4 residues fall on 32 distinct banks) and out as 16-byte
+      // stores, 512 contiguous bytes per instruction (the FP16 pairs of one thread are
+      // 16 bytes apart in the wave, so direct stores would write half sectors)
+      __half2* const hs = reinterpret_cast<__half2*>(xw);
 #pragma unroll
-      for (int n1 = 0; n1 < 32; ++n1) uh[4 * n1] = __floats2half2_rn(v[n1].x * sc, v[n1].y * sc);
+      for (int n1 = 0; n1 < 32; ++n1) hs[(ya & 7) * 132 + 4 * n1 + ra] = __floats2half2_rn(v[n1].x * sc, v[n1].y * sc);
+      __syncwarp();
+      uint4* const dst = reinterpret_cast<uint4*>(static_cast<__half2*>(J.Uh) + cfg * J.u_slot +
+                                                  static_cast<size_t>(oi) * (kW * kW) + (8 * (T >> 5)) * kW);
+#pragma unroll
+      for (int yl = 0; yl < 8; ++yl)
+        dst[yl * (kW / 4) + lane] = *reinterpret_cast<const uint4*>(hs + yl * 132 + 4 * lane);
       if (T == 0) J.Uscale[static_cast<size_t>(cfg) * J.n_translates + oi] = ldexpf(1.f, e);
     } else {
       const int oi = a.out_index ? a.out_index[li] : ti;
