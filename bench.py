@@ -399,6 +399,22 @@ def batching_measure(n_phonons: int, steps: int) -> dict:
     return out
 
 
+def replica_workload(rank: int):
+    """Replicas: rank r images its own specimen, the benchmark workload with frozen-phonon
+    seeds 1000 + 97 r + phi (rank 0 is the single-GPU workload)."""
+    return WL.perovskite_workload(seed_base=1000 + 97 * rank)
+
+
+def max_over_ranks(total_ms: float, world: int, dist=None, device: str = "cuda") -> float:
+    """The slowest rank's timed total (every rank gets it); world = 1 returns it unchanged."""
+    if world > 1:
+        import torch
+        t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms
+
+
 def profile_case() -> None:
     """The benchmark workload with one configuration, imaged twice with RECOMPUTE.
 
@@ -506,7 +522,7 @@ def main():
 
     # replicas: every rank simulates its own specimen (independent phonon seeds)
     if rank:
-        w = WL.perovskite_workload(seed_base=1000 + 97 * rank)
+        w = replica_workload(rank)
     ctx = lma.Context(local)
     stream = torch.cuda.current_stream()
     spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
@@ -547,9 +563,7 @@ def main():
     total_ms = sum(step_ms)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, world, dist)
     ms_per_step = total_ms / args.steps
     value = world * w.n_pixels / (ms_per_step / 1e3)
     img = out.cpu().numpy()
