@@ -159,8 +159,7 @@ def oracle_sample(w, n_probes: int, seed: int) -> dict:
         orc.exit_wave(0, i)
     t3 = time.perf_counter()
     masks = orc.detector_masks(w.detectors)
-    for p in probes:
-        orc.pixel(0, p, masks)
+    readings = [orc.pixel(0, p, masks) for p in probes]
     t4 = time.perf_counter()
     t_pot, t_tr, t_probe = t1 - t0, (t3 - t2) / len(needed), (t4 - t3) / len(probes)
     n_tr = orc.lattice.shape[0]
@@ -170,7 +169,33 @@ def oracle_sample(w, n_probes: int, seed: int) -> dict:
                        f"{len(needed)} of {n_tr} translate exit waves, {len(probes)} of "
                        f"{w.n_pixels} probes; full job extrapolated linearly "
                        f"({full:.0f} s); numpy FFT single-threaded"),
-            "sample_seconds": t4 - t0, "coefficient_setup_s": t2 - t1}
+            "sample_seconds": t4 - t0, "coefficient_setup_s": t2 - t1,
+            "probes": probes, "readings": readings}
+
+
+def sample_parity(ctx, w, sample: dict) -> dict:
+    """The oracle's readings of the CPU-baseline sample (configuration 0) against the GPU
+    path's image of the same probes with the same configuration, outside the timed region."""
+    import torch
+    from paper_2310_16829_gb300 import lma
+    w1 = w.with_phonons(1)
+    spec = lma.Specimen(ctx, w1.grid, w1.potential, w1.phonons)
+    basis = lma.Basis(ctx, spec, w1.probe, w1.basis)
+    rel, floor = [], []
+    for (px, py), ref in zip(sample["probes"], sample["readings"]):
+        got = basis.image(w1.detectors, WL.Region(px, py, 1, 1, w1.region.spacing_px), recompute=True)
+        for g, r in zip(got.reshape(-1), ref):
+            rel.append(abs(float(g) - r) / r)
+            floor.append(abs(float(g) - r) / max(r, 1e-4))
+    basis.close()
+    spec.close()
+    torch.cuda.synchronize()
+    return {"probes": len(sample["probes"]), "configurations": 1, "detectors": len(w1.detectors),
+            "readings_of_beam": [float(r) for ref in sample["readings"] for r in ref],
+            "max_rel_err_vs_oracle": max(rel), "max_err_vs_oracle_floored": max(floor), "bound": 1e-4,
+            "criterion": "|GPU - oracle| <= 1e-4 x max(reading, 1e-4 of the beam): readings below "
+                         "2.5e-5 of the beam sit on the complex64 rounding floor",
+            "pass": max(floor) <= 1e-4}
 
 
 def run_reference(args, w) -> None:
@@ -787,10 +812,12 @@ def main():
         batching = batching_measure(args.batch_phonons, steps=2)
 
     cpu = None
+    parity = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_sample(w, 2, seed=5)
-        cpu.pop("sample_seconds", None)
-        cpu.pop("coefficient_setup_s", None)
+        parity = sample_parity(ctx, w, cpu)
+        for k in ("sample_seconds", "coefficient_setup_s", "probes", "readings"):
+            cpu.pop(k, None)
 
     if rank == 0:
         line = {
@@ -808,6 +835,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "parity": parity,
             "e2e": {"value": world * w.n_pixels / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(host_out.nbytes), "matches_device_run": e2e_consistent},
             "gpu_launches": int(sum(v["launches"] for v in prof.values() if isinstance(v, dict))),
