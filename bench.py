@@ -181,21 +181,31 @@ def sample_parity(ctx, w, sample: dict) -> dict:
     w1 = w.with_phonons(1)
     spec = lma.Specimen(ctx, w1.grid, w1.potential, w1.phonons)
     basis = lma.Basis(ctx, spec, w1.probe, w1.basis)
-    rel, floor = [], []
-    for (px, py), ref in zip(sample["probes"], sample["readings"]):
-        got = basis.image(w1.detectors, WL.Region(px, py, 1, 1, w1.region.spacing_px), recompute=True)
-        for g, r in zip(got.reshape(-1), ref):
-            rel.append(abs(float(g) - r) / r)
-            floor.append(abs(float(g) - r) / max(r, 1e-4))
+    bm = lma.Basis(ctx, spec, w1.probe, dataclasses.replace(w1.basis, precision=WL.PREC_MIXED))
+
+    def errors(b):
+        rel, floor = [], []
+        for (px, py), ref in zip(sample["probes"], sample["readings"]):
+            got = b.image(w1.detectors, WL.Region(px, py, 1, 1, w1.region.spacing_px), recompute=True)
+            for g, r in zip(got.reshape(-1), ref):
+                rel.append(abs(float(g) - r) / r)
+                floor.append(abs(float(g) - r) / max(r, 1e-4))
+        return max(rel), max(floor)
+
+    rel, floor = errors(basis)
+    rel_m, floor_m = errors(bm)
+    bm.close()
     basis.close()
     spec.close()
     torch.cuda.synchronize()
     return {"probes": len(sample["probes"]), "configurations": 1, "detectors": len(w1.detectors),
             "readings_of_beam": [float(r) for ref in sample["readings"] for r in ref],
-            "max_rel_err_vs_oracle": max(rel), "max_err_vs_oracle_floored": max(floor), "bound": 1e-4,
+            "max_rel_err_vs_oracle": rel, "max_err_vs_oracle_floored": floor, "bound": 1e-4,
             "criterion": "|GPU - oracle| <= 1e-4 x max(reading, 1e-4 of the beam): readings below "
                          "2.5e-5 of the beam sit on the complex64 rounding floor",
-            "pass": max(floor) <= 1e-4}
+            "pass": floor <= 1e-4,
+            "mixed": {"max_rel_err_vs_oracle": rel_m, "max_err_vs_oracle_floored": floor_m, "bound": 1e-3,
+                      "pass_relative": rel_m <= 1e-3}}
 
 
 def run_reference(args, w) -> None:
