@@ -93,3 +93,21 @@ def test_non_square_grid(ctx):
     got, ref, basis = _image(ctx, w, dets, WL.Region(250, 120, 4, 3, (4, 4)))
     _assert_readings(got, ref)
     assert basis.info().nax == 64 and basis.info().nay == 32
+
+
+def test_odd_window_origins(ctx):
+    """Input lattice offset (1, 3): every window origin is odd along x, so the slice kernel
+    stages the transmission in 8-byte pieces (the other instantiation of its copy)."""
+    w = WL.simple_cubic_workload()
+    w.basis.in_offset_px = (1, 3)
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    basis.propagate(0)
+    orc = _oracle(w)
+    for i in (0, 31, 517, 1023):
+        got = basis.exit_wave(i)
+        ref = orc.exit_wave(0, i)
+        assert np.max(np.abs(got - ref)) < 5e-5 * np.max(np.abs(ref)), i
+    dets = [WL.Detector(0.0, 0.02), WL.Detector(0.02, 0.06)]
+    got, ref, _ = _image(ctx, w, dets, WL.Region(5, 9, 3, 2, (8, 8)))
+    _assert_readings(got, ref)
