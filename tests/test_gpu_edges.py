@@ -111,3 +111,37 @@ def test_odd_window_origins(ctx):
     dets = [WL.Detector(0.0, 0.02), WL.Detector(0.02, 0.06)]
     got, ref, _ = _image(ctx, w, dets, WL.Region(5, 9, 3, 2, (8, 8)))
     _assert_readings(got, ref)
+
+
+def test_fp16_store_readouts_are_consistent():
+    """FP16 exit-wave store with the 3D (rings) and 4D (pattern) readouts: rings summed over an
+    annulus and the pattern summed over it give the 2D reading of the same store (the FP16
+    rounding is the same in all three), and a wide bandlimit (general slice kernel) keeps the
+    bright field within 1e-3 of complex64."""
+    import torch
+    assert torch.cuda.is_available()
+    ctx = lma.Context(0)
+    w = WL.perovskite_workload(cells=5, nx=256, n_slices=8, n_phonons=2, seed_base=2300)
+    w = w.with_region(WL.Region(250, 12, 5, 3, (4, 4)))
+    w.basis.precision = WL.PREC_MIXED
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    rings = basis.image_rings(0.01, 9, w.region, recompute=True)
+    two_d = basis.image([WL.Detector(0.02, 0.06), WL.Detector(0.0, 0.09)], w.region)
+    assert np.max(np.abs(rings[2:6].sum(axis=0) / two_d[0] - 1)) < 1e-5
+    assert np.max(np.abs(rings.sum(axis=0) / two_d[1] - 1)) < 1e-5
+    A = w.basis.det_window // 2 - 1
+    pat = basis.image_4d(A, A, w.region, recompute=True).astype(np.float64)
+    dx = w.grid.lx / w.grid.nx
+    ia = np.arange(-A, A + 1)
+    ang = w.grid.lam * np.hypot(ia[None, :], ia[:, None]) / (w.basis.det_window * dx)
+    sel = (ang >= 0.02) & (ang < 0.06)
+    assert np.max(np.abs(pat[:, :, sel].sum(axis=-1) / two_d[0] - 1)) < 1e-5
+    # general (unpruned) slice kernel with the FP16 store: bandlimit radius 44.8 px
+    wide = dataclasses.replace(w, grid=dataclasses.replace(w.grid, bandlimit_frac=0.7))
+    spec_w = lma.Specimen(ctx, wide.grid, wide.potential, wide.phonons)
+    bf = [WL.Detector(0.0, 0.02)]
+    half = lma.Basis(ctx, spec_w, wide.probe, wide.basis).image(bf, wide.region, recompute=True)
+    full = lma.Basis(ctx, spec_w, wide.probe, dataclasses.replace(wide.basis, precision=WL.PREC_C64)
+                     ).image(bf, wide.region, recompute=True)
+    assert np.max(np.abs(half / full - 1)) < 1e-3
