@@ -695,7 +695,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice_rs(const SliceLaunch a, c
       // transmission (Sec. 3.2): psi <- t_s psi
       __syncthreads();
       const float2* ts = tb + s * slice_elems;
-      for (int p = T; p < kW * kW; p += kThreads) psi[p] = cmul(psi[p], ts[static_cast<size_t>(p >> 7) * pitch + (p & 127)]);
+      {
+        // all 32 loads of this thread's transmission values first (row (T >> 7) + 4 i,
+        // column T & 127), then the products
+        float2 tv[kW * kW / kThreads];
+#pragma unroll
+        for (int i = 0; i < kW * kW / kThreads; ++i)
+          tv[i] = ts[static_cast<size_t>((T >> 7) + 4 * i) * pitch + (T & 127)];
+#pragma unroll
+        for (int i = 0; i < kW * kW / kThreads; ++i) psi[T + kThreads * i] = cmul(psi[T + kThreads * i], tv[i]);
+      }
       __syncthreads();
       // propagation: periodic convolution with q
       float2 acc[8][4];
@@ -703,23 +712,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice_rs(const SliceLaunch a, c
       for (int j = 0; j < 8; ++j)
 #pragma unroll
         for (int m = 0; m < 4; ++m) acc[j][m] = make_float2(0.f, 0.f);
+      // input rows in the outer loop: row 8 wy + u feeds output rows j with dyi = j - u + h
+      // in [0, K2), so each input segment is read once for all of them (8 + K2 - 1 rows
+      // instead of 8 K2)
+      const int h = K2 / 2;
 #pragma unroll
       for (int mb = 0; mb < 4; mb += MB) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int y = 8 * wy + j;
 #pragma unroll 1
-          for (int dyi = 0; dyi < K2; ++dyi) {
-            const float2* row = psi + ((y - (dyi - K2 / 2)) & (kW - 1)) * kW;
-            float2 seg[MB][K1];
+        for (int u = h - (K2 - 1); u <= 7 + h; ++u) {
+          const float2* row = psi + ((8 * wy + u) & (kW - 1)) * kW;
+          float2 seg[MB][K1];
 #pragma unroll
-            for (int mm = 0; mm < MB; ++mm)
+          for (int mm = 0; mm < MB; ++mm)
 #pragma unroll
-              for (int dxi = 0; dxi < K1; ++dxi)
-                seg[mm][dxi] = row[(lane + 32 * (mb + mm) - (dxi - K1 / 2)) & (kW - 1)];
+            for (int dxi = 0; dxi < K1; ++dxi)
+              seg[mm][dxi] = row[(lane + 32 * (mb + mm) - (dxi - K1 / 2)) & (kW - 1)];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int dyi = j - u + h;
+            if (dyi < 0 || dyi >= K2) continue;
+            const float2* qr = q + dyi * K1;
 #pragma unroll
             for (int dxi = 0; dxi < K1; ++dxi) {
-              const float2 qv = q[dyi * K1 + dxi];
+              const float2 qv = qr[dxi];
 #pragma unroll
               for (int mm = 0; mm < MB; ++mm) acc[j][mb + mm] = cfma(acc[j][mb + mm], qv, seg[mm][dxi]);
             }
