@@ -434,6 +434,22 @@ def batching_measure(n_phonons: int, steps: int) -> dict:
     return out
 
 
+def profile_case_realspace(K: int) -> None:
+    """The benchmark workload with one configuration, imaged twice with the K x K real-space
+    propagation step (for ncu captures of k_slice_rs)."""
+    import torch
+    from paper_2310_16829_gb300 import lma
+    w = WL.perovskite_workload(n_phonons=1)
+    ctx = lma.Context(0)
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    out = torch.empty((1, w.region.npy, w.region.npx), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        basis.image_realspace(K, K, w.detectors, w.region, out=out, stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case_realspace": w.name, "K": K, "mean_haadf": float(out.mean())}))
+
+
 def replica_workload(rank: int):
     """Replicas: rank r images its own specimen, the benchmark workload with frozen-phonon
     seeds 1000 + 97 r + phi (rank 0 is the single-GPU workload)."""
@@ -523,6 +539,8 @@ def main():
                     help="configurations per specimen of the uneven three-specimen batch (0: skip)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one configuration of the workload, two image passes (for ncu captures)")
+    ap.add_argument("--profile-case-realspace", type=int, default=0, metavar="K",
+                    help="one configuration imaged twice with the K x K real-space step (for ncu)")
     ap.add_argument("--approx-curves", action="store_true",
                     help="probe approximation error against L and f per input-wave kind (host only)")
     args = ap.parse_args()
@@ -534,6 +552,9 @@ def main():
         return
     if args.approx_curves:
         approx_curves()
+        return
+    if args.profile_case_realspace:
+        profile_case_realspace(args.profile_case_realspace)
         return
     if args.impl == "reference":
         run_reference(args, w)
