@@ -474,6 +474,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
   bool c_live = false;
   int cur_job = -1;
   __shared__ int s_next;
+  __shared__ int s_wmax;      // FP16 store: bits of the wave's largest |component| (order-preserving for >= 0)
   float2* const xa = X + T * kXP;                                 // A row, + n or k1
   float2* const xb = X + (4 * n2y) * kXP + k1lo;                  // B slot (q, r): + (128 q + r) * kXP, + 16 (h = 1)
   float2* const xc = X + (128 * k2x + k1y) * kXP + k1x;           // C entry j: + 4 j * kXP
@@ -493,6 +494,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
       li = blockIdx.x + it * gridDim.x;
     }
     if (li >= a.n_list) break;
+    if (HALF && T == 0) s_wmax = 0;   // the previous item's reads ended at its last barrier
     int jb = 0;
     while (jb + 1 < a.n_jobs && li >= a.start[jb + 1]) ++jb;
     const SliceJob& J = a.job[jb];
@@ -616,22 +618,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
     if constexpr (HALF) {
       // power-of-two scale bringing the largest component into [0.5, 1): the scaling
       // is exact, the FP16 rounding (2^-11 of that component) is the only error
-      __shared__ float wmax[kThreads / 32 + 1];
       float m = 0.f;
 #pragma unroll
       for (int n1 = 0; n1 < 32; ++n1) m = fmaxf(m, fmaxf(fabsf(v[n1].x), fabsf(v[n1].y)));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if ((T & 31) == 0) wmax[T >> 5] = m;
+      if ((T & 31) == 0) atomicMax(&s_wmax, __float_as_int(m));
       __syncthreads();
-      if (T < 32) {
-        float x = T < kThreads / 32 ? wmax[T] : 0.f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
-        if (T == 0) wmax[kThreads / 32] = x;
-      }
-      __syncthreads();
-      const float mx = wmax[kThreads / 32];
+      const float mx = __int_as_float(s_wmax);
       int e = 0;
       if (mx > 0.f) frexpf(mx, &e);
       const float sc = ldexpf(1.f, -e);
@@ -656,7 +650,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
 #pragma unroll
       for (int n1 = 0; n1 < 32; ++n1) ud[4 * n1] = v[n1];
     }
-    __syncthreads();  // the table, wmax and s_next are rewritten by the next item
+    __syncthreads();  // the table, s_wmax and s_next are rewritten by the next item
   }
 }
 
