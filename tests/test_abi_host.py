@@ -269,3 +269,15 @@ def test_least_squares_error_never_rises_with_L():
             prev = e
             b.close()
             spec.close()
+
+
+def test_header_is_plain_c():
+    """include/lma.h is a C ABI: it compiles as strict C99 (gcc) with no C++ constructs."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    r = subprocess.run([gcc, "-std=c99", "-fsyntax-only", "-Wall", "-Wextra", "-pedantic", "-Werror", "-x", "c",
+                        os.path.join(ROOT, "include", "lma.h")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
