@@ -802,3 +802,45 @@ def test_trig_closed_coefficients_of_a_probe_on_a_periodic_window():
     assert cs.err_sup < 1e-12 and cs.err_l2 < 1e-12
     d = np.hypot(offsets[:, 0], offsets[:, 1])
     assert np.abs(cs.alpha[d == 0]).max() > 4 * np.abs(cs.alpha[d >= 3 * s]).max()
+
+
+# ---- helpers: detector masks, coefficient classes, window crops ----
+
+def test_detector_masks_are_annuli_of_the_right_size():
+    """r1 <= lambda |k| < r2 on the D x D window: 4-fold symmetric, empty outside the bandlimit,
+    and an annulus inside the band holds pi (k2^2 - k1^2) Fourier pixels up to its rim
+    (k = r / (lambda q), q = 1 / (D dx)); a mistaken angle scale (k instead of lambda k, a lost
+    factor 2 pi, pixels in place of Angstrom) moves the count far outside that bound."""
+    D, dx, lam = 128, 0.125, 0.02508
+    q = 1.0 / (D * dx)
+    for r1, r2 in ((0.0, 0.02), (0.02, 0.05), (0.03, 0.066)):
+        m = O.detector_mask(D, dx, dx, lam, r1, r2, 2 / 3)
+        assert np.array_equal(m, m.T) and np.array_equal(m, np.roll(m[::-1, :], 1, axis=0))
+        k1, k2 = r1 / (lam * q), r2 / (lam * q)
+        area = np.pi * (k2 ** 2 - k1 ** 2)
+        assert abs(m.sum() - area) <= 2 * np.pi * (k1 + k2) + 4, (r1, r2, m.sum(), area)
+    outside = O.detector_mask(D, dx, dx, lam, 0.0, 1.0, 2 / 3) ^ O.detector_mask(D, dx, dx, lam, 0.0, 1.0, None)
+    assert not np.any(outside & O.bandlimit_mask(D, D, 2 / 3))
+
+
+def test_coefficient_classes_follow_case_1_and_case_2():
+    """Sec. 4.2.1: probes on the input lattice's period share one coefficient set (Case 1,
+    R = cP); probes every p = r / c pixels fall into c x d classes (Case 2)."""
+    probes1 = [(x, y) for x in range(0, 64, 4) for y in range(0, 64, 4)]
+    assert len({O.class_key(p, (4, 4), (2, 2), 1) for p in probes1}) == 1
+    probes2 = [(x, y) for x in range(0, 64, 2) for y in range(0, 64, 1)]
+    assert len({O.class_key(p, (4, 4), (2, 2), 1) for p in probes2}) == 2 * 4
+    # f = 2 keeps every other input wave: the period doubles
+    assert len({O.class_key(p, (4, 4), (2, 2), 2) for p in probes1}) == 4
+
+
+def test_periodic_crop_and_embed_window_invert_each_other():
+    rng = np.random.default_rng(43)
+    a = rng.standard_normal((16, 24)) + 1j * rng.standard_normal((16, 24))
+    win = O.periodic_crop(a, -3, 20, 8, 8)                 # wraps on both axes
+    full = O.embed_window(win, -3, 20, 16, 24)
+    iy = np.mod(-3 + np.arange(8), 16)
+    ix = np.mod(20 + np.arange(8), 24)
+    keep = np.zeros((16, 24), bool)
+    keep[iy[:, None], ix[None, :]] = True
+    assert np.array_equal(full[keep], a[keep]) and not np.any(full[~keep])
