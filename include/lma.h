@@ -311,7 +311,8 @@ lma_status lma_image_realspace(lma_ctx* ctx, lma_specimen* spec, lma_basis* basi
 /* Partially coherent 2D STEM image: the simulation repeated over probe variants and
  * averaged (Sec. 1), computed from one set of exit waves. The input waves, and so the
  * exit waves, do not depend on the probe: each variant's coefficients are fitted to its
- * own probe (least squares on the basis's input waves, as in Sec. 4.2.2), its image is
+ * own probe (least squares on the basis's input waves, as in Sec. 4.2.2, or the closed
+ * form of LMA_COEF_TRIG_CLOSED when the basis uses it), its image is
  * synthesized and read out from the shared exit waves, and the images are averaged with
  * weights w_v / sum w. Variants may differ in defocus and C_s; alpha_max must equal the
  * basis probe's. out[n_det][npy][npx] (double, host or device); flags as for lma_image.
@@ -324,8 +325,8 @@ lma_status lma_image_coherent(lma_ctx* ctx, lma_specimen* spec, lma_basis* basis
 
 /* The smallest L in 1..L_max whose probe approximation error in the supremum norm,
  * relative to the probe's maximum, is at most eps_sup for every coefficient class of the
- * region (Sec. 4.2.6 fixes L by such a target). desc gives the input waves and lattice
- * (its L is ignored). *L_out = 0 when no L reaches the target; *err_out = the error at
+ * region (Sec. 4.2.6 fixes L by such a target). desc gives the input waves, the lattice
+ * and the coefficient mode (its L is ignored). *L_out = 0 when no L reaches the target; *err_out = the error at
  * the returned L (or at L_max). Host-only work. Errors: LMA_ERR_INVALID (L_max outside
  * 1..64 or above |I_f|, eps_sup <= 0, bad region or basis description). */
 lma_status lma_select_L(lma_ctx* ctx, const lma_specimen* spec, const lma_probe* probe,
