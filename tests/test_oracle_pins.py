@@ -844,3 +844,26 @@ def test_periodic_crop_and_embed_window_invert_each_other():
     keep = np.zeros((16, 24), bool)
     keep[iy[:, None], ix[None, :]] = True
     assert np.array_equal(full[keep], a[keep]) and not np.any(full[~keep])
+
+
+def test_l_nearest_sets_reproduce_the_paper_partition_counts():
+    """Sec. 4.2.4 prints the minimum number of Multislice runs T_P = |union of I_{f,p,L}| of a
+    48 x 48 sub-image: 1077 for L = 75 and 953 for L = 51 (u = probe, I = P + p/2, f = 2,
+    512 pixels, 158 probes per axis). With probes and input waves on whole pixels (floor of
+    their positions), I_f keeping the even input waves and the sub-image at probes 1..48,
+    the oracle's L-nearest rule gives both numbers."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+    gv = g["partition_minimum_runs"]
+    X, P = 512, 158
+    axis = np.array([int(np.floor((k + 0.5) * X / P)) for k in range(0, P, 2)])
+    lattice = np.stack(np.meshgrid(axis, axis, indexing="xy"), axis=-1).reshape(-1, 2)
+    probes = [int(np.floor(i * X / P)) for i in range(1, 49)]
+    for L, key in ((75, "L75"), (51, "L51")):
+        union = set()
+        for py in probes:
+            for px in probes:
+                idx, _ = O.nearest_translates((px, py), lattice, L, X, X)
+                union.update(int(i) for i in idx)
+        assert len(union) == gv[key], (L, len(union))
