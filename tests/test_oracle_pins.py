@@ -867,3 +867,24 @@ def test_l_nearest_sets_reproduce_the_paper_partition_counts():
                 idx, _ = O.nearest_translates((px, py), lattice, L, X, X)
                 union.update(int(i) for i in idx)
         assert len(union) == gv[key], (L, len(union))
+
+
+def test_row_by_row_partition_of_the_paper_at_L51():
+    """Sec. 4.2.4's partition figure, bottom row (L = 51): row by row gives l = 12 parts and
+    T = 953, the union itself, so no translate is recomputed. The caption gives no M; in the
+    whole-pixel geometry of the partition-count pin, M = 280 reproduces the printed pair. A
+    cost that drops the overlap term gives 3350; a part that overruns M fails the bound check."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+    gv = g["partition_row_by_row_L51"]
+    X, P = 512, 158
+    axis = np.array([int(np.floor((k + 0.5) * X / P)) for k in range(0, P, 2)])
+    lattice = np.stack(np.meshgrid(axis, axis, indexing="xy"), axis=-1).reshape(-1, 2)
+    probes = [int(np.floor(i * X / P)) for i in range(1, 49)]
+    sets = [frozenset(int(i) for i in O.nearest_translates((px, py), lattice, 51, X, X)[0])
+            for py in probes for px in probes]
+    parts = O.partition_rows(sets, 48, 48, 280)
+    assert len(parts) == gv["parts"]
+    assert all(len(frozenset().union(*[sets[q] for q in part])) <= 280 for part in parts)
+    assert O.partition_cost(sets, parts) == gv["T"]
