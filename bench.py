@@ -765,7 +765,7 @@ def main():
 
         ms_f, sl_f = timed_image(lambda: b1.image(dets, region, out=out1, recompute=True, stream=stream))
         ref = out1.cpu().numpy()
-        for K in (3, 5, 7, 9, 13):
+        for K in (3, 5, 7, 9, 13, 25):
             ms_r, sl_r = timed_image(lambda: b1.image_realspace(K, K, dets, region, out=out1, stream=stream))
             img_r = out1.cpu().numpy()
             rows.append({"K": K, "ms_per_image": ms_r, "slice_ms": sl_r, "slice_vs_fourier": sl_r / sl_f,

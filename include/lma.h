@@ -298,7 +298,7 @@ lma_status lma_image_4d(lma_ctx* ctx, lma_specimen* spec, lma_basis* basis, int3
  * window propagator exp(-i pi lambda eps |k|^2) times the bandlimit (FP64, rounded once to
  * complex64) at offsets -(K/2) .. K/2; with K1 = K2 = W it would reproduce the Fourier step.
  * Always recomputes; afterwards the basis's stored exit waves are marked stale for
- * lma_image. out as for lma_image. Errors: LMA_ERR_INVALID (K1 not odd in 3..13, K2 not odd
+ * lma_image. out as for lma_image. Errors: LMA_ERR_INVALID (K1 not odd in 3..25, K2 not odd
  * in 1..25, bad detectors or region), LMA_ERR_UNSUPPORTED (mixed store). */
 lma_status lma_image_realspace(lma_ctx* ctx, lma_specimen* spec, lma_basis* basis, int32_t K1, int32_t K2,
                                const lma_detector* det, int32_t n_det, const lma_region* region,

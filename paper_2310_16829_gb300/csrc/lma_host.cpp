@@ -2125,7 +2125,7 @@ lma_status lma_image_realspace(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, int
                                double* out, void* stream) {
   if (!ctx || !sp || !b || !out || !region) return fail(ctx, LMA_ERR_INVALID, "null argument");
   if (b->spec != sp) return fail(ctx, LMA_ERR_INVALID, "basis belongs to another specimen");
-  if (K1 < 3 || K1 > 13 || (K1 & 1) == 0) return fail(ctx, LMA_ERR_INVALID, "K1 must be odd in 3..13");
+  if (K1 < 3 || K1 > 25 || (K1 & 1) == 0) return fail(ctx, LMA_ERR_INVALID, "K1 must be odd in 3..25");
   if (K2 < 1 || K2 > 25 || (K2 & 1) == 0) return fail(ctx, LMA_ERR_INVALID, "K2 must be odd in 1..25");
   if (b->desc.precision != LMA_PREC_C64)
     return fail(ctx, LMA_ERR_UNSUPPORTED, "real-space propagation writes the complex64 store only");

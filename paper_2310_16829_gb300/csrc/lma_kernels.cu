@@ -659,7 +659,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
 // kernel q (Sec. 3.2, complexity paragraph). One CTA per translate, the wave in shared
 // memory; thread (lane, warp) accumulates the 32 outputs x = lane + 32 m (m < 4), y =
 // 8 warp + j (j < 8) in registers: out(x, y) = sum over offsets (oy, ox) of q(oy, ox) psi(y -
-// oy, x - ox), periodic on the window. MB columns share one register segment of K1 inputs.
+// oy, x - ox), periodic on the window. MB columns share one register segment of K1 inputs
+// (up to 13 at a time: K1 from 15 to 25 takes the segment in two pieces).
 // ------------------------------------------------------------------------------------------
 template <int K1, int MB>
 __global__ void __launch_bounds__(kThreads, 1) k_slice_rs(const SliceLaunch a, const float2* qg, const int K2) {
@@ -709,28 +710,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice_rs(const SliceLaunch a, c
       // input rows in the outer loop: row 8 wy + u feeds output rows j with dyi = j - u + h
       // in [0, K2), so each input segment is read once for all of them (8 + K2 - 1 rows
       // instead of 8 K2)
+      // kernels wider than 13 columns take their row segment in pieces of at most 13 (the
+      // register footprint of the 13-column kernel); narrower ones in one piece
       const int h = K2 / 2;
+      constexpr int KC = K1 < 13 ? K1 : 13;
 #pragma unroll
       for (int mb = 0; mb < 4; mb += MB) {
 #pragma unroll 1
         for (int u = h - (K2 - 1); u <= 7 + h; ++u) {
           const float2* row = psi + ((8 * wy + u) & (kW - 1)) * kW;
-          float2 seg[MB][K1];
 #pragma unroll
-          for (int mm = 0; mm < MB; ++mm)
+          for (int c0 = 0; c0 < K1; c0 += KC) {
+            float2 seg[MB][KC];
 #pragma unroll
-            for (int dxi = 0; dxi < K1; ++dxi)
-              seg[mm][dxi] = row[(lane + 32 * (mb + mm) - (dxi - K1 / 2)) & (kW - 1)];
+            for (int mm = 0; mm < MB; ++mm)
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int dyi = j - u + h;
-            if (dyi < 0 || dyi >= K2) continue;
-            const float2* qr = q + dyi * K1;
+              for (int d = 0; d < KC; ++d)
+                if (c0 + d < K1) seg[mm][d] = row[(lane + 32 * (mb + mm) - (c0 + d - K1 / 2)) & (kW - 1)];
 #pragma unroll
-            for (int dxi = 0; dxi < K1; ++dxi) {
-              const float2 qv = qr[dxi];
+            for (int j = 0; j < 8; ++j) {
+              const int dyi = j - u + h;
+              if (dyi < 0 || dyi >= K2) continue;
+              const float2* qr = q + dyi * K1 + c0;
 #pragma unroll
-              for (int mm = 0; mm < MB; ++mm) acc[j][mb + mm] = cfma(acc[j][mb + mm], qv, seg[mm][dxi]);
+              for (int d = 0; d < KC; ++d) {
+                if (c0 + d >= K1) continue;
+                const float2 qv = qr[d];
+#pragma unroll
+                for (int mm = 0; mm < MB; ++mm) acc[j][mb + mm] = cfma(acc[j][mb + mm], qv, seg[mm][d]);
+              }
             }
           }
         }
@@ -1294,7 +1302,8 @@ cudaError_t init_device_constants() {
   }
   const int sr = static_cast<int>(slice_rs_smem_bytes());
   for (auto f : {k_slice_rs<3, 4>, k_slice_rs<5, 4>, k_slice_rs<7, 4>, k_slice_rs<9, 2>, k_slice_rs<11, 2>,
-                 k_slice_rs<13, 2>})
+                 k_slice_rs<13, 2>, k_slice_rs<15, 2>, k_slice_rs<17, 2>, k_slice_rs<19, 2>, k_slice_rs<21, 2>,
+                 k_slice_rs<23, 2>, k_slice_rs<25, 2>})
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sr)) != cudaSuccess) return e;
   for (auto f : {k_synth_detect<false, kReadAnnuli, false>, k_synth_detect<true, kReadAnnuli, false>,
                  k_synth_detect<false, kReadLabels, false>, k_synth_detect<true, kReadLabels, false>,
@@ -1361,6 +1370,12 @@ cudaError_t launch_slice_rs(const SliceLaunch& a, const float2* q, int K1, int K
     case 9: k_slice_rs<9, 2><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
     case 11: k_slice_rs<11, 2><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
     case 13: k_slice_rs<13, 2><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
+    case 15: k_slice_rs<15, 2><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
+    case 17: k_slice_rs<17, 2><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
+    case 19: k_slice_rs<19, 2><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
+    case 21: k_slice_rs<21, 2><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
+    case 23: k_slice_rs<23, 2><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
+    case 25: k_slice_rs<25, 2><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

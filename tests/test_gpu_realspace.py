@@ -40,14 +40,17 @@ def _oracle(w, K):
     return orc
 
 
-@pytest.mark.parametrize("case", ["simple_cubic", "perovskite"])
+@pytest.mark.parametrize("case", ["simple_cubic", "perovskite", "wide_15x3", "wide_25x11"])
 def test_realspace_image_matches_oracle(ctx, case):
+    """K1 != K2 in the perovskite cases, so a transposed kernel fails; kernels wider than 13
+    columns take their row segment in two pieces (13 + 2 and 13 + 12 columns)."""
     if case == "simple_cubic":
         w = WL.simple_cubic_workload()
         region, K = WL.Region(0, 0, 3, 2, (8, 8)), (7, 7)
     else:
         w = WL.perovskite_workload(cells=5, nx=256, n_slices=5, n_phonons=2, seed_base=2700)
-        region, K = WL.Region(250, 60, 4, 3, (4, 4)), (5, 9)      # K1 != K2: a transposed kernel fails
+        region, K = WL.Region(250, 60, 4, 3, (4, 4)), {"perovskite": (5, 9), "wide_15x3": (15, 3),
+                                                       "wide_25x11": (25, 11)}[case]
     dets = [WL.Detector(0.0, 0.02), WL.Detector(0.06, 0.2)]
     spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
     basis = lma.Basis(ctx, spec, w.probe, w.basis)
@@ -68,7 +71,7 @@ def test_realspace_arguments(ctx):
     spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
     basis = lma.Basis(ctx, spec, w.probe, w.basis)
     region = WL.Region(0, 0, 2, 2, (8, 8))
-    for K1, K2 in ((4, 5), (15, 5), (1, 5), (5, 27), (5, 4)):
+    for K1, K2 in ((4, 5), (27, 5), (1, 5), (5, 27), (5, 4)):
         with pytest.raises(lma.LmaError) as e:
             basis.image_realspace(K1, K2, w.detectors, region)
         assert e.value.status == lma.LMA_ERR_INVALID
