@@ -787,7 +787,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
 
   const int T = threadIdx.x;
   load_twiddles(twA, twB, T);
-  const int ya = T >> 2, ra = T & 3;
+  const int ra = T & 3;
   const int k1lo = T & 15, n2y = T >> 4;
   const int kx = c_column(T), k1y = T >> 7, k1x = kx & 31, k2x = kx >> 5;
   const float2* tA = twA + ra * 34;

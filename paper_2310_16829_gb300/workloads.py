@@ -19,7 +19,7 @@ positions, 100-slice thickness, frozen-phonon averaging.
 """
 from __future__ import annotations
 
-from dataclasses import dataclass, field, replace
+from dataclasses import dataclass, replace
 from typing import List, Tuple
 
 import numpy as np
