@@ -842,6 +842,33 @@ def probe_translate_sets(prm: "LmaParams", probes: np.ndarray) -> List[frozenset
             for q in probes]
 
 
+def multislice_ops(n_slices: int, X: int, Y: int, K: Tuple[int, int] | None = None) -> float:
+    """Operation count of one multislice run on an X x Y domain (Sec. 3.2): N (2XY + 2XY log XY)
+    with the propagation step in Fourier space, N (XY + XY K1 K2) with the K1 x K2 real-space
+    kernel. log is base 2 (the 2048^2 crossover example of Sec. 4.2.1 holds only in that base)."""
+    xy = float(X) * float(Y)
+    if K is None:
+        return n_slices * (2.0 * xy + 2.0 * xy * math.log2(xy))
+    return n_slices * (xy + xy * K[0] * K[1])
+
+
+def lma_ops(n_I: int, f: int, n_slices: int, X: int, Y: int, n_P: int, L: int, Xp: int, Yp: int,
+            K: Tuple[int, int] | None = None) -> float:
+    """T_LMA of Sec. 4.2.1, coefficient precomputation excluded: |I_f| = |I| / f^2 multislice
+    runs plus |P| L X'Y' for the linear combinations. As the two formulas are printed, the
+    Fourier variant runs multislice on the X x Y domain and the real-space variant (K given)
+    on the X' x Y' domain."""
+    runs = n_I / f ** 2
+    per_run = multislice_ops(n_slices, X, Y) if K is None else multislice_ops(n_slices, Xp, Yp, K)
+    return runs * per_run + float(n_P) * L * Xp * Yp
+
+
+def realspace_crossover_f(X: int, Y: int, K1: int, K2: int) -> float:
+    """The f from which real-space propagation on X/f x Y/f windows costs no more than Fourier
+    propagation on the X x Y domain (Sec. 4.2.1): sqrt((1 + K1 K2) / (2 (1 + log XY)))."""
+    return math.sqrt(0.5 * (1.0 + K1 * K2) / (1.0 + math.log2(float(X) * float(Y))))
+
+
 def partition_cost(sets: Sequence[frozenset], parts: Sequence[Sequence[int]]) -> int:
     """T_{P_1..P_l} of Sec. 4.2.4: Multislice runs when the parts are computed in order and
     only the solutions shared by consecutive parts are kept."""

@@ -887,3 +887,26 @@ def test_row_by_row_partition_of_the_paper_at_L51():
     assert len(parts) == gv["parts"]
     assert all(len(frozenset().union(*[sets[q] for q in part])) <= 280 for part in parts)
     assert O.partition_cost(sets, parts) == gv["T"]
+
+
+def test_cost_model_reproduces_the_realspace_crossover_of_the_paper():
+    """Sec. 4.2.1: on a 2048^2 domain with a 25 x 25 kernel, real-space propagation on X/f
+    windows costs no more than Fourier propagation iff f >= 4. The two image costs are
+    compared for every f from 1 to 8, and the closed-form crossover falls in (3, 4]. Natural
+    logarithms would move the boundary to f = 5, a dropped factor 1/2 to f = 6, and Fourier
+    runs costed on the X' x Y' windows would make real space never cheaper."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+    gv = g["realspace_crossover"]
+    X, Y, K = gv["X"], gv["Y"], (gv["K1"], gv["K2"])
+    n_I, N, n_P, L = 4096, 100, 16384, 32
+    cheaper = [f for f in range(1, 9)
+               if O.lma_ops(n_I, f, N, X, Y, n_P, L, X // f, Y // f, K=K)
+               <= O.lma_ops(n_I, f, N, X, Y, n_P, L, X // f, Y // f)]
+    assert cheaper == list(range(gv["f_min"], 9))
+    c = O.realspace_crossover_f(X, Y, *K)
+    assert gv["f_min"] - 1 < c <= gv["f_min"]
+    # at f = 1 on the full domain the first summands stand in the per-run ratio of Sec. 3.2
+    r = O.multislice_ops(1, X, Y, K) / O.multislice_ops(1, X, Y)
+    assert abs(r - (1 + 625) / (2 + 2 * 22)) < 1e-12
