@@ -10,6 +10,7 @@ import math
 import os
 
 import numpy as np
+import pytest
 
 from oracle import lma_oracle as O
 
@@ -910,3 +911,27 @@ def test_cost_model_reproduces_the_realspace_crossover_of_the_paper():
     # at f = 1 on the full domain the first summands stand in the per-run ratio of Sec. 3.2
     r = O.multislice_ops(1, X, Y, K) / O.multislice_ops(1, X, Y)
     assert abs(r - (1 + 625) / (2 + 2 * 22)) < 1e-12
+
+
+@pytest.mark.parametrize("L", [8, 16, 48])
+def test_image_error_is_bounded_by_the_probe_approximation_error(L):
+    """Sec. 4.2.3 observes image errors below the probe approximation error. With W = D = X it
+    is a theorem: transmission (|t| = 1) and the bandlimited propagator (|P| <= 1) never raise
+    the L2 norm, so multislice maps the probe residual psi_p - sum alpha u to an exit-wave
+    residual no larger; a reading is the squared norm of a projection of the spectrum (1/D^2
+    Parseval), so |sqrt(I_LMA) - sqrt(I_std)| <= err_l2 for a unit-norm probe, per probe and
+    detector. Probe input waves on a 2-pixel lattice give errors of 0 to 6 %, and the bound
+    is nearly attained (up to 0.97 of it), so a misplaced translate or a wrongly normalised
+    residual or reading breaks it."""
+    prm = _small_params(kind=1, L=L, n_slices=3, in_spacing=(2, 2), in_offset=(1, 1))
+    at = _tiny_specimen(prm, seed=21)
+    orc = O.LmaOracle(prm)
+    orc.set_specimen([at], (300.0, 150.0), (0.7, 0.3), (0.15, 0.5), 3.0)
+    probes = O.region_probes(3, 1, 4, 4, (5, 7), 64, 64)
+    dets = [_Det(0.0, 0.02), _Det(0.02, 0.05), _Det(0.0, 1.0)]
+    img = orc.image(dets, probes)
+    std = O.standard_image(prm, orc.transmission_stack(0), dets, probes)
+    errs = np.array([orc.coefficient_set(tuple(int(v) for v in p))[0].err_l2 for p in probes])
+    assert 1e-3 < errs.max() < 0.1
+    gap = np.abs(np.sqrt(img) - np.sqrt(std))
+    assert np.all(gap <= errs[None, :] * (1 + 1e-12) + 1e-14), (gap / errs[None, :]).max()
