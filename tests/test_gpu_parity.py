@@ -151,6 +151,26 @@ def test_image_probe_input_waves(ctx):
     _assert_image(img.reshape(1, -1), ref)
 
 
+def test_standard_special_case_equals_brute_force_multislice(ctx):
+    """Sec. 4.2.3: u = probe, I = P, f = 1, L = 1 retrieves the standard algorithm. With
+    W = D = X on the 128^2 crystal, the GPU image of that configuration is compared with the
+    oracle's brute-force multislice of every probe on the full grid (not with its LMA)."""
+    w = WL.simple_cubic_workload()
+    w.basis.kind = WL.BASIS_PROBE
+    w.basis.L = 1
+    w.basis.in_spacing_px = (8, 8)
+    w.basis.in_offset_px = (0, 0)
+    region = WL.Region(0, 0, 16, 16, (8, 8))
+    dets = [WL.Detector(0.0, 0.03), WL.Detector(0.06, 0.2)]
+    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+    basis = lma.Basis(ctx, spec, w.probe, w.basis)
+    got = basis.image(dets, region).reshape(2, -1)
+    orc = _oracle(w)
+    ref = O.standard_image(O.params_from_workload(w), orc.transmission_stack(0), dets,
+                           _probes(region, 128, 128))
+    _assert_image(got, ref)
+
+
 def test_image_device_output_matches_host_output(ctx):
     import torch
     w = WL.simple_cubic_workload()
