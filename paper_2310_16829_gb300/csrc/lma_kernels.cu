@@ -662,8 +662,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
 // oy, x - ox), periodic on the window. MB columns share one register segment of K1 inputs
 // (up to 13 at a time: K1 from 15 to 25 takes the segment in two pieces).
 // ------------------------------------------------------------------------------------------
-template <int K1, int MB>
-__global__ void __launch_bounds__(kThreads, 1) k_slice_rs(const SliceLaunch a, const float2* qg, const int K2) {
+// One input row u of the convolution for the kernels with K2 fixed at compile time: its
+// segment of K1 inputs per output column (in pieces of KC), applied to every output row j
+// it feeds (kernel row dyi = j - u + h). The runtime-K2 kernels keep the same steps written
+// inline in their input-row loop (measured 2 % faster there at K = 13 and 25).
+template <int K1, int MB, int KC>
+__device__ __forceinline__ void rs_row_step(float2 (&acc)[8][4], const float2* psi, const float2* q, int wy,
+                                            int lane, int mb, int u, int h, int K2) {
+  const float2* row = psi + ((8 * wy + u) & (kW - 1)) * kW;
+#pragma unroll
+  for (int c0 = 0; c0 < K1; c0 += KC) {
+    float2 seg[MB][KC];
+#pragma unroll
+    for (int mm = 0; mm < MB; ++mm)
+#pragma unroll
+      for (int d = 0; d < KC; ++d)
+        if (c0 + d < K1) seg[mm][d] = row[(lane + 32 * (mb + mm) - (c0 + d - K1 / 2)) & (kW - 1)];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int dyi = j - u + h;
+      if (dyi < 0 || dyi >= K2) continue;
+      const float2* qr = q + dyi * K1 + c0;
+#pragma unroll
+      for (int d = 0; d < KC; ++d) {
+        if (c0 + d >= K1) continue;
+        const float2 qv = qr[d];
+#pragma unroll
+        for (int mm = 0; mm < MB; ++mm) acc[j][mb + mm] = cfma(acc[j][mb + mm], qv, seg[mm][d]);
+      }
+    }
+  }
+}
+
+// K2F > 0 fixes K2 at compile time (the small square kernels): the input-row loop then
+// unrolls, its row-range tests fold away and q is read at constant offsets.
+template <int K1, int MB, int K2F = 0>
+__global__ void __launch_bounds__(kThreads, 1) k_slice_rs(const SliceLaunch a, const float2* qg, const int K2arg) {
+  const int K2 = K2F > 0 ? K2F : K2arg;
   extern __shared__ __align__(16) float2 sm[];
   float2* psi = sm;                 // [W][W]
   float2* q = sm + kW * kW;         // [K2][K1]
@@ -716,28 +751,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice_rs(const SliceLaunch a, c
       constexpr int KC = K1 < 13 ? K1 : 13;
 #pragma unroll
       for (int mb = 0; mb < 4; mb += MB) {
+        if constexpr (K2F > 0) {
+#pragma unroll
+          for (int u = K2F / 2 - (K2F - 1); u <= 7 + K2F / 2; ++u)
+            rs_row_step<K1, MB, KC>(acc, psi, q, wy, lane, mb, u, h, K2);
+        } else {
 #pragma unroll 1
-        for (int u = h - (K2 - 1); u <= 7 + h; ++u) {
-          const float2* row = psi + ((8 * wy + u) & (kW - 1)) * kW;
+          for (int u = h - (K2 - 1); u <= 7 + h; ++u) {
+            const float2* row = psi + ((8 * wy + u) & (kW - 1)) * kW;
 #pragma unroll
-          for (int c0 = 0; c0 < K1; c0 += KC) {
-            float2 seg[MB][KC];
+            for (int c0 = 0; c0 < K1; c0 += KC) {
+              float2 seg[MB][KC];
 #pragma unroll
-            for (int mm = 0; mm < MB; ++mm)
+              for (int mm = 0; mm < MB; ++mm)
 #pragma unroll
-              for (int d = 0; d < KC; ++d)
-                if (c0 + d < K1) seg[mm][d] = row[(lane + 32 * (mb + mm) - (c0 + d - K1 / 2)) & (kW - 1)];
+                for (int d = 0; d < KC; ++d)
+                  if (c0 + d < K1) seg[mm][d] = row[(lane + 32 * (mb + mm) - (c0 + d - K1 / 2)) & (kW - 1)];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const int dyi = j - u + h;
-              if (dyi < 0 || dyi >= K2) continue;
-              const float2* qr = q + dyi * K1 + c0;
+              for (int j = 0; j < 8; ++j) {
+                const int dyi = j - u + h;
+                if (dyi < 0 || dyi >= K2) continue;
+                const float2* qr = q + dyi * K1 + c0;
 #pragma unroll
-              for (int d = 0; d < KC; ++d) {
-                if (c0 + d >= K1) continue;
-                const float2 qv = qr[d];
+                for (int d = 0; d < KC; ++d) {
+                  if (c0 + d >= K1) continue;
+                  const float2 qv = qr[d];
 #pragma unroll
-                for (int mm = 0; mm < MB; ++mm) acc[j][mb + mm] = cfma(acc[j][mb + mm], qv, seg[mm][d]);
+                  for (int mm = 0; mm < MB; ++mm) acc[j][mb + mm] = cfma(acc[j][mb + mm], qv, seg[mm][d]);
+                }
               }
             }
           }
@@ -1301,7 +1342,7 @@ cudaError_t init_device_constants() {
       if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
   }
   const int sr = static_cast<int>(slice_rs_smem_bytes());
-  for (auto f : {k_slice_rs<3, 4>, k_slice_rs<5, 4>, k_slice_rs<7, 4>, k_slice_rs<9, 2>, k_slice_rs<11, 2>,
+  for (auto f : {k_slice_rs<3, 4, 3>, k_slice_rs<5, 4, 5>, k_slice_rs<3, 4>, k_slice_rs<5, 4>, k_slice_rs<7, 4>, k_slice_rs<9, 2>, k_slice_rs<11, 2>,
                  k_slice_rs<13, 2>, k_slice_rs<15, 2>, k_slice_rs<17, 2>, k_slice_rs<19, 2>, k_slice_rs<21, 2>,
                  k_slice_rs<23, 2>, k_slice_rs<25, 2>})
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sr)) != cudaSuccess) return e;
@@ -1364,8 +1405,14 @@ cudaError_t launch_slice_rs(const SliceLaunch& a, const float2* q, int K1, int K
   if (K2 < 1 || K2 > 25 || (K2 & 1) == 0) return cudaErrorInvalidValue;
   const size_t sm = slice_rs_smem_bytes();
   switch (K1) {
-    case 3: k_slice_rs<3, 4><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
-    case 5: k_slice_rs<5, 4><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
+    case 3:
+      if (K2 == 3) k_slice_rs<3, 4, 3><<<a.n_list, kThreads, sm, s>>>(a, q, K2);
+      else k_slice_rs<3, 4><<<a.n_list, kThreads, sm, s>>>(a, q, K2);
+      break;
+    case 5:
+      if (K2 == 5) k_slice_rs<5, 4, 5><<<a.n_list, kThreads, sm, s>>>(a, q, K2);
+      else k_slice_rs<5, 4><<<a.n_list, kThreads, sm, s>>>(a, q, K2);
+      break;
     case 7: k_slice_rs<7, 4><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
     case 9: k_slice_rs<9, 2><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
     case 11: k_slice_rs<11, 2><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;

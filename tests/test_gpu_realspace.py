@@ -40,17 +40,19 @@ def _oracle(w, K):
     return orc
 
 
-@pytest.mark.parametrize("case", ["simple_cubic", "perovskite", "wide_15x3", "wide_25x11"])
+@pytest.mark.parametrize("case", ["simple_cubic", "perovskite", "square_3", "square_5", "wide_15x3",
+                                  "wide_25x11"])
 def test_realspace_image_matches_oracle(ctx, case):
-    """K1 != K2 in the perovskite cases, so a transposed kernel fails; kernels wider than 13
-    columns take their row segment in two pieces (13 + 2 and 13 + 12 columns)."""
+    """K1 != K2 in the perovskite and wide cases, so a transposed kernel fails; kernels wider
+    than 13 columns take their row segment in two pieces (13 + 2 and 13 + 12 columns); the
+    3 x 3 and 5 x 5 kernels run the instantiations with K2 fixed at compile time."""
     if case == "simple_cubic":
         w = WL.simple_cubic_workload()
         region, K = WL.Region(0, 0, 3, 2, (8, 8)), (7, 7)
     else:
         w = WL.perovskite_workload(cells=5, nx=256, n_slices=5, n_phonons=2, seed_base=2700)
-        region, K = WL.Region(250, 60, 4, 3, (4, 4)), {"perovskite": (5, 9), "wide_15x3": (15, 3),
-                                                       "wide_25x11": (25, 11)}[case]
+        region, K = WL.Region(250, 60, 4, 3, (4, 4)), {"perovskite": (5, 9), "square_3": (3, 3), "square_5": (5, 5),
+                                                       "wide_15x3": (15, 3), "wide_25x11": (25, 11)}[case]
     dets = [WL.Detector(0.0, 0.02), WL.Detector(0.06, 0.2)]
     spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
     basis = lma.Basis(ctx, spec, w.probe, w.basis)
