@@ -343,11 +343,13 @@ def serving_measure(n_requests: int, loads=(0.5, 0.8), seed: int = 4000) -> dict
 
 
 def batching_measure(n_phonons: int, steps: int) -> dict:
-    """Batched form against the plain complex64 LMA on three specimens of uneven size.
+    """Batched form against the plain complex64 LMA, on two sets of specimens.
 
-    Specimens: ABO3 5x5 cells on 256^2 (20 slices), 10x10 on 512^2 (50 slices), 20x20
+    Uneven sizes: ABO3 5x5 cells on 256^2 (20 slices), 10x10 on 512^2 (50 slices), 20x20
     on 1024^2 (100 slices), 64^2 / 128^2 / 256^2 probes every 4 px, `n_phonons` seeded
-    frozen-phonon configurations each.
+    frozen-phonon configurations each. Many small specimens: 16 of 2x2 cells on 128^2
+    (10 slices) and 8 of 5x5 cells on 256^2 (20 slices), 2 configurations each, with the
+    full input lattice and with the sub-lattice f = 4 (64 / 256 translates per specimen).
       plain:   one lma_image per specimen, one configuration per slice and synthesis
                launch (phonon batch 1), one CTA per translate.
       batched: one lma_image_many call: configurations in phonon batches (as many as fit
@@ -356,10 +358,21 @@ def batching_measure(n_phonons: int, steps: int) -> dict:
     Both run on one stream with device outputs and are timed with CUDA events; the
     outputs of the two forms are compared bitwise.
     """
+    out = _batching_case(WL.batch_workloads(n_phonons), n_phonons, steps,
+                         "abo3 256^2/20sl + 512^2/50sl + 1024^2/100sl, %d configurations each" % n_phonons)
+    out["small_specimens"] = _batching_case(
+        WL.small_batch_workloads(2), 2, max(steps, 3),
+        "16 x abo3 128^2/10sl + 8 x abo3 256^2/20sl, 2 configurations each")
+    out["small_specimens_f4"] = _batching_case(
+        WL.small_batch_workloads(2, f=4), 2, max(steps, 3),
+        "16 x abo3 128^2/10sl + 8 x abo3 256^2/20sl, 2 configurations each, input sub-lattice f = 4")
+    return out
+
+
+def _batching_case(ws, n_phonons: int, steps: int, label: str) -> dict:
     import torch
     from paper_2310_16829_gb300 import lma
     from dataclasses import replace
-    ws = WL.batch_workloads(n_phonons)
     pixels = sum(w.n_pixels for w in ws)
     ctx = lma.Context(0)
     st = torch.cuda.Stream()
@@ -418,8 +431,7 @@ def batching_measure(n_phonons: int, steps: int) -> dict:
     ms_b = timed(batched)
     same = all(np.array_equal(o.cpu().numpy(), r) for o, r in zip(o_b, ref))
     info = [b.info() for b in bases]
-    out = {"workload": "abo3 256^2/20sl + 512^2/50sl + 1024^2/100sl, %d configurations each" % n_phonons,
-           "pixels": pixels, "steps": steps,
+    out = {"workload": label, "pixels": pixels, "steps": steps,
            "plain": {"ms": ms_plain, "pixels_per_s": pixels / (ms_plain / 1e3)},
            "batched": {"ms": ms_b, "pixels_per_s": pixels / (ms_b / 1e3),
                        "phonon_batch": [int(i.phonon_batch) for i in info],

@@ -247,6 +247,21 @@ def batch_workloads(n_phonons: int = 32) -> List[Workload]:
     return out
 
 
+def small_batch_workloads(n_phonons: int = 2, f: int = 1) -> List[Workload]:
+    """Many small specimens: 16 ABO3 slabs of 2x2 cells on 128^2 (10 slices) and 8 of 5x5
+    cells on 256^2 (20 slices), probes every 4 px, input waves every 4 px thinned to the
+    sub-lattice I_f (Sec. 4.2.1, reduction (i)). With f = 1 each specimen's slice launch
+    is 7 or 27 waves of CTAs deep; with f = 4 it has 64 or 256 translates, fewer than or
+    under two waves of the GPU's SMs."""
+    out = []
+    for k in range(24):
+        cells, nx, ns = (2, 128, 10) if k < 16 else (5, 256, 20)
+        w = perovskite_workload(cells=cells, nx=nx, n_slices=ns, n_phonons=n_phonons,
+                                seed_base=4000 + 100 * k)
+        out.append(replace(w, basis=replace(w.basis, f=f)))
+    return out
+
+
 def serving_workload() -> Workload:
     """Resident 20x20-cell ABO3 specimen, 1024^2 grid, 200 A thick, one configuration."""
     w = perovskite_workload(cells=20, nx=1024, n_slices=100, n_phonons=1, seed_base=3000,
