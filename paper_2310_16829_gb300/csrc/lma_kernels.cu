@@ -695,9 +695,13 @@ __device__ __forceinline__ void rs_row_step(float2 (&acc)[8][4], const float2* p
 }
 
 // K2F > 0 fixes K2 at compile time (the small square kernels): the input-row loop then
-// unrolls, its row-range tests fold away and q is read at constant offsets.
+// unrolls, its row-range tests fold away and q is read at constant offsets. These kernels
+// also apply each slice's transmission as the previous convolution's outputs are written
+// (FUSE), instead of in a pass of its own over the wave in shared memory; the products
+// and their order are the same.
 template <int K1, int MB, int K2F = 0>
 __global__ void __launch_bounds__(kThreads, 1) k_slice_rs(const SliceLaunch a, const float2* qg, const int K2arg) {
+  constexpr bool FUSE = K2F > 0;
   const int K2 = K2F > 0 ? K2F : K2arg;
   extern __shared__ __align__(16) float2 sm[];
   float2* psi = sm;                 // [W][W]
@@ -720,12 +724,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice_rs(const SliceLaunch a, c
     const size_t slice_elems = static_cast<size_t>(pitch) * (J.ny + kW);
     const float2* tb = J.t + cfg * J.t_slot + static_cast<size_t>(oy) * pitch + ox;
     __syncthreads();   // the previous item's reads of psi are done
-    for (int p = T; p < kW * kW; p += kThreads) psi[p] = J.uW[p];
+    if (FUSE && J.n_slices > 0) {
+      // the first slice's transmission applied as the input wave is loaded
+      for (int p = T; p < kW * kW; p += kThreads)
+        psi[p] = cmul(J.uW[p], tb[static_cast<size_t>(p >> 7) * pitch + (p & (kW - 1))]);
+    } else {
+      for (int p = T; p < kW * kW; p += kThreads) psi[p] = J.uW[p];
+    }
     for (int s = 0; s < J.n_slices; ++s) {
-      // transmission (Sec. 3.2): psi <- t_s psi
-      __syncthreads();
-      const float2* ts = tb + s * slice_elems;
-      {
+      if constexpr (!FUSE) {
+        // transmission (Sec. 3.2): psi <- t_s psi
+        __syncthreads();
+        const float2* ts = tb + s * slice_elems;
         // all 32 loads of this thread's transmission values first (row (T >> 7) + 4 i,
         // column T & 127), then the products
         float2 tv[kW * kW / kThreads];
@@ -784,11 +794,46 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice_rs(const SliceLaunch a, c
           }
         }
       }
-      __syncthreads();
+      if constexpr (FUSE) {
+        // the outputs times the next slice's transmission at the same pixels (rows 8 wy + j,
+        // columns lane + 32 m), in two halves of 16 loads; the first half is in flight
+        // while the CTA waits for every read of psi to finish
+        const bool more = s + 1 < J.n_slices;
+        const float2* tn = more ? tb + (s + 1) * slice_elems + static_cast<size_t>(8 * wy) * pitch + lane : nullptr;
+        float2 tv[4][4];
+        if (more) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
+          for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int m = 0; m < 4; ++m) psi[(8 * wy + j) * kW + lane + 32 * m] = acc[j][m];
+            for (int m = 0; m < 4; ++m) tv[j][m] = tn[static_cast<size_t>(j) * pitch + 32 * m];
+        }
+        __syncthreads();
+        if (more) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) psi[(8 * wy + j) * kW + lane + 32 * m] = cmul(acc[j][m], tv[j][m]);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) tv[j][m] = tn[static_cast<size_t>(4 + j) * pitch + 32 * m];
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) psi[(8 * wy + 4 + j) * kW + lane + 32 * m] = cmul(acc[4 + j][m], tv[j][m]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) psi[(8 * wy + j) * kW + lane + 32 * m] = acc[j][m];
+        }
+      } else {
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+          for (int m = 0; m < 4; ++m) psi[(8 * wy + j) * kW + lane + 32 * m] = acc[j][m];
+      }
     }
     __syncthreads();
     const int oi = a.out_index ? a.out_index[li] : ti;
