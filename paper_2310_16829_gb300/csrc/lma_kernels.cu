@@ -1387,7 +1387,7 @@ cudaError_t init_device_constants() {
       if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
   }
   const int sr = static_cast<int>(slice_rs_smem_bytes());
-  for (auto f : {k_slice_rs<3, 4, 3>, k_slice_rs<5, 4, 5>, k_slice_rs<3, 4>, k_slice_rs<5, 4>, k_slice_rs<7, 4>, k_slice_rs<9, 2>, k_slice_rs<11, 2>,
+  for (auto f : {k_slice_rs<3, 4, 3>, k_slice_rs<5, 4, 5>, k_slice_rs<3, 4>, k_slice_rs<5, 4>, k_slice_rs<7, 2>, k_slice_rs<9, 2>, k_slice_rs<11, 2>,
                  k_slice_rs<13, 2>, k_slice_rs<15, 2>, k_slice_rs<17, 2>, k_slice_rs<19, 2>, k_slice_rs<21, 2>,
                  k_slice_rs<23, 2>, k_slice_rs<25, 2>})
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sr)) != cudaSuccess) return e;
@@ -1458,7 +1458,7 @@ cudaError_t launch_slice_rs(const SliceLaunch& a, const float2* q, int K1, int K
       if (K2 == 5) k_slice_rs<5, 4, 5><<<a.n_list, kThreads, sm, s>>>(a, q, K2);
       else k_slice_rs<5, 4><<<a.n_list, kThreads, sm, s>>>(a, q, K2);
       break;
-    case 7: k_slice_rs<7, 4><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
+    case 7: k_slice_rs<7, 2><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
     case 9: k_slice_rs<9, 2><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
     case 11: k_slice_rs<11, 2><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
     case 13: k_slice_rs<13, 2><<<a.n_list, kThreads, sm, s>>>(a, q, K2); break;
