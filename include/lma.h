@@ -230,7 +230,11 @@ lma_status lma_specimen_set_atoms(lma_ctx* ctx, lma_specimen* spec, const lma_at
  * W or D != 128 or a grid smaller than W. */
 lma_status lma_create_basis(lma_ctx* ctx, const lma_specimen* spec, const lma_probe* probe,
                             const lma_basis_desc* desc, lma_basis** out);
+/* Release the basis and its device memory (exit-wave store, tables). The handle is
+ * invalid afterwards. Errors: LMA_ERR_INVALID for NULL. */
 lma_status lma_free_basis(lma_basis* basis);
+/* Fill *out with the basis summary (lma_basis_info). Host-only; no device work.
+ * Errors: LMA_ERR_INVALID for a NULL argument. */
 lma_status lma_basis_get_info(const lma_basis* basis, lma_basis_info* out);
 
 /* Coefficients of the probe at pixel (px, py) (eqs. lma_approximation_exit1_0 /
