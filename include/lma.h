@@ -190,6 +190,8 @@ typedef struct {
  * Use one context per thread for concurrent work.
  * Errors: LMA_ERR_CUDA if the device cannot be selected, LMA_ERR_OOM. */
 lma_status lma_create(int32_t device, lma_ctx** out);
+/* Release the context with its graphs, caches and staging buffers; free its specimens and
+ * bases first. NULL is ignored. */
 void lma_destroy(lma_ctx* ctx);
 /* Last error message of the context ("" if none). The pointer stays valid until the next call. */
 const char* lma_last_error(const lma_ctx* ctx);
@@ -203,6 +205,8 @@ const char* lma_last_error(const lma_ctx* ctx);
  * r_cut >= half the cell, n_terms outside 1..4). */
 lma_status lma_create_specimen(lma_ctx* ctx, const lma_grid* grid, const lma_potential* pot,
                                const lma_atoms* phonons, int32_t n_phonons, lma_specimen** out);
+/* Release the specimen and its device memory (atoms, transmissions); free its bases first.
+ * Errors: LMA_ERR_INVALID for NULL. */
 lma_status lma_free_specimen(lma_specimen* spec);
 
 /* Build t_s = exp(i sigma v_s) for all slices of configuration `phonon` on the
