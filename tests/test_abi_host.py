@@ -281,3 +281,16 @@ def test_header_is_plain_c():
     r = subprocess.run([gcc, "-std=c99", "-fsyntax-only", "-Wall", "-Wextra", "-pedantic", "-Werror", "-x", "c",
                         os.path.join(ROOT, "include", "lma.h")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_binding_fails_loudly_without_the_cuda_library(tmp_path):
+    """No fallback: loading the binding's library from a path where it was not built raises
+    (checked in a fresh process, since a loaded library is cached)."""
+    import subprocess
+    import sys
+    missing = str(tmp_path / "liblma.so")
+    code = ("from paper_2310_16829_gb300 import lma\n"
+            "try:\n    lma.load(%r)\nexcept RuntimeError as e:\n    print('raised:', e)\n    raise SystemExit(3)\n" % missing)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 3 and "not built" in r.stdout, (r.returncode, r.stdout, r.stderr[-500:])
