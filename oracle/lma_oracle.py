@@ -683,11 +683,21 @@ class LmaOracle:
         return self._U[(phi, i)]
 
     # -- image ----------------------------------------------------------------
+    # the three steps after propagation; a restatement in another precision overrides them
+    def _synthesize(self, U, alpha, offsets) -> np.ndarray:
+        return synthesize(U, alpha, offsets, self.prm.D, self.prm.cyclic)
+
+    def _detect(self, psi: np.ndarray, mask: np.ndarray) -> float:
+        return detect(psi, mask)
+
+    def _pattern(self, psi: np.ndarray, A: int, B: int) -> np.ndarray:
+        return pattern(psi, A, B, self.prm.bandlimit_frac)
+
     def pixel(self, phi: int, p: Tuple[int, int], masks: Sequence[np.ndarray]) -> List[float]:
         cs, idx = self.coefficient_set(p)
         U = [self.exit_wave(phi, int(i)) for i in idx]
-        psi = synthesize(U, cs.alpha, cs.offsets, self.prm.D, self.prm.cyclic)
-        return [detect(psi, m) for m in masks]
+        psi = self._synthesize(U, cs.alpha, cs.offsets)
+        return [self._detect(psi, m) for m in masks]
 
     def detector_masks(self, detectors) -> List[np.ndarray]:
         p = self.prm
@@ -729,8 +739,8 @@ class LmaOracle:
                         sets[key] = (coefficients_closed(psi0, self.uW, offs, self.prm.degree, self.prm.lattice_m)
                                      if self.prm.coef_mode == 1 else coefficients(psi0, self.uW, offs))
                     U = [self.exit_wave(phi, int(i)) for i in idx]
-                    psi = synthesize(U, sets[key].alpha, offs, p.D, p.cyclic)
-                    img[:, k] += [detect(psi, m) for m in masks]
+                    psi = self._synthesize(U, sets[key].alpha, offs)
+                    img[:, k] += [self._detect(psi, m) for m in masks]
             out += (weight / wsum) * img / nphi
         return out
 
@@ -755,8 +765,8 @@ class LmaOracle:
             for k, pr in enumerate(probes):
                 cs, idx = self.coefficient_set((int(pr[0]), int(pr[1])))
                 U = [self.exit_wave(phi, int(i)) for i in idx]
-                psi = synthesize(U, cs.alpha, cs.offsets, self.prm.D, self.prm.cyclic)
-                out[k] += pattern(psi, A, B, self.prm.bandlimit_frac)
+                psi = self._synthesize(U, cs.alpha, cs.offsets)
+                out[k] += self._pattern(psi, A, B)
         return out / nphi
 
 
