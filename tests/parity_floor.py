@@ -1,0 +1,57 @@
+"""Parity criterion of the GPU tests: 1e-4 relative per reading, or twice the complex64 floor.
+
+The GPU path computes in complex64. For each compared image the tests also evaluate the
+oracle's pipeline restated in complex64 (``oracle.lma_c64``) on the same inputs; its error
+against the FP64 oracle is what single-precision arithmetic alone makes. Per detector row
+(one annulus, ring or pattern) the envelope of that error is kappa sqrt(I), kappa = max over
+the row of |I_c64 - I| / sqrt(I) (``lma_c64.floor_scale``). Every GPU reading must satisfy
+
+    |I_gpu - I| <= max(tol * I, 2 kappa sqrt(I)),
+
+pixel by pixel: the strict relative bound wherever complex64 can meet it, and otherwise no
+more than twice the error the complex64 restatement itself makes at that reading.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import lma_c64 as C
+from oracle import lma_oracle as O
+
+PIXEL_TOL = 1e-4
+MARGIN = 2.0
+
+
+def oracles(w, realspace=None):
+    """(FP64 oracle, complex64 restatement) with the workload's specimen set."""
+    out = []
+    for cls in (O.LmaOracle, C.LmaOracleC64):
+        orc = cls(O.params_from_workload(w), realspace=realspace)
+        orc.set_specimen(w.phonons, w.potential.peak, w.potential.term_frac, w.potential.term_width,
+                         w.potential.r_cut)
+        out.append(orc)
+    return out[0], out[1]
+
+
+def assert_floor(got, ref, emu, tol: float = PIXEL_TOL, margin: float = MARGIN, label: str = "") -> dict:
+    """Assert the criterion above; rows are the first axis of ``ref`` (detectors).
+    Returns the worst ratio of error to bound per row and the rows' kappa."""
+    ref2 = np.atleast_2d(np.asarray(ref, dtype=np.float64))
+    ref2 = ref2.reshape(ref2.shape[0], -1)
+    got2 = np.asarray(got, dtype=np.float64).reshape(ref2.shape)
+    emu2 = np.asarray(emu, dtype=np.float64).reshape(ref2.shape)
+    bound = C.floor_bound(ref2, emu2, tol, margin)
+    err = np.abs(got2 - ref2)
+    # a reading the oracle gives as exactly zero (outside the band) must be exactly zero
+    zero = ref2 == 0.0
+    assert np.all(got2[zero] == 0.0), f"{label}: nonzero GPU value where the oracle is exactly 0"
+    ratio = np.where(zero, 0.0, err / np.where(zero, 1.0, bound))
+    worst = ratio.max(axis=1)
+    kap = C.floor_scale(ref2, emu2)
+    for r in range(ref2.shape[0]):
+        k = int(np.argmax(ratio[r]))
+        assert worst[r] <= 1.0, (
+            f"{label} row {r}: reading {ref2[r, k]:.3e}, GPU error {err[r, k]:.3e} > bound {bound[r, k]:.3e} "
+            f"(tol {tol:g} relative, or {margin:g} x complex64 envelope kappa={kap[r]:.3e} x sqrt(I))")
+    return {"worst_ratio": worst.tolist(), "kappa": kap.tolist(),
+            "max_rel": float(np.max(np.where(zero, 0.0, err / np.where(zero, 1.0, ref2))))}

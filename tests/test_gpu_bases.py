@@ -1,11 +1,12 @@
 """Trigonometric input waves (Sec. 4.2.3: the tensor product phi_n(x) phi_n(y) and the radial
-phi_n(|v|)) through the GPU path against the FP64 oracle. Tolerance as for the 3D STEM rings:
-1e-4 x max(reading, 1e-4 of the beam) (complex64 rounding floor on weak readings)."""
+phi_n(|v|)) through the GPU path against the FP64 oracle. Readings are held to 1e-4 relative
+error, or to twice the complex64 floor of the same image (``parity_floor``)."""
 import numpy as np
 import pytest
 
 from oracle import lma_oracle as O
 from paper_2310_16829_gb300 import lma, workloads as WL
+from parity_floor import assert_floor, oracles
 
 pytestmark = pytest.mark.gpu
 
@@ -27,13 +28,10 @@ def test_trig_input_waves_match_oracle(ctx, kind):
         spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
         basis = lma.Basis(ctx, spec, w.probe, w.basis)
         got = basis.image(dets, region, recompute=True).reshape(2, -1)
-        orc = O.LmaOracle(O.params_from_workload(w))
-        orc.set_specimen(w.phonons, w.potential.peak, w.potential.term_frac, w.potential.term_width,
-                         w.potential.r_cut)
-        ref = orc.image(dets, O.region_probes(region.px0, region.py0, region.npx, region.npy,
-                                             region.spacing_px, w.grid.nx, w.grid.ny))
-        err = np.abs(got - ref) / np.maximum(ref, 1e-4)
-        assert err.max() < 1e-4, (w.name, kind, err.max())
+        orc, emu = oracles(w)
+        probes = O.region_probes(region.px0, region.py0, region.npx, region.npy, region.spacing_px,
+                                 w.grid.nx, w.grid.ny)
+        assert_floor(got, orc.image(dets, probes), emu.image(dets, probes), label=f"{w.name} {kind}")
 
 
 def test_closed_form_trig_coefficients_image_matches_oracle(ctx):
@@ -50,14 +48,11 @@ def test_closed_form_trig_coefficients_image_matches_oracle(ctx):
         spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
         basis = lma.Basis(ctx, spec, w.probe, w.basis)
         got = basis.image(dets, region, recompute=True).reshape(2, -1)
-        orc = O.LmaOracle(O.params_from_workload(w))
-        orc.set_specimen(w.phonons, w.potential.peak, w.potential.term_frac, w.potential.term_width,
-                         w.potential.r_cut)
+        orc, emu = oracles(w)
         probes = O.region_probes(region.px0, region.py0, region.npx, region.npy, region.spacing_px,
                                  w.grid.nx, w.grid.ny)
         ref = orc.image(dets, probes)
-        err = np.abs(got - ref) / np.maximum(ref, 1e-4)
-        assert err.max() < 1e-4, (w.name, err.max())
+        assert_floor(got, ref, emu.image(dets, probes), label=f"{w.name} closed form")
         w.basis.coef_mode = 0
         ls = lma.Basis(ctx, spec, w.probe, w.basis).image(dets, region, recompute=True).reshape(2, -1)
         assert np.max(np.abs(ls - got) / np.maximum(ref, 1e-4)) > 1e-3, w.name

@@ -1,8 +1,7 @@
 """Edge cases of the GPU path against the FP64 oracle: free space (no atoms), the extreme
 numbers of input waves per probe (L = 1 and the maximum 64), a region of one probe, and a
-non-square grid. Tolerances as in the parity tests: 1e-4 relative per reading, with the
-absolute floor of 1e-4 of the beam for weak readings (complex64 rounding floor), exit waves
-to 5e-5 of their peak."""
+non-square grid. Tolerances as in the parity tests: 1e-4 relative per reading, or twice the
+complex64 floor of the same image (``parity_floor``); exit waves to 5e-5 of their peak."""
 import dataclasses
 
 import numpy as np
@@ -10,6 +9,7 @@ import pytest
 
 from oracle import lma_oracle as O
 from paper_2310_16829_gb300 import lma, workloads as WL
+from parity_floor import assert_floor, oracles
 
 pytestmark = pytest.mark.gpu
 
@@ -22,24 +22,22 @@ def ctx():
 
 
 def _oracle(w):
-    orc = O.LmaOracle(O.params_from_workload(w))
-    orc.set_specimen(w.phonons, w.potential.peak, w.potential.term_frac, w.potential.term_width,
-                     w.potential.r_cut)
-    return orc
+    return oracles(w)[0]
 
 
 def _image(ctx, w, dets, region):
+    """GPU image, FP64 oracle image and the complex64 restatement's image of the region."""
     spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
     basis = lma.Basis(ctx, spec, w.probe, w.basis)
     got = basis.image(dets, region, recompute=True).reshape(len(dets), -1)
-    ref = _oracle(w).image(dets, O.region_probes(region.px0, region.py0, region.npx, region.npy,
-                                                 region.spacing_px, w.grid.nx, w.grid.ny))
-    return got, ref, basis
+    probes = O.region_probes(region.px0, region.py0, region.npx, region.npy, region.spacing_px,
+                             w.grid.nx, w.grid.ny)
+    orc, emu = oracles(w)
+    return got, (orc.image(dets, probes), emu.image(dets, probes)), basis
 
 
-def _assert_readings(got, ref):
-    err = np.abs(got - ref) / np.maximum(ref, 1e-4)
-    assert err.max() < 1e-4, err.max()
+def _assert_readings(got, ref_emu):
+    assert_floor(got, ref_emu[0], ref_emu[1])
 
 
 def test_free_space_exit_waves_conserve_the_norm_and_match_the_oracle(ctx):
@@ -63,8 +61,8 @@ def test_free_space_exit_waves_conserve_the_norm_and_match_the_oracle(ctx):
     dets = [WL.Detector(0.0, 0.02), WL.Detector(0.02, 0.06)]
     region = WL.Region(0, 0, 3, 2, (8, 8))
     got = basis.image(dets, region, recompute=True).reshape(2, -1)
-    ref = orc.image(dets, O.region_probes(0, 0, 3, 2, (8, 8), 128, 128))
-    _assert_readings(got, ref)
+    probes = O.region_probes(0, 0, 3, 2, (8, 8), 128, 128)
+    _assert_readings(got, (orc.image(dets, probes), oracles(w)[1].image(dets, probes)))
 
 
 @pytest.mark.parametrize("L", [1, 64])
@@ -123,7 +121,7 @@ def test_fp16_store_readouts_are_consistent():
     ctx = lma.Context(0)
     w = WL.perovskite_workload(cells=5, nx=256, n_slices=8, n_phonons=2, seed_base=2300)
     w = w.with_region(WL.Region(250, 12, 5, 3, (4, 4)))
-    w.basis.precision = WL.PREC_MIXED
+    w.basis.precision = WL.PREC_FP16_STORE
     spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
     basis = lma.Basis(ctx, spec, w.probe, w.basis)
     rings = basis.image_rings(0.01, 9, w.region, recompute=True)

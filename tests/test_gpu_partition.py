@@ -16,7 +16,7 @@ def ctx():
     return lma.Context(0)
 
 
-@pytest.mark.parametrize("precision", [WL.PREC_C64, WL.PREC_MIXED])
+@pytest.mark.parametrize("precision", [WL.PREC_C64, WL.PREC_FP16_STORE])
 def test_partitioned_image_equals_unbounded_image(ctx, precision):
     w = WL.perovskite_workload(cells=5, nx=256, n_slices=6, n_phonons=2, seed_base=2400)
     w.basis.precision = precision
