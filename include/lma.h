@@ -66,7 +66,7 @@ typedef int32_t lma_status;
                                    nearest input waves; needs m_x, m_y >= 2n + 1. */
 
 #define LMA_PREC_C64 0         /* complex64 everywhere on the device */
-#define LMA_PREC_MIXED 1       /* FP32 propagation; exit waves stored as FP16 pairs with a per-wave
+#define LMA_PREC_FP16_STORE 1       /* FP32 propagation; exit waves stored as FP16 pairs with a per-wave
                                   power-of-two scale: half the store; bright-field readings within
                                   1e-3, weak annular (HAADF) readings are not (FP16 rounding noise) */
 
@@ -143,7 +143,7 @@ typedef struct {
   int32_t L;                 /* input waves per probe (I_{f,p,L}) */
   int32_t window;            /* W: propagation window X' = Y' (128) */
   int32_t det_window;        /* D: synthesis / detection window (128) */
-  int32_t precision;         /* LMA_PREC_C64 or LMA_PREC_MIXED */
+  int32_t precision;         /* LMA_PREC_C64 or LMA_PREC_FP16_STORE */
   int32_t phonon_batch;      /* configurations propagated per launch and held at once;
                                 0 = as many as fit in 40 % of the free device memory */
   int32_t trig_degree;       /* LMA_BASIS_TRIG*: degree n of phi_n(t) = sum_{|k|<=n} e^{ikt} cos(k pi/(2n+2));
@@ -367,7 +367,7 @@ lma_status lma_partition(lma_ctx* ctx, lma_basis* basis, const lma_region* regio
  * are propagated and read out in order, keeping the waves shared by consecutive parts.
  * Every exit wave and reading is computed as in lma_image, so the image is bitwise equal
  * to lma_image's. The device store is max_resident * W^2 * 8 bytes (complex64) or half
- * that (LMA_PREC_MIXED); the plan's tables are kept in the basis for the next call.
+ * that (LMA_PREC_FP16_STORE); the plan's tables are kept in the basis for the next call.
  * Errors as for lma_image and lma_partition. */
 lma_status lma_image_partitioned(lma_ctx* ctx, lma_specimen* spec, lma_basis* basis,
                                  const lma_detector* det, int32_t n_det, const lma_region* region,
@@ -427,12 +427,22 @@ lma_status lma_affected_probes(lma_ctx* ctx, lma_basis* basis, const lma_region*
  * rejected with LMA_ERR_INVALID and a message giving the limit.
  *
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress); make that first call before any stream capture
+ * begins. (That rule is about this set-up step alone; it says nothing either
+ * way about capturing the readout itself.) With CUDA's default lazy module
+ * loading, the array -- 8 MiB plus the library's kernels -- comes into being
+ * on the device at the library's first kernel launch or first no-allocation
+ * call there: a caller whose footprint must not grow later makes one call
+ * (or sets CUDA_MODULE_LOADING=EAGER) before that phase starts.
  * Every call shares the array and the accumulator is cleared at the start of
  * each call, so calls that overlap on the GPU (several streams or host
- * threads) race: serialize them. The call synchronizes `stream` before it
- * returns. Errors as for lma_image; LMA_ERR_INVALID also when exit_waves or
- * out is not device memory. */
+ * threads) race: serialize them. The small host tables are copied from
+ * pageable memory, on purpose: a pinned staging buffer would be an
+ * allocation. Pageable copies pass through the driver's staging buffer, which
+ * the whole process shares, so they can hold up other threads' pageable
+ * copies (for instance the uploads of other contexts) for their duration. The
+ * call synchronizes `stream` before it returns. Errors as for lma_image;
+ * LMA_ERR_INVALID also when exit_waves or out is not device memory. */
 lma_status lma_readout_noalloc(lma_ctx* ctx, lma_basis* basis, const float* exit_waves,
                                const lma_detector* det, int32_t n_det, const lma_region* region,
                                double* out, void* stream);

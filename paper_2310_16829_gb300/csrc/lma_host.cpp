@@ -710,7 +710,7 @@ lma_status ensure_basis_device(lma_basis* b, cudaStream_t st) {
   lma_status s0 = ensure_basis_tables(b, st);
   if (s0 != LMA_OK) return s0;
   // phonon batch: configurations whose exit waves (and transmissions) are held at once
-  const bool half = b->desc.precision == LMA_PREC_MIXED;
+  const bool half = b->desc.precision == LMA_PREC_FP16_STORE;
   const int nph = static_cast<int>(b->spec->ph.size());
   const lma_grid& g = b->spec->g;
   const size_t u_cfg = static_cast<size_t>(b->nT) * kW * kW * (half ? 4 : sizeof(float2));
@@ -939,7 +939,7 @@ lma_dev::SliceJob make_job(const lma_basis* b, const lma_specimen* sp) {
   J.lat_sx = b->Sx;
   J.lat_sy = b->Sy;
   J.lat_nax = b->nax;
-  const bool half = b->desc.precision == LMA_PREC_MIXED;
+  const bool half = b->desc.precision == LMA_PREC_FP16_STORE;
   J.U = half ? nullptr : static_cast<float2*>(b->d_U.p);
   J.Uh = half ? b->d_U.p : nullptr;
   J.Uscale = half ? static_cast<float*>(b->d_Uscale.p) : nullptr;
@@ -1027,7 +1027,7 @@ lma_status propagate_jobs(lma_ctx* ctx, std::vector<JobWork>& work, cudaStream_t
   for (int hv = 0; hv < 2; ++hv) {
     std::vector<JobWork*> group;
     for (JobWork& w : work)
-      if (!w.items.empty() && (w.b->desc.precision == LMA_PREC_MIXED) == (hv == 1)) group.push_back(&w);
+      if (!w.items.empty() && (w.b->desc.precision == LMA_PREC_FP16_STORE) == (hv == 1)) group.push_back(&w);
     for (size_t c0 = 0; c0 < group.size(); c0 += lma_dev::kMaxJobs) {
       const int nj = static_cast<int>(std::min<size_t>(lma_dev::kMaxJobs, group.size() - c0));
       for (int part = 0; part < 2; ++part) {
@@ -1157,19 +1157,13 @@ lma_status build_region(lma_basis* b, const lma_region* r, cudaStream_t st) {
   return LMA_OK;
 }
 
-// detector bits in the C layout of the synthesis kernel: word T = kx + 128 k1y, bit j <-> ky = k1y + 4 j
-lma_status build_detectors(lma_basis* b, const lma_detector* det, int n_det, cudaStream_t st) {
-  lma_ctx* ctx = b->ctx;
-  std::vector<double> key;
-  for (int d = 0; d < n_det; ++d) {
-    key.push_back(det[d].r1);
-    key.push_back(det[d].r2);
-  }
-  if (b->d_det.p && key == b->det_key) return LMA_OK;
+// Detector bits in the C layout of the synthesis kernel: word T = kx + 128 k1y, bit j <-> ky =
+// k1y + 4 j; bit set where r1 <= lambda |k| < r2 inside the bandlimit (decided in FP64).
+void detector_bits_host(const lma_basis* b, const lma_detector* det, int n_det, std::vector<uint32_t>& bits) {
   const lma_grid& g = b->spec->g;
   const int D = b->desc.det_window;
   const double dx = g.lx / g.nx, dy = g.ly / g.ny, lam = g.lambda, frac = g.bandlimit_frac;
-  std::vector<uint32_t> bits(static_cast<size_t>(n_det) * lma_dev::kThreads, 0u);
+  bits.assign(static_cast<size_t>(n_det) * lma_dev::kThreads, 0u);
   for (int d = 0; d < n_det; ++d) {
     for (int iy = 0; iy < D; ++iy) {
       const int my = signed_index(iy, D);
@@ -1186,6 +1180,18 @@ lma_status build_detectors(lma_basis* b, const lma_detector* det, int n_det, cud
       }
     }
   }
+}
+
+lma_status build_detectors(lma_basis* b, const lma_detector* det, int n_det, cudaStream_t st) {
+  lma_ctx* ctx = b->ctx;
+  std::vector<double> key;
+  for (int d = 0; d < n_det; ++d) {
+    key.push_back(det[d].r1);
+    key.push_back(det[d].r2);
+  }
+  if (b->d_det.p && key == b->det_key) return LMA_OK;
+  std::vector<uint32_t> bits;
+  detector_bits_host(b, det, n_det, bits);
   CUDA_TRY(ctx, ensure(b->d_det, bits.size() * sizeof(uint32_t)));
   CUDA_TRY(ctx, upload(ctx, b->d_det.p, bits.data(), bits.size() * sizeof(uint32_t), st));
   b->det_key = key;
@@ -1314,7 +1320,7 @@ lma_status images_work(lma_ctx* ctx, const std::vector<ImageJob>& jobs, const Re
       const int nb = batch[k].second;
       if (nb == 0) continue;
       lma_basis* b = jobs[k].b;
-      const bool half = b->desc.precision == LMA_PREC_MIXED;
+      const bool half = b->desc.precision == LMA_PREC_FP16_STORE;
       const int64_t np = b->reg.n_probes;
       lma_dev::SynthArgs a{};
       a.U = half ? nullptr : static_cast<const float2*>(b->d_U.p);
@@ -1585,8 +1591,8 @@ lma_status lma_create_basis(lma_ctx* ctx, const lma_specimen* spec, const lma_pr
     return fail(ctx, LMA_ERR_INVALID, "coef_mode must be LMA_COEF_LSQ or LMA_COEF_TRIG_CLOSED");
   if (d.coef_mode == LMA_COEF_TRIG_CLOSED && d.kind != LMA_BASIS_TRIG)
     return fail(ctx, LMA_ERR_INVALID, "closed-form coefficients need the tensor trigonometric input waves (LMA_BASIS_TRIG)");
-  if (d.precision != LMA_PREC_C64 && d.precision != LMA_PREC_MIXED)
-    return fail(ctx, LMA_ERR_INVALID, "precision must be LMA_PREC_C64 or LMA_PREC_MIXED");
+  if (d.precision != LMA_PREC_C64 && d.precision != LMA_PREC_FP16_STORE)
+    return fail(ctx, LMA_ERR_INVALID, "precision must be LMA_PREC_C64 or LMA_PREC_FP16_STORE");
   if (!(probe->alpha_max > 0)) return fail(ctx, LMA_ERR_INVALID, "alpha_max must be positive");
   const int sx = d.in_spacing_px[0], sy = d.in_spacing_px[1];
   if (sx <= 0 || sy <= 0 || g.nx % sx || g.ny % sy)
@@ -1678,7 +1684,7 @@ lma_status lma_basis_get_info(const lma_basis* b, lma_basis_info* out) {
   out->det_window = b->desc.det_window;
   out->gauss_sigma = b->gauss_sigma;
   out->exit_wave_bytes = b->nT * static_cast<int64_t>(kW) * kW *
-                         (b->desc.precision == LMA_PREC_MIXED ? 4 : static_cast<int64_t>(sizeof(float2)));
+                         (b->desc.precision == LMA_PREC_FP16_STORE ? 4 : static_cast<int64_t>(sizeof(float2)));
   out->phonon_batch = b->B;
   return LMA_OK;
 }
@@ -1729,7 +1735,7 @@ lma_status lma_exit_wave(lma_ctx* ctx, lma_basis* b, int64_t translate, float* o
     return fail(ctx, LMA_ERR_INVALID, "exit wave not current");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool dev = is_device_pointer(out);
-  if (b->desc.precision == LMA_PREC_MIXED) {
+  if (b->desc.precision == LMA_PREC_FP16_STORE) {
     const size_t hbytes = static_cast<size_t>(kW) * kW * sizeof(__half2);
     const char* src = static_cast<const char*>(b->d_U.p) + translate * hbytes;
     float scale = 1.f;
@@ -2299,7 +2305,7 @@ lma_status lma_image_coherent(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, cons
   const int nph = static_cast<int>(sp->ph.size());
   const int64_t nout = np * n_det;
   CUDA_TRY(ctx, ensure(b->d_acc, static_cast<size_t>(nout) * (static_cast<size_t>(n_var) * nph + 1) * sizeof(double)));
-  const bool half = b->desc.precision == LMA_PREC_MIXED;
+  const bool half = b->desc.precision == LMA_PREC_FP16_STORE;
   const bool recompute = (flags & LMA_IMAGE_RECOMPUTE) != 0;
   AutotuneScope tuning(ctx, (flags & LMA_IMAGE_AUTOTUNE) != 0);
   for (int phi0 = 0; phi0 < nph; phi0 += b->B) {
@@ -2376,7 +2382,7 @@ lma_status lma_image_partitioned(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, c
   if ((s = ensure_basis_tables(b, st)) != LMA_OK) return s;
   if ((s = build_detectors(b, det, n_det, st)) != LMA_OK) return s;
   if ((s = make_plan(b, region, desc)) != LMA_OK) return s;
-  const bool half = b->desc.precision == LMA_PREC_MIXED;
+  const bool half = b->desc.precision == LMA_PREC_FP16_STORE;
   const int64_t M = std::min<int64_t>(desc->max_resident, b->nT);   // entries in use never exceed |I_f|
   if (!b->plan_dev) {
     CUDA_TRY(ctx, ensure(b->d_plan, std::max<size_t>(4, b->plan_tab.size() * sizeof(int32_t))));
@@ -2779,42 +2785,12 @@ lma_status lma_readout_noalloc(lma_ctx* ctx, lma_basis* b, const float* exit_wav
                 "holds %zu bytes (about %lld probes at L = %d)",
                 static_cast<long long>(np), L, need, lma_dev::kNoAllocScratchBytes,
                 static_cast<long long>(lma_dev::kNoAllocScratchBytes / (L * 20 + 8 * n_det + 1)), L);
-  // host tables (FP64 coefficients rounded once, as in lma_image)
-  std::vector<int32_t> tidx(static_cast<size_t>(np) * L), sh(2 * static_cast<size_t>(np) * L);
-  std::vector<float> al(2 * static_cast<size_t>(np) * L);
-  const int half = (b->desc.det_window - b->desc.window) / 2;
-  for (int pb = 0; pb < region->npy; ++pb)
-    for (int pa = 0; pa < region->npx; ++pa) {
-      const int px = mod(region->px0 + pa * region->spacing_px[0], b->nx);
-      const int py = mod(region->py0 + pb * region->spacing_px[1], b->ny);
-      const CoefSet* cs = nullptr;
-      if ((s = coef_set(b, px, py, &cs)) != LMA_OK) return s;
-      const size_t base = (static_cast<size_t>(pb) * region->npx + pa) * L;
-      for (int j = 0; j < L; ++j) {
-        tidx[base + j] = static_cast<int32_t>(translate_index(b, px + cs->odx[j], py + cs->ody[j]));
-        al[2 * (base + j)] = static_cast<float>(cs->alpha[j].real());
-        al[2 * (base + j) + 1] = static_cast<float>(cs->alpha[j].imag());
-        sh[2 * (base + j)] = cs->odx[j] + half;
-        sh[2 * (base + j) + 1] = cs->ody[j] + half;
-      }
-    }
-  const lma_grid& g = b->spec->g;
-  const int D = b->desc.det_window;
-  const double dx = g.lx / g.nx, dy = g.ly / g.ny, lam = g.lambda, frac = g.bandlimit_frac;
-  std::vector<uint32_t> bits(static_cast<size_t>(n_det) * lma_dev::kThreads, 0u);
-  for (int d = 0; d < n_det; ++d)
-    for (int iy = 0; iy < D; ++iy) {
-      const int my = signed_index(iy, D);
-      const double ky = my / (D * dy);
-      for (int ix = 0; ix < D; ++ix) {
-        const int mx = signed_index(ix, D);
-        const double kx = mx / (D * dx);
-        const double ang = lam * std::sqrt(ky * ky + kx * kx);
-        const bool band = static_cast<double>(4 * (my * my + mx * mx)) <= frac * frac * D * D;
-        if (ang >= det[d].r1 && ang < det[d].r2 && band)
-          bits[static_cast<size_t>(d) * lma_dev::kThreads + ix + 128 * (iy & 3)] |= 1u << (iy >> 2);
-      }
-    }
+  // host tables and detector bits, built as lma_image builds them (FP64 coefficients rounded once)
+  std::vector<int32_t> tidx, sh;
+  std::vector<float> al;
+  if ((s = region_tables_host(b, region, tidx, al, sh)) != LMA_OK) return s;
+  std::vector<uint32_t> bits;
+  detector_bits_host(b, det, n_det, bits);
   void* scratch = nullptr;
   CUDA_TRY(ctx, lma_dev::noalloc_scratch(&scratch));
   char* base = static_cast<char*>(scratch);

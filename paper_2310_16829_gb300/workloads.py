@@ -37,7 +37,7 @@ BASIS_PROBE = 1
 BASIS_TRIG = 2
 BASIS_TRIG_RADIAL = 3
 PREC_C64 = 0
-PREC_MIXED = 1
+PREC_FP16_STORE = 1
 
 
 @dataclass
