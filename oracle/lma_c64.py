@@ -172,21 +172,26 @@ class LmaOracleC64(O.LmaOracle):
 
 
 def floor_scale(ref: np.ndarray, emu: np.ndarray) -> np.ndarray:
-    """kappa per detector row: max over the row's readings of |emu - ref| / sqrt(ref).
+    """kappa per detector row: the envelope of |emu - ref| / sqrt(ref) over the row's readings.
 
     A reading I = (1/n^2) sum_det |Psi|^2 perturbed by a white rounding noise dPsi changes by
     2 Re sum Psi* dPsi + sum |dPsi|^2, whose first term grows as sqrt(I) times the noise on
     the detector; kappa sqrt(I) is therefore the envelope of the complex64 error of a row.
+    kappa is the largest normalised error of the row, but at least three times its root mean
+    square, so that a row of few readings (whose largest error is a poor estimate of the
+    envelope) does not understate it.
     """
     ref = np.atleast_2d(np.asarray(ref, dtype=np.float64))
     ref = ref.reshape(ref.shape[0], -1)
     emu = np.asarray(emu, dtype=np.float64).reshape(ref.shape)
     pos = ref > 0
     q = np.where(pos, np.abs(emu - ref) / np.sqrt(np.where(pos, ref, 1.0)), 0.0)
-    return np.max(q, axis=1)
+    n = np.maximum(pos.sum(axis=1), 1)
+    rms = np.sqrt(np.sum(q * q, axis=1) / n)
+    return np.maximum(np.max(q, axis=1), 3.0 * rms)
 
 
-def floor_bound(ref: np.ndarray, emu: np.ndarray, tol: float, margin: float = 2.0) -> np.ndarray:
+def floor_bound(ref: np.ndarray, emu: np.ndarray, tol: float, margin: float = 3.0) -> np.ndarray:
     """Per reading: max(tol * ref, margin * kappa_row * sqrt(ref)), the larger of the relative
     bound and ``margin`` times the complex64 envelope of its detector row."""
     ref2 = np.atleast_2d(np.asarray(ref, dtype=np.float64))

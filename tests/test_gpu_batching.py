@@ -67,7 +67,7 @@ def test_batched_image_matches_oracle_sampled(ctx):
     pix = np.stack([w.region.px0 + sample[:, 0] * 4, w.region.py0 + sample[:, 1] * 4], axis=1)
     orc, emu = oracles(w)
     got = img[sample[:, 1], sample[:, 0]]
-    # 8-slice slab: weak HAADF readings, against twice the complex64 floor of the same pixels
+    # 8-slice slab: weak HAADF readings, against three times the complex64 floor of the same pixels
     assert_floor(got.reshape(1, -1), orc.image(w.detectors, pix), emu.image(w.detectors, pix),
                  label="batched")
 

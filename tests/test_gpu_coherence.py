@@ -35,7 +35,7 @@ def test_coherent_image_matches_oracle(ctx):
     probes = O.region_probes(250, 100, 5, 3, (4, 4), w.grid.nx, w.grid.ny)
     ref = orc.image_coherent(dets, probes, VARIANTS)
     # bright field: 1e-4 relative; the 6-slice slab's HAADF (1e-7..1e-6 of the beam) against
-    # twice the complex64 floor of the same focal series
+    # three times the complex64 floor of the same focal series
     assert np.max(np.abs(got[0] - ref[0]) / ref[0]) < 1e-4
     assert_floor(got, ref, emu.image_coherent(dets, probes, VARIANTS), label="coherent")
 

@@ -1,6 +1,6 @@
 """Edge cases of the GPU path against the FP64 oracle: free space (no atoms), the extreme
 numbers of input waves per probe (L = 1 and the maximum 64), a region of one probe, and a
-non-square grid. Tolerances as in the parity tests: 1e-4 relative per reading, or twice the
+non-square grid. Tolerances as in the parity tests: 1e-4 relative per reading, or three times the
 complex64 floor of the same image (``parity_floor``); exit waves to 5e-5 of their peak."""
 import dataclasses
 

@@ -2,7 +2,7 @@
 
 Tolerances. Detector readings are compared pixel by pixel with ``parity_floor.assert_floor``:
 1e-4 relative error, or, for a reading too weak for complex64 to reach that, no more than
-twice the envelope of the error that the oracle's pipeline restated in complex64
+three times the envelope of the error that the oracle's pipeline restated in complex64
 (``oracle.lma_c64``) makes on the same inputs. Bright and dark field are also held to the
 strict 1e-4 on their own. Intermediate arrays are held to tighter, derived bounds: the
 transmission t = exp(i sigma v) to 2e-6 absolute (|t| = 1, FP32 potential sum and sincos),
@@ -243,19 +243,19 @@ def test_perovskite_512_two_configurations_four_subregions(ctx):
 @pytest.mark.slow
 def test_perovskite_512_eight_phonons_subregion(ctx):
     """The benchmark workload in the launch configuration the benchmark times (512^2, 50
-    slices, 8 configurations, 128 x 128 probes, RECOMPUTE): a 16 x 16-probe block whose
-    windows wrap around the cell edge, averaged over all 8 configurations, against the
+    slices, 8 configurations, 128 x 128 probes, RECOMPUTE): the last 16 x 16-probe block,
+    whose windows wrap around the cell edge, averaged over all 8 configurations, against the
     oracle; the FP16 store on the same probes to its regression bound."""
     w = WL.perovskite_workload()
     spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
     basis = lma.Basis(ctx, spec, w.probe, w.basis)
     img = basis.image(w.detectors, w.region, recompute=True)
     assert np.all(np.isfinite(img)) and np.all(img > 0)
-    got, r, _ = _subregions(w, img, w.detectors, [(120, 120)], None, "512 eight configurations")
+    got, r, _ = _subregions(w, img, w.detectors, [(112, 112)], None, "512 eight configurations")
     w.basis.precision = WL.PREC_FP16_STORE
     bm = lma.Basis(ctx, spec, w.probe, w.basis)
     img_m = bm.image(w.detectors, w.region, recompute=True)
-    got_m = img_m[:, 120:136, 120:136].reshape(1, -1)
+    got_m = img_m[:, 112:128, 112:128].reshape(1, -1)
     assert _rel_pixel_err(got_m, r["ref"]) < FP16_STORE_HAADF_REGRESSION
 
 

@@ -2,7 +2,7 @@
 pixels) on the GPU against the FP64 oracle with the same kernel, and the Fourier path left
 intact afterwards.
 
-Tolerance: 1e-4 relative per reading, or twice the complex64 floor of the same image
+Tolerance: 1e-4 relative per reading, or three times the complex64 floor of the same image
 (``parity_floor``), with the oracle's real-space pipeline restated in complex64.
 """
 import numpy as np

@@ -1,7 +1,7 @@
 """GPU parity of the 3D STEM (rings) and 4D STEM (diffraction pattern) readouts of Sec. 3.1
 against the FP64 oracle, and their consistency with the 2D image of the same exit waves.
 
-Tolerance: 1e-4 relative per reading (ring reading or pattern pixel), or twice the
+Tolerance: 1e-4 relative per reading (ring reading or pattern pixel), or three times the
 complex64 floor of the same readout (``parity_floor``: the oracle's readout restated in
 complex64 on the same inputs); pixels outside the bandlimit are exactly zero on both sides.
 """
