@@ -66,9 +66,12 @@ typedef int32_t lma_status;
                                    nearest input waves; needs m_x, m_y >= 2n + 1. */
 
 #define LMA_PREC_C64 0         /* complex64 everywhere on the device */
-#define LMA_PREC_FP16_STORE 1       /* FP32 propagation; exit waves stored as FP16 pairs with a per-wave
+#define LMA_PREC_FP16_STORE 1  /* FP32 propagation; exit waves stored as FP16 pairs with a per-wave
                                   power-of-two scale: half the store; bright-field readings within
                                   1e-3, weak annular (HAADF) readings are not (FP16 rounding noise) */
+#define LMA_PREC_MIXED 2       /* the 32-point DFT stages of the slice step (Sec. 3.2 multislice step)
+                                  as split-FP16 (hi + lo) tensor-core products accumulated in FP32;
+                                  the other stages in FP32, exit waves stored in complex64 */
 
 #define LMA_EDIT_REMOVE 0      /* remove the atoms of a column */
 #define LMA_EDIT_SET_SPECIES 1 /* give the atoms of a column another species */
@@ -143,7 +146,7 @@ typedef struct {
   int32_t L;                 /* input waves per probe (I_{f,p,L}) */
   int32_t window;            /* W: propagation window X' = Y' (128) */
   int32_t det_window;        /* D: synthesis / detection window (128) */
-  int32_t precision;         /* LMA_PREC_C64 or LMA_PREC_FP16_STORE */
+  int32_t precision;         /* LMA_PREC_C64, LMA_PREC_FP16_STORE or LMA_PREC_MIXED */
   int32_t phonon_batch;      /* configurations propagated per launch and held at once;
                                 0 = as many as fit in 40 % of the free device memory */
   int32_t trig_degree;       /* LMA_BASIS_TRIG*: degree n of phi_n(t) = sum_{|k|<=n} e^{ikt} cos(k pi/(2n+2));

@@ -51,6 +51,8 @@ struct SliceJob {
   const float2* ex;            // [W] exp(-i pi lambda eps kx^2) / W^2
   const float2* ey;            // [W] exp(-i pi lambda eps ky^2)
   int r2max;                   // bandlimit: m'^2 + n'^2 <= r2max
+  float tc_in, tc_out;         // tensor-core DFT (k_slice_tc): power-of-two factor of the input
+                               // wave, and its inverse applied to the exit wave
 };
 
 // How the CTAs of a slice launch take their items.
@@ -70,6 +72,7 @@ struct SliceLaunch {
                                // entry out_index[i] of its slot (bounded store of a partition)
   int n_list;
   int* counter;                // kSliceDynamic: zeroed before the launch
+  int* status;                 // k_slice_tc: set to 1 when a bounded tensor-core wait gives up
 };
 
 // Steps a4-a6: synthesis, detector reading, FP64 accumulation over configurations.
@@ -126,6 +129,10 @@ cudaError_t launch_potential(const PotArgs& a, cudaStream_t s);
 // (kSliceDynamic zeroes a.counter on the stream first)
 cudaError_t launch_slice(const SliceLaunch& a, bool even_origins, bool half, int mode, cudaStream_t s);
 int sm_count();
+// step a3 with the 32-point DFT passes as split-FP16 tensor-core products (complex64 store):
+// persistent CTAs, one per SM; a.status must be set
+cudaError_t launch_slice_tc(const SliceLaunch& a, bool even_origins, cudaStream_t s);
+size_t slice_tc_smem_bytes();
 cudaError_t launch_synth(const SynthArgs& a, bool half, int mode, cudaStream_t s);
 // step a3 with the propagation as a periodic convolution with the K1 x K2 kernel q (device,
 // [K2][K1] complex64, offsets -(K/2) .. K/2); K1 in {3, 5, ..., 13}, K2 odd <= 25; complex64 store

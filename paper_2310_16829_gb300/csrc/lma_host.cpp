@@ -69,7 +69,9 @@ struct lma_ctx {
   void* list_slab = nullptr;
   int64_t alloc_base = 0;                                   // device allocations at profile reset
   std::vector<std::pair<void*, uint64_t>> capture_lists;   // lists read by the capture in progress
-  int* d_counter = nullptr;                                 // work counter of dynamic slice launches
+  int* d_counter = nullptr;                                 // [0] work counter of dynamic slice launches,
+                                                            // [1] status word of the tensor-core slice kernel
+  bool tc_launched = false;                                 // a tensor-core slice launch since the last check
   void* stage = nullptr;                                    // pinned staging buffer (kStageBytes)
   // slice launch modes: forced (>= 0), or the timed choice per launch shape
   int forced_mode = -1;
@@ -378,6 +380,8 @@ struct lma_basis {
   lma_basis_desc desc{};
   double gauss_sigma = 0.0;
   int trig_n = 0;              // degree n of the trigonometric input waves
+  int W = 128;                 // propagation window W = detection window D (pixels)
+  float tc_in = 1.f, tc_out = 1.f;   // input-wave factor of the tensor-core DFT passes and its inverse
   int nx = 0, ny = 0;
   int Sx = 0, Sy = 0, ox = 0, oy = 0, nax = 0, nay = 0;
   int64_t nT = 0;
@@ -460,14 +464,14 @@ void build_probe(lma_basis* b) {
 void build_input_wave(lma_basis* b) {
   const lma_grid& g = b->spec->g;
   const double dx = g.lx / g.nx, dy = g.ly / g.ny;
-  b->uW.assign(static_cast<size_t>(kW) * kW, cd(0.0, 0.0));
+  b->uW.assign(static_cast<size_t>(b->W) * b->W, cd(0.0, 0.0));
   if (b->desc.kind == LMA_BASIS_GAUSS) {
     const double s = b->gauss_sigma;
-    for (int y = 0; y < kW; ++y) {
-      const double ry = (y - kW / 2) * dy;
-      for (int x = 0; x < kW; ++x) {
-        const double rx = (x - kW / 2) * dx;
-        b->uW[static_cast<size_t>(y) * kW + x] = cd(std::exp(-(ry * ry + rx * rx) / (2.0 * s * s)), 0.0);
+    for (int y = 0; y < b->W; ++y) {
+      const double ry = (y - b->W / 2) * dy;
+      for (int x = 0; x < b->W; ++x) {
+        const double rx = (x - b->W / 2) * dx;
+        b->uW[static_cast<size_t>(y) * b->W + x] = cd(std::exp(-(ry * ry + rx * rx) / (2.0 * s * s)), 0.0);
       }
     }
   } else if (b->desc.kind == LMA_BASIS_TRIG || b->desc.kind == LMA_BASIS_TRIG_RADIAL) {
@@ -479,28 +483,28 @@ void build_input_wave(lma_basis* b) {
       return v;
     };
     if (b->desc.kind == LMA_BASIS_TRIG) {
-      std::vector<double> py(kW), px(kW);
-      for (int i = 0; i < kW; ++i) {
-        py[i] = phi(2.0 * kPi * (i - kW / 2) / g.ny);
-        px[i] = phi(2.0 * kPi * (i - kW / 2) / g.nx);
+      std::vector<double> py(b->W), px(b->W);
+      for (int i = 0; i < b->W; ++i) {
+        py[i] = phi(2.0 * kPi * (i - b->W / 2) / g.ny);
+        px[i] = phi(2.0 * kPi * (i - b->W / 2) / g.nx);
       }
-      for (int y = 0; y < kW; ++y)
-        for (int x = 0; x < kW; ++x) b->uW[static_cast<size_t>(y) * kW + x] = cd(py[y] * px[x], 0.0);
+      for (int y = 0; y < b->W; ++y)
+        for (int x = 0; x < b->W; ++x) b->uW[static_cast<size_t>(y) * b->W + x] = cd(py[y] * px[x], 0.0);
     } else {
-      for (int y = 0; y < kW; ++y) {
-        const double ry = (y - kW / 2) * dy;
-        for (int x = 0; x < kW; ++x) {
-          const double rx = (x - kW / 2) * dx;
-          b->uW[static_cast<size_t>(y) * kW + x] = cd(phi(2.0 * kPi * std::sqrt(ry * ry + rx * rx) / g.lx), 0.0);
+      for (int y = 0; y < b->W; ++y) {
+        const double ry = (y - b->W / 2) * dy;
+        for (int x = 0; x < b->W; ++x) {
+          const double rx = (x - b->W / 2) * dx;
+          b->uW[static_cast<size_t>(y) * b->W + x] = cd(phi(2.0 * kPi * std::sqrt(ry * ry + rx * rx) / g.lx), 0.0);
         }
       }
     }
   } else {
     build_probe(b);
-    for (int y = 0; y < kW; ++y)
-      for (int x = 0; x < kW; ++x)
-        b->uW[static_cast<size_t>(y) * kW + x] =
-            b->psi0[static_cast<size_t>(mod(y - kW / 2, g.ny)) * g.nx + mod(x - kW / 2, g.nx)];
+    for (int y = 0; y < b->W; ++y)
+      for (int x = 0; x < b->W; ++x)
+        b->uW[static_cast<size_t>(y) * b->W + x] =
+            b->psi0[static_cast<size_t>(mod(y - b->W / 2, g.ny)) * g.nx + mod(x - b->W / 2, g.nx)];
   }
 }
 
@@ -582,10 +586,10 @@ lma_status solve_set_for(lma_basis* b, const std::vector<cd>& psi0, CoefSet& cs)
   // bounding box of the union of windows [o - W/2, o + W/2)
   int ylo = 1 << 30, yhi = -(1 << 30), xlo = 1 << 30, xhi = -(1 << 30);
   for (int j = 0; j < L; ++j) {
-    ylo = std::min(ylo, cs.ody[j] - kW / 2);
-    yhi = std::max(yhi, cs.ody[j] + kW / 2);
-    xlo = std::min(xlo, cs.odx[j] - kW / 2);
-    xhi = std::max(xhi, cs.odx[j] + kW / 2);
+    ylo = std::min(ylo, cs.ody[j] - b->W / 2);
+    yhi = std::max(yhi, cs.ody[j] + b->W / 2);
+    xlo = std::min(xlo, cs.odx[j] - b->W / 2);
+    xhi = std::max(xhi, cs.odx[j] + b->W / 2);
   }
   if (yhi - ylo >= ny) {
     ylo = 0;
@@ -601,7 +605,7 @@ lma_status solve_set_for(lma_basis* b, const std::vector<cd>& psi0, CoefSet& cs)
     for (int xx = xlo; xx < xhi; ++xx) {
       bool any = false;
       for (int j = 0; j < L && !any; ++j)
-        any = mod(yy - (cs.ody[j] - kW / 2), ny) < kW && mod(xx - (cs.odx[j] - kW / 2), nx) < kW;
+        any = mod(yy - (cs.ody[j] - b->W / 2), ny) < b->W && mod(xx - (cs.odx[j] - b->W / 2), nx) < b->W;
       if (any) rows.push_back(static_cast<size_t>(mod(yy, ny)) * nx + mod(xx, nx));
     }
   const int m = static_cast<int>(rows.size());
@@ -612,8 +616,8 @@ lma_status solve_set_for(lma_basis* b, const std::vector<cd>& psi0, CoefSet& cs)
     in_rows[rows[i]] = 1;
     rhs[i] = psi0[rows[i]];
     for (int j = 0; j < L; ++j) {
-      const int ly = mod(gy - (cs.ody[j] - kW / 2), ny), lx = mod(gx - (cs.odx[j] - kW / 2), nx);
-      if (ly < kW && lx < kW) A[static_cast<size_t>(j) * m + i] = b->uW[static_cast<size_t>(ly) * kW + lx];
+      const int ly = mod(gy - (cs.ody[j] - b->W / 2), ny), lx = mod(gx - (cs.odx[j] - b->W / 2), nx);
+      if (ly < b->W && lx < b->W) A[static_cast<size_t>(j) * m + i] = b->uW[static_cast<size_t>(ly) * b->W + lx];
     }
   }
   std::vector<cd> A0 = A, rhs0 = rhs, x;
@@ -685,10 +689,20 @@ lma_status validate_region(lma_ctx* ctx, const lma_basis* b, const lma_region* r
 
 // device tables of a basis (input wave, propagator factors)
 // input wave and propagator factors on the device (no exit-wave store)
+// windows the device kernels implement (geometry and coefficients take every supported W)
+lma_status device_window(const lma_basis* b) {
+  if (b->W == kW) return LMA_OK;
+  return fail(b->ctx, LMA_ERR_UNSUPPORTED,
+              "window %d: the device path propagates and detects on W = D = %d windows; other windows are "
+              "supported by the host functions (coefficients, probe approximation) only", b->W, kW);
+}
+
 lma_status ensure_basis_tables(lma_basis* b, cudaStream_t st) {
   lma_ctx* ctx = b->ctx;
+  lma_status sw = device_window(b);
+  if (sw != LMA_OK) return sw;
   if (b->d_uW.p && b->d_ex.p && b->d_ey.p) return LMA_OK;
-  std::vector<float> uw(2 * static_cast<size_t>(kW) * kW);
+  std::vector<float> uw(2 * static_cast<size_t>(b->W) * b->W);
   for (size_t k = 0; k < b->uW.size(); ++k) {
     uw[2 * k] = static_cast<float>(b->uW[k].real());
     uw[2 * k + 1] = static_cast<float>(b->uW[k].imag());
@@ -713,7 +727,7 @@ lma_status ensure_basis_device(lma_basis* b, cudaStream_t st) {
   const bool half = b->desc.precision == LMA_PREC_FP16_STORE;
   const int nph = static_cast<int>(b->spec->ph.size());
   const lma_grid& g = b->spec->g;
-  const size_t u_cfg = static_cast<size_t>(b->nT) * kW * kW * (half ? 4 : sizeof(float2));
+  const size_t u_cfg = static_cast<size_t>(b->nT) * b->W * b->W * (half ? 4 : sizeof(float2));
   const size_t t_cfg = static_cast<size_t>(g.n_slices) * (g.nx + kW) * (g.ny + kW) * sizeof(float2);
   int B = b->desc.phonon_batch;
   if (B <= 0) {
@@ -923,6 +937,28 @@ lma_status upload_list(lma_ctx* ctx, const std::vector<int32_t>& list, cudaStrea
   return LMA_OK;
 }
 
+// the work counter and the status word of the slice launches, zeroed once
+lma_status ensure_counter(lma_ctx* ctx) {
+  if (ctx->d_counter) return LMA_OK;
+  CUDA_TRY(ctx, counted_malloc(reinterpret_cast<void**>(&ctx->d_counter), 2 * sizeof(int)));
+  CUDA_TRY(ctx, cudaMemset(ctx->d_counter, 0, 2 * sizeof(int)));
+  return LMA_OK;
+}
+
+// After a synchronizing read: did a tensor-core slice launch give up a bounded wait?
+// (The status word is read only when such a launch ran since the last check.)
+lma_status check_slice_status(lma_ctx* ctx) {
+  if (!ctx->tc_launched || !ctx->d_counter) return LMA_OK;
+  int st = 0;
+  CUDA_TRY(ctx, cudaMemcpy(&st, ctx->d_counter + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  ctx->tc_launched = false;
+  if (st != 0) {
+    CUDA_TRY(ctx, cudaMemset(ctx->d_counter + 1, 0, sizeof(int)));
+    return fail(ctx, LMA_ERR_TIMEOUT, "a tensor-core slice launch gave up waiting for its MMAs; results are invalid");
+  }
+  return LMA_OK;
+}
+
 lma_dev::SliceJob make_job(const lma_basis* b, const lma_specimen* sp) {
   const lma_grid& g = sp->g;
   lma_dev::SliceJob J{};
@@ -933,7 +969,7 @@ lma_dev::SliceJob make_job(const lma_basis* b, const lma_specimen* sp) {
   J.t_slot = t_slot_elems(g);
   J.uW = static_cast<const float2*>(b->d_uW.p);
   J.n_translates = static_cast<int>(b->nT);
-  J.u_slot = static_cast<size_t>(b->nT) * kW * kW;
+  J.u_slot = static_cast<size_t>(b->nT) * b->W * b->W;
   J.lat_ox = b->ox;
   J.lat_oy = b->oy;
   J.lat_sx = b->Sx;
@@ -946,14 +982,25 @@ lma_dev::SliceJob make_job(const lma_basis* b, const lma_specimen* sp) {
   J.ex = static_cast<const float2*>(b->d_ex.p);
   J.ey = static_cast<const float2*>(b->d_ey.p);
   J.r2max = b->r2max;
+  J.tc_in = b->tc_in;
+  J.tc_out = b->tc_out;
   return J;
 }
 
 // Issue one slice launch, in the forced, tuned or default mode. With autotuning on
 // and a shape not seen before, every mode runs once (each writes the same exit
 // waves) and is timed with events on the stream; the fastest is kept.
-lma_status slice_launch(lma_ctx* ctx, const lma_dev::SliceLaunch& L, bool even, bool half, int64_t units,
+lma_status slice_launch(lma_ctx* ctx, const lma_dev::SliceLaunch& L0, bool even, int prec, int64_t units,
                         cudaStream_t st) {
+  const bool half = prec == LMA_PREC_FP16_STORE;
+  lma_dev::SliceLaunch L = L0;
+  L.status = ctx->d_counter + 1;
+  if (prec == LMA_PREC_MIXED && ctx->rs_k1 == 0) {
+    // tensor-core DFT passes: one persistent launch shape (no mode to tune)
+    ctx->tc_launched = true;
+    CUDA_TRY(ctx, counted(ctx, K_SLICE, units, st, [&] { return lma_dev::launch_slice_tc(L, even, st); }));
+    return LMA_OK;
+  }
   std::vector<int64_t> key{half ? 1 : 0, even ? 1 : 0, L.n_jobs, L.n_list};
   for (int j = 0; j < L.n_jobs; ++j) {
     key.push_back(L.job[j].nx);
@@ -1022,12 +1069,13 @@ struct JobWork {
 lma_status propagate_jobs(lma_ctx* ctx, std::vector<JobWork>& work, cudaStream_t st) {
   if (!ctx->d_counter) {
     if (ctx->capturing) return fail(ctx, LMA_ERR_CUDA, "work counter missing during graph capture");
-    CUDA_TRY(ctx, counted_malloc(reinterpret_cast<void**>(&ctx->d_counter), sizeof(int)));
+    lma_status s0 = ensure_counter(ctx);
+    if (s0 != LMA_OK) return s0;
   }
-  for (int hv = 0; hv < 2; ++hv) {
+  for (int prec : {LMA_PREC_C64, LMA_PREC_FP16_STORE, LMA_PREC_MIXED}) {
     std::vector<JobWork*> group;
     for (JobWork& w : work)
-      if (!w.items.empty() && (w.b->desc.precision == LMA_PREC_FP16_STORE) == (hv == 1)) group.push_back(&w);
+      if (!w.items.empty() && w.b->desc.precision == prec) group.push_back(&w);
     for (size_t c0 = 0; c0 < group.size(); c0 += lma_dev::kMaxJobs) {
       const int nj = static_cast<int>(std::min<size_t>(lma_dev::kMaxJobs, group.size() - c0));
       for (int part = 0; part < 2; ++part) {
@@ -1051,7 +1099,7 @@ lma_status propagate_jobs(lma_ctx* ctx, std::vector<JobWork>& work, cudaStream_t
         if (s != LMA_OK) return s;
         L.n_list = static_cast<int>(list.size());
         L.counter = ctx->d_counter;
-        if ((s = slice_launch(ctx, L, even, hv == 1, units, st)) != LMA_OK) return s;
+        if ((s = slice_launch(ctx, L, even, prec, units, st)) != LMA_OK) return s;
       }
     }
   }
@@ -1337,8 +1385,8 @@ lma_status images_work(lma_ctx* ctx, const std::vector<ImageJob>& jobs, const Re
       a.n_cfg = nb;
       a.cfg_base = batch[k].first;
       a.n_translates = static_cast<int>(b->nT);
-      a.u_slot = static_cast<size_t>(b->nT) * kW * kW;
-      a.cyclic = (b->nx == kW && b->ny == kW) ? 1 : 0;
+      a.u_slot = static_cast<size_t>(b->nT) * b->W * b->W;
+      a.cyclic = (b->nx == b->W && b->ny == b->W) ? 1 : 0;
       a.det_bits = static_cast<const uint32_t*>(b->d_det.p);
       a.n_det = ro.n_out;
       a.acc = static_cast<double*>(b->d_acc.p);
@@ -1570,7 +1618,10 @@ lma_status lma_transmission(lma_ctx* ctx, lma_specimen* sp, int32_t phonon, floa
                                     static_cast<size_t>(g.nx) * sizeof(float2), g.ny,
                                     dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   }
-  if (!dev) CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if (!dev) {
+    CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    return check_slice_status(ctx);
+  }
   return LMA_OK;
 }
 
@@ -1579,9 +1630,10 @@ lma_status lma_create_basis(lma_ctx* ctx, const lma_specimen* spec, const lma_pr
   if (!ctx || !spec || !probe || !desc || !out) return fail(ctx, LMA_ERR_INVALID, "null argument");
   const lma_grid& g = spec->g;
   const lma_basis_desc& d = *desc;
-  if (d.window != kW || d.det_window != kW)
-    return fail(ctx, LMA_ERR_UNSUPPORTED, "window and det_window must be %d", kW);
-  if (g.nx < kW || g.ny < kW) return fail(ctx, LMA_ERR_UNSUPPORTED, "grid smaller than the window");
+  if (d.window != 64 && d.window != 128 && d.window != 256)
+    return fail(ctx, LMA_ERR_UNSUPPORTED, "window must be 64, 128 or 256 pixels");
+  if (d.det_window != d.window) return fail(ctx, LMA_ERR_UNSUPPORTED, "det_window must equal window");
+  if (g.nx < d.window || g.ny < d.window) return fail(ctx, LMA_ERR_UNSUPPORTED, "grid smaller than the window");
   if (!is_pow2(g.nx) || !is_pow2(g.ny)) return fail(ctx, LMA_ERR_UNSUPPORTED, "grid sizes must be powers of two");
   if (d.kind != LMA_BASIS_GAUSS && d.kind != LMA_BASIS_PROBE && d.kind != LMA_BASIS_TRIG &&
       d.kind != LMA_BASIS_TRIG_RADIAL)
@@ -1591,8 +1643,8 @@ lma_status lma_create_basis(lma_ctx* ctx, const lma_specimen* spec, const lma_pr
     return fail(ctx, LMA_ERR_INVALID, "coef_mode must be LMA_COEF_LSQ or LMA_COEF_TRIG_CLOSED");
   if (d.coef_mode == LMA_COEF_TRIG_CLOSED && d.kind != LMA_BASIS_TRIG)
     return fail(ctx, LMA_ERR_INVALID, "closed-form coefficients need the tensor trigonometric input waves (LMA_BASIS_TRIG)");
-  if (d.precision != LMA_PREC_C64 && d.precision != LMA_PREC_FP16_STORE)
-    return fail(ctx, LMA_ERR_INVALID, "precision must be LMA_PREC_C64 or LMA_PREC_FP16_STORE");
+  if (d.precision != LMA_PREC_C64 && d.precision != LMA_PREC_FP16_STORE && d.precision != LMA_PREC_MIXED)
+    return fail(ctx, LMA_ERR_INVALID, "precision must be LMA_PREC_C64, LMA_PREC_FP16_STORE or LMA_PREC_MIXED");
   if (!(probe->alpha_max > 0)) return fail(ctx, LMA_ERR_INVALID, "alpha_max must be positive");
   const int sx = d.in_spacing_px[0], sy = d.in_spacing_px[1];
   if (sx <= 0 || sy <= 0 || g.nx % sx || g.ny % sy)
@@ -1628,23 +1680,33 @@ lma_status lma_create_basis(lma_ctx* ctx, const lma_specimen* spec, const lma_pr
   b->nay = g.ny / b->Sy;
   b->nT = nT;
   b->trig_n = trig_n;
+  b->W = d.window;
   build_input_wave(b);
+  {
+    // tensor-core DFT passes: a power of two bringing the input wave's norm into (2^10, 2^11],
+    // times the 2^7 that each transmission takes back (the propagator carries 2^-7, not 1/W^2)
+    double n2 = 0.0;
+    for (const cd& z : b->uW) n2 += std::norm(z);
+    const int e = n2 > 0.0 ? static_cast<int>(std::ceil(0.5 * std::log2(n2))) : 0;
+    b->tc_in = std::ldexp(1.0f, 11 - e + 7);
+    b->tc_out = std::ldexp(1.0f, -(11 - e + 7));
+  }
   // propagator factors on the W-grid: exp(-i pi lambda eps k^2); 1/W^2 folded into e_x
   const double dx = g.lx / g.nx, dy = g.ly / g.ny;
-  b->ex.resize(2 * kW);
-  b->ey.resize(2 * kW);
-  for (int m = 0; m < kW; ++m) {
-    const double kx = signed_index(m, kW) / (kW * dx);
-    const double ky = signed_index(m, kW) / (kW * dy);
+  b->ex.resize(2 * b->W);
+  b->ey.resize(2 * b->W);
+  for (int m = 0; m < b->W; ++m) {
+    const double kx = signed_index(m, b->W) / (b->W * dx);
+    const double ky = signed_index(m, b->W) / (b->W * dy);
     const double px = -kPi * g.lambda * g.slice_dz * kx * kx;
     const double py = -kPi * g.lambda * g.slice_dz * ky * ky;
-    const double sc = 1.0 / (static_cast<double>(kW) * kW);
+    const double sc = 1.0 / (static_cast<double>(b->W) * b->W);
     b->ex[2 * m] = static_cast<float>(std::cos(px) * sc);
     b->ex[2 * m + 1] = static_cast<float>(std::sin(px) * sc);
     b->ey[2 * m] = static_cast<float>(std::cos(py));
     b->ey[2 * m + 1] = static_cast<float>(std::sin(py));
   }
-  b->r2max = bandlimit_r2(g.bandlimit_frac, kW);
+  b->r2max = bandlimit_r2(g.bandlimit_frac, b->W);
   *out = b;
   return LMA_OK;
 }
@@ -1683,7 +1745,7 @@ lma_status lma_basis_get_info(const lma_basis* b, lma_basis_info* out) {
   out->window = b->desc.window;
   out->det_window = b->desc.det_window;
   out->gauss_sigma = b->gauss_sigma;
-  out->exit_wave_bytes = b->nT * static_cast<int64_t>(kW) * kW *
+  out->exit_wave_bytes = b->nT * static_cast<int64_t>(b->W) * b->W *
                          (b->desc.precision == LMA_PREC_FP16_STORE ? 4 : static_cast<int64_t>(sizeof(float2)));
   out->phonon_batch = b->B;
   return LMA_OK;
@@ -1736,7 +1798,7 @@ lma_status lma_exit_wave(lma_ctx* ctx, lma_basis* b, int64_t translate, float* o
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool dev = is_device_pointer(out);
   if (b->desc.precision == LMA_PREC_FP16_STORE) {
-    const size_t hbytes = static_cast<size_t>(kW) * kW * sizeof(__half2);
+    const size_t hbytes = static_cast<size_t>(b->W) * b->W * sizeof(__half2);
     const char* src = static_cast<const char*>(b->d_U.p) + translate * hbytes;
     float scale = 1.f;
     CUDA_TRY(ctx, cudaMemcpyAsync(&scale, static_cast<const float*>(b->d_Uscale.p) + translate, sizeof(float),
@@ -1746,7 +1808,7 @@ lma_status lma_exit_wave(lma_ctx* ctx, lma_basis* b, int64_t translate, float* o
       CUDA_TRY(ctx, lma_dev::launch_expand_half(src, scale, reinterpret_cast<float2*>(out), st));
       return LMA_OK;
     }
-    std::vector<__half2> h(static_cast<size_t>(kW) * kW);
+    std::vector<__half2> h(static_cast<size_t>(b->W) * b->W);
     CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), src, hbytes, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(ctx, cudaStreamSynchronize(st));
     for (size_t k = 0; k < h.size(); ++k) {
@@ -1756,10 +1818,13 @@ lma_status lma_exit_wave(lma_ctx* ctx, lma_basis* b, int64_t translate, float* o
     }
     return LMA_OK;
   }
-  const size_t bytes = static_cast<size_t>(kW) * kW * sizeof(float2);
+  const size_t bytes = static_cast<size_t>(b->W) * b->W * sizeof(float2);
   CUDA_TRY(ctx, cudaMemcpyAsync(out, static_cast<const char*>(b->d_U.p) + translate * bytes, bytes,
                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-  if (!dev) CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if (!dev) {
+    CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    return check_slice_status(ctx);
+  }
   return LMA_OK;
 }
 
@@ -1785,6 +1850,7 @@ lma_status lma_image(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, const lma_det
     const int64_t nout = b->reg.n_probes * n_det;
     const double* fin = static_cast<const double*>(b->d_acc.p) + static_cast<size_t>(sp->ph.size()) * nout;
     CUDA_TRY(ctx, read_back(ctx, out, fin, static_cast<size_t>(nout) * sizeof(double), st));
+    { const lma_status cs_ = check_slice_status(ctx); if (cs_ != LMA_OK) return cs_; }
   }
   CUDA_TRY(ctx, cudaGetLastError());
   return LMA_OK;
@@ -2097,17 +2163,17 @@ static lma_status make_plan(lma_basis* b, const lma_region* r, const lma_partiti
 static void realspace_kernel_host(const lma_basis* b, int K1, int K2, std::vector<float>& q) {
   const lma_grid& g = b->spec->g;
   const double dx = g.lx / g.nx, dy = g.ly / g.ny;
-  std::vector<cd> root(kW);
-  for (int m = 0; m < kW; ++m) root[m] = std::exp(cd(0.0, 2.0 * kPi * m / kW));
-  std::vector<cd> P(static_cast<size_t>(kW) * kW, cd(0.0, 0.0));
-  for (int iy = 0; iy < kW; ++iy) {
-    const int my = signed_index(iy, kW);
-    const double ky = my / (kW * dy);
-    for (int ix = 0; ix < kW; ++ix) {
-      const int mx = signed_index(ix, kW);
+  std::vector<cd> root(b->W);
+  for (int m = 0; m < b->W; ++m) root[m] = std::exp(cd(0.0, 2.0 * kPi * m / b->W));
+  std::vector<cd> P(static_cast<size_t>(b->W) * b->W, cd(0.0, 0.0));
+  for (int iy = 0; iy < b->W; ++iy) {
+    const int my = signed_index(iy, b->W);
+    const double ky = my / (b->W * dy);
+    for (int ix = 0; ix < b->W; ++ix) {
+      const int mx = signed_index(ix, b->W);
       if (my * my + mx * mx > b->r2max) continue;
-      const double kx = mx / (kW * dx);
-      P[static_cast<size_t>(iy) * kW + ix] = std::exp(cd(0.0, -kPi * g.lambda * g.slice_dz * (ky * ky + kx * kx)));
+      const double kx = mx / (b->W * dx);
+      P[static_cast<size_t>(iy) * b->W + ix] = std::exp(cd(0.0, -kPi * g.lambda * g.slice_dz * (ky * ky + kx * kx)));
     }
   }
   q.assign(2 * static_cast<size_t>(K1) * K2, 0.f);
@@ -2116,10 +2182,10 @@ static void realspace_kernel_host(const lma_basis* b, int K1, int K2, std::vecto
     for (int c = 0; c < K1; ++c) {
       const int ox = c - K1 / 2;
       cd sum(0.0, 0.0);
-      for (int iy = 0; iy < kW; ++iy)
-        for (int ix = 0; ix < kW; ++ix)
-          sum += P[static_cast<size_t>(iy) * kW + ix] * root[mod(iy * oy + ix * ox, kW)];
-      sum /= static_cast<double>(kW) * kW;
+      for (int iy = 0; iy < b->W; ++iy)
+        for (int ix = 0; ix < b->W; ++ix)
+          sum += P[static_cast<size_t>(iy) * b->W + ix] * root[mod(iy * oy + ix * ox, b->W)];
+      sum /= static_cast<double>(b->W) * b->W;
       q[2 * (static_cast<size_t>(a) * K1 + c)] = static_cast<float>(sum.real());
       q[2 * (static_cast<size_t>(a) * K1 + c) + 1] = static_cast<float>(sum.imag());
     }
@@ -2177,6 +2243,7 @@ lma_status lma_image_realspace(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, int
   if (!dev_out) {
     const int64_t nout = b->reg.n_probes * n_det;
     CUDA_TRY(ctx, read_back(ctx, out, basis_result(b, sp, n_det), static_cast<size_t>(nout) * sizeof(double), st));
+    { const lma_status cs_ = check_slice_status(ctx); if (cs_ != LMA_OK) return cs_; }
   }
   CUDA_TRY(ctx, cudaGetLastError());
   return LMA_OK;
@@ -2328,8 +2395,8 @@ lma_status lma_image_coherent(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, cons
       a.n_cfg = nb;
       a.cfg_base = phi0;
       a.n_translates = static_cast<int>(b->nT);
-      a.u_slot = static_cast<size_t>(b->nT) * kW * kW;
-      a.cyclic = (b->nx == kW && b->ny == kW) ? 1 : 0;
+      a.u_slot = static_cast<size_t>(b->nT) * b->W * b->W;
+      a.cyclic = (b->nx == b->W && b->ny == b->W) ? 1 : 0;
       a.det_bits = static_cast<const uint32_t*>(b->d_det.p);
       a.n_det = n_det;
       a.acc = static_cast<double*>(b->d_acc.p) + static_cast<size_t>(v) * nph * nout;
@@ -2344,7 +2411,10 @@ lma_status lma_image_coherent(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, cons
   double* fin = dev_out ? out : static_cast<double*>(b->d_acc.p) + static_cast<size_t>(n_var) * nph * nout;
   CUDA_TRY(ctx, counted(ctx, K_FIN, nout, st,
                         [&] { return lma_dev::launch_finalize_variants(acc, nout, nph, n_var, wdev, fin, st); }));
-  if (!dev_out) CUDA_TRY(ctx, read_back(ctx, out, fin, static_cast<size_t>(nout) * sizeof(double), st));
+  if (!dev_out) {
+    CUDA_TRY(ctx, read_back(ctx, out, fin, static_cast<size_t>(nout) * sizeof(double), st));
+    { const lma_status cs_ = check_slice_status(ctx); if (cs_ != LMA_OK) return cs_; }
+  }
   CUDA_TRY(ctx, cudaGetLastError());
   return LMA_OK;
 }
@@ -2389,9 +2459,9 @@ lma_status lma_image_partitioned(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, c
     CUDA_TRY(ctx, upload(ctx, b->d_plan.p, b->plan_tab.data(), b->plan_tab.size() * sizeof(int32_t), st));
     b->plan_dev = true;
   }
-  CUDA_TRY(ctx, ensure(b->d_Up, static_cast<size_t>(M) * kW * kW * (half ? 4 : sizeof(float2))));
+  CUDA_TRY(ctx, ensure(b->d_Up, static_cast<size_t>(M) * b->W * b->W * (half ? 4 : sizeof(float2))));
   if (half) CUDA_TRY(ctx, ensure(b->d_Upscale, static_cast<size_t>(M) * sizeof(float)));
-  if (!ctx->d_counter) CUDA_TRY(ctx, counted_malloc(reinterpret_cast<void**>(&ctx->d_counter), sizeof(int)));
+  if (!ctx->d_counter && (s = ensure_counter(ctx)) != LMA_OK) return s;
   const int nph = static_cast<int>(sp->ph.size());
   const int64_t np = static_cast<int64_t>(region->npx) * region->npy;
   const int64_t nout = np * n_det;
@@ -2409,7 +2479,7 @@ lma_status lma_image_partitioned(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, c
       Lh.job[0].U = half ? nullptr : static_cast<float2*>(b->d_Up.p);
       Lh.job[0].Uh = half ? b->d_Up.p : nullptr;
       Lh.job[0].Uscale = half ? static_cast<float*>(b->d_Upscale.p) : nullptr;
-      Lh.job[0].u_slot = static_cast<size_t>(M) * kW * kW;
+      Lh.job[0].u_slot = static_cast<size_t>(M) * b->W * b->W;
       Lh.counter = ctx->d_counter;
       for (int part = 0; part < 2; ++part) {
         const int off = part == 0 ? 0 : P.n_even;
@@ -2420,7 +2490,7 @@ lma_status lma_image_partitioned(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, c
         Lh.n_list = cnt;
         Lh.start[0] = 0;
         Lh.start[1] = cnt;
-        if ((s = slice_launch(ctx, Lh, part == 0, half, static_cast<int64_t>(cnt) * sp->g.n_slices, st)) != LMA_OK)
+        if ((s = slice_launch(ctx, Lh, part == 0, b->desc.precision, static_cast<int64_t>(cnt) * sp->g.n_slices, st)) != LMA_OK)
           return s;
       }
       lma_dev::SynthArgs a{};
@@ -2440,8 +2510,8 @@ lma_status lma_image_partitioned(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, c
       a.n_cfg = 1;
       a.cfg_base = phi;
       a.n_translates = static_cast<int>(M);
-      a.u_slot = static_cast<size_t>(M) * kW * kW;
-      a.cyclic = (b->nx == kW && b->ny == kW) ? 1 : 0;
+      a.u_slot = static_cast<size_t>(M) * b->W * b->W;
+      a.cyclic = (b->nx == b->W && b->ny == b->W) ? 1 : 0;
       a.det_bits = static_cast<const uint32_t*>(b->d_det.p);
       a.n_det = n_det;
       a.acc = static_cast<double*>(b->d_acc.p);
@@ -2454,7 +2524,10 @@ lma_status lma_image_partitioned(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, c
   const bool dev_out = is_device_pointer(out);
   double* fin = dev_out ? out : static_cast<double*>(b->d_acc.p) + static_cast<size_t>(nph) * nout;
   CUDA_TRY(ctx, counted(ctx, K_FIN, nout, st, [&] { return lma_dev::launch_finalize(acc, nout, nph, 1.0 / nph, fin, st); }));
-  if (!dev_out) CUDA_TRY(ctx, read_back(ctx, out, fin, static_cast<size_t>(nout) * sizeof(double), st));
+  if (!dev_out) {
+    CUDA_TRY(ctx, read_back(ctx, out, fin, static_cast<size_t>(nout) * sizeof(double), st));
+    { const lma_status cs_ = check_slice_status(ctx); if (cs_ != LMA_OK) return cs_; }
+  }
   CUDA_TRY(ctx, cudaGetLastError());
   return LMA_OK;
 }
@@ -2475,6 +2548,7 @@ static lma_status image_readout(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, co
   if (!dev_out) {
     const void* fin = ro.mode == lma_dev::kReadPattern ? b->d_pat.p : static_cast<const void*>(basis_result(b, sp, ro.n_out));
     CUDA_TRY(ctx, read_back(ctx, out, fin, out_bytes, st));
+    { const lma_status cs_ = check_slice_status(ctx); if (cs_ != LMA_OK) return cs_; }
   }
   CUDA_TRY(ctx, cudaGetLastError());
   return LMA_OK;
@@ -2559,6 +2633,7 @@ lma_status lma_image_many(lma_ctx* ctx, int32_t n, lma_specimen* const* specs, l
         const int64_t nout = bases[k]->reg.n_probes * n_det;
         const double* fin = static_cast<const double*>(bases[k]->d_acc.p) + specs[k]->ph.size() * nout;
         CUDA_TRY(ctx, read_back(ctx, outs[k], fin, static_cast<size_t>(nout) * sizeof(double), st));
+        { const lma_status cs_ = check_slice_status(ctx); if (cs_ != LMA_OK) return cs_; }
       }
     CUDA_TRY(ctx, cudaStreamSynchronize(st));
     return LMA_OK;
@@ -2732,8 +2807,8 @@ lma_status lma_edit_column(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, double 
         return d < aw || mod(a0 - b0, n) < bw;
       };
       for (int ib = 0; ib < b->nay; ++ib) {
-        const int wy0 = mod(b->oy + ib * b->Sy - kW / 2, g.ny);
-        if (!meets(wy0, kW, r.y0, r.h, g.ny)) continue;
+        const int wy0 = mod(b->oy + ib * b->Sy - b->W / 2, g.ny);
+        if (!meets(wy0, b->W, r.y0, r.h, g.ny)) continue;
         for (int ia = 0; ia < b->nax; ++ia) {
           const int wx0 = mod(b->ox + ia * b->Sx - kW / 2, g.nx);
           if (!meets(wx0, kW, r.x0, r.w, g.nx)) continue;
@@ -2766,6 +2841,7 @@ lma_status lma_readout_noalloc(lma_ctx* ctx, lma_basis* b, const float* exit_wav
   lma_status s = validate_region(ctx, b, region);
   if (s != LMA_OK) return s;
   if (!device_ready(ctx)) return fail(ctx, LMA_ERR_UNSUPPORTED, "no device in this context");
+  if ((s = device_window(b)) != LMA_OK) return s;
   if (!is_device_pointer(exit_waves) || !is_device_pointer(out))
     return fail(ctx, LMA_ERR_INVALID, "exit_waves and out must be device memory");
   const int L = b->desc.L;
@@ -2814,7 +2890,7 @@ lma_status lma_readout_noalloc(lma_ctx* ctx, lma_basis* b, const float* exit_wav
   a.cfg_base = 0;
   a.n_translates = static_cast<int>(b->nT);
   a.u_slot = 0;
-  a.cyclic = (b->nx == kW && b->ny == kW) ? 1 : 0;
+  a.cyclic = (b->nx == b->W && b->ny == b->W) ? 1 : 0;
   a.det_bits = reinterpret_cast<const uint32_t*>(base + o_det);
   a.n_det = n_det;
   a.acc = reinterpret_cast<double*>(base + o_acc);

@@ -33,6 +33,8 @@
 #include <cuda_fp16.h>
 
 #include <cstdio>
+#include <cstring>
+#include <vector>
 #include <mutex>
 #include <type_traits>
 
@@ -652,6 +654,441 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
     }
     __syncthreads();  // the table, s_wmax and s_next are rewritten by the next item
   }
+}
+
+// ------------------------------------------------------------------------------------------
+// step a3 with the 32-point DFT passes on the tensor cores (precision LMA_PREC_MIXED)
+// ------------------------------------------------------------------------------------------
+// Passes A and C of k_slice are 32-point DFTs of 512 rows of 32 complex values each (rows
+// (y, r) in pass A, rows (kx, k1y) in pass C): as a product, Y = X F with F[n][k] = W_32^(n k),
+// a [512 x 32] x [32 x 32] complex GEMM. In real form, row [Re x | Im x] (K = 64) times
+// B = [[Re F, Im F], [-Im F, Re F]] (64 x 64) gives [Re y | Im y]. Each operand is split into
+// FP16 parts, x = x_hi + x_lo (x_hi = fp16(x), x_lo = fp16(x - x_hi)), and the product is
+// taken as x_lo F_hi + x_hi F_lo + x_hi F_hi with FP32 accumulation in tensor memory (the
+// x_lo F_lo term, 2^-22 of the product, is dropped): tcgen05.mma kind::f16, M = 128 rows per
+// tile, four tiles per pass. The inverse DFT (conj F) uses the 32 x 32 sub-blocks of the same
+// B: Re y = Re x Re F + Im x Im F, Im y = -Re x Im F + Im x Re F. Pass B, the transmission
+// and the propagator products stay on the CUDA cores in FP32, as in k_slice.
+//
+// Scale. FP16 holds 11 significant bits between 2^-14 and 65504. The wave enters with a
+// power-of-two scale that brings its norm to (2^10, 2^11]; |t| = 1 and the bandlimited
+// propagator has modulus <= 1, so the norm never grows. Every GEMM operand is bounded by
+// the norm of its array: 2^11 before pass A, sqrt(512) 2^11 < 65504 before pass C, and with
+// the propagator scaled by 2^-7 (instead of 2^-14 = 1/W^2) 2^11 before the inverse pass C
+// and sqrt(512) 2^11 before the inverse pass A; the remaining 2^-7 is applied with the next
+// transmission. Typical magnitudes (norm / 128) stay above 16, so the FP16 low parts are
+// normal numbers almost everywhere.
+//
+// Shared memory: the A operand of tile t (rows 128 t .. 128 t + 127, FP16 high and low parts,
+// 2 x 16 KiB) lies inside the exchange-table rows of the same 128 threads, which the pass-B
+// exchanges use at other times; B (high and low, 2 x 8 KiB) has its own space. Operands are
+// K-major without swizzle: core matrices of 8 rows x 16 bytes, 128 bytes apart along K and
+// 1024 bytes apart along the rows.
+namespace tc {
+
+constexpr uint32_t kTileBytes = 128 * kXP * 8;               // 128 table rows of kXP float2
+static_assert(kTileBytes == 34816, "a tile's table rows");
+constexpr uint32_t kHalfBytes = 16384;                        // one FP16 part of a 128 x 64 tile
+constexpr int kTmemCols = 256;                                // 4 tiles x 64 FP32 columns
+constexpr uint32_t kBBytes = 8192;                            // one FP16 part of B (64 x 64)
+constexpr float kPropScale = 128.f;                           // 2^-7 / 2^-14: propagator factor
+constexpr float kTransScale = 1.f / 128.f;                    // 2^-7 with each transmission
+constexpr int kWaitLimit = 1 << 22;                           // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// byte offset of element (row, k) in a no-swizzle K-major operand with K = 64 FP16
+__host__ __device__ constexpr uint32_t op_offset(int row, int k) {
+  return static_cast<uint32_t>((row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+// shared-memory matrix descriptor: start, leading (K) byte offset 128, stride (row-group)
+// byte offset 1024, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return static_cast<uint64_t>((saddr >> 4) & 0x3FFF) | (static_cast<uint64_t>(128 >> 4) << 16) |
+         (static_cast<uint64_t>(1024 >> 4) << 32) | (static_cast<uint64_t>(1) << 46);
+}
+// instruction descriptor of kind::f16: FP32 accumulator, FP16 A and B, both K-major
+__host__ __device__ constexpr uint32_t idesc(int M, int N) {
+  return (1u << 4) | (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+// wait for the given phase of the mbarrier, giving up after kWaitLimit polls
+__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t phase) {
+  uint32_t done = 0;
+  for (int it = 0; it < kWaitLimit && !done; ++it)
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(phase)
+        : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// the 64 FP32 columns of this thread's TMEM lane from column c: y[k] = (col k, col 32 + k)
+__device__ __forceinline__ void load_row(uint32_t taddr, float2 (&y)[32]) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,"
+      "%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 32; ++k) y[k] = make_float2(__uint_as_float(r[k]), __uint_as_float(r[32 + k]));
+}
+
+// Row `row` of a tile's A operand from x: K index k < 32 holds Re x[k], k >= 32 Im x[k - 32];
+// high parts to `hi`, low parts to `lo` (16-byte stores: a quarter-warp's 8 rows fill 128
+// contiguous bytes)
+__device__ __forceinline__ void store_row(unsigned char* hi, unsigned char* lo, const float2 (&x)[32], int row) {
+  const uint32_t base = op_offset(row, 0);
+#pragma unroll
+  for (int kb = 0; kb < 8; ++kb) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int n = (kb & 3) * 8 + 2 * q;
+      const float a = kb < 4 ? x[n].x : x[n].y;
+      const float b = kb < 4 ? x[n + 1].x : x[n + 1].y;
+      const __half2 hh = __floats2half2_rn(a, b);
+      const float2 hf = __half22float2(hh);
+      const __half2 ll = __floats2half2_rn(a - hf.x, b - hf.y);
+      h[q] = *reinterpret_cast<const uint32_t*>(&hh);
+      l[q] = *reinterpret_cast<const uint32_t*>(&ll);
+    }
+    *reinterpret_cast<uint4*>(hi + base + kb * 128) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(lo + base + kb * 128) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+// the MMAs of one pass over the four tiles: forward D = A B (N = 64), inverse by sub-blocks
+// (N = 32); products lo x hi, hi x lo, hi x hi, the first overwriting D
+template <bool INV>
+__device__ __forceinline__ void issue_pass(uint32_t smA, uint32_t smB, uint32_t tmem) {
+  // descriptors differ only in their start-address field: base descriptor + (offset >> 4)
+  // (every operand lies below 256 KiB, so the 14-bit field never carries)
+  const uint64_t dB = sdesc(smB), dA = sdesc(smA);
+  constexpr uint64_t kLo = kHalfBytes >> 4, kBLo = kBBytes >> 4;
+#pragma unroll 1
+  for (int t = 0; t < 4; ++t) {
+    const uint64_t aH = dA + ((t * kTileBytes) >> 4);
+    const uint32_t d = tmem + 64 * t;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      // products lo x hi, hi x lo, hi x hi
+      const uint64_t a0 = p == 0 ? aH + kLo : aH;
+      const uint64_t b0 = p == 1 ? dB + kBLo : dB;
+      if constexpr (!INV) {
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          mma(d, a0 + kk * 16, b0 + kk * 16, idesc(128, 64), (p > 0 || kk > 0) ? 1u : 0u);
+      } else {
+        // Re y (columns 0..31) and Im y (32..63), each from Re x (K blocks 0, 1) and Im x (2, 3)
+#pragma unroll
+        for (int hv = 0; hv < 2; ++hv)
+#pragma unroll
+          for (int src = 0; src < 2; ++src)
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk)
+              mma(d + 32 * hv, a0 + (src * 2 + kk) * 16, b0 + src * 256 + (hv * 2 + kk) * 16, idesc(128, 32),
+                  (p > 0 || src > 0 || kk > 0) ? 1u : 0u);
+      }
+    }
+  }
+}
+
+}  // namespace tc
+
+// B operands of the 32-point DFT, high and low FP16 parts in the operand layout (built on the
+// host in FP64: B^T[n][k], n the output column of [Re y | Im y], k the input of [Re x | Im x])
+__device__ __align__(16) unsigned char g_tc_dft32[2 * tc::kBBytes];
+
+constexpr int kSliceTcSmemBytes = kXRows * 8 + 2 * tc::kBBytes + 64 * 16 + 128 * 8 + kPTab * 8 + 64;
+
+// One translate per CTA at a time (persistent CTAs, item li = blockIdx + k gridDim); the
+// exit waves are complex64. status: set to 1 when a tensor-core wait gives up.
+template <bool EVEN, bool PRUNE>
+__global__ void __launch_bounds__(kThreads, 1) k_slice_tc(const SliceLaunch a, int* status) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  float2* X = reinterpret_cast<float2*>(smraw);                                   // exchange table
+  unsigned char* const sB = smraw + kXRows * 8;                                   // B hi, B lo
+  float4* twr = reinterpret_cast<float4*>(sB + 2 * tc::kBBytes);
+  float2* twB = reinterpret_cast<float2*>(twr + 64);
+  float2* ptab = twB + 128;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(ptab + kPTab);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+
+  const int T = threadIdx.x, warp = T >> 5, lane = T & 31;
+  if (T < 128) twB[T] = c_w128[((T >> 2) * (T & 3)) & 127];
+  if (T < 64) twr[T] = T < 32 ? c_twrA[T] : c_twrB[T - 32];
+  for (int i = T; i < 2 * static_cast<int>(tc::kBBytes) / 16; i += kThreads)
+    reinterpret_cast<uint4*>(sB)[i] = reinterpret_cast<const uint4*>(g_tc_dft32)[i];
+  const uint32_t mb = tc::smem_u32(mbar);
+  if (T == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tmem_slot)),
+                 "r"(tc::kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tmem_slot;
+  // this thread's TMEM lane: tile warp / 4, lane 32 (warp % 4) + lane = row T % 128
+  const uint32_t t_row = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + 64 * (warp >> 2);
+  const uint32_t smA = tc::smem_u32(smraw), smB = tc::smem_u32(sB);
+  unsigned char* const aHi = smraw + (T >> 7) * tc::kTileBytes;
+  unsigned char* const aLo = aHi + tc::kHalfBytes;
+  const int arow = T & 127;
+
+  const int ya = T >> 2, ra = T & 3;
+  const int k1lo = T & 15, n2y = T >> 4;
+  const int kx = c_column(T), k1y = T >> 7, k1x = kx & 31, k2x = kx >> 5;
+  const float2* tB = twB + n2y * 4;
+  const int kxs = kx < 64 ? kx : kx - 128;
+  const float2* const pp = ptab + (kxs < 0 ? -kxs : kxs) * kPRow + k1y;
+  const float2* const pm = ptab + (kxs < 0 ? -kxs : kxs) * kPRow + 128 - k1y;
+  bool c_live = false;
+  int cur_job = -1;
+  float2* const xa = X + T * kXP;
+  float2* const xb = X + (4 * n2y) * kXP + k1lo;
+  float2* const xc = X + (128 * k2x + k1y) * kXP + k1x;
+  float2* const xw = X + (T >> 5) * (32 * kXP);
+  const float2* const tr = xw + (ya & 7) * kTRow + ra;
+  uint32_t phase = 0;
+  // a wait that gives up sets `bad`; the TMEM load after it still reads this CTA's own
+  // columns (values of no use), and the next CTA barrier (__syncthreads_or) abandons the launch
+  bool bad = false;
+
+  for (int li = blockIdx.x; li < a.n_list; li += gridDim.x) {
+    int jb = 0;
+    while (jb + 1 < a.n_jobs && li >= a.start[jb + 1]) ++jb;
+    const SliceJob& J = a.job[jb];
+    __syncthreads();   // the previous item's reads of the table and of ptab are done
+    if (jb != cur_job) {
+      cur_job = jb;
+      for (int e = T; e < kPTab; e += kThreads) {
+        const int pa = e / kPRow, pb = e - pa * kPRow;
+        const float2 v = cmul(J.ex[pa], J.ey[pb]);
+        ptab[e] = pa * pa + pb * pb <= J.r2max ? make_float2(v.x * tc::kPropScale, v.y * tc::kPropScale)
+                                               : make_float2(0.f, 0.f);
+      }
+      c_live = __any_sync(0xffffffffu, kxs * kxs <= J.r2max);
+    }
+    const int n_slices = J.n_slices;
+    const int pitch = J.nx + kW;
+    const size_t slice_elems = static_cast<size_t>(pitch) * (J.ny + kW);
+    const int item = a.list[li];
+    const int cfg = item / J.n_translates;
+    const int ti = item - cfg * J.n_translates;
+    const int ia = ti % J.lat_nax, ib = ti / J.lat_nax;
+    int ox = (J.lat_ox + ia * J.lat_sx - kW / 2) % J.nx;
+    if (ox < 0) ox += J.nx;
+    int oy = (J.lat_oy + ib * J.lat_sy - kW / 2) % J.ny;
+    if (oy < 0) oy += J.ny;
+    const float2* const gsrc = J.t + cfg * J.t_slot + static_cast<size_t>(oy + 8 * (T >> 5)) * pitch + ox;
+
+    stage_t_warp<EVEN>(xw, gsrc, pitch, lane);
+    float2 v[32];
+#pragma unroll
+    for (int n1 = 0; n1 < 32; ++n1) {
+      const float2 u = J.uW[ya * kW + 4 * n1 + ra];
+      v[n1] = make_float2(u.x * J.tc_in, u.y * J.tc_in);
+    }
+
+    for (int s = 0; s < n_slices; ++s) {
+      // transmission (Sec. 3.2), with the 2^-7 that the propagator leaves
+      cp_async_wait_all();
+      __syncwarp();
+#pragma unroll
+      for (int n1 = 0; n1 < 32; ++n1) {
+        const float2 p = cmul(v[n1], tr[4 * n1]);
+        v[n1] = make_float2(p.x * tc::kTransScale, p.y * tc::kTransScale);
+      }
+      // pass A forward on the tensor cores; this tile's table rows (its warps' staged
+      // transmission) are read once every thread of the tile has passed the barrier
+      __syncthreads();
+      tc::store_row(aHi, aLo, v, arow);
+      tc::fence_async_smem();
+      tc::fence_before();
+      if (__syncthreads_or(bad)) goto abort;
+      if (T == 0) {
+        tc::fence_after();
+        tc::issue_pass<false>(smA, smB, tmem);
+        tc::commit(mb);
+      }
+      bad = !__all_sync(0xffffffffu, tc::wait_phase(mb, phase));
+      phase ^= 1;
+      tc::fence_after();
+      tc::load_row(t_row, v);
+      // X1: this row's pass-A outputs (the tensor cores have read every tile)
+      float4* const xa4 = reinterpret_cast<float4*>(xa);
+#pragma unroll
+      for (int k = 0; k < 32; k += 2) xa4[k / 2] = make_float4(v[k].x, v[k].y, v[k + 1].x, v[k + 1].y);
+      tc::fence_before();
+      if (__syncthreads_or(bad)) goto abort;
+      float2 b0[16], b1[16];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          b0[q * 4 + r] = xb[(128 * q + r) * kXP];
+          b1[q * 4 + r] = xb[(128 * q + r) * kXP + 16];
+        }
+      passB_fwd_tw<false, PRUNE>(b0, tB, twr[k1lo], twr[32 + k1lo]);
+      passB_fwd_tw<true, PRUNE>(b1, tB, twr[16 + k1lo], twr[48 + k1lo]);
+      static_for<0, 4>([&](auto qq) {
+        constexpr int q = decltype(qq)::value;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          if constexpr (q != masked_k2x<false, PRUNE>()) xb[(128 * q + r) * kXP] = b0[r * 4 + q];
+          if constexpr (q != masked_k2x<true, PRUNE>()) xb[(128 * q + r) * kXP + 16] = b1[r * 4 + q];
+        }
+      });
+      __syncthreads();
+      // pass C forward: every row is read before the A operands overwrite the table
+      float2 c[32];
+      if (c_live) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) c[j] = xc[j * 4 * kXP];
+      }
+      __syncthreads();
+      if (c_live) tc::store_row(aHi, aLo, c, arow);
+      tc::fence_async_smem();
+      tc::fence_before();
+      __syncthreads();
+      if (T == 0) {
+        tc::fence_after();
+        tc::issue_pass<false>(smA, smB, tmem);
+        tc::commit(mb);
+      }
+      bad = !__all_sync(0xffffffffu, tc::wait_phase(mb, phase));
+      phase ^= 1;
+      tc::fence_after();
+      if (c_live) {
+        tc::load_row(t_row, c);
+        // propagation (Sec. 3.2): exp(-i pi lambda eps |k|^2), bandlimit, 2^-7
+#pragma unroll
+        for (int j = 0; j < 32; ++j) c[j] = cmul(c[j], j < 16 ? pp[4 * j] : pm[-4 * j]);
+        tc::store_row(aHi, aLo, c, arow);   // the tensor cores have read every tile
+      }
+      tc::fence_async_smem();
+      tc::fence_before();
+      if (__syncthreads_or(bad)) goto abort;
+      if (T == 0) {
+        tc::fence_after();
+        tc::issue_pass<true>(smA, smB, tmem);
+        tc::commit(mb);
+      }
+      bad = !__all_sync(0xffffffffu, tc::wait_phase(mb, phase));
+      phase ^= 1;
+      tc::fence_after();
+      if (c_live) {
+        tc::load_row(t_row, c);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) xc[j * 4 * kXP] = c[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) xc[j * 4 * kXP] = make_float2(0.f, 0.f);
+      }
+      tc::fence_before();
+      if (__syncthreads_or(bad)) goto abort;
+      static_for<0, 4>([&](auto qq) {
+        constexpr int q = decltype(qq)::value;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          if constexpr (q != masked_k2x<false, PRUNE>()) b0[r * 4 + q] = xb[(128 * q + r) * kXP];
+          if constexpr (q != masked_k2x<true, PRUNE>()) b1[r * 4 + q] = xb[(128 * q + r) * kXP + 16];
+        }
+      });
+      passB_inv_tw<false, PRUNE>(b0, tB, twr[k1lo], twr[32 + k1lo]);
+      passB_inv_tw<true, PRUNE>(b1, tB, twr[16 + k1lo], twr[48 + k1lo]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          xb[(128 * q + r) * kXP] = b0[q * 4 + r];
+          xb[(128 * q + r) * kXP + 16] = b1[q * 4 + r];
+        }
+      __syncthreads();
+      {
+        const float4* const xa4r = reinterpret_cast<const float4*>(xa);
+#pragma unroll
+        for (int k = 0; k < 32; k += 2) {
+          const float4 p = xa4r[k / 2];
+          v[k] = make_float2(p.x, p.y);
+          v[k + 1] = make_float2(p.z, p.w);
+        }
+      }
+      // pass A inverse: every row of the table is read before the A operands overwrite it
+      __syncthreads();
+      tc::store_row(aHi, aLo, v, arow);
+      tc::fence_async_smem();
+      tc::fence_before();
+      __syncthreads();
+      if (T == 0) {
+        tc::fence_after();
+        tc::issue_pass<true>(smA, smB, tmem);
+        tc::commit(mb);
+      }
+      bad = !__all_sync(0xffffffffu, tc::wait_phase(mb, phase));
+      phase ^= 1;
+      tc::fence_after();
+      tc::load_row(t_row, v);
+      // the tensor cores have read every tile: stage the next slice's transmission
+      __syncwarp();
+      if (s + 1 < n_slices) stage_t_warp<EVEN>(xw, gsrc + (s + 1) * slice_elems, pitch, lane);
+    }
+    if (__syncthreads_or(bad)) goto abort;
+    const int oi = a.out_index ? a.out_index[li] : ti;
+    float2* ud = J.U + cfg * J.u_slot + static_cast<size_t>(oi) * (kW * kW) + ya * kW + ra;
+#pragma unroll
+    for (int n1 = 0; n1 < 32; ++n1) ud[4 * n1] = make_float2(v[n1].x * J.tc_out, v[n1].y * J.tc_out);
+  }
+  if (false) {
+  abort:
+    // a tensor-core wait gave up (the decision is CTA-uniform)
+    bad = true;
+  }
+  cp_async_wait_all();
+  if (bad) {
+    if (T == 0) atomicOr(status, 1);
+    // the MMA group whose wait gave up may still be in flight: give it the same bounded
+    // wait before freeing TMEM
+    tc::wait_phase(mb, phase ^ 1);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tc::kTmemCols) : "memory");
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1337,6 +1774,7 @@ cudaError_t noalloc_scratch(void** ptr) {
 // ------------------------------------------------------------------------------------------
 size_t slice_smem_bytes() { return static_cast<size_t>(kSliceSmemFloat2) * sizeof(float2); }
 size_t synth_smem_bytes() { return static_cast<size_t>(kSynthSmemFloat2) * sizeof(float2); }
+size_t slice_tc_smem_bytes() { return static_cast<size_t>(kSliceTcSmemBytes); }
 size_t slice_rs_smem_bytes() { return static_cast<size_t>(kW * kW + 32 * 32) * sizeof(float2); }
 
 cudaError_t init_device_constants() {
@@ -1385,6 +1823,26 @@ cudaError_t init_device_constants() {
                          reinterpret_cast<const void*>(k_slice<true, true, false>),   reinterpret_cast<const void*>(k_slice<true, true, true>)};
     for (const void* f : ks)
       if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
+  }
+  {
+    // B^T[n][k] of the 32-point DFT in real form (n: output column of [Re y | Im y], k: input
+    // of [Re x | Im x]; F[k][n] = exp(-2 pi i k n / 32)), split into FP16 high and low parts
+    std::vector<unsigned char> bt(2 * tc::kBBytes, 0);
+    for (int n = 0; n < 64; ++n)
+      for (int k = 0; k < 64; ++k) {
+        const int kk = k & 31, nn = n & 31;
+        const double th = 2.0 * pi * ((kk * nn) & 31) / 32.0;
+        const double fr = cos(th), fi = -sin(th);
+        const double val = n < 32 ? (k < 32 ? fr : -fi) : (k < 32 ? fi : fr);
+        const __half hi = __float2half_rn(static_cast<float>(val));
+        const __half lo = __float2half_rn(static_cast<float>(val - static_cast<double>(__half2float(hi))));
+        std::memcpy(&bt[tc::op_offset(n, k)], &hi, 2);
+        std::memcpy(&bt[tc::kBBytes + tc::op_offset(n, k)], &lo, 2);
+      }
+    if ((e = cudaMemcpyToSymbol(g_tc_dft32, bt.data(), bt.size())) != cudaSuccess) return e;
+    const int st = static_cast<int>(slice_tc_smem_bytes());
+    for (auto f : {k_slice_tc<false, false>, k_slice_tc<false, true>, k_slice_tc<true, false>, k_slice_tc<true, true>})
+      if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, st)) != cudaSuccess) return e;
   }
   const int sr = static_cast<int>(slice_rs_smem_bytes());
   for (auto f : {k_slice_rs<3, 4, 3>, k_slice_rs<5, 4, 5>, k_slice_rs<3, 4>, k_slice_rs<5, 4>, k_slice_rs<7, 2>, k_slice_rs<9, 2>, k_slice_rs<11, 2>,
@@ -1442,6 +1900,23 @@ cudaError_t launch_slice(const SliceLaunch& a, bool even_origins, bool half, int
                              k_slice<true, true, false>,   k_slice<true, true, true>};
   const K f = table[(even_origins ? 4 : 0) + (half ? 2 : 0) + (prune ? 1 : 0)];
   f<<<grid, kThreads, sm, s>>>(a, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slice_tc(const SliceLaunch& a, bool even_origins, cudaStream_t s) {
+  if (a.n_list <= 0) return cudaSuccess;
+  if (a.n_jobs < 1 || a.n_jobs > kMaxJobs || a.start[0] != 0 || a.start[a.n_jobs] != a.n_list || !a.status)
+    return cudaErrorInvalidValue;
+  bool prune = true;
+  for (int i = 0; i < a.n_jobs; ++i) prune = prune && a.job[i].r2max < 44 * 44;
+  // persistent: one CTA per SM (its shared memory admits no second one), which holds the
+  // 256 TMEM columns it allocates for the whole launch
+  const int grid = a.n_list < sm_count() ? a.n_list : sm_count();
+  const size_t sm = slice_tc_smem_bytes();
+  using K = void (*)(const SliceLaunch, int*);
+  static const K table[4] = {k_slice_tc<false, false>, k_slice_tc<false, true>, k_slice_tc<true, false>,
+                             k_slice_tc<true, true>};
+  table[(even_origins ? 2 : 0) + (prune ? 1 : 0)]<<<grid, kThreads, sm, s>>>(a, a.status);
   return cudaGetLastError();
 }
 

@@ -36,6 +36,7 @@ LMA_COEF_LSQ = 0
 LMA_COEF_TRIG_CLOSED = 1
 LMA_PREC_C64 = 0
 LMA_PREC_FP16_STORE = 1
+LMA_PREC_MIXED = 2
 LMA_EDIT_REMOVE = 0
 LMA_EDIT_SET_SPECIES = 1
 LMA_IMAGE_RECOMPUTE = 1

@@ -38,6 +38,7 @@ BASIS_TRIG = 2
 BASIS_TRIG_RADIAL = 3
 PREC_C64 = 0
 PREC_FP16_STORE = 1
+PREC_MIXED = 2
 
 
 @dataclass
