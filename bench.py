@@ -531,34 +531,36 @@ def profile_case(precision: str = "c64") -> None:
 
 
 def approx_curves() -> None:
-    """Probe approximation error against L (1..64) and f for the input-wave kinds of Sec. 4.2.3
-    (the error-versus-L figures): host FP64 coefficients through the C-ABI, for the probe at
-    pixel (0, 0) of the E2-like geometry of workloads.probe_approximation_workload. Prints one
-    JSON line; no GPU work."""
+    """Probe approximation error against L and f for the input-wave kinds of Sec. 4.2.3 (the
+    error-versus-L figures) and for windows W = 64, 128, 256: host FP64 coefficients through
+    the C-ABI, for the probe at pixel (0, 0) of the E2-like geometry of
+    workloads.probe_approximation_workload. Prints one JSON line; no GPU work."""
     from paper_2310_16829_gb300 import lma
     ctx = lma.Context(-1)
-    cases = [("probe", WL.BASIS_PROBE, {}, (1, 2, 4)),
-             ("gauss_0.482A", WL.BASIS_GAUSS, {"gauss_sigma": 0.482}, (1, 2, 4)),
-             ("trig_lsq", WL.BASIS_TRIG, {}, (1, 2)),
-             ("trig_closed", WL.BASIS_TRIG, {"coef_mode": 1}, (1,))]
+    Ls = (1, 2, 4, 8, 12, 16, 24, 32, 48, 64)
+    cases = [("probe", WL.BASIS_PROBE, {}, (1, 2, 4), (64, 128, 256)),
+             ("gauss_0.482A", WL.BASIS_GAUSS, {"gauss_sigma": 0.482}, (1, 2, 4), (128, 256)),
+             ("trig_lsq", WL.BASIS_TRIG, {}, (1, 2), (128, 256)),
+             ("trig_closed", WL.BASIS_TRIG, {"coef_mode": 1}, (1,), (128,))]
     out = {}
     t0 = time.perf_counter()
-    for name, kind, extra, fs in cases:
+    for name, kind, extra, fs, Ws in cases:
         out[name] = {}
-        for f in fs:
-            rows = []
-            for L in range(1, 65):
-                w = WL.probe_approximation_workload(kind, f, L, **extra)
-                spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
-                b = lma.Basis(ctx, spec, w.probe, w.basis)
-                err = b.coefficients(0, 0)[3]
-                rows.append([L, float(err[0]), float(err[1])])
-                b.close()
-                spec.close()
-            out[name][f"f{f}"] = rows
+        for W in Ws:
+            for f in fs:
+                rows = []
+                for L in Ls:
+                    w = WL.probe_approximation_workload(kind, f, L, window=W, **extra)
+                    spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+                    b = lma.Basis(ctx, spec, w.probe, w.basis)
+                    err = b.coefficients(0, 0)[3]
+                    rows.append([L, float(err[0]), float(err[1])])
+                    b.close()
+                    spec.close()
+                out[name][f"W{W}_f{f}"] = rows
     ctx.close()
     print(json.dumps({"approx_curves": out, "geometry": "512^2 over 62.416 A, 200 kV, Z = 100 A, C_s = -2000 A, "
-                      "alpha_max = 26 mrad, input waves every 2 f px at offset 1 px, W = 128, probe at (0, 0)",
+                      "alpha_max = 26 mrad, input waves every 2 f px at offset 1 px, windows W x W, probe at (0, 0)",
                       "columns": ["L", "err_l2", "err_sup"], "seconds": time.perf_counter() - t0}))
 
 
@@ -580,6 +582,8 @@ def main():
                     help="skip the memory-bounded (partitioned) image measurement")
     ap.add_argument("--no-stem34", dest="stem34", action="store_false",
                     help="skip the 3D (rings) and 4D (pattern) STEM readout timings")
+    ap.add_argument("--no-windows", dest="windows", action="store_false",
+                    help="skip the W = 64 / 128 / 256 window timings on the 1024^2 specimen")
     ap.add_argument("--batch-phonons", type=int, default=4,
                     help="configurations per specimen of the uneven three-specimen batch (0: skip)")
     ap.add_argument("--profile-case", action="store_true",
@@ -834,6 +838,40 @@ def main():
         spec1.close()
         del out1
 
+    # ---- propagation windows W = 64, 128, 256 (detection window 128) on the serving specimen
+    # (20 x 20 ABO3 cells, 1024^2, 100 slices, one configuration, 256 x 256 probes): image time
+    # and the probe approximation error of each window (Sec. 4.2.1 option (ii), Sec. 4.2.3)
+    windows = None
+    if args.windows and rank == 0:
+        ww = WL.serving_workload()
+        wreg = WL.Region(0, 0, 256, 256, (4, 4))
+        specw = lma.Specimen(ctx, ww.grid, ww.potential, ww.phonons)
+        outw = torch.empty((len(dets), wreg.npy, wreg.npx), dtype=torch.float64, device="cuda")
+        windows = {"workload": ww.name + " (window W, detection window 128)", "probes": wreg.npx * wreg.npy}
+        for Wv in (64, 128, 256):
+            bw = lma.Basis(ctx, specw, ww.probe, dataclasses.replace(ww.basis, window=Wv))
+            bw.image(dets, wreg, out=outw, recompute=True, stream=stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ctx.profile_enable(True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            bw.image(dets, wreg, out=outw, recompute=True, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            prw = ctx.profile_read()
+            ctx.profile_enable(False)
+            ms_w = e0.elapsed_time(e1)
+            err = bw.coefficients(0, 0)[3]
+            windows[f"W{Wv}"] = {"ms_per_image": ms_w, "pixels_per_s": wreg.npx * wreg.npy / (ms_w / 1e3),
+                                 "slice_ms": prw["slice"]["total_ms"], "synth_ms": prw["synth"]["total_ms"],
+                                 "translate_slices": prw["slice"]["units"],
+                                 "probe_err_l2": float(err[0]), "probe_err_sup": float(err[1]),
+                                 "exit_wave_GB": bw.info().exit_wave_bytes / 1e9,
+                                 "mean_haadf": float(outw.mean())}
+            bw.close()
+        specw.close()
+        del outw
+
     # ---- end to end through the public API with host buffers
     host_out = np.empty((len(dets), region.npy, region.npx), dtype=np.float64)
     h2d = sum(a.x.nbytes + a.y.nbytes + a.species.nbytes + 4 * (w.grid.n_slices + 1) for a in w.phonons)
@@ -940,6 +978,7 @@ def main():
             "partition": partition,
             "coherence": coherence,
             "realspace": realspace,
+            "windows": windows,
             "clocks": clk,
             "kernels": kernels,
             "wall_s_timed_region": wall,

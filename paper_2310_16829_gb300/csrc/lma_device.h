@@ -53,6 +53,8 @@ struct SliceJob {
   int r2max;                   // bandlimit: m'^2 + n'^2 <= r2max
   float tc_in, tc_out;         // tensor-core DFT (k_slice_tc): power-of-two factor of the input
                                // wave, and its inverse applied to the exit wave
+  int W;                       // window of this job (kW, or 64 / 256 for k_slice_gen); uW, the
+                               // store entries and ex, ey have this size
 };
 
 // How the CTAs of a slice launch take their items.
@@ -93,7 +95,9 @@ struct SynthArgs {
   int cfg_base;                // index of slot 0's configuration in the accumulator
   int n_translates;            // |I_f| (stride of the per-wave factors between slots)
   size_t u_slot;               // elements of one slot of the exit-wave store
-  int cyclic;                  // windows are the whole periodic grid
+  int cyclic;                  // windows are the whole periodic grid (then W = D = kW)
+  int W;                       // exit-wave window (row length of the store), 64..256; the
+                               // probe window D is kW
   const uint32_t* det_bits;    // [n_det][kThreads] detector bits in C layout
   int n_det;                   // annuli: detectors; labels: labels (outputs per probe)
   double* acc;                 // [configuration][n_det][n_probes] readings (assigned)
@@ -133,6 +137,10 @@ int sm_count();
 // persistent CTAs, one per SM; a.status must be set
 cudaError_t launch_slice_tc(const SliceLaunch& a, bool even_origins, cudaStream_t s);
 size_t slice_tc_smem_bytes();
+// step a3 on W = 64 or W = 256 windows (every job of the launch has that W), complex64 store:
+// persistent CTAs, one per SM; W = 256 needs slice_gen_scratch_bytes(256) of scratch
+cudaError_t launch_slice_gen(const SliceLaunch& a, int W, float2* scratch, cudaStream_t s);
+size_t slice_gen_scratch_bytes(int W);
 cudaError_t launch_synth(const SynthArgs& a, bool half, int mode, cudaStream_t s);
 // step a3 with the propagation as a periodic convolution with the K1 x K2 kernel q (device,
 // [K2][K1] complex64, offsets -(K/2) .. K/2); K1 in {3, 5, ..., 13}, K2 odd <= 25; complex64 store

@@ -71,7 +71,9 @@ struct lma_ctx {
   std::vector<std::pair<void*, uint64_t>> capture_lists;   // lists read by the capture in progress
   int* d_counter = nullptr;                                 // [0] work counter of dynamic slice launches,
                                                             // [1] status word of the tensor-core slice kernel
-  bool tc_launched = false;                                 // a tensor-core slice launch since the last check
+  bool tc_launched = false;                                 // a slice launch with a status word since the last check
+  void* gen_scratch = nullptr;                              // per-CTA waves of the W = 256 slice kernel
+  size_t gen_scratch_bytes = 0;
   void* stage = nullptr;                                    // pinned staging buffer (kStageBytes)
   // slice launch modes: forced (>= 0), or the timed choice per launch shape
   int forced_mode = -1;
@@ -692,9 +694,10 @@ lma_status validate_region(lma_ctx* ctx, const lma_basis* b, const lma_region* r
 // windows the device kernels implement (geometry and coefficients take every supported W)
 lma_status device_window(const lma_basis* b) {
   if (b->W == kW) return LMA_OK;
-  return fail(b->ctx, LMA_ERR_UNSUPPORTED,
-              "window %d: the device path propagates and detects on W = D = %d windows; other windows are "
-              "supported by the host functions (coefficients, probe approximation) only", b->W, kW);
+  if (b->desc.precision != LMA_PREC_C64)
+    return fail(b->ctx, LMA_ERR_UNSUPPORTED, "window %d: the device path is complex64 only (W = %d has the "
+                "FP16 store and the tensor-core form)", b->W, kW);
+  return LMA_OK;
 }
 
 lma_status ensure_basis_tables(lma_basis* b, cudaStream_t st) {
@@ -984,6 +987,7 @@ lma_dev::SliceJob make_job(const lma_basis* b, const lma_specimen* sp) {
   J.r2max = b->r2max;
   J.tc_in = b->tc_in;
   J.tc_out = b->tc_out;
+  J.W = b->W;
   return J;
 }
 
@@ -995,6 +999,22 @@ lma_status slice_launch(lma_ctx* ctx, const lma_dev::SliceLaunch& L0, bool even,
   const bool half = prec == LMA_PREC_FP16_STORE;
   lma_dev::SliceLaunch L = L0;
   L.status = ctx->d_counter + 1;
+  if (L.job[0].W != kW) {
+    // W = 64 / 256 windows: k_slice_gen (complex64; the basis checks allow nothing else)
+    const size_t need = lma_dev::slice_gen_scratch_bytes(L.job[0].W);
+    if (need > ctx->gen_scratch_bytes) {
+      if (ctx->capturing) return fail(ctx, LMA_ERR_CUDA, "slice scratch missing during graph capture");
+      if (ctx->gen_scratch) cudaFree(ctx->gen_scratch);
+      ctx->gen_scratch = nullptr;
+      ctx->gen_scratch_bytes = 0;
+      CUDA_TRY(ctx, counted_malloc(&ctx->gen_scratch, need));
+      ctx->gen_scratch_bytes = need;
+    }
+    float2* scratch = static_cast<float2*>(ctx->gen_scratch);
+    ctx->tc_launched = true;   // the status word is checked at the next synchronizing read
+    CUDA_TRY(ctx, counted(ctx, K_SLICE, units, st, [&] { return lma_dev::launch_slice_gen(L, L.job[0].W, scratch, st); }));
+    return LMA_OK;
+  }
   if (prec == LMA_PREC_MIXED && ctx->rs_k1 == 0) {
     // tensor-core DFT passes: one persistent launch shape (no mode to tune)
     ctx->tc_launched = true;
@@ -1072,10 +1092,12 @@ lma_status propagate_jobs(lma_ctx* ctx, std::vector<JobWork>& work, cudaStream_t
     lma_status s0 = ensure_counter(ctx);
     if (s0 != LMA_OK) return s0;
   }
-  for (int prec : {LMA_PREC_C64, LMA_PREC_FP16_STORE, LMA_PREC_MIXED}) {
+  for (int gk = 0; gk < 9; ++gk) {
+    // one group per store precision and window
+    const int prec = gk / 3, wsize = 64 << (gk % 3);
     std::vector<JobWork*> group;
     for (JobWork& w : work)
-      if (!w.items.empty() && w.b->desc.precision == prec) group.push_back(&w);
+      if (!w.items.empty() && w.b->desc.precision == prec && w.b->W == wsize) group.push_back(&w);
     for (size_t c0 = 0; c0 < group.size(); c0 += lma_dev::kMaxJobs) {
       const int nj = static_cast<int>(std::min<size_t>(lma_dev::kMaxJobs, group.size() - c0));
       for (int part = 0; part < 2; ++part) {
@@ -1386,7 +1408,8 @@ lma_status images_work(lma_ctx* ctx, const std::vector<ImageJob>& jobs, const Re
       a.cfg_base = batch[k].first;
       a.n_translates = static_cast<int>(b->nT);
       a.u_slot = static_cast<size_t>(b->nT) * b->W * b->W;
-      a.cyclic = (b->nx == b->W && b->ny == b->W) ? 1 : 0;
+      a.cyclic = (b->W == kW && b->nx == kW && b->ny == kW) ? 1 : 0;
+      a.W = b->W;
       a.det_bits = static_cast<const uint32_t*>(b->d_det.p);
       a.n_det = ro.n_out;
       a.acc = static_cast<double*>(b->d_acc.p);
@@ -1533,6 +1556,7 @@ void lma_destroy(lma_ctx* ctx) {
     if (l.owned && l.p) cudaFree(l.p);
   if (ctx->list_slab) cudaFree(ctx->list_slab);
   if (ctx->d_counter) cudaFree(ctx->d_counter);
+  if (ctx->gen_scratch) cudaFree(ctx->gen_scratch);
   if (ctx->stage) cudaFreeHost(ctx->stage);
   delete ctx;
 }
@@ -1632,8 +1656,9 @@ lma_status lma_create_basis(lma_ctx* ctx, const lma_specimen* spec, const lma_pr
   const lma_basis_desc& d = *desc;
   if (d.window != 64 && d.window != 128 && d.window != 256)
     return fail(ctx, LMA_ERR_UNSUPPORTED, "window must be 64, 128 or 256 pixels");
-  if (d.det_window != d.window) return fail(ctx, LMA_ERR_UNSUPPORTED, "det_window must equal window");
-  if (g.nx < d.window || g.ny < d.window) return fail(ctx, LMA_ERR_UNSUPPORTED, "grid smaller than the window");
+  if (d.det_window != kW) return fail(ctx, LMA_ERR_UNSUPPORTED, "det_window (the detection window D) must be %d", kW);
+  if (g.nx < std::max(d.window, kW) || g.ny < std::max(d.window, kW))
+    return fail(ctx, LMA_ERR_UNSUPPORTED, "grid smaller than the window or than the detection window");
   if (!is_pow2(g.nx) || !is_pow2(g.ny)) return fail(ctx, LMA_ERR_UNSUPPORTED, "grid sizes must be powers of two");
   if (d.kind != LMA_BASIS_GAUSS && d.kind != LMA_BASIS_PROBE && d.kind != LMA_BASIS_TRIG &&
       d.kind != LMA_BASIS_TRIG_RADIAL)
@@ -2201,6 +2226,7 @@ lma_status lma_image_realspace(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, int
   if (K2 < 1 || K2 > 25 || (K2 & 1) == 0) return fail(ctx, LMA_ERR_INVALID, "K2 must be odd in 1..25");
   if (b->desc.precision != LMA_PREC_C64)
     return fail(ctx, LMA_ERR_UNSUPPORTED, "real-space propagation writes the complex64 store only");
+  if (b->W != kW) return fail(ctx, LMA_ERR_UNSUPPORTED, "real-space propagation runs on W = %d windows", kW);
   if (n_det <= 0 || n_det > lma_dev::kMaxDet || !det)
     return fail(ctx, LMA_ERR_INVALID, "need 1..%d detectors", lma_dev::kMaxDet);
   for (int d = 0; d < n_det; ++d)
@@ -2396,7 +2422,8 @@ lma_status lma_image_coherent(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, cons
       a.cfg_base = phi0;
       a.n_translates = static_cast<int>(b->nT);
       a.u_slot = static_cast<size_t>(b->nT) * b->W * b->W;
-      a.cyclic = (b->nx == b->W && b->ny == b->W) ? 1 : 0;
+      a.cyclic = (b->W == kW && b->nx == kW && b->ny == kW) ? 1 : 0;
+      a.W = b->W;
       a.det_bits = static_cast<const uint32_t*>(b->d_det.p);
       a.n_det = n_det;
       a.acc = static_cast<double*>(b->d_acc.p) + static_cast<size_t>(v) * nph * nout;
@@ -2511,7 +2538,8 @@ lma_status lma_image_partitioned(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, c
       a.cfg_base = phi;
       a.n_translates = static_cast<int>(M);
       a.u_slot = static_cast<size_t>(M) * b->W * b->W;
-      a.cyclic = (b->nx == b->W && b->ny == b->W) ? 1 : 0;
+      a.cyclic = (b->W == kW && b->nx == kW && b->ny == kW) ? 1 : 0;
+      a.W = b->W;
       a.det_bits = static_cast<const uint32_t*>(b->d_det.p);
       a.n_det = n_det;
       a.acc = static_cast<double*>(b->d_acc.p);
@@ -2890,7 +2918,8 @@ lma_status lma_readout_noalloc(lma_ctx* ctx, lma_basis* b, const float* exit_wav
   a.cfg_base = 0;
   a.n_translates = static_cast<int>(b->nT);
   a.u_slot = 0;
-  a.cyclic = (b->nx == b->W && b->ny == b->W) ? 1 : 0;
+  a.cyclic = (b->W == kW && b->nx == kW && b->ny == kW) ? 1 : 0;
+      a.W = b->W;
   a.det_bits = reinterpret_cast<const uint32_t*>(base + o_det);
   a.n_det = n_det;
   a.acc = reinterpret_cast<double*>(base + o_acc);

@@ -666,8 +666,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
 // FP16 parts, x = x_hi + x_lo (x_hi = fp16(x), x_lo = fp16(x - x_hi)), and the product is
 // taken as x_lo F_hi + x_hi F_lo + x_hi F_hi with FP32 accumulation in tensor memory (the
 // x_lo F_lo term, 2^-22 of the product, is dropped): tcgen05.mma kind::f16, M = 128 rows per
-// tile, four tiles per pass. The inverse DFT (conj F) uses the 32 x 32 sub-blocks of the same
-// B: Re y = Re x Re F + Im x Im F, Im y = -Re x Im F + Im x Re F. Pass B, the transmission
+// tile, four tiles per pass. The inverse DFT (conj F) has its own B, [[Re F, -Im F], [Im F,
+// Re F]] (Re y = Re x Re F + Im x Im F, Im y = -Re x Im F + Im x Re F). Pass B, the transmission
 // and the propagator products stay on the CUDA cores in FP32, as in k_slice.
 //
 // Scale. FP16 holds 11 significant bits between 2^-14 and 65504. The wave enters with a
@@ -681,7 +681,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
 //
 // Shared memory: the A operand of tile t (rows 128 t .. 128 t + 127, FP16 high and low parts,
 // 2 x 16 KiB) lies inside the exchange-table rows of the same 128 threads, which the pass-B
-// exchanges use at other times; B (high and low, 2 x 8 KiB) has its own space. Operands are
+// exchanges use at other times; the forward and inverse B (high and low parts, 4 x 8 KiB)
+// have their own space. Operands are
 // K-major without swizzle: core matrices of 8 rows x 16 bytes, 128 bytes apart along K and
 // 1024 bytes apart along the rows.
 namespace tc {
@@ -693,7 +694,6 @@ constexpr int kTmemCols = 256;                                // 4 tiles x 64 FP
 constexpr uint32_t kBBytes = 8192;                            // one FP16 part of B (64 x 64)
 constexpr float kPropScale = 128.f;                           // 2^-7 / 2^-14: propagator factor
 constexpr float kTransScale = 1.f / 128.f;                    // 2^-7 with each transmission
-constexpr int kWaitLimit = 1 << 22;                           // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -723,16 +723,44 @@ __device__ __forceinline__ void commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
                : "memory");
 }
-// wait for the given phase of the mbarrier, giving up after kWaitLimit polls
+__device__ __forceinline__ uint32_t try_wait(uint32_t mbar, uint32_t phase) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(phase)
+      : "memory");
+  return done;
+}
+// try_wait that lets the thread be suspended up to kSuspendNs while the phase is incomplete
+// (woken when it completes), instead of spinning on the shared-memory pipe
+constexpr uint32_t kSuspendNs = 1000000;
+constexpr int kSuspendLimit = 2000;          // at least 2 s in all before giving up
+__device__ __forceinline__ uint32_t try_wait_sleep(uint32_t mbar, uint32_t phase) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(phase), "r"(kSuspendNs)
+      : "memory");
+  return done;
+}
+// wait for the given phase of the mbarrier, giving up after kSuspendLimit suspended tries
+// (one thread)
 __device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t phase) {
   uint32_t done = 0;
-  for (int it = 0; it < kWaitLimit && !done; ++it)
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(phase)
-        : "memory");
+  for (int it = 0; it < kSuspendLimit && !done; ++it) done = try_wait_sleep(mbar, phase);
   return done != 0;
+}
+// the same for a whole warp: lane 0 polls, then every lane observes the completed phase
+// itself (one try_wait each, for the memory ordering), so 31 lanes do not spin on the
+// shared-memory pipe; warp-uniform result
+__device__ __forceinline__ bool wait_phase_warp(uint32_t mbar, uint32_t phase) {
+  uint32_t done = 0;
+  if ((threadIdx.x & 31) == 0) done = wait_phase(mbar, phase) ? 1u : 0u;
+  done = __shfl_sync(0xffffffffu, done, 0);
+  if (done) done = try_wait(mbar, phase);
+  return __all_sync(0xffffffffu, done != 0);
 }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -786,71 +814,70 @@ __device__ __forceinline__ void store_row(unsigned char* hi, unsigned char* lo, 
 
 // the MMAs of one pass over the four tiles: forward D = A B (N = 64), inverse by sub-blocks
 // (N = 32); products lo x hi, hi x lo, hi x hi, the first overwriting D
+// named barrier of the 128 threads of tile t (barrier 0 is __syncthreads)
+__device__ __forceinline__ void tile_sync(int t) { asm volatile("bar.sync %0, 128;" ::"r"(t + 1) : "memory"); }
+
+// the 12 MMAs of tile t of one pass: products lo x hi, hi x lo, hi x hi over four K steps of
+// 16, the first overwriting D; forward or inverse B
 template <bool INV>
-__device__ __forceinline__ void issue_pass(uint32_t smA, uint32_t smB, uint32_t tmem) {
+__device__ __forceinline__ void issue_tile(uint32_t smA, uint32_t smB, uint32_t tmem, int t) {
   // descriptors differ only in their start-address field: base descriptor + (offset >> 4)
   // (every operand lies below 256 KiB, so the 14-bit field never carries)
-  const uint64_t dB = sdesc(smB), dA = sdesc(smA);
+  const uint64_t dB = sdesc(smB + (INV ? 2 * kBBytes : 0));
+  const uint64_t aH = sdesc(smA + t * kTileBytes);
   constexpr uint64_t kLo = kHalfBytes >> 4, kBLo = kBBytes >> 4;
-#pragma unroll 1
-  for (int t = 0; t < 4; ++t) {
-    const uint64_t aH = dA + ((t * kTileBytes) >> 4);
-    const uint32_t d = tmem + 64 * t;
+  const uint32_t d = tmem + 64 * t;
 #pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      // products lo x hi, hi x lo, hi x hi
-      const uint64_t a0 = p == 0 ? aH + kLo : aH;
-      const uint64_t b0 = p == 1 ? dB + kBLo : dB;
-      if constexpr (!INV) {
+  for (int p = 0; p < 3; ++p) {
+    const uint64_t a0 = p == 0 ? aH + kLo : aH;
+    const uint64_t b0 = p == 1 ? dB + kBLo : dB;
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma(d, a0 + kk * 16, b0 + kk * 16, idesc(128, 64), (p > 0 || kk > 0) ? 1u : 0u);
-      } else {
-        // Re y (columns 0..31) and Im y (32..63), each from Re x (K blocks 0, 1) and Im x (2, 3)
-#pragma unroll
-        for (int hv = 0; hv < 2; ++hv)
-#pragma unroll
-          for (int src = 0; src < 2; ++src)
-#pragma unroll
-            for (int kk = 0; kk < 2; ++kk)
-              mma(d + 32 * hv, a0 + (src * 2 + kk) * 16, b0 + src * 256 + (hv * 2 + kk) * 16, idesc(128, 32),
-                  (p > 0 || src > 0 || kk > 0) ? 1u : 0u);
-      }
-    }
+    for (int kk = 0; kk < 4; ++kk)
+      mma(d, a0 + kk * 16, b0 + kk * 16, idesc(128, 64), (p > 0 || kk > 0) ? 1u : 0u);
   }
 }
 
 }  // namespace tc
 
-// B operands of the 32-point DFT, high and low FP16 parts in the operand layout (built on the
-// host in FP64: B^T[n][k], n the output column of [Re y | Im y], k the input of [Re x | Im x])
-__device__ __align__(16) unsigned char g_tc_dft32[2 * tc::kBBytes];
+// B operands of the forward and inverse 32-point DFT, high and low FP16 parts each, in the
+// operand layout (built on the host in FP64: B^T[n][k], n the output column of [Re y | Im y],
+// k the input of [Re x | Im x])
+__device__ __align__(16) unsigned char g_tc_dft32[4 * tc::kBBytes];
 
-constexpr int kSliceTcSmemBytes = kXRows * 8 + 2 * tc::kBBytes + 64 * 16 + 128 * 8 + kPTab * 8 + 64;
+constexpr int kSliceTcSmemBytes = kXRows * 8 + 4 * tc::kBBytes + 64 * 16 + 128 * 8 + kPTab * 8 + 4 * 8 + 16;
 
 // One translate per CTA at a time (persistent CTAs, item li = blockIdx + k gridDim); the
 // exit waves are complex64. status: set to 1 when a tensor-core wait gives up.
+//
+// The four M-tiles of a pass are independent: tile t is rows 128 t .. 128 t + 127, the rows
+// of warps 4 t .. 4 t + 3, whose A operand lies in those threads' own table rows and whose
+// accumulator is TMEM columns 64 t .. 64 t + 63. Each tile synchronizes its 128 threads with
+// a named barrier, one elected thread issues the tile's MMAs and commits them to the tile's
+// mbarrier, and the tile's threads read their rows back as soon as it completes: the tensor
+// cores work on one tile while the CUDA cores split, store or read back the others. CTA
+// barriers remain where data cross tiles: the pass-B exchanges (X1..X4), the reads of X2
+// before pass C's operands overwrite the table, and the X3 writes after every tile's
+// inverse pass C.
 template <bool EVEN, bool PRUNE>
 __global__ void __launch_bounds__(kThreads, 1) k_slice_tc(const SliceLaunch a, int* status) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   float2* X = reinterpret_cast<float2*>(smraw);                                   // exchange table
-  unsigned char* const sB = smraw + kXRows * 8;                                   // B hi, B lo
-  float4* twr = reinterpret_cast<float4*>(sB + 2 * tc::kBBytes);
+  unsigned char* const sB = smraw + kXRows * 8;                    // forward B hi, lo; inverse B hi, lo
+  float4* twr = reinterpret_cast<float4*>(sB + 4 * tc::kBBytes);
   float2* twB = reinterpret_cast<float2*>(twr + 64);
   float2* ptab = twB + 128;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(ptab + kPTab);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(ptab + kPTab);      // one per tile
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 4);
 
   const int T = threadIdx.x, warp = T >> 5, lane = T & 31;
+  const int tile = T >> 7;
+  const bool elected = (T & 127) == 0;
   if (T < 128) twB[T] = c_w128[((T >> 2) * (T & 3)) & 127];
   if (T < 64) twr[T] = T < 32 ? c_twrA[T] : c_twrB[T - 32];
-  for (int i = T; i < 2 * static_cast<int>(tc::kBBytes) / 16; i += kThreads)
+  for (int i = T; i < 4 * static_cast<int>(tc::kBBytes) / 16; i += kThreads)
     reinterpret_cast<uint4*>(sB)[i] = reinterpret_cast<const uint4*>(g_tc_dft32)[i];
-  const uint32_t mb = tc::smem_u32(mbar);
-  if (T == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
+  if (T < 4) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(mbar + T)) : "memory");
+  if (T == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tmem_slot)),
                  "r"(tc::kTmemCols)
@@ -862,10 +889,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice_tc(const SliceLaunch a, i
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tmem_slot;
+  const uint32_t mb = tc::smem_u32(mbar + tile);
   // this thread's TMEM lane: tile warp / 4, lane 32 (warp % 4) + lane = row T % 128
-  const uint32_t t_row = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + 64 * (warp >> 2);
+  const uint32_t t_row = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + 64 * tile;
   const uint32_t smA = tc::smem_u32(smraw), smB = tc::smem_u32(sB);
-  unsigned char* const aHi = smraw + (T >> 7) * tc::kTileBytes;
+  unsigned char* const aHi = smraw + tile * tc::kTileBytes;
   unsigned char* const aLo = aHi + tc::kHalfBytes;
   const int arow = T & 127;
 
@@ -883,10 +911,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice_tc(const SliceLaunch a, i
   float2* const xc = X + (128 * k2x + k1y) * kXP + k1x;
   float2* const xw = X + (T >> 5) * (32 * kXP);
   const float2* const tr = xw + (ya & 7) * kTRow + ra;
-  uint32_t phase = 0;
+  uint32_t phase = 0;   // parity of the next round of every tile's mbarrier
   // a wait that gives up sets `bad`; the TMEM load after it still reads this CTA's own
   // columns (values of no use), and the next CTA barrier (__syncthreads_or) abandons the launch
   bool bad = false;
+
+  // one MMA round of this thread's tile: operands stored and fenced by every thread of the
+  // tile, then issued by the elected thread; returns after the tile's products are in TMEM
+  auto round = [&](auto inv) {
+    tc::fence_async_smem();
+    tc::fence_before();
+    tc::tile_sync(tile);
+    if (elected) {
+      tc::fence_after();
+      tc::issue_tile<decltype(inv)::value>(smA, smB, tmem, tile);
+      tc::commit(mb);
+    }
+    bad |= !tc::wait_phase_warp(mb, phase);
+    phase ^= 1;
+    tc::fence_after();
+  };
 
   for (int li = blockIdx.x; li < a.n_list; li += gridDim.x) {
     int jb = 0;
@@ -902,6 +946,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice_tc(const SliceLaunch a, i
                                                : make_float2(0.f, 0.f);
       }
       c_live = __any_sync(0xffffffffu, kxs * kxs <= J.r2max);
+      __syncthreads();   // ptab complete
     }
     const int n_slices = J.n_slices;
     const int pitch = J.nx + kW;
@@ -933,27 +978,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice_tc(const SliceLaunch a, i
         const float2 p = cmul(v[n1], tr[4 * n1]);
         v[n1] = make_float2(p.x * tc::kTransScale, p.y * tc::kTransScale);
       }
-      // pass A forward on the tensor cores; this tile's table rows (its warps' staged
-      // transmission) are read once every thread of the tile has passed the barrier
-      __syncthreads();
+      // pass A forward: the tile's staged transmission rows are read before its operands
+      // overwrite them
+      tc::tile_sync(tile);
       tc::store_row(aHi, aLo, v, arow);
-      tc::fence_async_smem();
-      tc::fence_before();
-      if (__syncthreads_or(bad)) goto abort;
-      if (T == 0) {
-        tc::fence_after();
-        tc::issue_pass<false>(smA, smB, tmem);
-        tc::commit(mb);
-      }
-      bad = !__all_sync(0xffffffffu, tc::wait_phase(mb, phase));
-      phase ^= 1;
-      tc::fence_after();
+      round(std::false_type{});
       tc::load_row(t_row, v);
-      // X1: this row's pass-A outputs (the tensor cores have read every tile)
+      // X1: this row's pass-A outputs, in the tile's own rows (its MMAs are complete)
       float4* const xa4 = reinterpret_cast<float4*>(xa);
 #pragma unroll
       for (int k = 0; k < 32; k += 2) xa4[k / 2] = make_float4(v[k].x, v[k].y, v[k + 1].x, v[k + 1].y);
-      tc::fence_before();
       if (__syncthreads_or(bad)) goto abort;
       float2 b0[16], b1[16];
 #pragma unroll
@@ -974,7 +1008,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice_tc(const SliceLaunch a, i
         }
       });
       __syncthreads();
-      // pass C forward: every row is read before the A operands overwrite the table
+      // pass C forward: every row of X2 is read before the operands overwrite the table
       float2 c[32];
       if (c_live) {
 #pragma unroll
@@ -982,37 +1016,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice_tc(const SliceLaunch a, i
       }
       __syncthreads();
       if (c_live) tc::store_row(aHi, aLo, c, arow);
-      tc::fence_async_smem();
-      tc::fence_before();
-      __syncthreads();
-      if (T == 0) {
-        tc::fence_after();
-        tc::issue_pass<false>(smA, smB, tmem);
-        tc::commit(mb);
-      }
-      bad = !__all_sync(0xffffffffu, tc::wait_phase(mb, phase));
-      phase ^= 1;
-      tc::fence_after();
+      round(std::false_type{});
       if (c_live) {
         tc::load_row(t_row, c);
         // propagation (Sec. 3.2): exp(-i pi lambda eps |k|^2), bandlimit, 2^-7
 #pragma unroll
         for (int j = 0; j < 32; ++j) c[j] = cmul(c[j], j < 16 ? pp[4 * j] : pm[-4 * j]);
-        tc::store_row(aHi, aLo, c, arow);   // the tensor cores have read every tile
+        tc::store_row(aHi, aLo, c, arow);   // the tile's MMAs have read its operands
       }
-      tc::fence_async_smem();
-      tc::fence_before();
-      if (__syncthreads_or(bad)) goto abort;
-      if (T == 0) {
-        tc::fence_after();
-        tc::issue_pass<true>(smA, smB, tmem);
-        tc::commit(mb);
-      }
-      bad = !__all_sync(0xffffffffu, tc::wait_phase(mb, phase));
-      phase ^= 1;
-      tc::fence_after();
+      round(std::true_type{});
+      if (c_live) tc::load_row(t_row, c);
+      // X3 goes to every tile's rows: every tile's inverse products must be complete
+#pragma unroll 1
+      for (int u = 0; u < 4; ++u)
+        if (u != tile) bad |= !tc::wait_phase_warp(tc::smem_u32(mbar + u), phase ^ 1);
       if (c_live) {
-        tc::load_row(t_row, c);
 #pragma unroll
         for (int j = 0; j < 32; ++j) xc[j * 4 * kXP] = c[j];
       } else {
@@ -1048,22 +1066,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice_tc(const SliceLaunch a, i
           v[k + 1] = make_float2(p.z, p.w);
         }
       }
-      // pass A inverse: every row of the table is read before the A operands overwrite it
-      __syncthreads();
+      // pass A inverse: the tile's X4 rows (read only by the tile) are read before its
+      // operands overwrite them
+      tc::tile_sync(tile);
       tc::store_row(aHi, aLo, v, arow);
-      tc::fence_async_smem();
-      tc::fence_before();
-      __syncthreads();
-      if (T == 0) {
-        tc::fence_after();
-        tc::issue_pass<true>(smA, smB, tmem);
-        tc::commit(mb);
-      }
-      bad = !__all_sync(0xffffffffu, tc::wait_phase(mb, phase));
-      phase ^= 1;
-      tc::fence_after();
+      round(std::true_type{});
       tc::load_row(t_row, v);
-      // the tensor cores have read every tile: stage the next slice's transmission
+      // the tile's MMAs have read its rows: stage the next slice's transmission there
       __syncwarp();
       if (s + 1 < n_slices) stage_t_warp<EVEN>(xw, gsrc + (s + 1) * slice_elems, pitch, lane);
     }
@@ -1081,14 +1090,283 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice_tc(const SliceLaunch a, i
   cp_async_wait_all();
   if (bad) {
     if (T == 0) atomicOr(status, 1);
-    // the MMA group whose wait gave up may still be in flight: give it the same bounded
-    // wait before freeing TMEM
+    // the tile's last MMA group may still be in flight: give it the same bounded wait
+    // before freeing TMEM
     tc::wait_phase(mb, phase ^ 1);
   }
   tc::fence_before();
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tc::kTmemCols) : "memory");
+}
+
+// ------------------------------------------------------------------------------------------
+// step a3 on windows W = 64 and W = 256 (k_slice_gen)
+// ------------------------------------------------------------------------------------------
+// Every W-point transform (a row or a column of the window) is done by one warp in registers:
+// lane l holds the R = W / 32 values of indices l + 32 j. The forward transform is radix-2
+// decimation in frequency (natural order in, bit-reversed order out): its stages of span W/2
+// .. 32 pair values of one lane, those of span 16 .. 1 pair lanes (shuffles). The propagator is
+// applied in the bit-reversed order that the forward transforms leave, and the inverse
+// transforms are decimation in time (bit-reversed in, natural out), so no pass reorders data.
+// Each slice is two passes: columns (forward, propagator, inverse), then rows (inverse, the
+// next slice's transmission, forward); the first slice's transmission and forward rows come
+// before the loop, the last inverse rows after it.
+//
+// W = 64: the wave (32 KiB) stays in shared memory, rows padded to 65 values. W = 256: the
+// wave (512 KiB) is more than one SM holds, so it lives in a scratch area of global memory, one
+// per CTA (L2-resident with one CTA per SM). Rows are read and written there directly
+// (coalesced); columns go through shared memory in panels of 32 columns, each panel row a
+// 256-byte segment moved by the TMA engine's bulk copies (cp.async.bulk), completed on an
+// mbarrier (loads) or a bulk group (stores).
+namespace gen {
+
+constexpr int kThreadsGen = 512;
+constexpr int kPanel = 32;                // columns per panel (W = 256)
+constexpr int kPanelPitch = 34;           // complex values per panel row (16-byte rows)
+
+// exp(-2 pi i m / W), m < W / 2, built on the host in FP64 and rounded once
+__constant__ float2 c_tw64[32];
+__constant__ float2 c_tw256[128];
+
+template <int W>
+__device__ __forceinline__ float2 tw(int m) {
+  if constexpr (W == 64) return c_tw64[m];
+  else return c_tw256[m];
+}
+template <int W>
+__device__ __forceinline__ int brev(int i) {
+  constexpr int bits = W == 64 ? 6 : 8;
+  return static_cast<int>(__brev(static_cast<unsigned>(i)) >> (32 - bits));
+}
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
+// forward DIF over x[l + 32 j] (v[j] in lane l); afterwards v[j] holds X[brev(l + 32 j)]
+template <int W>
+__device__ __forceinline__ void fft_fwd(float2 (&v)[W / 32], int lane) {
+  constexpr int R = W / 32;
+#pragma unroll
+  for (int jh = R / 2; jh >= 1; jh >>= 1) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      if (j & jh) continue;
+      const float2 a = v[j], b = v[j + jh];
+      v[j] = cadd(a, b);
+      v[j + jh] = cmul(csub(a, b), tw<W>((lane + 32 * (j & (jh - 1))) * (W / (64 * jh))));
+    }
+  }
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool upper = (lane & h) != 0;
+    const float2 w = tw<W>((lane & (h - 1)) * (W / (2 * h)));
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const float2 p = shfl_xor2(v[j], h);
+      v[j] = upper ? cmul(csub(p, v[j]), w) : cadd(v[j], p);
+    }
+  }
+}
+
+// inverse DIT (conjugate twiddles, no 1/W): v[j] holding X[brev(l + 32 j)] becomes x[l + 32 j]
+template <int W>
+__device__ __forceinline__ void fft_inv(float2 (&v)[W / 32], int lane) {
+  constexpr int R = W / 32;
+#pragma unroll
+  for (int h = 1; h <= 16; h <<= 1) {
+    const bool upper = (lane & h) != 0;
+    const float2 w = tw<W>((lane & (h - 1)) * (W / (2 * h)));
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const float2 mine = upper ? cmulc(v[j], w) : v[j];
+      const float2 p = shfl_xor2(mine, h);
+      v[j] = upper ? csub(p, mine) : cadd(mine, p);
+    }
+  }
+#pragma unroll
+  for (int jh = 1; jh <= R / 2; jh <<= 1) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      if (j & jh) continue;
+      const float2 a = v[j];
+      const float2 b = cmulc(v[j + jh], tw<W>((lane + 32 * (j & (jh - 1))) * (W / (64 * jh))));
+      v[j] = cadd(a, b);
+      v[j + jh] = csub(a, b);
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+}  // namespace gen
+
+// One translate per CTA at a time (persistent CTAs); complex64 exit waves. scratch: W x W
+// complex64 per CTA (W = 256); status: set to 1 when a bulk-copy wait gives up.
+template <int W>
+__global__ void __launch_bounds__(gen::kThreadsGen, 1) k_slice_gen(const SliceLaunch a, float2* scratch, int* status) {
+  constexpr int R = W / 32;
+  constexpr int kWarps = gen::kThreadsGen / 32;
+  constexpr bool kResident = W <= 64;
+  extern __shared__ __align__(16) unsigned char smg[];
+  // W = 64: the wave, [W][W + 1]; W = 256: one column panel, [W][kPanelPitch], and an mbarrier
+  float2* const S = reinterpret_cast<float2*>(smg);
+  uint64_t* const mbar = reinterpret_cast<uint64_t*>(smg + (kResident ? W * (W + 1) : W * gen::kPanelPitch) * 8);
+  const int T = threadIdx.x, warp = T >> 5, lane = T & 31;
+  float2* const G = kResident ? nullptr : scratch + static_cast<size_t>(blockIdx.x) * W * W;
+  const uint32_t mb = gen::smem_u32(mbar);
+  if (!kResident && T == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  bool bad = false;
+  // element (y, x) of the wave
+  auto at = [&](int y, int x) -> float2& {
+    if constexpr (kResident) return S[y * (W + 1) + x];
+    else return G[static_cast<size_t>(y) * W + x];
+  };
+
+  for (int li = blockIdx.x; li < a.n_list; li += gridDim.x) {
+    int jb = 0;
+    while (jb + 1 < a.n_jobs && li >= a.start[jb + 1]) ++jb;
+    const SliceJob& J = a.job[jb];
+    const int n_slices = J.n_slices;
+    const int pitch = J.nx + kW;                          // padded transmission row
+    const size_t slice_elems = static_cast<size_t>(pitch) * (J.ny + kW);
+    const int item = a.list[li];
+    const int cfg = item / J.n_translates;
+    const int ti = item - cfg * J.n_translates;
+    const int ia = ti % J.lat_nax, ib = ti / J.lat_nax;
+    int ox = (J.lat_ox + ia * J.lat_sx - W / 2) % J.nx;
+    if (ox < 0) ox += J.nx;
+    int oy = (J.lat_oy + ib * J.lat_sy - W / 2) % J.ny;
+    if (oy < 0) oy += J.ny;
+    const float2* const tbase = J.t + cfg * J.t_slot;
+    // transmission of slice s at window pixel (y, x): the periodic cell, indices wrapped
+    auto tval = [&](int s, int y, int x) -> float2 {
+      int gy = oy + y, gx = ox + x;
+      if (gy >= J.ny) gy -= J.ny;
+      if (gx >= J.nx) gx -= J.nx;
+      return tbase[s * slice_elems + static_cast<size_t>(gy) * pitch + gx];
+    };
+    __syncthreads();   // the previous item's use of the wave and the panel is over
+    // rows: input wave, transmission of slice 0, forward transform
+    for (int y = warp; y < W && n_slices > 0; y += kWarps) {
+      float2 v[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) v[j] = cmul(J.uW[y * W + lane + 32 * j], tval(0, y, lane + 32 * j));
+      gen::fft_fwd<W>(v, lane);
+#pragma unroll
+      for (int j = 0; j < R; ++j) at(y, lane + 32 * j) = v[j];
+    }
+    if (n_slices == 0)
+      for (int y = warp; y < W; y += kWarps)
+#pragma unroll
+        for (int j = 0; j < R; ++j) at(y, lane + 32 * j) = J.uW[y * W + lane + 32 * j];
+    for (int s = 0; s < n_slices; ++s) {
+      // the rows' generic writes to the scratch are ordered before the bulk copies read it
+      if constexpr (!kResident) asm volatile("fence.proxy.async.global;" ::: "memory");
+      __syncthreads();
+      // columns: forward transform, propagator (Sec. 3.2) at (kx, ky) = (brev(x), brev(y)),
+      // inverse transform
+      auto column = [&](float2 (&v)[R], int x) {
+        gen::fft_fwd<W>(v, lane);
+        const int kxb = gen::brev<W>(x);
+        const int kxs = kxb < W / 2 ? kxb : kxb - W;
+        const float2 ex = J.ex[kxb];
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          const int kyb = gen::brev<W>(lane + 32 * j);
+          const int kys = kyb < W / 2 ? kyb : kyb - W;
+          v[j] = kxs * kxs + kys * kys <= J.r2max ? cmul(v[j], cmul(ex, J.ey[kyb])) : make_float2(0.f, 0.f);
+        }
+        gen::fft_inv<W>(v, lane);
+      };
+      if constexpr (kResident) {
+        for (int x = warp; x < W; x += kWarps) {
+          float2 v[R];
+#pragma unroll
+          for (int j = 0; j < R; ++j) v[j] = S[(lane + 32 * j) * (W + 1) + x];
+          column(v, x);
+#pragma unroll
+          for (int j = 0; j < R; ++j) S[(lane + 32 * j) * (W + 1) + x] = v[j];
+        }
+      } else {
+        for (int x0 = 0; x0 < W; x0 += gen::kPanel) {
+          // panel load: W segments of 256 bytes, one per thread of the first W threads
+          if (T == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
+                         "r"(W * gen::kPanel * 8)
+                         : "memory");
+          __syncthreads();   // expect_tx is set before any copy can complete
+          if (T < W)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    gen::smem_u32(S + T * gen::kPanelPitch)),
+                "l"(G + static_cast<size_t>(T) * W + x0), "r"(gen::kPanel * 8), "r"(mb)
+                : "memory");
+          uint32_t done = 0;
+          for (int it = 0; it < (1 << 22) && !done; ++it)
+            asm volatile(
+                "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(mb), "r"(phase)
+                : "memory");
+          phase ^= 1;
+          bad |= !done;
+          if (done) {
+            for (int c = warp; c < gen::kPanel; c += kWarps) {
+              float2 v[R];
+#pragma unroll
+              for (int j = 0; j < R; ++j) v[j] = S[(lane + 32 * j) * gen::kPanelPitch + c];
+              column(v, x0 + c);
+#pragma unroll
+              for (int j = 0; j < R; ++j) S[(lane + 32 * j) * gen::kPanelPitch + c] = v[j];
+            }
+          }
+          // panel store: the threads' writes are made visible to the bulk copies first
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncthreads();
+          if (T < W) {
+            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(
+                             G + static_cast<size_t>(T) * W + x0),
+                         "r"(gen::smem_u32(S + T * gen::kPanelPitch)), "r"(gen::kPanel * 8)
+                         : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            // the panel buffer is reloaded next: its reads by the store are over first;
+            // the rows pass reads the stored values: their writes are complete and ordered
+            // before the generic reads
+            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+          }
+          __syncthreads();
+        }
+      }
+      __syncthreads();
+      // rows: inverse transform, then the next slice's transmission and forward transform
+      const bool more = s + 1 < n_slices;
+      for (int y = warp; y < W; y += kWarps) {
+        float2 v[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) v[j] = at(y, lane + 32 * j);
+        gen::fft_inv<W>(v, lane);
+        if (more) {
+#pragma unroll
+          for (int j = 0; j < R; ++j) v[j] = cmul(v[j], tval(s + 1, y, lane + 32 * j));
+          gen::fft_fwd<W>(v, lane);
+        }
+#pragma unroll
+        for (int j = 0; j < R; ++j) at(y, lane + 32 * j) = v[j];
+      }
+    }
+    if (__syncthreads_or(bad)) break;
+    const int oi = a.out_index ? a.out_index[li] : ti;
+    float2* const ud = J.U + cfg * J.u_slot + static_cast<size_t>(oi) * (W * W);
+    for (int e = T; e < W * W; e += gen::kThreadsGen) ud[e] = at(e / W, e % W);
+  }
+  if (bad && T == 0) atomicOr(status, 1);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1336,6 +1614,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
   const bool c_live = __any_sync(0xffffffffu, any_bits != 0u);
   __syncthreads();
 
+  // exit-wave window W (the store's row length); the probe window D is kW. The periodic
+  // placement (CYCLIC) has W = D = kW.
+  const int Wu = CYCLIC ? kW : a.W;
   const int n_walk = a.probe_list ? a.n_list : a.n_probes;
   const int n_items = n_walk * a.n_cfg;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -1380,17 +1661,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
           // element (y0 + yl, x0 + 64 kk) of translate ti is at signed offset base + yl W +
           // 64 kk; only offsets of rows and columns inside the window are dereferenced
           const int y0 = 8 * warp_id - sh.y, x0 = 2 * lane_id - sh.x;
-          const long long base = static_cast<long long>(ti) * (kW * kW) + y0 * kW + x0;
-          const bool okx0 = static_cast<unsigned>(x0) < static_cast<unsigned>(kW);
-          const bool okx1 = static_cast<unsigned>(x0 + 64) < static_cast<unsigned>(kW);
+          const long long base = static_cast<long long>(ti) * (Wu * Wu) + y0 * Wu + x0;
+          const bool okx0 = static_cast<unsigned>(x0) < static_cast<unsigned>(Wu);
+          const bool okx1 = static_cast<unsigned>(x0 + 64) < static_cast<unsigned>(Wu);
 #pragma unroll
           for (int yl = 0; yl < 8; ++yl) {
-            const bool oky = static_cast<unsigned>(y0 + yl) < static_cast<unsigned>(kW);
+            const bool oky = static_cast<unsigned>(y0 + yl) < static_cast<unsigned>(Wu);
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
               Raw r{};
               if (oky && (kk ? okx1 : okx0)) {
-                const long long e = base + (yl * kW + 64 * kk);
+                const long long e = base + (yl * Wu + 64 * kk);
                 if constexpr (HALF)
                   r = *reinterpret_cast<const uint2*>(static_cast<const __half2*>(Uhc) + e);
                 else
@@ -1407,8 +1688,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
           if constexpr (CYCLIC)
             yy &= (kW - 1);
           else
-            ok = yy >= 0 && yy < kW;
-          const size_t off = static_cast<size_t>(ti) * (kW * kW) + yy * kW;
+            ok = yy >= 0 && yy < Wu;
+          const size_t off = static_cast<size_t>(ti) * (Wu * Wu) + yy * Wu;
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk) {
             int xp = 64 * kk + 2 * lane_id - sh.x;
@@ -1416,7 +1697,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
             if constexpr (CYCLIC)
               xp &= (kW - 1);
             else
-              okx = okx && xp >= 0 && xp < kW;
+              okx = okx && xp >= 0 && xp < Wu;
             Raw r{};
             if (okx) {
               if constexpr (HALF)
@@ -1447,16 +1728,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
           int yy = 8 * warp_id + yl - sh.y;
           if constexpr (CYCLIC) {
             yy &= (kW - 1);
-          } else if (yy < 0 || yy >= kW) {
+          } else if (yy < 0 || yy >= Wu) {
             continue;
           }
-          const size_t off = static_cast<size_t>(ti) * (kW * kW) + yy * kW;
+          const size_t off = static_cast<size_t>(ti) * (Wu * Wu) + yy * Wu;
 #pragma unroll
           for (int m = 0; m < 4; ++m) {
             int xe = 64 * (m >> 1) + 2 * lane_id + (m & 1) - sh.x;
             if constexpr (CYCLIC) {
               xe &= (kW - 1);
-            } else if (xe < 0 || xe >= kW) {
+            } else if (xe < 0 || xe >= Wu) {
               continue;
             }
             if constexpr (HALF)
@@ -1775,6 +2056,12 @@ cudaError_t noalloc_scratch(void** ptr) {
 size_t slice_smem_bytes() { return static_cast<size_t>(kSliceSmemFloat2) * sizeof(float2); }
 size_t synth_smem_bytes() { return static_cast<size_t>(kSynthSmemFloat2) * sizeof(float2); }
 size_t slice_tc_smem_bytes() { return static_cast<size_t>(kSliceTcSmemBytes); }
+static size_t slice_gen_smem_bytes(int W) {
+  return (W <= 64 ? static_cast<size_t>(W) * (W + 1) : static_cast<size_t>(W) * gen::kPanelPitch) * sizeof(float2) + 16;
+}
+size_t slice_gen_scratch_bytes(int W) {
+  return W <= 64 ? 0 : static_cast<size_t>(sm_count()) * W * W * sizeof(float2);
+}
 size_t slice_rs_smem_bytes() { return static_cast<size_t>(kW * kW + 32 * 32) * sizeof(float2); }
 
 cudaError_t init_device_constants() {
@@ -1826,23 +2113,41 @@ cudaError_t init_device_constants() {
   }
   {
     // B^T[n][k] of the 32-point DFT in real form (n: output column of [Re y | Im y], k: input
-    // of [Re x | Im x]; F[k][n] = exp(-2 pi i k n / 32)), split into FP16 high and low parts
-    std::vector<unsigned char> bt(2 * tc::kBBytes, 0);
-    for (int n = 0; n < 64; ++n)
-      for (int k = 0; k < 64; ++k) {
-        const int kk = k & 31, nn = n & 31;
-        const double th = 2.0 * pi * ((kk * nn) & 31) / 32.0;
-        const double fr = cos(th), fi = -sin(th);
-        const double val = n < 32 ? (k < 32 ? fr : -fi) : (k < 32 ? fi : fr);
-        const __half hi = __float2half_rn(static_cast<float>(val));
-        const __half lo = __float2half_rn(static_cast<float>(val - static_cast<double>(__half2float(hi))));
-        std::memcpy(&bt[tc::op_offset(n, k)], &hi, 2);
-        std::memcpy(&bt[tc::kBBytes + tc::op_offset(n, k)], &lo, 2);
-      }
+    // of [Re x | Im x]; F[k][n] = exp(-2 pi i k n / 32)), split into FP16 high and low parts;
+    // then the same for conj F (the inverse): the off-diagonal blocks change sign
+    std::vector<unsigned char> bt(4 * tc::kBBytes, 0);
+    for (int inv = 0; inv < 2; ++inv)
+      for (int n = 0; n < 64; ++n)
+        for (int k = 0; k < 64; ++k) {
+          const int kk = k & 31, nn = n & 31;
+          const double th = 2.0 * pi * ((kk * nn) & 31) / 32.0;
+          const double fr = cos(th), fi = inv ? sin(th) : -sin(th);
+          const double val = n < 32 ? (k < 32 ? fr : -fi) : (k < 32 ? fi : fr);
+          const __half hi = __float2half_rn(static_cast<float>(val));
+          const __half lo = __float2half_rn(static_cast<float>(val - static_cast<double>(__half2float(hi))));
+          const size_t base = static_cast<size_t>(inv) * 2 * tc::kBBytes;
+          std::memcpy(&bt[base + tc::op_offset(n, k)], &hi, 2);
+          std::memcpy(&bt[base + tc::kBBytes + tc::op_offset(n, k)], &lo, 2);
+        }
     if ((e = cudaMemcpyToSymbol(g_tc_dft32, bt.data(), bt.size())) != cudaSuccess) return e;
     const int st = static_cast<int>(slice_tc_smem_bytes());
     for (auto f : {k_slice_tc<false, false>, k_slice_tc<false, true>, k_slice_tc<true, false>, k_slice_tc<true, true>})
       if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, st)) != cudaSuccess) return e;
+  }
+  {
+    // twiddles of the W = 64 and W = 256 transforms: exp(-2 pi i m / W), m < W / 2
+    float2 t64[32], t256[128];
+    for (int m = 0; m < 32; ++m) t64[m] = make_float2(static_cast<float>(cos(-2.0 * pi * m / 64)), static_cast<float>(sin(-2.0 * pi * m / 64)));
+    for (int m = 0; m < 128; ++m)
+      t256[m] = make_float2(static_cast<float>(cos(-2.0 * pi * m / 256)), static_cast<float>(sin(-2.0 * pi * m / 256)));
+    if ((e = cudaMemcpyToSymbol(gen::c_tw64, t64, sizeof(t64))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(gen::c_tw256, t256, sizeof(t256))) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_slice_gen<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(slice_gen_smem_bytes(64)))) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(k_slice_gen<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(slice_gen_smem_bytes(256)))) != cudaSuccess)
+      return e;
   }
   const int sr = static_cast<int>(slice_rs_smem_bytes());
   for (auto f : {k_slice_rs<3, 4, 3>, k_slice_rs<5, 4, 5>, k_slice_rs<3, 4>, k_slice_rs<5, 4>, k_slice_rs<7, 2>, k_slice_rs<9, 2>, k_slice_rs<11, 2>,
@@ -1917,6 +2222,23 @@ cudaError_t launch_slice_tc(const SliceLaunch& a, bool even_origins, cudaStream_
   static const K table[4] = {k_slice_tc<false, false>, k_slice_tc<false, true>, k_slice_tc<true, false>,
                              k_slice_tc<true, true>};
   table[(even_origins ? 2 : 0) + (prune ? 1 : 0)]<<<grid, kThreads, sm, s>>>(a, a.status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slice_gen(const SliceLaunch& a, int W, float2* scratch, cudaStream_t s) {
+  if (a.n_list <= 0) return cudaSuccess;
+  if (a.n_jobs < 1 || a.n_jobs > kMaxJobs || a.start[0] != 0 || a.start[a.n_jobs] != a.n_list || !a.status)
+    return cudaErrorInvalidValue;
+  // persistent, one CTA per SM: W = 256 takes one scratch wave per CTA
+  const int grid = a.n_list < sm_count() ? a.n_list : sm_count();
+  if (W == 64) {
+    k_slice_gen<64><<<grid, gen::kThreadsGen, slice_gen_smem_bytes(64), s>>>(a, nullptr, a.status);
+  } else if (W == 256) {
+    if (!scratch) return cudaErrorInvalidValue;
+    k_slice_gen<256><<<grid, gen::kThreadsGen, slice_gen_smem_bytes(256), s>>>(a, scratch, a.status);
+  } else {
+    return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -308,19 +308,19 @@ LAMBDA_200KV_FIG = 0.0250793
 
 
 def probe_approximation_workload(kind: int, f: int = 1, L: int = 32, gauss_sigma: float = 0.0,
-                                 coef_mode: int = 0) -> Workload:
+                                 coef_mode: int = 0, window: int = 128) -> Workload:
     """Probe approximation (coefficients only; one atom, one slice as a placeholder specimen)."""
     grid = Grid(nx=512, ny=512, lx=62.416, ly=62.416, slice_dz=2.0, n_slices=1,
                 lam=LAMBDA_200KV_FIG, sigma=SIGMA_CFG0)
     atoms = Atoms(np.array([0.0]), np.array([0.0]), np.array([0], np.int32), np.array([0], np.int16))
     return Workload(
-        name=f"probe_approx_512sq_kind{kind}_f{f}",
+        name=f"probe_approx_512sq_kind{kind}_f{f}_W{window}",
         grid=grid,
         potential=Potential(peak=(300.0,)),
         phonons=[atoms],
         probe=Probe(alpha_max=0.026, cs=-2000.0, defocus=100.0),
         basis=BasisDesc(kind=kind, gauss_sigma=gauss_sigma, in_spacing_px=(2, 2), in_offset_px=(1, 1),
-                        f=f, L=L, coef_mode=coef_mode),
+                        f=f, L=L, coef_mode=coef_mode, window=window),
         detectors=[Detector(0.07, 0.2)],
         region=Region(0, 0, 1, 1, (2, 2)),
         notes="probe approximation error versus L and f (no image)",

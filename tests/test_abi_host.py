@@ -77,6 +77,16 @@ def test_coefficients_match_oracle_on_a_512_grid():
     _check_coefficients(w, [(0, 0), (508, 4)])
 
 
+@pytest.mark.parametrize("W", [64, 256])
+def test_coefficients_match_oracle_other_windows(W):
+    """Input waves sampled on W x W windows (Sec. 4.2.1 option (ii)): the least squares over the
+    union of the L windows, against the oracle with the same W."""
+    w = WL.perovskite_workload(n_phonons=1)
+    w = w.__class__(**{**w.__dict__, "basis": WL.BasisDesc(**{**w.basis.__dict__, "window": W})})
+    b = _check_coefficients(w, [(0, 0), (508, 4)])
+    assert b.info().window == W and b.info().exit_wave_bytes == 128 * 128 * W * W * 8
+
+
 def test_basis_info_and_lattice_count():
     w = WL.perovskite_workload(n_phonons=1)
     ctx, spec, basis = _host_objects(w)
@@ -102,10 +112,11 @@ def test_validation_errors():
         with pytest.raises(lma.LmaError) as e:
             lma.Basis(ctx, spec, w.probe, d)
         assert e.value.status == lma.LMA_ERR_INVALID, kw
-    d = WL.BasisDesc(**{**w.basis.__dict__, "window": 64})
-    with pytest.raises(lma.LmaError) as e:
-        lma.Basis(ctx, spec, w.probe, d)
-    assert e.value.status == lma.LMA_ERR_UNSUPPORTED
+    for kw in (dict(window=32), dict(det_window=64), dict(window=256)):   # 256 > this 128^2 grid
+        d = WL.BasisDesc(**{**w.basis.__dict__, **kw})
+        with pytest.raises(lma.LmaError) as e:
+            lma.Basis(ctx, spec, w.probe, d)
+        assert e.value.status == lma.LMA_ERR_UNSUPPORTED, kw
     # atoms with a slice out of range
     at = w.phonons[0]
     bad_at = WL.Atoms(at.x, at.y, at.slice + 100, at.species)
