@@ -830,8 +830,11 @@ def main():
         for K in (3, 5, 7, 9, 13, 25):
             ms_r, sl_r = timed_image(lambda: b1.image_realspace(K, K, dets, region, out=out1, stream=stream))
             img_r = out1.cpu().numpy()
+            g_all, g_band = b1.realspace_gain(K, K)
             rows.append({"K": K, "ms_per_image": ms_r, "slice_ms": sl_r, "slice_vs_fourier": sl_r / sl_f,
                          "model_ratio": (1 + K * K) / (2 + 2 * 2 * np.log2(W)),
+                         "per_slice_gain_max": g_all, "per_slice_gain_band": g_band,
+                         "gain_over_slices": g_band ** w1.grid.n_slices,
                          "max_abs_diff_of_fourier_image_max": float(np.max(np.abs(img_r - ref)) / np.max(ref))})
         realspace = {"workload": w1.name, "fourier": {"ms_per_image": ms_f, "slice_ms": sl_f}, "kernels": rows}
         b1.close()

@@ -315,6 +315,17 @@ lma_status lma_image_realspace(lma_ctx* ctx, lma_specimen* spec, lma_basis* basi
                                const lma_detector* det, int32_t n_det, const lma_region* region,
                                uint32_t flags, double* out, void* stream);
 
+/* Per-slice amplification of the real-space propagation step (Sec. 3.2, complexity
+ * paragraph): with q the K1 x K2 kernel that lma_image_realspace uses (the inverse DFT of
+ * the window's propagator and bandlimit, truncated to odd K1, K2 <= W pixels), the
+ * convolution multiplies spectral component k of the W x W window by Q(k) = sum over the
+ * kernel offsets d of q(d) exp(-2 pi i k.d / W). *gain_all receives max_k |Q(k)| over the
+ * window and *gain_band the maximum over the bandlimit's disc. The Fourier step has
+ * |P(k)| <= 1; a gain above 1 grows those components slice by slice. Host-only (FP64),
+ * any context. LMA_ERR_INVALID for even or out-of-range K. */
+lma_status lma_realspace_gain(lma_ctx* ctx, const lma_basis* basis, int32_t K1, int32_t K2, double* gain_all,
+                              double* gain_band);
+
 /* ---- partial coherence and the choice of L ---------------------------------------------- */
 
 #define LMA_MAX_VARIANTS 32

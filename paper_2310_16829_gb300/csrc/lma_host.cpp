@@ -2185,7 +2185,9 @@ static lma_status make_plan(lma_basis* b, const lma_region* r, const lma_partiti
 
 // q discretized to K1 x K2 pixels: the inverse DFT (FP64) of the window propagator
 // exp(-i pi lambda eps |k|^2) times the bandlimit, at offsets -(K/2) .. K/2
-static void realspace_kernel_host(const lma_basis* b, int K1, int K2, std::vector<float>& q) {
+// q of Sec. 3.2 discretized to K1 x K2 pixels, in FP64: the inverse DFT of the window's
+// propagator (bandlimit included) at offsets -(K/2) .. K - 1 - K/2, [K2][K1]
+static void realspace_kernel_fp64(const lma_basis* b, int K1, int K2, std::vector<cd>& q) {
   const lma_grid& g = b->spec->g;
   const double dx = g.lx / g.nx, dy = g.ly / g.ny;
   std::vector<cd> root(b->W);
@@ -2201,7 +2203,7 @@ static void realspace_kernel_host(const lma_basis* b, int K1, int K2, std::vecto
       P[static_cast<size_t>(iy) * b->W + ix] = std::exp(cd(0.0, -kPi * g.lambda * g.slice_dz * (ky * ky + kx * kx)));
     }
   }
-  q.assign(2 * static_cast<size_t>(K1) * K2, 0.f);
+  q.assign(static_cast<size_t>(K1) * K2, cd(0.0, 0.0));
   for (int a = 0; a < K2; ++a) {
     const int oy = a - K2 / 2;
     for (int c = 0; c < K1; ++c) {
@@ -2210,11 +2212,49 @@ static void realspace_kernel_host(const lma_basis* b, int K1, int K2, std::vecto
       for (int iy = 0; iy < b->W; ++iy)
         for (int ix = 0; ix < b->W; ++ix)
           sum += P[static_cast<size_t>(iy) * b->W + ix] * root[mod(iy * oy + ix * ox, b->W)];
-      sum /= static_cast<double>(b->W) * b->W;
-      q[2 * (static_cast<size_t>(a) * K1 + c)] = static_cast<float>(sum.real());
-      q[2 * (static_cast<size_t>(a) * K1 + c) + 1] = static_cast<float>(sum.imag());
+      q[static_cast<size_t>(a) * K1 + c] = sum / (static_cast<double>(b->W) * b->W);
     }
   }
+}
+
+// the same kernel rounded once to complex64 for the device
+static void realspace_kernel_host(const lma_basis* b, int K1, int K2, std::vector<float>& q) {
+  std::vector<cd> qd;
+  realspace_kernel_fp64(b, K1, K2, qd);
+  q.assign(2 * qd.size(), 0.f);
+  for (size_t k = 0; k < qd.size(); ++k) {
+    q[2 * k] = static_cast<float>(qd[k].real());
+    q[2 * k + 1] = static_cast<float>(qd[k].imag());
+  }
+}
+
+lma_status lma_realspace_gain(lma_ctx* ctx, const lma_basis* b, int32_t K1, int32_t K2, double* gain_all,
+                              double* gain_band) {
+  if (!ctx || !b || !gain_all || !gain_band) return fail(ctx, LMA_ERR_INVALID, "null argument");
+  if (K1 < 1 || K2 < 1 || K1 > b->W || K2 > b->W || (K1 & 1) == 0 || (K2 & 1) == 0)
+    return fail(ctx, LMA_ERR_INVALID, "K1 and K2 must be odd in 1..W");
+  std::vector<cd> q;
+  realspace_kernel_fp64(b, K1, K2, q);
+  const int W = b->W;
+  std::vector<cd> root(W);
+  for (int m = 0; m < W; ++m) root[m] = std::exp(cd(0.0, -2.0 * kPi * m / W));
+  double ga = 0.0, gb = 0.0;
+  for (int iy = 0; iy < W; ++iy) {
+    const int my = signed_index(iy, W);
+    for (int ix = 0; ix < W; ++ix) {
+      const int mx = signed_index(ix, W);
+      cd Q(0.0, 0.0);
+      for (int a = 0; a < K2; ++a)
+        for (int c = 0; c < K1; ++c)
+          Q += q[static_cast<size_t>(a) * K1 + c] * root[mod(iy * (a - K2 / 2) + ix * (c - K1 / 2), W)];
+      const double m = std::abs(Q);
+      ga = std::max(ga, m);
+      if (my * my + mx * mx <= b->r2max) gb = std::max(gb, m);
+    }
+  }
+  *gain_all = ga;
+  *gain_band = gb;
+  return LMA_OK;
 }
 
 lma_status lma_image_realspace(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, int32_t K1, int32_t K2,

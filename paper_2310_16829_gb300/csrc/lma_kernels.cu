@@ -58,6 +58,10 @@ __constant__ float4 c_twrB[32];
 // ------------------------------------------------------------------------------------------
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// the same sums as one packed FP32 instruction each (add.rn.f32x2, and fma.rn.f32x2 with -1,
+// whose product is exact): bit for bit equal to cadd / csub, half the issued instructions
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -118,8 +122,8 @@ __device__ __forceinline__ void bfly(float2 (&t)[32]) {
     static_assert(M == 0, "zero inputs are pruned in the first stage only");
     t[I + H] = a;
   } else if constexpr (M == 0) {
-    if constexpr (NX) t[I] = cadd(a, b);
-    if constexpr (NY) t[I + H] = csub(a, b);
+    if constexpr (NX) t[I] = padd(a, b);
+    if constexpr (NY) t[I + H] = psub(a, b);
   } else if constexpr (M == 8) {
     // w b = -i b (forward) or i b (inverse)
     const float2 wb = INV ? make_float2(-b.y, b.x) : make_float2(b.y, -b.x);
@@ -198,13 +202,13 @@ __device__ __forceinline__ void dft32(float2 (&v)[32]) {
 
 template <bool INV>
 __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
-  const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
+  const float2 s02 = padd(a0, a2), d02 = psub(a0, a2), s13 = padd(a1, a3), d13 = psub(a1, a3);
   // forward: X1 = d02 - i d13, X3 = d02 + i d13; inverse swaps the sign of i
   const float2 j13 = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
-  a0 = cadd(s02, s13);
-  a2 = csub(s02, s13);
-  a1 = cadd(d02, j13);
-  a3 = csub(d02, j13);
+  a0 = padd(s02, s13);
+  a2 = psub(s02, s13);
+  a1 = padd(d02, j13);
+  a3 = psub(d02, j13);
 }
 
 // dft4 with input Z known to be zero (Z = -1: none); the outputs are those of dft4
@@ -1578,7 +1582,9 @@ __device__ __forceinline__ int probe_of(int q, int npx, int npy, int sw) {
 // HALF reads the FP16 store and folds each wave's factor into its coefficient. MODE
 // selects the readout (ReadMode): 2D annuli, labelled pixel sets (3D STEM rings) or the
 // diffraction pattern on a centred crop (4D STEM).
-template <bool HALF, int MODE, bool CYCLIC>
+// WS: the exit-wave window at compile time (kW), or 0 to take it from a.W (windows of other
+// sizes, non-periodic placement only)
+template <bool HALF, int MODE, bool CYCLIC, int WS = kW>
 __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a) {
   extern __shared__ __align__(16) float2 sm[];
   float2* R0 = sm;
@@ -1616,7 +1622,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
 
   // exit-wave window W (the store's row length); the probe window D is kW. The periodic
   // placement (CYCLIC) has W = D = kW.
-  const int Wu = CYCLIC ? kW : a.W;
+  static_assert(!CYCLIC || WS == kW, "periodic placement has W = D");
+  const int Wu = WS > 0 ? WS : a.W;
   const int n_walk = a.probe_list ? a.n_list : a.n_probes;
   const int n_items = n_walk * a.n_cfg;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -2159,7 +2166,9 @@ cudaError_t init_device_constants() {
                  k_synth_detect<false, kReadPattern, false>, k_synth_detect<true, kReadPattern, false>,
                  k_synth_detect<false, kReadAnnuli, true>, k_synth_detect<true, kReadAnnuli, true>,
                  k_synth_detect<false, kReadLabels, true>, k_synth_detect<true, kReadLabels, true>,
-                 k_synth_detect<false, kReadPattern, true>, k_synth_detect<true, kReadPattern, true>})
+                 k_synth_detect<false, kReadPattern, true>, k_synth_detect<true, kReadPattern, true>,
+                 k_synth_detect<false, kReadAnnuli, false, 0>, k_synth_detect<false, kReadLabels, false, 0>,
+                 k_synth_detect<false, kReadPattern, false, 0>})
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sy)) != cudaSuccess) return e;
   return cudaSuccess;
 }
@@ -2286,6 +2295,14 @@ cudaError_t launch_synth(const SynthArgs& a, bool half, int mode, cudaStream_t s
        {k_synth_detect<true, kReadPattern, false>, k_synth_detect<true, kReadPattern, true>}}};
   if (mode != kReadAnnuli && mode != kReadLabels && mode != kReadPattern) return cudaErrorInvalidValue;
   const int mi = mode == kReadAnnuli ? 0 : (mode == kReadLabels ? 1 : 2);
+  if (a.W != kW) {
+    // other windows: complex64 store, non-periodic placement, W read at run time
+    static const K other[3] = {k_synth_detect<false, kReadAnnuli, false, 0>, k_synth_detect<false, kReadLabels, false, 0>,
+                               k_synth_detect<false, kReadPattern, false, 0>};
+    if (half || a.cyclic || a.W < 32 || a.W > 256) return cudaErrorInvalidValue;
+    other[mi]<<<grid, kThreads, sm, s>>>(a);
+    return cudaGetLastError();
+  }
   table[half ? 1 : 0][mi][a.cyclic ? 1 : 0]<<<grid, kThreads, sm, s>>>(a);
   return cudaGetLastError();
 }

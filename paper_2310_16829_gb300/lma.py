@@ -62,7 +62,7 @@ EXPORTS = [
     "lma_propagate_basis", "lma_exit_wave",
     "lma_image", "lma_image_rings", "lma_image_4d", "lma_image_many", "lma_edit_column",
     "lma_affected_probes",
-    "lma_profile_enable", "lma_profile_read", "lma_readout_noalloc",
+    "lma_profile_enable", "lma_profile_read", "lma_readout_noalloc", "lma_realspace_gain",
     "lma_set_slice_mode", "lma_tuning_read", "lma_partition", "lma_image_partitioned",
     "lma_image_coherent", "lma_select_L", "lma_image_realspace",
 ]
@@ -177,6 +177,7 @@ _SIGS = {
     "lma_edit_column": (C.c_int32, [_VP, _VP, _VP, C.c_double, C.c_double, C.c_double, C.c_int32,
                                     C.c_int16, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "lma_affected_probes": (C.c_int32, [_VP, _VP, C.POINTER(Region), _VP, C.POINTER(C.c_int64)]),
+    "lma_realspace_gain": (C.c_int32, [_VP, _VP, C.c_int32, C.c_int32, _VP, _VP]),
     "lma_readout_noalloc": (C.c_int32, [_VP, _VP, _VP, C.POINTER(Detector), C.c_int32, C.POINTER(Region),
                                         _VP, _VP]),
     "lma_set_slice_mode": (C.c_int32, [_VP, C.c_int32]),
@@ -450,6 +451,12 @@ class Basis:
                                                         len(detectors), C.byref(reg), 0, _ptr(out),
                                                         _stream(stream)))
         return out
+
+    def realspace_gain(self, K1: int, K2: int):
+        """(max_k |Q(k)|, max over the bandlimit) of the K1 x K2 real-space kernel (host)."""
+        ga, gb = C.c_double(), C.c_double()
+        self.ctx.check(self.ctx.lib.lma_realspace_gain(self.ctx.h, self.h, K1, K2, C.byref(ga), C.byref(gb)))
+        return ga.value, gb.value
 
     def image_coherent(self, variants, detectors, region, out=None, recompute: bool = False, stream=None):
         """Partially coherent image: variants = [(defocus, cs, weight), ...] of the basis probe

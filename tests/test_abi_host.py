@@ -305,3 +305,30 @@ def test_binding_fails_loudly_without_the_cuda_library(tmp_path):
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
     assert r.returncode == 3 and "not built" in r.stdout, (r.returncode, r.stdout, r.stderr[-500:])
+
+
+def test_realspace_gain_matches_the_dft_of_the_oracle_kernel():
+    """lma_realspace_gain against numpy's DFT of the oracle's truncated kernel (Sec. 3.2):
+    max |Q(k)| of the zero-padded K x K kernel on the W x W window; the untruncated kernel
+    (K = W - 1 covers all but one row and column; K = 1 is the kernel's centre) bounds."""
+    w = WL.perovskite_workload(n_phonons=1, n_slices=2)
+    ctx, spec, basis = _host_objects(w)
+    prm = O.params_from_workload(w)
+    prop = O.fresnel_propagator(128, 128, prm.dy, prm.dx, prm.lam, prm.slice_dz, prm.bandlimit_frac)
+    for K1, K2 in ((3, 3), (5, 9), (13, 13)):
+        qK = O.realspace_kernel(prop, K1, K2)
+        full = np.zeros((128, 128), complex)
+        for iy, dy in enumerate(O.kernel_offsets(K2)):
+            for ix, dx in enumerate(O.kernel_offsets(K1)):
+                full[dy % 128, dx % 128] = qK[iy, ix]
+        Q = np.abs(np.fft.fft2(full))
+        band = O.bandlimit_mask(128, 128, prm.bandlimit_frac)
+        ga, gb = basis.realspace_gain(K1, K2)
+        assert abs(ga - Q.max()) < 1e-12 and abs(gb - Q[band].max()) < 1e-12, (K1, K2)
+    # the centre alone is the propagator's mean; the full-but-one kernel is close to |P| <= 1
+    ga, _ = basis.realspace_gain(1, 1)
+    assert abs(ga - abs(prop.mean())) < 1e-12
+    assert abs(basis.realspace_gain(127, 127)[0] - 1.0) < 0.05
+    with pytest.raises(lma.LmaError):
+        basis.realspace_gain(4, 3)
+
