@@ -584,7 +584,7 @@ def main():
                     help="skip the 3D (rings) and 4D (pattern) STEM readout timings")
     ap.add_argument("--no-windows", dest="windows", action="store_false",
                     help="skip the W = 64 / 128 / 256 window timings on the 1024^2 specimen")
-    ap.add_argument("--batch-phonons", type=int, default=4,
+    ap.add_argument("--batch-phonons", type=int, default=32,
                     help="configurations per specimen of the uneven three-specimen batch (0: skip)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one configuration of the workload, two image passes (for ncu captures)")
@@ -943,7 +943,8 @@ def main():
     batching = None
     if rank == 0 and args.batch_phonons > 0:
         torch.cuda.synchronize()
-        batching = batching_measure(args.batch_phonons, steps=2)
+        # 32 configurations per specimen is about 19 s per pass: one timed pass per arm
+        batching = batching_measure(args.batch_phonons, steps=1 if args.batch_phonons >= 16 else 2)
 
     cpu = None
     parity = None

@@ -1147,9 +1147,30 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
   return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
 }
 
+// The twiddles one lane uses, read once from the constant table into registers (a constant
+// read whose address differs across the lanes of a warp is serialized): c[b] for the shuffle
+// stage of span h = 2^b, exp(-2 pi i (l mod h) W / (2h) / W); i[jh - 1 + jj] for the in-lane
+// stage of span 32 jh and value index jj = j mod jh, exp(-2 pi i (l + 32 jj) / (64 jh)).
+template <int W>
+struct LaneTw {
+  float2 c[5];
+  float2 i[W / 32 > 1 ? W / 32 - 1 : 1];
+  __device__ __forceinline__ explicit LaneTw(int lane) {
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+      const int h = 1 << b;
+      c[b] = tw<W>((lane & (h - 1)) * (W / (2 * h)));
+    }
+#pragma unroll
+    for (int jh = 1; jh <= W / 64; jh <<= 1)
+#pragma unroll
+      for (int jj = 0; jj < jh; ++jj) i[jh - 1 + jj] = tw<W>((lane + 32 * jj) * (W / (64 * jh)));
+  }
+};
+
 // forward DIF over x[l + 32 j] (v[j] in lane l); afterwards v[j] holds X[brev(l + 32 j)]
 template <int W>
-__device__ __forceinline__ void fft_fwd(float2 (&v)[W / 32], int lane) {
+__device__ __forceinline__ void fft_fwd(float2 (&v)[W / 32], int lane, const LaneTw<W>& tw) {
   constexpr int R = W / 32;
 #pragma unroll
   for (int jh = R / 2; jh >= 1; jh >>= 1) {
@@ -1158,13 +1179,14 @@ __device__ __forceinline__ void fft_fwd(float2 (&v)[W / 32], int lane) {
       if (j & jh) continue;
       const float2 a = v[j], b = v[j + jh];
       v[j] = cadd(a, b);
-      v[j + jh] = cmul(csub(a, b), tw<W>((lane + 32 * (j & (jh - 1))) * (W / (64 * jh))));
+      v[j + jh] = cmul(csub(a, b), tw.i[jh - 1 + (j & (jh - 1))]);
     }
   }
 #pragma unroll
-  for (int h = 16; h >= 1; h >>= 1) {
+  for (int bi = 4; bi >= 0; --bi) {
+    const int h = 1 << bi;
     const bool upper = (lane & h) != 0;
-    const float2 w = tw<W>((lane & (h - 1)) * (W / (2 * h)));
+    const float2 w = tw.c[bi];
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       const float2 p = shfl_xor2(v[j], h);
@@ -1175,12 +1197,13 @@ __device__ __forceinline__ void fft_fwd(float2 (&v)[W / 32], int lane) {
 
 // inverse DIT (conjugate twiddles, no 1/W): v[j] holding X[brev(l + 32 j)] becomes x[l + 32 j]
 template <int W>
-__device__ __forceinline__ void fft_inv(float2 (&v)[W / 32], int lane) {
+__device__ __forceinline__ void fft_inv(float2 (&v)[W / 32], int lane, const LaneTw<W>& tw) {
   constexpr int R = W / 32;
 #pragma unroll
-  for (int h = 1; h <= 16; h <<= 1) {
+  for (int bi = 0; bi <= 4; ++bi) {
+    const int h = 1 << bi;
     const bool upper = (lane & h) != 0;
-    const float2 w = tw<W>((lane & (h - 1)) * (W / (2 * h)));
+    const float2 w = tw.c[bi];
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       const float2 mine = upper ? cmulc(v[j], w) : v[j];
@@ -1194,7 +1217,7 @@ __device__ __forceinline__ void fft_inv(float2 (&v)[W / 32], int lane) {
     for (int j = 0; j < R; ++j) {
       if (j & jh) continue;
       const float2 a = v[j];
-      const float2 b = cmulc(v[j + jh], tw<W>((lane + 32 * (j & (jh - 1))) * (W / (64 * jh))));
+      const float2 b = cmulc(v[j + jh], tw.i[jh - 1 + (j & (jh - 1))]);
       v[j] = cadd(a, b);
       v[j + jh] = csub(a, b);
     }
@@ -1205,32 +1228,63 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return static_cast
 
 }  // namespace gen
 
+// bulk-copy helpers of the W = 256 path (TMA engine, non-tensor form)
+namespace gen {
+__device__ __forceinline__ void expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* smem_dst, const void* gsrc, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(smem_dst)),
+               "l"(gsrc), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* gdst, const void* smem_src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_u32(smem_src)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool wait_load(uint32_t mbar, uint32_t phase) {
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 22) && !done; ++it)
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(phase)
+        : "memory");
+  return done != 0;
+}
+}  // namespace gen
+
 // One translate per CTA at a time (persistent CTAs); complex64 exit waves. scratch: W x W
 // complex64 per CTA (W = 256); status: set to 1 when a bulk-copy wait gives up.
+//
+// W = 256 pipeline: each slice is a column phase and a row phase of 8 panels each (32
+// columns or 32 rows, 64 KiB). A panel is loaded by bulk copies into one of two shared
+// buffers (completion on that buffer's mbarrier), transformed, and stored back by bulk
+// copies; the next panel's load into the other buffer is issued before the current one is
+// transformed, once that buffer's previous store has read it. At the end of a phase every
+// store is complete before the other phase reads the scratch.
 template <int W>
 __global__ void __launch_bounds__(gen::kThreadsGen, 1) k_slice_gen(const SliceLaunch a, float2* scratch, int* status) {
   constexpr int R = W / 32;
   constexpr int kWarps = gen::kThreadsGen / 32;
   constexpr bool kResident = W <= 64;
+  constexpr int kBuf = W * gen::kPanelPitch;              // float2 per panel buffer (W = 256)
   extern __shared__ __align__(16) unsigned char smg[];
-  // W = 64: the wave, [W][W + 1]; W = 256: one column panel, [W][kPanelPitch], and an mbarrier
+  // W = 64: the wave, [W][W + 1]; W = 256: two panel buffers and their mbarriers
   float2* const S = reinterpret_cast<float2*>(smg);
-  uint64_t* const mbar = reinterpret_cast<uint64_t*>(smg + (kResident ? W * (W + 1) : W * gen::kPanelPitch) * 8);
+  uint64_t* const mbar = reinterpret_cast<uint64_t*>(smg + (kResident ? W * (W + 1) : 2 * kBuf) * 8);
   const int T = threadIdx.x, warp = T >> 5, lane = T & 31;
+  const gen::LaneTw<W> tw(lane);
   float2* const G = kResident ? nullptr : scratch + static_cast<size_t>(blockIdx.x) * W * W;
-  const uint32_t mb = gen::smem_u32(mbar);
-  if (!kResident && T == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (!kResident && T < 2) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(gen::smem_u32(mbar + T)) : "memory");
+    if (T == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  uint32_t phase = 0;
+  uint32_t ph[2] = {0u, 0u};
   bool bad = false;
-  // element (y, x) of the wave
-  auto at = [&](int y, int x) -> float2& {
-    if constexpr (kResident) return S[y * (W + 1) + x];
-    else return G[static_cast<size_t>(y) * W + x];
-  };
 
   for (int li = blockIdx.x; li < a.n_list; li += gridDim.x) {
     int jb = 0;
@@ -1255,40 +1309,45 @@ __global__ void __launch_bounds__(gen::kThreadsGen, 1) k_slice_gen(const SliceLa
       if (gx >= J.nx) gx -= J.nx;
       return tbase[s * slice_elems + static_cast<size_t>(gy) * pitch + gx];
     };
-    __syncthreads();   // the previous item's use of the wave and the panel is over
-    // rows: input wave, transmission of slice 0, forward transform
-    for (int y = warp; y < W && n_slices > 0; y += kWarps) {
-      float2 v[R];
+    // columns: forward transform, propagator (Sec. 3.2) at (kx, ky) = (brev(x), brev(y)),
+    // inverse transform
+    auto column = [&](float2 (&v)[R], int x) {
+      gen::fft_fwd<W>(v, lane, tw);
+      const int kxb = gen::brev<W>(x);
+      const int kxs = kxb < W / 2 ? kxb : kxb - W;
+      const float2 ex = J.ex[kxb];
 #pragma unroll
-      for (int j = 0; j < R; ++j) v[j] = cmul(J.uW[y * W + lane + 32 * j], tval(0, y, lane + 32 * j));
-      gen::fft_fwd<W>(v, lane);
+      for (int j = 0; j < R; ++j) {
+        const int kyb = gen::brev<W>(lane + 32 * j);
+        const int kys = kyb < W / 2 ? kyb : kyb - W;
+        v[j] = kxs * kxs + kys * kys <= J.r2max ? cmul(v[j], cmul(ex, J.ey[kyb])) : make_float2(0.f, 0.f);
+      }
+      gen::fft_inv<W>(v, lane, tw);
+    };
+    // rows after the column phase: inverse transform, then (if another slice follows) its
+    // transmission and the forward transform
+    auto row = [&](float2 (&v)[R], int y, int s) {
+      gen::fft_inv<W>(v, lane, tw);
+      if (s + 1 < n_slices) {
 #pragma unroll
-      for (int j = 0; j < R; ++j) at(y, lane + 32 * j) = v[j];
-    }
-    if (n_slices == 0)
-      for (int y = warp; y < W; y += kWarps)
+        for (int j = 0; j < R; ++j) v[j] = cmul(v[j], tval(s + 1, y, lane + 32 * j));
+        gen::fft_fwd<W>(v, lane, tw);
+      }
+    };
+    __syncthreads();   // the previous item's use of the wave and the buffers is over
+    if constexpr (kResident) {
+      // rows: input wave, transmission of slice 0, forward transform
+      for (int y = warp; y < W; y += kWarps) {
+        float2 v[R];
 #pragma unroll
-        for (int j = 0; j < R; ++j) at(y, lane + 32 * j) = J.uW[y * W + lane + 32 * j];
-    for (int s = 0; s < n_slices; ++s) {
-      // the rows' generic writes to the scratch are ordered before the bulk copies read it
-      if constexpr (!kResident) asm volatile("fence.proxy.async.global;" ::: "memory");
-      __syncthreads();
-      // columns: forward transform, propagator (Sec. 3.2) at (kx, ky) = (brev(x), brev(y)),
-      // inverse transform
-      auto column = [&](float2 (&v)[R], int x) {
-        gen::fft_fwd<W>(v, lane);
-        const int kxb = gen::brev<W>(x);
-        const int kxs = kxb < W / 2 ? kxb : kxb - W;
-        const float2 ex = J.ex[kxb];
+        for (int j = 0; j < R; ++j)
+          v[j] = n_slices > 0 ? cmul(J.uW[y * W + lane + 32 * j], tval(0, y, lane + 32 * j)) : J.uW[y * W + lane + 32 * j];
+        if (n_slices > 0) gen::fft_fwd<W>(v, lane, tw);
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
-          const int kyb = gen::brev<W>(lane + 32 * j);
-          const int kys = kyb < W / 2 ? kyb : kyb - W;
-          v[j] = kxs * kxs + kys * kys <= J.r2max ? cmul(v[j], cmul(ex, J.ey[kyb])) : make_float2(0.f, 0.f);
-        }
-        gen::fft_inv<W>(v, lane);
-      };
-      if constexpr (kResident) {
+        for (int j = 0; j < R; ++j) S[y * (W + 1) + lane + 32 * j] = v[j];
+      }
+      for (int s = 0; s < n_slices; ++s) {
+        __syncthreads();
         for (int x = warp; x < W; x += kWarps) {
           float2 v[R];
 #pragma unroll
@@ -1297,78 +1356,108 @@ __global__ void __launch_bounds__(gen::kThreadsGen, 1) k_slice_gen(const SliceLa
 #pragma unroll
           for (int j = 0; j < R; ++j) S[(lane + 32 * j) * (W + 1) + x] = v[j];
         }
-      } else {
-        for (int x0 = 0; x0 < W; x0 += gen::kPanel) {
-          // panel load: W segments of 256 bytes, one per thread of the first W threads
-          if (T == 0)
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
-                         "r"(W * gen::kPanel * 8)
-                         : "memory");
-          __syncthreads();   // expect_tx is set before any copy can complete
-          if (T < W)
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    gen::smem_u32(S + T * gen::kPanelPitch)),
-                "l"(G + static_cast<size_t>(T) * W + x0), "r"(gen::kPanel * 8), "r"(mb)
-                : "memory");
-          uint32_t done = 0;
-          for (int it = 0; it < (1 << 22) && !done; ++it)
-            asm volatile(
-                "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                : "=r"(done)
-                : "r"(mb), "r"(phase)
-                : "memory");
-          phase ^= 1;
-          bad |= !done;
-          if (done) {
-            for (int c = warp; c < gen::kPanel; c += kWarps) {
-              float2 v[R];
+        __syncthreads();
+        for (int y = warp; y < W; y += kWarps) {
+          float2 v[R];
 #pragma unroll
-              for (int j = 0; j < R; ++j) v[j] = S[(lane + 32 * j) * gen::kPanelPitch + c];
-              column(v, x0 + c);
+          for (int j = 0; j < R; ++j) v[j] = S[y * (W + 1) + lane + 32 * j];
+          row(v, y, s);
 #pragma unroll
-              for (int j = 0; j < R; ++j) S[(lane + 32 * j) * gen::kPanelPitch + c] = v[j];
-            }
-          }
-          // panel store: the threads' writes are made visible to the bulk copies first
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          __syncthreads();
-          if (T < W) {
-            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(
-                             G + static_cast<size_t>(T) * W + x0),
-                         "r"(gen::smem_u32(S + T * gen::kPanelPitch)), "r"(gen::kPanel * 8)
-                         : "memory");
-            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-            // the panel buffer is reloaded next: its reads by the store are over first;
-            // the rows pass reads the stored values: their writes are complete and ordered
-            // before the generic reads
-            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-            asm volatile("fence.proxy.async.global;" ::: "memory");
-          }
-          __syncthreads();
+          for (int j = 0; j < R; ++j) S[y * (W + 1) + lane + 32 * j] = v[j];
         }
       }
       __syncthreads();
-      // rows: inverse transform, then the next slice's transmission and forward transform
-      const bool more = s + 1 < n_slices;
+      const int oi = a.out_index ? a.out_index[li] : ti;
+      float2* const ud = J.U + cfg * J.u_slot + static_cast<size_t>(oi) * (W * W);
+      for (int e = T; e < W * W; e += gen::kThreadsGen) ud[e] = S[(e / W) * (W + 1) + e % W];
+    } else {
+      constexpr int kPanels = W / gen::kPanel;
+      // rows of the scratch: input wave, transmission of slice 0, forward transform (plain
+      // coalesced stores; ordered before the bulk copies by the proxy fence below)
       for (int y = warp; y < W; y += kWarps) {
         float2 v[R];
 #pragma unroll
-        for (int j = 0; j < R; ++j) v[j] = at(y, lane + 32 * j);
-        gen::fft_inv<W>(v, lane);
-        if (more) {
+        for (int j = 0; j < R; ++j)
+          v[j] = n_slices > 0 ? cmul(J.uW[y * W + lane + 32 * j], tval(0, y, lane + 32 * j)) : J.uW[y * W + lane + 32 * j];
+        if (n_slices > 0) gen::fft_fwd<W>(v, lane, tw);
 #pragma unroll
-          for (int j = 0; j < R; ++j) v[j] = cmul(v[j], tval(s + 1, y, lane + 32 * j));
-          gen::fft_fwd<W>(v, lane);
-        }
-#pragma unroll
-        for (int j = 0; j < R; ++j) at(y, lane + 32 * j) = v[j];
+        for (int j = 0; j < R; ++j) G[static_cast<size_t>(y) * W + lane + 32 * j] = v[j];
       }
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      __syncthreads();
+      for (int s = 0; s < n_slices && !bad; ++s) {
+        for (int phase_k = 0; phase_k < 2 && !bad; ++phase_k) {
+          const bool cols = phase_k == 0;
+          // issue the load of panel p into buffer p & 1 (T = 0 sets the byte count first)
+          auto issue_load = [&](int p) {
+            const int b = p & 1;
+            float2* const buf = S + b * kBuf;
+            const uint32_t mb = gen::smem_u32(mbar + b);
+            if (T == 0) gen::expect_tx(mb, static_cast<uint32_t>(W) * gen::kPanel * 8);
+            __syncthreads();
+            if (cols) {
+              if (T < W) gen::bulk_load(buf + T * gen::kPanelPitch, G + static_cast<size_t>(T) * W + p * gen::kPanel,
+                                        gen::kPanel * 8, mb);
+            } else if (T == 0) {
+              gen::bulk_load(buf, G + static_cast<size_t>(p) * gen::kPanel * W, W * gen::kPanel * 8, mb);
+            }
+          };
+          issue_load(0);
+          for (int p = 0; p < kPanels; ++p) {
+            const int b = p & 1;
+            float2* const buf = S + b * kBuf;
+            if (p + 1 < kPanels) {
+              // the other buffer's last store (panel p - 1) has read it before the next load
+              asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+              issue_load(p + 1);
+            }
+            const bool ok = gen::wait_load(gen::smem_u32(mbar + b), ph[b]);
+            ph[b] ^= 1;
+            bad |= !ok;
+            if (ok) {
+              if (cols) {
+                for (int c = warp; c < gen::kPanel; c += kWarps) {
+                  float2 v[R];
+#pragma unroll
+                  for (int j = 0; j < R; ++j) v[j] = buf[(lane + 32 * j) * gen::kPanelPitch + c];
+                  column(v, p * gen::kPanel + c);
+#pragma unroll
+                  for (int j = 0; j < R; ++j) buf[(lane + 32 * j) * gen::kPanelPitch + c] = v[j];
+                }
+              } else {
+                for (int r = warp; r < gen::kPanel; r += kWarps) {
+                  float2 v[R];
+#pragma unroll
+                  for (int j = 0; j < R; ++j) v[j] = buf[r * W + lane + 32 * j];
+                  row(v, p * gen::kPanel + r, s);
+#pragma unroll
+                  for (int j = 0; j < R; ++j) buf[r * W + lane + 32 * j] = v[j];
+                }
+              }
+            }
+            // the threads' writes are made visible to the bulk copies, then the panel goes back
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (cols) {
+              if (T < W) gen::bulk_store(G + static_cast<size_t>(T) * W + p * gen::kPanel, buf + T * gen::kPanelPitch,
+                                         gen::kPanel * 8);
+            } else if (T == 0) {
+              gen::bulk_store(G + static_cast<size_t>(p) * gen::kPanel * W, buf, W * gen::kPanel * 8);
+            }
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          }
+          // every store of the phase is complete (and ordered before the generic and bulk
+          // reads of the next phase)
+          asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+          asm volatile("fence.proxy.async.global;" ::: "memory");
+          bad = __syncthreads_or(bad);
+        }
+      }
+      if (__syncthreads_or(bad)) break;
+      const int oi = a.out_index ? a.out_index[li] : ti;
+      float2* const ud = J.U + cfg * J.u_slot + static_cast<size_t>(oi) * (W * W);
+      for (int e = T; e < W * W; e += gen::kThreadsGen) ud[e] = G[e];
     }
-    if (__syncthreads_or(bad)) break;
-    const int oi = a.out_index ? a.out_index[li] : ti;
-    float2* const ud = J.U + cfg * J.u_slot + static_cast<size_t>(oi) * (W * W);
-    for (int e = T; e < W * W; e += gen::kThreadsGen) ud[e] = at(e / W, e % W);
   }
   if (bad && T == 0) atomicOr(status, 1);
 }
@@ -2064,7 +2153,7 @@ size_t slice_smem_bytes() { return static_cast<size_t>(kSliceSmemFloat2) * sizeo
 size_t synth_smem_bytes() { return static_cast<size_t>(kSynthSmemFloat2) * sizeof(float2); }
 size_t slice_tc_smem_bytes() { return static_cast<size_t>(kSliceTcSmemBytes); }
 static size_t slice_gen_smem_bytes(int W) {
-  return (W <= 64 ? static_cast<size_t>(W) * (W + 1) : static_cast<size_t>(W) * gen::kPanelPitch) * sizeof(float2) + 16;
+  return (W <= 64 ? static_cast<size_t>(W) * (W + 1) : 2 * static_cast<size_t>(W) * gen::kPanelPitch) * sizeof(float2) + 16;
 }
 size_t slice_gen_scratch_bytes(int W) {
   return W <= 64 ? 0 : static_cast<size_t>(sm_count()) * W * W * sizeof(float2);
