@@ -141,6 +141,9 @@ size_t slice_tc_smem_bytes();
 // persistent CTAs, one per SM; W = 256 needs slice_gen_scratch_bytes(256) of scratch
 cudaError_t launch_slice_gen(const SliceLaunch& a, int W, float2* scratch, cudaStream_t s);
 size_t slice_gen_scratch_bytes(int W);
+// one warp runs the bounded mbarrier wait of the tensor-core (which = 0) or W = 256 (which = 1)
+// slice kernel on a phase that never completes; *status |= 1 when it gives up
+cudaError_t launch_selftest_wait(int which, int* status, cudaStream_t s);
 cudaError_t launch_synth(const SynthArgs& a, bool half, int mode, cudaStream_t s);
 // step a3 with the propagation as a periodic convolution with the K1 x K2 kernel q (device,
 // [K2][K1] complex64, offsets -(K/2) .. K/2); K1 in {3, 5, ..., 13}, K2 odd <= 25; complex64 store

@@ -948,8 +948,8 @@ lma_status ensure_counter(lma_ctx* ctx) {
   return LMA_OK;
 }
 
-// After a synchronizing read: did a tensor-core slice launch give up a bounded wait?
-// (The status word is read only when such a launch ran since the last check.)
+// After a synchronizing read: did a slice launch with bounded waits (tensor-core or W = 256)
+// give up one? (The status word is read only when such a launch ran since the last check.)
 lma_status check_slice_status(lma_ctx* ctx) {
   if (!ctx->tc_launched || !ctx->d_counter) return LMA_OK;
   int st = 0;
@@ -957,7 +957,7 @@ lma_status check_slice_status(lma_ctx* ctx) {
   ctx->tc_launched = false;
   if (st != 0) {
     CUDA_TRY(ctx, cudaMemset(ctx->d_counter + 1, 0, sizeof(int)));
-    return fail(ctx, LMA_ERR_TIMEOUT, "a tensor-core slice launch gave up waiting for its MMAs; results are invalid");
+    return fail(ctx, LMA_ERR_TIMEOUT, "a slice launch gave up a bounded wait for its MMAs or bulk copies; results are invalid");
   }
   return LMA_OK;
 }
@@ -2226,6 +2226,19 @@ static void realspace_kernel_host(const lma_basis* b, int K1, int K2, std::vecto
     q[2 * k] = static_cast<float>(qd[k].real());
     q[2 * k + 1] = static_cast<float>(qd[k].imag());
   }
+}
+
+lma_status lma_selftest_wait(lma_ctx* ctx, int32_t which, void* stream) {
+  if (!ctx) return LMA_ERR_INVALID;
+  if (which != 0 && which != 1) return fail(ctx, LMA_ERR_INVALID, "lma_selftest_wait: which must be 0 or 1");
+  if (!device_ready(ctx)) return fail(ctx, LMA_ERR_UNSUPPORTED, "no device in this context");
+  const lma_status s0 = ensure_counter(ctx);
+  if (s0 != LMA_OK) return s0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CUDA_TRY(ctx, lma_dev::launch_selftest_wait(which, ctx->d_counter + 1, st));
+  ctx->tc_launched = true;
+  CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  return check_slice_status(ctx);
 }
 
 lma_status lma_realspace_gain(lma_ctx* ctx, const lma_basis* b, int32_t K1, int32_t K2, double* gain_all,

@@ -1256,6 +1256,22 @@ __device__ __forceinline__ bool wait_load(uint32_t mbar, uint32_t phase) {
 }
 }  // namespace gen
 
+// Self-test of the bounded waits: one warp waits on phase 0 of an mbarrier that nothing
+// completes, with the wait of the tensor-core slice kernel (which = 0: lane 0 suspended up to
+// kSuspendLimit tries of kSuspendNs) or of the W = 256 kernel (which = 1: every lane polls
+// 2^22 times), and reports the give-up in *status as those kernels do.
+__global__ void k_selftest_wait(int which, int* status) {
+  __shared__ __align__(8) uint64_t mbar;
+  const uint32_t mb = tc::smem_u32(&mbar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const bool ok = which == 0 ? tc::wait_phase_warp(mb, 0) : __all_sync(0xffffffffu, gen::wait_load(mb, 0));
+  if (!ok && threadIdx.x == 0) atomicOr(status, 1);
+}
+
 // One translate per CTA at a time (persistent CTAs); complex64 exit waves. scratch: W x W
 // complex64 per CTA (W = 256); status: set to 1 when a bulk-copy wait gives up.
 //
@@ -2154,6 +2170,10 @@ size_t synth_smem_bytes() { return static_cast<size_t>(kSynthSmemFloat2) * sizeo
 size_t slice_tc_smem_bytes() { return static_cast<size_t>(kSliceTcSmemBytes); }
 static size_t slice_gen_smem_bytes(int W) {
   return (W <= 64 ? static_cast<size_t>(W) * (W + 1) : 2 * static_cast<size_t>(W) * gen::kPanelPitch) * sizeof(float2) + 16;
+}
+cudaError_t launch_selftest_wait(int which, int* status, cudaStream_t s) {
+  k_selftest_wait<<<1, 32, 0, s>>>(which, status);
+  return cudaGetLastError();
 }
 size_t slice_gen_scratch_bytes(int W) {
   return W <= 64 ? 0 : static_cast<size_t>(sm_count()) * W * W * sizeof(float2);

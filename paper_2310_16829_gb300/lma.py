@@ -64,7 +64,7 @@ EXPORTS = [
     "lma_affected_probes",
     "lma_profile_enable", "lma_profile_read", "lma_readout_noalloc", "lma_realspace_gain",
     "lma_set_slice_mode", "lma_tuning_read", "lma_partition", "lma_image_partitioned",
-    "lma_image_coherent", "lma_select_L", "lma_image_realspace",
+    "lma_image_coherent", "lma_select_L", "lma_image_realspace", "lma_selftest_wait",
 ]
 
 
@@ -178,6 +178,7 @@ _SIGS = {
                                     C.c_int16, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "lma_affected_probes": (C.c_int32, [_VP, _VP, C.POINTER(Region), _VP, C.POINTER(C.c_int64)]),
     "lma_realspace_gain": (C.c_int32, [_VP, _VP, C.c_int32, C.c_int32, _VP, _VP]),
+    "lma_selftest_wait": (C.c_int32, [_VP, C.c_int32, _VP]),
     "lma_readout_noalloc": (C.c_int32, [_VP, _VP, _VP, C.POINTER(Detector), C.c_int32, C.POINTER(Region),
                                         _VP, _VP]),
     "lma_set_slice_mode": (C.c_int32, [_VP, C.c_int32]),
@@ -260,6 +261,12 @@ class Context:
         p = Profile()
         self.check(self.lib.lma_profile_read(self.h, C.byref(p)))
         return p.as_dict()
+
+    def selftest_wait(self, which: int, stream=None) -> int:
+        """Run one bounded device wait on an mbarrier phase that never completes (0: the
+        tensor-core slice kernel's form, 1: the W = 256 kernel's); returns the status code,
+        LMA_ERR_TIMEOUT when the wait gave up as it should."""
+        return self.lib.lma_selftest_wait(self.h, which, _stream(stream))
 
     def set_slice_mode(self, mode: int) -> None:
         self.check(self.lib.lma_set_slice_mode(self.h, mode))

@@ -332,3 +332,12 @@ def test_realspace_gain_matches_the_dft_of_the_oracle_kernel():
     with pytest.raises(lma.LmaError):
         basis.realspace_gain(4, 3)
 
+
+
+def test_selftest_wait_checks_its_arguments_before_the_device():
+    """lma_selftest_wait rejects an unknown wait form with LMA_ERR_INVALID and needs a device
+    for the known ones (host-only context: LMA_ERR_UNSUPPORTED)."""
+    ctx = lma.Context(-1)
+    assert ctx.selftest_wait(2) == lma.LMA_ERR_INVALID
+    assert ctx.selftest_wait(-1) == lma.LMA_ERR_INVALID
+    assert ctx.selftest_wait(0) == lma.LMA_ERR_UNSUPPORTED

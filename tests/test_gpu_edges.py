@@ -143,3 +143,34 @@ def test_fp16_store_readouts_are_consistent():
     full = lma.Basis(ctx, spec_w, wide.probe, dataclasses.replace(wide.basis, precision=WL.PREC_C64)
                      ).image(bf, wide.region, recompute=True)
     assert np.max(np.abs(half / full - 1)) < 1e-3
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_bounded_wait_gives_up_and_the_context_stays_usable(which):
+    """The bounded mbarrier waits of the tensor-core (0) and W = 256 (1) slice kernels, run on
+    a phase that nothing completes, give up, and the call returns LMA_ERR_TIMEOUT. The status
+    word is cleared: the next tensor-core image in the same context is bit for bit the image
+    of a fresh context."""
+    import time
+
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    c1 = lma.Context(0)
+    t0 = time.perf_counter()
+    st = c1.selftest_wait(which)
+    dt = time.perf_counter() - t0
+    assert st == lma.LMA_ERR_TIMEOUT, st
+    assert "gave up a bounded wait" in c1.lib.lma_last_error(c1.h).decode()
+    assert dt < 30.0, dt
+    w = WL.simple_cubic_workload()
+    w = dataclasses.replace(w, basis=dataclasses.replace(w.basis, precision=WL.PREC_MIXED))
+    region = WL.Region(0, 0, 4, 4, (8, 8))
+
+    def image(c):
+        spec = lma.Specimen(c, w.grid, w.potential, w.phonons)
+        basis = lma.Basis(c, spec, w.probe, w.basis)
+        return basis.image(w.detectors, region, recompute=True)
+
+    got = image(c1)
+    ref = image(lma.Context(0))
+    assert np.array_equal(got, ref)
