@@ -317,14 +317,14 @@ lma_status lma_image_realspace(lma_ctx* ctx, lma_specimen* spec, lma_basis* basi
 
 /* Self-test of the bounded device waits. The tensor-core slice kernel (LMA_PREC_MIXED) and
  * the W = 256 slice kernel wait on shared-memory mbarriers for the MMAs and bulk copies they
- * issue. Each wait is bounded (the tensor-core form: 2000 suspended tries of up to 1 ms; the
- * bulk-copy form: 2^22 polls); a wait that gives up sets the launch's status word, the kernel
- * returns, and the next call that reads results returns LMA_ERR_TIMEOUT. This call runs the
- * wait of one form (which = 0: tensor-core, 1: bulk-copy) in one warp on an mbarrier phase
- * that nothing completes, on `stream`, synchronizes it and returns what a real give-up returns:
- * LMA_ERR_TIMEOUT with its message; the status word is cleared and the context stays usable.
- * LMA_ERR_INVALID for another `which`, LMA_ERR_UNSUPPORTED without a device. Takes up to a few
- * seconds. */
+ * issue, each wait one polling lane per warp with at most 2000 suspended tries of up to 1 ms;
+ * a wait that gives up sets the launch's status word, the kernel returns, and the next call
+ * that reads results returns LMA_ERR_TIMEOUT. This call runs that wait on an mbarrier phase
+ * that nothing completes, in one warp (which = 0, as in the tensor-core kernel's per-tile
+ * waits) or in the 16 warps of a CTA (which = 1, as in the W = 256 kernel's panel waits), on
+ * `stream`, synchronizes it and returns what a real give-up returns: LMA_ERR_TIMEOUT with its
+ * message; the status word is cleared and the context stays usable. LMA_ERR_INVALID for
+ * another `which`, LMA_ERR_UNSUPPORTED without a device. Takes a few seconds. */
 lma_status lma_selftest_wait(lma_ctx* ctx, int32_t which, void* stream);
 
 /* Per-slice amplification of the real-space propagation step (Sec. 3.2, complexity

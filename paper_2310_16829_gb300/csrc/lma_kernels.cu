@@ -110,8 +110,8 @@ __device__ __forceinline__ void static_for(F&& f) {
 // NX / NY: whether X = t[I] / Y = t[I + H] is needed; Z (M = 0 only): 1 if a is known to
 // be zero, 2 if b is (the outputs are then copies of the other input, exactly as the sum
 // and difference would give).
-template <bool INV, int I, int H, int M, bool NX = true, bool NY = true, int Z = 0>
-__device__ __forceinline__ void bfly(float2 (&t)[32]) {
+template <bool INV, int I, int H, int M, bool NX = true, bool NY = true, int Z = 0, int N = 32>
+__device__ __forceinline__ void bfly(float2 (&t)[N]) {
   const float2 a = t[I];
   const float2 b = t[I + H];
   if constexpr (Z == 1) {
@@ -195,6 +195,32 @@ __device__ __forceinline__ void dft32(float2 (&v)[32]) {
     });
   });
   static_for<0, 32>([&](auto k) {
+    constexpr int K = decltype(k)::value;
+    v[K] = t[K];
+  });
+}
+
+// In-register 16-point DFT, natural order in and out: the first four stages of dft32 on 16
+// values (W_16^m = W_32^(2m), so stage H takes the twiddle index j (16 / H) of dft32)
+__host__ __device__ constexpr int brev4(int k) { return ((k & 1) << 3) | ((k & 2) << 1) | ((k & 4) >> 1) | ((k & 8) >> 3); }
+template <bool INV>
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+  float2 t[16];
+  static_for<0, 16>([&](auto k) {
+    constexpr int K = decltype(k)::value;
+    t[K] = v[brev4(K)];
+  });
+  static_for<0, 4>([&](auto st) {
+    constexpr int H = 1 << decltype(st)::value;
+    static_for<0, 8 / H>([&](auto blk) {
+      static_for<0, H>([&](auto j) {
+        constexpr int I = decltype(blk)::value * 2 * H + decltype(j)::value;
+        constexpr int M = decltype(j)::value * (16 / H);
+        bfly<INV, I, H, M>(t);
+      });
+    });
+  });
+  static_for<0, 16>([&](auto k) {
     constexpr int K = decltype(k)::value;
     v[K] = t[K];
   });
@@ -1105,7 +1131,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice_tc(const SliceLaunch a, i
 }
 
 // ------------------------------------------------------------------------------------------
-// step a3 on windows W = 64 and W = 256 (k_slice_gen)
+// step a3 on windows W = 64 (k_slice_gen)
 // ------------------------------------------------------------------------------------------
 // Every W-point transform (a row or a column of the window) is done by one warp in registers:
 // lane l holds the R = W / 32 values of indices l + 32 j. The forward transform is radix-2
@@ -1115,33 +1141,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice_tc(const SliceLaunch a, i
 // transforms are decimation in time (bit-reversed in, natural out), so no pass reorders data.
 // Each slice is two passes: columns (forward, propagator, inverse), then rows (inverse, the
 // next slice's transmission, forward); the first slice's transmission and forward rows come
-// before the loop, the last inverse rows after it.
-//
-// W = 64: the wave (32 KiB) stays in shared memory, rows padded to 65 values. W = 256: the
-// wave (512 KiB) is more than one SM holds, so it lives in a scratch area of global memory, one
-// per CTA (L2-resident with one CTA per SM). Rows are read and written there directly
-// (coalesced); columns go through shared memory in panels of 32 columns, each panel row a
-// 256-byte segment moved by the TMA engine's bulk copies (cp.async.bulk), completed on an
-// mbarrier (loads) or a bulk group (stores).
+// before the loop, the last inverse rows after it. The wave (32 KiB) stays in shared memory,
+// rows padded to 65 values. (W = 256 has its own kernel, k_slice_256, below.)
 namespace gen {
 
 constexpr int kThreadsGen = 512;
-constexpr int kPanel = 32;                // columns per panel (W = 256)
-constexpr int kPanelPitch = 34;           // complex values per panel row (16-byte rows)
 
 // exp(-2 pi i m / W), m < W / 2, built on the host in FP64 and rounded once
 __constant__ float2 c_tw64[32];
-__constant__ float2 c_tw256[128];
 
 template <int W>
 __device__ __forceinline__ float2 tw(int m) {
-  if constexpr (W == 64) return c_tw64[m];
-  else return c_tw256[m];
+  static_assert(W == 64, "the warp transforms serve W = 64");
+  return c_tw64[m];
 }
 template <int W>
 __device__ __forceinline__ int brev(int i) {
-  constexpr int bits = W == 64 ? 6 : 8;
-  return static_cast<int>(__brev(static_cast<unsigned>(i)) >> (32 - bits));
+  static_assert(W == 64, "the warp transforms serve W = 64");
+  return static_cast<int>(__brev(static_cast<unsigned>(i)) >> 26);
 }
 __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
   return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
@@ -1233,74 +1250,35 @@ namespace gen {
 __device__ __forceinline__ void expect_tx(uint32_t mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void bulk_load(void* smem_dst, const void* gsrc, uint32_t bytes, uint32_t mbar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(smem_dst)),
-               "l"(gsrc), "r"(bytes), "r"(mbar)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_store(void* gdst, const void* smem_src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_u32(smem_src)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool wait_load(uint32_t mbar, uint32_t phase) {
-  uint32_t done = 0;
-  for (int it = 0; it < (1 << 22) && !done; ++it)
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(phase)
-        : "memory");
-  return done != 0;
-}
 }  // namespace gen
 
-// Self-test of the bounded waits: one warp waits on phase 0 of an mbarrier that nothing
-// completes, with the wait of the tensor-core slice kernel (which = 0: lane 0 suspended up to
-// kSuspendLimit tries of kSuspendNs) or of the W = 256 kernel (which = 1: every lane polls
-// 2^22 times), and reports the give-up in *status as those kernels do.
-__global__ void k_selftest_wait(int which, int* status) {
+// Self-test of the bounded waits: warps wait on phase 0 of an mbarrier that nothing completes,
+// with the bounded warp wait of the tensor-core and W = 256 slice kernels (lane 0 suspended up
+// to kSuspendLimit tries of kSuspendNs, then one try_wait per lane), in one warp (which = 0) or
+// in the 16 warps of a W = 256 CTA (which = 1), and report the give-up in *status as those
+// kernels do.
+__global__ void k_selftest_wait(int* status) {
   __shared__ __align__(8) uint64_t mbar;
   const uint32_t mb = tc::smem_u32(&mbar);
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  __syncwarp();
-  const bool ok = which == 0 ? tc::wait_phase_warp(mb, 0) : __all_sync(0xffffffffu, gen::wait_load(mb, 0));
-  if (!ok && threadIdx.x == 0) atomicOr(status, 1);
+  __syncthreads();
+  const bool ok = tc::wait_phase_warp(mb, 0);
+  if (!ok && (threadIdx.x & 31) == 0) atomicOr(status, 1);
 }
 
-// One translate per CTA at a time (persistent CTAs); complex64 exit waves. scratch: W x W
-// complex64 per CTA (W = 256); status: set to 1 when a bulk-copy wait gives up.
-//
-// W = 256 pipeline: each slice is a column phase and a row phase of 8 panels each (32
-// columns or 32 rows, 64 KiB). A panel is loaded by bulk copies into one of two shared
-// buffers (completion on that buffer's mbarrier), transformed, and stored back by bulk
-// copies; the next panel's load into the other buffer is issued before the current one is
-// transformed, once that buffer's previous store has read it. At the end of a phase every
-// store is complete before the other phase reads the scratch.
+// One translate per CTA at a time (persistent CTAs); complex64 exit waves, W = 64.
 template <int W>
-__global__ void __launch_bounds__(gen::kThreadsGen, 1) k_slice_gen(const SliceLaunch a, float2* scratch, int* status) {
+__global__ void __launch_bounds__(gen::kThreadsGen, 1) k_slice_gen(const SliceLaunch a) {
+  static_assert(W == 64, "the wave of W = 64 stays in shared memory");
   constexpr int R = W / 32;
   constexpr int kWarps = gen::kThreadsGen / 32;
-  constexpr bool kResident = W <= 64;
-  constexpr int kBuf = W * gen::kPanelPitch;              // float2 per panel buffer (W = 256)
   extern __shared__ __align__(16) unsigned char smg[];
-  // W = 64: the wave, [W][W + 1]; W = 256: two panel buffers and their mbarriers
-  float2* const S = reinterpret_cast<float2*>(smg);
-  uint64_t* const mbar = reinterpret_cast<uint64_t*>(smg + (kResident ? W * (W + 1) : 2 * kBuf) * 8);
+  float2* const S = reinterpret_cast<float2*>(smg);   // the wave, [W][W + 1]
   const int T = threadIdx.x, warp = T >> 5, lane = T & 31;
   const gen::LaneTw<W> tw(lane);
-  float2* const G = kResident ? nullptr : scratch + static_cast<size_t>(blockIdx.x) * W * W;
-  if (!kResident && T < 2) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(gen::smem_u32(mbar + T)) : "memory");
-    if (T == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  uint32_t ph[2] = {0u, 0u};
-  bool bad = false;
 
   for (int li = blockIdx.x; li < a.n_list; li += gridDim.x) {
     int jb = 0;
@@ -1350,130 +1328,335 @@ __global__ void __launch_bounds__(gen::kThreadsGen, 1) k_slice_gen(const SliceLa
         gen::fft_fwd<W>(v, lane, tw);
       }
     };
-    __syncthreads();   // the previous item's use of the wave and the buffers is over
-    if constexpr (kResident) {
-      // rows: input wave, transmission of slice 0, forward transform
+    __syncthreads();   // the previous item's use of the wave is over
+    // rows: input wave, transmission of slice 0, forward transform
+    for (int y = warp; y < W; y += kWarps) {
+      float2 v[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j)
+        v[j] = n_slices > 0 ? cmul(J.uW[y * W + lane + 32 * j], tval(0, y, lane + 32 * j)) : J.uW[y * W + lane + 32 * j];
+      if (n_slices > 0) gen::fft_fwd<W>(v, lane, tw);
+#pragma unroll
+      for (int j = 0; j < R; ++j) S[y * (W + 1) + lane + 32 * j] = v[j];
+    }
+    for (int s = 0; s < n_slices; ++s) {
+      __syncthreads();
+      for (int x = warp; x < W; x += kWarps) {
+        float2 v[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) v[j] = S[(lane + 32 * j) * (W + 1) + x];
+        column(v, x);
+#pragma unroll
+        for (int j = 0; j < R; ++j) S[(lane + 32 * j) * (W + 1) + x] = v[j];
+      }
+      __syncthreads();
       for (int y = warp; y < W; y += kWarps) {
         float2 v[R];
 #pragma unroll
-        for (int j = 0; j < R; ++j)
-          v[j] = n_slices > 0 ? cmul(J.uW[y * W + lane + 32 * j], tval(0, y, lane + 32 * j)) : J.uW[y * W + lane + 32 * j];
-        if (n_slices > 0) gen::fft_fwd<W>(v, lane, tw);
+        for (int j = 0; j < R; ++j) v[j] = S[y * (W + 1) + lane + 32 * j];
+        row(v, y, s);
 #pragma unroll
         for (int j = 0; j < R; ++j) S[y * (W + 1) + lane + 32 * j] = v[j];
       }
-      for (int s = 0; s < n_slices; ++s) {
-        __syncthreads();
-        for (int x = warp; x < W; x += kWarps) {
-          float2 v[R];
+    }
+    __syncthreads();
+    const int oi = a.out_index ? a.out_index[li] : ti;
+    float2* const ud = J.U + cfg * J.u_slot + static_cast<size_t>(oi) * (W * W);
+    for (int e = T; e < W * W; e += gen::kThreadsGen) ud[e] = S[(e / W) * (W + 1) + e % W];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// step a3 on W = 256 windows: each 256-point transform as two in-register 16-point passes
+// ------------------------------------------------------------------------------------------
+// With x = 16 n + q and k = k1 + 16 k2 (Cooley-Tukey, 256 = 16 x 16),
+//   X[k1 + 16 k2] = sum_q W_16^(q k2) W_256^(q k1) sum_n W_16^(n k1) x[16 n + q].
+// Pass 1: the thread of residue q takes x[16 n + q] (n < 16), takes the 16-point DFT over n,
+// multiplies by W_256^(q k1) and puts the results back where it read them (entry 16 k1 + q).
+// Pass 2: the thread of k1 takes entries 16 k1 + q (q < 16), takes the DFT over q and puts
+// X[k1 + 16 k2] at entry 16 k1 + k2. The spectrum thus stays in digit-reversed order (entry
+// 16 a + b holds frequency a + 16 b), where the propagator indexes it; the inverse runs the
+// passes back with conjugate twiddles, each thread writing only entries it has just read.
+//
+// The wave lives in a per-CTA scratch in global memory (L2). Each slice is a column phase
+// (forward over y, propagator, inverse over y) and a row phase (inverse over x, transmission
+// of the next slice, forward over x), each over 8 panels of 32 columns or 32 rows (64 KiB),
+// double-buffered in shared memory and moved by bulk copies completing on an mbarrier.
+//   Column panel [256 y][34]: thread (c, g) = (lane, warp); pass 1 is residue q = g, pass 2
+//   is k1 = g; CTA barriers between the passes. 32 lanes read 32 consecutive entries.
+//   Row panel [32 r][256]: thread (r, j) = (2 warp + lane / 16, lane % 16), so that a row's
+//   passes stay in one half-warp (__syncwarp between them). Scratch rows and row panels hold
+//   entry p at the swizzled position swz(p) (low four bits XOR the high four): the pass-2
+//   reads of entries 16 j + k2 and the pass-1 reads of 16 k1 + j then fall on 16 distinct
+//   bank pairs, and a panel still moves as one contiguous bulk copy.
+namespace w256 {
+constexpr int kN = 256;
+constexpr int kPanels = 8;
+constexpr int kPC = 34;                  // column-panel row pitch (32 entries + 16-byte pad)
+constexpr int kBuf = kN * kPC;           // float2 per panel buffer (a row panel takes 32 x 256)
+// W_256^m = exp(-2 pi i m / 256), m < 256, built on the host in FP64 and rounded once
+__constant__ float2 c_tw[kN];
+__host__ __device__ constexpr int swz(int p) { return (p & ~15) | ((p & 15) ^ ((p >> 4) & 15)); }
+
+// L2 policy of the scratch copies: keep the scratch resident (the exit waves stream past it)
+__device__ __forceinline__ uint64_t policy_keep() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void load(void* smem_dst, const void* gsrc, uint32_t bytes, uint32_t mbar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          gen::smem_u32(smem_dst)),
+      "l"(gsrc), "r"(bytes), "r"(mbar), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ void store(void* gdst, const void* smem_src, uint32_t bytes, uint64_t pol) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(gdst),
+               "r"(gen::smem_u32(smem_src)), "r"(bytes), "l"(pol)
+               : "memory");
+}
+
+// column panel: forward over y, propagator and bandlimit, inverse over y (thread (c, g));
+// eyt: the job's exp(-i pi lambda eps ky^2) in shared memory (read at warp-uniform ky)
+__device__ __forceinline__ void column_panel(float2* buf, int p, const SliceJob& J, const float2* eyt, int c, int g) {
+  float2 v[16];
 #pragma unroll
-          for (int j = 0; j < R; ++j) v[j] = S[(lane + 32 * j) * (W + 1) + x];
-          column(v, x);
+  for (int n = 0; n < 16; ++n) v[n] = buf[(16 * n + g) * kPC + c];
+  dft16<false>(v);
 #pragma unroll
-          for (int j = 0; j < R; ++j) S[(lane + 32 * j) * (W + 1) + x] = v[j];
+  for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmul(v[k1], c_tw[g * k1]);
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) buf[(16 * k1 + g) * kPC + c] = v[k1];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = buf[(16 * g + q) * kPC + c];
+  dft16<false>(v);
+  // propagation (Sec. 3.2) at (kx, ky): the column at scratch position 32 p + c holds row entry
+  // e = swz(32 p + c), frequency kx = e / 16 + 16 (e % 16); v[k2] has ky = g + 16 k2
+  const int e = swz(32 * p + c);
+  const int kxi = (e >> 4) + 16 * (e & 15);
+  const int kxs = kxi < kN / 2 ? kxi : kxi - kN;
+  const float2 ex = J.ex[kxi];
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) {
+    const int kyi = g + 16 * k2;
+    const int kys = kyi < kN / 2 ? kyi : kyi - kN;
+    v[k2] = kxs * kxs + kys * kys <= J.r2max ? cmul(v[k2], cmul(ex, eyt[kyi])) : make_float2(0.f, 0.f);
+  }
+  dft16<true>(v);
+#pragma unroll
+  for (int q = 1; q < 16; ++q) v[q] = cmulc(v[q], c_tw[g * q]);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) buf[(16 * g + q) * kPC + c] = v[q];
+  __syncthreads();
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) v[k1] = buf[(16 * k1 + g) * kPC + c];
+  dft16<true>(v);
+#pragma unroll
+  for (int n = 0; n < 16; ++n) buf[(16 * n + g) * kPC + c] = v[n];
+}
+
+// forward over x of one row (pass 1 from v[n] = x[16 n + j], then pass 2), into the panel row
+__device__ __forceinline__ void row_forward(float2* row, float2 (&v)[16], int j, const float2 (&twj)[16]) {
+  dft16<false>(v);
+#pragma unroll
+  for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmul(v[k1], twj[k1]);
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) row[16 * k1 + (j ^ k1)] = v[k1];   // entry 16 k1 + j
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = row[16 * j + (q ^ j)];           // entry 16 j + q
+  dft16<false>(v);
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) row[16 * j + (k2 ^ j)] = v[k2];      // entry 16 j + k2
+}
+
+// inverse over x of one row: v[n] = x[16 n + j] afterwards (the row's entries are consumed)
+__device__ __forceinline__ void row_inverse(float2* row, float2 (&v)[16], int j, const float2 (&twj)[16]) {
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) v[k2] = row[16 * j + (k2 ^ j)];
+  dft16<true>(v);
+#pragma unroll
+  for (int q = 1; q < 16; ++q) v[q] = cmulc(v[q], twj[q]);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) row[16 * j + (q ^ j)] = v[q];
+  __syncwarp();
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) v[k1] = row[16 * k1 + (j ^ k1)];
+  dft16<true>(v);
+}
+}  // namespace w256
+
+// One translate per CTA at a time (persistent CTAs), complex64 exit waves, W = 256. scratch:
+// 256 x 256 complex64 per CTA; status: set to 1 when a bulk-copy wait gives up.
+//
+// Column phase: the CTA moves panels of 32 columns (256 copies of 256 bytes, threads T < 256)
+// through two buffers on two mbarriers; the next panel's load is issued before the current one
+// is transformed (after the issuing thread's own previous store from that buffer has read it;
+// the byte count may reach the mbarrier before or after the copies do). Row phase: each warp
+// moves its own two rows of each panel (one 4 KiB copy in, one out, by lane 0) through its
+// two row slots on its own two mbarriers, so the row phase has no CTA barrier. Every wait is
+// one polling lane per warp (bounded, suspended tries) and then one try_wait per lane. Scratch
+// copies carry an evict-last L2 policy; the exit wave is written with streaming stores.
+__global__ void __launch_bounds__(gen::kThreadsGen, 1) k_slice_256(const SliceLaunch a, float2* scratch, int* status) {
+  using namespace w256;
+  extern __shared__ __align__(16) unsigned char smg[];
+  float2* const S = reinterpret_cast<float2*>(smg);
+  float2* const eyt = S + 2 * kBuf;                                  // the job's ey, kN entries
+  // mbarriers: [0, 2) column buffers; 2 + 2 w + b: row slot b of warp w
+  uint64_t* const mbar = reinterpret_cast<uint64_t*>(eyt + kN);
+  const int T = threadIdx.x, warp = T >> 5, lane = T & 31;
+  const int rr = 2 * warp + (lane >> 4), jj = lane & 15;   // row-phase thread (r, j)
+  // W_256^(j m): this thread's row-phase twiddles, read once (a constant read whose address
+  // differs across a warp is serialized)
+  float2 twj[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) twj[m] = c_tw[jj * m];
+  float2* const G = scratch + static_cast<size_t>(blockIdx.x) * kN * kN;
+  const uint64_t keep = policy_keep();
+  if (T < 2 + 2 * (gen::kThreadsGen / 32)) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(gen::smem_u32(mbar + T)) : "memory");
+    if (T == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const uint32_t mrow = gen::smem_u32(mbar + 2 + 2 * warp);        // this warp's row mbarriers (+ 8 b)
+  uint32_t phc = 0u, phr = 0u;                                      // completed-phase parity per buffer
+  bool bad = false;
+  int cur_job = -1;
+  constexpr uint32_t kRowBytes = 2 * kN * 8;                         // a warp's two rows
+
+  for (int li = blockIdx.x; li < a.n_list; li += gridDim.x) {
+    int jb = 0;
+    while (jb + 1 < a.n_jobs && li >= a.start[jb + 1]) ++jb;
+    const SliceJob& J = a.job[jb];
+    const int n_slices = J.n_slices;
+    const int pitch = J.nx + kW;                          // padded transmission row
+    const size_t slice_elems = static_cast<size_t>(pitch) * (J.ny + kW);
+    const int item = a.list[li];
+    const int cfg = item / J.n_translates;
+    const int ti = item - cfg * J.n_translates;
+    const int ia = ti % J.lat_nax, ib = ti / J.lat_nax;
+    int ox = (J.lat_ox + ia * J.lat_sx - kN / 2) % J.nx;
+    if (ox < 0) ox += J.nx;
+    int oy = (J.lat_oy + ib * J.lat_sy - kN / 2) % J.ny;
+    if (oy < 0) oy += J.ny;
+    const float2* const tbase = J.t + cfg * J.t_slot;
+    // transmission of slice s at window pixel (y, x): the periodic cell, indices wrapped (the
+    // halo of the stored array is narrower than this window)
+    auto tval = [&](int s, int y, int x) -> float2 {
+      int gy = oy + y, gx = ox + x;
+      if (gy >= J.ny) gy -= J.ny;
+      if (gx >= J.nx) gx -= J.nx;
+      return tbase[s * slice_elems + static_cast<size_t>(gy) * pitch + gx];
+    };
+    const int oi = a.out_index ? a.out_index[li] : ti;
+    float2* const ud = J.U + cfg * J.u_slot + static_cast<size_t>(oi) * (kN * kN);
+    __syncthreads();   // the previous item's use of the buffers and of eyt is over
+    if (n_slices == 0) {
+      for (int e = T; e < kN * kN; e += gen::kThreadsGen) ud[e] = J.uW[e];
+      continue;
+    }
+    if (jb != cur_job) {
+      cur_job = jb;
+      for (int e = T; e < kN; e += gen::kThreadsGen) eyt[e] = J.ey[e];   // read after the barriers below
+    }
+    // rows of the scratch: input wave times the transmission of slice 0, forward over x (each
+    // warp its own two rows per panel, alternating row slots)
+    for (int p = 0; p < kPanels; ++p) {
+      float2* const slot = S + (p & 1) * kBuf + 2 * warp * kN;
+      if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");   // slot's store of p - 2
+      __syncwarp();
+      const int y = 32 * p + rr;
+      float2 v[16];
+#pragma unroll
+      for (int n = 0; n < 16; ++n) v[n] = cmul(J.uW[y * kN + 16 * n + jj], tval(0, y, 16 * n + jj));
+      row_forward(S + (p & 1) * kBuf + rr * kN, v, jj, twj);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        store(G + static_cast<size_t>(32 * p + 2 * warp) * kN, slot, kRowBytes, keep);
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      }
+    }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __syncthreads();
+    for (int s = 0; s < n_slices && !bad; ++s) {
+      // ---- column phase ----
+      auto issue_col = [&](int pn) {
+        const int bn = pn & 1;
+        const uint32_t mb = gen::smem_u32(mbar + bn);
+        if (T == 0) gen::expect_tx(mb, 32u * kN * 8u);
+        if (T < kN) load(S + bn * kBuf + T * kPC, G + static_cast<size_t>(T) * kN + pn * 32, 32 * 8, mb, keep);
+      };
+      issue_col(0);
+      for (int p = 0; p < kPanels; ++p) {
+        const int b = p & 1;
+        float2* const buf = S + b * kBuf;
+        if (p + 1 < kPanels) {
+          // this thread's store of panel p - 1 has read its part of the other buffer
+          if (T < kN) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+          issue_col(p + 1);
         }
+        bad |= !tc::wait_phase_warp(gen::smem_u32(mbar + b), (phc >> b) & 1u);
+        phc ^= 1u << b;
+        column_panel(buf, p, J, eyt, lane, warp);
+        // the threads' writes are made visible to the bulk copies, then the panel goes back
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        for (int y = warp; y < W; y += kWarps) {
-          float2 v[R];
-#pragma unroll
-          for (int j = 0; j < R; ++j) v[j] = S[y * (W + 1) + lane + 32 * j];
-          row(v, y, s);
-#pragma unroll
-          for (int j = 0; j < R; ++j) S[y * (W + 1) + lane + 32 * j] = v[j];
+        if (T < kN) {
+          store(G + static_cast<size_t>(T) * kN + p * 32, buf + T * kPC, 32 * 8, keep);
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         }
       }
-      __syncthreads();
-      const int oi = a.out_index ? a.out_index[li] : ti;
-      float2* const ud = J.U + cfg * J.u_slot + static_cast<size_t>(oi) * (W * W);
-      for (int e = T; e < W * W; e += gen::kThreadsGen) ud[e] = S[(e / W) * (W + 1) + e % W];
-    } else {
-      constexpr int kPanels = W / gen::kPanel;
-      // rows of the scratch: input wave, transmission of slice 0, forward transform (plain
-      // coalesced stores; ordered before the bulk copies by the proxy fence below)
-      for (int y = warp; y < W; y += kWarps) {
-        float2 v[R];
-#pragma unroll
-        for (int j = 0; j < R; ++j)
-          v[j] = n_slices > 0 ? cmul(J.uW[y * W + lane + 32 * j], tval(0, y, lane + 32 * j)) : J.uW[y * W + lane + 32 * j];
-        if (n_slices > 0) gen::fft_fwd<W>(v, lane, tw);
-#pragma unroll
-        for (int j = 0; j < R; ++j) G[static_cast<size_t>(y) * W + lane + 32 * j] = v[j];
-      }
+      // every store of the phase is complete before the row phase reads the scratch
+      if (T < kN) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
       asm volatile("fence.proxy.async.global;" ::: "memory");
       __syncthreads();
-      for (int s = 0; s < n_slices && !bad; ++s) {
-        for (int phase_k = 0; phase_k < 2 && !bad; ++phase_k) {
-          const bool cols = phase_k == 0;
-          // issue the load of panel p into buffer p & 1 (T = 0 sets the byte count first)
-          auto issue_load = [&](int p) {
-            const int b = p & 1;
-            float2* const buf = S + b * kBuf;
-            const uint32_t mb = gen::smem_u32(mbar + b);
-            if (T == 0) gen::expect_tx(mb, static_cast<uint32_t>(W) * gen::kPanel * 8);
-            __syncthreads();
-            if (cols) {
-              if (T < W) gen::bulk_load(buf + T * gen::kPanelPitch, G + static_cast<size_t>(T) * W + p * gen::kPanel,
-                                        gen::kPanel * 8, mb);
-            } else if (T == 0) {
-              gen::bulk_load(buf, G + static_cast<size_t>(p) * gen::kPanel * W, W * gen::kPanel * 8, mb);
-            }
-          };
-          issue_load(0);
-          for (int p = 0; p < kPanels; ++p) {
-            const int b = p & 1;
-            float2* const buf = S + b * kBuf;
-            if (p + 1 < kPanels) {
-              // the other buffer's last store (panel p - 1) has read it before the next load
-              asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-              issue_load(p + 1);
-            }
-            const bool ok = gen::wait_load(gen::smem_u32(mbar + b), ph[b]);
-            ph[b] ^= 1;
-            bad |= !ok;
-            if (ok) {
-              if (cols) {
-                for (int c = warp; c < gen::kPanel; c += kWarps) {
-                  float2 v[R];
+      // ---- row phase: each warp its own two rows of every panel ----
+      const bool last = s + 1 == n_slices;   // rows go to the exit wave, not back
+      auto issue_row = [&](int pn) {
+        if (lane == 0) {
+          const uint32_t mb = mrow + 8 * (pn & 1);
+          gen::expect_tx(mb, kRowBytes);
+          load(S + (pn & 1) * kBuf + 2 * warp * kN, G + static_cast<size_t>(32 * pn + 2 * warp) * kN, kRowBytes, mb, keep);
+        }
+      };
+      issue_row(0);
+      for (int p = 0; p < kPanels; ++p) {
+        const int b = p & 1;
+        if (p + 1 < kPanels) {
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // slot's store of p - 1
+          issue_row(p + 1);
+        }
+        bad |= !tc::wait_phase_warp(mrow + 8 * b, (phr >> b) & 1u);
+        phr ^= 1u << b;
+        float2* const row = S + b * kBuf + rr * kN;
+        const int y = 32 * p + rr;
+        float2 v[16];
+        row_inverse(row, v, jj, twj);
+        if (last) {
 #pragma unroll
-                  for (int j = 0; j < R; ++j) v[j] = buf[(lane + 32 * j) * gen::kPanelPitch + c];
-                  column(v, p * gen::kPanel + c);
+          for (int n = 0; n < 16; ++n) __stcs(ud + y * kN + 16 * n + jj, v[n]);
+          __syncwarp();   // every lane has read the slot before lane 0 loads the next panel into it
+        } else {
 #pragma unroll
-                  for (int j = 0; j < R; ++j) buf[(lane + 32 * j) * gen::kPanelPitch + c] = v[j];
-                }
-              } else {
-                for (int r = warp; r < gen::kPanel; r += kWarps) {
-                  float2 v[R];
-#pragma unroll
-                  for (int j = 0; j < R; ++j) v[j] = buf[r * W + lane + 32 * j];
-                  row(v, p * gen::kPanel + r, s);
-#pragma unroll
-                  for (int j = 0; j < R; ++j) buf[r * W + lane + 32 * j] = v[j];
-                }
-              }
-            }
-            // the threads' writes are made visible to the bulk copies, then the panel goes back
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (cols) {
-              if (T < W) gen::bulk_store(G + static_cast<size_t>(T) * W + p * gen::kPanel, buf + T * gen::kPanelPitch,
-                                         gen::kPanel * 8);
-            } else if (T == 0) {
-              gen::bulk_store(G + static_cast<size_t>(p) * gen::kPanel * W, buf, W * gen::kPanel * 8);
-            }
+          for (int n = 0; n < 16; ++n) v[n] = cmul(v[n], tval(s + 1, y, 16 * n + jj));
+          row_forward(row, v, jj, twj);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) {
+            store(G + static_cast<size_t>(32 * p + 2 * warp) * kN, S + b * kBuf + 2 * warp * kN, kRowBytes, keep);
             asm volatile("cp.async.bulk.commit_group;" ::: "memory");
           }
-          // every store of the phase is complete (and ordered before the generic and bulk
-          // reads of the next phase)
-          asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-          asm volatile("fence.proxy.async.global;" ::: "memory");
-          bad = __syncthreads_or(bad);
         }
       }
-      if (__syncthreads_or(bad)) break;
-      const int oi = a.out_index ? a.out_index[li] : ti;
-      float2* const ud = J.U + cfg * J.u_slot + static_cast<size_t>(oi) * (W * W);
-      for (int e = T; e < W * W; e += gen::kThreadsGen) ud[e] = G[e];
+      if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      bad = __syncthreads_or(bad);
     }
+    if (__syncthreads_or(bad)) break;
   }
   if (bad && T == 0) atomicOr(status, 1);
 }
@@ -2169,10 +2352,12 @@ size_t slice_smem_bytes() { return static_cast<size_t>(kSliceSmemFloat2) * sizeo
 size_t synth_smem_bytes() { return static_cast<size_t>(kSynthSmemFloat2) * sizeof(float2); }
 size_t slice_tc_smem_bytes() { return static_cast<size_t>(kSliceTcSmemBytes); }
 static size_t slice_gen_smem_bytes(int W) {
-  return (W <= 64 ? static_cast<size_t>(W) * (W + 1) : 2 * static_cast<size_t>(W) * gen::kPanelPitch) * sizeof(float2) + 16;
+  return W <= 64 ? static_cast<size_t>(W) * (W + 1) * sizeof(float2)
+                 : (2 * static_cast<size_t>(w256::kBuf) + w256::kN) * sizeof(float2) +
+                       (2 + 2 * gen::kThreadsGen / 32) * sizeof(uint64_t);   // two panel buffers, ey, mbarriers
 }
 cudaError_t launch_selftest_wait(int which, int* status, cudaStream_t s) {
-  k_selftest_wait<<<1, 32, 0, s>>>(which, status);
+  k_selftest_wait<<<1, which == 0 ? 32 : gen::kThreadsGen, 0, s>>>(status);
   return cudaGetLastError();
 }
 size_t slice_gen_scratch_bytes(int W) {
@@ -2251,17 +2436,18 @@ cudaError_t init_device_constants() {
       if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, st)) != cudaSuccess) return e;
   }
   {
-    // twiddles of the W = 64 and W = 256 transforms: exp(-2 pi i m / W), m < W / 2
-    float2 t64[32], t256[128];
+    // twiddles of the W = 64 (exp(-2 pi i m / 64), m < 32) and W = 256 (m < 256) transforms
+    float2 t64[32];
     for (int m = 0; m < 32; ++m) t64[m] = make_float2(static_cast<float>(cos(-2.0 * pi * m / 64)), static_cast<float>(sin(-2.0 * pi * m / 64)));
-    for (int m = 0; m < 128; ++m)
-      t256[m] = make_float2(static_cast<float>(cos(-2.0 * pi * m / 256)), static_cast<float>(sin(-2.0 * pi * m / 256)));
     if ((e = cudaMemcpyToSymbol(gen::c_tw64, t64, sizeof(t64))) != cudaSuccess) return e;
-    if ((e = cudaMemcpyToSymbol(gen::c_tw256, t256, sizeof(t256))) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_slice_gen<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(slice_gen_smem_bytes(64)))) != cudaSuccess)
       return e;
-    if ((e = cudaFuncSetAttribute(k_slice_gen<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    float2 tw2[w256::kN];
+    for (int m = 0; m < w256::kN; ++m)
+      tw2[m] = make_float2(static_cast<float>(cos(-2.0 * pi * m / 256)), static_cast<float>(sin(-2.0 * pi * m / 256)));
+    if ((e = cudaMemcpyToSymbol(w256::c_tw, tw2, sizeof(tw2))) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_slice_256, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(slice_gen_smem_bytes(256)))) != cudaSuccess)
       return e;
   }
@@ -2350,10 +2536,10 @@ cudaError_t launch_slice_gen(const SliceLaunch& a, int W, float2* scratch, cudaS
   // persistent, one CTA per SM: W = 256 takes one scratch wave per CTA
   const int grid = a.n_list < sm_count() ? a.n_list : sm_count();
   if (W == 64) {
-    k_slice_gen<64><<<grid, gen::kThreadsGen, slice_gen_smem_bytes(64), s>>>(a, nullptr, a.status);
+    k_slice_gen<64><<<grid, gen::kThreadsGen, slice_gen_smem_bytes(64), s>>>(a);
   } else if (W == 256) {
     if (!scratch) return cudaErrorInvalidValue;
-    k_slice_gen<256><<<grid, gen::kThreadsGen, slice_gen_smem_bytes(256), s>>>(a, scratch, a.status);
+    k_slice_256<<<grid, gen::kThreadsGen, slice_gen_smem_bytes(256), s>>>(a, scratch, a.status);
   } else {
     return cudaErrorInvalidValue;
   }

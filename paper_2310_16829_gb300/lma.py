@@ -263,9 +263,9 @@ class Context:
         return p.as_dict()
 
     def selftest_wait(self, which: int, stream=None) -> int:
-        """Run one bounded device wait on an mbarrier phase that never completes (0: the
-        tensor-core slice kernel's form, 1: the W = 256 kernel's); returns the status code,
-        LMA_ERR_TIMEOUT when the wait gave up as it should."""
+        """Run the slice kernels' bounded mbarrier wait on a phase that never completes (0: in
+        one warp, 1: in the 16 warps of a CTA); returns the status code, LMA_ERR_TIMEOUT when
+        the wait gave up as it should."""
         return self.lib.lma_selftest_wait(self.h, which, _stream(stream))
 
     def set_slice_mode(self, mode: int) -> None:

@@ -147,10 +147,10 @@ def test_fp16_store_readouts_are_consistent():
 
 @pytest.mark.parametrize("which", [0, 1])
 def test_bounded_wait_gives_up_and_the_context_stays_usable(which):
-    """The bounded mbarrier waits of the tensor-core (0) and W = 256 (1) slice kernels, run on
-    a phase that nothing completes, give up, and the call returns LMA_ERR_TIMEOUT. The status
-    word is cleared: the next tensor-core image in the same context is bit for bit the image
-    of a fresh context."""
+    """The bounded mbarrier wait of the tensor-core and W = 256 slice kernels, run on a phase
+    that nothing completes in one warp (0) and in the 16 warps of a CTA (1), gives up, and the
+    call returns LMA_ERR_TIMEOUT. The status word is cleared: the next tensor-core image in the
+    same context is bit for bit the image of a fresh context."""
     import time
 
     import torch
