@@ -53,7 +53,7 @@ struct SliceJob {
   int r2max;                   // bandlimit: m'^2 + n'^2 <= r2max
   float tc_in, tc_out;         // tensor-core DFT (k_slice_tc): power-of-two factor of the input
                                // wave, and its inverse applied to the exit wave
-  int W;                       // window of this job (kW, or 64 / 256 for k_slice_gen); uW, the
+  int W;                       // window of this job (kW, or 64 / 256 for k_slice_64 / k_slice_256); uW, the
                                // store entries and ex, ey have this size
 };
 
@@ -138,7 +138,8 @@ int sm_count();
 cudaError_t launch_slice_tc(const SliceLaunch& a, bool even_origins, cudaStream_t s);
 size_t slice_tc_smem_bytes();
 // step a3 on W = 64 or W = 256 windows (every job of the launch has that W), complex64 store:
-// persistent CTAs, one per SM; W = 256 needs slice_gen_scratch_bytes(256) of scratch
+// persistent CTAs (two per SM at W = 64, one at W = 256); W = 256 needs
+// slice_gen_scratch_bytes(256) of scratch
 cudaError_t launch_slice_gen(const SliceLaunch& a, int W, float2* scratch, cudaStream_t s);
 size_t slice_gen_scratch_bytes(int W);
 // one warp runs the bounded mbarrier wait of the tensor-core (which = 0) or W = 256 (which = 1)

@@ -1000,7 +1000,7 @@ lma_status slice_launch(lma_ctx* ctx, const lma_dev::SliceLaunch& L0, bool even,
   lma_dev::SliceLaunch L = L0;
   L.status = ctx->d_counter + 1;
   if (L.job[0].W != kW) {
-    // W = 64 / 256 windows: k_slice_gen (complex64; the basis checks allow nothing else)
+    // W = 64 / 256 windows: k_slice_64 / k_slice_256 (complex64; the basis checks allow nothing else)
     const size_t need = lma_dev::slice_gen_scratch_bytes(L.job[0].W);
     if (need > ctx->gen_scratch_bytes) {
       if (ctx->capturing) return fail(ctx, LMA_ERR_CUDA, "slice scratch missing during graph capture");

@@ -1131,115 +1131,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice_tc(const SliceLaunch a, i
 }
 
 // ------------------------------------------------------------------------------------------
-// step a3 on windows W = 64 (k_slice_gen)
+// helpers of the W = 256 kernel's bulk copies (and the thread count of the W = 64 / 256 kernels)
 // ------------------------------------------------------------------------------------------
-// Every W-point transform (a row or a column of the window) is done by one warp in registers:
-// lane l holds the R = W / 32 values of indices l + 32 j. The forward transform is radix-2
-// decimation in frequency (natural order in, bit-reversed order out): its stages of span W/2
-// .. 32 pair values of one lane, those of span 16 .. 1 pair lanes (shuffles). The propagator is
-// applied in the bit-reversed order that the forward transforms leave, and the inverse
-// transforms are decimation in time (bit-reversed in, natural out), so no pass reorders data.
-// Each slice is two passes: columns (forward, propagator, inverse), then rows (inverse, the
-// next slice's transmission, forward); the first slice's transmission and forward rows come
-// before the loop, the last inverse rows after it. The wave (32 KiB) stays in shared memory,
-// rows padded to 65 values. (W = 256 has its own kernel, k_slice_256, below.)
 namespace gen {
 
 constexpr int kThreadsGen = 512;
-
-// exp(-2 pi i m / W), m < W / 2, built on the host in FP64 and rounded once
-__constant__ float2 c_tw64[32];
-
-template <int W>
-__device__ __forceinline__ float2 tw(int m) {
-  static_assert(W == 64, "the warp transforms serve W = 64");
-  return c_tw64[m];
-}
-template <int W>
-__device__ __forceinline__ int brev(int i) {
-  static_assert(W == 64, "the warp transforms serve W = 64");
-  return static_cast<int>(__brev(static_cast<unsigned>(i)) >> 26);
-}
-__device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
-  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
-}
-
-// The twiddles one lane uses, read once from the constant table into registers (a constant
-// read whose address differs across the lanes of a warp is serialized): c[b] for the shuffle
-// stage of span h = 2^b, exp(-2 pi i (l mod h) W / (2h) / W); i[jh - 1 + jj] for the in-lane
-// stage of span 32 jh and value index jj = j mod jh, exp(-2 pi i (l + 32 jj) / (64 jh)).
-template <int W>
-struct LaneTw {
-  float2 c[5];
-  float2 i[W / 32 > 1 ? W / 32 - 1 : 1];
-  __device__ __forceinline__ explicit LaneTw(int lane) {
-#pragma unroll
-    for (int b = 0; b < 5; ++b) {
-      const int h = 1 << b;
-      c[b] = tw<W>((lane & (h - 1)) * (W / (2 * h)));
-    }
-#pragma unroll
-    for (int jh = 1; jh <= W / 64; jh <<= 1)
-#pragma unroll
-      for (int jj = 0; jj < jh; ++jj) i[jh - 1 + jj] = tw<W>((lane + 32 * jj) * (W / (64 * jh)));
-  }
-};
-
-// forward DIF over x[l + 32 j] (v[j] in lane l); afterwards v[j] holds X[brev(l + 32 j)]
-template <int W>
-__device__ __forceinline__ void fft_fwd(float2 (&v)[W / 32], int lane, const LaneTw<W>& tw) {
-  constexpr int R = W / 32;
-#pragma unroll
-  for (int jh = R / 2; jh >= 1; jh >>= 1) {
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-      if (j & jh) continue;
-      const float2 a = v[j], b = v[j + jh];
-      v[j] = cadd(a, b);
-      v[j + jh] = cmul(csub(a, b), tw.i[jh - 1 + (j & (jh - 1))]);
-    }
-  }
-#pragma unroll
-  for (int bi = 4; bi >= 0; --bi) {
-    const int h = 1 << bi;
-    const bool upper = (lane & h) != 0;
-    const float2 w = tw.c[bi];
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-      const float2 p = shfl_xor2(v[j], h);
-      v[j] = upper ? cmul(csub(p, v[j]), w) : cadd(v[j], p);
-    }
-  }
-}
-
-// inverse DIT (conjugate twiddles, no 1/W): v[j] holding X[brev(l + 32 j)] becomes x[l + 32 j]
-template <int W>
-__device__ __forceinline__ void fft_inv(float2 (&v)[W / 32], int lane, const LaneTw<W>& tw) {
-  constexpr int R = W / 32;
-#pragma unroll
-  for (int bi = 0; bi <= 4; ++bi) {
-    const int h = 1 << bi;
-    const bool upper = (lane & h) != 0;
-    const float2 w = tw.c[bi];
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-      const float2 mine = upper ? cmulc(v[j], w) : v[j];
-      const float2 p = shfl_xor2(mine, h);
-      v[j] = upper ? csub(p, mine) : cadd(mine, p);
-    }
-  }
-#pragma unroll
-  for (int jh = 1; jh <= R / 2; jh <<= 1) {
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-      if (j & jh) continue;
-      const float2 a = v[j];
-      const float2 b = cmulc(v[j + jh], tw.i[jh - 1 + (j & (jh - 1))]);
-      v[j] = cadd(a, b);
-      v[j + jh] = csub(a, b);
-    }
-  }
-}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
@@ -1269,102 +1165,6 @@ __global__ void k_selftest_wait(int* status) {
   if (!ok && (threadIdx.x & 31) == 0) atomicOr(status, 1);
 }
 
-// One translate per CTA at a time (persistent CTAs); complex64 exit waves, W = 64.
-template <int W>
-__global__ void __launch_bounds__(gen::kThreadsGen, 1) k_slice_gen(const SliceLaunch a) {
-  static_assert(W == 64, "the wave of W = 64 stays in shared memory");
-  constexpr int R = W / 32;
-  constexpr int kWarps = gen::kThreadsGen / 32;
-  extern __shared__ __align__(16) unsigned char smg[];
-  float2* const S = reinterpret_cast<float2*>(smg);   // the wave, [W][W + 1]
-  const int T = threadIdx.x, warp = T >> 5, lane = T & 31;
-  const gen::LaneTw<W> tw(lane);
-
-  for (int li = blockIdx.x; li < a.n_list; li += gridDim.x) {
-    int jb = 0;
-    while (jb + 1 < a.n_jobs && li >= a.start[jb + 1]) ++jb;
-    const SliceJob& J = a.job[jb];
-    const int n_slices = J.n_slices;
-    const int pitch = J.nx + kW;                          // padded transmission row
-    const size_t slice_elems = static_cast<size_t>(pitch) * (J.ny + kW);
-    const int item = a.list[li];
-    const int cfg = item / J.n_translates;
-    const int ti = item - cfg * J.n_translates;
-    const int ia = ti % J.lat_nax, ib = ti / J.lat_nax;
-    int ox = (J.lat_ox + ia * J.lat_sx - W / 2) % J.nx;
-    if (ox < 0) ox += J.nx;
-    int oy = (J.lat_oy + ib * J.lat_sy - W / 2) % J.ny;
-    if (oy < 0) oy += J.ny;
-    const float2* const tbase = J.t + cfg * J.t_slot;
-    // transmission of slice s at window pixel (y, x): the periodic cell, indices wrapped
-    auto tval = [&](int s, int y, int x) -> float2 {
-      int gy = oy + y, gx = ox + x;
-      if (gy >= J.ny) gy -= J.ny;
-      if (gx >= J.nx) gx -= J.nx;
-      return tbase[s * slice_elems + static_cast<size_t>(gy) * pitch + gx];
-    };
-    // columns: forward transform, propagator (Sec. 3.2) at (kx, ky) = (brev(x), brev(y)),
-    // inverse transform
-    auto column = [&](float2 (&v)[R], int x) {
-      gen::fft_fwd<W>(v, lane, tw);
-      const int kxb = gen::brev<W>(x);
-      const int kxs = kxb < W / 2 ? kxb : kxb - W;
-      const float2 ex = J.ex[kxb];
-#pragma unroll
-      for (int j = 0; j < R; ++j) {
-        const int kyb = gen::brev<W>(lane + 32 * j);
-        const int kys = kyb < W / 2 ? kyb : kyb - W;
-        v[j] = kxs * kxs + kys * kys <= J.r2max ? cmul(v[j], cmul(ex, J.ey[kyb])) : make_float2(0.f, 0.f);
-      }
-      gen::fft_inv<W>(v, lane, tw);
-    };
-    // rows after the column phase: inverse transform, then (if another slice follows) its
-    // transmission and the forward transform
-    auto row = [&](float2 (&v)[R], int y, int s) {
-      gen::fft_inv<W>(v, lane, tw);
-      if (s + 1 < n_slices) {
-#pragma unroll
-        for (int j = 0; j < R; ++j) v[j] = cmul(v[j], tval(s + 1, y, lane + 32 * j));
-        gen::fft_fwd<W>(v, lane, tw);
-      }
-    };
-    __syncthreads();   // the previous item's use of the wave is over
-    // rows: input wave, transmission of slice 0, forward transform
-    for (int y = warp; y < W; y += kWarps) {
-      float2 v[R];
-#pragma unroll
-      for (int j = 0; j < R; ++j)
-        v[j] = n_slices > 0 ? cmul(J.uW[y * W + lane + 32 * j], tval(0, y, lane + 32 * j)) : J.uW[y * W + lane + 32 * j];
-      if (n_slices > 0) gen::fft_fwd<W>(v, lane, tw);
-#pragma unroll
-      for (int j = 0; j < R; ++j) S[y * (W + 1) + lane + 32 * j] = v[j];
-    }
-    for (int s = 0; s < n_slices; ++s) {
-      __syncthreads();
-      for (int x = warp; x < W; x += kWarps) {
-        float2 v[R];
-#pragma unroll
-        for (int j = 0; j < R; ++j) v[j] = S[(lane + 32 * j) * (W + 1) + x];
-        column(v, x);
-#pragma unroll
-        for (int j = 0; j < R; ++j) S[(lane + 32 * j) * (W + 1) + x] = v[j];
-      }
-      __syncthreads();
-      for (int y = warp; y < W; y += kWarps) {
-        float2 v[R];
-#pragma unroll
-        for (int j = 0; j < R; ++j) v[j] = S[y * (W + 1) + lane + 32 * j];
-        row(v, y, s);
-#pragma unroll
-        for (int j = 0; j < R; ++j) S[y * (W + 1) + lane + 32 * j] = v[j];
-      }
-    }
-    __syncthreads();
-    const int oi = a.out_index ? a.out_index[li] : ti;
-    float2* const ud = J.U + cfg * J.u_slot + static_cast<size_t>(oi) * (W * W);
-    for (int e = T; e < W * W; e += gen::kThreadsGen) ud[e] = S[(e / W) * (W + 1) + e % W];
-  }
-}
 
 // ------------------------------------------------------------------------------------------
 // step a3 on W = 256 windows: each 256-point transform as two in-register 16-point passes
@@ -1659,6 +1459,189 @@ __global__ void __launch_bounds__(gen::kThreadsGen, 1) k_slice_256(const SliceLa
     if (__syncthreads_or(bad)) break;
   }
   if (bad && T == 0) atomicOr(status, 1);
+}
+
+// ------------------------------------------------------------------------------------------
+// step a3 on W = 64 windows: each 64-point transform as two in-register 8-point passes
+// ------------------------------------------------------------------------------------------
+// 64 = 8 x 8 as for W = 256: with x = 8 n + q and k = k1 + 8 k2, pass 1 takes the 8-point DFT
+// over n for residue q and multiplies by W_64^(q k1), pass 2 the DFT over q for k1; the
+// spectrum stays in digit-reversed order (entry 8 a + b holds frequency a + 8 b). The wave
+// (32 KiB) stays in shared memory in two buffers of opposite orientation, A[y][x] and
+// B[x][y] (rows of 65 entries). A phase reads one buffer with thread (c, g): c the position
+// along the other axis (the 32 lanes of a warp on consecutive positions), g = warp / 2 the
+// residue (pass 1) or k1 (pass 2); its passes work in place between CTA barriers, and it
+// writes its result transposed into the other buffer, so that the row phase runs the column
+// phase's code on B. Column phase: forward over y, propagator, inverse over y (A -> B). Row
+// phase: inverse over x, the next slice's transmission, forward over x (B -> A). The next
+// slice's transmission is staged into a third buffer by 8-byte cp.async while the column
+// phase runs. About 100 KB of shared memory: two CTAs per SM.
+namespace w64 {
+constexpr int kN = 64;
+constexpr int kP = 65;                   // buffer row pitch (64-bit accesses of 16 lanes at stride 65 or 1: 32 banks)
+constexpr int kBufE = kN * kP;           // float2 per buffer
+// W_64^m = exp(-2 pi i m / 64), m < 64, built on the host in FP64 and rounded once
+__constant__ float2 c_tw[kN];
+
+// in-register 8-point DFT, natural order in and out: the first three stages of dft32
+template <bool INV>
+__device__ __forceinline__ void dft8(float2 (&v)[8]) {
+  float2 t[8];
+  static_for<0, 8>([&](auto k) {
+    constexpr int K = decltype(k)::value;
+    t[K] = v[((K & 1) << 2) | (K & 2) | ((K & 4) >> 2)];
+  });
+  static_for<0, 3>([&](auto st) {
+    constexpr int H = 1 << decltype(st)::value;
+    static_for<0, 4 / H>([&](auto blk) {
+      static_for<0, H>([&](auto j) {
+        constexpr int I = decltype(blk)::value * 2 * H + decltype(j)::value;
+        constexpr int M = decltype(j)::value * (16 / H);
+        bfly<INV, I, H, M>(t);
+      });
+    });
+  });
+  static_for<0, 8>([&](auto k) {
+    constexpr int K = decltype(k)::value;
+    v[K] = t[K];
+  });
+}
+
+// forward over one axis for thread (c, g) of buffer X: pass 1 from v[n] = x[8 n + g] (already
+// in registers), pass 2; X[entry][c] is the in-place scratch; v[k2] = X[g + 8 k2] after it
+__device__ __forceinline__ void forward(float2* X, float2 (&v)[8], int c, int g) {
+  dft8<false>(v);
+#pragma unroll
+  for (int k1 = 1; k1 < 8; ++k1) v[k1] = cmul(v[k1], c_tw[g * k1]);
+#pragma unroll
+  for (int k1 = 0; k1 < 8; ++k1) X[(8 * k1 + g) * kP + c] = v[k1];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = X[(8 * g + q) * kP + c];
+  dft8<false>(v);
+}
+// inverse over one axis for thread (c, g), from v[k2] = X[g + 8 k2] (in registers); v[n] =
+// x[8 n + g] after it
+__device__ __forceinline__ void inverse(float2* X, float2 (&v)[8], int c, int g) {
+  dft8<true>(v);
+#pragma unroll
+  for (int q = 1; q < 8; ++q) v[q] = cmulc(v[q], c_tw[g * q]);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) X[(8 * g + q) * kP + c] = v[q];
+  __syncthreads();
+#pragma unroll
+  for (int k1 = 0; k1 < 8; ++k1) v[k1] = X[(8 * k1 + g) * kP + c];
+  dft8<true>(v);
+}
+}  // namespace w64
+
+// One translate per CTA at a time (persistent CTAs, two per SM), complex64 exit waves, W = 64.
+__global__ void __launch_bounds__(512, 2) k_slice_64(const SliceLaunch a) {
+  using namespace w64;
+  extern __shared__ __align__(16) float2 s64[];
+  float2* const A = s64;                 // A[y][x entry]
+  float2* const B = A + kBufE;           // B[x][y]
+  float2* const Tb = B + kBufE;          // staged transmission [y][x]
+  float2* const eyt = Tb + kBufE;        // the job's ey
+  const int T = threadIdx.x, lane = T & 31, warp = T >> 5;
+  const int c = lane + 32 * (warp & 1), g = warp >> 1;
+  int cur_job = -1;
+  for (int li = blockIdx.x; li < a.n_list; li += gridDim.x) {
+    int jb = 0;
+    while (jb + 1 < a.n_jobs && li >= a.start[jb + 1]) ++jb;
+    const SliceJob& J = a.job[jb];
+    const int n_slices = J.n_slices;
+    const int pitch = J.nx + kW;                          // padded transmission row
+    const size_t slice_elems = static_cast<size_t>(pitch) * (J.ny + kW);
+    const int item = a.list[li];
+    const int cfg = item / J.n_translates;
+    const int ti = item - cfg * J.n_translates;
+    const int ia = ti % J.lat_nax, ib = ti / J.lat_nax;
+    int ox = (J.lat_ox + ia * J.lat_sx - kN / 2) % J.nx;
+    if (ox < 0) ox += J.nx;
+    int oy = (J.lat_oy + ib * J.lat_sy - kN / 2) % J.ny;
+    if (oy < 0) oy += J.ny;
+    // the halo of kW >= 64 pixels keeps every window inside the padded array
+    const float2* const tw0 = J.t + cfg * J.t_slot + static_cast<size_t>(oy) * pitch + ox;
+    const int oi = a.out_index ? a.out_index[li] : ti;
+    float2* const ud = J.U + cfg * J.u_slot + static_cast<size_t>(oi) * (kN * kN);
+    __syncthreads();   // the previous item's use of the buffers is over
+    if (n_slices == 0) {
+      for (int e = T; e < kN * kN; e += 512) ud[e] = J.uW[e];
+      continue;
+    }
+    if (jb != cur_job) {
+      cur_job = jb;
+      if (T < kN) eyt[T] = J.ey[T];
+    }
+    // slice s's transmission window into Tb (coalesced rows, asynchronous)
+    auto stage = [&](int s) {
+      const float2* const src = tw0 + static_cast<size_t>(s) * slice_elems;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int e = T + 512 * i, y = e >> 6, x = e & 63;
+        cp_async8(Tb + y * kP + x, src + static_cast<size_t>(y) * pitch + x);
+      }
+      cp_async_commit();
+    };
+    stage(0);
+    cp_async_wait_all();
+    __syncthreads();
+    {
+      // rows y = c: the input wave times the transmission of slice 0, forward over x into A
+      float2 v[8];
+#pragma unroll
+      for (int n = 0; n < 8; ++n) v[n] = cmul(J.uW[c * kN + 8 * n + g], Tb[c * kP + 8 * n + g]);
+      forward(B, v, c, g);
+#pragma unroll
+      for (int k2 = 0; k2 < 8; ++k2) A[c * kP + 8 * g + k2] = v[k2];
+    }
+    // propagator of this thread's column phase: the column at x entry c holds kx = c / 8 + 8 (c % 8)
+    const int kxi = (c >> 3) + 8 * (c & 7);
+    const int kxs = kxi < kN / 2 ? kxi : kxi - kN;
+    const float2 ex = J.ex[kxi];
+    __syncthreads();
+    for (int s = 0; s < n_slices; ++s) {
+      if (s + 1 < n_slices) stage(s + 1);   // Tb's last reads (slice s's transmission) are done
+      // column phase: x entry c, forward over y, propagation (Sec. 3.2), inverse over y, into B
+      {
+        float2 v[8];
+#pragma unroll
+        for (int n = 0; n < 8; ++n) v[n] = A[(8 * n + g) * kP + c];
+        forward(A, v, c, g);
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) {
+          const int kyi = g + 8 * k2;
+          const int kys = kyi < kN / 2 ? kyi : kyi - kN;
+          v[k2] = kxs * kxs + kys * kys <= J.r2max ? cmul(v[k2], cmul(ex, eyt[kyi])) : make_float2(0.f, 0.f);
+        }
+        inverse(A, v, c, g);
+#pragma unroll
+        for (int n = 0; n < 8; ++n) B[c * kP + 8 * n + g] = v[n];
+      }
+      cp_async_wait_all();
+      __syncthreads();
+      // row phase: row y = c, inverse over x, the next slice's transmission, forward over x, into A
+      {
+        float2 v[8];
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) v[k2] = B[(8 * g + k2) * kP + c];
+        inverse(B, v, c, g);
+        if (s + 1 < n_slices) {
+#pragma unroll
+          for (int n = 0; n < 8; ++n) v[n] = cmul(v[n], Tb[c * kP + 8 * n + g]);
+          forward(B, v, c, g);
+#pragma unroll
+          for (int k2 = 0; k2 < 8; ++k2) A[c * kP + 8 * g + k2] = v[k2];
+        } else {
+#pragma unroll
+          for (int n = 0; n < 8; ++n) A[c * kP + 8 * n + g] = v[n];   // natural x: the exit wave
+        }
+      }
+      __syncthreads();
+    }
+    for (int e = T; e < kN * kN; e += 512) ud[e] = A[(e >> 6) * kP + (e & 63)];
+  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -2352,7 +2335,7 @@ size_t slice_smem_bytes() { return static_cast<size_t>(kSliceSmemFloat2) * sizeo
 size_t synth_smem_bytes() { return static_cast<size_t>(kSynthSmemFloat2) * sizeof(float2); }
 size_t slice_tc_smem_bytes() { return static_cast<size_t>(kSliceTcSmemBytes); }
 static size_t slice_gen_smem_bytes(int W) {
-  return W <= 64 ? static_cast<size_t>(W) * (W + 1) * sizeof(float2)
+  return W <= 64 ? (3 * static_cast<size_t>(w64::kBufE) + w64::kN) * sizeof(float2)   // A, B, staged t, ey
                  : (2 * static_cast<size_t>(w256::kBuf) + w256::kN) * sizeof(float2) +
                        (2 + 2 * gen::kThreadsGen / 32) * sizeof(uint64_t);   // two panel buffers, ey, mbarriers
 }
@@ -2436,11 +2419,12 @@ cudaError_t init_device_constants() {
       if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, st)) != cudaSuccess) return e;
   }
   {
-    // twiddles of the W = 64 (exp(-2 pi i m / 64), m < 32) and W = 256 (m < 256) transforms
-    float2 t64[32];
-    for (int m = 0; m < 32; ++m) t64[m] = make_float2(static_cast<float>(cos(-2.0 * pi * m / 64)), static_cast<float>(sin(-2.0 * pi * m / 64)));
-    if ((e = cudaMemcpyToSymbol(gen::c_tw64, t64, sizeof(t64))) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_slice_gen<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // twiddles of the W = 64 and W = 256 transforms: exp(-2 pi i m / W), m < W
+    float2 tw1[w64::kN];
+    for (int m = 0; m < w64::kN; ++m)
+      tw1[m] = make_float2(static_cast<float>(cos(-2.0 * pi * m / 64)), static_cast<float>(sin(-2.0 * pi * m / 64)));
+    if ((e = cudaMemcpyToSymbol(w64::c_tw, tw1, sizeof(tw1))) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_slice_64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(slice_gen_smem_bytes(64)))) != cudaSuccess)
       return e;
     float2 tw2[w256::kN];
@@ -2536,7 +2520,9 @@ cudaError_t launch_slice_gen(const SliceLaunch& a, int W, float2* scratch, cudaS
   // persistent, one CTA per SM: W = 256 takes one scratch wave per CTA
   const int grid = a.n_list < sm_count() ? a.n_list : sm_count();
   if (W == 64) {
-    k_slice_gen<64><<<grid, gen::kThreadsGen, slice_gen_smem_bytes(64), s>>>(a);
+    // two CTAs per SM
+    const int grid64 = a.n_list < 2 * sm_count() ? a.n_list : 2 * sm_count();
+    k_slice_64<<<grid64, 512, slice_gen_smem_bytes(64), s>>>(a);
   } else if (W == 256) {
     if (!scratch) return cudaErrorInvalidValue;
     k_slice_256<<<grid, gen::kThreadsGen, slice_gen_smem_bytes(256), s>>>(a, scratch, a.status);

@@ -99,3 +99,23 @@ def test_window_forms_that_need_w128_are_rejected(ctx):
     with pytest.raises(lma.LmaError) as e:
         b.image_realspace(3, 3, w.detectors, WL.Region(0, 0, 2, 2, (4, 4)))
     assert e.value.status == lma.LMA_ERR_UNSUPPORTED
+
+
+def test_window_256_specimens_of_different_grids_in_one_launch(ctx):
+    """Two W = 256 specimens with different grids, slice counts and propagators share one slice
+    launch in lma_image_many (one job each: the kernel switches the propagator table between
+    them); each image is bit for bit the image of its own call."""
+    ws = [_with_window(WL.perovskite_workload(cells=5, nx=256, n_slices=6, n_phonons=1, seed_base=3300), 256),
+          _with_window(WL.perovskite_workload(cells=10, nx=512, n_slices=3, n_phonons=1, seed_base=3400), 256)]
+    regions = [WL.Region(250, 60, 4, 3, (4, 4)), WL.Region(100, 400, 5, 4, (4, 4))]
+    objs = []
+    single = []
+    for w, r in zip(ws, regions):
+        spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
+        basis = lma.Basis(ctx, spec, w.probe, w.basis)
+        objs.append((spec, basis))
+        single.append(basis.image(w.detectors, r, recompute=True))
+    outs = [np.empty_like(s) for s in single]
+    lma.image_many(ctx, [b for _, b in objs], ws[0].detectors, regions, outs)
+    for o, s in zip(outs, single):
+        assert np.array_equal(o, s)
