@@ -512,7 +512,7 @@ def profile_case(precision: str = "c64", window: int = 128) -> None:
     """The benchmark workload with one configuration, imaged twice with RECOMPUTE, in the
     given precision (c64, fp16_store or mixed: the tensor-core slice kernel k_slice_tc).
     window = 64 or 256: the ABO3 256^2 specimen (5 x 5 cells, 20 slices, 4096 translates) with
-    that propagation window instead (k_slice_gen or k_slice_256; store 0.13 or 2.1 GB).
+    that propagation window instead (k_slice_64 or k_slice_256; store 0.13 or 2.1 GB).
 
     Launch order per pass: k_potential, k_slice (or k_slice_tc), k_synth_detect, k_finalize.
     Device footprint about 2.5 GB (exit waves 2.15 GB, padded transmission 164 MB).
