@@ -14,8 +14,9 @@ constexpr int kMaxDet = 4;
 
 // Step a1: projected potential and transmission of one configuration.
 struct PotArgs {
-  const double* ax;            // atom x (Angstrom) in [0, l_x), sorted by slice
-  const double* ay;            // atom y in [0, l_y)
+  const float2* ax;            // atom x (Angstrom) in [0, l_x), sorted by slice, as an exact
+                               // pair x = hi + lo of the FP64 value (lo = fp32(x - hi))
+  const float2* ay;            // atom y in [0, l_y), the same form
   const int16_t* asp;          // species
   const int32_t* slice_start;  // [n_slices + 1]
   const float* peak;           // [n_species] V*Angstrom
@@ -24,10 +25,13 @@ struct PotArgs {
   float frac[kMaxTerms];
   float inv2w2[kMaxTerms];     // 1 / (2 w^2)
   float rc2;                   // r_cut^2
-  double rc;
   int nx, ny, n_slices;
-  double dx, dy, lx, ly;
+  double dx, dy;
   float dx_hi, dx_lo, dy_hi, dy_lo;
+  float lx_hi, lx_lo, ly_hi, ly_lo;          // the periods as hi + lo
+  float c75x_hi, c75x_lo, c75y_hi, c75y_lo;  // 7.5 dx and 7.5 dy (tile centre to pixel 0) as hi + lo
+  float limx, limy;            // r_cut + 8 dx (8 dy) rounded up: an atom farther from the tile
+                               // centre on either axis reaches none of its pixels
   float sigma;
   int rx0, ry0, rw, rh;        // pixel rectangle to (re)build, may wrap; full grid = (0,0,nx,ny)
   float2* t;                   // [n_slices][ny][nx]

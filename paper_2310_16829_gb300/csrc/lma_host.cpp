@@ -748,18 +748,31 @@ lma_status ensure_basis_device(lma_basis* b, cudaStream_t st) {
   return LMA_OK;
 }
 
+// x = hi + lo with hi = fp32(x), lo = fp32(x - hi)
+float2 split_f32(double x) {
+  const float hi = static_cast<float>(x);
+  return make_float2(hi, static_cast<float>(x - static_cast<double>(hi)));
+}
+
 // upload the atoms of a configuration (slice-sorted) if they changed
 lma_status ensure_atoms_device(lma_specimen* sp, int phi, cudaStream_t st) {
   lma_ctx* ctx = sp->ctx;
   PhononSet& p = sp->ph[phi];
   if (!p.dirty && p.dx.p) return LMA_OK;
   const size_t n = std::max<size_t>(1, p.x.size());
-  CUDA_TRY(ctx, ensure(p.dx, n * sizeof(double)));
-  CUDA_TRY(ctx, ensure(p.dy, n * sizeof(double)));
+  // positions as exact pairs hi + lo of FP32 values (the same 8 bytes as the FP64 value; the
+  // potential kernel works with them in FP32 instructions only)
+  std::vector<float2> xs(p.x.size()), ys(p.y.size());
+  for (size_t i = 0; i < p.x.size(); ++i) {
+    xs[i] = split_f32(p.x[i]);
+    ys[i] = split_f32(p.y[i]);
+  }
+  CUDA_TRY(ctx, ensure(p.dx, n * sizeof(float2)));
+  CUDA_TRY(ctx, ensure(p.dy, n * sizeof(float2)));
   CUDA_TRY(ctx, ensure(p.dsp, n * sizeof(int16_t)));
   CUDA_TRY(ctx, ensure(p.dss, p.slice_start.size() * sizeof(int32_t)));
-  CUDA_TRY(ctx, upload_parts(ctx, {HostPart{p.dx.p, p.x.data(), p.x.size() * sizeof(double)},
-                                    HostPart{p.dy.p, p.y.data(), p.y.size() * sizeof(double)},
+  CUDA_TRY(ctx, upload_parts(ctx, {HostPart{p.dx.p, xs.data(), xs.size() * sizeof(float2)},
+                                    HostPart{p.dy.p, ys.data(), ys.size() * sizeof(float2)},
                                     HostPart{p.dsp.p, p.sp.data(), p.sp.size() * sizeof(int16_t)},
                                     HostPart{p.dss.p, p.slice_start.data(), p.slice_start.size() * sizeof(int32_t)}},
                              st));
@@ -784,8 +797,8 @@ lma_status launch_t(lma_specimen* sp, int slot, int phi, const Rect& r, cudaStre
   const lma_grid& g = sp->g;
   PhononSet& p = sp->ph[phi];
   lma_dev::PotArgs a{};
-  a.ax = static_cast<const double*>(p.dx.p);
-  a.ay = static_cast<const double*>(p.dy.p);
+  a.ax = static_cast<const float2*>(p.dx.p);
+  a.ay = static_cast<const float2*>(p.dy.p);
   a.asp = static_cast<const int16_t*>(p.dsp.p);
   a.slice_start = static_cast<const int32_t*>(p.dss.p);
   a.peak = static_cast<const float*>(sp->d_peak.p);
@@ -795,19 +808,28 @@ lma_status launch_t(lma_specimen* sp, int slot, int phi, const Rect& r, cudaStre
     a.frac[q] = static_cast<float>(sp->frac[q]);
     a.inv2w2[q] = static_cast<float>(1.0 / (2.0 * sp->width[q] * sp->width[q]));
   }
-  a.rc = sp->r_cut;
   a.rc2 = static_cast<float>(sp->r_cut * sp->r_cut);
   a.nx = g.nx;
   a.ny = g.ny;
   a.n_slices = g.n_slices;
-  a.lx = g.lx;
-  a.ly = g.ly;
   a.dx = g.lx / g.nx;
   a.dy = g.ly / g.ny;
   a.dx_hi = static_cast<float>(a.dx);
   a.dx_lo = static_cast<float>(a.dx - static_cast<double>(a.dx_hi));
   a.dy_hi = static_cast<float>(a.dy);
   a.dy_lo = static_cast<float>(a.dy - static_cast<double>(a.dy_hi));
+  const float2 lx2 = split_f32(g.lx), ly2 = split_f32(g.ly), c75x = split_f32(7.5 * a.dx), c75y = split_f32(7.5 * a.dy);
+  a.lx_hi = lx2.x;
+  a.lx_lo = lx2.y;
+  a.ly_hi = ly2.x;
+  a.ly_lo = ly2.y;
+  a.c75x_hi = c75x.x;
+  a.c75x_lo = c75x.y;
+  a.c75y_hi = c75y.x;
+  a.c75y_lo = c75y.y;
+  // a margin far above the FP32 rounding of the offsets keeps the test a superset of the exact one
+  a.limx = static_cast<float>(sp->r_cut + 8.0 * a.dx) + 1e-4f;
+  a.limy = static_cast<float>(sp->r_cut + 8.0 * a.dy) + 1e-4f;
   a.sigma = static_cast<float>(g.sigma);
   // Tiles sit on the absolute 16-pixel grid whatever the rectangle, so a
   // pixel is always computed by the same tile origin: a partial rebuild is

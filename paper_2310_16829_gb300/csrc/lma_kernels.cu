@@ -2197,6 +2197,23 @@ struct AtomRel {
 // atom terms in the same order whatever the tile or rectangle: a partial
 // rebuild is bitwise equal to a full one. Each pixel value is written to all
 // its periodic copies in the padded array [ny + W][nx + W].
+// Double-float arithmetic (an unevaluated sum h + l of two FP32 values): Knuth's two-sum is
+// exact, so offsets of the FP64 atom positions from the tile centre stay accurate to about
+// 2^-46 of their size with FP32 instructions only (FP64 runs at a small fraction of the FP32
+// rate on this GPU).
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return make_float2(s, (a - (s - bb)) + (b - bb));
+}
+// (h + l) + (bh + bl), renormalized so that |l| <= ulp(h) / 2
+__device__ __forceinline__ float2 df_add(float2 a, float bh, float bl) {
+  const float2 s = two_sum(a.x, bh);
+  const float e = s.y + (a.y + bl);
+  const float h = s.x + e;
+  return make_float2(h, e - (h - s.x));
+}
+
 __global__ void __launch_bounds__(256) k_potential(const PotArgs a) {
   __shared__ AtomRel lst[256];
   __shared__ int wcount[8];
@@ -2206,9 +2223,11 @@ __global__ void __launch_bounds__(256) k_potential(const PotArgs a) {
   const bool in_rect = (bx + tx < a.rw) && (by + ty < a.rh);
   const int gx0 = (a.rx0 + bx) % a.nx;
   const int gy0 = (a.ry0 + by) % a.ny;
-  // atoms are taken relative to the tile origin; the minimum image is found in FP64
+  // atoms are taken relative to the tile centre (two FP64 products per tile, split into hi + lo)
   const double Xc = (gx0 + 7.5) * a.dx, Yc = (gy0 + 7.5) * a.dy;
-  const double limx = a.rc + 8.0 * a.dx, limy = a.rc + 8.0 * a.dy;
+  const float xch = static_cast<float>(Xc), xcl = static_cast<float>(Xc - static_cast<double>(xch));
+  const float ych = static_cast<float>(Yc), ycl = static_cast<float>(Yc - static_cast<double>(ych));
+  const float hlx = 0.5f * a.lx_hi, hly = 0.5f * a.ly_hi;
   const int a0 = a.slice_start[s], a1 = a.slice_start[s + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float v = 0.f;
@@ -2218,23 +2237,25 @@ __global__ void __launch_bounds__(256) k_potential(const PotArgs a) {
     AtomRel e{0.f, 0.f, 0.f, 0.f, 0.f};
     if (k < a1) {
       // positions lie in [0, l) and the tile centre in [0, l + 8 dx): one period at most
-      // brings the offset to its minimum image
-      double ddx = a.ax[k] - Xc, ddy = a.ay[k] - Yc;
-      if (ddx >= 0.5 * a.lx)
-        ddx -= a.lx;
-      else if (ddx < -0.5 * a.lx)
-        ddx += a.lx;
-      if (ddy >= 0.5 * a.ly)
-        ddy -= a.ly;
-      else if (ddy < -0.5 * a.ly)
-        ddy += a.ly;
-      keep = fabs(ddx) < limx && fabs(ddy) < limy;
+      // brings the offset to its minimum image (decided on the high part: an offset near
+      // half a period is far outside the tile either way)
+      float2 ddx = df_add(a.ax[k], -xch, -xcl), ddy = df_add(a.ay[k], -ych, -ycl);
+      if (ddx.x >= hlx)
+        ddx = df_add(ddx, -a.lx_hi, -a.lx_lo);
+      else if (ddx.x < -hlx)
+        ddx = df_add(ddx, a.lx_hi, a.lx_lo);
+      if (ddy.x >= hly)
+        ddy = df_add(ddy, -a.ly_hi, -a.ly_lo);
+      else if (ddy.x < -hly)
+        ddy = df_add(ddy, a.ly_hi, a.ly_lo);
+      keep = fabsf(ddx.x) < a.limx && fabsf(ddy.x) < a.limy;
       if (keep) {
-        const double rx = ddx + 7.5 * a.dx, ry = ddy + 7.5 * a.dy;
-        e.x_hi = static_cast<float>(rx);
-        e.x_lo = static_cast<float>(rx - static_cast<double>(e.x_hi));
-        e.y_hi = static_cast<float>(ry);
-        e.y_lo = static_cast<float>(ry - static_cast<double>(e.y_hi));
+        // offset from pixel (0, 0) of the tile, as hi + lo
+        const float2 rx = df_add(ddx, a.c75x_hi, a.c75x_lo), ry = df_add(ddy, a.c75y_hi, a.c75y_lo);
+        e.x_hi = rx.x;
+        e.x_lo = rx.y;
+        e.y_hi = ry.x;
+        e.y_lo = ry.y;
         const int spc = a.asp[k];
         e.peak = (spc >= 0 && spc < a.n_species) ? a.peak[spc] : 0.f;
       }
