@@ -26,8 +26,7 @@ struct PotArgs {
   float inv2w2[kMaxTerms];     // 1 / (2 w^2)
   float rc2;                   // r_cut^2
   int nx, ny, n_slices;
-  double dx, dy;
-  float dx_hi, dx_lo, dy_hi, dy_lo;
+  float dx_hi, dx_lo, dy_hi, dy_lo;          // the pixel pitch as hi + lo
   float lx_hi, lx_lo, ly_hi, ly_lo;          // the periods as hi + lo
   float c75x_hi, c75x_lo, c75y_hi, c75y_lo;  // 7.5 dx and 7.5 dy (tile centre to pixel 0) as hi + lo
   float limx, limy;            // r_cut + 8 dx (8 dy) rounded up: an atom farther from the tile

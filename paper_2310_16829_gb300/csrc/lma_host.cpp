@@ -812,13 +812,13 @@ lma_status launch_t(lma_specimen* sp, int slot, int phi, const Rect& r, cudaStre
   a.nx = g.nx;
   a.ny = g.ny;
   a.n_slices = g.n_slices;
-  a.dx = g.lx / g.nx;
-  a.dy = g.ly / g.ny;
-  a.dx_hi = static_cast<float>(a.dx);
-  a.dx_lo = static_cast<float>(a.dx - static_cast<double>(a.dx_hi));
-  a.dy_hi = static_cast<float>(a.dy);
-  a.dy_lo = static_cast<float>(a.dy - static_cast<double>(a.dy_hi));
-  const float2 lx2 = split_f32(g.lx), ly2 = split_f32(g.ly), c75x = split_f32(7.5 * a.dx), c75y = split_f32(7.5 * a.dy);
+  const double dx = g.lx / g.nx, dy = g.ly / g.ny;
+  const float2 dx2 = split_f32(dx), dy2 = split_f32(dy);
+  a.dx_hi = dx2.x;
+  a.dx_lo = dx2.y;
+  a.dy_hi = dy2.x;
+  a.dy_lo = dy2.y;
+  const float2 lx2 = split_f32(g.lx), ly2 = split_f32(g.ly), c75x = split_f32(7.5 * dx), c75y = split_f32(7.5 * dy);
   a.lx_hi = lx2.x;
   a.lx_lo = lx2.y;
   a.ly_hi = ly2.x;
@@ -828,8 +828,8 @@ lma_status launch_t(lma_specimen* sp, int slot, int phi, const Rect& r, cudaStre
   a.c75y_hi = c75y.x;
   a.c75y_lo = c75y.y;
   // a margin far above the FP32 rounding of the offsets keeps the test a superset of the exact one
-  a.limx = static_cast<float>(sp->r_cut + 8.0 * a.dx) + 1e-4f;
-  a.limy = static_cast<float>(sp->r_cut + 8.0 * a.dy) + 1e-4f;
+  a.limx = static_cast<float>(sp->r_cut + 8.0 * dx) + 1e-4f;
+  a.limy = static_cast<float>(sp->r_cut + 8.0 * dy) + 1e-4f;
   a.sigma = static_cast<float>(g.sigma);
   // Tiles sit on the absolute 16-pixel grid whatever the rectangle, so a
   // pixel is always computed by the same tile origin: a partial rebuild is

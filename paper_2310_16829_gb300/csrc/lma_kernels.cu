@@ -2214,6 +2214,14 @@ __device__ __forceinline__ float2 df_add(float2 a, float bh, float bl) {
   return make_float2(h, e - (h - s.x));
 }
 
+// g (bh + bl) as hi + lo: g bh exactly as p + fma(g, bh, -p), plus g bl
+__device__ __forceinline__ float2 prod_df(float g, float bh, float bl) {
+  const float p = g * bh;
+  const float e = fmaf(g, bl, fmaf(g, bh, -p));
+  const float h = p + e;
+  return make_float2(h, e - (h - p));
+}
+
 __global__ void __launch_bounds__(256) k_potential(const PotArgs a) {
   __shared__ AtomRel lst[256];
   __shared__ int wcount[8];
@@ -2223,10 +2231,11 @@ __global__ void __launch_bounds__(256) k_potential(const PotArgs a) {
   const bool in_rect = (bx + tx < a.rw) && (by + ty < a.rh);
   const int gx0 = (a.rx0 + bx) % a.nx;
   const int gy0 = (a.ry0 + by) % a.ny;
-  // atoms are taken relative to the tile centre (two FP64 products per tile, split into hi + lo)
-  const double Xc = (gx0 + 7.5) * a.dx, Yc = (gy0 + 7.5) * a.dy;
-  const float xch = static_cast<float>(Xc), xcl = static_cast<float>(Xc - static_cast<double>(xch));
-  const float ych = static_cast<float>(Yc), ycl = static_cast<float>(Yc - static_cast<double>(ych));
+  // atoms are taken relative to the tile centre (gx0 + 7.5) dx, formed as hi + lo from the
+  // pair dx = dx_hi + dx_lo with an exact FMA product (gx0 + 7.5 is exact in FP32)
+  const float2 xc = prod_df(static_cast<float>(gx0) + 7.5f, a.dx_hi, a.dx_lo);
+  const float2 yc = prod_df(static_cast<float>(gy0) + 7.5f, a.dy_hi, a.dy_lo);
+  const float xch = xc.x, xcl = xc.y, ych = yc.x, ycl = yc.y;
   const float hlx = 0.5f * a.lx_hi, hly = 0.5f * a.ly_hi;
   const int a0 = a.slice_start[s], a1 = a.slice_start[s + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
