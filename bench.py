@@ -46,6 +46,9 @@ UNIT = "pixels/s"
 W = 128
 FLOPS_PER_TRANSLATE_SLICE = 2 * 5 * W * W * 14 + 12 * W * W   # 2,490,368
 FP32_LANES_PER_SM = 128
+# FP32 throughput reached by independent scalar FMA chains (152 x 4 CTAs of 256 threads) on this
+# pool's GB300 at 2070 MHz: the practical ceiling beside the derived peak
+FMA_MICROBENCH_TFLOPS = 74.3
 # DRAM bytes (read + write) of one k_slice launch of one configuration (16384 translates x 50
 # slices) from an ncu capture, with the SHA-256 of the kernel source it was taken on. The bench
 # launch carries all configurations, so the figure is scaled by translate-slices (reads and the
@@ -921,7 +924,9 @@ def main():
                                 "the one-configuration launch, scaled by translate-slices); null when the "
                                 "kernel source differs from the captured one",
                 "peak_source": f"FP32 FMA: {n_sms} SMs (device query) x {FP32_LANES_PER_SM} lanes x 2 flop x "
-                               f"{sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json); of measured clocks",
+                               f"{sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json); of measured clocks. "
+                               f"An FMA-chain microbenchmark reached {FMA_MICROBENCH_TFLOPS} TFLOP/s on this GPU",
+                "frac_of_fma_microbenchmark": achieved / FMA_MICROBENCH_TFLOPS,
                 "algorithmic": f"{FLOPS_PER_TRANSLATE_SLICE} flop per translate-slice x "
                                f"{sl['units'] // max(1, sl['launches'])} translate-slices per launch",
                 "share_of_step": sl["total_ms"] / max(1e-9, sum(v["total_ms"] for v in prof.values() if isinstance(v, dict))),
