@@ -471,7 +471,7 @@ def _batching_case(ws, n_phonons: int, steps: int, label: str) -> dict:
                        "passes": int(max(-(-n_phonons // max(1, i.phonon_batch)) for i in info)),
                        "first_call_s": first_s},
            "speedup": ms_plain / ms_b, "bitwise_equal": bool(same),
-           "tuning": ctx.tuning()}
+           "tuning": ctx.tuning(), "synth_tuning": ctx.synth_tuning()}
     for spec, basis in objs:
         basis.close()
         spec.close()

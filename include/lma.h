@@ -79,8 +79,9 @@ typedef int32_t lma_status;
 #define LMA_IMAGE_RECOMPUTE 1u /* treat every stored exit wave as stale (full path) */
 #define LMA_MAX_RINGS 256      /* rings of one 3D STEM image */
 #define LMA_IMAGE_GRAPH 2u     /* lma_image_many: replay the device work as one CUDA graph */
-#define LMA_IMAGE_AUTOTUNE 4u  /* time every slice launch mode on this call's first launch of each
-                                  shape and keep the fastest for that shape (lma_tuning_read) */
+#define LMA_IMAGE_AUTOTUNE 4u  /* time every slice launch mode, and every synthesis strip width and
+                                  grid, on this call's first launch of each shape and keep the
+                                  fastest for that shape (lma_tuning_read, lma_synth_tuning_read) */
 
 /* Partition strategies of a probe region (Sec. 4.2.4). */
 #define LMA_PART_ROWS 0                    /* row by row */
@@ -523,6 +524,30 @@ lma_status lma_set_slice_mode(lma_ctx* ctx, int32_t mode);
 /* Copy up to cap tuned launch shapes (LMA_IMAGE_AUTOTUNE) to out, oldest
  * first (out may be NULL when cap is 0); *n receives how many the context holds. */
 lma_status lma_tuning_read(lma_ctx* ctx, lma_tuning* out, int32_t cap, int32_t* n);
+
+/* One autotuned synthesis launch shape (steps a4-a6 under LMA_IMAGE_AUTOTUNE): the readout,
+ * store precision, probe region or list, configurations, L and window W of the launch; the
+ * probe-strip width and grid chosen, and the duration of each variant (ms; CUDA events on the
+ * caller's stream, one launch each). Variant v = 2 s + g: strip width 16, 32, 64 for s = 0, 1,
+ * 2 (probes are walked in vertical strips of that many columns, which sets how many exit waves
+ * the CTAs in flight share in L2) and grid g = 0 one CTA per probe, g = 1 persistent (one CTA
+ * per SM walking the probes in order). Every variant gives the same readings bit for bit, so
+ * the timed launches' results are kept. Launches over a probe list (edits, partitions) walk
+ * the list in order and time the grids only (ms of the other strips: 0). */
+typedef struct {
+  int32_t readout;           /* 0: annular detectors, 1: labelled rings (3D), 2: patterns (4D) */
+  int32_t half;              /* 1: FP16 exit-wave store */
+  int64_t n_items;           /* probes x configurations of the launch */
+  int32_t L;                 /* input waves per probe */
+  int32_t window;            /* exit-wave window W */
+  int32_t strip;             /* chosen strip width */
+  int32_t persistent;        /* chosen grid: 1 persistent, 0 one CTA per probe */
+  double ms[6];              /* duration per variant, indexed 2 s + g */
+} lma_synth_tuning;
+
+/* Copy up to cap tuned synthesis launch shapes to out, oldest first (out may be NULL when cap
+ * is 0); *n receives how many the context holds. */
+lma_status lma_synth_tuning_read(lma_ctx* ctx, lma_synth_tuning* out, int32_t cap, int32_t* n);
 
 #ifdef __cplusplus
 }

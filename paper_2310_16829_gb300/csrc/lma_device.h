@@ -148,7 +148,10 @@ size_t slice_gen_scratch_bytes(int W);
 // one warp runs the bounded mbarrier wait of the tensor-core (which = 0) or W = 256 (which = 1)
 // slice kernel on a phase that never completes; *status |= 1 when it gives up
 cudaError_t launch_selftest_wait(int which, int* status, cudaStream_t s);
-cudaError_t launch_synth(const SynthArgs& a, bool half, int mode, cudaStream_t s);
+// synthesis grid: kSynthGridAuto (persistent for the complex64 store, one CTA per item for the
+// FP16 store), one CTA per item, or persistent (one CTA per SM); every grid gives the same bits
+constexpr int kSynthGridAuto = 0, kSynthGridPerItem = 1, kSynthGridPersistent = 2;
+cudaError_t launch_synth(const SynthArgs& a, bool half, int mode, int grid_mode, cudaStream_t s);
 // step a3 with the propagation as a periodic convolution with the K1 x K2 kernel q (device,
 // [K2][K1] complex64, offsets -(K/2) .. K/2); K1 in {3, 5, ..., 13}, K2 odd <= 25; complex64 store
 cudaError_t launch_slice_rs(const SliceLaunch& a, const float2* q, int K1, int K2, cudaStream_t s);

@@ -86,6 +86,11 @@ struct lma_ctx {
     lma_tuning rec;
   };
   std::vector<Tune> tune;
+  struct SynthTune {
+    std::vector<int64_t> key;
+    lma_synth_tuning rec;
+  };
+  std::vector<SynthTune> synth_tune;
   // captured image sequences (lma_image_many with LMA_IMAGE_GRAPH)
   struct Graph {
     std::vector<uintptr_t> key;
@@ -984,6 +989,66 @@ lma_status check_slice_status(lma_ctx* ctx) {
   return LMA_OK;
 }
 
+// Issue one synthesis launch with the tuned strip width and grid of its shape, else the
+// defaults. With autotuning on and a shape not seen before, every variant runs once (each
+// assigns the same readings) and is timed with events on the stream; the fastest is kept.
+lma_status synth_launch(lma_ctx* ctx, lma_dev::SynthArgs& a, bool half, int mode, int64_t units, cudaStream_t st) {
+  const bool listed = a.probe_list != nullptr;
+  std::vector<int64_t> key{half ? 1 : 0, mode, listed ? 1 : 0, listed ? a.n_list : a.n_probes, a.npx, a.npy, a.n_cfg,
+                           a.L, a.W, a.cyclic};
+  const lma_ctx::SynthTune* tuned = nullptr;
+  for (const auto& t : ctx->synth_tune)
+    if (t.key == key) tuned = &t;
+  auto launch = [&](int strip, int grid) {
+    a.strip = strip;
+    return counted(ctx, K_SYNTH, units, st, [&] { return lma_dev::launch_synth(a, half, mode, grid, st); });
+  };
+  if (tuned || !ctx->autotune || ctx->capturing) {
+    if (tuned)
+      CUDA_TRY(ctx, launch(tuned->rec.strip,
+                           tuned->rec.persistent ? lma_dev::kSynthGridPersistent : lma_dev::kSynthGridPerItem));
+    else
+      CUDA_TRY(ctx, launch(kSynthStrip, lma_dev::kSynthGridAuto));
+    return LMA_OK;
+  }
+  static const int kStrips[3] = {16, 32, 64};
+  lma_ctx::SynthTune t;
+  t.key = key;
+  t.rec = lma_synth_tuning{};
+  t.rec.readout = mode == lma_dev::kReadAnnuli ? 0 : (mode == lma_dev::kReadLabels ? 1 : 2);
+  t.rec.half = half ? 1 : 0;
+  t.rec.n_items = static_cast<int64_t>(listed ? a.n_list : a.n_probes) * a.n_cfg;
+  t.rec.L = a.L;
+  t.rec.window = a.W;
+  cudaEvent_t ev[7];
+  for (auto& e : ev) CUDA_TRY(ctx, cudaEventCreate(&e));
+  cudaError_t err = cudaEventRecord(ev[0], st);
+  int nv = 0;
+  int var[6];
+  for (int si = 0; si < 3 && err == cudaSuccess; ++si) {
+    if (listed && si != 1) continue;   // a list is walked in order: the strip does not apply
+    for (int g = 0; g < 2 && err == cudaSuccess; ++g) {
+      err = launch(kStrips[si], g ? lma_dev::kSynthGridPersistent : lma_dev::kSynthGridPerItem);
+      if (err == cudaSuccess) err = cudaEventRecord(ev[nv + 1], st);
+      var[nv++] = 2 * si + g;
+    }
+  }
+  if (err == cudaSuccess) err = cudaEventSynchronize(ev[nv]);
+  int best = -1;
+  for (int i = 0; i < nv && err == cudaSuccess; ++i) {
+    float ms = 0.f;
+    err = cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+    t.rec.ms[var[i]] = ms;
+    if (best < 0 || t.rec.ms[var[i]] < t.rec.ms[best]) best = var[i];
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  CUDA_TRY(ctx, err);
+  t.rec.strip = kStrips[best / 2];
+  t.rec.persistent = best % 2;
+  ctx->synth_tune.push_back(t);
+  return LMA_OK;
+}
+
 lma_dev::SliceJob make_job(const lma_basis* b, const lma_specimen* sp) {
   const lma_grid& g = sp->g;
   lma_dev::SliceJob J{};
@@ -1445,8 +1510,7 @@ lma_status images_work(lma_ctx* ctx, const std::vector<ImageJob>& jobs, const Re
         a.pat_a = ro.pat_a;
         a.pat_b = ro.pat_b;
       }
-      CUDA_TRY(ctx, counted(ctx, K_SYNTH, np * nb, st,
-                            [&] { return lma_dev::launch_synth(a, half, ro.mode, st); }));
+      { const lma_status ss_ = synth_launch(ctx, a, half, ro.mode, np * nb, st); if (ss_ != LMA_OK) return ss_; }
       if (pattern) {
         const int64_t n = np * ro.pat_size();
         CUDA_TRY(ctx, counted(ctx, K_FIN, n, st, [&] {
@@ -2503,8 +2567,7 @@ lma_status lma_image_coherent(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, cons
       a.n_det = n_det;
       a.acc = static_cast<double*>(b->d_acc.p) + static_cast<size_t>(v) * nph * nout;
       a.band_r2 = b->r2max;
-      CUDA_TRY(ctx, counted(ctx, K_SYNTH, np * nb, st,
-                            [&] { return lma_dev::launch_synth(a, half, lma_dev::kReadAnnuli, st); }));
+      { const lma_status ss_ = synth_launch(ctx, a, half, lma_dev::kReadAnnuli, np * nb, st); if (ss_ != LMA_OK) return ss_; }
     }
   }
   const double* acc = static_cast<const double*>(b->d_acc.p);
@@ -2619,8 +2682,7 @@ lma_status lma_image_partitioned(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, c
       a.n_det = n_det;
       a.acc = static_cast<double*>(b->d_acc.p);
       a.band_r2 = b->r2max;
-      CUDA_TRY(ctx, counted(ctx, K_SYNTH, static_cast<int64_t>(P.probes.size()), st,
-                            [&] { return lma_dev::launch_synth(a, half, lma_dev::kReadAnnuli, st); }));
+      { const lma_status ss_ = synth_launch(ctx, a, half, lma_dev::kReadAnnuli, static_cast<int64_t>(P.probes.size()), st); if (ss_ != LMA_OK) return ss_; }
     }
   }
   const double* acc = static_cast<const double*>(b->d_acc.p);
@@ -2840,6 +2902,13 @@ lma_status lma_tuning_read(lma_ctx* ctx, lma_tuning* out, int32_t cap, int32_t* 
   return LMA_OK;
 }
 
+lma_status lma_synth_tuning_read(lma_ctx* ctx, lma_synth_tuning* out, int32_t cap, int32_t* n) {
+  if (!ctx || !n || cap < 0 || (cap > 0 && !out)) return fail(ctx, LMA_ERR_INVALID, "null argument");
+  *n = static_cast<int32_t>(ctx->synth_tune.size());
+  for (int32_t i = 0; i < cap && i < *n; ++i) out[i] = ctx->synth_tune[i].rec;
+  return LMA_OK;
+}
+
 lma_status lma_edit_column(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, double cx, double cy, double r_site,
                            int32_t op, int16_t new_species, int64_t* n_atoms_changed, int64_t* n_stale) {
   if (!ctx || !sp) return fail(ctx, LMA_ERR_INVALID, "null argument");
@@ -2998,7 +3067,7 @@ lma_status lma_readout_noalloc(lma_ctx* ctx, lma_basis* b, const float* exit_wav
   a.det_bits = reinterpret_cast<const uint32_t*>(base + o_det);
   a.n_det = n_det;
   a.acc = reinterpret_cast<double*>(base + o_acc);
-  CUDA_TRY(ctx, lma_dev::launch_synth(a, false, lma_dev::kReadAnnuli, st));
+  CUDA_TRY(ctx, lma_dev::launch_synth(a, false, lma_dev::kReadAnnuli, lma_dev::kSynthGridAuto, st));
   CUDA_TRY(ctx, lma_dev::launch_finalize(a.acc, nout, 1, 1.0, out, st));
   // the host tables above are pageable: keep them alive until the copies have run
   CUDA_TRY(ctx, cudaStreamSynchronize(st));

@@ -2590,14 +2590,16 @@ cudaError_t launch_slice_rs(const SliceLaunch& a, const float2* q, int K1, int K
   return cudaGetLastError();
 }
 
-cudaError_t launch_synth(const SynthArgs& a, bool half, int mode, cudaStream_t s) {
+cudaError_t launch_synth(const SynthArgs& a, bool half, int mode, int grid_mode, cudaStream_t s) {
   const int n_walk = a.probe_list ? a.n_list : a.n_probes;
   if (n_walk <= 0) return cudaSuccess;
-  // complex64 store: persistent, one CTA per SM walking the items in order (the per-CTA set-up
-  // is paid once; 30.5 -> 29.7 ms on the benchmark). FP16 store: one CTA per item, whose
-  // hardware scheduling balances its shorter items better (28.1 ms against 31.6 persistent).
+  // kSynthGridAuto: the complex64 store persistent, one CTA per SM walking the items in order
+  // (the per-CTA set-up is paid once; 30.5 -> 29.7 ms on the benchmark), the FP16 store one
+  // CTA per item, whose hardware scheduling balances its shorter items better (28.1 ms against
+  // 31.6 persistent); the other modes force one of the two (the autotuner times both)
   const int n_items = n_walk * a.n_cfg;
-  const int grid = half ? n_items : (n_items < sm_count() ? n_items : sm_count());
+  const bool persistent = grid_mode == kSynthGridPersistent || (grid_mode == kSynthGridAuto && !half);
+  const int grid = persistent ? (n_items < sm_count() ? n_items : sm_count()) : n_items;
   const size_t sm = synth_smem_bytes();
   // periodic probe windows (the window is the whole cell) wrap; others are zero outside
   using K = void (*)(const SynthArgs);

@@ -64,7 +64,7 @@ EXPORTS = [
     "lma_affected_probes",
     "lma_profile_enable", "lma_profile_read", "lma_readout_noalloc", "lma_realspace_gain",
     "lma_set_slice_mode", "lma_tuning_read", "lma_partition", "lma_image_partitioned",
-    "lma_image_coherent", "lma_select_L", "lma_image_realspace", "lma_selftest_wait",
+    "lma_image_coherent", "lma_select_L", "lma_image_realspace", "lma_selftest_wait", "lma_synth_tuning_read",
 ]
 
 
@@ -142,6 +142,18 @@ class Tuning(C.Structure):
                 "ms": {SLICE_MODE_NAMES[m]: float(self.ms[m]) for m in range(3)}}
 
 
+class SynthTuning(C.Structure):
+    _fields_ = [("readout", C.c_int32), ("half", C.c_int32), ("n_items", C.c_int64), ("L", C.c_int32),
+                ("window", C.c_int32), ("strip", C.c_int32), ("persistent", C.c_int32), ("ms", C.c_double * 6)]
+
+    def as_dict(self):
+        return {"readout": ("annuli", "labels", "pattern")[int(self.readout)], "half": bool(self.half),
+                "n_items": int(self.n_items), "L": int(self.L), "window": int(self.window),
+                "strip": int(self.strip), "persistent": bool(self.persistent),
+                "ms": {f"strip{16 << (v // 2)}_{'persistent' if v % 2 else 'per_probe'}": float(self.ms[v])
+                       for v in range(6) if self.ms[v] > 0}}
+
+
 class LmaError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -193,6 +205,7 @@ _SIGS = {
     "lma_image_partitioned": (C.c_int32, [_VP, _VP, _VP, C.POINTER(Detector), C.c_int32, C.POINTER(Region),
                                           C.POINTER(PartitionDesc), C.c_uint32, _VP, _VP]),
     "lma_tuning_read": (C.c_int32, [_VP, C.POINTER(Tuning), C.c_int32, C.POINTER(C.c_int32)]),
+    "lma_synth_tuning_read": (C.c_int32, [_VP, C.POINTER(SynthTuning), C.c_int32, C.POINTER(C.c_int32)]),
 }
 
 _LIB: Optional[C.CDLL] = None
@@ -276,6 +289,13 @@ class Context:
         self.check(self.lib.lma_tuning_read(self.h, None, 0, C.byref(n)))
         recs = (Tuning * max(1, n.value))()
         self.check(self.lib.lma_tuning_read(self.h, recs, n.value, C.byref(n)))
+        return [recs[i].as_dict() for i in range(n.value)]
+
+    def synth_tuning(self) -> list:
+        n = C.c_int32()
+        self.check(self.lib.lma_synth_tuning_read(self.h, None, 0, C.byref(n)))
+        recs = (SynthTuning * max(1, n.value))()
+        self.check(self.lib.lma_synth_tuning_read(self.h, recs, n.value, C.byref(n)))
         return [recs[i].as_dict() for i in range(n.value)]
 
     def close(self) -> None:

@@ -341,3 +341,12 @@ def test_selftest_wait_checks_its_arguments_before_the_device():
     assert ctx.selftest_wait(2) == lma.LMA_ERR_INVALID
     assert ctx.selftest_wait(-1) == lma.LMA_ERR_INVALID
     assert ctx.selftest_wait(0) == lma.LMA_ERR_UNSUPPORTED
+
+
+def test_synth_tuning_read_reports_nothing_before_tuning():
+    """lma_synth_tuning_read counts the tuned synthesis shapes (none in a fresh context) and
+    checks its arguments."""
+    ctx = lma.Context(-1)
+    assert ctx.synth_tuning() == []
+    n = ctypes.c_int32()
+    assert ctx.lib.lma_synth_tuning_read(ctx.h, None, 1, ctypes.byref(n)) == lma.LMA_ERR_INVALID

@@ -195,7 +195,20 @@ def test_autotune_times_every_mode_and_keeps_results():
     assert r["n_items"] > 0 and r["translate_slices"] >= 6 * r["n_items"]
     assert all(v > 0 for v in r["ms"].values())
     assert r["mode"] == min(r["ms"], key=r["ms"].get)
-    # a second tuned call reuses the choice
-    lma.image_many(c, bases, ws[0].detectors, regions, tuned, autotune=True)
-    assert len(c.tuning()) == 1
+    # the synthesis of each specimen is tuned as well: every strip width and grid timed once,
+    # the fastest kept (the readings above are those of the untuned call, bit for bit)
+    srecs = c.synth_tuning()
+    assert len(srecs) == len(ws)
+    for sr, w in zip(srecs, ws):
+        assert sr["readout"] == "annuli" and not sr["half"] and sr["window"] == w.basis.window
+        assert sr["n_items"] == w.region.npx * w.region.npy * len(w.phonons)
+        assert len(sr["ms"]) == 6 and all(v > 0 for v in sr["ms"].values())
+        chosen = f"strip{sr['strip']}_{'persistent' if sr['persistent'] else 'per_probe'}"
+        assert chosen == min(sr["ms"], key=sr["ms"].get)
+    # a second tuned call reuses the choices, with the same bits
+    again = [np.empty_like(p) for p in plain]
+    lma.image_many(c, bases, ws[0].detectors, regions, again, autotune=True)
+    assert len(c.tuning()) == 1 and len(c.synth_tuning()) == len(ws)
+    for t, p in zip(again, plain):
+        assert np.array_equal(t, p)
     c.close()
