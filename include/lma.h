@@ -527,23 +527,51 @@ lma_status lma_tuning_read(lma_ctx* ctx, lma_tuning* out, int32_t cap, int32_t* 
 
 /* One autotuned synthesis launch shape (steps a4-a6 under LMA_IMAGE_AUTOTUNE): the readout,
  * store precision, probe region or list, configurations, L and window W of the launch; the
- * probe-strip width and grid chosen, and the duration of each variant (ms; CUDA events on the
- * caller's stream, one launch each). Variant v = 2 s + g: strip width 16, 32, 64 for s = 0, 1,
- * 2 (probes are walked in vertical strips of that many columns, which sets how many exit waves
- * the CTAs in flight share in L2) and grid g = 0 one CTA per probe, g = 1 persistent (one CTA
- * per SM walking the probes in order). Every variant gives the same readings bit for bit, so
- * the timed launches' results are kept. Launches over a probe list (edits, partitions) walk
- * the list in order and time the grids only (ms of the other strips: 0). */
+ * form chosen, and the duration of each variant (ms; CUDA events on the caller's stream, one
+ * launch each, or for the grouped form the group and detection launches of every
+ * configuration). Variants 0..5 are the per-probe gather, v = 2 s + g: strip width 16, 32, 64
+ * for s = 0, 1, 2 (probes are walked in vertical strips of that many columns, which sets how
+ * many exit waves the CTAs in flight share in L2) and grid g = 0 one CTA per probe, g = 1
+ * persistent (one CTA per SM walking the probes in order). Variants 6 and 7 are the grouped
+ * form (LMA_SYNTH_GROUPED) with the group shapes group_shape[0] and group_shape[1] (ms 0 where
+ * the launch does not admit it). Every variant gives the same readings bit for bit, so the
+ * timed launches' results are kept. Launches over a probe list (edits, partitions) walk the
+ * list in order and time the grids of the gather only (ms of the other variants: 0). */
 typedef struct {
   int32_t readout;           /* 0: annular detectors, 1: labelled rings (3D), 2: patterns (4D) */
   int32_t half;              /* 1: FP16 exit-wave store */
   int64_t n_items;           /* probes x configurations of the launch */
   int32_t L;                 /* input waves per probe */
   int32_t window;            /* exit-wave window W */
-  int32_t strip;             /* chosen strip width */
-  int32_t persistent;        /* chosen grid: 1 persistent, 0 one CTA per probe */
-  double ms[6];              /* duration per variant, indexed 2 s + g */
+  int32_t strip;             /* chosen strip width (gather) */
+  int32_t persistent;        /* chosen grid (gather): 1 persistent, 0 one CTA per probe */
+  int32_t grouped;           /* 1: the grouped form was chosen, with group_x x group_y probes */
+  int32_t group_x, group_y;
+  int32_t group_shape[2][2]; /* the two timed group shapes (x, y) of variants 6 and 7 */
+  double ms[8];              /* duration per variant */
 } lma_synth_tuning;
+
+/* How the synthesis (step a4) forms each probe's wave Psi_p = sum_j alpha_j U_{i_j}.
+ * Both forms sum each probe's terms in ascending translate index and give the same readings
+ * bit for bit. */
+#define LMA_SYNTH_AUTO -1     /* the tuned form of the launch shape, else grouped where the
+                                 launch admits it (a whole region, non-periodic windows) */
+#define LMA_SYNTH_GATHER 0    /* one CTA per probe gathers its L windows and detects */
+#define LMA_SYNTH_GROUPED 1   /* one CTA per group of up to 16 neighbouring probes loads each
+                                 exit-wave element once for all of them and writes their waves
+                                 to a device buffer (probes x 128 KiB, allocated by the
+                                 context); a second pass detects; falls back to the gather
+                                 where the launch does not admit it */
+
+/* Force the synthesis form of this context (LMA_SYNTH_*). LMA_ERR_INVALID for an unknown form. */
+lma_status lma_set_synth_mode(lma_ctx* ctx, int32_t mode);
+/* Largest probe-wave buffer of the grouped synthesis (bytes; 0: the default, 2 GiB). A region
+ * whose waves (probes x 128 KiB) exceed it is synthesized in chunks of whole group rows; a
+ * limit below one group row's waves leaves the gather. The buffer is allocated on first use
+ * (when it has to grow, only if it is at most half the free device memory) and kept by the
+ * context; under graph capture a missing or short buffer leaves the gather.
+ * LMA_ERR_INVALID for a negative limit. */
+lma_status lma_set_synth_buffer_limit(lma_ctx* ctx, int64_t bytes);
 
 /* Copy up to cap tuned synthesis launch shapes to out, oldest first (out may be NULL when cap
  * is 0); *n receives how many the context holds. */

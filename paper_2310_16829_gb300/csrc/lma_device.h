@@ -152,6 +152,30 @@ cudaError_t launch_selftest_wait(int which, int* status, cudaStream_t s);
 // FP16 store), one CTA per item, or persistent (one CTA per SM); every grid gives the same bits
 constexpr int kSynthGridAuto = 0, kSynthGridPerItem = 1, kSynthGridPersistent = 2;
 cudaError_t launch_synth(const SynthArgs& a, bool half, int mode, int grid_mode, cudaStream_t s);
+
+// Step a4 for groups of neighbouring probes (probe_list null, non-periodic placement): each
+// CTA takes gx x gy probes of the region, forms the union of their (translate, placement)
+// pairs in ascending translate order and writes Psi_p = sum_j alpha_j U_{i_j} of every probe
+// of the group into psi, loading each exit-wave element once for all the group's probes that
+// use it. Each probe's terms are summed in ascending translate index, as k_synth_detect does
+// with tables sorted that way, so a detection pass over psi (launch_synth with the identity
+// tables below) gives the same bits as the per-probe gather.
+struct GroupArgs {
+  int gx, gy;                  // probes per group along x and y: gx gy <= 16, gx gy L <= 512
+  int psx, psy;                // probe spacing (pixels): offset between neighbouring probe windows
+  int ngx, ngy;                // groups per region row; group rows of this launch
+  int gb_base;                 // first group row of this launch
+  int gstrip;                  // groups are visited in vertical strips of this many columns
+  int cfg;                     // store slot read
+  float2* psi;                 // probe waves of the launch's probe rows, [probe - gb_base gy npx][kW][kW]
+};
+constexpr int kGroupMaxProbes = 16, kGroupMaxEntries = 512;
+constexpr int kGroupPosBias = 2048;   // translate placements in a group's frame lie in [-2048, 2048)
+size_t synth_group_smem_bytes();
+// grid_mode as for launch_synth (kSynthGridAuto: persistent)
+cudaError_t launch_synth_group(const SynthArgs& a, const GroupArgs& g, bool half, int grid_mode, cudaStream_t s);
+// tables of the detection pass over psi: tidx[i] = i, alpha[i] = 1, shift[i] = 0, i < n
+cudaError_t launch_identity_tables(int n, int32_t* tidx, float2* alpha, int2* shift, cudaStream_t s);
 // step a3 with the propagation as a periodic convolution with the K1 x K2 kernel q (device,
 // [K2][K1] complex64, offsets -(K/2) .. K/2); K1 in {3, 5, ..., 13}, K2 odd <= 25; complex64 store
 cudaError_t launch_slice_rs(const SliceLaunch& a, const float2* q, int K1, int K2, cudaStream_t s);

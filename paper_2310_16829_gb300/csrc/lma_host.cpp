@@ -74,6 +74,14 @@ struct lma_ctx {
   bool tc_launched = false;                                 // a slice launch with a status word since the last check
   void* gen_scratch = nullptr;                              // per-CTA waves of the W = 256 slice kernel
   size_t gen_scratch_bytes = 0;
+  // grouped synthesis: probe waves of a chunk of probe rows, and the detection pass's tables
+  // (tidx = i, which also serves as the list of region indices, alpha = 1, shift = 0)
+  void* psi = nullptr;
+  size_t psi_bytes = 0;
+  void* psi_tab = nullptr;
+  int64_t psi_tab_n = 0;
+  int synth_mode = -1;                                      // LMA_SYNTH_*
+  int64_t psi_max = int64_t(2) << 30;                       // largest probe-wave buffer (bytes)
   void* stage = nullptr;                                    // pinned staging buffer (kStageBytes)
   // slice launch modes: forced (>= 0), or the timed choice per launch shape
   int forced_mode = -1;
@@ -378,6 +386,7 @@ struct RegionTables {
   DevBuf tidx, alpha, shift;
   std::vector<int32_t> h_tidx;   // host copy of the translate indices
   std::vector<uint8_t> needed;   // translates the region reads
+  int shift_abs = 0;             // largest |component| of the placements
 };
 
 struct lma_basis {
@@ -989,63 +998,204 @@ lma_status check_slice_status(lma_ctx* ctx) {
   return LMA_OK;
 }
 
-// Issue one synthesis launch with the tuned strip width and grid of its shape, else the
-// defaults. With autotuning on and a shape not seen before, every variant runs once (each
-// assigns the same readings) and is timed with events on the stream; the fastest is kept.
-lma_status synth_launch(lma_ctx* ctx, lma_dev::SynthArgs& a, bool half, int mode, int64_t units, cudaStream_t st) {
+// Probe geometry of a synthesis launch over a whole region (psx = 0: none, the grouped form
+// does not apply).
+struct SynthGeom {
+  int psx = 0, psy = 0;        // probe spacing (pixels)
+  int shift_abs = 0;           // largest |component| of the region's placements
+};
+
+SynthGeom region_geom(const lma_basis* b) {
+  SynthGeom g;
+  g.psx = b->reg.r.spacing_px[0];
+  g.psy = b->reg.r.spacing_px[1];
+  g.shift_abs = b->reg.shift_abs;
+  return g;
+}
+
+// The two group shapes timed for L input waves per probe: up to 16 probes and 512
+// (probe, wave) entries per group; 0 when no group of two probes fits.
+int group_shapes(int L, int shapes[2][2]) {
+  const int gmax = std::min(lma_dev::kGroupMaxProbes, lma_dev::kGroupMaxEntries / std::max(1, L));
+  static const int cand[4][2][2] = {{{4, 4}, {8, 2}}, {{4, 2}, {8, 1}}, {{2, 2}, {4, 1}}, {{2, 1}, {1, 2}}};
+  const int k = gmax >= 16 ? 0 : gmax >= 8 ? 1 : gmax >= 4 ? 2 : gmax >= 2 ? 3 : -1;
+  if (k < 0) return 0;
+  std::memcpy(shapes, cand[k], sizeof(cand[k]));
+  return 2;
+}
+
+// Issue the synthesis of one launch shape in the tuned form, else the default: the grouped
+// form where the launch admits it, else the gather with the default strip and grid. With
+// autotuning on and a shape not seen before, every variant runs once (each assigns the same
+// readings) and is timed with events on the stream; the fastest is kept.
+lma_status synth_launch(lma_ctx* ctx, lma_dev::SynthArgs& a, bool half, int mode, int64_t units, const SynthGeom& geo,
+                        cudaStream_t st) {
   const bool listed = a.probe_list != nullptr;
   std::vector<int64_t> key{half ? 1 : 0, mode, listed ? 1 : 0, listed ? a.n_list : a.n_probes, a.npx, a.npy, a.n_cfg,
-                           a.L, a.W, a.cyclic};
-  const lma_ctx::SynthTune* tuned = nullptr;
-  for (const auto& t : ctx->synth_tune)
-    if (t.key == key) tuned = &t;
-  auto launch = [&](int strip, int grid) {
+                           a.L, a.W, a.cyclic, geo.psx, geo.psy};
+  // ---- the grouped form's admission: a whole region, non-periodic windows, placements that
+  // fit the sort key, and a wave buffer (allocated here, outside a capture)
+  int shapes[2][2] = {};
+  bool admit[2] = {false, false};
+  const int nsh = (!listed && !a.cyclic && geo.psx > 0 && geo.psy > 0 && a.n_translates < (1 << 30))
+                      ? group_shapes(a.L, shapes) : 0;
+  const int64_t row_bytes = static_cast<int64_t>(a.npx) * kW * kW * sizeof(float2);
+  for (int i = 0; i < nsh; ++i) {
+    const int gx = shapes[i][0], gy = shapes[i][1];
+    admit[i] = (std::max(gx, gy) - 1) * std::max(geo.psx, geo.psy) + geo.shift_abs < lma_dev::kGroupPosBias &&
+               gy * row_bytes <= ctx->psi_max;
+  }
+  auto psi_ready = [&](int gy) -> bool {
+    const int64_t rows = std::min<int64_t>(a.npy, (ctx->psi_max / (gy * row_bytes)) * gy);
+    const size_t need = static_cast<size_t>(rows * row_bytes);
+    const int64_t n_tab = static_cast<int64_t>(a.npx) * a.npy;
+    if (ctx->psi_bytes >= need && ctx->psi_tab_n >= n_tab) return true;
+    if (ctx->capturing) return false;
+    if (ctx->psi_bytes < need) {
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) != cudaSuccess || need > fr / 2) return false;
+      if (ctx->psi) cudaFree(ctx->psi);
+      ctx->psi = nullptr;
+      ctx->psi_bytes = 0;
+      if (counted_malloc(&ctx->psi, need) != cudaSuccess) return false;
+      ctx->psi_bytes = need;
+    }
+    if (ctx->psi_tab_n < n_tab) {
+      if (ctx->psi_tab) cudaFree(ctx->psi_tab);
+      ctx->psi_tab = nullptr;
+      ctx->psi_tab_n = 0;
+      if (counted_malloc(&ctx->psi_tab, static_cast<size_t>(n_tab) * 20) != cudaSuccess) return false;
+      char* t = static_cast<char*>(ctx->psi_tab);
+      if (lma_dev::launch_identity_tables(static_cast<int>(n_tab), reinterpret_cast<int32_t*>(t + 16 * n_tab),
+                                          reinterpret_cast<float2*>(t), reinterpret_cast<int2*>(t + 8 * n_tab),
+                                          st) != cudaSuccess)
+        return false;
+      ctx->psi_tab_n = n_tab;
+    }
+    return true;
+  };
+  auto gather = [&](int strip, int grid) -> cudaError_t {
     a.strip = strip;
     return counted(ctx, K_SYNTH, units, st, [&] { return lma_dev::launch_synth(a, half, mode, grid, st); });
   };
+  // grouped form: per configuration and chunk of group rows, the group launch writes the
+  // chunk's probe waves and the detection pass (L = 1, identity tables, the chunk's probes
+  // as a list of region indices) reads them out into the configuration's slot
+  auto grouped = [&](int gx, int gy) -> cudaError_t {
+    lma_dev::GroupArgs g{};
+    g.gx = gx;
+    g.gy = gy;
+    g.psx = geo.psx;
+    g.psy = geo.psy;
+    g.ngx = (a.npx + gx - 1) / gx;
+    const int ngy = (a.npy + gy - 1) / gy;
+    const int cg = std::max<int>(1, static_cast<int>(ctx->psi_max / (gy * row_bytes)));
+    g.gstrip = std::max(1, kSynthStrip / gx);
+    g.psi = static_cast<float2*>(ctx->psi);
+    const int64_t n_tab = ctx->psi_tab_n;
+    const char* t = static_cast<const char*>(ctx->psi_tab);
+    const int32_t* iota = reinterpret_cast<const int32_t*>(t + 16 * n_tab);
+    const int64_t pat_size = static_cast<int64_t>(2 * a.pat_a + 1) * (2 * a.pat_b + 1);
+    for (int c = 0; c < a.n_cfg; ++c) {
+      for (int gr0 = 0; gr0 < ngy; gr0 += cg) {
+        g.gb_base = gr0;
+        g.ngy = std::min(cg, ngy - gr0);
+        g.cfg = c;
+        const int p0 = gr0 * gy * a.npx;
+        const int p1 = std::min(a.npy, (gr0 + g.ngy) * gy) * a.npx;
+        cudaError_t e = counted(ctx, K_SYNTH, 0, st, [&] { return lma_dev::launch_synth_group(a, g, half, lma_dev::kSynthGridAuto, st); });
+        if (e != cudaSuccess) return e;
+        lma_dev::SynthArgs d = a;
+        d.U = static_cast<const float2*>(ctx->psi);
+        d.Uh = nullptr;
+        d.Uscale = nullptr;
+        d.tidx = iota;
+        d.alpha = reinterpret_cast<const float2*>(t);
+        d.shift = reinterpret_cast<const int2*>(t + 8 * n_tab);
+        d.L = 1;
+        d.probe_list = iota + p0;
+        d.n_list = p1 - p0;
+        d.n_cfg = 1;
+        d.cfg_base = a.cfg_base + c;
+        d.n_translates = p1 - p0;
+        d.u_slot = 0;
+        d.W = kW;
+        d.cyclic = 0;
+        d.strip = kSynthStrip;
+        if (a.pat) d.pat = a.pat + static_cast<int64_t>(c) * a.n_probes * pat_size;
+        e = counted(ctx, K_SYNTH, static_cast<int64_t>(p1 - p0), st,
+                    [&] { return lma_dev::launch_synth(d, false, mode, lma_dev::kSynthGridAuto, st); });
+        if (e != cudaSuccess) return e;
+      }
+    }
+    return cudaSuccess;
+  };
+  const lma_ctx::SynthTune* tuned = nullptr;
+  for (const auto& tt : ctx->synth_tune)
+    if (tt.key == key) tuned = &tt;
+  const bool want_group = ctx->synth_mode != LMA_SYNTH_GATHER;
   if (tuned || !ctx->autotune || ctx->capturing) {
-    if (tuned)
-      CUDA_TRY(ctx, launch(tuned->rec.strip,
-                           tuned->rec.persistent ? lma_dev::kSynthGridPersistent : lma_dev::kSynthGridPerItem));
-    else
-      CUDA_TRY(ctx, launch(kSynthStrip, lma_dev::kSynthGridAuto));
+    if (ctx->synth_mode == LMA_SYNTH_AUTO && tuned) {
+      const lma_synth_tuning& r = tuned->rec;
+      if (r.grouped && psi_ready(r.group_y)) CUDA_TRY(ctx, grouped(r.group_x, r.group_y));
+      else CUDA_TRY(ctx, gather(r.strip, r.persistent ? lma_dev::kSynthGridPersistent : lma_dev::kSynthGridPerItem));
+    } else if (want_group && admit[0] && psi_ready(shapes[0][1])) {
+      CUDA_TRY(ctx, grouped(shapes[0][0], shapes[0][1]));
+    } else {
+      CUDA_TRY(ctx, gather(kSynthStrip, lma_dev::kSynthGridAuto));
+    }
     return LMA_OK;
   }
   static const int kStrips[3] = {16, 32, 64};
-  lma_ctx::SynthTune t;
-  t.key = key;
-  t.rec = lma_synth_tuning{};
-  t.rec.readout = mode == lma_dev::kReadAnnuli ? 0 : (mode == lma_dev::kReadLabels ? 1 : 2);
-  t.rec.half = half ? 1 : 0;
-  t.rec.n_items = static_cast<int64_t>(listed ? a.n_list : a.n_probes) * a.n_cfg;
-  t.rec.L = a.L;
-  t.rec.window = a.W;
-  cudaEvent_t ev[7];
+  lma_ctx::SynthTune tn;
+  tn.key = key;
+  tn.rec = lma_synth_tuning{};
+  tn.rec.readout = mode == lma_dev::kReadAnnuli ? 0 : (mode == lma_dev::kReadLabels ? 1 : 2);
+  tn.rec.half = half ? 1 : 0;
+  tn.rec.n_items = static_cast<int64_t>(listed ? a.n_list : a.n_probes) * a.n_cfg;
+  tn.rec.L = a.L;
+  tn.rec.window = a.W;
+  std::memcpy(tn.rec.group_shape, shapes, sizeof(shapes));
+  cudaEvent_t ev[9];
   for (auto& e : ev) CUDA_TRY(ctx, cudaEventCreate(&e));
   cudaError_t err = cudaEventRecord(ev[0], st);
   int nv = 0;
-  int var[6];
+  int var[8];
   for (int si = 0; si < 3 && err == cudaSuccess; ++si) {
     if (listed && si != 1) continue;   // a list is walked in order: the strip does not apply
     for (int g = 0; g < 2 && err == cudaSuccess; ++g) {
-      err = launch(kStrips[si], g ? lma_dev::kSynthGridPersistent : lma_dev::kSynthGridPerItem);
+      err = gather(kStrips[si], g ? lma_dev::kSynthGridPersistent : lma_dev::kSynthGridPerItem);
       if (err == cudaSuccess) err = cudaEventRecord(ev[nv + 1], st);
       var[nv++] = 2 * si + g;
     }
+  }
+  for (int i = 0; i < nsh && err == cudaSuccess; ++i) {
+    if (!admit[i] || !psi_ready(shapes[i][1])) continue;
+    err = grouped(shapes[i][0], shapes[i][1]);
+    if (err == cudaSuccess) err = cudaEventRecord(ev[nv + 1], st);
+    var[nv++] = 6 + i;
   }
   if (err == cudaSuccess) err = cudaEventSynchronize(ev[nv]);
   int best = -1;
   for (int i = 0; i < nv && err == cudaSuccess; ++i) {
     float ms = 0.f;
     err = cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
-    t.rec.ms[var[i]] = ms;
-    if (best < 0 || t.rec.ms[var[i]] < t.rec.ms[best]) best = var[i];
+    tn.rec.ms[var[i]] = ms;
+    if (best < 0 || tn.rec.ms[var[i]] < tn.rec.ms[best]) best = var[i];
   }
   for (auto& e : ev) cudaEventDestroy(e);
   CUDA_TRY(ctx, err);
-  t.rec.strip = kStrips[best / 2];
-  t.rec.persistent = best % 2;
-  ctx->synth_tune.push_back(t);
+  if (best >= 6) {
+    tn.rec.grouped = 1;
+    tn.rec.group_x = shapes[best - 6][0];
+    tn.rec.group_y = shapes[best - 6][1];
+    tn.rec.strip = kSynthStrip;
+    tn.rec.persistent = half ? 0 : 1;
+  } else {
+    tn.rec.strip = kStrips[best / 2];
+    tn.rec.persistent = best % 2;
+  }
+  ctx->synth_tune.push_back(tn);
   return LMA_OK;
 }
 
@@ -1277,12 +1427,19 @@ lma_status region_tables_host(lma_basis* b, const lma_region* r, std::vector<int
       lma_status s = coef_set(b, px, py, &cs);
       if (s != LMA_OK) return s;
       const size_t base = (static_cast<size_t>(pb) * r->npx + pa) * L;
-      for (int j = 0; j < L; ++j) {
-        tidx[base + j] = static_cast<int32_t>(translate_index(b, px + cs->odx[j], py + cs->ody[j]));
-        al[2 * (base + j)] = static_cast<float>(cs->alpha[j].real());
-        al[2 * (base + j) + 1] = static_cast<float>(cs->alpha[j].imag());
-        sh[2 * (base + j)] = cs->odx[j] + half;
-        sh[2 * (base + j) + 1] = cs->ody[j] + half;
+      // the probe's entries in ascending translate index: the order in which both synthesis
+      // forms sum them
+      std::vector<std::pair<int32_t, int>> order(L);
+      for (int j = 0; j < L; ++j)
+        order[j] = {static_cast<int32_t>(translate_index(b, px + cs->odx[j], py + cs->ody[j])), j};
+      std::sort(order.begin(), order.end());
+      for (int i = 0; i < L; ++i) {
+        const int j = order[i].second;
+        tidx[base + i] = order[i].first;
+        al[2 * (base + i)] = static_cast<float>(cs->alpha[j].real());
+        al[2 * (base + i) + 1] = static_cast<float>(cs->alpha[j].imag());
+        sh[2 * (base + i)] = cs->odx[j] + half;
+        sh[2 * (base + i) + 1] = cs->ody[j] + half;
       }
     }
   }
@@ -1309,6 +1466,8 @@ lma_status build_region(lma_basis* b, const lma_region* r, cudaStream_t st) {
                              st));
   R.r = *r;
   R.n_probes = np;
+  R.shift_abs = 0;
+  for (int32_t v : sh) R.shift_abs = std::max(R.shift_abs, v < 0 ? -v : v);
   R.h_tidx.swap(tidx);
   b->reg_valid = true;
   return LMA_OK;
@@ -1510,7 +1669,7 @@ lma_status images_work(lma_ctx* ctx, const std::vector<ImageJob>& jobs, const Re
         a.pat_a = ro.pat_a;
         a.pat_b = ro.pat_b;
       }
-      { const lma_status ss_ = synth_launch(ctx, a, half, ro.mode, np * nb, st); if (ss_ != LMA_OK) return ss_; }
+      { const lma_status ss_ = synth_launch(ctx, a, half, ro.mode, np * nb, region_geom(b), st); if (ss_ != LMA_OK) return ss_; }
       if (pattern) {
         const int64_t n = np * ro.pat_size();
         CUDA_TRY(ctx, counted(ctx, K_FIN, n, st, [&] {
@@ -1643,6 +1802,8 @@ void lma_destroy(lma_ctx* ctx) {
   if (ctx->list_slab) cudaFree(ctx->list_slab);
   if (ctx->d_counter) cudaFree(ctx->d_counter);
   if (ctx->gen_scratch) cudaFree(ctx->gen_scratch);
+  if (ctx->psi) cudaFree(ctx->psi);
+  if (ctx->psi_tab) cudaFree(ctx->psi_tab);
   if (ctx->stage) cudaFreeHost(ctx->stage);
   delete ctx;
 }
@@ -2567,7 +2728,7 @@ lma_status lma_image_coherent(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, cons
       a.n_det = n_det;
       a.acc = static_cast<double*>(b->d_acc.p) + static_cast<size_t>(v) * nph * nout;
       a.band_r2 = b->r2max;
-      { const lma_status ss_ = synth_launch(ctx, a, half, lma_dev::kReadAnnuli, np * nb, st); if (ss_ != LMA_OK) return ss_; }
+      { const lma_status ss_ = synth_launch(ctx, a, half, lma_dev::kReadAnnuli, np * nb, region_geom(b), st); if (ss_ != LMA_OK) return ss_; }
     }
   }
   const double* acc = static_cast<const double*>(b->d_acc.p);
@@ -2682,7 +2843,7 @@ lma_status lma_image_partitioned(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, c
       a.n_det = n_det;
       a.acc = static_cast<double*>(b->d_acc.p);
       a.band_r2 = b->r2max;
-      { const lma_status ss_ = synth_launch(ctx, a, half, lma_dev::kReadAnnuli, static_cast<int64_t>(P.probes.size()), st); if (ss_ != LMA_OK) return ss_; }
+      { const lma_status ss_ = synth_launch(ctx, a, half, lma_dev::kReadAnnuli, static_cast<int64_t>(P.probes.size()), SynthGeom{}, st); if (ss_ != LMA_OK) return ss_; }
     }
   }
   const double* acc = static_cast<const double*>(b->d_acc.p);
@@ -2892,6 +3053,20 @@ lma_status lma_set_slice_mode(lma_ctx* ctx, int32_t mode) {
   if (!ctx) return LMA_ERR_INVALID;
   if (mode < LMA_SLICE_AUTO || mode >= lma_dev::kSliceModes) return fail(ctx, LMA_ERR_INVALID, "unknown slice mode %d", mode);
   ctx->forced_mode = mode;
+  return LMA_OK;
+}
+
+lma_status lma_set_synth_mode(lma_ctx* ctx, int32_t mode) {
+  if (!ctx) return LMA_ERR_INVALID;
+  if (mode < LMA_SYNTH_AUTO || mode > LMA_SYNTH_GROUPED) return fail(ctx, LMA_ERR_INVALID, "unknown synthesis form %d", mode);
+  ctx->synth_mode = mode;
+  return LMA_OK;
+}
+
+lma_status lma_set_synth_buffer_limit(lma_ctx* ctx, int64_t bytes) {
+  if (!ctx) return LMA_ERR_INVALID;
+  if (bytes < 0) return fail(ctx, LMA_ERR_INVALID, "negative buffer limit");
+  ctx->psi_max = bytes == 0 ? (int64_t(2) << 30) : bytes;
   return LMA_OK;
 }
 

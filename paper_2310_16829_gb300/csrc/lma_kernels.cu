@@ -2159,6 +2159,197 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
   }
 }
 
+// Step a4 for a group of neighbouring probes. The group's frame is the union of its probe
+// windows: probe q = (qi, qj) of the group has its window at (qi psx, qj psy), and the
+// translate of its entry j sits at that corner plus shift_j. The CTA sorts the group's
+// entries by (translate, frame position, entry) in shared memory (bitonic sort, one entry per
+// thread), merges equal (translate, position) pairs into one union entry u with a coefficient
+// per probe (zero where the probe does not use it) and a mask of the probes that do.
+// Each warp then takes 8 x 8 pixel blocks of the frame (lane (r, c) holds rows r and r + 4,
+// column c): for every union entry whose window meets the block and that a probe covering the
+// block uses, it loads the two pixels once and adds them into the accumulators of those
+// probes (16 probes x 2 pixels per lane), in union order, which for each probe is its
+// ascending translate order. Pixels of a probe's accumulator outside that probe's window are
+// never stored.
+template <bool HALF>
+__global__ void __launch_bounds__(kThreads, 1) k_synth_group(const SynthArgs a, const GroupArgs g) {
+  constexpr int kQ = kGroupMaxProbes, kE = kGroupMaxEntries;
+  static_assert(kE == kThreads, "one group entry per thread");
+  extern __shared__ __align__(16) unsigned char smq[];
+  uint64_t* const keys = reinterpret_cast<uint64_t*>(smq);                     // [kE]
+  float2* const atab = reinterpret_cast<float2*>(keys + kE);                   // [u][q]
+  int2* const upos = reinterpret_cast<int2*>(atab + kE * kQ);                  // frame position of u
+  uint32_t* const umask = reinterpret_cast<uint32_t*>(upos + kE);              // probes using u
+  int* const ut = reinterpret_cast<int*>(umask + kE);                          // translate of u
+  int4* const pinfo = reinterpret_cast<int4*>(ut + kE);                        // probe q: (p, x0, y0)
+  int* const wsum = reinterpret_cast<int*>(pinfo + kQ);                        // first entries per warp
+  const int T = threadIdx.x, lane = T & 31, warp = T >> 5;
+  const int W = a.W;
+  const long long WW = static_cast<long long>(W) * W;
+  const float2* const Uc = HALF ? nullptr : a.U + g.cfg * a.u_slot;
+  const __half2* const Uhc = HALF ? static_cast<const __half2*>(a.Uh) + g.cfg * a.u_slot : nullptr;
+  const float* const Usc = HALF ? a.Uscale + static_cast<size_t>(g.cfg) * a.n_translates : nullptr;
+  const int r8 = lane >> 3, c8 = lane & 7;
+  const int n_groups = g.ngx * g.ngy;
+  const int p_base = g.gb_base * g.gy * a.npx;   // region index of psi's first probe
+  for (int gi = blockIdx.x; gi < n_groups; gi += gridDim.x) {
+    const int gid = probe_of(gi, g.ngx, g.ngy, g.gstrip);
+    const int gl = gid / g.ngx, ga = gid - gl * g.ngx;
+    const int a0 = ga * g.gx, b0 = (g.gb_base + gl) * g.gy;
+    const int nqa = min(g.gx, a.npx - a0), nqb = min(g.gy, a.npy - b0);
+    const int G = nqa * nqb, n_ent = G * a.L;
+    __syncthreads();   // the previous group's reads of the tables are over
+    {
+      uint64_t key = ~0ull;
+      if (T < n_ent) {
+        const int q = T / a.L, j = T - q * a.L;
+        const int qj = q / nqa, qi = q - qj * nqa;
+        const size_t o = (static_cast<size_t>(b0 + qj) * a.npx + a0 + qi) * a.L + j;
+        const int2 sh = a.shift[o];
+        const uint64_t px = static_cast<uint64_t>(qi * g.psx + sh.x + kGroupPosBias);
+        const uint64_t py = static_cast<uint64_t>(qj * g.psy + sh.y + kGroupPosBias);
+        key = (static_cast<uint64_t>(a.tidx[o]) << 34) | (px << 22) | (py << 10) | static_cast<uint64_t>(T);
+      }
+      keys[T] = key;
+      umask[T] = 0u;
+#pragma unroll
+      for (int q = 0; q < kQ; ++q) atab[q * kE + T] = make_float2(0.f, 0.f);
+      if (T < G) {
+        const int qj = T / nqa, qi = T - qj * nqa;
+        pinfo[T] = make_int4((b0 + qj) * a.npx + a0 + qi, qi * g.psx, qj * g.psy, 0);
+      }
+    }
+    __syncthreads();
+    for (int k = 2; k <= kE; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const int l = T ^ j;
+        if (l > T) {
+          const uint64_t x = keys[T], y = keys[l];
+          if ((x > y) == ((T & k) == 0)) {
+            keys[T] = y;
+            keys[l] = x;
+          }
+        }
+        __syncthreads();
+      }
+    // union entries: the first of each run of equal (translate, position) keys
+    const uint64_t kt = keys[T];
+    const bool valid = T < n_ent;
+    const bool first = valid && (T == 0 || (keys[T - 1] >> 10) != (kt >> 10));
+    const uint32_t bal = __ballot_sync(0xffffffffu, first);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, K = 0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) {
+      const int c = wsum[w];
+      before += w < warp ? c : 0;
+      K += c;
+    }
+    if (valid) {
+      const int u = before + __popc(bal & ((1u << lane) - 1u)) - (first ? 0 : 1);
+      const int e = static_cast<int>(kt & 1023u);
+      const int q = e / a.L, j = e - q * a.L;
+      const int t = static_cast<int>(kt >> 34);
+      float2 al = a.alpha[static_cast<size_t>(pinfo[q].x) * a.L + j];
+      if constexpr (HALF) {
+        const float f = Usc[t];
+        al.x *= f;
+        al.y *= f;
+      }
+      atab[u * kQ + q] = al;
+      atomicOr(&umask[u], 1u << q);
+      if (first) {
+        ut[u] = t;
+        upos[u] = make_int2(static_cast<int>((kt >> 22) & 4095u) - kGroupPosBias,
+                            static_cast<int>((kt >> 10) & 4095u) - kGroupPosBias);
+      }
+    }
+    __syncthreads();
+    // ---- the frame in 8 x 8 blocks, one warp per block
+    const int Fx = (nqa - 1) * g.psx + kW, Fy = (nqb - 1) * g.psy + kW;
+    const int nbx = (Fx + 7) >> 3, nblk = nbx * ((Fy + 7) >> 3);
+    for (int bk = warp; bk < nblk; bk += kThreads / 32) {
+      const int by0 = 8 * (bk / nbx), bx0 = 8 * (bk - (bk / nbx) * nbx);
+      uint32_t cov = 0u;   // probes whose windows meet the block
+      for (int q = 0; q < G; ++q) {
+        const int4 pi = pinfo[q];
+        if (bx0 < pi.y + kW && bx0 + 8 > pi.y && by0 < pi.z + kW && by0 + 8 > pi.z) cov |= 1u << q;
+      }
+      if (cov == 0u) continue;
+      float2 acc[kQ][2];
+#pragma unroll
+      for (int q = 0; q < kQ; ++q) acc[q][0] = acc[q][1] = make_float2(0.f, 0.f);
+      for (int u0 = 0; u0 < K; u0 += 4) {
+        // the loads of four union entries, then their products
+        float2 v[4][2];
+        uint32_t m[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+          const int u = u0 + d;
+          m[d] = 0u;
+          v[d][0] = v[d][1] = make_float2(0.f, 0.f);
+          if (u < K) {
+            const int2 P = upos[u];
+            const int xw = bx0 - P.x, yw = by0 - P.y;   // the block's corner in the translate's window
+            if (xw < W && xw + 8 > 0 && yw < W && yw + 8 > 0) m[d] = umask[u] & cov;
+            if (m[d] != 0u) {
+              const int x = xw + c8, y0 = yw + r8;
+              const bool okx = static_cast<unsigned>(x) < static_cast<unsigned>(W);
+              const long long tb = static_cast<long long>(ut[u]) * WW + x;
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int y = y0 + 4 * h;
+                if (okx && static_cast<unsigned>(y) < static_cast<unsigned>(W)) {
+                  if constexpr (HALF)
+                    v[d][h] = __half22float2(Uhc[tb + static_cast<long long>(y) * W]);
+                  else
+                    v[d][h] = Uc[tb + static_cast<long long>(y) * W];
+                }
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+          if (m[d] == 0u) continue;
+          const float2* const ar = atab + (u0 + d) * kQ;
+#pragma unroll
+          for (int q = 0; q < kQ; ++q) {
+            if (m[d] & (1u << q)) {
+              const float2 al = ar[q];
+              acc[q][0] = cfma(acc[q][0], al, v[d][0]);
+              acc[q][1] = cfma(acc[q][1], al, v[d][1]);
+            }
+          }
+        }
+      }
+      // the block's pixels of each covering probe's window
+#pragma unroll
+      for (int q = 0; q < kQ; ++q) {
+        if (cov & (1u << q)) {
+          const int4 pi = pinfo[q];
+          const int lx = bx0 + c8 - pi.y, ly = by0 + r8 - pi.z;
+          float2* const dst = g.psi + static_cast<size_t>(pi.x - p_base) * (kW * kW);
+          if (static_cast<unsigned>(lx) < static_cast<unsigned>(kW)) {
+            if (static_cast<unsigned>(ly) < static_cast<unsigned>(kW)) __stcs(dst + ly * kW + lx, acc[q][0]);
+            if (static_cast<unsigned>(ly + 4) < static_cast<unsigned>(kW)) __stcs(dst + (ly + 4) * kW + lx, acc[q][1]);
+          }
+        }
+      }
+    }
+  }
+}
+
+__global__ void k_identity_tables(int n, int32_t* tidx, float2* alpha, int2* shift) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    tidx[i] = i;
+    alpha[i] = make_float2(1.f, 0.f);
+    shift[i] = make_int2(0, 0);
+  }
+}
+
 __global__ void k_finalize_variants(const double* acc, int64_t n, int n_cfg, int n_var, const double* w,
                                     double* out) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -2479,6 +2670,10 @@ cudaError_t init_device_constants() {
                  k_synth_detect<false, kReadAnnuli, false, 0>, k_synth_detect<false, kReadLabels, false, 0>,
                  k_synth_detect<false, kReadPattern, false, 0>})
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sy)) != cudaSuccess) return e;
+  for (auto f : {k_synth_group<false>, k_synth_group<true>})
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(synth_group_smem_bytes()))) != cudaSuccess)
+      return e;
   return cudaSuccess;
 }
 
@@ -2621,6 +2816,32 @@ cudaError_t launch_synth(const SynthArgs& a, bool half, int mode, int grid_mode,
     return cudaGetLastError();
   }
   table[half ? 1 : 0][mi][a.cyclic ? 1 : 0]<<<grid, kThreads, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+size_t synth_group_smem_bytes() {
+  return static_cast<size_t>(kGroupMaxEntries) * (8 + 8 * kGroupMaxProbes + 8 + 4 + 4) + 16 * kGroupMaxProbes +
+         4 * (kThreads / 32);
+}
+
+cudaError_t launch_synth_group(const SynthArgs& a, const GroupArgs& g, bool half, int grid_mode, cudaStream_t s) {
+  const int n_groups = g.ngx * g.ngy;
+  if (n_groups <= 0) return cudaSuccess;
+  if (a.probe_list || a.cyclic || a.L < 1 || g.gx < 1 || g.gy < 1 || g.gx * g.gy > kGroupMaxProbes ||
+      g.gx * g.gy * a.L > kGroupMaxEntries || (half && a.W != kW) || a.W < 32 || a.W > 256 || !g.psi)
+    return cudaErrorInvalidValue;
+  const int grid = grid_mode == kSynthGridPerItem ? n_groups : (n_groups < sm_count() ? n_groups : sm_count());
+  const size_t sm = synth_group_smem_bytes();
+  if (half)
+    k_synth_group<true><<<grid, kThreads, sm, s>>>(a, g);
+  else
+    k_synth_group<false><<<grid, kThreads, sm, s>>>(a, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_identity_tables(int n, int32_t* tidx, float2* alpha, int2* shift, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_identity_tables<<<(n + 255) / 256, 256, 0, s>>>(n, tidx, alpha, shift);
   return cudaGetLastError();
 }
 

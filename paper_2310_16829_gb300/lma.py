@@ -52,6 +52,9 @@ LMA_SLICE_AUTO = -1
 LMA_SLICE_ONE_PER_ITEM = 0
 LMA_SLICE_PERSISTENT = 1
 LMA_SLICE_DYNAMIC = 2
+LMA_SYNTH_AUTO = -1
+LMA_SYNTH_GATHER = 0
+LMA_SYNTH_GROUPED = 1
 SLICE_MODE_NAMES = {0: "one_per_item", 1: "persistent", 2: "dynamic"}
 
 # every symbol include/lma.h declares (checked by the CPU tests)
@@ -65,6 +68,7 @@ EXPORTS = [
     "lma_profile_enable", "lma_profile_read", "lma_readout_noalloc", "lma_realspace_gain",
     "lma_set_slice_mode", "lma_tuning_read", "lma_partition", "lma_image_partitioned",
     "lma_image_coherent", "lma_select_L", "lma_image_realspace", "lma_selftest_wait", "lma_synth_tuning_read",
+    "lma_set_synth_mode", "lma_set_synth_buffer_limit",
 ]
 
 
@@ -144,14 +148,22 @@ class Tuning(C.Structure):
 
 class SynthTuning(C.Structure):
     _fields_ = [("readout", C.c_int32), ("half", C.c_int32), ("n_items", C.c_int64), ("L", C.c_int32),
-                ("window", C.c_int32), ("strip", C.c_int32), ("persistent", C.c_int32), ("ms", C.c_double * 6)]
+                ("window", C.c_int32), ("strip", C.c_int32), ("persistent", C.c_int32), ("grouped", C.c_int32),
+                ("group_x", C.c_int32), ("group_y", C.c_int32), ("group_shape", (C.c_int32 * 2) * 2),
+                ("ms", C.c_double * 8)]
+
+    def variant_name(self, v: int) -> str:
+        if v < 6:
+            return f"strip{16 << (v // 2)}_{'persistent' if v % 2 else 'per_probe'}"
+        gx, gy = self.group_shape[v - 6][0], self.group_shape[v - 6][1]
+        return f"grouped_{gx}x{gy}"
 
     def as_dict(self):
         return {"readout": ("annuli", "labels", "pattern")[int(self.readout)], "half": bool(self.half),
                 "n_items": int(self.n_items), "L": int(self.L), "window": int(self.window),
-                "strip": int(self.strip), "persistent": bool(self.persistent),
-                "ms": {f"strip{16 << (v // 2)}_{'persistent' if v % 2 else 'per_probe'}": float(self.ms[v])
-                       for v in range(6) if self.ms[v] > 0}}
+                "strip": int(self.strip), "persistent": bool(self.persistent), "grouped": bool(self.grouped),
+                "group": [int(self.group_x), int(self.group_y)] if self.grouped else None,
+                "ms": {self.variant_name(v): float(self.ms[v]) for v in range(8) if self.ms[v] > 0}}
 
 
 class LmaError(RuntimeError):
@@ -194,6 +206,8 @@ _SIGS = {
     "lma_readout_noalloc": (C.c_int32, [_VP, _VP, _VP, C.POINTER(Detector), C.c_int32, C.POINTER(Region),
                                         _VP, _VP]),
     "lma_set_slice_mode": (C.c_int32, [_VP, C.c_int32]),
+    "lma_set_synth_mode": (C.c_int32, [_VP, C.c_int32]),
+    "lma_set_synth_buffer_limit": (C.c_int32, [_VP, C.c_int64]),
     "lma_image_realspace": (C.c_int32, [_VP, _VP, _VP, C.c_int32, C.c_int32, C.POINTER(Detector), C.c_int32,
                                         C.POINTER(Region), C.c_uint32, _VP, _VP]),
     "lma_image_coherent": (C.c_int32, [_VP, _VP, _VP, C.POINTER(Probe), C.POINTER(C.c_double), C.c_int32,
@@ -283,6 +297,14 @@ class Context:
 
     def set_slice_mode(self, mode: int) -> None:
         self.check(self.lib.lma_set_slice_mode(self.h, mode))
+
+    def set_synth_mode(self, mode: int) -> None:
+        """LMA_SYNTH_AUTO, LMA_SYNTH_GATHER or LMA_SYNTH_GROUPED (same readings bit for bit)."""
+        self.check(self.lib.lma_set_synth_mode(self.h, mode))
+
+    def set_synth_buffer_limit(self, nbytes: int) -> None:
+        """Largest probe-wave buffer of the grouped synthesis (0: the default, 2 GiB)."""
+        self.check(self.lib.lma_set_synth_buffer_limit(self.h, nbytes))
 
     def tuning(self) -> list:
         n = C.c_int32()

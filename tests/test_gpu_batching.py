@@ -202,8 +202,13 @@ def test_autotune_times_every_mode_and_keeps_results():
     for sr, w in zip(srecs, ws):
         assert sr["readout"] == "annuli" and not sr["half"] and sr["window"] == w.basis.window
         assert sr["n_items"] == w.region.npx * w.region.npy * len(w.phonons)
-        assert len(sr["ms"]) == 6 and all(v > 0 for v in sr["ms"].values())
-        chosen = f"strip{sr['strip']}_{'persistent' if sr['persistent'] else 'per_probe'}"
+        # six gather variants, and two group shapes where the windows are not periodic
+        periodic = w.grid.nx == w.basis.window == 128 and w.grid.ny == 128
+        assert len(sr["ms"]) == (6 if periodic else 8) and all(v > 0 for v in sr["ms"].values())
+        if sr["grouped"]:
+            chosen = f"grouped_{sr['group'][0]}x{sr['group'][1]}"
+        else:
+            chosen = f"strip{sr['strip']}_{'persistent' if sr['persistent'] else 'per_probe'}"
         assert chosen == min(sr["ms"], key=sr["ms"].get)
     # a second tuned call reuses the choices, with the same bits
     again = [np.empty_like(p) for p in plain]
