@@ -932,13 +932,16 @@ def main():
                 "share_of_step": sl["total_ms"] / max(1e-9, sum(v["total_ms"] for v in prof.values() if isinstance(v, dict))),
                 "launch_ms": slice_ms}
     syn = prof["synth"]
-    synth_ms = syn["total_ms"] / max(1, syn["launches"])
+    # the synthesis of one step: the grouped form is a group launch and a detection launch per
+    # configuration, the gather one launch for all configurations
+    synth_ms = syn["total_ms"] / args.steps
     u_bytes = basis.info().exit_wave_bytes
     n_translates = int(basis.info().n_translates)
     kernels = {k: {"launches_per_step": v["launches"] / args.steps,
-                   "ms_per_launch": v["total_ms"] / max(1, v["launches"])} for k, v in prof.items()
+                   "ms_per_launch": v["total_ms"] / max(1, v["launches"]),
+                   "ms_per_step": v["total_ms"] / args.steps} for k, v in prof.items()
                if isinstance(v, dict)}
-    # one synthesis launch reads the exit-wave store of every configuration once
+    # the synthesis of a step reads the exit-wave store of every configuration once
     kernels["synth"]["exit_wave_store_GBps"] = (u_bytes * len(w.phonons) / (synth_ms / 1e3) / 1e9
                                                 if synth_ms else None)
 

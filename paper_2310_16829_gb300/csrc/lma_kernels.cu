@@ -73,6 +73,12 @@ __device__ __forceinline__ float2 cfma(float2 acc, float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
 }
 
+// cfma with the coefficient given as (a.x, a.x, -a.y, a.y): the same four FMAs in the same
+// order, as two packed FP32 instructions
+__device__ __forceinline__ float2 cfma2(float2 acc, float4 a, float2 b) {
+  return __ffma2_rn(make_float2(a.x, a.y), b, __ffma2_rn(make_float2(a.z, a.w), make_float2(b.y, b.x), acc));
+}
+
 __host__ __device__ constexpr int brev5(int k) {
   return ((k & 1) << 4) | ((k & 2) << 2) | (k & 4) | ((k & 8) >> 2) | ((k & 16) >> 4);
 }
@@ -2177,11 +2183,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_group(const SynthArgs a, 
   static_assert(kE == kThreads, "one group entry per thread");
   extern __shared__ __align__(16) unsigned char smq[];
   uint64_t* const keys = reinterpret_cast<uint64_t*>(smq);                     // [kE]
-  float2* const atab = reinterpret_cast<float2*>(keys + kE);                   // [u][q]
-  int2* const upos = reinterpret_cast<int2*>(atab + kE * kQ);                  // frame position of u
-  uint32_t* const umask = reinterpret_cast<uint32_t*>(upos + kE);              // probes using u
-  int* const ut = reinterpret_cast<int*>(umask + kE);                          // translate of u
-  int4* const pinfo = reinterpret_cast<int4*>(ut + kE);                        // probe q: (p, x0, y0)
+  float4* const atab = reinterpret_cast<float4*>(keys + kE);                   // [u][q]: (ax, ax, -ay, ay)
+  int4* const uent = reinterpret_cast<int4*>(atab + kE * kQ);                  // u: (x, y, probe mask, translate)
+  int4* const pinfo = reinterpret_cast<int4*>(uent + kE);                      // probe q: (p, x0, y0)
   int* const wsum = reinterpret_cast<int*>(pinfo + kQ);                        // first entries per warp
   const int T = threadIdx.x, lane = T & 31, warp = T >> 5;
   const int W = a.W;
@@ -2211,9 +2215,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_group(const SynthArgs a, 
         key = (static_cast<uint64_t>(a.tidx[o]) << 34) | (px << 22) | (py << 10) | static_cast<uint64_t>(T);
       }
       keys[T] = key;
-      umask[T] = 0u;
+      uent[T].z = 0;
 #pragma unroll
-      for (int q = 0; q < kQ; ++q) atab[q * kE + T] = make_float2(0.f, 0.f);
+      for (int q = 0; q < kQ; ++q) atab[q * kE + T] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (T < G) {
         const int qj = T / nqa, qi = T - qj * nqa;
         pinfo[T] = make_int4((b0 + qj) * a.npx + a0 + qi, qi * g.psx, qj * g.psy, 0);
@@ -2257,12 +2261,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_group(const SynthArgs a, 
         al.x *= f;
         al.y *= f;
       }
-      atab[u * kQ + q] = al;
-      atomicOr(&umask[u], 1u << q);
+      atab[u * kQ + q] = make_float4(al.x, al.x, -al.y, al.y);
+      atomicOr(&uent[u].z, 1 << q);
       if (first) {
-        ut[u] = t;
-        upos[u] = make_int2(static_cast<int>((kt >> 22) & 4095u) - kGroupPosBias,
-                            static_cast<int>((kt >> 10) & 4095u) - kGroupPosBias);
+        uent[u].x = static_cast<int>((kt >> 22) & 4095u) - kGroupPosBias;
+        uent[u].y = static_cast<int>((kt >> 10) & 4095u) - kGroupPosBias;
+        uent[u].w = t;
       }
     }
     __syncthreads();
@@ -2280,23 +2284,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_group(const SynthArgs a, 
       float2 acc[kQ][2];
 #pragma unroll
       for (int q = 0; q < kQ; ++q) acc[q][0] = acc[q][1] = make_float2(0.f, 0.f);
-      for (int u0 = 0; u0 < K; u0 += 4) {
-        // the loads of four union entries, then their products
-        float2 v[4][2];
-        uint32_t m[4];
+      // loads of four union entries (zero outside the translate's window; none for an entry
+      // that no covering probe uses or whose window misses the block)
+      auto fetch = [&](int u0, float2 (&v)[4][2], uint32_t (&m)[4]) {
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
           const int u = u0 + d;
           m[d] = 0u;
           v[d][0] = v[d][1] = make_float2(0.f, 0.f);
           if (u < K) {
-            const int2 P = upos[u];
-            const int xw = bx0 - P.x, yw = by0 - P.y;   // the block's corner in the translate's window
-            if (xw < W && xw + 8 > 0 && yw < W && yw + 8 > 0) m[d] = umask[u] & cov;
+            const int4 E = uent[u];
+            const int xw = bx0 - E.x, yw = by0 - E.y;   // the block's corner in the translate's window
+            if (xw < W && xw + 8 > 0 && yw < W && yw + 8 > 0) m[d] = static_cast<uint32_t>(E.z) & cov;
             if (m[d] != 0u) {
               const int x = xw + c8, y0 = yw + r8;
               const bool okx = static_cast<unsigned>(x) < static_cast<unsigned>(W);
-              const long long tb = static_cast<long long>(ut[u]) * WW + x;
+              const long long tb = static_cast<long long>(E.w) * WW + x;
 #pragma unroll
               for (int h = 0; h < 2; ++h) {
                 const int y = y0 + 4 * h;
@@ -2310,19 +2313,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_group(const SynthArgs a, 
             }
           }
         }
+      };
+      // their products into the accumulators of the probes that use them
+      auto consume = [&](int u0, const float2 (&v)[4][2], const uint32_t (&m)[4]) {
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
           if (m[d] == 0u) continue;
-          const float2* const ar = atab + (u0 + d) * kQ;
+          const float4* const ar = atab + (u0 + d) * kQ;
 #pragma unroll
           for (int q = 0; q < kQ; ++q) {
             if (m[d] & (1u << q)) {
-              const float2 al = ar[q];
-              acc[q][0] = cfma(acc[q][0], al, v[d][0]);
-              acc[q][1] = cfma(acc[q][1], al, v[d][1]);
+              const float4 al = ar[q];
+              acc[q][0] = cfma2(acc[q][0], al, v[d][0]);
+              acc[q][1] = cfma2(acc[q][1], al, v[d][1]);
             }
           }
         }
+      };
+      // two sets of loads in flight: the next four entries are fetched before the current
+      // four are consumed
+      float2 va[4][2], vb[4][2];
+      uint32_t ma[4], mb[4];
+      fetch(0, va, ma);
+      for (int u0 = 0; u0 < K; u0 += 8) {
+        fetch(u0 + 4, vb, mb);
+        consume(u0, va, ma);
+        fetch(u0 + 8, va, ma);
+        consume(u0 + 4, vb, mb);
       }
       // the block's pixels of each covering probe's window
 #pragma unroll
@@ -2820,7 +2837,7 @@ cudaError_t launch_synth(const SynthArgs& a, bool half, int mode, int grid_mode,
 }
 
 size_t synth_group_smem_bytes() {
-  return static_cast<size_t>(kGroupMaxEntries) * (8 + 8 * kGroupMaxProbes + 8 + 4 + 4) + 16 * kGroupMaxProbes +
+  return static_cast<size_t>(kGroupMaxEntries) * (8 + 16 * kGroupMaxProbes + 16) + 16 * kGroupMaxProbes +
          4 * (kThreads / 32);
 }
 
