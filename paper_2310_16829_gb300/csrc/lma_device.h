@@ -161,7 +161,7 @@ cudaError_t launch_synth(const SynthArgs& a, bool half, int mode, int grid_mode,
 // with tables sorted that way, so a detection pass over psi (launch_synth with the identity
 // tables below) gives the same bits as the per-probe gather.
 struct GroupArgs {
-  int gx, gy;                  // probes per group along x and y: gx gy <= 16, gx gy L <= 512
+  int gx, gy;                  // probes per group along x and y: gx gy <= 4, gx gy L <= 512
   int psx, psy;                // probe spacing (pixels): offset between neighbouring probe windows
   int ngx, ngy;                // groups per region row; group rows of this launch
   int gb_base;                 // first group row of this launch
@@ -170,6 +170,7 @@ struct GroupArgs {
   float2* psi;                 // probe waves of the launch's probe rows, [probe - gb_base gy npx][kW][kW]
 };
 constexpr int kGroupMaxProbes = 16, kGroupMaxEntries = 512;
+constexpr int kGroupDenseProbes = 4;  // probes per group of the kernel's accumulators (gx gy <= 4)
 constexpr int kGroupPosBias = 2048;   // translate placements in a group's frame lie in [-2048, 2048)
 size_t synth_group_smem_bytes();
 // grid_mode as for launch_synth (kSynthGridAuto: persistent)

@@ -1013,12 +1013,12 @@ SynthGeom region_geom(const lma_basis* b) {
   return g;
 }
 
-// The two group shapes timed for L input waves per probe: up to 16 probes and 512
+// The two group shapes timed for L input waves per probe: up to 4 probes and 512
 // (probe, wave) entries per group; 0 when no group of two probes fits.
 int group_shapes(int L, int shapes[2][2]) {
-  const int gmax = std::min(lma_dev::kGroupMaxProbes, lma_dev::kGroupMaxEntries / std::max(1, L));
-  static const int cand[4][2][2] = {{{4, 4}, {8, 2}}, {{4, 2}, {8, 1}}, {{2, 2}, {4, 1}}, {{2, 1}, {1, 2}}};
-  const int k = gmax >= 16 ? 0 : gmax >= 8 ? 1 : gmax >= 4 ? 2 : gmax >= 2 ? 3 : -1;
+  const int gmax = std::min(lma_dev::kGroupDenseProbes, lma_dev::kGroupMaxEntries / std::max(1, L));
+  static const int cand[2][2][2] = {{{2, 2}, {4, 1}}, {{2, 1}, {1, 2}}};
+  const int k = gmax >= 4 ? 0 : gmax >= 2 ? 1 : -1;
   if (k < 0) return 0;
   std::memcpy(shapes, cand[k], sizeof(cand[k]));
   return 2;

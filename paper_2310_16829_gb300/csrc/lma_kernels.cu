@@ -2171,15 +2171,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
 // entries by (translate, frame position, entry) in shared memory (bitonic sort, one entry per
 // thread), merges equal (translate, position) pairs into one union entry u with a coefficient
 // per probe (zero where the probe does not use it) and a mask of the probes that do.
-// Each warp then takes 8 x 8 pixel blocks of the frame (lane (r, c) holds rows r and r + 4,
-// column c): for every union entry whose window meets the block and that a probe covering the
-// block uses, it loads the two pixels once and adds them into the accumulators of those
-// probes (16 probes x 2 pixels per lane), in union order, which for each probe is its
-// ascending translate order. Pixels of a probe's accumulator outside that probe's window are
-// never stored.
+// Each warp then takes blocks of 8 x 16 pixels of the frame: for every union entry whose
+// window meets the block and that a probe covering the block uses, it loads the block's
+// pixels once and adds them into the accumulators of all the group's probes (up to 4 probes
+// x 4 pixels per lane), in union order, which for each probe is its ascending translate order;
+// a zero coefficient leaves a sum unchanged. Pixels of a probe's accumulator outside that
+// probe's window are never stored. The products are dense over the group (no per-probe
+// branch): with groups of 16 probes and a branch per probe and entry the kernel spent most
+// of its time on branches and instruction fetch.
 template <bool HALF>
 __global__ void __launch_bounds__(kThreads, 1) k_synth_group(const SynthArgs a, const GroupArgs g) {
   constexpr int kQ = kGroupMaxProbes, kE = kGroupMaxEntries;
+  constexpr int kGQ = kGroupDenseProbes;   // accumulators per lane: every probe of the group
   static_assert(kE == kThreads, "one group entry per thread");
   extern __shared__ __align__(16) unsigned char smq[];
   uint64_t* const keys = reinterpret_cast<uint64_t*>(smq);                     // [kE]
@@ -2193,7 +2196,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_group(const SynthArgs a, 
   const float2* const Uc = HALF ? nullptr : a.U + g.cfg * a.u_slot;
   const __half2* const Uhc = HALF ? static_cast<const __half2*>(a.Uh) + g.cfg * a.u_slot : nullptr;
   const float* const Usc = HALF ? a.Uscale + static_cast<size_t>(g.cfg) * a.n_translates : nullptr;
-  const int r8 = lane >> 3, c8 = lane & 7;
+  const int r2 = lane >> 4, c16 = lane & 15;
   const int n_groups = g.ngx * g.ngy;
   const int p_base = g.gb_base * g.gy * a.npx;   // region index of psi's first probe
   for (int gi = blockIdx.x; gi < n_groups; gi += gridDim.x) {
@@ -2270,39 +2273,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_group(const SynthArgs a, 
       }
     }
     __syncthreads();
-    // ---- the frame in 8 x 8 blocks, one warp per block
+    // ---- the frame in blocks of 8 rows x 16 columns, one warp per block; lane (r, c) holds
+    // rows r + 2 h (h < 4) of column c, for each of the group's (up to 4) probes
     const int Fx = (nqa - 1) * g.psx + kW, Fy = (nqb - 1) * g.psy + kW;
-    const int nbx = (Fx + 7) >> 3, nblk = nbx * ((Fy + 7) >> 3);
+    const int nbx = (Fx + 15) >> 4, nblk = nbx * ((Fy + 7) >> 3);
     for (int bk = warp; bk < nblk; bk += kThreads / 32) {
-      const int by0 = 8 * (bk / nbx), bx0 = 8 * (bk - (bk / nbx) * nbx);
+      const int by0 = 8 * (bk / nbx), bx0 = 16 * (bk - (bk / nbx) * nbx);
       uint32_t cov = 0u;   // probes whose windows meet the block
       for (int q = 0; q < G; ++q) {
         const int4 pi = pinfo[q];
-        if (bx0 < pi.y + kW && bx0 + 8 > pi.y && by0 < pi.z + kW && by0 + 8 > pi.z) cov |= 1u << q;
+        if (bx0 < pi.y + kW && bx0 + 16 > pi.y && by0 < pi.z + kW && by0 + 8 > pi.z) cov |= 1u << q;
       }
       if (cov == 0u) continue;
-      float2 acc[kQ][2];
+      float2 acc[kGQ][4];
 #pragma unroll
-      for (int q = 0; q < kQ; ++q) acc[q][0] = acc[q][1] = make_float2(0.f, 0.f);
-      // loads of four union entries (zero outside the translate's window; none for an entry
+      for (int q = 0; q < kGQ; ++q)
+#pragma unroll
+        for (int h = 0; h < 4; ++h) acc[q][h] = make_float2(0.f, 0.f);
+      // loads of two union entries (zero outside the translate's window; none for an entry
       // that no covering probe uses or whose window misses the block)
-      auto fetch = [&](int u0, float2 (&v)[4][2], uint32_t (&m)[4]) {
+      auto fetch = [&](int u0, float2 (&v)[2][4], bool (&live)[2]) {
 #pragma unroll
-        for (int d = 0; d < 4; ++d) {
+        for (int d = 0; d < 2; ++d) {
           const int u = u0 + d;
-          m[d] = 0u;
-          v[d][0] = v[d][1] = make_float2(0.f, 0.f);
+          live[d] = false;
+#pragma unroll
+          for (int h = 0; h < 4; ++h) v[d][h] = make_float2(0.f, 0.f);
           if (u < K) {
             const int4 E = uent[u];
             const int xw = bx0 - E.x, yw = by0 - E.y;   // the block's corner in the translate's window
-            if (xw < W && xw + 8 > 0 && yw < W && yw + 8 > 0) m[d] = static_cast<uint32_t>(E.z) & cov;
-            if (m[d] != 0u) {
-              const int x = xw + c8, y0 = yw + r8;
+            live[d] = xw < W && xw + 16 > 0 && yw < W && yw + 8 > 0 && (static_cast<uint32_t>(E.z) & cov) != 0u;
+            if (live[d]) {
+              const int x = xw + c16, y0 = yw + r2;
               const bool okx = static_cast<unsigned>(x) < static_cast<unsigned>(W);
               const long long tb = static_cast<long long>(E.w) * WW + x;
 #pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const int y = y0 + 4 * h;
+              for (int h = 0; h < 4; ++h) {
+                const int y = y0 + 2 * h;
                 if (okx && static_cast<unsigned>(y) < static_cast<unsigned>(W)) {
                   if constexpr (HALF)
                     v[d][h] = __half22float2(Uhc[tb + static_cast<long long>(y) * W]);
@@ -2314,43 +2321,45 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_group(const SynthArgs a, 
           }
         }
       };
-      // their products into the accumulators of the probes that use them
-      auto consume = [&](int u0, const float2 (&v)[4][2], const uint32_t (&m)[4]) {
+      // their products into every probe's accumulator (a probe that does not use an entry
+      // has a zero coefficient, which leaves its sums unchanged)
+      auto consume = [&](int u0, const float2 (&v)[2][4], const bool (&live)[2]) {
 #pragma unroll
-        for (int d = 0; d < 4; ++d) {
-          if (m[d] == 0u) continue;
+        for (int d = 0; d < 2; ++d) {
+          if (!live[d]) continue;
           const float4* const ar = atab + (u0 + d) * kQ;
+          float4 al[kGQ];
 #pragma unroll
-          for (int q = 0; q < kQ; ++q) {
-            if (m[d] & (1u << q)) {
-              const float4 al = ar[q];
-              acc[q][0] = cfma2(acc[q][0], al, v[d][0]);
-              acc[q][1] = cfma2(acc[q][1], al, v[d][1]);
-            }
-          }
+          for (int q = 0; q < kGQ; ++q) al[q] = ar[q];
+#pragma unroll
+          for (int q = 0; q < kGQ; ++q)
+#pragma unroll
+            for (int h = 0; h < 4; ++h) acc[q][h] = cfma2(acc[q][h], al[q], v[d][h]);
         }
       };
-      // two sets of loads in flight: the next four entries are fetched before the current
-      // four are consumed
-      float2 va[4][2], vb[4][2];
-      uint32_t ma[4], mb[4];
-      fetch(0, va, ma);
-      for (int u0 = 0; u0 < K; u0 += 8) {
-        fetch(u0 + 4, vb, mb);
-        consume(u0, va, ma);
-        fetch(u0 + 8, va, ma);
-        consume(u0 + 4, vb, mb);
+      // two sets of loads in flight: the next two entries are fetched before the current two
+      // are consumed
+      float2 va[2][4], vb[2][4];
+      bool la[2], lb[2];
+      fetch(0, va, la);
+      for (int u0 = 0; u0 < K; u0 += 4) {
+        fetch(u0 + 2, vb, lb);
+        consume(u0, va, la);
+        fetch(u0 + 4, va, la);
+        consume(u0 + 2, vb, lb);
       }
       // the block's pixels of each covering probe's window
 #pragma unroll
-      for (int q = 0; q < kQ; ++q) {
+      for (int q = 0; q < kGQ; ++q) {
         if (cov & (1u << q)) {
           const int4 pi = pinfo[q];
-          const int lx = bx0 + c8 - pi.y, ly = by0 + r8 - pi.z;
+          const int lx = bx0 + c16 - pi.y, ly = by0 + r2 - pi.z;
           float2* const dst = g.psi + static_cast<size_t>(pi.x - p_base) * (kW * kW);
           if (static_cast<unsigned>(lx) < static_cast<unsigned>(kW)) {
-            if (static_cast<unsigned>(ly) < static_cast<unsigned>(kW)) __stcs(dst + ly * kW + lx, acc[q][0]);
-            if (static_cast<unsigned>(ly + 4) < static_cast<unsigned>(kW)) __stcs(dst + (ly + 4) * kW + lx, acc[q][1]);
+#pragma unroll
+            for (int h = 0; h < 4; ++h)
+              if (static_cast<unsigned>(ly + 2 * h) < static_cast<unsigned>(kW))
+                __stcs(dst + (ly + 2 * h) * kW + lx, acc[q][h]);
           }
         }
       }
@@ -2844,7 +2853,7 @@ size_t synth_group_smem_bytes() {
 cudaError_t launch_synth_group(const SynthArgs& a, const GroupArgs& g, bool half, int grid_mode, cudaStream_t s) {
   const int n_groups = g.ngx * g.ngy;
   if (n_groups <= 0) return cudaSuccess;
-  if (a.probe_list || a.cyclic || a.L < 1 || g.gx < 1 || g.gy < 1 || g.gx * g.gy > kGroupMaxProbes ||
+  if (a.probe_list || a.cyclic || a.L < 1 || g.gx < 1 || g.gy < 1 || g.gx * g.gy > kGroupDenseProbes ||
       g.gx * g.gy * a.L > kGroupMaxEntries || (half && a.W != kW) || a.W < 32 || a.W > 256 || !g.psi)
     return cudaErrorInvalidValue;
   const int grid = grid_mode == kSynthGridPerItem ? n_groups : (n_groups < sm_count() ? n_groups : sm_count());
