@@ -511,14 +511,16 @@ def max_over_ranks(total_ms: float, world: int, dist=None, device: str = "cuda")
     return total_ms
 
 
-def profile_case(precision: str = "c64", window: int = 128) -> None:
+def profile_case(precision: str = "c64", window: int = 128, synth: str = "gather") -> None:
     """The benchmark workload with one configuration, imaged twice with RECOMPUTE, in the
     given precision (c64, fp16_store or mixed: the tensor-core slice kernel k_slice_tc).
     window = 64 or 256: the ABO3 256^2 specimen (5 x 5 cells, 20 slices, 4096 translates) with
     that propagation window instead (k_slice_64 or k_slice_256; store 0.13 or 2.1 GB).
 
-    Launch order per pass: k_potential, k_slice (or k_slice_tc), k_synth_detect, k_finalize.
-    Device footprint about 2.5 GB (exit waves 2.15 GB, padded transmission 164 MB).
+    Launch order per pass: k_potential, k_slice (or k_slice_tc), k_synth_detect, k_finalize;
+    with synth = "grouped", k_synth_group and then k_synth_detect over its probe waves.
+    Device footprint about 2.5 GB (exit waves 2.15 GB, padded transmission 164 MB), and with
+    the grouped synthesis the probe waves (2.15 GB).
     """
     import torch
     from paper_2310_16829_gb300 import lma
@@ -530,6 +532,7 @@ def profile_case(precision: str = "c64", window: int = 128) -> None:
     prec = {"c64": WL.PREC_C64, "fp16_store": WL.PREC_FP16_STORE, "mixed": WL.PREC_MIXED}[precision]
     w = dataclasses.replace(w, basis=dataclasses.replace(w.basis, precision=prec))
     ctx = lma.Context(0)
+    ctx.set_synth_mode(lma.LMA_SYNTH_GROUPED if synth == "grouped" else lma.LMA_SYNTH_GATHER)
     spec = lma.Specimen(ctx, w.grid, w.potential, w.phonons)
     basis = lma.Basis(ctx, spec, w.probe, w.basis)
     out = torch.empty((1, w.region.npy, w.region.npx), dtype=torch.float64, device="cuda")
@@ -601,6 +604,8 @@ def main():
                     help="precision of --profile-case")
     ap.add_argument("--profile-window", type=int, default=128, choices=[64, 128, 256],
                     help="propagation window of --profile-case (64 and 256 on a 256^2 specimen)")
+    ap.add_argument("--profile-synth", default="gather", choices=["gather", "grouped"],
+                    help="synthesis form of --profile-case")
     ap.add_argument("--profile-case-realspace", type=int, default=0, metavar="K",
                     help="one configuration imaged twice with the K x K real-space step (for ncu)")
     ap.add_argument("--approx-curves", action="store_true",
@@ -610,7 +615,7 @@ def main():
 
     w = WL.perovskite_workload()
     if args.profile_case:
-        profile_case(args.profile_precision, args.profile_window)
+        profile_case(args.profile_precision, args.profile_window, args.profile_synth)
         return
     if args.approx_curves:
         approx_curves()

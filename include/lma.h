@@ -554,10 +554,9 @@ typedef struct {
 /* How the synthesis (step a4) forms each probe's wave Psi_p = sum_j alpha_j U_{i_j}.
  * Both forms sum each probe's terms in ascending translate index and give the same readings
  * bit for bit. */
-#define LMA_SYNTH_AUTO -1     /* the tuned form of the launch shape, else grouped where the
-                                 launch admits it (a whole region, non-periodic windows) */
+#define LMA_SYNTH_AUTO -1     /* the tuned form of the launch shape, else the gather */
 #define LMA_SYNTH_GATHER 0    /* one CTA per probe gathers its L windows and detects */
-#define LMA_SYNTH_GROUPED 1   /* one CTA per group of up to 16 neighbouring probes loads each
+#define LMA_SYNTH_GROUPED 1   /* one CTA per group of up to 4 neighbouring probes loads each
                                  exit-wave element once for all of them and writes their waves
                                  to a device buffer (probes x 128 KiB, allocated by the
                                  context); a second pass detects; falls back to the gather

@@ -1,5 +1,5 @@
 """Grouped synthesis (step a4, Sec. 4.2.2): Psi_p = sum_j alpha_j U_{i_j} for groups of up to
-16 neighbouring probes, each exit-wave element loaded once for all the group's probes that use
+4 neighbouring probes, each exit-wave element loaded once for all the group's probes that use
 it, then a detection pass over the probe waves. Both forms sum every probe's terms in ascending
 translate index, so the grouped form gives the readings of the per-probe gather bit for bit:
 annuli (2D), rings (3D), patterns (4D), the FP16 store, windows W = 64 and 256, ragged groups at
@@ -94,8 +94,7 @@ def test_grouped_chunks_of_group_rows_equal_one_launch(ctx):
 
 
 def test_grouped_image_matches_oracle(ctx):
-    """The grouped form against the FP64 oracle on a ragged region that wraps around the cell
-    (the default form of every other image test as well)."""
+    """The grouped form against the FP64 oracle on a ragged region that wraps around the cell."""
     w = WL.perovskite_workload(cells=5, nx=256, n_slices=6, n_phonons=2, seed_base=5400)
     r = WL.Region(240, 230, 7, 6, (4, 4))
     spec, basis = _objects(ctx, w)
