@@ -1413,6 +1413,17 @@ lma_status ensure_batch(lma_basis* b, lma_specimen* sp, int phi0, int nb, const 
 
 // Probe tables of a region on the host: for probe p = b * npx + a and j < L, the translate
 // index of its j-th input wave, its coefficient (complex64) and its window placement.
+// A probe's table entries in ascending translate index (translate, index into the coefficient
+// set): the order in which both synthesis forms sum them. Every table of per-probe coefficients
+// (the region's, the coherence variants') follows it.
+void entry_order(const lma_basis* b, int px, int py, const CoefSet& cs, std::vector<std::pair<int32_t, int>>& order) {
+  const int L = b->desc.L;
+  order.resize(L);
+  for (int j = 0; j < L; ++j)
+    order[j] = {static_cast<int32_t>(translate_index(b, px + cs.odx[j], py + cs.ody[j])), j};
+  std::sort(order.begin(), order.end());
+}
+
 lma_status region_tables_host(lma_basis* b, const lma_region* r, std::vector<int32_t>& tidx,
                               std::vector<float>& al, std::vector<int32_t>& sh) {
   const int L = b->desc.L;
@@ -1429,12 +1440,8 @@ lma_status region_tables_host(lma_basis* b, const lma_region* r, std::vector<int
       lma_status s = coef_set(b, px, py, &cs);
       if (s != LMA_OK) return s;
       const size_t base = (static_cast<size_t>(pb) * r->npx + pa) * L;
-      // the probe's entries in ascending translate index: the order in which both synthesis
-      // forms sum them
-      std::vector<std::pair<int32_t, int>> order(L);
-      for (int j = 0; j < L; ++j)
-        order[j] = {static_cast<int32_t>(translate_index(b, px + cs->odx[j], py + cs->ody[j])), j};
-      std::sort(order.begin(), order.end());
+      std::vector<std::pair<int32_t, int>> order;
+      entry_order(b, px, py, *cs, order);
       for (int i = 0; i < L; ++i) {
         const int j = order[i].second;
         tidx[base + i] = order[i].first;
@@ -2662,6 +2669,7 @@ lma_status lma_image_coherent(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, cons
   const size_t tab_floats = static_cast<size_t>(n_var) * np * L * 2;
   if (!b->d_var.p || key != b->var_key) {
     std::vector<float> tab(tab_floats + 2 * static_cast<size_t>(n_var), 0.f);
+    std::vector<std::pair<int32_t, int>> order;
     for (int v = 0; v < n_var; ++v) {
       std::vector<cd> psi0;
       probe_at_origin(b, variants[v], psi0);
@@ -2678,11 +2686,13 @@ lma_status lma_image_coherent(lma_ctx* ctx, lma_specimen* sp, lma_basis* b, cons
             if ((s = solve_set_for(b, psi0, cs)) != LMA_OK) return s;
             it = sets.emplace(k, std::move(cs)).first;
           }
-          // same translate order as the region tables (nearest() is deterministic)
+          // the entry order of the region tables (nearest() is deterministic)
           const size_t base = ((static_cast<size_t>(v) * np) + static_cast<size_t>(pb) * region->npx + pa) * L;
-          for (int j = 0; j < L; ++j) {
-            tab[2 * (base + j)] = static_cast<float>(it->second.alpha[j].real());
-            tab[2 * (base + j) + 1] = static_cast<float>(it->second.alpha[j].imag());
+          entry_order(b, px, py, it->second, order);
+          for (int i = 0; i < L; ++i) {
+            const int j = order[i].second;
+            tab[2 * (base + i)] = static_cast<float>(it->second.alpha[j].real());
+            tab[2 * (base + i) + 1] = static_cast<float>(it->second.alpha[j].imag());
           }
         }
     }
