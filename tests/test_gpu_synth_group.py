@@ -41,7 +41,8 @@ def _objects(ctx, w):
     return spec, lma.Basis(ctx, spec, w.probe, w.basis)
 
 
-@pytest.mark.parametrize("case", ["w128_ragged", "w128_spacing8_wrap", "w64", "w256", "fp16_store", "L12"])
+@pytest.mark.parametrize("case", ["w128_ragged", "w128_spacing8_wrap", "spacing_3_5", "case2_spacing2", "w64", "w256",
+                                  "fp16_store", "L12", "L64"])
 def test_grouped_equals_gather_bitwise(ctx, case):
     w = WL.perovskite_workload(cells=5, nx=256, n_slices=6, n_phonons=2, seed_base=5100)
     region = WL.Region(3, 5, 37, 23, (4, 4))            # 37 x 23 probes: ragged groups on two sides
@@ -54,8 +55,14 @@ def test_grouped_equals_gather_bitwise(ctx, case):
         region = WL.Region(40, 60, 13, 10, (4, 4))
     elif case == "fp16_store":
         w = dataclasses.replace(w, basis=dataclasses.replace(w.basis, precision=WL.PREC_FP16_STORE))
+    elif case == "spacing_3_5":
+        region = WL.Region(7, 2, 11, 9, (3, 5))         # many coefficient sets, odd placements
+    elif case == "case2_spacing2":
+        region = WL.Region(0, 0, 18, 14, (2, 2))        # P = c R (Case 2): four coefficient sets
     elif case == "L12":
         w = dataclasses.replace(w, basis=dataclasses.replace(w.basis, L=12))
+    elif case == "L64":
+        w = dataclasses.replace(w, basis=dataclasses.replace(w.basis, L=64))   # groups of 4 x 64 entries
     spec, basis = _objects(ctx, w)
     dets = [WL.Detector(0.0, 0.02), WL.Detector(0.03, 0.06), WL.Detector(0.07, 0.2)]
     g, q = _both(ctx, lambda: basis.image(dets, region, recompute=True))
