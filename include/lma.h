@@ -79,9 +79,10 @@ typedef int32_t lma_status;
 #define LMA_IMAGE_RECOMPUTE 1u /* treat every stored exit wave as stale (full path) */
 #define LMA_MAX_RINGS 256      /* rings of one 3D STEM image */
 #define LMA_IMAGE_GRAPH 2u     /* lma_image_many: replay the device work as one CUDA graph */
-#define LMA_IMAGE_AUTOTUNE 4u  /* time every slice launch mode, and every synthesis strip width and
-                                  grid, on this call's first launch of each shape and keep the
-                                  fastest for that shape (lma_tuning_read, lma_synth_tuning_read) */
+#define LMA_IMAGE_AUTOTUNE 4u  /* time every slice launch mode, and every synthesis form (gather
+                                  strip width and grid, grouped shapes), on this call's first
+                                  launch of each shape and keep the fastest for that shape
+                                  (lma_tuning_read, lma_synth_tuning_read) */
 
 /* Partition strategies of a probe region (Sec. 4.2.4). */
 #define LMA_PART_ROWS 0                    /* row by row */

@@ -169,8 +169,8 @@ struct GroupArgs {
   int cfg;                     // store slot read
   float2* psi;                 // probe waves of the launch's probe rows, [probe - gb_base gy npx][kW][kW]
 };
-constexpr int kGroupMaxProbes = 16, kGroupMaxEntries = 512;
-constexpr int kGroupDenseProbes = 4;  // probes per group of the kernel's accumulators (gx gy <= 4)
+constexpr int kGroupMaxEntries = 512;  // (probe, wave) entries of one group
+constexpr int kGroupDenseProbes = 4;   // probes per group of the kernel's accumulators (gx gy <= 4)
 constexpr int kGroupPosBias = 2048;   // translate placements in a group's frame lie in [-2048, 2048)
 size_t synth_group_smem_bytes();
 // grid_mode as for launch_synth (kSynthGridAuto: persistent)

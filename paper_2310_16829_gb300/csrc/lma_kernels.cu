@@ -2181,7 +2181,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
 // of its time on branches and instruction fetch.
 template <bool HALF>
 __global__ void __launch_bounds__(kThreads, 1) k_synth_group(const SynthArgs a, const GroupArgs g) {
-  constexpr int kQ = kGroupMaxProbes, kE = kGroupMaxEntries;
+  constexpr int kQ = kGroupDenseProbes, kE = kGroupMaxEntries;
   constexpr int kGQ = kGroupDenseProbes;   // accumulators per lane: every probe of the group
   static_assert(kE == kThreads, "one group entry per thread");
   extern __shared__ __align__(16) unsigned char smq[];
@@ -2846,7 +2846,7 @@ cudaError_t launch_synth(const SynthArgs& a, bool half, int mode, int grid_mode,
 }
 
 size_t synth_group_smem_bytes() {
-  return static_cast<size_t>(kGroupMaxEntries) * (8 + 16 * kGroupMaxProbes + 16) + 16 * kGroupMaxProbes +
+  return static_cast<size_t>(kGroupMaxEntries) * (8 + 16 * kGroupDenseProbes + 16) + 16 * kGroupDenseProbes +
          4 * (kThreads / 32);
 }
 
