@@ -1933,6 +1933,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
         al.x *= f;
         al.y *= f;
       }
+      const float4 al4 = make_float4(al.x, al.x, -al.y, al.y);   // cfma2's form of the coefficient
       const bool pair = (sh.x & 1) == 0;   // column pairs stay aligned and unbroken
       if (pair) {
         // all 16 loads of this translate first (pairs outside a non-periodic window read
@@ -2003,8 +2004,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
             f0 = make_float2(buf[b].x, buf[b].y);
             f1 = make_float2(buf[b].z, buf[b].w);
           }
-          acc[2 * b] = cfma(acc[2 * b], al, f0);
-          acc[2 * b + 1] = cfma(acc[2 * b + 1], al, f1);
+          acc[2 * b] = cfma2(acc[2 * b], al4, f0);
+          acc[2 * b + 1] = cfma2(acc[2 * b + 1], al4, f1);
         }
       } else {
 #pragma unroll
