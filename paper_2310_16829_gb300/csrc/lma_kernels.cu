@@ -1843,10 +1843,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice_rs(const SliceLaunch a, c
 // ------------------------------------------------------------------------------------------
 constexpr int kSynthSmemFloat2 = kX1 + kTwA + 128 + (kThreads / 32) * kMaxDet;
 
-// Zeros read by the synthesis in place of window columns outside a translate's window: 7 rows of
-// the widest window plus one aligned pair (zero-initialized device memory, never written)
-__device__ __align__(16) float2 g_zero_rows[8 * 256];
-
 // Probe of visit index q: the region is walked in vertical strips of sw columns (the
 // last strip narrower), row by row within a strip. The CTAs in flight then read the
 // exit waves of a compact patch of translates, which stays in L2 while the strip moves
@@ -1943,81 +1939,73 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth_detect(const SynthArgs a)
         // all 16 loads of this translate first (pairs outside a non-periodic window read
         // as zero), then the 32 complex FMAs; the FP16 store is kept packed until then
         using Raw = typename std::conditional<HALF, uint2, float4>::type;
-        auto products = [&](const Raw (&buf)[16]) {
-#pragma unroll
-          for (int b = 0; b < 16; ++b) {
-            float2 f0, f1;
-            if constexpr (HALF) {
-              f0 = __half22float2(*reinterpret_cast<const __half2*>(&buf[b].x));
-              f1 = __half22float2(*reinterpret_cast<const __half2*>(&buf[b].y));
-            } else {
-              f0 = make_float2(buf[b].x, buf[b].y);
-              f1 = make_float2(buf[b].z, buf[b].w);
-            }
-            acc[2 * b] = cfma2(acc[2 * b], al4, f0);
-            acc[2 * b + 1] = cfma2(acc[2 * b + 1], al4, f1);
-          }
-        };
+        Raw buf[16];
         if constexpr (!CYCLIC) {
-          // one pointer per translate, the 16 loads at fixed offsets (rows yl, halves kk)
+          // one pointer per translate, the 16 loads at fixed offsets (rows yl, halves kk);
+          // rows and columns outside the window are predicated off
           // element (y0 + yl, x0 + 64 kk) of translate ti is at signed offset base + yl W +
           // 64 kk; only offsets of rows and columns inside the window are dereferenced
           const int y0 = 8 * warp_id - sh.y, x0 = 2 * lane_id - sh.x;
           const long long base = static_cast<long long>(ti) * (Wu * Wu) + y0 * Wu + x0;
           const bool okx0 = static_cast<unsigned>(x0) < static_cast<unsigned>(Wu);
           const bool okx1 = static_cast<unsigned>(x0 + 64) < static_cast<unsigned>(Wu);
-          if (y0 >= 0 && y0 + 8 <= Wu) {
-            // the warp's 8 rows inside (warp-uniform): a column half outside the window reads
-            // the zero block instead, so no load needs a predicate or a zeroed register
-            using Elem = typename std::conditional<HALF, __half2, float2>::type;
-            const Elem* const zero = reinterpret_cast<const Elem*>(g_zero_rows);
-            const Elem* const src = HALF ? reinterpret_cast<const Elem*>(Uhc) : reinterpret_cast<const Elem*>(Uc);
-            const Elem* const c0 = okx0 ? src + base : zero;
-            const Elem* const c1 = okx1 ? src + base + 64 : zero;
-            Raw buf[16];
-#pragma unroll
-            for (int yl = 0; yl < 8; ++yl) {
-              buf[yl * 2] = *reinterpret_cast<const Raw*>(c0 + yl * Wu);
-              buf[yl * 2 + 1] = *reinterpret_cast<const Raw*>(c1 + yl * Wu);
-            }
-            products(buf);
-          } else {
-            // rows and columns outside the window are predicated off
-            Raw buf[16];
-#pragma unroll
-            for (int yl = 0; yl < 8; ++yl) {
-              const bool oky = static_cast<unsigned>(y0 + yl) < static_cast<unsigned>(Wu);
-#pragma unroll
-              for (int kk = 0; kk < 2; ++kk) {
-                Raw r{};
-                if (oky && (kk ? okx1 : okx0)) {
-                  const long long e = base + (yl * Wu + 64 * kk);
-                  if constexpr (HALF)
-                    r = *reinterpret_cast<const uint2*>(static_cast<const __half2*>(Uhc) + e);
-                  else
-                    r = *reinterpret_cast<const float4*>(Uc + e);
-                }
-                buf[yl * 2 + kk] = r;
-              }
-            }
-            products(buf);
-          }
-        } else {
-          Raw buf[16];
 #pragma unroll
           for (int yl = 0; yl < 8; ++yl) {
-            const int yy = (8 * warp_id + yl - sh.y) & (kW - 1);
-            const size_t off = static_cast<size_t>(ti) * (Wu * Wu) + yy * Wu;
+            const bool oky = static_cast<unsigned>(y0 + yl) < static_cast<unsigned>(Wu);
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
-              const int xp = (64 * kk + 2 * lane_id - sh.x) & (kW - 1);
-              if constexpr (HALF)
-                buf[yl * 2 + kk] = *reinterpret_cast<const uint2*>(static_cast<const __half2*>(Uhc) + off + xp);
-              else
-                buf[yl * 2 + kk] = *reinterpret_cast<const float4*>(Uc + off + xp);
+              Raw r{};
+              if (oky && (kk ? okx1 : okx0)) {
+                const long long e = base + (yl * Wu + 64 * kk);
+                if constexpr (HALF)
+                  r = *reinterpret_cast<const uint2*>(static_cast<const __half2*>(Uhc) + e);
+                else
+                  r = *reinterpret_cast<const float4*>(Uc + e);
+              }
+              buf[yl * 2 + kk] = r;
             }
           }
-          products(buf);
+        } else {
+#pragma unroll
+        for (int yl = 0; yl < 8; ++yl) {
+          int yy = 8 * warp_id + yl - sh.y;
+          bool ok = true;
+          if constexpr (CYCLIC)
+            yy &= (kW - 1);
+          else
+            ok = yy >= 0 && yy < Wu;
+          const size_t off = static_cast<size_t>(ti) * (Wu * Wu) + yy * Wu;
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            int xp = 64 * kk + 2 * lane_id - sh.x;
+            bool okx = ok;
+            if constexpr (CYCLIC)
+              xp &= (kW - 1);
+            else
+              okx = okx && xp >= 0 && xp < Wu;
+            Raw r{};
+            if (okx) {
+              if constexpr (HALF)
+                r = *reinterpret_cast<const uint2*>(static_cast<const __half2*>(Uhc) + off + xp);
+              else
+                r = *reinterpret_cast<const float4*>(Uc + off + xp);
+            }
+            buf[yl * 2 + kk] = r;
+          }
+        }
+        }
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+          float2 f0, f1;
+          if constexpr (HALF) {
+            f0 = __half22float2(*reinterpret_cast<const __half2*>(&buf[b].x));
+            f1 = __half22float2(*reinterpret_cast<const __half2*>(&buf[b].y));
+          } else {
+            f0 = make_float2(buf[b].x, buf[b].y);
+            f1 = make_float2(buf[b].z, buf[b].w);
+          }
+          acc[2 * b] = cfma2(acc[2 * b], al4, f0);
+          acc[2 * b + 1] = cfma2(acc[2 * b + 1], al4, f1);
         }
       } else {
 #pragma unroll
