@@ -350,3 +350,18 @@ def test_synth_tuning_read_reports_nothing_before_tuning():
     assert ctx.synth_tuning() == []
     n = ctypes.c_int32()
     assert ctx.lib.lma_synth_tuning_read(ctx.h, None, 1, ctypes.byref(n)) == lma.LMA_ERR_INVALID
+
+
+def test_synth_form_and_buffer_limit_arguments():
+    """lma_set_synth_mode takes LMA_SYNTH_AUTO, _GATHER and _GROUPED only, and
+    lma_set_synth_buffer_limit a byte count >= 0 (0 restores the default); both are context
+    state, set without a device."""
+    ctx = lma.Context(-1)
+    for m in (lma.LMA_SYNTH_GATHER, lma.LMA_SYNTH_GROUPED, lma.LMA_SYNTH_AUTO):
+        ctx.set_synth_mode(m)
+    for m in (-2, 2):
+        assert ctx.lib.lma_set_synth_mode(ctx.h, m) == lma.LMA_ERR_INVALID
+    ctx.set_synth_buffer_limit(1 << 20)
+    ctx.set_synth_buffer_limit(0)
+    assert ctx.lib.lma_set_synth_buffer_limit(ctx.h, -1) == lma.LMA_ERR_INVALID
+    assert ctx.lib.lma_set_synth_mode(None, 0) == lma.LMA_ERR_INVALID
