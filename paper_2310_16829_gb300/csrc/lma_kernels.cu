@@ -98,15 +98,6 @@ __device__ __forceinline__ int c_column(int T) {
   return 32 * w + l;
 }
 
-// c_column of the thread whose lane has bits 3 and 4 swapped: each warp keeps its set of
-// columns (so the fully masked warps stay fully masked) and lane l gets k1x = l with those
-// bits swapped. The C layout of k_slice, whose exchange rows hold k1 in the order 0, 16, 1,
-// 17, ...: a half-warp then reads 16 consecutive entries of a row, on 16 distinct bank pairs.
-__device__ __forceinline__ int c_column_paired(int T) {
-  const int l = T & 31;
-  return c_column((T & ~31) | (l & 7) | ((l & 8) << 1) | ((l & 16) >> 1));
-}
-
 // compile-time loop: f(std::integral_constant<int, I>) for I = B..E-1
 template <int B, int E, class F>
 __device__ __forceinline__ void static_for(F&& f) {
@@ -511,10 +502,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
   const int ya = T >> 2, ra = T & 3;
   // B layout: groups (k1 = (T & 15) + 16 h, n2y = T >> 4), h = 0, 1
   const int k1lo = T & 15, n2y = T >> 4;
-  // C layout: thread (kx, k1y), kx permuted within each k1y group (c_column), then bits 3
-  // and 4 of k1x swapped, so that a half-warp's 16 entries k1x lie in one 16-entry half of
-  // the row layout below
-  const int kx = c_column_paired(T), k1y = T >> 7, k1x = kx & 31, k2x = kx >> 5;
+  // C layout: thread (kx, k1y), kx permuted within each k1y group (c_column)
+  const int kx = c_column(T), k1y = T >> 7, k1x = kx & 31, k2x = kx >> 5;
   const float2* tB = twB + n2y * 4;
   const int kxs = kx < 64 ? kx : kx - 128;
   // entry j of this C thread: ky = k1y + 4 j, |ky| = k1y + 4 j (j < 16), 128 - k1y - 4 j
@@ -524,11 +513,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
   int cur_job = -1;
   __shared__ int s_next;
   __shared__ int s_wmax;      // FP16 store: bits of the wave's largest |component| (order-preserving for >= 0)
-  // Spectral entries of a row in the order k1 = 0, 16, 1, 17, ...: entry 2 m + h holds
-  // k1 = m + 16 h, so the two values of a pass-B thread (k1lo, k1lo + 16) are one 16-byte pair
-  float2* const xa = X + T * kXP;                                 // A row: pair m = (k1 = m, m + 16)
-  float4* const xb = reinterpret_cast<float4*>(X + (4 * n2y) * kXP) + k1lo;   // B pair (q, r): + (128 q + r) * kXP / 2
-  float2* const xc = X + (128 * k2x + k1y) * kXP + 2 * (k1x & 15) + (k1x >> 4);   // C entry j: + 4 j * kXP
+  float2* const xa = X + T * kXP;                                 // A row, + n or k1
+  float2* const xb = X + (4 * n2y) * kXP + k1lo;                  // B slot (q, r): + (128 q + r) * kXP, + 16 (h = 1)
+  float2* const xc = X + (128 * k2x + k1y) * kXP + k1x;           // C entry j: + 4 j * kXP
   const int lane = T & 31;
   float2* const xw = X + (T >> 5) * (32 * kXP);                   // this warp's table rows
   const float2* const tr = xw + (ya & 7) * kTRow + ra;            // t(y, 4 n + r) at + 4 n
@@ -591,16 +578,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
       __syncwarp();
       float4* const xa4 = reinterpret_cast<float4*>(xa);
 #pragma unroll
-      for (int m = 0; m < 16; ++m) xa4[m] = make_float4(v[m].x, v[m].y, v[m + 16].x, v[m + 16].y);
+      for (int k = 0; k < 32; k += 2) xa4[k / 2] = make_float4(v[k].x, v[k].y, v[k + 1].x, v[k + 1].y);
       __syncthreads();
       float2 b0[16], b1[16];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          const float4 p = xb[(128 * q + r) * (kXP / 2)];
-          b0[q * 4 + r] = make_float2(p.x, p.y);
-          b1[q * 4 + r] = make_float2(p.z, p.w);
+          b0[q * 4 + r] = xb[(128 * q + r) * kXP];
+          b1[q * 4 + r] = xb[(128 * q + r) * kXP + 16];
         }
       passB_fwd_tw<false, PRUNE>(b0, tB, twr[k1lo], twr[32 + k1lo]);
       passB_fwd_tw<true, PRUNE>(b1, tB, twr[16 + k1lo], twr[48 + k1lo]);
@@ -608,16 +594,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
       // (pass C finds finite values of this slice's X1 there and multiplies them by zero)
       static_for<0, 4>([&](auto qq) {
         constexpr int q = decltype(qq)::value;
-        constexpr bool w0 = q != masked_k2x<false, PRUNE>(), w1 = q != masked_k2x<true, PRUNE>();
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          float4* const d = xb + (128 * q + r) * (kXP / 2);
-          if constexpr (w0 && w1)
-            *d = make_float4(b0[r * 4 + q].x, b0[r * 4 + q].y, b1[r * 4 + q].x, b1[r * 4 + q].y);
-          else if constexpr (w0)
-            reinterpret_cast<float2*>(d)[0] = b0[r * 4 + q];
-          else if constexpr (w1)
-            reinterpret_cast<float2*>(d)[1] = b1[r * 4 + q];
+          if constexpr (q != masked_k2x<false, PRUNE>()) xb[(128 * q + r) * kXP] = b0[r * 4 + q];
+          if constexpr (q != masked_k2x<true, PRUNE>()) xb[(128 * q + r) * kXP + 16] = b1[r * 4 + q];
         }
       });
       __syncthreads();
@@ -640,19 +620,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
       __syncthreads();
       static_for<0, 4>([&](auto qq) {
         constexpr int q = decltype(qq)::value;
-        constexpr bool w0 = q != masked_k2x<false, PRUNE>(), w1 = q != masked_k2x<true, PRUNE>();
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          const float4* const d = xb + (128 * q + r) * (kXP / 2);
-          if constexpr (w0 && w1) {
-            const float4 p = *d;
-            b0[r * 4 + q] = make_float2(p.x, p.y);
-            b1[r * 4 + q] = make_float2(p.z, p.w);
-          } else if constexpr (w0) {
-            b0[r * 4 + q] = reinterpret_cast<const float2*>(d)[0];
-          } else if constexpr (w1) {
-            b1[r * 4 + q] = reinterpret_cast<const float2*>(d)[1];
-          }
+          if constexpr (q != masked_k2x<false, PRUNE>()) b0[r * 4 + q] = xb[(128 * q + r) * kXP];
+          if constexpr (q != masked_k2x<true, PRUNE>()) b1[r * 4 + q] = xb[(128 * q + r) * kXP + 16];
         }
       });
       passB_inv_tw<false, PRUNE>(b0, tB, twr[k1lo], twr[32 + k1lo]);
@@ -661,16 +632,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-          xb[(128 * q + r) * (kXP / 2)] = make_float4(b0[q * 4 + r].x, b0[q * 4 + r].y, b1[q * 4 + r].x, b1[q * 4 + r].y);
+        for (int r = 0; r < 4; ++r) {
+          xb[(128 * q + r) * kXP] = b0[q * 4 + r];
+          xb[(128 * q + r) * kXP + 16] = b1[q * 4 + r];
+        }
       __syncthreads();
       {
         const float4* const xa4 = reinterpret_cast<const float4*>(xa);
 #pragma unroll
-        for (int m = 0; m < 16; ++m) {
-          const float4 p = xa4[m];
-          v[m] = make_float2(p.x, p.y);
-          v[m + 16] = make_float2(p.z, p.w);
+        for (int k = 0; k < 32; k += 2) {
+          const float4 p = xa4[k / 2];
+          v[k] = make_float2(p.x, p.y);
+          v[k + 1] = make_float2(p.z, p.w);
         }
       }
       // the warp's rows are free again once every lane has read them: prefetch the next
