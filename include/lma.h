@@ -191,7 +191,8 @@ typedef struct {
 /* Create a context on CUDA device `device` (or a host-only context with device = -1).
  * A context and the specimens and bases made in it serve one host thread: its calls
  * must not overlap in time, also not on different streams (the slice work counter, the
- * item-list cache and the pinned staging buffer of host copies belong to the context).
+ * item-list cache, the pinned staging buffer of host copies and the grouped synthesis's
+ * probe-wave buffer belong to the context).
  * Use one context per thread for concurrent work.
  * Errors: LMA_ERR_CUDA if the device cannot be selected, LMA_ERR_OOM. */
 lma_status lma_create(int32_t device, lma_ctx** out);
