@@ -458,16 +458,6 @@ static_assert(8 * kTRow <= 32 * kXP, "a warp's 8 transmission rows fit its 32 ta
 // the 16 consecutive a of a half-warp over distinct bank pairs
 constexpr int kPRow = 65;
 constexpr int kPTab = kPRow * kPRow;
-// row of |kx| in k_slice's propagator table: rows 49..53 and 59..63 swapped (an involution).
-// The half-warp of pass C that holds |kx| = 32..42 and 49..53 then reads 16 rows on 16
-// distinct bank pairs (49..53 fell on the bank pairs of 33..37), and so do the half-warps
-// holding 43..47 and 54..64 when the bandlimit leaves them unmasked.
-__host__ __device__ constexpr int prow(int a) {
-  return (a >= 49 && a <= 53) ? a + 10 : ((a >= 59 && a <= 63) ? a - 10 : a);
-}
-static_assert(prow(49) == 59 && prow(63) == 53 && prow(prow(51)) == 51 && prow(48) == 48 && prow(54) == 54 &&
-                  prow(64) == 64,
-              "prow is the swap of rows 49..53 and 59..63");
 constexpr int kSliceSmemFloat2 = kXRows + 128 + 128 + kPTab;
 
 // Warp w copies window rows 8 w .. 8 w + 7 of one slice (g points at the first) into its
@@ -517,8 +507,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
   const float2* tB = twB + n2y * 4;
   const int kxs = kx < 64 ? kx : kx - 128;
   // entry j of this C thread: ky = k1y + 4 j, |ky| = k1y + 4 j (j < 16), 128 - k1y - 4 j
-  const float2* const pp = ptab + prow(kxs < 0 ? -kxs : kxs) * kPRow + k1y;            // + 4 j
-  const float2* const pm = ptab + prow(kxs < 0 ? -kxs : kxs) * kPRow + 128 - k1y;      // - 4 j
+  const float2* const pp = ptab + (kxs < 0 ? -kxs : kxs) * kPRow + k1y;            // + 4 j
+  const float2* const pm = ptab + (kxs < 0 ? -kxs : kxs) * kPRow + 128 - k1y;      // - 4 j
   bool c_live = false;
   int cur_job = -1;
   __shared__ int s_next;
@@ -551,7 +541,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_slice(const SliceLaunch a, cons
       // below publishes it before pass C reads it
       cur_job = jb;
       for (int e = T; e < kPTab; e += kThreads) {
-        const int pr = e / kPRow, pb = e - pr * kPRow, pa = prow(pr);   // row pr holds |kx| = prow(pr)
+        const int pa = e / kPRow, pb = e - pa * kPRow;
         ptab[e] = pa * pa + pb * pb <= J.r2max ? cmul(J.ex[pa], J.ey[pb]) : make_float2(0.f, 0.f);
       }
       // a warp whose columns are all outside the bandlimit skips pass C: its spectrum is zero
